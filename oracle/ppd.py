@@ -1,0 +1,185 @@
+"""Preconditioned primal-dual iteration (Algorithm 3) in plain FP64.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Paper passages: Algorithm 3 (Section 4) with lambda = 1 and no randomised
+active sets (Section 5.1); the dual data step through the generalised Moreau
+identity (Eq. "generalised-proximity-operator-decomposition") and the
+ellipsoid prox (Section 4.1, Algorithm 2); the prior step (I - S_k) with
+threshold kappa ||Psi W||_S^2 (Section 4.2); parameters tau = 0.49,
+zeta = 1/||Psi||_S^2, eta = 1/||U^{1/2} Phi||_S^2, kappa = 1e-4 (Section 5.1);
+eps^2 two standard deviations above the chi^2 mean (Section 5.1);
+the convergence condition (Eq. "convergence-req-explicit-pd").
+
+Readings (the paper is silent or its printed step is garbled):
+
+* Dual step (Algorithm 3, data update): with z = U^{-1} v + Theta G a the
+  update is vbar = U (z - p), p = prox^U_h(z) computed by Algorithm 2; this
+  is the generalised Moreau identity with alpha = 1 after the rescaling
+  v <- v/eta that puts eta in the primal step.
+* Algorithm 2 starts from the previous iteration's p (warm start) and, on
+  the first iteration, from P_B(z).  n_itr fixed (default 1).
+* mu_j = 1/max_e(U_j,e)^2 (Algorithm 2, as printed).
+* Per-block bound eps_j^2 = M_j + 2 sqrt(M_j) in whitened units (the
+  chi^2 rule applied per block; y whitened as Theta y).
+* Initial state x = xt = 0, u = 0, v = 0.
+* Power iteration for ||U^{1/2} Phi||_S^2 on Phi^dagger U Phi from the
+  all-ones vector, stopped at relative change < 1e-10 or 1000 steps.
+
+Parity: the invariants of the whole iteration (feasibility, positivity,
+PPD and PD reaching the same minimiser, U = I reducing to PD) are pinned by
+tests; the trajectory itself is "parity unpinned" beyond them.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+from . import nufft, prox, sara
+
+
+def eps_chi2(block: np.ndarray, n_blocks: int) -> np.ndarray:
+    """eps_j = sqrt(M_j + 2 sqrt(M_j)) (whitened noise: ||n_j||^2 ~ chi^2 with mean M_j, std sqrt(M_j))."""
+    Mj = np.bincount(np.asarray(block, np.int64), minlength=n_blocks).astype(np.float64)
+    return np.sqrt(Mj + 2.0 * np.sqrt(Mj))
+
+
+def op_norm_sq(P: nufft.Plan, U: np.ndarray, max_iter: int = 1000, tol: float = 1e-10,
+               start: np.ndarray | None = None):
+    """||U^{1/2} Phi||_S^2 by power iteration on Phi^dagger U Phi. Returns (value, iterations)."""
+    x = np.ones((P.L0, P.L1)) if start is None else np.array(start, dtype=np.float64)
+    x /= np.linalg.norm(x)
+    val = 0.0
+    for it in range(1, max_iter + 1):
+        y = nufft.phi_adjoint(U * nufft.phi(x, P), P)
+        new = float(np.linalg.norm(y))
+        x = y / new
+        if abs(new - val) <= tol * new:
+            return new, it
+        val = new
+    return val, max_iter
+
+
+@dataclasses.dataclass
+class Setup:
+    P: nufft.Plan
+    yw: np.ndarray          # whitened data Theta y
+    U: np.ndarray           # preconditioner diagonal
+    block: np.ndarray
+    n_blocks: int
+    eps: np.ndarray         # per block
+    mu: np.ndarray          # per block
+    eta: float
+    zeta: float = 1.0
+    tau: float = 0.49
+    kappa: float = 1e-4
+    n_itr: int = 1
+    levels: int = 4
+    x_true: np.ndarray | None = None
+
+    def __post_init__(self):
+        self.members = [np.flatnonzero(self.block == j) for j in range(self.n_blocks)]
+        self.hs = sara.filters()
+
+
+def make_setup(omega, y, theta, block, n_blocks, L, *, precond: bool = True,
+               eta: float | None = None, eps=None, U=None, n_itr: int = 1,
+               tau: float = 0.49, kappa: float = 1e-4, x_true=None,
+               power_iters: int = 1000) -> Setup:
+    P = nufft.Plan(omega, L, L, theta=theta)
+    if U is None:
+        U = nufft.uniform_weights(omega, P.K0, P.K1)[0] if precond else np.ones(P.M)
+    U = np.asarray(U, dtype=np.float64)
+    block = np.asarray(block, np.int64)
+    eps = eps_chi2(block, n_blocks) if eps is None else np.asarray(eps, np.float64)
+    mu = np.ones(n_blocks)
+    for j in range(n_blocks):
+        sel = block == j
+        if np.any(sel):
+            mu[j] = 1.0 / float(np.max(U[sel])) ** 2
+    if eta is None:
+        eta = 1.0 / op_norm_sq(P, U, max_iter=power_iters)[0]
+    return Setup(P=P, yw=np.asarray(theta) * np.asarray(y), U=U, block=block,
+                 n_blocks=n_blocks, eps=eps, mu=mu, eta=float(eta), tau=tau, kappa=kappa,
+                 n_itr=n_itr, x_true=x_true)
+
+
+def convergence_lhs(S: Setup, psi_norm_sq: float = 1.0, phi_norm_sq: float | None = None):
+    """tau zeta ||Psi||^2 + tau eta ||U^{1/2} Phi||^2 (must be < 1)."""
+    if phi_norm_sq is None:
+        phi_norm_sq = 1.0 / S.eta
+    return S.tau * S.zeta * psi_norm_sq + S.tau * S.eta * phi_norm_sq
+
+
+@dataclasses.dataclass
+class State:
+    x: np.ndarray
+    xt: np.ndarray
+    u: np.ndarray
+    v: np.ndarray
+    p: np.ndarray | None = None
+    t: int = 0
+
+
+def init_state(S: Setup) -> State:
+    L0, L1 = S.P.L0, S.P.L1
+    return State(x=np.zeros((L0, L1)), xt=np.zeros((L0, L1)),
+                 u=np.zeros((sara.N_BASES, L0, L1)), v=np.zeros(S.P.M, np.complex128))
+
+
+def iterate(st: State, S: Setup) -> dict:
+    """One iteration of Algorithm 3 (lambda = 1, all blocks and bases active)."""
+    P = S.P
+    # forward: a = F Z xt, Theta G a
+    phix = P.theta * nufft.interpolate(np.fft.fft2(nufft.zero_pad_scale(st.xt, P)), P)
+    res = np.array([np.linalg.norm(phix[m] - S.yw[m]) for m in S.members])
+    # dual data step (Algorithm 2 inside the Moreau identity)
+    z = st.v / S.U + phix
+    p = np.empty_like(z)
+    for j, m in enumerate(S.members):
+        if m.size == 0:
+            continue
+        if st.p is None:
+            start = prox.proj_l2ball(z[m], S.yw[m], S.eps[j])
+        else:
+            start = st.p[m]
+        p[m] = prox.ellipsoid_prox_fb(z[m], S.yw[m], S.eps[j], S.U[m], S.n_itr,
+                                      start=start, mu=S.mu[j])
+    v = S.U * (z - p)
+    g = nufft.phi_adjoint(v, P)
+    # prior step: clip (I - S_kappa) of u + Psi^dagger xt, then synthesis
+    c = sara.psi_adjoint(st.xt, S.levels, S.hs)
+    u = prox.clip_complement(st.u + c, S.kappa * 1.0)
+    ut = sara.psi(u, S.levels, S.hs)
+    # primal step
+    xbar = prox.proj_positive(st.x - S.tau * (S.eta * g + S.zeta * ut))
+    dx = float(np.linalg.norm(xbar - st.x))
+    nx = float(np.linalg.norm(xbar))
+    xt = 2.0 * xbar - st.x
+    st.x, st.xt, st.u, st.v, st.p = xbar, xt, u, v, p
+    st.t += 1
+    stats = dict(residual=res, rel_var=dx / nx if nx > 0 else float("inf"))
+    if S.x_true is not None:
+        stats["snr"] = snr(S.x_true, xbar)
+    return stats
+
+
+def run(S: Setup, n_iters: int, st: State | None = None):
+    st = init_state(S) if st is None else st
+    hist = []
+    for _ in range(n_iters):
+        hist.append(iterate(st, S))
+    return st, hist
+
+
+def snr(x_true: np.ndarray, x: np.ndarray) -> float:
+    """SNR = 20 log10(||x_true|| / ||x_true - x||) (Section 5)."""
+    den = float(np.linalg.norm(x_true - x))
+    return 20.0 * math.log10(float(np.linalg.norm(x_true)) / den) if den > 0 else float("inf")
+
+
+def l1_objective(x: np.ndarray, levels: int = 4) -> float:
+    """||Psi^dagger x||_1, the objective of the minimisation problem."""
+    return float(np.sum(np.abs(sara.psi_adjoint(x, levels))))

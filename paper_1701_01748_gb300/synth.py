@@ -1,0 +1,174 @@
+"""Seeded synthetic radio-interferometric problems.
+
+This module makes the *inputs* of the imaging problem and nothing else: a
+positive sky image, the u-v sampling, the data-block split, the noisy
+visibilities and the noise level.  It holds none of the solver's arithmetic
+(no interpolation kernel, no oversampled FFT, no preconditioner, no bound on
+the noise norm), so the FP64 oracle and the CUDA library can both be fed from
+it without sharing any of the method.
+
+Visibilities are the exact measurement of the pixelised sky,
+``y_m = sum_n x[n] exp(-i <omega_m, n - L/2>)`` (the discretised measurement
+equation of Section 2, with DDEs ignored as in the paper's simulations),
+plus circular complex Gaussian noise whose power is set from the noise-free
+signal power for a given input SNR (Section 5, "iSNR").  The sum is evaluated
+exactly: point sources one by one, the smooth Gaussian blobs through a
+truncated SVD of their pixel image (the DTFT is separable per rank-one term).
+
+The shapes stand in for the paper's workloads (its images and coverages are
+not available): point sources plus elliptical Gaussian blobs for the sky, a
+Gaussian u-v density (the paper's generalised Gaussian with shape 2) whose
+width sets how non-uniform the sampling is, and radial u-v bands as uneven
+data blocks.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+__all__ = ["Problem", "CONFIGS", "make_problem", "sky_image", "sample_uv",
+           "radial_blocks", "exact_visibilities"]
+
+
+@dataclasses.dataclass
+class Problem:
+    """One synthetic imaging problem (all arrays FP64 / int32, host)."""
+    name: str
+    L: int                    # image side (square images, L x L)
+    x_true: np.ndarray        # (L, L) float64, >= 0
+    omega: np.ndarray         # (M, 2) float64 in [-pi, pi); col 0 -> image rows
+    y: np.ndarray             # (M,) complex128, raw (un-whitened) visibilities
+    sigma: float              # noise standard deviation of each complex visibility
+    theta: np.ndarray         # (M,) float64 natural weights 1/sigma_e
+    block: np.ndarray         # (M,) int32 data-block id in [0, n_blocks)
+    n_blocks: int
+    isnr_db: float
+    seed: int
+
+    @property
+    def M(self) -> int:
+        return int(self.omega.shape[0])
+
+
+# Workload shapes.  uv_sigma is the std of omega per axis in units of pi.
+CONFIGS = {
+    # 128x128, 8192 visibilities, one block, broad Gaussian coverage
+    "c1_128": dict(L=128, M=8192, n_blocks=1, uv_sigma=0.25, seed=1701),
+    # 512x512, 524288 visibilities, strongly non-uniform, 16 radial blocks
+    "c2_512": dict(L=512, M=524288, n_blocks=16, uv_sigma=0.1, seed=1702),
+    # 1024x1024, 4M visibilities, 64 radial blocks
+    "c3_1024": dict(L=1024, M=4194304, n_blocks=64, uv_sigma=0.1, seed=1703),
+}
+
+
+def sky_image(L: int, rng: np.random.Generator, n_points: int = 20,
+              n_blobs: int = 3):
+    """Positive test sky: point sources plus elliptical Gaussian blobs.
+
+    Returns (points, blob_image): points is a list of (row, col, flux) with
+    integer pixel positions (collisions add), blob_image is (L, L) float64.
+    Point fluxes are log-uniform in [1e-3, 1]; blob centres uniform in the
+    central half, major-axis std uniform in [0.02L, 0.08L], axis ratio uniform
+    in [0.3, 1], position angle uniform in [0, pi), peak log-uniform in
+    [1e-2, 1e-1].
+    """
+    pos = rng.integers(0, L, size=(n_points, 2))
+    flux = 10.0 ** rng.uniform(-3.0, 0.0, size=n_points)
+    points = [(int(p[0]), int(p[1]), float(f)) for p, f in zip(pos, flux)]
+    r = np.arange(L, dtype=np.float64)
+    R0, R1 = np.meshgrid(r, r, indexing="ij")
+    blob = np.zeros((L, L))
+    for _ in range(n_blobs):
+        c0, c1 = rng.uniform(L / 4, 3 * L / 4, size=2)
+        smaj = rng.uniform(0.02 * L, 0.08 * L)
+        smin = smaj * rng.uniform(0.3, 1.0)
+        ang = rng.uniform(0.0, math.pi)
+        peak = 10.0 ** rng.uniform(-2.0, -1.0)
+        ca, sa = math.cos(ang), math.sin(ang)
+        d0, d1 = R0 - c0, R1 - c1
+        a = ca * d0 + sa * d1
+        b = -sa * d0 + ca * d1
+        blob += peak * np.exp(-0.5 * ((a / smaj) ** 2 + (b / smin) ** 2))
+    return points, blob
+
+
+def sample_uv(M: int, uv_sigma: float, rng: np.random.Generator) -> np.ndarray:
+    """omega ~ N(0, (uv_sigma*pi)^2) per axis, redrawn until inside [-pi, pi)^2."""
+    out = np.empty((0, 2))
+    while out.shape[0] < M:
+        need = M - out.shape[0]
+        s = rng.normal(0.0, uv_sigma * math.pi, size=(need + need // 8 + 16, 2))
+        ok = np.all((s >= -math.pi) & (s < math.pi), axis=1)
+        out = np.concatenate([out, s[ok]], axis=0)
+    return np.ascontiguousarray(out[:M])
+
+
+def radial_blocks(omega: np.ndarray, n_blocks: int) -> np.ndarray:
+    """Uneven data blocks: equal-width radial bands of |omega| (FP64)."""
+    r = np.hypot(omega[:, 0], omega[:, 1])
+    rmax = float(r.max()) if r.size else 1.0
+    b = np.floor(n_blocks * r / rmax).astype(np.int64)
+    return np.minimum(b, n_blocks - 1).astype(np.int32)
+
+
+def _phase_rows(w: np.ndarray, L: int) -> np.ndarray:
+    """exp(-i w (n - L/2)) for n = 0..L-1, as an (m, L) array.
+
+    Built as an outer product of a coarse and a fine factor (n = S*a + b) so
+    that only m*(L/S + S) complex exponentials are evaluated.
+    """
+    S = 32 if L % 32 == 0 else 1
+    a = np.arange(L // S, dtype=np.float64) * S
+    b = np.arange(S, dtype=np.float64)
+    A = np.exp(-1j * w[:, None] * (a[None, :] - L / 2))
+    B = np.exp(-1j * w[:, None] * b[None, :])
+    return (A[:, :, None] * B[:, None, :]).reshape(w.shape[0], L)
+
+
+def exact_visibilities(points, blob: np.ndarray, omega: np.ndarray,
+                       chunk: int = 8192) -> np.ndarray:
+    """Exact y_m = sum_n x[n] exp(-i <omega_m, n - L/2>) of the pixel sky."""
+    L = blob.shape[0]
+    M = omega.shape[0]
+    y = np.zeros(M, dtype=np.complex128)
+    for (p0, p1, f) in points:
+        y += f * np.exp(-1j * (omega[:, 0] * (p0 - L / 2) + omega[:, 1] * (p1 - L / 2)))
+    if np.any(blob):
+        U, s, Vt = np.linalg.svd(blob)
+        r = int(np.sum(s > s[0] * 1e-15))
+        Us = U[:, :r] * s[None, :r]
+        V = Vt[:r, :].T
+        for i in range(0, M, chunk):
+            w = omega[i:i + chunk]
+            e0 = _phase_rows(w[:, 0], L) @ Us
+            e1 = _phase_rows(w[:, 1], L) @ V
+            y[i:i + chunk] += np.sum(e0 * e1, axis=1)
+    return y
+
+
+def make_problem(name: str = "c1_128", *, L: int | None = None, M: int | None = None,
+                 n_blocks: int | None = None, uv_sigma: float | None = None,
+                 seed: int | None = None, isnr_db: float = 30.0,
+                 n_points: int = 20, n_blobs: int = 3) -> Problem:
+    """Build a seeded problem; keyword arguments override the named shape."""
+    cfg = dict(CONFIGS.get(name, CONFIGS["c1_128"]))
+    for k, v in dict(L=L, M=M, n_blocks=n_blocks, uv_sigma=uv_sigma, seed=seed).items():
+        if v is not None:
+            cfg[k] = v
+    rng = np.random.default_rng(cfg["seed"])
+    Lv = int(cfg["L"])
+    points, blob = sky_image(Lv, rng, n_points=n_points, n_blobs=n_blobs)
+    x = blob.copy()
+    for (p0, p1, f) in points:
+        x[p0, p1] += f
+    omega = sample_uv(int(cfg["M"]), float(cfg["uv_sigma"]), rng)
+    block = radial_blocks(omega, int(cfg["n_blocks"]))
+    y0 = exact_visibilities(points, blob, omega)
+    Mv = omega.shape[0]
+    sigma = math.sqrt(float(np.vdot(y0, y0).real) / Mv * 10.0 ** (-isnr_db / 10.0))
+    noise = sigma * (rng.normal(size=Mv) + 1j * rng.normal(size=Mv)) / math.sqrt(2.0)
+    return Problem(name=name, L=Lv, x_true=x, omega=omega, y=y0 + noise, sigma=sigma,
+                   theta=np.full(Mv, 1.0 / sigma), block=block,
+                   n_blocks=int(cfg["n_blocks"]), isnr_db=isnr_db, seed=int(cfg["seed"]))

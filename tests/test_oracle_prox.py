@@ -1,0 +1,91 @@
+"""Pins of the oracle's proximity operators (Section 3.3, Section 4.1, Algorithm 2)."""
+import numpy as np
+import pytest
+from scipy import optimize
+
+from oracle import prox
+
+
+def test_positive_projection_by_hand():
+    z = np.array([1.5 + 2j, -0.5 + 1j, 0.0, 3.0 - 7j])
+    assert np.array_equal(prox.proj_positive(z), [1.5, 0.0, 0.0, 3.0])
+
+
+def test_soft_threshold_by_hand():
+    z = np.array([3.0, -0.5, 0.0, -2.0, 3 + 4j])
+    out = prox.soft(z, 1.0)
+    assert np.allclose(out, [2.0, 0.0, 0.0, -1.0, (3 + 4j) * 4 / 5], rtol=0, atol=1e-15)
+    # (I - S_alpha) is the clip for real input
+    r = np.array([3.0, -0.5, 0.0, -2.0, 0.99])
+    assert np.array_equal(prox.clip_complement(r, 1.0), np.clip(r, -1.0, 1.0))
+
+
+def test_l2_ball_projection_by_hand():
+    y = np.array([1.0 + 0j, 0.0])
+    z = np.array([4.0 + 0j, 4.0j])           # ||z - y|| = 5
+    p = prox.proj_l2ball(z, y, 2.5)
+    assert np.allclose(p, [1.0 + 1.5, 2.0j], rtol=0, atol=1e-15)
+    inside = np.array([1.1 + 0j, 0.1j])
+    assert np.array_equal(prox.proj_l2ball(inside, y, 2.5), inside)
+
+
+def _block(seed, m=12, cond=4.0):
+    rng = np.random.default_rng(seed)
+    y = rng.normal(size=m) + 1j * rng.normal(size=m)
+    z = y + 3.0 * (rng.normal(size=m) + 1j * rng.normal(size=m))
+    U = rng.uniform(1.0 / cond, 1.0, size=m)
+    return z, y, U
+
+
+def test_exact_ellipsoid_prox_matches_generic_solver():
+    z, y, U = _block(1, m=6)
+    eps = 1.5
+    p, lam = prox.ellipsoid_prox_exact(z, y, eps, U)
+    # independent: SLSQP on the real-packed problem
+    def obj(q):
+        pc = q[:6] + 1j * q[6:]
+        return 0.5 * float(np.sum(U * np.abs(z - pc) ** 2))
+    cons = {"type": "ineq", "fun": lambda q: eps ** 2 - float(np.sum(np.abs(q[:6] + 1j * q[6:] - y) ** 2))}
+    q0 = np.concatenate([y.real, y.imag])
+    res = optimize.minimize(obj, q0, constraints=[cons], method="SLSQP",
+                            options=dict(ftol=1e-15, maxiter=500))
+    pq = res.x[:6] + 1j * res.x[6:]
+    assert np.abs(pq - p).max() <= 1e-5
+
+
+@pytest.mark.parametrize("seed", [2, 3, 4])
+def test_exact_ellipsoid_prox_kkt(seed):
+    z, y, U = _block(seed, m=20)
+    eps = 2.0
+    p, lam = prox.ellipsoid_prox_exact(z, y, eps, U)
+    assert lam > 0
+    assert abs(np.linalg.norm(p - y) - eps) <= 1e-12 * eps
+    assert np.abs(U * (z - p) - lam * (p - y)).max() <= 1e-12 * np.abs(U * (z - p)).max()
+
+
+@pytest.mark.parametrize("seed", [5, 6, 7])
+def test_algorithm2_converges_to_exact_prox(seed):
+    z, y, U = _block(seed, m=64, cond=3.0)
+    eps = 4.0
+    p_exact, _ = prox.ellipsoid_prox_exact(z, y, eps, U)
+    p_fb = prox.ellipsoid_prox_fb(z, y, eps, U, n_itr=5000)
+    assert np.abs(p_fb - p_exact).max() <= 1e-8 * np.abs(p_exact).max()
+
+
+def test_identity_metric_reduces_to_ball_projection():
+    z, y, _ = _block(8, m=16)
+    U = np.ones(16)
+    start = y + 100.0        # any start: one step with mu = 1 lands on P_B(z)
+    p = prox.ellipsoid_prox_fb(z, y, 1.0, U, n_itr=1, start=start)
+    assert np.allclose(p, prox.proj_l2ball(z, y, 1.0), rtol=0, atol=1e-14)
+    p_exact, _ = prox.ellipsoid_prox_exact(z, y, 1.0, U)
+    assert np.allclose(p_exact, prox.proj_l2ball(z, y, 1.0), rtol=0, atol=1e-12)
+
+
+def test_inside_the_ball_the_prox_is_the_point():
+    z, y, U = _block(9, m=8)
+    z = y + 1e-3
+    p = prox.ellipsoid_prox_fb(z, y, 1.0, U, n_itr=3, start=z)
+    assert np.array_equal(p, z)
+    p2 = prox.ellipsoid_prox_fb(z, y, 1.0, U, n_itr=4000, start=y)
+    assert np.abs(p2 - z).max() <= 1e-12
