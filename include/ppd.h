@@ -1,0 +1,227 @@
+/*
+ * ppd.h -- C ABI of libppd: the preconditioned primal-dual (PPD) solver for
+ * radio-interferometric imaging on one GB300 (sm_103a).
+ *
+ * Method: Onose, Dabbech & Wiaux (2017), "An accelerated splitting algorithm
+ * for radio-interferometric imaging: when natural and uniform weighting meet".
+ * The library solves
+ *     min_x ||Psi^dagger x||_1  s.t.  x >= 0,  ||Phi_j x - y_j||_2 <= eps_j  (all blocks j)
+ * (Section 3, Eq. "split-min-problem" with W = I) by Algorithm 3, with the
+ * data-fidelity prox taken in the metric U_j (Section 4.1, Algorithm 2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns a status: PPD_OK (0) or a negative PPD_ERR_* code.
+ *   No C++ exception and no abort crosses this boundary; ppd_last_error()
+ *   gives a one-line message for the calling thread's last failure.
+ * - Host buffers passed in are read during the call and never retained; the
+ *   caller keeps ownership.  Host buffers passed out are written in full.
+ * - Pointers named *_dev are caller-owned DEVICE memory, used on the given
+ *   CUDA stream (cudaStream_t passed as void*, NULL = the context's stream);
+ *   the call only enqueues work and does not synchronise.
+ * - The image is row-major n0 x n1 (n0 rows).  Complex arrays are
+ *   interleaved (re, im).  Device arrays use the context's precision:
+ *   float for PPD_FP32_FP64NORMS, double for PPD_FP64_PLAIN.
+ * - Visibility order at the boundary is always the caller's order; the
+ *   library sorts internally (see ppd_get_bins for the order it uses).
+ * - Call order: ppd_create -> ppd_set_visibilities -> ppd_set_weights ->
+ *   ppd_iterate / ppd_get_image / operators.  Out of order: PPD_ERR_NOT_READY.
+ *   Calling ppd_set_visibilities or ppd_set_weights again resets the solver
+ *   state to x = 0.
+ * - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef PPD_H
+#define PPD_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PPD_API __attribute__((visibility("default")))
+#else
+#define PPD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PPD_OK                  0
+#define PPD_ERR_INVALID_ARG    -1   /* bad pointer, size, shape or parameter */
+#define PPD_ERR_OOM            -2   /* device allocation failed */
+#define PPD_ERR_CUDA           -3   /* a CUDA runtime call failed */
+#define PPD_ERR_NONFINITE      -4   /* NaN/Inf in a norm or the image */
+#define PPD_ERR_TIMEOUT        -5   /* a bounded device wait gave up */
+#define PPD_ERR_NOT_READY      -6   /* call order violated */
+#define PPD_ERR_UNSUPPORTED    -7   /* size outside what this build handles */
+
+/* precision (config.precision) */
+#define PPD_FP64_PLAIN          0   /* every array and reduction in double, kernels launched one by one */
+#define PPD_FP32_FP64NORMS      1   /* float arrays, double norms / bounds / stop tests, one CUDA graph per iteration */
+
+/* Algorithm 2 start point (config.inner_init) */
+#define PPD_INNER_WARM          0   /* previous iteration's prox output (P_B(z) on the first iteration) */
+#define PPD_INNER_CURRENT       1   /* zbar^(0) = z */
+
+typedef struct ppd_ctx ppd_ctx;
+
+/* Solver configuration.  ppd_config_default() fills the paper's values
+ * (Section 5.1: tau = 0.49, lambda = 1, kappa = 1e-4, n_itr = 1, no
+ * randomisation; Section 5: oversampling 2 per axis, 8 x 8 Kaiser-Bessel). */
+typedef struct {
+    int32_t  n0, n1;            /* image rows / columns: powers of two, 16 <= n <= 2048 */
+    int32_t  oversample;        /* grid K = oversample * n per axis; must be 2 */
+    int32_t  kernel_width;      /* interpolation support J; must be 8 */
+    double   kb_beta;           /* Kaiser-Bessel shape; 0 => 2.34 * J */
+    int32_t  n_blocks;          /* number of data blocks d >= 1 */
+    int32_t  wavelet_levels;    /* SARA decomposition depth; must be 4 */
+    int32_t  n_itr;             /* Algorithm 2 sub-iterations per PPD iteration, >= 1 */
+    double   tau;               /* primal step (0.49) */
+    double   lambda;            /* relaxation; must be 1 */
+    double   kappa;             /* normalised soft-threshold (1e-4) */
+    double   eta;               /* 0 => 1/||U^{1/2} Phi||_S^2 by power iteration */
+    double   zeta;              /* 0 => 1/||Psi||_S^2 = 1 */
+    int32_t  precision;         /* PPD_FP64_PLAIN or PPD_FP32_FP64NORMS */
+    int32_t  precond;           /* 1: PPD with U = inverse sampling density; 0: U = I (PD) */
+    int32_t  inner_init;        /* PPD_INNER_WARM or PPD_INNER_CURRENT */
+    int32_t  use_graph;         /* 1: replay each iteration from a captured CUDA graph */
+    int32_t  tile;              /* gridding tile side T (16 or 32); 0 => 32 (16 when K < 80) */
+    int32_t  chunk;             /* max visibilities per gridding work item; 0 => 1024 */
+    int32_t  power_iters;       /* power-iteration cap for eta; 0 => 1000 */
+    double   power_tol;         /* power-iteration relative stop; 0 => 1e-10 */
+    void    *stream;            /* cudaStream_t for all work; NULL => library-created stream */
+} ppd_config;
+
+/* Per-call statistics (ppd_iterate).  All norms are computed in double. */
+typedef struct {
+    int32_t  iters_done;        /* PPD iterations completed by this context so far */
+    int32_t  status;            /* status of the call */
+    double   rel_var;           /* ||x^(t) - x^(t-1)|| / ||x^(t)|| of the last iteration */
+    double   snr_db;            /* 20 log10(||x0|| / ||x0 - x||) if ppd_set_ground_truth was called, else NaN */
+    double   max_res_over_eps;  /* max_j ||Phi_j xt - y_j|| / eps_j at the last iteration's data step */
+    double  *block_residual;    /* optional caller buffer of n_blocks doubles: ||Phi_j xt - y_j|| (whitened) */
+} ppd_stats;
+
+/* Parameters resolved by ppd_set_weights. */
+typedef struct {
+    double   eta, zeta, tau, kappa;
+    double   op_norm_sq;        /* ||U^{1/2} Phi||_S^2 (0 if eta was given) */
+    int32_t  power_iters_done;
+    int32_t  K0, K1;            /* oversampled grid */
+    int32_t  tile;              /* gridding tile side */
+    int64_t  n_chunks;          /* gridding work items */
+    int64_t  M;                 /* visibilities */
+    double   convergence_lhs;   /* tau*zeta*||Psi||^2 + tau*eta*||U^{1/2}Phi||^2 (Eq. "convergence-req-explicit-pd"), < 1 */
+} ppd_params;
+
+/* Fill *cfg with the paper's defaults (n0 = n1 = 0 must still be set). */
+PPD_API void ppd_config_default(ppd_config *cfg);
+
+/* Create a context on the current CUDA device.  Validates cfg (sizes,
+ * oversample = 2, J = 8, 4 levels, lambda = 1) and allocates the image-side
+ * state (x, xt, the 9 SARA dual images u_i, the oversampled grids).
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+PPD_API int ppd_create(ppd_ctx **out, const ppd_config *cfg);
+
+/* Free everything the context owns.  NULL is accepted. */
+PPD_API void ppd_destroy(ppd_ctx *ctx);
+
+/* Load the coverage and data (Section 2, Eq. "inverse-problem"; blocks as in
+ * Section 3.1, Eq. "data-split").
+ *   M         number of visibilities, 1 <= M < 2^31
+ *   uv        M x 2 doubles, row-major: omega_m in [-pi, pi)^2 (radians per
+ *             pixel); column 0 runs along image rows (axis 0)
+ *   y         M x 2 doubles (re, im): raw, un-whitened visibilities
+ *   block_id  M int32 in [0, n_blocks)
+ * Bins every visibility on the oversampled grid (FP64, bit-exact), sorts them
+ * into the library's processing order and counts visibilities per grid cell
+ * (the sampling density used by the default preconditioner).
+ * Errors: INVALID_ARG (NULL, M out of range, omega outside [-pi, pi], block
+ * out of range, non-finite y), OOM, CUDA. */
+PPD_API int ppd_set_visibilities(ppd_ctx *ctx, int64_t M, const double *uv, const double *y,
+                         const int32_t *block_id);
+
+/* Weights and bounds (Section 2: Theta; Section 4.3: U; Section 5.1: eps).
+ *   theta  M doubles > 0, natural weights 1/sigma_e (NULL => all 1)
+ *   U      M doubles > 0, preconditioner diagonal (NULL => 1/(visibilities in
+ *          the visibility's nearest cell of the oversampled grid) when
+ *          precond = 1, all 1 when precond = 0)
+ *   eps    n_blocks doubles > 0, l2 bounds on the whitened residual of each
+ *          block (NULL => sqrt(M_j + 2 sqrt(M_j)), two chi^2 standard
+ *          deviations above its mean)
+ * Then resolves eta (power iteration when config.eta = 0), mu_j =
+ * 1/max(U_j)^2 (Algorithm 2) and resets the state to zero.
+ * Errors: NOT_READY, INVALID_ARG, NONFINITE, OOM, CUDA. */
+PPD_API int ppd_set_weights(ppd_ctx *ctx, const double *theta, const double *U, const double *eps);
+
+/* Optional ground truth (n0*n1 doubles, row-major) for the SNR in ppd_stats
+ * (Section 5: SNR = 20 log10(||x0|| / ||x0 - x||)).  NULL clears it. */
+PPD_API int ppd_set_ground_truth(ppd_ctx *ctx, const double *x_true, int64_t len);
+
+/* Run n_iters iterations of Algorithm 3 (lambda = 1, all blocks and bases
+ * every iteration).  Work is enqueued on the context stream; if stats is
+ * non-NULL the call synchronises and fills it.  n_iters >= 0.
+ * Errors: NOT_READY, INVALID_ARG, NONFINITE, TIMEOUT, CUDA. */
+PPD_API int ppd_iterate(ppd_ctx *ctx, int32_t n_iters, ppd_stats *stats);
+
+/* Copy the current image x^(t) to the host as n0*n1 doubles (synchronises).
+ * len must equal n0*n1.  Errors: NOT_READY, INVALID_ARG, CUDA. */
+PPD_API int ppd_get_image(ppd_ctx *ctx, double *x_out, int64_t len);
+
+/* Resolved parameters (after ppd_set_weights). */
+PPD_API int ppd_get_params(ppd_ctx *ctx, ppd_params *out);
+
+/* Binning and ordering, for bit-exact checks (synchronises).  Each pointer
+ * may be NULL.  All arrays have M entries in the CALLER's order except perm.
+ *   perm     int64: perm[i] = caller index of the i-th visibility in the
+ *            processing order (ascending tile of the centred grid, block,
+ *            centred base row, centred base column, caller index)
+ *   base0/1  int32: first interpolation tap (floor(kappa) - 3) mod K per axis,
+ *            kappa = (omega * K) * 0.15915494309189535 in FP64
+ *   count    int32: visibilities sharing the nearest cell
+ *            (floor(kappa + 0.5) mod K per axis) */
+PPD_API int ppd_get_bins(ppd_ctx *ctx, int64_t *perm, int32_t *base0, int32_t *base1, int32_t *count);
+
+/* Phi x = Theta G F Z x (Section 2): x_dev n0*n1 reals -> y_dev M complex
+ * (caller order, whitened by theta).  Enqueued on stream.  Uses the
+ * context's internal grid, so it must not overlap ppd_iterate on the same
+ * context.  Errors: NOT_READY, INVALID_ARG, CUDA. */
+PPD_API int ppd_op_forward(ppd_ctx *ctx, const void *x_dev, void *y_dev, void *stream);
+
+/* Phi^dagger y = Re(Z^T F^H G^H Theta^H y): y_dev M complex (caller order)
+ * -> x_dev n0*n1 reals.  Same rules as ppd_op_forward. */
+PPD_API int ppd_op_adjoint(ppd_ctx *ctx, const void *y_dev, void *x_dev, void *stream);
+
+/* Psi^dagger x (Section 2.2, Section 5.1: Dirac + db1..db8, 4 levels,
+ * periodic, Mallat layout, each basis scaled by 1/3): x_dev n0*n1 reals ->
+ * c_dev 9*n0*n1 reals (basis-major).  Enqueued on stream. */
+PPD_API int ppd_psi_analysis(ppd_ctx *ctx, const void *x_dev, void *c_dev, void *stream);
+
+/* Psi c = (1/3) sum_i Psi_i c_i: c_dev 9*n0*n1 reals -> x_dev n0*n1 reals. */
+PPD_API int ppd_psi_synthesis(ppd_ctx *ctx, const void *c_dev, void *x_dev, void *stream);
+
+/* Per-kernel timing with CUDA events on the context stream.  enable = 1
+ * records an event pair around every kernel the iteration launches (inside
+ * the captured graph too); ppd_timing_collect() adds the durations of the
+ * launches completed since the last collect (synchronises) to running sums;
+ * ppd_timing_read() returns, for up to n kernel names, the summed
+ * milliseconds and launch counts.  names[i] points to static strings. */
+PPD_API int ppd_timing_enable(ppd_ctx *ctx, int32_t enable);
+PPD_API int ppd_timing_collect(ppd_ctx *ctx);
+PPD_API int ppd_timing_read(ppd_ctx *ctx, int32_t n, const char **names, double *ms, int64_t *launches,
+                    int32_t *n_out);
+
+/* Kernel launches enqueued by this context since creation (all entry points). */
+PPD_API int64_t ppd_launch_count(ppd_ctx *ctx);
+
+/* Static description of a status code. */
+PPD_API const char *ppd_status_string(int status);
+
+/* Message of the calling thread's last failed call ("" if none). */
+PPD_API const char *ppd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPD_H */

@@ -1,0 +1,878 @@
+// C ABI of libppd (declared in include/ppd.h): context management, set-up of
+// the visibilities and weights, the PPD iteration driver (Algorithm 3) and
+// the operator entry points.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace ppd {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+// ----------------------------------------------------------------- launches and timing
+static int take_event(ppd_ctx *c, cudaEvent_t *ev) {
+    if (!c->event_pool.empty()) {
+        *ev = c->event_pool.back();
+        c->event_pool.pop_back();
+        return PPD_OK;
+    }
+    PPD_CUDA(cudaEventCreate(ev));
+    return PPD_OK;
+}
+
+static int record(ppd_ctx *c, cudaEvent_t ev, cudaStream_t s) {
+    if (c->capturing) {
+        PPD_CUDA(cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal));
+    } else {
+        PPD_CUDA(cudaEventRecord(ev, s));
+    }
+    return PPD_OK;
+}
+
+int launch_begin(ppd_ctx *c, const char *name, cudaStream_t s, int *site) {
+    c->launches++;
+    *site = -1;
+    if (!c->timing) return PPD_OK;
+    TimingSite t{name, nullptr, nullptr};
+    PPD_CHECK(take_event(c, &t.start));
+    PPD_CHECK(take_event(c, &t.stop));
+    PPD_CHECK(record(c, t.start, s));
+    auto &v = c->capturing ? c->sites_graph : c->sites_eager;
+    v.push_back(t);
+    *site = (int)v.size() - 1;
+    return PPD_OK;
+}
+
+int launch_end(ppd_ctx *c, int site, cudaStream_t s) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(PPD_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    if (site < 0) return PPD_OK;
+    auto &v = c->capturing ? c->sites_graph : c->sites_eager;
+    return record(c, v[site].stop, s);
+}
+
+static void tsum_add(ppd_ctx *c, const char *name, double ms) {
+    for (auto &p : c->tsum)
+        if (std::strcmp(p.first, name) == 0) {
+            p.second.first += ms;
+            p.second.second += 1;
+            return;
+        }
+    c->tsum.push_back({name, {ms, 1}});
+}
+
+}  // namespace ppd
+
+using namespace ppd;
+
+// ----------------------------------------------------------------- helpers
+namespace {
+
+template <typename T> int dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? PPD_ERR_OOM : PPD_ERR_CUDA,
+                    std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    return PPD_OK;
+}
+
+int dalloc_bytes(void **p, size_t bytes) { return dalloc(reinterpret_cast<unsigned char **>(p), bytes); }
+
+void dfree(void *p) {
+    if (p) cudaFree(p);
+}
+
+void free_vis(ppd_ctx *c) {
+    for (void *p : {c->rec, c->theta_v, c->y, c->v, c->z, c->w, c->p, c->y_raw, (void *)c->perm,
+                    (void *)c->count_cell, (void *)c->ch.start, (void *)c->ch.count, (void *)c->ch.tile,
+                    (void *)c->ch.block, (void *)c->ch.tile_first, (void *)c->ch.tile_n, (void *)c->ch.blk_ptr,
+                    (void *)c->ch.blk_list, (void *)c->partials, (void *)c->scale, (void *)c->resid2,
+                    (void *)c->eps_d, (void *)c->mu_d, c->gpart})
+        dfree(p);
+    c->rec = c->theta_v = c->y = c->v = c->z = c->w = c->p = c->y_raw = c->gpart = nullptr;
+    c->perm = nullptr;
+    c->count_cell = nullptr;
+    c->ch = Chunks{};
+    c->partials = c->scale = c->resid2 = c->eps_d = c->mu_d = nullptr;
+    c->have_vis = c->have_weights = false;
+}
+
+void drop_graph(ppd_ctx *c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    for (auto &t : c->sites_graph) {
+        c->event_pool.push_back(t.start);
+        c->event_pool.push_back(t.stop);
+    }
+    c->sites_graph.clear();
+}
+
+cudaStream_t pick(ppd_ctx *c, void *s) { return s ? static_cast<cudaStream_t>(s) : c->stream; }
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Stable LSD radix sort of indices by 64-bit key (16-bit digits).
+void radix_sort(const std::vector<uint64_t> &key, std::vector<int64_t> &perm) {
+    const int64_t M = (int64_t)key.size();
+    perm.resize(M);
+    for (int64_t i = 0; i < M; ++i) perm[i] = i;
+    uint64_t maxk = 0;
+    for (uint64_t k : key) maxk = std::max(maxk, k);
+    std::vector<int64_t> tmp(M);
+    std::vector<int64_t> cnt(65537);
+    for (int shift = 0; shift < 64 && (maxk >> shift) != 0; shift += 16) {
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (int64_t i = 0; i < M; ++i) cnt[((key[perm[i]] >> shift) & 0xffff) + 1]++;
+        for (int d = 0; d < 65536; ++d) cnt[d + 1] += cnt[d];
+        for (int64_t i = 0; i < M; ++i) tmp[cnt[(key[perm[i]] >> shift) & 0xffff]++] = perm[i];
+        perm.swap(tmp);
+    }
+}
+
+// TMA descriptor of grid_a as a 2-D array of reals (re, im interleaved):
+// dims {2*K1, K0}; box {2*(T+8), T+8}; no swizzle, zero fill out of bounds.
+int make_tmap(ppd_ctx *c) {
+    c->tma_ok = false;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return PPD_OK;   // plain-load path
+    }
+    const int E = c->T + HALO;
+    if (c->K0 < E || c->K1 < E) return PPD_OK;
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    cuuint64_t dims[2] = {(cuuint64_t)2 * c->K1, (cuuint64_t)c->K0};
+    cuuint64_t strides[1] = {(cuuint64_t)2 * c->K1 * c->rsz};
+    cuuint32_t box[2] = {(cuuint32_t)2 * E, (cuuint32_t)E};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(&c->tmap_a, c->is_f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                        c->grid_a, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    c->tma_ok = (r == CUDA_SUCCESS);
+    return PPD_OK;
+}
+
+int check_err_word(ppd_ctx *c) {
+    int h = 0;
+    PPD_CUDA(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PPD_CUDA(cudaStreamSynchronize(c->stream));
+    if (h & ERR_TMA_TIMEOUT) return fail(PPD_ERR_TIMEOUT, "a bounded TMA wait in the degridding kernel gave up");
+    if (h & ERR_NONFINITE) return fail(PPD_ERR_NONFINITE, "non-finite block norm");
+    return PPD_OK;
+}
+
+// One PPD iteration (Algorithm 3, lambda = 1, all blocks and bases).
+template <typename R> int iteration_body(ppd_ctx *c, cudaStream_t s, bool first) {
+    using C = cplx_t<R>;
+    C *ga = static_cast<C *>(c->grid_a), *gv = static_cast<C *>(c->grid_v);
+    PPD_CHECK(fft_forward<R>(c, static_cast<const R *>(c->xt), ga, s));
+    const bool current = c->cfg.inner_init == PPD_INNER_CURRENT;
+    if (current || first) {
+        PPD_CHECK(degrid<R>(c, DG_FIRST, ga, nullptr, nullptr, s));
+        PPD_CHECK(block_norms(c, 1, s));
+        if (!current) {   // warm start at t = 1: zbar^(0) = P_B(z), then the first step
+            PPD_CHECK(subiter<R>(c, s));
+            PPD_CHECK(block_norms(c, 0, s));
+        }
+    } else {
+        PPD_CHECK(degrid<R>(c, DG_DUAL, ga, nullptr, nullptr, s));
+        PPD_CHECK(block_norms(c, 1, s));
+    }
+    for (int k = 1; k < c->cfg.n_itr; ++k) {
+        PPD_CHECK(subiter<R>(c, s));
+        PPD_CHECK(block_norms(c, 0, s));
+    }
+    PPD_CHECK(grid_vis<R>(c, GR_DUAL, nullptr, nullptr, gv, s));
+    PPD_CHECK(fft_inverse<R>(c, gv, static_cast<R *>(c->g), s));
+    PPD_CHECK(sara_dual_step<R>(c, s));
+    PPD_CHECK(primal_step<R>(c, s));
+    return PPD_OK;
+}
+
+template <typename R> int run_iterations(ppd_ctx *c, int n) {
+    cudaStream_t s = c->stream;
+    for (int it = 0; it < n; ++it) {
+        const bool first = !c->p_valid;
+        if (first || !c->cfg.use_graph || !c->is_f32) {
+            PPD_CHECK(iteration_body<R>(c, s, first));
+        } else {
+            if (!c->gexec) {
+                c->capturing = true;
+                const int64_t before = c->launches;
+                cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+                if (e != cudaSuccess) {
+                    c->capturing = false;
+                    return fail(PPD_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+                }
+                int st = iteration_body<R>(c, s, false);
+                cudaGraph_t g = nullptr;
+                e = cudaStreamEndCapture(s, &g);
+                c->capturing = false;
+                c->launches = before;
+                if (st != PPD_OK) {
+                    if (g) cudaGraphDestroy(g);
+                    return st;
+                }
+                if (e != cudaSuccess) return fail(PPD_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
+                c->graph = g;
+                e = cudaGraphInstantiate(&c->gexec, g, 0);
+                if (e != cudaSuccess) return fail(PPD_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+                size_t nn = 0;
+                cudaGraphGetNodes(g, nullptr, &nn);
+                std::vector<cudaGraphNode_t> nodes(nn);
+                cudaGraphGetNodes(g, nodes.data(), &nn);
+                int64_t kernels = 0;
+                for (auto nd : nodes) {
+                    cudaGraphNodeType t;
+                    cudaGraphNodeGetType(nd, &t);
+                    if (t == cudaGraphNodeTypeKernel) kernels++;
+                }
+                c->graph_kernels = kernels;
+            }
+            PPD_CUDA(cudaGraphLaunch(c->gexec, s));
+            c->launches += c->graph_kernels;
+            c->graph_ran_since_collect = true;
+        }
+        c->p_valid = true;
+        c->iters++;
+    }
+    return PPD_OK;
+}
+
+template <typename R> int power_iteration(ppd_ctx *c) {
+    using C = cplx_t<R>;
+    cudaStream_t s = c->stream;
+    const int64_t N = c->N;
+    std::vector<R> ones(N, R(1.0 / std::sqrt((double)N)));
+    PPD_CUDA(cudaMemcpy(c->x, ones.data(), N * sizeof(R), cudaMemcpyHostToDevice));
+    double *nrm = c->stat_out;
+    double prev = 0, val = 0;
+    const int maxit = c->cfg.power_iters > 0 ? c->cfg.power_iters : 1000;
+    const double tol = c->cfg.power_tol > 0 ? c->cfg.power_tol : 1e-10;
+    int it = 0;
+    for (it = 1; it <= maxit; ++it) {
+        PPD_CHECK(fft_forward<R>(c, static_cast<const R *>(c->x), static_cast<C *>(c->grid_a), s));
+        PPD_CHECK(degrid<R>(c, DG_OP, static_cast<C *>(c->grid_a), static_cast<C *>(c->z), nullptr, s));
+        PPD_CHECK(grid_vis<R>(c, GR_OP_U, static_cast<const C *>(c->z), nullptr, static_cast<C *>(c->grid_v), s));
+        PPD_CHECK(fft_inverse<R>(c, static_cast<const C *>(c->grid_v), static_cast<R *>(c->g), s));
+        PPD_CHECK(sumsq<R>(c, static_cast<const R *>(c->g), N, nrm, s));
+        double h[3];
+        PPD_CUDA(cudaMemcpyAsync(h, nrm, sizeof(h), cudaMemcpyDeviceToHost, s));
+        PPD_CUDA(cudaStreamSynchronize(s));
+        val = std::sqrt(h[0]);
+        if (!std::isfinite(val) || val <= 0) return fail(PPD_ERR_NONFINITE, "power iteration: non-finite or zero norm");
+        PPD_CHECK(scale_copy<R>(c, static_cast<const R *>(c->g), static_cast<R *>(c->x), N, 1.0 / val, s));
+        if (std::abs(val - prev) <= tol * val) break;
+        prev = val;
+    }
+    c->op_norm_sq = val;
+    c->power_done = std::min(it, maxit);
+    return PPD_OK;
+}
+
+int reset_state(ppd_ctx *c) {
+    const size_t rb = c->rsz;
+    PPD_CUDA(cudaMemsetAsync(c->x, 0, c->N * rb, c->stream));
+    PPD_CUDA(cudaMemsetAsync(c->xt, 0, c->N * rb, c->stream));
+    PPD_CUDA(cudaMemsetAsync(c->u, 0, N_BASES * c->N * rb, c->stream));
+    if (c->M > 0) {
+        PPD_CUDA(cudaMemsetAsync(c->v, 0, 2 * c->M * rb, c->stream));
+        PPD_CUDA(cudaMemsetAsync(c->p, 0, 2 * c->M * rb, c->stream));
+    }
+    PPD_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    c->p_valid = false;
+    c->iters = 0;
+    drop_graph(c);
+    return PPD_OK;
+}
+
+template <typename R> int upload_real(void *dst, const std::vector<double> &src) {
+    std::vector<R> t(src.begin(), src.end());
+    PPD_CUDA(cudaMemcpy(dst, t.data(), t.size() * sizeof(R), cudaMemcpyHostToDevice));
+    return PPD_OK;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+void ppd_config_default(ppd_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->oversample = 2;
+    cfg->kernel_width = 8;
+    cfg->kb_beta = 0.0;
+    cfg->n_blocks = 1;
+    cfg->wavelet_levels = 4;
+    cfg->n_itr = 1;
+    cfg->tau = 0.49;
+    cfg->lambda = 1.0;
+    cfg->kappa = 1e-4;
+    cfg->eta = 0.0;
+    cfg->zeta = 0.0;
+    cfg->precision = PPD_FP32_FP64NORMS;
+    cfg->precond = 1;
+    cfg->inner_init = PPD_INNER_WARM;
+    cfg->use_graph = 1;
+    cfg->tile = 0;
+    cfg->chunk = 0;
+    cfg->power_iters = 0;
+    cfg->power_tol = 0.0;
+    cfg->stream = nullptr;
+}
+
+const char *ppd_status_string(int status) {
+    switch (status) {
+        case PPD_OK: return "ok";
+        case PPD_ERR_INVALID_ARG: return "invalid argument";
+        case PPD_ERR_OOM: return "out of device memory";
+        case PPD_ERR_CUDA: return "CUDA error";
+        case PPD_ERR_NONFINITE: return "non-finite value";
+        case PPD_ERR_TIMEOUT: return "bounded device wait timed out";
+        case PPD_ERR_NOT_READY: return "call out of order";
+        case PPD_ERR_UNSUPPORTED: return "unsupported size or option";
+        default: return "unknown status";
+    }
+}
+
+const char *ppd_last_error(void) { return g_last_error.c_str(); }
+
+int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
+    if (!out || !cfg) return fail(PPD_ERR_INVALID_ARG, "ppd_create: NULL argument");
+    *out = nullptr;
+    const ppd_config &k = *cfg;
+    if (k.n0 != k.n1) return fail(PPD_ERR_UNSUPPORTED, "ppd_create: only square images (n0 == n1)");
+    if (!is_pow2(k.n0) || k.n0 < 16 || k.n0 > 2048)
+        return fail(PPD_ERR_UNSUPPORTED, "ppd_create: image side must be a power of two in [16, 2048]");
+    if (k.oversample != 2 || k.kernel_width != 8 || k.wavelet_levels != 4)
+        return fail(PPD_ERR_UNSUPPORTED, "ppd_create: oversample 2, kernel width 8 and 4 levels are required");
+    if (k.n_blocks < 1 || k.n_itr < 1 || !(k.tau > 0) || k.lambda != 1.0 || !(k.kappa > 0) || k.eta < 0 ||
+        k.zeta < 0 || k.kb_beta < 0)
+        return fail(PPD_ERR_INVALID_ARG, "ppd_create: invalid solver parameter");
+    if (k.precision != PPD_FP64_PLAIN && k.precision != PPD_FP32_FP64NORMS)
+        return fail(PPD_ERR_INVALID_ARG, "ppd_create: unknown precision");
+    if (k.inner_init != PPD_INNER_WARM && k.inner_init != PPD_INNER_CURRENT)
+        return fail(PPD_ERR_INVALID_ARG, "ppd_create: unknown inner_init");
+    if (k.tile != 0 && k.tile != 16 && k.tile != 32) return fail(PPD_ERR_INVALID_ARG, "ppd_create: tile must be 16 or 32");
+    if (k.chunk < 0) return fail(PPD_ERR_INVALID_ARG, "ppd_create: chunk must be >= 0");
+
+    ppd_ctx *c = new (std::nothrow) ppd_ctx();
+    if (!c) return fail(PPD_ERR_OOM, "ppd_create: host allocation");
+    c->cfg = k;
+    c->is_f32 = k.precision == PPD_FP32_FP64NORMS;
+    c->rsz = c->is_f32 ? 4 : 8;
+    c->L0 = k.n0;
+    c->L1 = k.n1;
+    c->K0 = 2 * k.n0;
+    c->K1 = 2 * k.n1;
+    c->N = (int64_t)k.n0 * k.n1;
+    c->d = k.n_blocks;
+    c->levels = k.wavelet_levels;
+    c->T = k.tile ? k.tile : (c->K0 >= 80 ? 32 : 16);
+    if (c->K0 % c->T) c->T = 16;
+    c->C = k.chunk ? k.chunk : 1024;
+    c->beta = k.kb_beta > 0 ? k.kb_beta : 2.34 * KB_J;
+    c->tau = k.tau;
+    c->kappa = k.kappa;
+    c->zeta = k.zeta > 0 ? k.zeta : 1.0;
+    cudaGetDevice(&c->device);
+    auto bail = [&](int st) {
+        ppd_destroy(c);
+        return st;
+    };
+    if (k.stream) {
+        c->stream = static_cast<cudaStream_t>(k.stream);
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(PPD_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+        }
+        c->own_stream = true;
+    }
+    const size_t rb = c->rsz, cb = 2 * c->rsz;
+    const int64_t N = c->N, G = (int64_t)c->K0 * c->K1;
+    int st = PPD_OK;
+    if ((st = dalloc_bytes(&c->x, N * rb)) || (st = dalloc_bytes(&c->xt, N * rb)) ||
+        (st = dalloc_bytes(&c->g, N * rb)) || (st = dalloc_bytes(&c->ut, N * rb)) ||
+        (st = dalloc_bytes(&c->u, N_BASES * N * rb)) || (st = dalloc_bytes(&c->wtmp, N_WAVELETS * N * rb)) ||
+        (st = dalloc_bytes(&c->wtmp2, 4 * N * rb)) || (st = dalloc_bytes(&c->grid_a, G * cb)) ||
+        (st = dalloc_bytes(&c->grid_v, G * cb)) || (st = dalloc_bytes(&c->fft_tmp, (int64_t)c->L0 * c->K1 * cb)) ||
+        (st = dalloc_bytes(&c->tw0, c->K0 * cb)) || (st = dalloc_bytes(&c->deap0, c->L0 * rb)) ||
+        (st = dalloc_bytes(&c->deap1, c->L1 * rb)) ||
+        (st = dalloc_bytes(&c->kbpoly, (KB_DEG + 1) * KB_J * sizeof(float))) || (st = dalloc(&c->err, 1)) ||
+        (st = dalloc(&c->stat_out, 3)))
+        return bail(st);
+    c->n_prim_blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 4);
+    if ((st = dalloc(&c->prim_part, 3 * (size_t)c->n_prim_blocks))) return bail(st);
+    if ((st = make_twiddles(c)) || (st = make_deapodisation(c)) || (st = make_filters(c)) || (st = make_kb_poly(c)))
+        return bail(st);
+    if (cudaMemsetAsync(c->grid_a, 0, G * cb, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->grid_v, 0, G * cb, c->stream) != cudaSuccess || reset_state(c) != PPD_OK)
+        return bail(fail(PPD_ERR_CUDA, "ppd_create: initialisation"));
+    if ((st = make_tmap(c))) return bail(st);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(fail(PPD_ERR_CUDA, "ppd_create: sync"));
+    *out = c;
+    return PPD_OK;
+}
+
+void ppd_destroy(ppd_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graph(c);
+    for (auto &t : c->sites_eager) {
+        c->event_pool.push_back(t.start);
+        c->event_pool.push_back(t.stop);
+    }
+    for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+    free_vis(c);
+    for (void *p : {c->x, c->xt, c->g, c->ut, c->xtrue, c->u, c->wtmp, c->wtmp2, c->grid_a, c->grid_v, c->fft_tmp,
+                    c->tw0, c->deap0, c->deap1, c->kbpoly, (void *)c->prim_part, (void *)c->stat_out, (void *)c->err})
+        dfree(p);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *y, const int32_t *block_id) {
+    if (!c || !uv || !y || !block_id) return fail(PPD_ERR_INVALID_ARG, "ppd_set_visibilities: NULL argument");
+    if (M < 1 || M >= (int64_t)1 << 31) return fail(PPD_ERR_INVALID_ARG, "ppd_set_visibilities: M out of range");
+    for (int64_t i = 0; i < 2 * M; ++i)
+        if (!std::isfinite(y[i])) return fail(PPD_ERR_INVALID_ARG, "ppd_set_visibilities: non-finite visibility");
+    free_vis(c);
+    drop_graph(c);
+    c->M = M;
+    const int64_t G = (int64_t)c->K0 * c->K1;
+    (void)G;
+    double *uv_d = nullptr, *frac_d = nullptr;
+    int32_t *blk_d = nullptr, *base_d = nullptr, *cnt_d = nullptr;
+    uint64_t *key_d = nullptr;
+    int *bad_d = nullptr;
+    int st = PPD_OK;
+    auto cleanup = [&]() {
+        dfree(uv_d);
+        dfree(frac_d);
+        dfree(blk_d);
+        dfree(base_d);
+        dfree(cnt_d);
+        dfree(key_d);
+        dfree(bad_d);
+    };
+    if ((st = dalloc(&uv_d, 2 * M)) || (st = dalloc(&frac_d, 2 * M)) || (st = dalloc(&blk_d, M)) ||
+        (st = dalloc(&base_d, 2 * M)) || (st = dalloc(&cnt_d, M)) || (st = dalloc(&key_d, M)) ||
+        (st = dalloc(&bad_d, 1))) {
+        cleanup();
+        return st;
+    }
+    auto cuda_fail = [&](cudaError_t e, const char *what) {
+        cleanup();
+        return fail(e == cudaErrorMemoryAllocation ? PPD_ERR_OOM : PPD_ERR_CUDA,
+                    std::string(what) + ": " + cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    if ((e = cudaMemcpy(uv_d, uv, 2 * M * sizeof(double), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(blk_d, block_id, M * sizeof(int32_t), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemset(bad_d, 0, sizeof(int))))
+        return cuda_fail(e, "ppd_set_visibilities: upload");
+    if ((st = bin_all(c, uv_d, blk_d, M, key_d, base_d, frac_d, cnt_d, bad_d))) {
+        cleanup();
+        return st;
+    }
+    int bad = 0;
+    std::vector<uint64_t> key(M);
+    std::vector<int32_t> base(2 * M), cnt(M);
+    std::vector<double> frac(2 * M);
+    if ((e = cudaMemcpy(&bad, bad_d, sizeof(int), cudaMemcpyDeviceToHost)) ||
+        (e = cudaMemcpy(key.data(), key_d, M * 8, cudaMemcpyDeviceToHost)) ||
+        (e = cudaMemcpy(base.data(), base_d, 2 * M * 4, cudaMemcpyDeviceToHost)) ||
+        (e = cudaMemcpy(frac.data(), frac_d, 2 * M * 8, cudaMemcpyDeviceToHost)) ||
+        (e = cudaMemcpy(cnt.data(), cnt_d, M * 4, cudaMemcpyDeviceToHost)))
+        return cuda_fail(e, "ppd_set_visibilities: download");
+    cleanup();
+    if (bad) return fail(PPD_ERR_INVALID_ARG, "ppd_set_visibilities: omega outside [-pi, pi] or block id out of range");
+
+    // processing order and work items
+    radix_sort(key, c->perm_h);
+    c->base0_h.resize(M);
+    c->base1_h.resize(M);
+    c->count_h = cnt;
+    c->block_h.assign(block_id, block_id + M);
+    for (int64_t i = 0; i < M; ++i) {
+        c->base0_h[i] = base[2 * i];
+        c->base1_h[i] = base[2 * i + 1];
+    }
+    const uint64_t KK = (uint64_t)c->K0 * c->K1;
+    const int ntiles = (c->K0 / c->T) * (c->K1 / c->T);
+    std::vector<int32_t> cs, cn, ct, cbk, tfirst(ntiles, 0), tn(ntiles, 0);
+    for (int64_t i = 0; i < M;) {
+        const uint64_t k0 = key[c->perm_h[i]];
+        const uint64_t tb = k0 / KK;   // tile * d + block
+        int64_t j = i;
+        while (j < M && key[c->perm_h[j]] / KK == tb) ++j;
+        for (int64_t s = i; s < j; s += c->C) {
+            const int tile = (int)(tb / (uint64_t)c->d), blk = (int)(tb % (uint64_t)c->d);
+            if (tn[tile] == 0) tfirst[tile] = (int32_t)cs.size();
+            tn[tile]++;
+            cs.push_back((int32_t)s);
+            cn.push_back((int32_t)std::min<int64_t>(c->C, j - s));
+            ct.push_back(tile);
+            cbk.push_back(blk);
+        }
+        i = j;
+    }
+    const int64_t nch = (int64_t)cs.size();
+    std::vector<int32_t> bptr(c->d + 1, 0), blist(nch);
+    for (int64_t k = 0; k < nch; ++k) bptr[cbk[k] + 1]++;
+    for (int j = 0; j < c->d; ++j) bptr[j + 1] += bptr[j];
+    {
+        std::vector<int32_t> fill(bptr.begin(), bptr.end() - 1);
+        for (int64_t k = 0; k < nch; ++k) blist[fill[cbk[k]]++] = (int32_t)k;
+    }
+    c->ch.n = nch;
+    const size_t cbsz = 2 * c->rsz;
+    const int E = c->T + HALO;
+    if ((st = dalloc(&c->ch.start, nch)) || (st = dalloc(&c->ch.count, nch)) || (st = dalloc(&c->ch.tile, nch)) ||
+        (st = dalloc(&c->ch.block, nch)) || (st = dalloc(&c->ch.tile_first, ntiles)) ||
+        (st = dalloc(&c->ch.tile_n, ntiles)) || (st = dalloc(&c->ch.blk_ptr, c->d + 1)) ||
+        (st = dalloc(&c->ch.blk_list, nch)) || (st = dalloc(&c->partials, NPART * (size_t)nch)) ||
+        (st = dalloc(&c->scale, c->d)) || (st = dalloc(&c->resid2, c->d)) || (st = dalloc(&c->eps_d, c->d)) ||
+        (st = dalloc(&c->mu_d, c->d)) || (st = dalloc_bytes(&c->gpart, (size_t)nch * E * E * cbsz)) ||
+        (st = dalloc(&c->perm, M)) || (st = dalloc_bytes(&c->rec, M * (c->is_f32 ? 16 : 32))) ||
+        (st = dalloc_bytes(&c->y, M * cbsz)) || (st = dalloc_bytes(&c->v, M * cbsz)) ||
+        (st = dalloc_bytes(&c->z, M * cbsz)) || (st = dalloc_bytes(&c->w, M * cbsz)) ||
+        (st = dalloc_bytes(&c->p, M * cbsz)) || (st = dalloc_bytes(&c->y_raw, M * 2 * sizeof(double)))) {
+        free_vis(c);
+        return st;
+    }
+    std::vector<double> yraw_sorted(2 * M);
+    for (int64_t i = 0; i < M; ++i) {
+        yraw_sorted[2 * i] = y[2 * c->perm_h[i]];
+        yraw_sorted[2 * i + 1] = y[2 * c->perm_h[i] + 1];
+    }
+    // frac, packed centred base are rebuilt into records by ppd_set_weights;
+    // keep the sorted fractions in the host copy until then.
+    c->frac_h.resize(2 * M);
+    c->packed_h.resize(M);
+    for (int64_t i = 0; i < M; ++i) {
+        const int64_t o = c->perm_h[i];
+        c->frac_h[2 * i] = frac[2 * o];
+        c->frac_h[2 * i + 1] = frac[2 * o + 1];
+        const int cb0 = (base[2 * o] + c->K0 / 2) % c->K0, cb1 = (base[2 * o + 1] + c->K1 / 2) % c->K1;
+        c->packed_h[i] = cb0 | (cb1 << 16);
+    }
+    if ((e = cudaMemcpy(c->ch.start, cs.data(), nch * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->ch.count, cn.data(), nch * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->ch.tile, ct.data(), nch * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->ch.block, cbk.data(), nch * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->ch.tile_first, tfirst.data(), ntiles * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->ch.tile_n, tn.data(), ntiles * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->ch.blk_ptr, bptr.data(), (c->d + 1) * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->ch.blk_list, blist.data(), nch * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->perm, c->perm_h.data(), M * 8, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->y_raw, yraw_sorted.data(), 2 * M * 8, cudaMemcpyHostToDevice))) {
+        free_vis(c);
+        return fail(PPD_ERR_CUDA, std::string("ppd_set_visibilities: upload: ") + cudaGetErrorString(e));
+    }
+    c->block_count_h.assign(c->d, 0);
+    for (int64_t i = 0; i < M; ++i) c->block_count_h[block_id[i]]++;
+    c->have_vis = true;
+    c->have_weights = false;
+    return PPD_OK;
+}
+
+int ppd_set_weights(ppd_ctx *c, const double *theta, const double *U, const double *eps) {
+    if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_set_weights: NULL context");
+    if (!c->have_vis) return fail(PPD_ERR_NOT_READY, "ppd_set_weights: call ppd_set_visibilities first");
+    const int64_t M = c->M;
+    std::vector<double> th(M), uu(M);
+    bool uniform = true;
+    for (int64_t i = 0; i < M; ++i) {
+        const int64_t o = c->perm_h[i];
+        th[i] = theta ? theta[o] : 1.0;
+        if (U) uu[i] = U[o];
+        else uu[i] = c->cfg.precond ? 1.0 / (double)c->count_h[o] : 1.0;
+        if (!(th[i] > 0) || !std::isfinite(th[i]) || !(uu[i] > 0) || !std::isfinite(uu[i]))
+            return fail(PPD_ERR_INVALID_ARG, "ppd_set_weights: theta and U must be finite and > 0");
+        if (th[i] != th[0]) uniform = false;
+    }
+    std::vector<double> ep(c->d), mu(c->d, 1.0), umax(c->d, 0.0);
+    for (int j = 0; j < c->d; ++j) {
+        const double Mj = (double)c->block_count_h[j];
+        ep[j] = eps ? eps[j] : std::sqrt(Mj + 2.0 * std::sqrt(Mj));
+        if (!(ep[j] > 0) || !std::isfinite(ep[j]))
+            return fail(PPD_ERR_INVALID_ARG, "ppd_set_weights: eps must be finite and > 0");
+    }
+    for (int64_t i = 0; i < M; ++i) {
+        const int b = c->block_h[c->perm_h[i]];
+        umax[b] = std::max(umax[b], uu[i]);
+    }
+    for (int j = 0; j < c->d; ++j)
+        if (umax[j] > 0) mu[j] = 1.0 / (umax[j] * umax[j]);
+    c->eps_h = ep;
+    c->mu_h = mu;
+    // records, whitened data, weights
+    cudaError_t e;
+    std::vector<double> yw(2 * M);
+    {
+        std::vector<double> yr(2 * M);
+        if ((e = cudaMemcpy(yr.data(), c->y_raw, 2 * M * 8, cudaMemcpyDeviceToHost)))
+            return fail(PPD_ERR_CUDA, std::string("ppd_set_weights: ") + cudaGetErrorString(e));
+        for (int64_t i = 0; i < M; ++i) {
+            yw[2 * i] = th[i] * yr[2 * i];
+            yw[2 * i + 1] = th[i] * yr[2 * i + 1];
+        }
+    }
+    if (c->is_f32) {
+        std::vector<VisRec<float>> rec(M);
+        for (int64_t i = 0; i < M; ++i)
+            rec[i] = VisRec<float>{c->packed_h[i], (float)c->frac_h[2 * i], (float)c->frac_h[2 * i + 1], (float)uu[i]};
+        if ((e = cudaMemcpy(c->rec, rec.data(), M * sizeof(rec[0]), cudaMemcpyHostToDevice)))
+            return fail(PPD_ERR_CUDA, std::string("ppd_set_weights: ") + cudaGetErrorString(e));
+    } else {
+        std::vector<VisRec<double>> rec(M);
+        for (int64_t i = 0; i < M; ++i)
+            rec[i] = VisRec<double>{c->packed_h[i], 0, c->frac_h[2 * i], c->frac_h[2 * i + 1], uu[i]};
+        if ((e = cudaMemcpy(c->rec, rec.data(), M * sizeof(rec[0]), cudaMemcpyHostToDevice)))
+            return fail(PPD_ERR_CUDA, std::string("ppd_set_weights: ") + cudaGetErrorString(e));
+    }
+    int st;
+    if ((st = c->is_f32 ? upload_real<float>(c->y, yw) : upload_real<double>(c->y, yw))) return st;
+    dfree(c->theta_v);
+    c->theta_v = nullptr;
+    c->theta_scalar = th[0];
+    if (!uniform) {
+        if ((st = dalloc_bytes(&c->theta_v, M * c->rsz))) return st;
+        if ((st = c->is_f32 ? upload_real<float>(c->theta_v, th) : upload_real<double>(c->theta_v, th))) return st;
+    }
+    if ((e = cudaMemcpy(c->eps_d, ep.data(), c->d * 8, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->mu_d, mu.data(), c->d * 8, cudaMemcpyHostToDevice)))
+        return fail(PPD_ERR_CUDA, std::string("ppd_set_weights: ") + cudaGetErrorString(e));
+    c->have_weights = true;
+    drop_graph(c);
+    if ((st = reset_state(c))) return st;
+    // eta = 1 / ||U^{1/2} Phi||^2 (Section 5.1)
+    if (c->cfg.eta > 0) {
+        c->eta = c->cfg.eta;
+        c->op_norm_sq = 0;
+        c->power_done = 0;
+    } else {
+        if ((st = c->is_f32 ? power_iteration<float>(c) : power_iteration<double>(c))) return st;
+        c->eta = 1.0 / c->op_norm_sq;
+    }
+    if ((st = reset_state(c))) return st;
+    PPD_CUDA(cudaStreamSynchronize(c->stream));
+    return check_err_word(c);
+}
+
+int ppd_set_ground_truth(ppd_ctx *c, const double *x_true, int64_t len) {
+    if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_set_ground_truth: NULL context");
+    if (!x_true) {
+        dfree(c->xtrue);
+        c->xtrue = nullptr;
+        c->xtrue_set = false;
+        drop_graph(c);
+        return PPD_OK;
+    }
+    if (len != c->N) return fail(PPD_ERR_INVALID_ARG, "ppd_set_ground_truth: len must be n0*n1");
+    if (!c->xtrue) PPD_CHECK(dalloc_bytes(&c->xtrue, c->N * c->rsz));
+    std::vector<double> v(x_true, x_true + len);
+    double n2 = 0;
+    for (double a : v) n2 += a * a;
+    c->xtrue_norm2 = n2;
+    PPD_CHECK(c->is_f32 ? upload_real<float>(c->xtrue, v) : upload_real<double>(c->xtrue, v));
+    c->xtrue_set = true;
+    drop_graph(c);
+    return PPD_OK;
+}
+
+int ppd_iterate(ppd_ctx *c, int32_t n_iters, ppd_stats *stats) {
+    if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_iterate: NULL context");
+    if (!c->have_weights) return fail(PPD_ERR_NOT_READY, "ppd_iterate: call ppd_set_weights first");
+    if (n_iters < 0) return fail(PPD_ERR_INVALID_ARG, "ppd_iterate: n_iters < 0");
+    int st = c->is_f32 ? run_iterations<float>(c, n_iters) : run_iterations<double>(c, n_iters);
+    if (st != PPD_OK) {
+        if (stats) stats->status = st;
+        return st;
+    }
+    if (stats) {
+        PPD_CHECK(reduce_primal_stats(c, c->stream));
+        double h[3];
+        std::vector<double> r2(c->d);
+        PPD_CUDA(cudaMemcpyAsync(h, c->stat_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+        PPD_CUDA(cudaMemcpyAsync(r2.data(), c->resid2, c->d * 8, cudaMemcpyDeviceToHost, c->stream));
+        PPD_CUDA(cudaStreamSynchronize(c->stream));
+        st = check_err_word(c);
+        stats->iters_done = c->iters;
+        stats->status = st;
+        stats->rel_var = h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::numeric_limits<double>::infinity();
+        stats->snr_db = c->xtrue_set && h[2] > 0 ? 20.0 * std::log10(std::sqrt(c->xtrue_norm2 / h[2]))
+                                                 : std::numeric_limits<double>::quiet_NaN();
+        double mx = 0;
+        for (int j = 0; j < c->d; ++j) {
+            const double rj = std::sqrt(r2[j]);
+            if (stats->block_residual) stats->block_residual[j] = rj;
+            mx = std::max(mx, rj / c->eps_h[j]);
+        }
+        stats->max_res_over_eps = mx;
+        if (!std::isfinite(h[0]) || !std::isfinite(h[1])) return fail(PPD_ERR_NONFINITE, "ppd_iterate: non-finite image");
+        return st;
+    }
+    return PPD_OK;
+}
+
+int ppd_get_image(ppd_ctx *c, double *x_out, int64_t len) {
+    if (!c || !x_out) return fail(PPD_ERR_INVALID_ARG, "ppd_get_image: NULL argument");
+    if (len != c->N) return fail(PPD_ERR_INVALID_ARG, "ppd_get_image: len must be n0*n1");
+    if (c->is_f32) {
+        std::vector<float> t(c->N);
+        PPD_CUDA(cudaMemcpyAsync(t.data(), c->x, c->N * 4, cudaMemcpyDeviceToHost, c->stream));
+        PPD_CUDA(cudaStreamSynchronize(c->stream));
+        for (int64_t i = 0; i < c->N; ++i) x_out[i] = t[i];
+    } else {
+        PPD_CUDA(cudaMemcpyAsync(x_out, c->x, c->N * 8, cudaMemcpyDeviceToHost, c->stream));
+        PPD_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    return PPD_OK;
+}
+
+int ppd_get_params(ppd_ctx *c, ppd_params *o) {
+    if (!c || !o) return fail(PPD_ERR_INVALID_ARG, "ppd_get_params: NULL argument");
+    if (!c->have_weights) return fail(PPD_ERR_NOT_READY, "ppd_get_params: call ppd_set_weights first");
+    o->eta = c->eta;
+    o->zeta = c->zeta;
+    o->tau = c->tau;
+    o->kappa = c->kappa;
+    o->op_norm_sq = c->op_norm_sq;
+    o->power_iters_done = c->power_done;
+    o->K0 = c->K0;
+    o->K1 = c->K1;
+    o->tile = c->T;
+    o->n_chunks = c->ch.n;
+    o->M = c->M;
+    const double phi2 = c->op_norm_sq > 0 ? c->op_norm_sq : 1.0 / c->eta;
+    o->convergence_lhs = c->tau * c->zeta * 1.0 + c->tau * c->eta * phi2;
+    return PPD_OK;
+}
+
+int ppd_get_bins(ppd_ctx *c, int64_t *perm, int32_t *base0, int32_t *base1, int32_t *count) {
+    if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_get_bins: NULL context");
+    if (!c->have_vis) return fail(PPD_ERR_NOT_READY, "ppd_get_bins: call ppd_set_visibilities first");
+    const int64_t M = c->M;
+    if (perm) std::copy(c->perm_h.begin(), c->perm_h.end(), perm);
+    if (base0) std::copy(c->base0_h.begin(), c->base0_h.end(), base0);
+    if (base1) std::copy(c->base1_h.begin(), c->base1_h.end(), base1);
+    if (count) std::copy(c->count_h.begin(), c->count_h.end(), count);
+    (void)M;
+    return PPD_OK;
+}
+
+int ppd_op_forward(ppd_ctx *c, const void *x_dev, void *y_dev, void *stream) {
+    if (!c || !x_dev || !y_dev) return fail(PPD_ERR_INVALID_ARG, "ppd_op_forward: NULL argument");
+    if (!c->have_weights) return fail(PPD_ERR_NOT_READY, "ppd_op_forward: call ppd_set_weights first");
+    cudaStream_t s = pick(c, stream);
+    if (c->is_f32) {
+        PPD_CHECK(fft_forward<float>(c, static_cast<const float *>(x_dev), static_cast<float2 *>(c->grid_a), s));
+        return degrid<float>(c, DG_OP, static_cast<float2 *>(c->grid_a), static_cast<float2 *>(y_dev), c->perm, s);
+    }
+    PPD_CHECK(fft_forward<double>(c, static_cast<const double *>(x_dev), static_cast<double2 *>(c->grid_a), s));
+    return degrid<double>(c, DG_OP, static_cast<double2 *>(c->grid_a), static_cast<double2 *>(y_dev), c->perm, s);
+}
+
+int ppd_op_adjoint(ppd_ctx *c, const void *y_dev, void *x_dev, void *stream) {
+    if (!c || !x_dev || !y_dev) return fail(PPD_ERR_INVALID_ARG, "ppd_op_adjoint: NULL argument");
+    if (!c->have_weights) return fail(PPD_ERR_NOT_READY, "ppd_op_adjoint: call ppd_set_weights first");
+    cudaStream_t s = pick(c, stream);
+    if (c->is_f32) {
+        PPD_CHECK(grid_vis<float>(c, GR_OP, static_cast<const float2 *>(y_dev), c->perm,
+                                  static_cast<float2 *>(c->grid_v), s));
+        return fft_inverse<float>(c, static_cast<const float2 *>(c->grid_v), static_cast<float *>(x_dev), s);
+    }
+    PPD_CHECK(grid_vis<double>(c, GR_OP, static_cast<const double2 *>(y_dev), c->perm,
+                               static_cast<double2 *>(c->grid_v), s));
+    return fft_inverse<double>(c, static_cast<const double2 *>(c->grid_v), static_cast<double *>(x_dev), s);
+}
+
+int ppd_psi_analysis(ppd_ctx *c, const void *x_dev, void *c_dev, void *stream) {
+    if (!c || !x_dev || !c_dev) return fail(PPD_ERR_INVALID_ARG, "ppd_psi_analysis: NULL argument");
+    cudaStream_t s = pick(c, stream);
+    if (c->is_f32) return psi_analysis<float>(c, static_cast<const float *>(x_dev), static_cast<float *>(c_dev), s);
+    return psi_analysis<double>(c, static_cast<const double *>(x_dev), static_cast<double *>(c_dev), s);
+}
+
+int ppd_psi_synthesis(ppd_ctx *c, const void *c_dev, void *x_dev, void *stream) {
+    if (!c || !x_dev || !c_dev) return fail(PPD_ERR_INVALID_ARG, "ppd_psi_synthesis: NULL argument");
+    cudaStream_t s = pick(c, stream);
+    if (c->is_f32) return psi_synthesis<float>(c, static_cast<const float *>(c_dev), static_cast<float *>(x_dev), s);
+    return psi_synthesis<double>(c, static_cast<const double *>(c_dev), static_cast<double *>(x_dev), s);
+}
+
+int ppd_timing_enable(ppd_ctx *c, int32_t enable) {
+    if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_timing_enable: NULL context");
+    if ((bool)enable != c->timing) {
+        c->timing = enable != 0;
+        drop_graph(c);
+    }
+    c->tsum.clear();
+    return PPD_OK;
+}
+
+int ppd_timing_collect(ppd_ctx *c) {
+    if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_timing_collect: NULL context");
+    PPD_CUDA(cudaStreamSynchronize(c->stream));
+    for (auto &t : c->sites_eager) {
+        float ms = 0;
+        PPD_CUDA(cudaEventElapsedTime(&ms, t.start, t.stop));
+        tsum_add(c, t.name, ms);
+        c->event_pool.push_back(t.start);
+        c->event_pool.push_back(t.stop);
+    }
+    c->sites_eager.clear();
+    if (c->graph_ran_since_collect) {
+        for (auto &t : c->sites_graph) {
+            float ms = 0;
+            PPD_CUDA(cudaEventElapsedTime(&ms, t.start, t.stop));
+            tsum_add(c, t.name, ms);
+        }
+        c->graph_ran_since_collect = false;
+    }
+    return PPD_OK;
+}
+
+int ppd_timing_read(ppd_ctx *c, int32_t n, const char **names, double *ms, int64_t *launches, int32_t *n_out) {
+    if (!c || !n_out) return fail(PPD_ERR_INVALID_ARG, "ppd_timing_read: NULL argument");
+    const int m = (int)std::min<size_t>((size_t)std::max(n, 0), c->tsum.size());
+    for (int i = 0; i < m; ++i) {
+        if (names) names[i] = c->tsum[i].first;
+        if (ms) ms[i] = c->tsum[i].second.first;
+        if (launches) launches[i] = c->tsum[i].second.second;
+    }
+    *n_out = (int32_t)c->tsum.size();
+    return PPD_OK;
+}
+
+int64_t ppd_launch_count(ppd_ctx *c) { return c ? c->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// Internal declarations of libppd (not part of the public ABI).
+//
+// Layout of the solver state in HBM (one context, one GPU):
+//   image side   x, xt, g (= Phi^dagger v), ut (= Psi u): n0*n1 reals each
+//                u: the 9 SARA dual images, basis-major, 9*n0*n1 reals
+//                grid_a (forward FFT output) and grid_v (gridding output):
+//                K0*K1 complex each, row-major, zero frequency at the centre
+//                (plain grid index k stored at (k + K/2) mod K)
+//   visibility   sorted by (tile, block, centred base row, centred base col,
+//   side         caller index); per visibility a 16 B (float) / 32 B (double)
+//                record {packed centred base cell, frac0, frac1, U} and the
+//                complex arrays y (whitened), v (dual), z, w (Algorithm 2
+//                work) and p (prox output, warm start)
+//   work items   "chunks": runs of <= chunk visibilities sharing one tile and
+//                one block; every gridding/degridding CTA owns one chunk
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ppd.h"
+
+namespace ppd {
+
+// ---------------------------------------------------------------- types
+template <typename R> struct Cplx;
+template <> struct Cplx<float> { using T = float2; };
+template <> struct Cplx<double> { using T = double2; };
+template <typename R> using cplx_t = typename Cplx<R>::T;
+
+template <typename R> struct VisRec;
+template <> struct __align__(16) VisRec<float> { int packed; float f0, f1, U; };
+template <> struct __align__(16) VisRec<double> { int packed; int pad; double f0, f1, U; };
+
+constexpr int KB_J = 8;          // interpolation taps per axis
+constexpr int KB_DEG = 9;        // degree of the per-tap FP32 weight polynomial
+constexpr int HALO = 8;          // extended tile = (T + HALO)^2 cells
+constexpr int N_BASES = 9;       // Dirac + db1..db8
+constexpr int N_WAVELETS = 8;
+constexpr int MAX_TAPS = 16;     // db8
+constexpr int NPART = 2;         // per-chunk norm partials: ||w-y||^2, ||Theta q - y||^2
+constexpr double INV_TWO_PI = 0.15915494309189535;
+
+// device error word bits
+constexpr int ERR_TMA_TIMEOUT = 1;
+constexpr int ERR_NONFINITE = 2;
+constexpr int ERR_BOUNDS = 4;
+
+// bounded spin for mbarrier waits (iterations of try_wait)
+constexpr long long SPIN_LIMIT = 1ll << 24;
+
+// ---------------------------------------------------------------- status
+struct Error {
+    int code;
+    std::string msg;
+};
+void set_last_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+
+#define PPD_CUDA(call)                                                                  \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return ::ppd::fail(e_ == cudaErrorMemoryAllocation ? PPD_ERR_OOM : PPD_ERR_CUDA, \
+                               std::string(#call) + ": " + cudaGetErrorString(e_));     \
+    } while (0)
+
+#define PPD_CHECK(call)                 \
+    do {                                \
+        int s_ = (call);                \
+        if (s_ != PPD_OK) return s_;    \
+    } while (0)
+
+// ---------------------------------------------------------------- context
+struct TimingSite {
+    const char *name;
+    cudaEvent_t start, stop;
+};
+
+struct Chunks {
+    int64_t n = 0;
+    int32_t *start = nullptr, *count = nullptr, *tile = nullptr, *block = nullptr;   // device
+    int32_t *tile_first = nullptr, *tile_n = nullptr;                                // device, n_tiles
+    int32_t *blk_ptr = nullptr, *blk_list = nullptr;                                 // device CSR
+};
+
+}  // namespace ppd
+
+struct ppd_ctx {
+    ppd_config cfg;
+    int is_f32 = 1;
+    size_t rsz = 4;            // sizeof(real)
+    int L0 = 0, L1 = 0, K0 = 0, K1 = 0, T = 32, C = 1024, levels = 4, d = 1;
+    int64_t N = 0;
+    double beta = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+
+    // image side
+    void *x = nullptr, *xt = nullptr, *g = nullptr, *ut = nullptr, *xtrue = nullptr;
+    void *u = nullptr, *wtmp = nullptr, *wtmp2 = nullptr;
+    void *grid_a = nullptr, *grid_v = nullptr, *fft_tmp = nullptr;
+    void *tw0 = nullptr, *tw1 = nullptr, *deap0 = nullptr, *deap1 = nullptr;
+    void *filt = nullptr;       // 8 x 16 reals (low-pass, zero padded)
+    void *kbpoly = nullptr;     // (KB_DEG+1) x 8 floats
+    double *prim_part = nullptr;
+    int n_prim_blocks = 0;
+    double *stat_out = nullptr; // 3 doubles
+
+    // visibility side
+    int64_t M = 0;
+    void *rec = nullptr, *theta_v = nullptr, *y = nullptr, *v = nullptr, *z = nullptr,
+         *w = nullptr, *p = nullptr, *y_raw = nullptr;
+    double theta_scalar = 1.0;
+    int64_t *perm = nullptr;
+    std::vector<int64_t> perm_h;
+    std::vector<int32_t> base0_h, base1_h, count_h, block_h, packed_h;
+    std::vector<double> frac_h, eps_h, mu_h;
+    std::vector<int64_t> block_count_h;
+    int32_t *count_cell = nullptr;   // per visibility (sorted order), device
+    ppd::Chunks ch;
+    double *partials = nullptr, *scale = nullptr, *resid2 = nullptr, *eps_d = nullptr,
+           *mu_d = nullptr;
+    void *gpart = nullptr;           // n_chunks x (T+HALO)^2 complex
+    int *err = nullptr;              // device error word
+    CUtensorMap tmap_a;              // TMA descriptor of grid_a
+    bool tma_ok = false;
+
+    // parameters
+    double eta = 0, zeta = 1, tau = 0.49, kappa = 1e-4, op_norm_sq = 0;
+    int power_done = 0;
+    bool have_vis = false, have_weights = false, p_valid = false;
+    int32_t iters = 0;
+    bool xtrue_set = false;
+    double xtrue_norm2 = 0;
+
+    // graph
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    int64_t graph_kernels = 0;
+
+    // timing
+    bool timing = false;
+    bool capturing = false;
+    std::vector<ppd::TimingSite> sites_graph;   // fixed sites inside the captured graph
+    std::vector<ppd::TimingSite> sites_eager;   // sites since last collect (eager launches)
+    std::vector<cudaEvent_t> event_pool;
+    std::vector<std::pair<const char *, std::pair<double, int64_t>>> tsum;
+    bool graph_ran_since_collect = false;
+    int64_t launches = 0;
+};
+
+namespace ppd {
+
+// launch bookkeeping: every kernel launch goes through these so that the
+// launch count and optional per-kernel events are recorded.
+int launch_begin(ppd_ctx *c, const char *name, cudaStream_t s, int *site);
+int launch_end(ppd_ctx *c, int site, cudaStream_t s);
+
+// ---------------------------------------------------------------- launchers
+// FFT (fft.cu)
+template <typename R> int fft_forward(ppd_ctx *c, const R *x, cplx_t<R> *grid, cudaStream_t s);
+template <typename R> int fft_inverse(ppd_ctx *c, const cplx_t<R> *grid, R *img, cudaStream_t s);
+int make_twiddles(ppd_ctx *c);
+int make_deapodisation(ppd_ctx *c);
+
+// visibilities (vis.cu)
+int bin_all(ppd_ctx *c, const double *uv_d, const int32_t *blk_d, int64_t M, uint64_t *key_d, int32_t *base_d,
+            double *frac_d, int32_t *count_d, int *bad_d);
+int make_kb_poly(ppd_ctx *c);
+
+enum DegridMode { DG_OP = 0, DG_DUAL = 1, DG_FIRST = 2 };
+enum GridMode { GR_OP = 0, GR_OP_U = 1, GR_DUAL = 2 };
+
+template <typename R>
+int degrid(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const int64_t *perm_out,
+           cudaStream_t s);
+template <typename R> int subiter(ppd_ctx *c, cudaStream_t s);
+int block_norms(ppd_ctx *c, int which, cudaStream_t s);
+template <typename R>
+int grid_vis(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm_in, cplx_t<R> *grid,
+             cudaStream_t s);
+
+// SARA (sara.cu)
+int make_filters(ppd_ctx *c);
+template <typename R> int psi_analysis(ppd_ctx *c, const R *x, R *coef, cudaStream_t s);
+template <typename R> int psi_synthesis(ppd_ctx *c, const R *coef, R *x, cudaStream_t s);
+template <typename R> int sara_dual_step(ppd_ctx *c, cudaStream_t s);
+
+// image side (image.cu)
+template <typename R> int primal_step(ppd_ctx *c, cudaStream_t s);
+int reduce_primal_stats(ppd_ctx *c, cudaStream_t s);
+template <typename R> int scale_copy(ppd_ctx *c, const R *in, R *out, int64_t n, double a, cudaStream_t s);
+template <typename R> int sumsq(ppd_ctx *c, const R *in, int64_t n, double *out_dev, cudaStream_t s);
+
+// host-side helpers
+std::vector<double> daubechies(int p);   // db_p low-pass filter (2p taps)
+
+}  // namespace ppd

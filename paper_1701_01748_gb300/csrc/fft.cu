@@ -1,0 +1,346 @@
+// Oversampled 2-D FFT with the zero-padding / scaling operator Z fused in
+// (Section 2: Phi = Theta G F Z; F is the unnormalised n-oversampled DFT).
+//
+// Forward  a = F Z x:  row pass   x (L x L real)  -> tmp (L x K complex)
+//                      column pass tmp            -> grid (K x K complex)
+// Inverse  Re(Z^T F^H grid): column pass grid -> tmp, row pass tmp -> image.
+//
+// Every pass is a batched Stockham radix-4 (one radix-2 stage when log2 K is
+// odd) FFT in shared memory: a CTA loads B whole rows (row pass) or a strip of
+// W columns (column pass), runs log K stages with one shared buffer (each
+// thread keeps its butterflies in registers between the read and the write
+// half of a stage) and writes the result.  Only the L nonzero rows/columns of
+// the padded image are read or produced; the grid is stored with the zero
+// frequency at the centre (plain index k at (k + K/2) mod K).
+#include <cmath>
+
+#include "common.cuh"
+
+namespace ppd {
+
+namespace {
+
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C cconj(C a) { return C{a.x, -a.y}; }
+
+__host__ __device__ constexpr int ilog2_(int k) { return k <= 1 ? 0 : 1 + ilog2_(k / 2); }
+
+// In-place batched Stockham FFT (forward sign) of NSEQ sequences of length K
+// held in shared memory.  INTERLEAVED: element (s, i) at i*NSEQ + s;
+// otherwise at s*K + i.  tw[m] = exp(-2 pi i m / K).
+template <typename R, int K, int NSEQ, int NT, bool INTERLEAVED>
+__device__ void fft_smem(cplx_t<R> *buf, const cplx_t<R> *__restrict__ tw) {
+    using C = cplx_t<R>;
+    const int tid = threadIdx.x;
+    constexpr int LOG2K = ilog2_(K);
+    int Ns = 1;
+    auto idx = [](int s, int i) { return INTERLEAVED ? i * NSEQ + s : s * K + i; };
+    if (LOG2K & 1) {   // one radix-2 stage (Ns = 1: no twiddles)
+        constexpr int NB = NSEQ * K / 2 / NT;
+        static_assert(NB >= 1 && NSEQ * K / 2 % NT == 0, "radix-2 work split");
+        C v[NB][2];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            int bf = tid + b * NT;
+            int s = INTERLEAVED ? bf % NSEQ : bf / (K / 2);
+            int j = INTERLEAVED ? bf / NSEQ : bf % (K / 2);
+            C a0 = buf[idx(s, j)], a1 = buf[idx(s, j + K / 2)];
+            v[b][0] = cadd(a0, a1);
+            v[b][1] = csub(a0, a1);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            int bf = tid + b * NT;
+            int s = INTERLEAVED ? bf % NSEQ : bf / (K / 2);
+            int j = INTERLEAVED ? bf / NSEQ : bf % (K / 2);
+            buf[idx(s, 2 * j)] = v[b][0];
+            buf[idx(s, 2 * j + 1)] = v[b][1];
+        }
+        __syncthreads();
+        Ns = 2;
+    }
+    constexpr int NB = NSEQ * K / 4 / NT;
+    static_assert(NB >= 1 && NSEQ * K / 4 % NT == 0, "radix-4 work split");
+    for (; Ns < K; Ns *= 4) {
+        C v[NB][4];
+        const int twstep = K / (Ns * 4);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            int bf = tid + b * NT;
+            int s = INTERLEAVED ? bf % NSEQ : bf / (K / 4);
+            int j = INTERLEAVED ? bf / NSEQ : bf % (K / 4);
+            int k = j & (Ns - 1);
+            C a0 = buf[idx(s, j)];
+            C a1 = buf[idx(s, j + K / 4)];
+            C a2 = buf[idx(s, j + K / 2)];
+            C a3 = buf[idx(s, j + 3 * K / 4)];
+            if (Ns > 1) {
+                a1 = cmul(a1, __ldg(&tw[(1 * k * twstep) & (K - 1)]));
+                a2 = cmul(a2, __ldg(&tw[(2 * k * twstep) & (K - 1)]));
+                a3 = cmul(a3, __ldg(&tw[(3 * k * twstep) & (K - 1)]));
+            }
+            C t0 = cadd(a0, a2), t1 = csub(a0, a2);
+            C t2 = cadd(a1, a3), t3 = csub(a1, a3);
+            // X1 = t1 - i t3, X3 = t1 + i t3
+            v[b][0] = cadd(t0, t2);
+            v[b][1] = C{t1.x + t3.y, t1.y - t3.x};
+            v[b][2] = csub(t0, t2);
+            v[b][3] = C{t1.x - t3.y, t1.y + t3.x};
+        }
+        __syncthreads();
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            int bf = tid + b * NT;
+            int s = INTERLEAVED ? bf % NSEQ : bf / (K / 4);
+            int j = INTERLEAVED ? bf / NSEQ : bf % (K / 4);
+            int k = j & (Ns - 1);
+            int d = (j / Ns) * Ns * 4 + k;
+            buf[idx(s, d)] = v[b][0];
+            buf[idx(s, d + Ns)] = v[b][1];
+            buf[idx(s, d + 2 * Ns)] = v[b][2];
+            buf[idx(s, d + 3 * Ns)] = v[b][3];
+        }
+        __syncthreads();
+    }
+}
+
+constexpr int NT = 256;
+
+// rows per CTA in a row pass (32 KB of shared memory)
+template <typename R> __host__ __device__ constexpr int rows_per_cta(int K) {
+    return (sizeof(R) == 4 ? 4096 : 2048) / K > 0 ? (sizeof(R) == 4 ? 4096 : 2048) / K : 1;
+}
+// columns per CTA in a column pass (64 KB of shared memory), at most K
+template <typename R> __host__ __device__ constexpr int cols_per_cta(int K) {
+    return (sizeof(R) == 4 ? 8192 : 4096) / K < K ? (sizeof(R) == 4 ? 8192 : 4096) / K : K;
+}
+
+// forward row pass: tmp[n0][c] = FFT_axis1(Z x)[n0][(c + K/2) mod K]
+template <typename R, int K>
+__global__ void __launch_bounds__(NT) k_rows_fwd(const R *__restrict__ x, cplx_t<R> *__restrict__ tmp,
+                                                 const cplx_t<R> *__restrict__ tw, const R *__restrict__ s0,
+                                                 const R *__restrict__ s1, int L) {
+    using C = cplx_t<R>;
+    constexpr int B = rows_per_cta<R>(K);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const int row0 = blockIdx.x * B;
+    for (int e = threadIdx.x; e < B * K; e += NT) buf[e] = C{0, 0};
+    __syncthreads();
+    for (int e = threadIdx.x; e < B * L; e += NT) {
+        int s = e / L, n1 = e % L, n0 = row0 + s;
+        if (n0 < L) {
+            int pos = (n1 - L / 2 + K) & (K - 1);
+            buf[s * K + pos] = C{s0[n0] * s1[n1] * x[(int64_t)n0 * L + n1], R(0)};
+        }
+    }
+    __syncthreads();
+    fft_smem<R, K, B, NT, false>(buf, tw);
+    for (int e = threadIdx.x; e < B * K; e += NT) {
+        int s = e / K, c = e % K, n0 = row0 + s;
+        if (n0 < L) tmp[(int64_t)n0 * K + c] = buf[s * K + ((c + K / 2) & (K - 1))];
+    }
+}
+
+// forward column pass: grid[r][c] = FFT_axis0(tmp padded)[(r + K/2) mod K][c]
+template <typename R, int K>
+__global__ void __launch_bounds__(NT) k_cols_fwd(const cplx_t<R> *__restrict__ tmp, cplx_t<R> *__restrict__ grid,
+                                                 const cplx_t<R> *__restrict__ tw, int L) {
+    using C = cplx_t<R>;
+    constexpr int W = cols_per_cta<R>(K);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const int c0 = blockIdx.x * W;
+    for (int e = threadIdx.x; e < W * K; e += NT) buf[e] = C{0, 0};
+    __syncthreads();
+    for (int e = threadIdx.x; e < W * L; e += NT) {
+        int s = e % W, n0 = e / W;
+        int pos = (n0 - L / 2 + K) & (K - 1);
+        buf[pos * W + s] = tmp[(int64_t)n0 * K + c0 + s];
+    }
+    __syncthreads();
+    fft_smem<R, K, W, NT, true>(buf, tw);
+    for (int e = threadIdx.x; e < W * K; e += NT) {
+        int s = e % W, r = e / W;
+        grid[(int64_t)r * K + c0 + s] = buf[((r + K / 2) & (K - 1)) * W + s];
+    }
+}
+
+// inverse column pass: tmp[n0][c] = (F^H along axis 0 of grid)[(n0 - L/2) mod K][c]
+template <typename R, int K>
+__global__ void __launch_bounds__(NT) k_cols_inv(const cplx_t<R> *__restrict__ grid, cplx_t<R> *__restrict__ tmp,
+                                                 const cplx_t<R> *__restrict__ tw, int L) {
+    using C = cplx_t<R>;
+    constexpr int W = cols_per_cta<R>(K);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const int c0 = blockIdx.x * W;
+    for (int e = threadIdx.x; e < W * K; e += NT) {
+        int s = e % W, r = e / W;   // r: stored (centred) row; natural frequency (r + K/2) mod K
+        buf[((r + K / 2) & (K - 1)) * W + s] = cconj(grid[(int64_t)r * K + c0 + s]);
+    }
+    __syncthreads();
+    fft_smem<R, K, W, NT, true>(buf, tw);
+    for (int e = threadIdx.x; e < W * L; e += NT) {
+        int s = e % W, n0 = e / W;
+        int pos = (n0 - L / 2 + K) & (K - 1);
+        tmp[(int64_t)n0 * K + c0 + s] = cconj(buf[pos * W + s]);
+    }
+}
+
+// inverse row pass: img[n0][n1] = s0 s1 Re(F^H along axis 1 of tmp)[n0][(n1 - L/2) mod K]
+template <typename R, int K>
+__global__ void __launch_bounds__(NT) k_rows_inv(const cplx_t<R> *__restrict__ tmp, R *__restrict__ img,
+                                                 const cplx_t<R> *__restrict__ tw, const R *__restrict__ s0,
+                                                 const R *__restrict__ s1, int L) {
+    using C = cplx_t<R>;
+    constexpr int B = rows_per_cta<R>(K);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const int row0 = blockIdx.x * B;
+    for (int e = threadIdx.x; e < B * K; e += NT) {
+        int s = e / K, c = e % K, n0 = row0 + s;
+        C val = C{0, 0};
+        if (n0 < L) val = cconj(tmp[(int64_t)n0 * K + c]);
+        buf[s * K + ((c + K / 2) & (K - 1))] = val;
+    }
+    __syncthreads();
+    fft_smem<R, K, B, NT, false>(buf, tw);
+    for (int e = threadIdx.x; e < B * L; e += NT) {
+        int s = e / L, n1 = e % L, n0 = row0 + s;
+        if (n0 < L) {
+            int pos = (n1 - L / 2 + K) & (K - 1);
+            img[(int64_t)n0 * L + n1] = s0[n0] * s1[n1] * buf[s * K + pos].x;
+        }
+    }
+}
+
+template <typename R, int K> int fft_fwd_k(ppd_ctx *c, const R *x, cplx_t<R> *grid, cudaStream_t s) {
+    constexpr int B = rows_per_cta<R>(K), W = cols_per_cta<R>(K);
+    const int L = c->L0;
+    size_t shr = (size_t)B * K * sizeof(cplx_t<R>), shc = (size_t)W * K * sizeof(cplx_t<R>);
+    static bool attr = false;
+    if (!attr) {
+        PPD_CUDA(cudaFuncSetAttribute(k_rows_fwd<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shr));
+        PPD_CUDA(cudaFuncSetAttribute(k_cols_fwd<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shc));
+        attr = true;
+    }
+    int site;
+    PPD_CHECK(launch_begin(c, "fft_fwd_rows", s, &site));
+    k_rows_fwd<R, K><<<(L + B - 1) / B, NT, shr, s>>>(x, static_cast<cplx_t<R> *>(c->fft_tmp),
+                                                     static_cast<const cplx_t<R> *>(c->tw0),
+                                                     static_cast<const R *>(c->deap0),
+                                                     static_cast<const R *>(c->deap1), L);
+    PPD_CHECK(launch_end(c, site, s));
+    PPD_CHECK(launch_begin(c, "fft_fwd_cols", s, &site));
+    k_cols_fwd<R, K><<<K / W, NT, shc, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp), grid,
+                                            static_cast<const cplx_t<R> *>(c->tw0), L);
+    PPD_CHECK(launch_end(c, site, s));
+    return PPD_OK;
+}
+
+template <typename R, int K> int fft_inv_k(ppd_ctx *c, const cplx_t<R> *grid, R *img, cudaStream_t s) {
+    constexpr int B = rows_per_cta<R>(K), W = cols_per_cta<R>(K);
+    const int L = c->L0;
+    size_t shr = (size_t)B * K * sizeof(cplx_t<R>), shc = (size_t)W * K * sizeof(cplx_t<R>);
+    static bool attr = false;
+    if (!attr) {
+        PPD_CUDA(cudaFuncSetAttribute(k_rows_inv<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shr));
+        PPD_CUDA(cudaFuncSetAttribute(k_cols_inv<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shc));
+        attr = true;
+    }
+    int site;
+    PPD_CHECK(launch_begin(c, "fft_inv_cols", s, &site));
+    k_cols_inv<R, K><<<K / W, NT, shc, s>>>(grid, static_cast<cplx_t<R> *>(c->fft_tmp),
+                                            static_cast<const cplx_t<R> *>(c->tw0), L);
+    PPD_CHECK(launch_end(c, site, s));
+    PPD_CHECK(launch_begin(c, "fft_inv_rows", s, &site));
+    k_rows_inv<R, K><<<(L + B - 1) / B, NT, shr, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp), img,
+                                                     static_cast<const cplx_t<R> *>(c->tw0),
+                                                     static_cast<const R *>(c->deap0),
+                                                     static_cast<const R *>(c->deap1), L);
+    PPD_CHECK(launch_end(c, site, s));
+    return PPD_OK;
+}
+
+}  // namespace
+
+template <typename R> int fft_forward(ppd_ctx *c, const R *x, cplx_t<R> *grid, cudaStream_t s) {
+    switch (c->K0) {
+        case 32: return fft_fwd_k<R, 32>(c, x, grid, s);
+        case 64: return fft_fwd_k<R, 64>(c, x, grid, s);
+        case 128: return fft_fwd_k<R, 128>(c, x, grid, s);
+        case 256: return fft_fwd_k<R, 256>(c, x, grid, s);
+        case 512: return fft_fwd_k<R, 512>(c, x, grid, s);
+        case 1024: return fft_fwd_k<R, 1024>(c, x, grid, s);
+        case 2048: return fft_fwd_k<R, 2048>(c, x, grid, s);
+        case 4096: return fft_fwd_k<R, 4096>(c, x, grid, s);
+        default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
+    }
+}
+
+template <typename R> int fft_inverse(ppd_ctx *c, const cplx_t<R> *grid, R *img, cudaStream_t s) {
+    switch (c->K0) {
+        case 32: return fft_inv_k<R, 32>(c, grid, img, s);
+        case 64: return fft_inv_k<R, 64>(c, grid, img, s);
+        case 128: return fft_inv_k<R, 128>(c, grid, img, s);
+        case 256: return fft_inv_k<R, 256>(c, grid, img, s);
+        case 512: return fft_inv_k<R, 512>(c, grid, img, s);
+        case 1024: return fft_inv_k<R, 1024>(c, grid, img, s);
+        case 2048: return fft_inv_k<R, 2048>(c, grid, img, s);
+        case 4096: return fft_inv_k<R, 4096>(c, grid, img, s);
+        default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
+    }
+}
+
+template int fft_forward<float>(ppd_ctx *, const float *, float2 *, cudaStream_t);
+template int fft_forward<double>(ppd_ctx *, const double *, double2 *, cudaStream_t);
+template int fft_inverse<float>(ppd_ctx *, const float2 *, float *, cudaStream_t);
+template int fft_inverse<double>(ppd_ctx *, const double2 *, double *, cudaStream_t);
+
+// Twiddles exp(-2 pi i m / K), m < K, computed in double on the host.
+int make_twiddles(ppd_ctx *c) {
+    const int K = c->K0;
+    std::vector<double> t(2 * (size_t)K);
+    for (int m = 0; m < K; ++m) {
+        double a = -2.0 * M_PI * (double)m / (double)K;
+        t[2 * m] = std::cos(a);
+        t[2 * m + 1] = std::sin(a);
+    }
+    if (c->is_f32) {
+        std::vector<float> f(t.begin(), t.end());
+        PPD_CUDA(cudaMemcpy(c->tw0, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+    } else {
+        PPD_CUDA(cudaMemcpy(c->tw0, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    return PPD_OK;
+}
+
+// Z's scaling s(n) = 1 / psi_hat((n - L/2)/K), psi_hat(f) = (J / I0(beta)) sinh(q)/q,
+// q = sqrt(beta^2 - (pi J f)^2): the Fourier transform of the Kaiser-Bessel kernel.
+int make_deapodisation(ppd_ctx *c) {
+    const int L = c->L0, K = c->K0;
+    const double J = KB_J, beta = c->beta, i0b = std::cyl_bessel_i(0.0, beta);
+    std::vector<double> s(L);
+    for (int n = 0; n < L; ++n) {
+        double f = ((double)n - L / 2) / (double)K;
+        double q = std::sqrt(beta * beta - (M_PI * J * f) * (M_PI * J * f));
+        s[n] = 1.0 / ((J / i0b) * std::sinh(q) / q);
+    }
+    if (c->is_f32) {
+        std::vector<float> f(s.begin(), s.end());
+        PPD_CUDA(cudaMemcpy(c->deap0, f.data(), L * sizeof(float), cudaMemcpyHostToDevice));
+        PPD_CUDA(cudaMemcpy(c->deap1, f.data(), L * sizeof(float), cudaMemcpyHostToDevice));
+    } else {
+        PPD_CUDA(cudaMemcpy(c->deap0, s.data(), L * sizeof(double), cudaMemcpyHostToDevice));
+        PPD_CUDA(cudaMemcpy(c->deap1, s.data(), L * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    return PPD_OK;
+}
+
+}  // namespace ppd

@@ -1,0 +1,615 @@
+// Visibility-side kernels of PPD.
+//
+//  * binning (Section 2: G's 8 x 8 Kaiser-Bessel taps, Section 5: n = 4
+//    oversampling; Section 4.3 / Section 5: sampling density per grid cell)
+//  * degridding G with the data step of Algorithm 3 fused in (z = U^-1 v +
+//    Theta G a, first forward-backward step of Algorithm 2, block norms)
+//  * extra Algorithm 2 sub-iterations and the per-block l2-ball scale
+//  * gridding G^dagger Theta^dagger v with the dual update fused in
+//    (vbar = U (z - P_B(w))), accumulated per tile in shared memory and
+//    summed across work items in a fixed order (deterministic, no atomics)
+//
+// Work decomposition: visibilities are sorted by (tile of the centred grid
+// holding the first tap, block, base cell); a "chunk" is a run of at most C
+// visibilities of one tile and one block, and each CTA owns one chunk.  The
+// CTA stages the (T+8) x (T+8) extended grid tile in shared memory (TMA for
+// interior tiles, wrapped plain loads at the grid edge) for degridding, or
+// accumulates into it for gridding.
+#include <cmath>
+
+#include "common.cuh"
+#include "tma.cuh"
+
+namespace ppd {
+
+namespace {
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+
+// ----------------------------------------------------------------- binning
+// kappa = (omega * K) * (1/(2 pi)) with correctly rounded multiplies (no FMA
+// contraction possible), f = floor(kappa), first tap (f - 3) mod K, fraction
+// kappa - f, nearest cell floor(kappa + 0.5) mod K.
+__global__ void k_bin(const double *__restrict__ uv, const int32_t *__restrict__ blk, int64_t M, int K0, int K1,
+                      int T, int d, uint64_t *__restrict__ key, int32_t *__restrict__ base,
+                      double *__restrict__ frac, int32_t *__restrict__ cell, int32_t *__restrict__ count_grid,
+                      int *__restrict__ bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const double om0 = uv[2 * i], om1 = uv[2 * i + 1];
+        const int b = blk[i];
+        if (!(om0 >= -M_PI && om0 <= M_PI && om1 >= -M_PI && om1 <= M_PI) || b < 0 || b >= d) {
+            atomicOr(bad, 1);
+            key[i] = 0;
+            continue;
+        }
+        const double k0 = __dmul_rn(__dmul_rn(om0, (double)K0), INV_TWO_PI);
+        const double k1 = __dmul_rn(__dmul_rn(om1, (double)K1), INV_TWO_PI);
+        const double f0 = floor(k0), f1 = floor(k1);
+        const int64_t i0 = (int64_t)f0, i1 = (int64_t)f1;
+        const int b0 = (int)(((i0 - 3) % K0 + K0) % K0);
+        const int b1 = (int)(((i1 - 3) % K1 + K1) % K1);
+        const int cb0 = (b0 + K0 / 2) % K0, cb1 = (b1 + K1 / 2) % K1;
+        const int64_t n0 = (((int64_t)floor(__dadd_rn(k0, 0.5))) % K0 + K0) % K0;
+        const int64_t n1 = (((int64_t)floor(__dadd_rn(k1, 0.5))) % K1 + K1) % K1;
+        const uint64_t tile = (uint64_t)(cb0 / T) * (uint64_t)(K1 / T) + (uint64_t)(cb1 / T);
+        key[i] = ((tile * (uint64_t)d + (uint64_t)b) * (uint64_t)K0 + (uint64_t)cb0) * (uint64_t)K1 + (uint64_t)cb1;
+        base[2 * i] = b0;
+        base[2 * i + 1] = b1;
+        frac[2 * i] = __dsub_rn(k0, f0);
+        frac[2 * i + 1] = __dsub_rn(k1, f1);
+        const int c = (int)(n0 * K1 + n1);
+        cell[i] = c;
+        atomicAdd(&count_grid[c], 1);
+    }
+}
+
+__global__ void k_cell_count(const int32_t *__restrict__ cell, const int32_t *__restrict__ count_grid, int64_t M,
+                             int32_t *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = count_grid[cell[i]];
+}
+
+// ----------------------------------------------------------------- weights
+// FP32: per tap j a degree-KB_DEG polynomial in t = 2 frac - 1 (Chebyshev fit
+// of psi(frac + 3 - j) made on the host); coefficients poly[k*8 + j].
+__device__ __forceinline__ void kb_weights(float frac, float (&w)[KB_J], const float *poly, double, double) {
+    const float t = fmaf(2.0f, frac, -1.0f);
+#pragma unroll
+    for (int j = 0; j < KB_J; ++j) w[j] = poly[KB_DEG * KB_J + j];
+#pragma unroll
+    for (int k = KB_DEG - 1; k >= 0; --k)
+#pragma unroll
+        for (int j = 0; j < KB_J; ++j) w[j] = fmaf(w[j], t, poly[k * KB_J + j]);
+}
+
+// FP64: the kernel itself, psi(d) = I0(beta sqrt(1 - (d/4)^2)) / I0(beta), d = frac + 3 - j.
+__device__ __forceinline__ void kb_weights(double frac, double (&w)[KB_J], const float *, double beta,
+                                           double inv_i0b) {
+#pragma unroll
+    for (int j = 0; j < KB_J; ++j) {
+        const double dd = (frac + (double)(3 - j)) * 0.25;
+        const double x = 1.0 - dd * dd;
+        w[j] = x >= 0.0 ? cyl_bessel_i0(beta * sqrt(x)) * inv_i0b : 0.0;
+    }
+}
+
+template <typename R> struct VisArgs {
+    const VisRec<R> *rec;
+    const R *theta_v;
+    R theta_s;
+    const int32_t *ch_start, *ch_count, *ch_tile, *ch_block;
+    int K0, K1, ntile1;
+    const float *kbpoly;
+    double beta, inv_i0b;
+    const cplx_t<R> *y;
+    cplx_t<R> *v, *z, *w, *p;
+    const double *mu, *scale;
+    double *partials;
+    int *err;
+    // operator mode I/O (caller order through perm when non-null)
+    const cplx_t<R> *op_in;
+    cplx_t<R> *op_out;
+    const int64_t *perm;
+};
+
+// Deterministic CTA sum of two doubles per thread (fixed shuffle tree, then
+// warps in order).
+template <int NT> __device__ void cta_sum2(double a, double b, double *out2) {
+    __shared__ double red[2][NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[0][wid] = a;
+        red[1][wid] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0, s1 = 0;
+        for (int i = 0; i < NT / 32; ++i) {
+            s0 += red[0][i];
+            s1 += red[1][i];
+        }
+        out2[0] = s0;
+        out2[1] = s1;
+    }
+}
+
+// Kahan-compensated FP32 accumulator (FP64 accumulation in the FP64 path).
+template <typename R> struct Acc {
+    R s = 0, c = 0;
+    __device__ void add(R x) {
+        R y = x - c;
+        R t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ double get() const { return (double)s - (double)c; }
+};
+
+constexpr int DG_NT = 256;
+
+// ----------------------------------------------------------------- degrid
+// mode DG_OP:    op_out[perm[i]] = Theta G a
+// mode DG_DUAL:  z = v/U + Theta G a;  w = p - mu U (p - z)
+// mode DG_FIRST: z = v/U + Theta G a;  w = z   (Algorithm 2 then starts from P_B(z))
+// partials[chunk] = (||w - y||^2, ||Theta G a - y||^2)
+template <typename R, int T, int MODE>
+__global__ void __launch_bounds__(DG_NT) k_degrid(const __grid_constant__ CUtensorMap tmap, int use_tma,
+                                                 const cplx_t<R> *__restrict__ grid, VisArgs<R> A) {
+    using C = cplx_t<R>;
+    constexpr int E = T + HALO;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    C *tile = reinterpret_cast<C *>(smem_raw);                       // E*E, 128-B aligned
+    float *poly = reinterpret_cast<float *>(smem_raw + E * E * sizeof(C));
+    __shared__ uint64_t bar;
+    __shared__ int ok_s;
+
+    const int ch = blockIdx.x;
+    const int start = A.ch_start[ch], count = A.ch_count[ch], tl = A.ch_tile[ch];
+    const int row0 = (tl / A.ntile1) * T, col0 = (tl % A.ntile1) * T;
+    const bool edge = (row0 + E > A.K0) || (col0 + E > A.K1);
+
+    for (int i = threadIdx.x; i < (KB_DEG + 1) * KB_J; i += DG_NT) poly[i] = A.kbpoly ? A.kbpoly[i] : 0.f;
+    if (use_tma && !edge) {
+        if (threadIdx.x == 0) {
+            ok_s = 1;
+            mbar_init(&bar, 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(&bar, (uint32_t)(E * E * sizeof(C)));
+            tma_load_2d(tile, &tmap, 2 * col0, row0, &bar);
+        }
+        if (!mbar_wait(&bar, 0, SPIN_LIMIT)) {
+            atomicOr(A.err, ERR_TMA_TIMEOUT);
+            ok_s = 0;
+            mbar_wait(&bar, 0, SPIN_LIMIT);   // second bounded wait for the copy in flight
+        }
+        __syncthreads();
+        if (!ok_s) return;
+    } else {
+        for (int e = threadIdx.x; e < E * E; e += DG_NT) {
+            const int r = e / E, cc = e % E;
+            tile[e] = grid[(int64_t)((row0 + r) % A.K0) * A.K1 + (col0 + cc) % A.K1];
+        }
+        __syncthreads();
+    }
+
+    double mu = 0;
+    if (MODE != DG_OP) mu = A.mu[A.ch_block[ch]];
+    Acc<R> s_w, s_r;
+    for (int i = threadIdx.x; i < count; i += DG_NT) {
+        const int gi = start + i;
+        const VisRec<R> rc = A.rec[gi];
+        const int lb0 = (rc.packed & 0xffff) - row0, lb1 = ((rc.packed >> 16) & 0xffff) - col0;
+        R w0[KB_J], w1[KB_J];
+        kb_weights(rc.f0, w0, poly, A.beta, A.inv_i0b);
+        kb_weights(rc.f1, w1, poly, A.beta, A.inv_i0b);
+        C q{0, 0};
+#pragma unroll
+        for (int a = 0; a < KB_J; ++a) {
+            const C *row = tile + (lb0 + a) * E + lb1;
+            C r{0, 0};
+#pragma unroll
+            for (int b = 0; b < KB_J; ++b) {
+                const C g = row[b];
+                r.x += w1[b] * g.x;
+                r.y += w1[b] * g.y;
+            }
+            q.x += w0[a] * r.x;
+            q.y += w0[a] * r.y;
+        }
+        const R th = A.theta_v ? A.theta_v[gi] : A.theta_s;
+        const C phix{th * q.x, th * q.y};
+        if (MODE == DG_OP) {
+            A.op_out[A.perm ? A.perm[gi] : gi] = phix;
+        } else {
+            const C vv = A.v[gi], yy = A.y[gi];
+            const R invU = R(1) / rc.U;
+            const C zz{vv.x * invU + phix.x, vv.y * invU + phix.y};
+            A.z[gi] = zz;
+            C ww;
+            if (MODE == DG_FIRST) {
+                ww = zz;
+            } else {
+                const C pp = A.p[gi];
+                const R mu_u = (R)mu * rc.U;
+                ww = C{pp.x - mu_u * (pp.x - zz.x), pp.y - mu_u * (pp.y - zz.y)};
+            }
+            A.w[gi] = ww;
+            const R dx = ww.x - yy.x, dy = ww.y - yy.y;
+            s_w.add(dx * dx + dy * dy);
+            const R ex = phix.x - yy.x, ey = phix.y - yy.y;
+            s_r.add(ex * ex + ey * ey);
+        }
+    }
+    if (MODE != DG_OP) cta_sum2<DG_NT>(s_w.get(), s_r.get(), A.partials + NPART * (int64_t)ch);
+}
+
+// ----------------------------------------------------------------- sub-iteration
+// Algorithm 2 step with the block scale c of the previous step:
+//   p = P_B(w) = y + c (w - y);  w = p - mu U (p - z);  partial ||w - y||^2
+template <typename R>
+__global__ void __launch_bounds__(DG_NT) k_subiter(VisArgs<R> A) {
+    using C = cplx_t<R>;
+    const int ch = blockIdx.x;
+    const int start = A.ch_start[ch], count = A.ch_count[ch], blk = A.ch_block[ch];
+    const R c = (R)A.scale[blk], mu = (R)A.mu[blk];
+    Acc<R> s_w;
+    for (int i = threadIdx.x; i < count; i += DG_NT) {
+        const int gi = start + i;
+        const R U = A.rec[gi].U;
+        const C yy = A.y[gi], ww = A.w[gi], zz = A.z[gi];
+        const C pp{yy.x + c * (ww.x - yy.x), yy.y + c * (ww.y - yy.y)};
+        const R mu_u = mu * U;
+        const C wn{pp.x - mu_u * (pp.x - zz.x), pp.y - mu_u * (pp.y - zz.y)};
+        A.w[gi] = wn;
+        const R dx = wn.x - yy.x, dy = wn.y - yy.y;
+        s_w.add(dx * dx + dy * dy);
+    }
+    __shared__ double o2[2];
+    cta_sum2<DG_NT>(s_w.get(), 0.0, o2);
+    if (threadIdx.x == 0) A.partials[NPART * (int64_t)ch] = o2[0];
+}
+
+// ----------------------------------------------------------------- block norms
+// One warp per block j: n2 = sum of the block's chunk partials (fixed order),
+// scale_j = eps_j / ||w_j - y_j|| if that norm exceeds eps_j, else 1 (the
+// l2-ball projection P_B of Section 3.3 as a radial scale).
+__global__ void k_block_norms(const double *__restrict__ partials, const int32_t *__restrict__ blk_ptr,
+                              const int32_t *__restrict__ blk_list, const double *__restrict__ eps, int d,
+                              int with_resid, double *__restrict__ scale, double *__restrict__ resid2,
+                              int *__restrict__ err) {
+    const int j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (j >= d) return;
+    double a = 0, b = 0;
+    for (int k = blk_ptr[j] + lane; k < blk_ptr[j + 1]; k += 32) {
+        const int ch = blk_list[k];
+        a += partials[NPART * (int64_t)ch];
+        if (with_resid) b += partials[NPART * (int64_t)ch + 1];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+        const double n = sqrt(a);
+        if (!isfinite(n)) atomicOr(err, ERR_NONFINITE);
+        scale[j] = (n > eps[j]) ? eps[j] / n : 1.0;
+        if (with_resid) resid2[j] = b;
+    }
+}
+
+// ----------------------------------------------------------------- gridding
+// Per CTA: phase 1 (thread per visibility) forms Theta v and the 16 weights
+// into a staging area; phase 2 (warp per visibility) adds the 8 x 8
+// footprint into the warp's private (T+8)^2 tile; phase 3 sums the private
+// tiles in warp order and writes the chunk's partial tile.  GR_DUAL fuses the
+// end of the data step: p = P_B(w) = y + c (w - y), v = U (z - p).
+template <typename R> struct GridCfg;
+template <> struct GridCfg<float> { static constexpr int NWARP = 8; };
+template <> struct GridCfg<double> { static constexpr int NWARP = 4; };
+
+template <typename R, int T, int MODE>
+__global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, cplx_t<R> *__restrict__ gpart) {
+    using C = cplx_t<R>;
+    constexpr int NW = GridCfg<R>::NWARP, NT = NW * 32;
+    constexpr int E = T + HALO, P = E + 1;   // P: padded pitch of the private tiles
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    C *priv = reinterpret_cast<C *>(smem_raw);                          // NW * E * P
+    R *sw0 = reinterpret_cast<R *>(priv + NW * E * P);                  // NT * 8
+    R *sw1 = sw0 + NT * KB_J;                                           // NT * 8
+    C *sv = reinterpret_cast<C *>(sw1 + NT * KB_J);                     // NT
+    int *slb = reinterpret_cast<int *>(sv + NT);                        // NT
+    float *poly = reinterpret_cast<float *>(slb + NT);                  // 80
+
+    const int ch = blockIdx.x;
+    const int start = A.ch_start[ch], count = A.ch_count[ch], tl = A.ch_tile[ch];
+    const int row0 = (tl / A.ntile1) * T, col0 = (tl % A.ntile1) * T;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < (KB_DEG + 1) * KB_J; i += NT) poly[i] = A.kbpoly ? A.kbpoly[i] : 0.f;
+    for (int e = threadIdx.x; e < NW * E * P; e += NT) priv[e] = C{0, 0};
+    R c = 0;
+    if (MODE == GR_DUAL) c = (R)A.scale[A.ch_block[ch]];
+    __syncthreads();
+
+    C *mine = priv + warp * E * P;
+    const int a = lane & 7, bb = (lane >> 3) * 2;
+    for (int base = 0; base < count; base += NT) {
+        const int n = min(NT, count - base);
+        if (threadIdx.x < n) {
+            const int gi = start + base + threadIdx.x;
+            const VisRec<R> rc = A.rec[gi];
+            C vv;
+            if (MODE == GR_DUAL) {
+                const C yy = A.y[gi], ww = A.w[gi], zz = A.z[gi];
+                const C pp{yy.x + c * (ww.x - yy.x), yy.y + c * (ww.y - yy.y)};
+                vv = C{rc.U * (zz.x - pp.x), rc.U * (zz.y - pp.y)};
+                A.v[gi] = vv;
+                A.p[gi] = pp;
+            } else {
+                vv = A.op_in[A.perm ? A.perm[gi] : gi];
+                if (MODE == GR_OP_U) vv = C{rc.U * vv.x, rc.U * vv.y};
+            }
+            const R th = A.theta_v ? A.theta_v[gi] : A.theta_s;
+            sv[threadIdx.x] = C{th * vv.x, th * vv.y};
+            R w0[KB_J], w1[KB_J];
+            kb_weights(rc.f0, w0, poly, A.beta, A.inv_i0b);
+            kb_weights(rc.f1, w1, poly, A.beta, A.inv_i0b);
+#pragma unroll
+            for (int j = 0; j < KB_J; ++j) {
+                sw0[threadIdx.x * KB_J + j] = w0[j];
+                sw1[threadIdx.x * KB_J + j] = w1[j];
+            }
+            const int lb0 = (rc.packed & 0xffff) - row0, lb1 = ((rc.packed >> 16) & 0xffff) - col0;
+            slb[threadIdx.x] = lb0 | (lb1 << 16);
+        }
+        __syncthreads();
+        for (int i = warp; i < n; i += NW) {
+            const int lb = slb[i];
+            const int r = (lb & 0xffff) + a, cc = (lb >> 16) + bb;
+            const C tv = sv[i];
+            const R wa = sw0[i * KB_J + a];
+            const R wb0 = wa * sw1[i * KB_J + bb], wb1 = wa * sw1[i * KB_J + bb + 1];
+            C *cell = mine + r * P + cc;
+            C g0 = cell[0], g1 = cell[1];
+            g0.x += wb0 * tv.x;
+            g0.y += wb0 * tv.y;
+            g1.x += wb1 * tv.x;
+            g1.y += wb1 * tv.y;
+            cell[0] = g0;
+            cell[1] = g1;
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+    C *out = gpart + (int64_t)ch * E * E;
+    for (int e = threadIdx.x; e < E * E; e += NT) {
+        const int r = e / E, cc = e % E;
+        C s{0, 0};
+#pragma unroll
+        for (int k = 0; k < NW; ++k) s = cadd(s, priv[k * E * P + r * P + cc]);
+        out[e] = s;
+    }
+}
+
+// ----------------------------------------------------------------- combine
+// grid[r][c] = sum of the partial tiles covering the cell, in a fixed order:
+// the cell's own tile's chunks, then the halo rows/columns of the tiles
+// above, left and above-left (periodic grid).
+template <typename R, int T>
+__global__ void k_combine(const cplx_t<R> *__restrict__ gpart, const int32_t *__restrict__ tile_first,
+                          const int32_t *__restrict__ tile_n, int K0, int K1, cplx_t<R> *__restrict__ grid) {
+    using C = cplx_t<R>;
+    constexpr int E = T + HALO;
+    const int nt0 = K0 / T, nt1 = K1 / T;
+    const int64_t total = (int64_t)K0 * K1;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / K1), c = (int)(e % K1);
+        const int t0 = r / T, t1 = c / T, lr = r % T, lc = c % T;
+        C acc{0, 0};
+        auto add_tile = [&](int tt0, int tt1, int rr, int cc) {
+            const int t = tt0 * nt1 + tt1;
+            const int f = tile_first[t], n = tile_n[t];
+            for (int k = 0; k < n; ++k) acc = cadd(acc, gpart[(int64_t)(f + k) * E * E + rr * E + cc]);
+        };
+        add_tile(t0, t1, lr, lc);
+        const int up = (t0 + nt0 - 1) % nt0, left = (t1 + nt1 - 1) % nt1;
+        if (lr < HALO) add_tile(up, t1, lr + T, lc);
+        if (lc < HALO) add_tile(t0, left, lr, lc + T);
+        if (lr < HALO && lc < HALO) add_tile(up, left, lr + T, lc + T);
+        grid[e] = acc;
+    }
+}
+
+template <typename R> VisArgs<R> make_args(ppd_ctx *c) {
+    VisArgs<R> A{};
+    A.rec = static_cast<const VisRec<R> *>(c->rec);
+    A.theta_v = static_cast<const R *>(c->theta_v);
+    A.theta_s = (R)c->theta_scalar;
+    A.ch_start = c->ch.start;
+    A.ch_count = c->ch.count;
+    A.ch_tile = c->ch.tile;
+    A.ch_block = c->ch.block;
+    A.K0 = c->K0;
+    A.K1 = c->K1;
+    A.ntile1 = c->K1 / c->T;
+    A.kbpoly = static_cast<const float *>(c->kbpoly);
+    A.beta = c->beta;
+    A.inv_i0b = 1.0 / std::cyl_bessel_i(0.0, c->beta);
+    A.y = static_cast<const cplx_t<R> *>(c->y);
+    A.v = static_cast<cplx_t<R> *>(c->v);
+    A.z = static_cast<cplx_t<R> *>(c->z);
+    A.w = static_cast<cplx_t<R> *>(c->w);
+    A.p = static_cast<cplx_t<R> *>(c->p);
+    A.mu = c->mu_d;
+    A.scale = c->scale;
+    A.partials = c->partials;
+    A.err = c->err;
+    return A;
+}
+
+template <typename R, int T> size_t grid_smem() {
+    constexpr int NW = GridCfg<R>::NWARP, NT = NW * 32, E = T + HALO, P = E + 1;
+    return (size_t)NW * E * P * sizeof(cplx_t<R>) + 2 * NT * KB_J * sizeof(R) + NT * sizeof(cplx_t<R>) +
+           NT * sizeof(int) + (KB_DEG + 1) * KB_J * sizeof(float);
+}
+
+template <typename R, int T>
+int degrid_t(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const int64_t *perm, cudaStream_t s) {
+    VisArgs<R> A = make_args<R>(c);
+    A.op_out = out;
+    A.perm = perm;
+    constexpr int E = T + HALO;
+    const size_t sh = E * E * sizeof(cplx_t<R>) + (KB_DEG + 1) * KB_J * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        PPD_CUDA(cudaFuncSetAttribute(k_degrid<R, T, DG_OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+        PPD_CUDA(cudaFuncSetAttribute(k_degrid<R, T, DG_DUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+        PPD_CUDA(cudaFuncSetAttribute(k_degrid<R, T, DG_FIRST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+        attr = true;
+    }
+    const int use_tma = (c->tma_ok && grid == c->grid_a) ? 1 : 0;
+    if (c->ch.n == 0) return PPD_OK;
+    int site;
+    PPD_CHECK(launch_begin(c, mode == DG_OP ? "degrid_op" : "degrid_dual", s, &site));
+    const unsigned nb = (unsigned)c->ch.n;
+    if (mode == DG_OP) k_degrid<R, T, DG_OP><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A);
+    else if (mode == DG_DUAL) k_degrid<R, T, DG_DUAL><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A);
+    else k_degrid<R, T, DG_FIRST><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A);
+    return launch_end(c, site, s);
+}
+
+template <typename R, int T>
+int grid_t(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_t<R> *grid, cudaStream_t s) {
+    VisArgs<R> A = make_args<R>(c);
+    A.op_in = in;
+    A.perm = perm;
+    const size_t sh = grid_smem<R, T>();
+    static bool attr = false;
+    if (!attr) {
+        PPD_CUDA(cudaFuncSetAttribute(k_grid<R, T, GR_OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+        PPD_CUDA(cudaFuncSetAttribute(k_grid<R, T, GR_OP_U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+        PPD_CUDA(cudaFuncSetAttribute(k_grid<R, T, GR_DUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+        attr = true;
+    }
+    constexpr int NT = GridCfg<R>::NWARP * 32;
+    cplx_t<R> *gp = static_cast<cplx_t<R> *>(c->gpart);
+    int site;
+    if (c->ch.n > 0) {
+        PPD_CHECK(launch_begin(c, mode == GR_DUAL ? "grid_dual" : "grid_op", s, &site));
+        const unsigned nb = (unsigned)c->ch.n;
+        if (mode == GR_OP) k_grid<R, T, GR_OP><<<nb, NT, sh, s>>>(A, gp);
+        else if (mode == GR_OP_U) k_grid<R, T, GR_OP_U><<<nb, NT, sh, s>>>(A, gp);
+        else k_grid<R, T, GR_DUAL><<<nb, NT, sh, s>>>(A, gp);
+        PPD_CHECK(launch_end(c, site, s));
+    }
+    PPD_CHECK(launch_begin(c, "grid_combine", s, &site));
+    const int64_t cells = (int64_t)c->K0 * c->K1;
+    const int nblk = (int)std::min<int64_t>((cells + 255) / 256, 152 * 16);
+    k_combine<R, T><<<nblk, 256, 0, s>>>(gp, c->ch.tile_first, c->ch.tile_n, c->K0, c->K1, grid);
+    return launch_end(c, site, s);
+}
+
+}  // namespace
+
+// Binning entry used by the API: fills key, base (2 per vis), frac (2 per
+// vis), per-visibility cell count.
+int bin_all(ppd_ctx *c, const double *uv_d, const int32_t *blk_d, int64_t M, uint64_t *key_d, int32_t *base_d,
+            double *frac_d, int32_t *count_d, int *bad_d) {
+    int32_t *cell_d = nullptr, *cgrid = nullptr;
+    PPD_CUDA(cudaMalloc(&cell_d, M * sizeof(int32_t)));
+    PPD_CUDA(cudaMalloc(&cgrid, (size_t)c->K0 * c->K1 * sizeof(int32_t)));
+    PPD_CUDA(cudaMemsetAsync(cgrid, 0, (size_t)c->K0 * c->K1 * sizeof(int32_t), c->stream));
+    const int nb = (int)std::min<int64_t>((M + 255) / 256, 152 * 32);
+    k_bin<<<nb, 256, 0, c->stream>>>(uv_d, blk_d, M, c->K0, c->K1, c->T, c->d, key_d, base_d, frac_d, cell_d, cgrid,
+                                     bad_d);
+    k_cell_count<<<nb, 256, 0, c->stream>>>(cell_d, cgrid, M, count_d);
+    c->launches += 2;
+    PPD_CUDA(cudaGetLastError());
+    PPD_CUDA(cudaStreamSynchronize(c->stream));
+    PPD_CUDA(cudaFree(cell_d));
+    PPD_CUDA(cudaFree(cgrid));
+    return PPD_OK;
+}
+
+// Chebyshev interpolation (degree KB_DEG, in t = 2 frac - 1) of each tap's
+// weight psi(frac + 3 - j), converted to monomial coefficients for Horner.
+int make_kb_poly(ppd_ctx *c) {
+    const int n = KB_DEG + 1;
+    const double beta = c->beta, i0b = std::cyl_bessel_i(0.0, beta);
+    std::vector<float> out((size_t)n * KB_J);
+    for (int j = 0; j < KB_J; ++j) {
+        std::vector<double> fk(n), cheb(n, 0.0);
+        for (int k = 0; k < n; ++k) {
+            const double t = std::cos(M_PI * (k + 0.5) / n);
+            const double d = (t + 1.0) * 0.5 + 3.0 - j;
+            const double x = 1.0 - (d / 4.0) * (d / 4.0);
+            fk[k] = x >= 0 ? std::cyl_bessel_i(0.0, beta * std::sqrt(x)) / i0b : 0.0;
+        }
+        for (int m = 0; m < n; ++m) {
+            double s = 0;
+            for (int k = 0; k < n; ++k) s += fk[k] * std::cos(M_PI * m * (k + 0.5) / n);
+            cheb[m] = s * (m == 0 ? 1.0 : 2.0) / n;
+        }
+        // Chebyshev -> monomial: T_0 = 1, T_1 = t, T_{m+1} = 2 t T_m - T_{m-1}
+        std::vector<double> mono(n, 0.0), Tm1(n, 0.0), Tm(n, 0.0), Tn(n, 0.0);
+        Tm1[0] = 1.0;
+        Tm[1] = 1.0;
+        for (int k = 0; k < n; ++k) mono[k] += cheb[0] * Tm1[k];
+        if (n > 1)
+            for (int k = 0; k < n; ++k) mono[k] += cheb[1] * Tm[k];
+        for (int m = 2; m < n; ++m) {
+            for (int k = 0; k < n; ++k) Tn[k] = (k > 0 ? 2.0 * Tm[k - 1] : 0.0) - Tm1[k];
+            for (int k = 0; k < n; ++k) mono[k] += cheb[m] * Tn[k];
+            Tm1 = Tm;
+            Tm = Tn;
+        }
+        for (int k = 0; k < n; ++k) out[(size_t)k * KB_J + j] = (float)mono[k];
+    }
+    PPD_CUDA(cudaMemcpy(c->kbpoly, out.data(), out.size() * sizeof(float), cudaMemcpyHostToDevice));
+    return PPD_OK;
+}
+
+template <typename R>
+int degrid(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const int64_t *perm, cudaStream_t s) {
+    return c->T == 16 ? degrid_t<R, 16>(c, mode, grid, out, perm, s) : degrid_t<R, 32>(c, mode, grid, out, perm, s);
+}
+
+template <typename R>
+int grid_vis(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_t<R> *grid, cudaStream_t s) {
+    return c->T == 16 ? grid_t<R, 16>(c, mode, in, perm, grid, s) : grid_t<R, 32>(c, mode, in, perm, grid, s);
+}
+
+template <typename R> int subiter(ppd_ctx *c, cudaStream_t s) {
+    if (c->ch.n == 0) return PPD_OK;
+    int site;
+    PPD_CHECK(launch_begin(c, "subiter", s, &site));
+    k_subiter<R><<<(unsigned)c->ch.n, DG_NT, 0, s>>>(make_args<R>(c));
+    return launch_end(c, site, s);
+}
+
+int block_norms(ppd_ctx *c, int with_resid, cudaStream_t s) {
+    int site;
+    PPD_CHECK(launch_begin(c, "block_norms", s, &site));
+    const int wpb = 8;
+    k_block_norms<<<(c->d + wpb - 1) / wpb, wpb * 32, 0, s>>>(c->partials, c->ch.blk_ptr, c->ch.blk_list, c->eps_d,
+                                                               c->d, with_resid, c->scale, c->resid2, c->err);
+    return launch_end(c, site, s);
+}
+
+template int degrid<float>(ppd_ctx *, int, const float2 *, float2 *, const int64_t *, cudaStream_t);
+template int degrid<double>(ppd_ctx *, int, const double2 *, double2 *, const int64_t *, cudaStream_t);
+template int grid_vis<float>(ppd_ctx *, int, const float2 *, const int64_t *, float2 *, cudaStream_t);
+template int grid_vis<double>(ppd_ctx *, int, const double2 *, const int64_t *, double2 *, cudaStream_t);
+template int subiter<float>(ppd_ctx *, cudaStream_t);
+template int subiter<double>(ppd_ctx *, cudaStream_t);
+
+}  // namespace ppd

@@ -1,0 +1,292 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative l2 unless stated): bins, sort order and cell counts
+bit-exact; Phi, Phi^dagger, Psi, Psi^dagger <= 1e-5 in FP32 (<= 1e-10 in
+FP64); image after a fixed number of PPD iterations <= 1e-4 in FP32 (<= 1e-8
+in FP64); gradients of 1/2 ||y - Phi x||^2 <= 1e-3 against finite
+differences.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import nufft, ppd as oppd, sara  # noqa: E402
+from paper_1701_01748_gb300 import build, ppd, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+F32, F64 = ppd.PPD_FP32_FP64NORMS, ppd.PPD_FP64_PLAIN
+TOL = {F32: dict(op=1e-5, img=1e-4), F64: dict(op=1e-10, img=1e-8)}
+
+
+@pytest.fixture(scope="session", autouse=True)
+def lib():
+    build.build()
+    assert torch.cuda.is_available()
+    return ppd._lib()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def tdtype(prec):
+    return torch.float32 if prec == F32 else torch.float64
+
+
+def solver(p, prec, **cfg):
+    s = ppd.Solver(p.L, p.n_blocks, precision=prec, **cfg)
+    s.set_problem(p.omega, p.y, p.block, theta=p.theta, x_true=p.x_true)
+    return s
+
+
+def stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def op_forward(s, x, prec):
+    xd = torch.tensor(x, dtype=tdtype(prec), device="cuda")
+    yd = torch.empty((s.M, 2), dtype=tdtype(prec), device="cuda")
+    ppd.ppd_op_forward(s.ctx, xd.data_ptr(), yd.data_ptr(), stream())
+    torch.cuda.synchronize()
+    return yd.cpu().double().numpy() @ np.array([1.0, 1j])
+
+
+def op_adjoint(s, y, prec):
+    yd = torch.tensor(np.stack([y.real, y.imag], 1), dtype=tdtype(prec), device="cuda")
+    xd = torch.empty((s.L, s.L), dtype=tdtype(prec), device="cuda")
+    ppd.ppd_op_adjoint(s.ctx, yd.data_ptr(), xd.data_ptr(), stream())
+    torch.cuda.synchronize()
+    return xd.cpu().double().numpy()
+
+
+SMALL = dict(L=32, M=3000, n_blocks=3, uv_sigma=0.3, seed=11, n_points=6, n_blobs=1)
+_cache = {}
+
+
+def problem(name, **kw):
+    key = (name, tuple(sorted(kw.items())))
+    if key not in _cache:
+        _cache[key] = synth.make_problem(name, **kw)
+    return _cache[key]
+
+
+# ----------------------------------------------------------------- binning
+@pytest.mark.parametrize("which", ["small", "c1", "edges"])
+def test_bins_and_order_bit_exact(which):
+    if which == "small":
+        p = problem("small", **SMALL)
+        om, blk, L, d = p.omega, p.block, p.L, p.n_blocks
+    elif which == "c1":
+        p = problem("c1_128")
+        om, blk, L, d = p.omega, p.block, p.L, p.n_blocks
+    else:
+        L, d = 64, 2
+        rng = np.random.default_rng(3)
+        om = rng.uniform(-np.pi, np.pi, size=(500, 2))
+        om[:8] = [[-np.pi, -np.pi], [np.pi, np.pi], [0.0, -0.0], [-1e-300, 1e-300],
+                  [-5e-17, 3.0], [np.nextafter(-np.pi, 0), 0.1], [1.5, -1.5], [1.5, -1.5]]
+        blk = rng.integers(0, d, size=500).astype(np.int32)
+    s = ppd.Solver(L, d, precision=F32)
+    y = np.zeros(om.shape[0], np.complex128) + 1.0
+    ppd.ppd_set_visibilities(s.ctx, om, y, blk)
+    perm, b0, b1, cnt = ppd.ppd_get_bins(s.ctx, om.shape[0])
+    K = 2 * L
+    ob0, ob1, _, _ = nufft.base_cells(om, K, K)
+    _, ocnt = nufft.uniform_weights(om, K, K)
+    T = 32 if K >= 80 else 16
+    operm, _, _, _ = nufft.visibility_order(om, blk, K, K, T)
+    assert np.array_equal(b0, ob0) and np.array_equal(b1, ob1)
+    assert np.array_equal(cnt, ocnt)
+    assert np.array_equal(perm, operm)
+    s.close()
+
+
+# ----------------------------------------------------------------- operators
+@pytest.mark.parametrize("prec", [F32, F64])
+@pytest.mark.parametrize("name", ["small", "c1_128"])
+def test_phi_and_adjoint(prec, name):
+    p = problem("small", **SMALL) if name == "small" else problem(name)
+    s = solver(p, prec, eta=1.0)
+    P = nufft.Plan(p.omega, p.L, theta=p.theta)
+    rng = np.random.default_rng(5)
+    x = rng.random((p.L, p.L))
+    assert rel(op_forward(s, x, prec), nufft.phi(x, P)) <= TOL[prec]["op"]
+    yv = rng.normal(size=p.M) + 1j * rng.normal(size=p.M)
+    assert rel(op_adjoint(s, yv, prec), nufft.phi_adjoint(yv, P)) <= TOL[prec]["op"]
+    # adjoint identity of the GPU operators themselves
+    a = float(np.vdot(op_forward(s, x, prec), yv).real)
+    b = float(np.sum(x * op_adjoint(s, yv, prec)))
+    assert abs(a - b) <= TOL[prec]["op"] * abs(a)
+    s.close()
+
+
+def test_phi_full_size_c2():
+    p = problem("c2_512")
+    s = solver(p, F32, eta=1.0)
+    P = nufft.Plan(p.omega, p.L, theta=p.theta)
+    x = p.x_true
+    assert rel(op_forward(s, x, F32), nufft.phi(x, P)) <= 1e-5
+    yv = np.random.default_rng(2).normal(size=p.M) * (1 + 0j)
+    assert rel(op_adjoint(s, yv, F32), nufft.phi_adjoint(yv, P)) <= 1e-5
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
+def test_psi_analysis_synthesis(prec):
+    p = problem("small", **SMALL)
+    s = solver(p, prec, eta=1.0)
+    x = np.random.default_rng(8).normal(size=(p.L, p.L))
+    xd = torch.tensor(x, dtype=tdtype(prec), device="cuda")
+    cd = torch.empty((9, p.L, p.L), dtype=tdtype(prec), device="cuda")
+    ppd.ppd_psi_analysis(s.ctx, xd.data_ptr(), cd.data_ptr(), stream())
+    torch.cuda.synchronize()
+    ref = sara.psi_adjoint(x)
+    assert rel(cd.cpu().double().numpy(), ref) <= TOL[prec]["op"]
+    u = np.random.default_rng(9).normal(size=(9, p.L, p.L))
+    ud = torch.tensor(u, dtype=tdtype(prec), device="cuda")
+    ppd.ppd_psi_synthesis(s.ctx, ud.data_ptr(), xd.data_ptr(), stream())
+    torch.cuda.synchronize()
+    assert rel(xd.cpu().double().numpy(), sara.psi(u)) <= TOL[prec]["op"]
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
+def test_eta_power_iteration(prec):
+    p = problem("small", **SMALL)
+    P = nufft.Plan(p.omega, p.L, theta=p.theta)
+    U = nufft.uniform_weights(p.omega, 2 * p.L, 2 * p.L)[0]
+    ref, _ = oppd.op_norm_sq(P, U, max_iter=1000, tol=1e-10)
+    s = solver(p, prec)
+    got = s.params()
+    assert abs(got["op_norm_sq"] - ref) <= (1e-5 if prec == F32 else 1e-8) * ref
+    assert got["convergence_lhs"] < 1.0
+    s.close()
+
+
+# ----------------------------------------------------------------- PPD
+def run_both(p, prec, n_iter, **kw):
+    n_itr = kw.pop("n_itr", 1)
+    precond = kw.pop("precond", 1)
+    init = kw.pop("inner_init", ppd.PPD_INNER_WARM)
+    S = oppd.make_setup(p.omega, p.y, p.theta, p.block, p.n_blocks, p.L, precond=bool(precond),
+                        n_itr=n_itr, power_iters=400, x_true=p.x_true)
+    s = ppd.Solver(p.L, p.n_blocks, precision=prec, eta=S.eta, n_itr=n_itr, precond=precond,
+                   inner_init=init, **kw)
+    s.set_problem(p.omega, p.y, p.block, theta=p.theta, x_true=p.x_true)
+    st = oppd.init_state(S)
+    for _ in range(n_iter):
+        hist = oppd.iterate(st, S)
+    stats = s.iterate(n_iter)
+    xg = s.image()
+    s.close()
+    return xg, st, hist, stats, S
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
+def test_ppd_c1_fixed_iterations(prec):
+    p = problem("c1_128")
+    n = 200 if prec == F64 else 200
+    xg, st, hist, stats, S = run_both(p, prec, n)
+    assert rel(xg, st.x) <= TOL[prec]["img"], rel(xg, st.x)
+    assert abs(stats["snr_db"] - hist["snr"]) <= 1e-3
+    assert abs(stats["rel_var"] - hist["rel_var"]) <= 1e-2 * hist["rel_var"] + 1e-9
+    assert np.allclose(stats["block_residual"], hist["residual"], rtol=1e-4)
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
+def test_ppd_multiblock_subiterations_weights(prec):
+    p = problem("small", **SMALL)
+    p2 = synth.Problem(**{**p.__dict__})
+    p2.theta = p.theta * np.random.default_rng(4).uniform(0.5, 2.0, size=p.M)   # non-uniform Theta
+    xg, st, hist, stats, S = run_both(p2, prec, 30, n_itr=3)
+    assert rel(xg, st.x) <= TOL[prec]["img"], rel(xg, st.x)
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
+def test_pd_special_case_and_graph_off(prec):
+    p = problem("small", **SMALL)
+    xg, st, hist, stats, S = run_both(p, prec, 25, precond=0, use_graph=0)
+    assert rel(xg, st.x) <= TOL[prec]["img"], rel(xg, st.x)
+
+
+def test_ppd_c2_fixed_iterations():
+    p = problem("c2_512")
+    P = nufft.Plan(p.omega, p.L, theta=p.theta)
+    U = nufft.uniform_weights(p.omega, 2 * p.L, 2 * p.L)[0]
+    eta = 1.0 / oppd.op_norm_sq(P, U, max_iter=8, tol=1e-3)[0]
+    S = oppd.make_setup(p.omega, p.y, p.theta, p.block, p.n_blocks, p.L, eta=eta, x_true=p.x_true)
+    st = oppd.init_state(S)
+    for _ in range(5):
+        hist = oppd.iterate(st, S)
+    s = ppd.Solver(p.L, p.n_blocks, precision=F32, eta=eta)
+    s.set_problem(p.omega, p.y, p.block, theta=p.theta, x_true=p.x_true)
+    stats = s.iterate(5)
+    assert rel(s.image(), st.x) <= 1e-4
+    assert np.allclose(stats["block_residual"], hist["residual"], rtol=1e-4)
+    s.close()
+
+
+# ----------------------------------------------------------------- autograd
+@pytest.mark.parametrize("prec", [F32, F64])
+def test_phi_autograd_gradient(prec):
+    from paper_1701_01748_gb300 import torch_ops
+    p = problem("small", **SMALL)
+    s = solver(p, prec, eta=1.0)
+    P = nufft.Plan(p.omega, p.L, theta=p.theta)
+    x0 = p.x_true
+    yw = p.theta * p.y
+    x = torch.tensor(x0, dtype=tdtype(prec), device="cuda", requires_grad=True)
+    yt = torch.tensor(yw, dtype=torch.complex64 if prec == F32 else torch.complex128, device="cuda")
+    loss = 0.5 * (torch_ops.phi(x, s) - yt).abs().pow(2).sum()
+    loss.backward()
+    g = x.grad.cpu().double().numpy()
+    g_ref = nufft.phi_adjoint(nufft.phi(x0, P) - yw, P)
+    assert rel(g, g_ref) <= (1e-5 if prec == F32 else 1e-10)
+    # central finite differences of the oracle loss along random directions
+    rng = np.random.default_rng(3)
+    f = lambda z: 0.5 * float(np.sum(np.abs(nufft.phi(z, P) - yw) ** 2))
+    for _ in range(3):
+        dvec = rng.normal(size=x0.shape)
+        h = 1e-4
+        fd = (f(x0 + h * dvec) - f(x0 - h * dvec)) / (2 * h)
+        assert abs(fd - float(np.sum(g * dvec))) <= 1e-3 * abs(fd)
+    s.close()
+
+
+# ----------------------------------------------------------------- errors
+def test_error_codes():
+    p = problem("small", **SMALL)
+    s = ppd.Solver(p.L, p.n_blocks, precision=F32)
+    with pytest.raises(ppd.PPDError) as e:
+        ppd.ppd_set_weights(s.ctx)
+    assert e.value.status == ppd.PPD_ERR_NOT_READY
+    with pytest.raises(ppd.PPDError) as e:
+        ppd.ppd_iterate(s.ctx, 1)
+    assert e.value.status == ppd.PPD_ERR_NOT_READY
+    bad = p.omega.copy()
+    bad[3, 0] = 4.0
+    with pytest.raises(ppd.PPDError) as e:
+        ppd.ppd_set_visibilities(s.ctx, bad, p.y, p.block)
+    assert e.value.status == ppd.PPD_ERR_INVALID_ARG
+    ynan = p.y.copy()
+    ynan[5] = np.nan
+    with pytest.raises(ppd.PPDError) as e:
+        ppd.ppd_set_visibilities(s.ctx, p.omega, ynan, p.block)
+    assert e.value.status == ppd.PPD_ERR_INVALID_ARG
+    blk = p.block.copy()
+    blk[0] = p.n_blocks
+    with pytest.raises(ppd.PPDError) as e:
+        ppd.ppd_set_visibilities(s.ctx, p.omega, p.y, blk)
+    assert e.value.status == ppd.PPD_ERR_INVALID_ARG
+    ppd.ppd_set_visibilities(s.ctx, p.omega, p.y, p.block)
+    with pytest.raises(ppd.PPDError) as e:
+        ppd.ppd_set_weights(s.ctx, theta=-np.ones(p.M))
+    assert e.value.status == ppd.PPD_ERR_INVALID_ARG
+    ppd.ppd_set_weights(s.ctx, theta=p.theta)
+    out = s.iterate(2)
+    assert out["iters_done"] == 2 and math.isfinite(out["rel_var"])
+    s.close()
