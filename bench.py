@@ -1,0 +1,389 @@
+"""Benchmark of the PPD hot path on one GB300 (or N independent replicas).
+
+Workload (default): 512 x 512 image, 524,288 visibilities drawn from a
+strongly non-uniform Gaussian u-v density (std 0.1 pi), 16 uneven radial
+blocks, 30 dB input SNR, seeded synthetic sky (point sources and Gaussian
+blobs).  A step is one PPD iteration (Algorithm 3: forward FFT + degridding
+with the data step, block norms, gridding with the dual update, inverse FFT,
+SARA prior step, primal step) on inputs resident in HBM; L2 is flushed
+(256 MiB write) between timed steps, outside the timed region.
+
+Printed JSON line (rank 0): PPD iterations per second of the FP32-batched
+path (FP32 arrays, FP64 norms, one CUDA graph per iteration), with the FP64
+plain path, the SNR reached after 500 iterations by each, the iterations and
+seconds the FP32 path needs to reach the FP64 path's SNR, an end-to-end
+number through the host API, the roofline of the dominant kernel and the
+FP64 oracle timed on the host cores.
+
+--impl reference times the oracle itself (one oracle PPD iteration per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "PPD iters/s and time-to-target-SNR, FP32-batched vs FP64-plain on 1 GB300"
+UNIT = "iters/s"
+SNR_ITERS = 500
+WORKLOAD = "c2_512"
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ------------------------------------------------------------------ roofline model
+def algorithmic_bytes(name: str, L: int, M: int, d: int, rsz: int = 4) -> float:
+    """Algorithmic HBM bytes of one launch (FP32: real 4 B, complex 8 B)."""
+    N, K2 = L * L, 4 * L * L
+    c = 2 * rsz
+    table = {
+        # record (16) + v, y, p in; z, w out
+        "degrid_dual": (16 + 3 * c + 2 * c) * M + c * K2,
+        # record, y, w, z in; v, p out; grid written once
+        "grid_dual": (16 + 3 * c + 2 * c) * M + c * K2,
+        "grid_combine": c * K2,
+        "fft_fwd_rows": rsz * N + c * 2 * N,
+        "fft_fwd_cols": c * 2 * N + c * K2,
+        "fft_inv_cols": c * K2 + c * 2 * N,
+        "fft_inv_rows": c * 2 * N + rsz * N,
+        # x, xt, g, ut, u0 in; x, xt, u0 out
+        "primal": 8 * rsz * N,
+        "block_norms": 8.0 * 0,
+        "subiter": (16 + 3 * c + c) * M,
+    }
+    return float(table.get(name, 0.0))
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the measured region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return out
+        sm, smax, busy, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                s, mx, util = float(r[1]), float(r[2]), float(r[9])
+            except Exception:
+                continue
+            sm.append(s)
+            smax.append(mx)
+            if util > 0:
+                busy.append(s)
+            for n, v in zip(names, r[5:9]):
+                if v.strip() == "Active":
+                    reasons.add(n)
+        if sm:
+            out["sm_mhz"] = statistics.median(busy if busy else sm)
+            out["sm_max_mhz"] = max(smax)
+            out["samples"] = len(sm)
+            out["samples_busy"] = len(busy)
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def oracle_worker(args):
+    """Run in a fresh single-threaded interpreter: time oracle PPD iterations."""
+    from oracle import ppd as oppd
+    from paper_1701_01748_gb300 import synth
+    p = synth.make_problem(args.workload, seed=args.seed)
+    S = oppd.make_setup(p.omega, p.y, p.theta, p.block, p.n_blocks, p.L, eta=1.0, x_true=p.x_true)
+    st = oppd.init_state(S)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oppd.iterate(st, S)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    print(json.dumps({"times": times}))
+
+
+def run_oracle(workload: str, seed: int, steps: int, warmup: int):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", "--workload", workload,
+           "--seed", str(seed), "--steps", str(steps), "--warmup", str(warmup)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])["times"]
+
+
+def cpu_info():
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")) and not model:
+                model = line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return model, os.cpu_count()
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--seed", type=int, default=None)
+    ap.add_argument("--oracle-worker", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-steps", type=int, default=3)
+    ap.add_argument("--quick", action="store_true",
+                    help="only the timed FP32 steps (for profiler launch lists); eta from 20 power steps")
+    args = ap.parse_args()
+    if args.oracle_worker:
+        oracle_worker(args)
+        return
+    rank, world, local = _env_rank()
+    from paper_1701_01748_gb300 import synth
+    base_seed = synth.CONFIGS[args.workload]["seed"]
+    seed = (args.seed if args.seed is not None else base_seed) + 1000 * rank
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        times = run_oracle(args.workload, seed, args.steps, max(args.warmup, 0))
+        v = len(times) / sum(times)
+        model, ncpu = cpu_info()
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "image": "512x512", "visibilities": 524288,
+                           "blocks": 16, "uv_density": "gaussian sigma=0.1pi", "isnr_db": 30},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"{len(times)} oracle PPD iterations of the workload "
+                                           f"(FP64 NumPy, 1 thread) on {model} ({ncpu} cores)"},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    from paper_1701_01748_gb300 import build, ppd
+    build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    p = synth.make_problem(args.workload, seed=seed)
+    stream = torch.cuda.Stream(dev)
+    sp = stream.cuda_stream
+
+    def make(prec, **kw):
+        s = ppd.Solver(p.L, p.n_blocks, precision=prec, stream=sp, **kw)
+        s.set_problem(p.omega, p.y, p.block, theta=p.theta, x_true=p.x_true)
+        return s
+
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    if args.quick:
+        s32 = make(ppd.PPD_FP32_FP64NORMS, power_iters=20)
+    else:
+        s32 = make(ppd.PPD_FP32_FP64NORMS)
+        s64 = make(ppd.PPD_FP64_PLAIN)
+
+    def timed_steps(s, steps, warmup, kernel_timing):
+        ppd.ppd_timing_enable(s.ctx, kernel_timing)
+        ppd.ppd_set_weights(s.ctx, p.theta, None, None)   # reset state (eta recomputed) - untimed
+        for _ in range(warmup):
+            ppd.ppd_iterate(s.ctx, 1, stats=False)
+        torch.cuda.synchronize(dev)
+        ppd.ppd_timing_collect(s.ctx)
+        ppd.ppd_timing_enable(s.ctx, kernel_timing)      # clears sums
+        total = 0.0
+        launches0 = ppd.ppd_launch_count(s.ctx)
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            ppd.ppd_iterate(s.ctx, 1, stats=False)
+            ev1.record(stream)
+            ev1.synchronize()
+            total += ev0.elapsed_time(ev1)
+            if kernel_timing:
+                ppd.ppd_timing_collect(s.ctx)
+        launches = ppd.ppd_launch_count(s.ctx) - launches0
+        kt = ppd.ppd_timing_read(s.ctx) if kernel_timing else {}
+        return total / 1e3, launches, kt
+
+    def snr_run(s, iters):
+        ppd.ppd_timing_enable(s.ctx, False)
+        ppd.ppd_set_weights(s.ctx, p.theta, None, None)
+        snr = []
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(iters // 10):
+            st = ppd.ppd_iterate(s.ctx, 10, p.n_blocks)
+            snr.append(st["snr_db"])
+        dt = time.perf_counter() - t0
+        return snr, dt
+
+    if args.quick:
+        ppd.ppd_timing_enable(s32.ctx, False)
+        for _ in range(args.warmup):
+            ppd.ppd_iterate(s32.ctx, 1, stats=False)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ppd.ppd_iterate(s32.ctx, 1, stats=False)
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"quick": True, "ms_per_step": 1e3 * (time.perf_counter() - t0) / args.steps}))
+        s32.close()
+        return
+    if dist is not None:
+        dist.barrier()
+    with Clocks(local) as clk:
+        # main timed region: FP32-batched, per-kernel events on the library stream
+        t32, launches, kt = timed_steps(s32, args.steps, max(args.warmup, 3), True)
+        # FP64 plain, same protocol
+        t64, _, _ = timed_steps(s64, max(3, args.steps // 4), 3, False)
+        snr32, wall32 = snr_run(s32, SNR_ITERS)
+        snr64, wall64 = snr_run(s64, SNR_ITERS)
+        # end to end through the host API: upload, set-up, 500 iterations with per-10 stats, image back
+        e2e_t = []
+        for _ in range(2):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            ppd.ppd_set_visibilities(s32.ctx, p.omega, p.y, p.block)
+            ppd.ppd_set_weights(s32.ctx, p.theta, None, None)
+            for _ in range(SNR_ITERS // 10):
+                ppd.ppd_iterate(s32.ctx, 10, p.n_blocks)
+            img = ppd.ppd_get_image(s32.ctx, p.L, p.L)
+            e2e_t.append(time.perf_counter() - t0)
+    clocks = clk.summary()
+
+    ips32 = args.steps / t32
+    steps64 = max(3, args.steps // 4)
+    ips64 = steps64 / t64
+    if dist is not None:
+        t = torch.tensor([t32 / args.steps], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        per_step = float(t.item())
+        dist.destroy_process_group()
+    else:
+        per_step = t32 / args.steps
+    if rank != 0:
+        return
+    value = world / per_step
+    target = snr64[-1]
+    it_to_target = None
+    for i, v in enumerate(snr32):
+        if v >= target - 0.05:
+            it_to_target = 10 * (i + 1)
+            break
+    # roofline of the dominant kernel
+    peak, peak_kind = read_peaks()
+    dom = max(kt.items(), key=lambda kv: kv[1][0]) if kt else None
+    roof = None
+    if dom:
+        name, (ms, n) = dom
+        avg_s = ms / n / 1e3
+        ab = algorithmic_bytes(name, p.L, p.M, p.n_blocks)
+        ach = ab / avg_s / 1e9 if ab > 0 else None
+        roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": (ach / peak if ach else None), "traffic": None, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": ab, "avg_launch_us": avg_s * 1e6,
+                "share_of_kernel_time": ms / sum(v[0] for v in kt.values())}
+    kern = {k: {"avg_us": 1e3 * ms / n, "launches": n, "share": ms / sum(v[0] for v in kt.values())}
+            for k, (ms, n) in sorted(kt.items(), key=lambda kv: -kv[1][0])}
+    in_bytes = p.M * (16 + 16 + 4 + 8)
+    out_bytes = p.L * p.L * 8
+    stats_bytes = (SNR_ITERS // 10) * (3 * 8 + p.n_blocks * 8 + 4)
+    e2e_v = SNR_ITERS / min(e2e_t)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "image": f"{p.L}x{p.L}", "visibilities": p.M,
+                   "blocks": p.n_blocks, "uv_density": "gaussian sigma=0.1pi", "isnr_db": 30,
+                   "l2": "flushed (256 MiB write) between timed steps", "graph": "one CUDA graph per iteration",
+                   "replicas": world},
+        "fp64_plain": {"iters_per_s": ips64, "snr_db_at_500": target, "seconds_500": wall64},
+        "fp32_batched": {"iters_per_s": ips32, "snr_db_at_500": snr32[-1], "seconds_500": wall32,
+                         "iters_to_target_snr": it_to_target,
+                         "seconds_to_target_snr": (wall32 * it_to_target / SNR_ITERS) if it_to_target else None},
+        "speedup_iters_per_s": ips32 / ips64,
+        "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": in_bytes / SNR_ITERS,
+                "d2h_bytes_per_step": (out_bytes + stats_bytes) / SNR_ITERS,
+                "what": "ppd_set_visibilities + ppd_set_weights (eta by power iteration) + 500 iterations "
+                        "with stats every 10 + ppd_get_image, from host buffers"},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "kernels": kern,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        times = run_oracle(args.workload, seed, args.oracle_steps, 0)
+        model, ncpu = cpu_info()
+        line["cpu_baseline"] = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{len(times)} oracle PPD iterations of the same workload "
+                                          f"(FP64 NumPy, 1 thread) on {model} ({ncpu} cores)"}
+    print(json.dumps(line), flush=True)
+    s32.close()
+    s64.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -17,7 +17,8 @@
  * - Host buffers passed in are read during the call and never retained; the
  *   caller keeps ownership.  Host buffers passed out are written in full.
  * - Pointers named *_dev are caller-owned DEVICE memory, used on the given
- *   CUDA stream (cudaStream_t passed as void*, NULL = the context's stream);
+ *   CUDA stream (cudaStream_t passed as void*; NULL = the context's own
+ *   stream, so pass cudaStreamLegacy to mean the legacy default stream);
  *   the call only enqueues work and does not synchronise.
  * - The image is row-major n0 x n1 (n0 rows).  Complex arrays are
  *   interleaved (re, im).  Device arrays use the context's precision:

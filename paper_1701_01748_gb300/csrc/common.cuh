@@ -51,7 +51,7 @@ constexpr int ERR_NONFINITE = 2;
 constexpr int ERR_BOUNDS = 4;
 
 // bounded spin for mbarrier waits (iterations of try_wait)
-constexpr long long SPIN_LIMIT = 1ll << 24;
+constexpr long long SPIN_LIMIT = 1ll << 21;
 
 // ---------------------------------------------------------------- status
 struct Error {

@@ -106,6 +106,17 @@ def _check(status: int, where: str):
         raise PPDError(status, where)
 
 
+# cudaStreamLegacy: the handle CUDA uses for the legacy default stream
+_STREAM_LEGACY = 1
+
+
+def _stream(s):
+    """None -> NULL (the context's own stream); 0 (PyTorch's default stream) -> cudaStreamLegacy."""
+    if s is None:
+        return None
+    return _STREAM_LEGACY if int(s) == 0 else int(s)
+
+
 def _dptr(a: np.ndarray):
     return a.ctypes.data_as(ct.POINTER(ct.c_double)) if a is not None else None
 
@@ -191,20 +202,20 @@ def ppd_get_bins(ctx: int, M: int):
     return perm, b0, b1, cnt
 
 
-def ppd_op_forward(ctx: int, x_dev: int, y_dev: int, stream: int = 0) -> None:
-    _check(_lib().ppd_op_forward(ctx, x_dev, y_dev, stream or None), "ppd_op_forward")
+def ppd_op_forward(ctx: int, x_dev: int, y_dev: int, stream=None) -> None:
+    _check(_lib().ppd_op_forward(ctx, x_dev, y_dev, _stream(stream)), "ppd_op_forward")
 
 
-def ppd_op_adjoint(ctx: int, y_dev: int, x_dev: int, stream: int = 0) -> None:
-    _check(_lib().ppd_op_adjoint(ctx, y_dev, x_dev, stream or None), "ppd_op_adjoint")
+def ppd_op_adjoint(ctx: int, y_dev: int, x_dev: int, stream=None) -> None:
+    _check(_lib().ppd_op_adjoint(ctx, y_dev, x_dev, _stream(stream)), "ppd_op_adjoint")
 
 
-def ppd_psi_analysis(ctx: int, x_dev: int, c_dev: int, stream: int = 0) -> None:
-    _check(_lib().ppd_psi_analysis(ctx, x_dev, c_dev, stream or None), "ppd_psi_analysis")
+def ppd_psi_analysis(ctx: int, x_dev: int, c_dev: int, stream=None) -> None:
+    _check(_lib().ppd_psi_analysis(ctx, x_dev, c_dev, _stream(stream)), "ppd_psi_analysis")
 
 
-def ppd_psi_synthesis(ctx: int, c_dev: int, x_dev: int, stream: int = 0) -> None:
-    _check(_lib().ppd_psi_synthesis(ctx, c_dev, x_dev, stream or None), "ppd_psi_synthesis")
+def ppd_psi_synthesis(ctx: int, c_dev: int, x_dev: int, stream=None) -> None:
+    _check(_lib().ppd_psi_synthesis(ctx, c_dev, x_dev, _stream(stream)), "ppd_psi_synthesis")
 
 
 def ppd_timing_enable(ctx: int, enable: bool) -> None:
@@ -246,6 +257,8 @@ class Solver:
     def __init__(self, L: int, n_blocks: int = 1, precision: int = PPD_FP32_FP64NORMS, **cfg):
         self.L = L
         self.n_blocks = n_blocks
+        if "stream" in cfg:
+            cfg["stream"] = _stream(cfg["stream"])
         self.cfg = ppd_config_default(n0=L, n1=L, n_blocks=n_blocks, precision=precision, **cfg)
         self.ctx = ppd_create(self.cfg)
         self.M = 0
