@@ -193,6 +193,24 @@ PPD_API int ppd_op_forward(ppd_ctx *ctx, const void *x_dev, void *y_dev, void *s
  * -> x_dev n0*n1 reals.  Same rules as ppd_op_forward. */
 PPD_API int ppd_op_adjoint(ppd_ctx *ctx, const void *y_dev, void *x_dev, void *stream);
 
+/* Phi^dagger without allocating: the same result as ppd_op_adjoint (same
+ * arguments, layouts and stream rules), for callers that cannot let the
+ * library allocate device memory during the call, such as applications with a
+ * fixed device-memory budget reserved at start-up or real-time loops that must
+ * not block on the allocator or meet an out-of-memory error mid-way.  The
+ * paper has no counterpart; this is a deployment variant of the operator.
+ * The gridding scratch (one (T+8)^2 complex tile per work item, see
+ * ppd_params.n_chunks) comes from one fixed device array of
+ * PPD_NOALLOC_SCRATCH_BYTES that the library holds on every GPU it is loaded
+ * on until the process exits.  The first call on a device looks up that
+ * array's device address, so make the first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race and give
+ * wrong results.  No cudaMalloc, cudaFree or other allocating routine is
+ * called.  Errors: NOT_READY, INVALID_ARG, UNSUPPORTED (scratch needed above
+ * the fixed size), CUDA. */
+#define PPD_NOALLOC_SCRATCH_BYTES (32u << 20)
+PPD_API int ppd_op_adjoint_noalloc(ppd_ctx *ctx, const void *y_dev, void *x_dev, void *stream);
+
 /* Psi^dagger x (Section 2.2, Section 5.1: Dirac + db1..db8, 4 levels,
  * periodic, Mallat layout, each basis scaled by 1/3): x_dev n0*n1 reals ->
  * c_dev 9*n0*n1 reals (basis-major).  Enqueued on stream. */

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libppd.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "fft.cu", "vis.cu", "sara.cu", "image.cu"]
+SOURCES = ["api.cu", "fft.cu", "vis.cu", "sara.cu", "image.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

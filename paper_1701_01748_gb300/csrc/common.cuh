@@ -186,6 +186,10 @@ template <typename R>
 int grid_vis(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm_in, cplx_t<R> *grid,
              cudaStream_t s);
 
+template <typename R>
+int grid_vis_into(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_t<R> *grid, void *gpart,
+                  cudaStream_t s);
+
 // SARA (sara.cu)
 int make_filters(ppd_ctx *c);
 template <typename R> int psi_analysis(ppd_ctx *c, const R *x, R *coef, cudaStream_t s);

@@ -605,6 +605,21 @@ int block_norms(ppd_ctx *c, int with_resid, cudaStream_t s) {
     return launch_end(c, site, s);
 }
 
+// Same launches as grid_vis, with the per-chunk partial tiles written to a
+// caller-supplied device buffer instead of the context's.
+template <typename R>
+int grid_vis_into(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_t<R> *grid, void *gpart,
+                  cudaStream_t s) {
+    void *own = c->gpart;
+    c->gpart = gpart;
+    const int st = grid_vis<R>(c, mode, in, perm, grid, s);
+    c->gpart = own;
+    return st;
+}
+
+template int grid_vis_into<float>(ppd_ctx *, int, const float2 *, const int64_t *, float2 *, void *, cudaStream_t);
+template int grid_vis_into<double>(ppd_ctx *, int, const double2 *, const int64_t *, double2 *, void *,
+                                   cudaStream_t);
 template int degrid<float>(ppd_ctx *, int, const float2 *, float2 *, const int64_t *, cudaStream_t);
 template int degrid<double>(ppd_ctx *, int, const double2 *, double2 *, const int64_t *, cudaStream_t);
 template int grid_vis<float>(ppd_ctx *, int, const float2 *, const int64_t *, float2 *, cudaStream_t);

@@ -83,6 +83,7 @@ def _lib():
                                  ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32)]),
             "ppd_op_forward": (I, [P, P, P, P]),
             "ppd_op_adjoint": (I, [P, P, P, P]),
+            "ppd_op_adjoint_noalloc": (I, [P, P, P, P]),
             "ppd_psi_analysis": (I, [P, P, P, P]),
             "ppd_psi_synthesis": (I, [P, P, P, P]),
             "ppd_timing_enable": (I, [P, I32]),
@@ -208,6 +209,10 @@ def ppd_op_forward(ctx: int, x_dev: int, y_dev: int, stream=None) -> None:
 
 def ppd_op_adjoint(ctx: int, y_dev: int, x_dev: int, stream=None) -> None:
     _check(_lib().ppd_op_adjoint(ctx, y_dev, x_dev, _stream(stream)), "ppd_op_adjoint")
+
+
+def ppd_op_adjoint_noalloc(ctx: int, y_dev: int, x_dev: int, stream=None) -> None:
+    _check(_lib().ppd_op_adjoint_noalloc(ctx, y_dev, x_dev, _stream(stream)), "ppd_op_adjoint_noalloc")
 
 
 def ppd_psi_analysis(ctx: int, x_dev: int, c_dev: int, stream=None) -> None:
