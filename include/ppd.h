@@ -86,7 +86,7 @@ typedef struct {
     int32_t  precond;           /* 1: PPD with U = inverse sampling density; 0: U = I (PD) */
     int32_t  inner_init;        /* PPD_INNER_WARM or PPD_INNER_CURRENT */
     int32_t  use_graph;         /* 1: replay each iteration from a captured CUDA graph */
-    int32_t  tile;              /* gridding tile side T (16 or 32); 0 => 32 (16 when K < 80) */
+    int32_t  tile;              /* gridding tile side T (16 or 32); 0 => 16 */
     int32_t  chunk;             /* max visibilities per gridding work item; 0 => 1024 */
     int32_t  power_iters;       /* power-iteration cap for eta; 0 => 1000 */
     double   power_tol;         /* power-iteration relative stop; 0 => 1e-10 */

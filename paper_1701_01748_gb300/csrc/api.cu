@@ -104,7 +104,7 @@ void free_vis(ppd_ctx *c) {
     for (void *p : {c->rec, c->theta_v, c->y, c->v, c->z, c->w, c->p, c->y_raw, (void *)c->perm,
                     (void *)c->count_cell, (void *)c->ch.start, (void *)c->ch.count, (void *)c->ch.tile,
                     (void *)c->ch.block, (void *)c->ch.tile_first, (void *)c->ch.tile_n, (void *)c->ch.blk_ptr,
-                    (void *)c->ch.blk_list, (void *)c->partials, (void *)c->scale, (void *)c->resid2,
+                    (void *)c->ch.blk_list, (void *)c->ch.active, (void *)c->partials, (void *)c->scale, (void *)c->resid2,
                     (void *)c->eps_d, (void *)c->mu_d, c->gpart})
         dfree(p);
     c->rec = c->theta_v = c->y = c->v = c->z = c->w = c->p = c->y_raw = c->gpart = nullptr;
@@ -184,31 +184,47 @@ int check_err_word(ppd_ctx *c) {
     return PPD_OK;
 }
 
-// One PPD iteration (Algorithm 3, lambda = 1, all blocks and bases).
+// One PPD iteration (Algorithm 3, lambda = 1, all blocks and bases).  The
+// prior branch (SARA analysis, clip, synthesis down to level 1) needs only
+// xt and u, so in the FP32 path it runs on a second stream beside the data
+// branch (FFT, degridding with the data step, gridding, inverse FFT); both
+// join before the fused level-0 synthesis + primal step.  The per-block P_B
+// scales are computed in the prologue of the kernel that uses them, from the
+// previous launch's chunk partials (two banks).
 template <typename R> int iteration_body(ppd_ctx *c, cudaStream_t s, bool first) {
     using C = cplx_t<R>;
     C *ga = static_cast<C *>(c->grid_a), *gv = static_cast<C *>(c->grid_v);
+    const bool fork = c->is_f32 && c->stream2;
+    cudaStream_t s2 = fork ? c->stream2 : s;
+    if (fork) {
+        PPD_CUDA(cudaEventRecord(c->ev_fork, s));
+        PPD_CUDA(cudaStreamWaitEvent(s2, c->ev_fork, 0));
+    }
+    const R *ll0 = nullptr;
+    PPD_CHECK(sara_prior_branch<R>(c, &ll0, s2));
+    if (fork) PPD_CUDA(cudaEventRecord(c->ev_join, s2));
+
+    double *bank[2] = {c->partials, c->partials + NPART * c->ch.n};
+    int cur = 0;
     PPD_CHECK(fft_forward<R>(c, static_cast<const R *>(c->xt), ga, s));
     const bool current = c->cfg.inner_init == PPD_INNER_CURRENT;
-    if (current || first) {
-        PPD_CHECK(degrid<R>(c, DG_FIRST, ga, nullptr, nullptr, s));
-        PPD_CHECK(block_norms(c, 1, s));
-        if (!current) {   // warm start at t = 1: zbar^(0) = P_B(z), then the first step
-            PPD_CHECK(subiter<R>(c, s));
-            PPD_CHECK(block_norms(c, 0, s));
-        }
-    } else {
-        PPD_CHECK(degrid<R>(c, DG_DUAL, ga, nullptr, nullptr, s));
-        PPD_CHECK(block_norms(c, 1, s));
-    }
-    for (int k = 1; k < c->cfg.n_itr; ++k) {
+    c->part_out = bank[0];
+    c->part_in = bank[1];
+    PPD_CHECK(degrid<R>(c, (current || first) ? DG_FIRST : DG_DUAL, ga, nullptr, nullptr, s));
+    // warm start at t = 1: zbar^(0) = P_B(z), then the first step; plus n_itr - 1 steps
+    const int steps = c->cfg.n_itr - 1 + ((first && !current) ? 1 : 0);
+    for (int k = 0; k < steps; ++k) {
+        c->part_in = bank[cur];
+        c->part_out = bank[cur ^ 1];
         PPD_CHECK(subiter<R>(c, s));
-        PPD_CHECK(block_norms(c, 0, s));
+        cur ^= 1;
     }
+    c->part_in = bank[cur];
+    c->part_out = bank[0];
     PPD_CHECK(grid_vis<R>(c, GR_DUAL, nullptr, nullptr, gv, s));
     PPD_CHECK(fft_inverse<R>(c, gv, static_cast<R *>(c->g), s));
-    PPD_CHECK(sara_dual_step<R>(c, s));
-    PPD_CHECK(primal_step<R>(c, s));
+    if (fork) PPD_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
+    PPD_CHECK(sara_primal<R>(c, ll0, s));
     return PPD_OK;
 }
 
@@ -392,7 +408,7 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
     c->N = (int64_t)k.n0 * k.n1;
     c->d = k.n_blocks;
     c->levels = k.wavelet_levels;
-    c->T = k.tile ? k.tile : (c->K0 >= 80 ? 32 : 16);
+    c->T = k.tile ? k.tile : 16;
     if (c->K0 % c->T) c->T = 16;
     c->C = k.chunk ? k.chunk : 1024;
     c->beta = k.kb_beta > 0 ? k.kb_beta : 2.34 * KB_J;
@@ -414,6 +430,10 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
         }
         c->own_stream = true;
     }
+    if (cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(PPD_ERR_CUDA, "ppd_create: stream/event creation"));
     const size_t rb = c->rsz, cb = 2 * c->rsz;
     const int64_t N = c->N, G = (int64_t)c->K0 * c->K1;
     int st = PPD_OK;
@@ -427,7 +447,8 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
         (st = dalloc_bytes(&c->kbpoly, (KB_DEG + 1) * KB_J * sizeof(float))) || (st = dalloc(&c->err, 1)) ||
         (st = dalloc(&c->stat_out, 3)))
         return bail(st);
-    c->n_prim_blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 4);
+    // the primal step runs inside the finest SARA synthesis, one CTA per tile
+    c->n_prim_blocks = sara_primal_blocks(c);
     if ((st = dalloc(&c->prim_part, 3 * (size_t)c->n_prim_blocks))) return bail(st);
     if ((st = make_twiddles(c)) || (st = make_deapodisation(c)) || (st = make_filters(c)) || (st = make_kb_poly(c)))
         return bail(st);
@@ -453,6 +474,12 @@ void ppd_destroy(ppd_ctx *c) {
     for (void *p : {c->x, c->xt, c->g, c->ut, c->xtrue, c->u, c->wtmp, c->wtmp2, c->grid_a, c->grid_v, c->fft_tmp,
                     c->tw0, c->deap0, c->deap1, c->kbpoly, (void *)c->prim_part, (void *)c->stat_out, (void *)c->err})
         dfree(p);
+    if (c->stream2) {
+        cudaStreamSynchronize(c->stream2);
+        cudaStreamDestroy(c->stream2);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -544,6 +571,21 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
         i = j;
     }
     const int64_t nch = (int64_t)cs.size();
+    // tiles the gridding can reach: a tile with chunks and the tiles below,
+    // right and below-right of it (the extended footprint's halo)
+    std::vector<int32_t> active;
+    {
+        const int nt0 = c->K0 / c->T, nt1 = c->K1 / c->T;
+        std::vector<char> mark(ntiles, 0);
+        for (int t = 0; t < ntiles; ++t)
+            if (tn[t]) {
+                const int a0 = t / nt1, a1 = t % nt1;
+                for (int d0 = 0; d0 < 2; ++d0)
+                    for (int d1 = 0; d1 < 2; ++d1) mark[((a0 + d0) % nt0) * nt1 + (a1 + d1) % nt1] = 1;
+            }
+        for (int t = 0; t < ntiles; ++t)
+            if (mark[t]) active.push_back(t);
+    }
     std::vector<int32_t> bptr(c->d + 1, 0), blist(nch);
     for (int64_t k = 0; k < nch; ++k) bptr[cbk[k] + 1]++;
     for (int j = 0; j < c->d; ++j) bptr[j + 1] += bptr[j];
@@ -552,12 +594,14 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
         for (int64_t k = 0; k < nch; ++k) blist[fill[cbk[k]]++] = (int32_t)k;
     }
     c->ch.n = nch;
+    c->ch.n_active = (int64_t)active.size();
     const size_t cbsz = 2 * c->rsz;
     const int E = c->T + HALO;
     if ((st = dalloc(&c->ch.start, nch)) || (st = dalloc(&c->ch.count, nch)) || (st = dalloc(&c->ch.tile, nch)) ||
         (st = dalloc(&c->ch.block, nch)) || (st = dalloc(&c->ch.tile_first, ntiles)) ||
         (st = dalloc(&c->ch.tile_n, ntiles)) || (st = dalloc(&c->ch.blk_ptr, c->d + 1)) ||
-        (st = dalloc(&c->ch.blk_list, nch)) || (st = dalloc(&c->partials, NPART * (size_t)nch)) ||
+        (st = dalloc(&c->ch.blk_list, nch)) || (st = dalloc(&c->ch.active, active.size())) ||
+        (st = dalloc(&c->partials, 2 * NPART * (size_t)nch)) ||
         (st = dalloc(&c->scale, c->d)) || (st = dalloc(&c->resid2, c->d)) || (st = dalloc(&c->eps_d, c->d)) ||
         (st = dalloc(&c->mu_d, c->d)) || (st = dalloc_bytes(&c->gpart, (size_t)nch * E * E * cbsz)) ||
         (st = dalloc(&c->perm, M)) || (st = dalloc_bytes(&c->rec, M * (c->is_f32 ? 16 : 32))) ||
@@ -591,10 +635,16 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
         (e = cudaMemcpy(c->ch.tile_n, tn.data(), ntiles * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->ch.blk_ptr, bptr.data(), (c->d + 1) * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->ch.blk_list, blist.data(), nch * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->ch.active, active.data(), active.size() * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->perm, c->perm_h.data(), M * 8, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->y_raw, yraw_sorted.data(), 2 * M * 8, cudaMemcpyHostToDevice))) {
         free_vis(c);
         return fail(PPD_ERR_CUDA, std::string("ppd_set_visibilities: upload: ") + cudaGetErrorString(e));
+    }
+    // the combine pass only writes tiles this coverage reaches: clear the rest
+    if ((e = cudaMemset(c->grid_v, 0, (size_t)c->K0 * c->K1 * 2 * c->rsz))) {
+        free_vis(c);
+        return fail(PPD_ERR_CUDA, std::string("ppd_set_visibilities: clear: ") + cudaGetErrorString(e));
     }
     c->block_count_h.assign(c->d, 0);
     for (int64_t i = 0; i < M; ++i) c->block_count_h[block_id[i]]++;
@@ -718,6 +768,8 @@ int ppd_iterate(ppd_ctx *c, int32_t n_iters, ppd_stats *stats) {
         return st;
     }
     if (stats) {
+        c->part_out = c->partials;   // bank 0 holds the last data step's residual partials
+        PPD_CHECK(block_norms(c, 1, c->stream));
         PPD_CHECK(reduce_primal_stats(c, c->stream));
         double h[3];
         std::vector<double> r2(c->d);

@@ -86,6 +86,8 @@ struct Chunks {
     int32_t *start = nullptr, *count = nullptr, *tile = nullptr, *block = nullptr;   // device
     int32_t *tile_first = nullptr, *tile_n = nullptr;                                // device, n_tiles
     int32_t *blk_ptr = nullptr, *blk_list = nullptr;                                 // device CSR
+    int32_t *active = nullptr;   // tiles the combine pass writes (device)
+    int64_t n_active = 0;
 };
 
 }  // namespace ppd
@@ -126,6 +128,9 @@ struct ppd_ctx {
     ppd::Chunks ch;
     double *partials = nullptr, *scale = nullptr, *resid2 = nullptr, *eps_d = nullptr,
            *mu_d = nullptr;
+    double *part_in = nullptr, *part_out = nullptr;   // chunk-partial banks for the next launch
+    cudaStream_t stream2 = nullptr;                   // prior (SARA) branch of the iteration
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     void *gpart = nullptr;           // n_chunks x (T+HALO)^2 complex
     int *err = nullptr;              // device error word
     CUtensorMap tmap_a;              // TMA descriptor of grid_a
@@ -194,10 +199,11 @@ int grid_vis_into(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm
 int make_filters(ppd_ctx *c);
 template <typename R> int psi_analysis(ppd_ctx *c, const R *x, R *coef, cudaStream_t s);
 template <typename R> int psi_synthesis(ppd_ctx *c, const R *coef, R *x, cudaStream_t s);
-template <typename R> int sara_dual_step(ppd_ctx *c, cudaStream_t s);
+template <typename R> int sara_prior_branch(ppd_ctx *c, const R **ll0, cudaStream_t s);
+template <typename R> int sara_primal(ppd_ctx *c, const R *ll0, cudaStream_t s);
+int sara_primal_blocks(ppd_ctx *c);
 
 // image side (image.cu)
-template <typename R> int primal_step(ppd_ctx *c, cudaStream_t s);
 int reduce_primal_stats(ppd_ctx *c, cudaStream_t s);
 template <typename R> int scale_copy(ppd_ctx *c, const R *in, R *out, int64_t n, double a, cudaStream_t s);
 template <typename R> int sumsq(ppd_ctx *c, const R *in, int64_t n, double *out_dev, cudaStream_t s);

@@ -33,7 +33,7 @@ __host__ __device__ constexpr int ilog2_(int k) { return k <= 1 ? 0 : 1 + ilog2_
 // held in shared memory.  INTERLEAVED: element (s, i) at i*NSEQ + s;
 // otherwise at s*K + i.  tw[m] = exp(-2 pi i m / K).
 template <typename R, int K, int NSEQ, int NT, bool INTERLEAVED>
-__device__ void fft_smem(cplx_t<R> *buf, const cplx_t<R> *__restrict__ tw) {
+__device__ void fft_smem(cplx_t<R> *buf, const cplx_t<R> *tw) {
     using C = cplx_t<R>;
     const int tid = threadIdx.x;
     constexpr int LOG2K = ilog2_(K);
@@ -80,9 +80,9 @@ __device__ void fft_smem(cplx_t<R> *buf, const cplx_t<R> *__restrict__ tw) {
             C a2 = buf[idx(s, j + K / 2)];
             C a3 = buf[idx(s, j + 3 * K / 4)];
             if (Ns > 1) {
-                a1 = cmul(a1, __ldg(&tw[(1 * k * twstep) & (K - 1)]));
-                a2 = cmul(a2, __ldg(&tw[(2 * k * twstep) & (K - 1)]));
-                a3 = cmul(a3, __ldg(&tw[(3 * k * twstep) & (K - 1)]));
+                a1 = cmul(a1, tw[(1 * k * twstep) & (K - 1)]);
+                a2 = cmul(a2, tw[(2 * k * twstep) & (K - 1)]);
+                a3 = cmul(a3, tw[(3 * k * twstep) & (K - 1)]);
             }
             C t0 = cadd(a0, a2), t1 = csub(a0, a2);
             C t2 = cadd(a1, a3), t3 = csub(a1, a3);
@@ -111,13 +111,12 @@ __device__ void fft_smem(cplx_t<R> *buf, const cplx_t<R> *__restrict__ tw) {
 
 constexpr int NT = 256;
 
-// rows per CTA in a row pass (32 KB of shared memory)
-template <typename R> __host__ __device__ constexpr int rows_per_cta(int K) {
-    return (sizeof(R) == 4 ? 4096 : 2048) / K > 0 ? (sizeof(R) == 4 ? 4096 : 2048) / K : 1;
-}
-// columns per CTA in a column pass (64 KB of shared memory), at most K
+// rows per CTA in a row pass: enough butterflies for 256 threads
+template <typename R> __host__ __device__ constexpr int rows_per_cta(int K) { return 1024 / K > 0 ? 1024 / K : 1; }
+// columns per CTA in a column pass (32 KB of shared memory), at most K
 template <typename R> __host__ __device__ constexpr int cols_per_cta(int K) {
-    return (sizeof(R) == 4 ? 8192 : 4096) / K < K ? (sizeof(R) == 4 ? 8192 : 4096) / K : K;
+    return (sizeof(R) == 4 ? 4096 : 2048) / K < 1 ? 1
+           : (sizeof(R) == 4 ? 4096 : 2048) / K < K ? (sizeof(R) == 4 ? 4096 : 2048) / K : K;
 }
 
 // forward row pass: tmp[n0][c] = FFT_axis1(Z x)[n0][(c + K/2) mod K]
@@ -129,6 +128,8 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(const R *__restrict__ x, cplx_t
     constexpr int B = rows_per_cta<R>(K);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
+    C *tws = buf + B * K;   // twiddles staged in shared memory
+    for (int e = threadIdx.x; e < K; e += NT) tws[e] = tw[e];
     const int row0 = blockIdx.x * B;
     for (int e = threadIdx.x; e < B * K; e += NT) buf[e] = C{0, 0};
     __syncthreads();
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(const R *__restrict__ x, cplx_t
         }
     }
     __syncthreads();
-    fft_smem<R, K, B, NT, false>(buf, tw);
+    fft_smem<R, K, B, NT, false>(buf, tws);
     for (int e = threadIdx.x; e < B * K; e += NT) {
         int s = e / K, c = e % K, n0 = row0 + s;
         if (n0 < L) tmp[(int64_t)n0 * K + c] = buf[s * K + ((c + K / 2) & (K - 1))];
@@ -155,6 +156,8 @@ __global__ void __launch_bounds__(NT) k_cols_fwd(const cplx_t<R> *__restrict__ t
     constexpr int W = cols_per_cta<R>(K);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
+    C *tws = buf + W * K;   // twiddles staged in shared memory
+    for (int e = threadIdx.x; e < K; e += NT) tws[e] = tw[e];
     const int c0 = blockIdx.x * W;
     for (int e = threadIdx.x; e < W * K; e += NT) buf[e] = C{0, 0};
     __syncthreads();
@@ -164,7 +167,7 @@ __global__ void __launch_bounds__(NT) k_cols_fwd(const cplx_t<R> *__restrict__ t
         buf[pos * W + s] = tmp[(int64_t)n0 * K + c0 + s];
     }
     __syncthreads();
-    fft_smem<R, K, W, NT, true>(buf, tw);
+    fft_smem<R, K, W, NT, true>(buf, tws);
     for (int e = threadIdx.x; e < W * K; e += NT) {
         int s = e % W, r = e / W;
         grid[(int64_t)r * K + c0 + s] = buf[((r + K / 2) & (K - 1)) * W + s];
@@ -179,13 +182,15 @@ __global__ void __launch_bounds__(NT) k_cols_inv(const cplx_t<R> *__restrict__ g
     constexpr int W = cols_per_cta<R>(K);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
+    C *tws = buf + W * K;   // twiddles staged in shared memory
+    for (int e = threadIdx.x; e < K; e += NT) tws[e] = tw[e];
     const int c0 = blockIdx.x * W;
     for (int e = threadIdx.x; e < W * K; e += NT) {
         int s = e % W, r = e / W;   // r: stored (centred) row; natural frequency (r + K/2) mod K
         buf[((r + K / 2) & (K - 1)) * W + s] = cconj(grid[(int64_t)r * K + c0 + s]);
     }
     __syncthreads();
-    fft_smem<R, K, W, NT, true>(buf, tw);
+    fft_smem<R, K, W, NT, true>(buf, tws);
     for (int e = threadIdx.x; e < W * L; e += NT) {
         int s = e % W, n0 = e / W;
         int pos = (n0 - L / 2 + K) & (K - 1);
@@ -202,6 +207,8 @@ __global__ void __launch_bounds__(NT) k_rows_inv(const cplx_t<R> *__restrict__ t
     constexpr int B = rows_per_cta<R>(K);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
+    C *tws = buf + B * K;   // twiddles staged in shared memory
+    for (int e = threadIdx.x; e < K; e += NT) tws[e] = tw[e];
     const int row0 = blockIdx.x * B;
     for (int e = threadIdx.x; e < B * K; e += NT) {
         int s = e / K, c = e % K, n0 = row0 + s;
@@ -210,7 +217,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(const cplx_t<R> *__restrict__ t
         buf[s * K + ((c + K / 2) & (K - 1))] = val;
     }
     __syncthreads();
-    fft_smem<R, K, B, NT, false>(buf, tw);
+    fft_smem<R, K, B, NT, false>(buf, tws);
     for (int e = threadIdx.x; e < B * L; e += NT) {
         int s = e / L, n1 = e % L, n0 = row0 + s;
         if (n0 < L) {
@@ -223,7 +230,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(const cplx_t<R> *__restrict__ t
 template <typename R, int K> int fft_fwd_k(ppd_ctx *c, const R *x, cplx_t<R> *grid, cudaStream_t s) {
     constexpr int B = rows_per_cta<R>(K), W = cols_per_cta<R>(K);
     const int L = c->L0;
-    size_t shr = (size_t)B * K * sizeof(cplx_t<R>), shc = (size_t)W * K * sizeof(cplx_t<R>);
+    size_t shr = (size_t)(B + 1) * K * sizeof(cplx_t<R>), shc = (size_t)(W + 1) * K * sizeof(cplx_t<R>);
     static bool attr = false;
     if (!attr) {
         PPD_CUDA(cudaFuncSetAttribute(k_rows_fwd<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shr));
@@ -247,7 +254,7 @@ template <typename R, int K> int fft_fwd_k(ppd_ctx *c, const R *x, cplx_t<R> *gr
 template <typename R, int K> int fft_inv_k(ppd_ctx *c, const cplx_t<R> *grid, R *img, cudaStream_t s) {
     constexpr int B = rows_per_cta<R>(K), W = cols_per_cta<R>(K);
     const int L = c->L0;
-    size_t shr = (size_t)B * K * sizeof(cplx_t<R>), shc = (size_t)W * K * sizeof(cplx_t<R>);
+    size_t shr = (size_t)(B + 1) * K * sizeof(cplx_t<R>), shc = (size_t)(W + 1) * K * sizeof(cplx_t<R>);
     static bool attr = false;
     if (!attr) {
         PPD_CUDA(cudaFuncSetAttribute(k_rows_inv<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shr));

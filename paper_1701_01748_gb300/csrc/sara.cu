@@ -32,54 +32,74 @@ template <typename R> __device__ __forceinline__ R hfilt(int b, int F, int k) {
 }
 
 constexpr int NT = 256;
+constexpr int TSA = 16;                       // analysis: quadrant positions per tile side
+constexpr int TS = 8;                         // synthesis: quadrant positions per tile side
+constexpr int AEXT = 2 * TSA + MAX_TAPS - 2;  // analysis input tile side (46)
+constexpr int SEXT = TS + MAX_TAPS / 2 - 1;   // synthesis quadrant tile side (15)
 
-// analysis along rows of an n x n block: out[r][m] = [a | d]
-template <typename R>
-__global__ void k_ana_rows(const R *__restrict__ x, int x_pitch, int x_stride_basis, R *__restrict__ out, int n,
-                           int64_t out_stride_basis) {
-    const int b = blockIdx.z, F = 2 * (b + 1);
-    const R *in = x + (int64_t)b * x_stride_basis;
-    R *o = out + (int64_t)b * out_stride_basis;
-    const int h = n / 2;
-    for (int e = blockIdx.x * NT + threadIdx.x; e < n * n; e += gridDim.x * NT) {
-        const int r = e / n, m = e % n;
-        const int mm = m < h ? m : m - h;
-        const R *row = in + (int64_t)r * x_pitch;
-        R s = 0;
-        if (m < h) {
-            for (int k = 0; k < F; ++k) s += filt<R>(b, k) * row[(2 * mm + k) % n];
-        } else {
-            for (int k = 0; k < F; ++k) s += hfilt<R>(b, F, k) * row[(2 * mm + k) % n];
-        }
-        o[e] = s;
+// periodic index for power-of-two n (two's complement makes the mask exact
+// for negative i)
+__device__ __forceinline__ int wrap(int i, int n) { return i & (n - 1); }
+
+// low-pass h and high-pass g[k] = (-1)^k h[F-1-k] of basis b, staged in shared memory
+template <typename R> __device__ __forceinline__ void stage_filters(R *fh, R *fg, int b, int F) {
+    if (threadIdx.x < MAX_TAPS) {
+        const int k = threadIdx.x;
+        fh[k] = k < F ? filt<R>(b, k) : R(0);
+        fg[k] = k < F ? hfilt<R>(b, F, k) : R(0);
     }
 }
 
-// analysis along columns; LL quadrant to ll (compact, pitch n/2) unless last
-// level, every other coefficient (times 1/3) to coef[b+1] (pitch L):
-// mode 0 writes it, mode 1 applies u = clip(u + c, -kappa, kappa).
+// One analysis level for all 8 wavelet bases (grid.y = basis), one tile of
+// ts x ts positions of each of the 4 quadrants per CTA.  Rows (axis 1) are
+// filtered into shared memory, then columns (axis 0).
+//   in:   level input, basis b at in + b*in_bstride, row pitch in_pitch
+//   LL:   next level's input (compact, pitch h) unless last
+//   coef: coefficient images (basis b+1 at coef + (b+1)*N, pitch L), written
+//         (mode 0: c = W x / 3) or clip-updated (mode 1: u = clip(u + W x / 3, kappa))
 template <typename R>
-__global__ void k_ana_cols(const R *__restrict__ t, int64_t t_stride_basis, int n, R *__restrict__ ll,
-                           int64_t ll_stride_basis, int last, R *__restrict__ coef, int L, int64_t N, int mode,
-                           R kappa) {
-    const int b = blockIdx.z, F = 2 * (b + 1);
-    const R *in = t + (int64_t)b * t_stride_basis;
-    const int h = n / 2;
+__global__ void __launch_bounds__(NT) k_sara_ana(const R *__restrict__ in, int in_pitch, int64_t in_bstride, int n,
+                                                 int ts, R *__restrict__ ll, int64_t ll_bstride, int last,
+                                                 R *__restrict__ coef, int L, int64_t N, int mode, R kappa) {
+    __shared__ R tin[AEXT * AEXT];
+    __shared__ R rowf[AEXT * 2 * TSA];
+    __shared__ R fh[MAX_TAPS], fg[MAX_TAPS];
+    const int b = blockIdx.y, F = 2 * (b + 1);
+    const int h = n / 2, tpd = h / ts;
+    const int R0 = (blockIdx.x / tpd) * ts, C0 = (blockIdx.x % tpd) * ts;
+    const int ext = 2 * ts + F - 2;
+    const R *src = in + (int64_t)b * in_bstride;
+    stage_filters(fh, fg, b, F);
+    for (int e = threadIdx.x; e < ext * ext; e += NT) {
+        const int i = e / ext, j = e % ext;
+        tin[i * AEXT + j] = src[(int64_t)wrap(2 * R0 + i, n) * in_pitch + wrap(2 * C0 + j, n)];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ext * 2 * ts; e += NT) {
+        const int i = e / (2 * ts), q = e % (2 * ts);
+        const int cc = q % ts;
+        const bool hi = q >= ts;
+        const R *row = tin + i * AEXT + 2 * cc;
+        const R *f = hi ? fg : fh;
+        R acc = 0;
+        for (int k = 0; k < F; ++k) acc += f[k] * row[k];
+        rowf[i * 2 * TSA + q] = acc;
+    }
+    __syncthreads();
     R *cb = coef + (int64_t)(b + 1) * N;
-    for (int e = blockIdx.x * NT + threadIdx.x; e < n * n; e += gridDim.x * NT) {
-        const int r = e / n, c = e % n;
-        const int rr = r < h ? r : r - h;
-        R s = 0;
-        if (r < h) {
-            for (int k = 0; k < F; ++k) s += filt<R>(b, k) * in[(int64_t)((2 * rr + k) % n) * n + c];
+    for (int e = threadIdx.x; e < 4 * ts * ts; e += NT) {
+        const int rq = e / (2 * ts), q = e % (2 * ts);
+        const int rr = rq % ts, cc = q % ts;
+        const bool hi0 = rq >= ts, hi1 = q >= ts;
+        const R *f = hi0 ? fg : fh;
+        const R *col = rowf + 2 * rr * 2 * TSA + q;
+        R acc = 0;
+        for (int k = 0; k < F; ++k) acc += f[k] * col[k * 2 * TSA];
+        if (!hi0 && !hi1 && !last) {
+            ll[(int64_t)b * ll_bstride + (R0 + rr) * h + C0 + cc] = acc;
         } else {
-            for (int k = 0; k < F; ++k) s += hfilt<R>(b, F, k) * in[(int64_t)((2 * rr + k) % n) * n + c];
-        }
-        if (r < h && c < h && !last) {
-            ll[(int64_t)b * ll_stride_basis + r * h + c] = s;
-        } else {
-            const R cv = s * R(1.0 / 3.0);
-            R *dst = cb + (int64_t)r * L + c;
+            R *dst = cb + (int64_t)((hi0 ? h : 0) + R0 + rr) * L + (hi1 ? h : 0) + C0 + cc;
+            const R cv = acc * R(1.0 / 3.0);
             if (mode == 0) {
                 *dst = cv;
             } else {
@@ -90,71 +110,177 @@ __global__ void k_ana_cols(const R *__restrict__ t, int64_t t_stride_basis, int 
     }
 }
 
-// synthesis along columns: out[r][c] (compact pitch n) from the A rows
-// (top h rows: the LL' block for c < h, coefficients otherwise) and D rows.
+// Load the four quadrant tiles of basis b for the synthesis of the tile whose
+// quadrant positions start at (R0, C0): rows/cols R0 - F/2 + 1 ... R0 + ts - 1.
 template <typename R>
-__global__ void k_syn_cols(const R *__restrict__ coef, int L, int64_t N, const R *__restrict__ sll, int sll_from_coef,
-                           int64_t sll_stride_basis, int n, R *__restrict__ out, int64_t out_stride_basis) {
-    const int b = blockIdx.z, F = 2 * (b + 1);
-    const int h = n / 2;
-    const R *cb = coef + (int64_t)(b + 1) * N;
-    const R *sl = sll + (int64_t)b * sll_stride_basis;
-    R *o = out + (int64_t)b * out_stride_basis;
-    for (int e = blockIdx.x * NT + threadIdx.x; e < n * n; e += gridDim.x * NT) {
-        const int r = e / n, c = e % n;
-        R s = 0;
-        for (int k = (r & 1); k < F; k += 2) {
-            const int i = ((r - k) % n + n) % n / 2;
-            R av;
-            if (c < h) av = sll_from_coef ? cb[(int64_t)i * L + c] : sl[i * h + c];
-            else av = cb[(int64_t)i * L + c];
-            const R dv = cb[(int64_t)(i + h) * L + c];
-            s += filt<R>(b, k) * av + hfilt<R>(b, F, k) * dv;
-        }
-        o[e] = s;
+__device__ __forceinline__ void syn_load(R *qs, const R *cb, const R *sl, int from_coef, int L, int h, int R0,
+                                         int C0, int ext, int F) {
+    for (int e = threadIdx.x; e < 4 * ext * ext; e += NT) {
+        const int qd = e / (ext * ext), r = e % (ext * ext);
+        const int i = r / ext, j = r % ext;
+        const int gi = wrap(R0 - F / 2 + 1 + i, h), gj = wrap(C0 - F / 2 + 1 + j, h);
+        R v;
+        if (qd == 0) v = from_coef ? cb[(int64_t)gi * L + gj] : sl[gi * h + gj];
+        else if (qd == 1) v = cb[(int64_t)gi * L + h + gj];
+        else if (qd == 2) v = cb[(int64_t)(h + gi) * L + gj];
+        else v = cb[(int64_t)(h + gi) * L + h + gj];
+        qs[qd * SEXT * SEXT + i * SEXT + j] = v;
     }
 }
 
-// synthesis along rows: out[r][m] from [a | d] of t (compact pitch n).
+// Inverse along axis 0: tl/th[mm][j] (mm < 2 ts, j < ext) from the quadrants.
 template <typename R>
-__global__ void k_syn_rows(const R *__restrict__ t, int64_t t_stride_basis, int n, R *__restrict__ out,
-                           int64_t out_stride_basis) {
-    const int b = blockIdx.z, F = 2 * (b + 1);
-    const int h = n / 2;
-    const R *in = t + (int64_t)b * t_stride_basis;
-    R *o = out + (int64_t)b * out_stride_basis;
-    for (int e = blockIdx.x * NT + threadIdx.x; e < n * n; e += gridDim.x * NT) {
-        const int r = e / n, m = e % n;
-        const R *row = in + (int64_t)r * n;
-        R s = 0;
+__device__ __forceinline__ void syn_cols(const R *qs, R *tl, R *th, const R *fh, const R *fg, int F, int n, int h,
+                                         int R0, int ts, int ext) {
+    for (int e = threadIdx.x; e < 2 * ts * ext; e += NT) {
+        const int mm = e / ext, j = e % ext;
+        const int m = 2 * R0 + mm;
+        R sl = 0, sh = 0;
         for (int k = (m & 1); k < F; k += 2) {
-            const int i = ((m - k) % n + n) % n / 2;
-            s += filt<R>(b, k) * row[i] + hfilt<R>(b, F, k) * row[i + h];
+            const int ig = wrap(m - k, n) >> 1;
+            const int il = wrap(ig - (R0 - F / 2 + 1), h);
+            const R a = fh[k], c = fg[k];
+            sl += a * qs[0 * SEXT * SEXT + il * SEXT + j] + c * qs[2 * SEXT * SEXT + il * SEXT + j];
+            sh += a * qs[1 * SEXT * SEXT + il * SEXT + j] + c * qs[3 * SEXT * SEXT + il * SEXT + j];
         }
-        o[e] = s;
+        tl[mm * SEXT + j] = sl;
+        th[mm * SEXT + j] = sh;
     }
 }
 
-// last synthesis row pass for all bases together:
-// out = scale * (dirac + sum_b W_b^T u_b), summed in basis order.
+// Inverse along axis 1 for output (mm, nn') of the tile.
 template <typename R>
-__global__ void k_syn_rows_sum(const R *__restrict__ t, int64_t t_stride_basis, int n, const R *__restrict__ dirac,
-                               R scale, R *__restrict__ out) {
-    const int h = n / 2;
-    for (int e = blockIdx.x * NT + threadIdx.x; e < n * n; e += gridDim.x * NT) {
-        const int r = e / n, m = e % n;
-        R tot = dirac ? dirac[e] : R(0);
-        for (int b = 0; b < N_WAVELETS; ++b) {
-            const int F = 2 * (b + 1);
-            const R *row = t + (int64_t)b * t_stride_basis + (int64_t)r * n;
-            R s = 0;
-            for (int k = (m & 1); k < F; k += 2) {
-                const int i = ((m - k) % n + n) % n / 2;
-                s += filt<R>(b, k) * row[i] + hfilt<R>(b, F, k) * row[i + h];
-            }
-            tot += s;
+__device__ __forceinline__ R syn_row(const R *tl, const R *th, const R *fh, const R *fg, int F, int n, int h, int C0,
+                                     int mm, int nnl) {
+    const int nn = 2 * C0 + nnl;
+    R s = 0;
+    for (int j = (nn & 1); j < F; j += 2) {
+        const int jg = wrap(nn - j, n) >> 1;
+        const int jl = wrap(jg - (C0 - F / 2 + 1), h);
+        s += fh[j] * tl[mm * SEXT + jl] + fg[j] * th[mm * SEXT + jl];
+    }
+    return s;
+}
+
+// One synthesis level l > 0 for all 8 bases: out_b (compact pitch n) = W_b^T of
+// (LL' block, detail quadrants).  LL' comes from the coefficients at the
+// coarsest level (from_coef) or from the coarser level's output sl.
+template <typename R>
+__global__ void __launch_bounds__(NT) k_sara_syn(const R *__restrict__ coef, int L, int64_t N, const R *__restrict__ sll,
+                                                 int from_coef, int64_t sll_bstride, int n, int ts, R *__restrict__ out,
+                                                 int64_t out_bstride) {
+    __shared__ R qs[4 * SEXT * SEXT];
+    __shared__ R tl[2 * TS * SEXT], th[2 * TS * SEXT];
+    __shared__ R fh[MAX_TAPS], fg[MAX_TAPS];
+    const int b = blockIdx.y, F = 2 * (b + 1);
+    const int h = n / 2, tpd = h / ts;
+    const int R0 = (blockIdx.x / tpd) * ts, C0 = (blockIdx.x % tpd) * ts;
+    const int ext = ts + F / 2 - 1;
+    stage_filters(fh, fg, b, F);
+    syn_load(qs, coef + (int64_t)(b + 1) * N, sll + (int64_t)b * sll_bstride, from_coef, L, h, R0, C0, ext, F);
+    __syncthreads();
+    syn_cols(qs, tl, th, fh, fg, F, n, h, R0, ts, ext);
+    __syncthreads();
+    R *o = out + (int64_t)b * out_bstride;
+    for (int e = threadIdx.x; e < 4 * ts * ts; e += NT) {
+        const int mm = e / (2 * ts), nnl = e % (2 * ts);
+        o[(int64_t)(2 * R0 + mm) * n + 2 * C0 + nnl] = syn_row(tl, th, fh, fg, F, n, h, C0, mm, nnl);
+    }
+}
+
+// Finest synthesis level, all 8 bases summed in order per output sample.
+// mode 0 (operator):  out = scale * (dirac + sum_b W_b^T c_b)
+// mode 1 (PPD step):  u0 <- clip(u0 + xt/3, kappa); ut = (u0 + sum_b W_b^T u_b)/3;
+//                     xbar = max(0, x - tau (eta g + zeta ut)); xt = 2 xbar - x; x = xbar
+//                     with FP64 partial sums (||dx||^2, ||xbar||^2, ||xbar - x0||^2) per CTA.
+template <typename R> struct PrimalArgs {
+    R *x, *xt, *u0;
+    const R *g, *xtrue;
+    R tau, eta, zeta, kappa;
+    double *part;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(NT) k_sara_syn0(const R *__restrict__ coef, int L, int64_t N, const R *__restrict__ sll,
+                                                  int from_coef, int64_t sll_bstride, int ts, int mode,
+                                                  const R *__restrict__ dirac, R scale, R *__restrict__ out,
+                                                  PrimalArgs<R> P) {
+    __shared__ R qs[4 * SEXT * SEXT];
+    __shared__ R tl[2 * TS * SEXT], th[2 * TS * SEXT];
+    __shared__ R fh[MAX_TAPS], fg[MAX_TAPS];
+    __shared__ double red[3][NT / 32];
+    const int n = L, h = n / 2, tpd = h / ts;
+    const int R0 = (blockIdx.x / tpd) * ts, C0 = (blockIdx.x % tpd) * ts;
+    constexpr int PER = (4 * TS * TS + NT - 1) / NT;
+    R acc[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) acc[k] = 0;
+    for (int b = 0; b < N_WAVELETS; ++b) {
+        const int F = 2 * (b + 1), ext = ts + F / 2 - 1;
+        stage_filters(fh, fg, b, F);
+        syn_load(qs, coef + (int64_t)(b + 1) * N, sll + (int64_t)b * sll_bstride, from_coef, L, h, R0, C0, ext, F);
+        __syncthreads();
+        syn_cols(qs, tl, th, fh, fg, F, n, h, R0, ts, ext);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = threadIdx.x + k * NT;
+            if (e < 4 * ts * ts) acc[k] += syn_row(tl, th, fh, fg, F, n, h, C0, e / (2 * ts), e % (2 * ts));
         }
-        out[e] = scale * tot;
+        __syncthreads();
+    }
+    double sd = 0, sx = 0, se = 0;
+    const R third = R(1.0 / 3.0);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int e = threadIdx.x + k * NT;
+        if (e >= 4 * ts * ts) continue;
+        const int64_t idx = (int64_t)(2 * R0 + e / (2 * ts)) * L + 2 * C0 + e % (2 * ts);
+        if (mode == 0) {
+            out[idx] = scale * ((dirac ? dirac[idx] : R(0)) + acc[k]);
+        } else {
+            const R xo = P.x[idx], xte = P.xt[idx];
+            R un = P.u0[idx] + xte * third;
+            un = fmin(fmax(un, -P.kappa), P.kappa);
+            P.u0[idx] = un;
+            const R utot = (un + acc[k]) * third;
+            const R xb = fmax(R(0), xo - P.tau * (P.eta * P.g[idx] + P.zeta * utot));
+            P.xt[idx] = R(2) * xb - xo;
+            P.x[idx] = xb;
+            const double dd = (double)xb - (double)xo;
+            sd += dd * dd;
+            sx += (double)xb * (double)xb;
+            if (P.xtrue) {
+                const double de = (double)xb - (double)P.xtrue[idx];
+                se += de * de;
+            }
+        }
+    }
+    if (mode == 1) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sd += __shfl_down_sync(0xffffffffu, sd, o);
+            sx += __shfl_down_sync(0xffffffffu, sx, o);
+            se += __shfl_down_sync(0xffffffffu, se, o);
+        }
+        const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (lane == 0) {
+            red[0][wid] = sd;
+            red[1][wid] = sx;
+            red[2][wid] = se;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a0 = 0, a1 = 0, a2 = 0;
+            for (int i = 0; i < NT / 32; ++i) {
+                a0 += red[0][i];
+                a1 += red[1][i];
+                a2 += red[2][i];
+            }
+            P.part[3 * (int64_t)blockIdx.x] = a0;
+            P.part[3 * (int64_t)blockIdx.x + 1] = a1;
+            P.part[3 * (int64_t)blockIdx.x + 2] = a2;
+        }
     }
 }
 
@@ -163,52 +289,81 @@ template <typename R> __global__ void k_scale_copy(const R *__restrict__ in, R *
 }
 
 inline unsigned nblk(int64_t work) { return (unsigned)std::min<int64_t>((work + NT - 1) / NT, 152 * 8); }
+inline int tile_side(int h) { return h < TS ? h : TS; }
 
-// Psi_b^dagger for b = 1..8 (times 1/3) into coef[b] (mode 0), or the fused
-// clip update of u (mode 1).  x has pitch L.
-template <typename R> int analysis_core(ppd_ctx *c, const R *x, R *coef, int mode, cudaStream_t s) {
+inline int tile_side_ana(int h) { return h < TSA ? h : TSA; }
+
+// Analysis of all levels (tiled).  mode 0 writes c = W x / 3, mode 1
+// clip-updates u.
+template <typename R> int analysis_all(ppd_ctx *c, const R *x, R *coef, int mode, cudaStream_t s) {
     const int L = c->L0;
     const int64_t N = c->N;
-    R *tmp = static_cast<R *>(c->wtmp);          // 8 x L^2
-    R *ll = static_cast<R *>(c->wtmp2);          // 8 x (L/2)^2
+    R *ll[2] = {static_cast<R *>(c->wtmp), static_cast<R *>(c->wtmp) + (int64_t)N_WAVELETS * (L / 2) * (L / 2)};
     const int64_t ll_stride = (int64_t)(L / 2) * (L / 2);
     int site;
     for (int l = 0; l < c->levels; ++l) {
-        const int n = L >> l;
+        const int n = L >> l, h = n / 2, ts = tile_side_ana(h);
         const bool last = (l == c->levels - 1);
-        PPD_CHECK(launch_begin(c, "sara_ana_rows", s, &site));
-        if (l == 0) k_ana_rows<R><<<dim3(nblk((int64_t)n * n), 1, N_WAVELETS), NT, 0, s>>>(x, L, 0, tmp, n, N);
-        else k_ana_rows<R><<<dim3(nblk((int64_t)n * n), 1, N_WAVELETS), NT, 0, s>>>(ll, n, (int)ll_stride, tmp, n, N);
-        PPD_CHECK(launch_end(c, site, s));
-        PPD_CHECK(launch_begin(c, "sara_ana_cols", s, &site));
-        k_ana_cols<R><<<dim3(nblk((int64_t)n * n), 1, N_WAVELETS), NT, 0, s>>>(tmp, N, n, ll, ll_stride, last, coef, L,
-                                                                               N, mode, (R)c->kappa);
+        const R *in = l == 0 ? x : ll[(l - 1) & 1];
+        const int pitch = l == 0 ? L : n;
+        const int64_t bstride = l == 0 ? 0 : ll_stride;
+        PPD_CHECK(launch_begin(c, "sara_analysis", s, &site));
+        k_sara_ana<R><<<dim3((h / ts) * (h / ts), N_WAVELETS), NT, 0, s>>>(in, pitch, bstride, n, ts, ll[l & 1],
+                                                                           ll_stride, last, coef, L, N, mode,
+                                                                           (R)c->kappa);
         PPD_CHECK(launch_end(c, site, s));
     }
     return PPD_OK;
 }
 
-// sum over wavelet bases of W_b^T coef[b+1], plus scale*dirac -> out
-template <typename R> int synthesis_core(ppd_ctx *c, const R *coef, const R *dirac, R scale, R *out, cudaStream_t s) {
+// Synthesis of the 8 wavelet bases, levels coarsest .. 1 (tiled); returns
+// the buffer holding the LL' block of level 0.
+template <typename R> int synthesis_levels(ppd_ctx *c, const R *coef, const R **ll0, cudaStream_t s) {
     const int L = c->L0;
     const int64_t N = c->N;
-    R *tmp = static_cast<R *>(c->wtmp);                          // 8 x L^2
-    R *sl = static_cast<R *>(c->wtmp2) + (int64_t)N_WAVELETS * (L / 2) * (L / 2);   // 8 x (L/2)^2
-    const int64_t sl_stride = (int64_t)(L / 2) * (L / 2);
-    int site;
-    for (int l = c->levels - 1; l >= 0; --l) {
-        const int n = L >> l;
+    const int64_t st = (int64_t)(L / 2) * (L / 2);
+    R *buf[2] = {static_cast<R *>(c->wtmp2), static_cast<R *>(c->wtmp2) + (int64_t)N_WAVELETS * st};
+    const R *prev = nullptr;
+    int site, k = 0;
+    for (int l = c->levels - 1; l >= 1; --l, ++k) {
+        const int n = L >> l, h = n / 2, ts = tile_side(h);
         const bool coarsest = (l == c->levels - 1);
-        PPD_CHECK(launch_begin(c, "sara_syn_cols", s, &site));
-        k_syn_cols<R><<<dim3(nblk((int64_t)n * n), 1, N_WAVELETS), NT, 0, s>>>(coef, L, N, sl, coarsest ? 1 : 0,
-                                                                               sl_stride, n, tmp, N);
+        PPD_CHECK(launch_begin(c, "sara_synthesis", s, &site));
+        k_sara_syn<R><<<dim3((h / ts) * (h / ts), N_WAVELETS), NT, 0, s>>>(coef, L, N, coarsest ? coef : prev,
+                                                                           coarsest ? 1 : 0, st, n, ts, buf[k & 1],
+                                                                           st);
         PPD_CHECK(launch_end(c, site, s));
-        PPD_CHECK(launch_begin(c, "sara_syn_rows", s, &site));
-        if (l > 0) k_syn_rows<R><<<dim3(nblk((int64_t)n * n), 1, N_WAVELETS), NT, 0, s>>>(tmp, N, n, sl, sl_stride);
-        else k_syn_rows_sum<R><<<nblk((int64_t)n * n), NT, 0, s>>>(tmp, N, n, dirac, scale, out);
-        PPD_CHECK(launch_end(c, site, s));
+        prev = buf[k & 1];
     }
+    *ll0 = prev;
     return PPD_OK;
+}
+
+template <typename R>
+int synthesis_final(ppd_ctx *c, const R *coef, const R *ll0, int mode, const R *dirac, R scale, R *out,
+                    cudaStream_t s) {
+    const int L = c->L0;
+    const int h = L / 2, ts = tile_side(h);
+    const int64_t st = (int64_t)(L / 2) * (L / 2);
+    PrimalArgs<R> P{};
+    if (mode == 1) {
+        P.x = static_cast<R *>(c->x);
+        P.xt = static_cast<R *>(c->xt);
+        P.u0 = static_cast<R *>(c->u);
+        P.g = static_cast<const R *>(c->g);
+        P.xtrue = static_cast<const R *>(c->xtrue);
+        P.tau = (R)c->tau;
+        P.eta = (R)c->eta;
+        P.zeta = (R)c->zeta;
+        P.kappa = (R)c->kappa;
+        P.part = c->prim_part;
+    }
+    const bool from_coef = ll0 == nullptr;   // levels == 1: LL' straight from the coefficients
+    int site;
+    PPD_CHECK(launch_begin(c, mode == 1 ? "sara_synthesis_primal" : "sara_synthesis", s, &site));
+    k_sara_syn0<R><<<(h / ts) * (h / ts), NT, 0, s>>>(coef, L, c->N, from_coef ? coef : ll0, from_coef ? 1 : 0, st, ts,
+                                                        mode, dirac, scale, out, P);
+    return launch_end(c, site, s);
 }
 
 // Durand-Kerner roots of the polynomial with real coefficients a (ascending).
@@ -312,27 +467,43 @@ template <typename R> int psi_analysis(ppd_ctx *c, const R *x, R *coef, cudaStre
     PPD_CHECK(launch_begin(c, "sara_dirac", s, &site));
     k_scale_copy<R><<<nblk(c->N), NT, 0, s>>>(x, coef, c->N, R(1.0 / 3.0));
     PPD_CHECK(launch_end(c, site, s));
-    return analysis_core<R>(c, x, coef, 0, s);
+    return analysis_all<R>(c, x, coef, 0, s);
 }
 
 template <typename R> int psi_synthesis(ppd_ctx *c, const R *coef, R *x, cudaStream_t s) {
-    return synthesis_core<R>(c, coef, coef, R(1.0 / 3.0), x, s);
+    const R *ll0 = nullptr;
+    PPD_CHECK(synthesis_levels<R>(c, coef, &ll0, s));
+    return synthesis_final<R>(c, coef, ll0, 0, coef, R(1.0 / 3.0), x, s);
 }
 
-// Prior dual step for the 8 wavelet bases and synthesis of their sum:
-// u_b <- clip(u_b + Psi_b^dagger xt, kappa); ut <- sum_b W_b^T u_b (the Dirac
-// basis and the 1/3 are applied in the primal step).
-template <typename R> int sara_dual_step(ppd_ctx *c, cudaStream_t s) {
+// Prior dual step of Algorithm 3 for the 8 wavelet bases up to the level-0
+// synthesis: u_b <- clip(u_b + Psi_b^dagger xt, kappa), then the synthesis of
+// levels coarsest .. 1.  Needs only xt and u, so it can run beside the data
+// branch of the iteration.
+template <typename R> int sara_prior_branch(ppd_ctx *c, const R **ll0, cudaStream_t s) {
     R *u = static_cast<R *>(c->u);
-    PPD_CHECK(analysis_core<R>(c, static_cast<const R *>(c->xt), u, 1, s));
-    return synthesis_core<R>(c, u, nullptr, R(1), static_cast<R *>(c->ut), s);
+    PPD_CHECK(analysis_all<R>(c, static_cast<const R *>(c->xt), u, 1, s));
+    return synthesis_levels<R>(c, u, ll0, s);
+}
+
+// Level-0 synthesis summed over the bases with the Dirac basis, fused with
+// the primal step (needs g = Phi^dagger v from the data branch).
+template <typename R> int sara_primal(ppd_ctx *c, const R *ll0, cudaStream_t s) {
+    return synthesis_final<R>(c, static_cast<const R *>(c->u), ll0, 1, nullptr, R(1), nullptr, s);
+}
+
+int sara_primal_blocks(ppd_ctx *c) {
+    const int h = c->L0 / 2, ts = tile_side(h);
+    return (h / ts) * (h / ts);
 }
 
 template int psi_analysis<float>(ppd_ctx *, const float *, float *, cudaStream_t);
 template int psi_analysis<double>(ppd_ctx *, const double *, double *, cudaStream_t);
 template int psi_synthesis<float>(ppd_ctx *, const float *, float *, cudaStream_t);
 template int psi_synthesis<double>(ppd_ctx *, const double *, double *, cudaStream_t);
-template int sara_dual_step<float>(ppd_ctx *, cudaStream_t);
-template int sara_dual_step<double>(ppd_ctx *, cudaStream_t);
+template int sara_prior_branch<float>(ppd_ctx *, const float **, cudaStream_t);
+template int sara_prior_branch<double>(ppd_ctx *, const double **, cudaStream_t);
+template int sara_primal<float>(ppd_ctx *, const float *, cudaStream_t);
+template int sara_primal<double>(ppd_ctx *, const double *, cudaStream_t);
 
 }  // namespace ppd

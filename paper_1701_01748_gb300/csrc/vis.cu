@@ -105,7 +105,10 @@ template <typename R> struct VisArgs {
     const cplx_t<R> *y;
     cplx_t<R> *v, *z, *w, *p;
     const double *mu, *scale;
-    double *partials;
+    double *partials;            // this launch's chunk partials
+    const double *part_in;       // previous step's chunk partials (P_B scale)
+    const int32_t *blk_ptr, *blk_list;
+    const double *eps;
     int *err;
     // operator mode I/O (caller order through perm when non-null)
     const cplx_t<R> *op_in;
@@ -152,6 +155,27 @@ template <typename R> struct Acc {
 };
 
 constexpr int DG_NT = 256;
+
+// P_B scale of block `blk` (Section 3.3, Eq. "proj-L2" as a radial scale):
+// eps / ||w - y|| if that norm exceeds eps, else 1, from the previous step's
+// chunk partials summed in a fixed order (the same result in every CTA).
+template <typename R> __device__ double block_scale(const VisArgs<R> &A, int blk) {
+    __shared__ double sc_s;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double a = 0;
+        for (int k = A.blk_ptr[blk] + lane; k < A.blk_ptr[blk + 1]; k += 32) a += A.part_in[NPART * A.blk_list[k]];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) {
+            const double nrm = sqrt(a);
+            if (!isfinite(nrm)) atomicOr(A.err, ERR_NONFINITE);
+            sc_s = (nrm > A.eps[blk]) ? A.eps[blk] / nrm : 1.0;
+        }
+    }
+    __syncthreads();
+    return sc_s;
+}
 
 // ----------------------------------------------------------------- degrid
 // mode DG_OP:    op_out[perm[i]] = Theta G a
@@ -259,7 +283,7 @@ __global__ void __launch_bounds__(DG_NT) k_subiter(VisArgs<R> A) {
     using C = cplx_t<R>;
     const int ch = blockIdx.x;
     const int start = A.ch_start[ch], count = A.ch_count[ch], blk = A.ch_block[ch];
-    const R c = (R)A.scale[blk], mu = (R)A.mu[blk];
+    const R c = (R)block_scale(A, blk), mu = (R)A.mu[blk];
     Acc<R> s_w;
     for (int i = threadIdx.x; i < count; i += DG_NT) {
         const int gi = start + i;
@@ -337,7 +361,7 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
     for (int i = threadIdx.x; i < (KB_DEG + 1) * KB_J; i += NT) poly[i] = A.kbpoly ? A.kbpoly[i] : 0.f;
     for (int e = threadIdx.x; e < NW * E * P; e += NT) priv[e] = C{0, 0};
     R c = 0;
-    if (MODE == GR_DUAL) c = (R)A.scale[A.ch_block[ch]];
+    if (MODE == GR_DUAL) c = (R)block_scale(A, A.ch_block[ch]);
     __syncthreads();
 
     C *mine = priv + warp * E * P;
@@ -372,21 +396,40 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
             slb[threadIdx.x] = lb0 | (lb1 << 16);
         }
         __syncthreads();
-        for (int i = warp; i < n; i += NW) {
+        // warp w takes a contiguous segment of the staged visibilities; the
+        // sort order makes runs of visibilities share a first tap, so each
+        // lane accumulates its two footprint cells in registers and writes
+        // the warp's private tile only when the base cell changes.
+        const int seg = (n + NW - 1) / NW;
+        const int i0 = warp * seg, i1 = min(n, i0 + seg);
+        int cur = -1;
+        C acc0{0, 0}, acc1{0, 0};
+        for (int i = i0; i < i1; ++i) {
             const int lb = slb[i];
-            const int r = (lb & 0xffff) + a, cc = (lb >> 16) + bb;
+            if (lb != cur) {
+                if (cur >= 0) {
+                    C *cell = mine + ((cur & 0xffff) + a) * P + (cur >> 16) + bb;
+                    C g0 = cell[0], g1 = cell[1];
+                    cell[0] = cadd(g0, acc0);
+                    cell[1] = cadd(g1, acc1);
+                }
+                cur = lb;
+                acc0 = C{0, 0};
+                acc1 = C{0, 0};
+            }
             const C tv = sv[i];
             const R wa = sw0[i * KB_J + a];
             const R wb0 = wa * sw1[i * KB_J + bb], wb1 = wa * sw1[i * KB_J + bb + 1];
-            C *cell = mine + r * P + cc;
+            acc0.x += wb0 * tv.x;
+            acc0.y += wb0 * tv.y;
+            acc1.x += wb1 * tv.x;
+            acc1.y += wb1 * tv.y;
+        }
+        if (cur >= 0) {
+            C *cell = mine + ((cur & 0xffff) + a) * P + (cur >> 16) + bb;
             C g0 = cell[0], g1 = cell[1];
-            g0.x += wb0 * tv.x;
-            g0.y += wb0 * tv.y;
-            g1.x += wb1 * tv.x;
-            g1.y += wb1 * tv.y;
-            cell[0] = g0;
-            cell[1] = g1;
-            __syncwarp();
+            cell[0] = cadd(g0, acc0);
+            cell[1] = cadd(g1, acc1);
         }
         __syncthreads();
     }
@@ -401,31 +444,47 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
 }
 
 // ----------------------------------------------------------------- combine
+// One CTA per active tile (a tile with chunks, or below/right of one):
 // grid[r][c] = sum of the partial tiles covering the cell, in a fixed order:
 // the cell's own tile's chunks, then the halo rows/columns of the tiles
-// above, left and above-left (periodic grid).
+// above, left and above-left (periodic grid).  Tiles never touched by any
+// visibility stay zero from the initial clear.
 template <typename R, int T>
-__global__ void k_combine(const cplx_t<R> *__restrict__ gpart, const int32_t *__restrict__ tile_first,
-                          const int32_t *__restrict__ tile_n, int K0, int K1, cplx_t<R> *__restrict__ grid) {
+__global__ void __launch_bounds__(256) k_combine(const cplx_t<R> *__restrict__ gpart,
+                                                 const int32_t *__restrict__ tile_first,
+                                                 const int32_t *__restrict__ tile_n,
+                                                 const int32_t *__restrict__ active, int K1, int nt0, int nt1,
+                                                 cplx_t<R> *__restrict__ grid) {
     using C = cplx_t<R>;
     constexpr int E = T + HALO;
-    const int nt0 = K0 / T, nt1 = K1 / T;
-    const int64_t total = (int64_t)K0 * K1;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(e / K1), c = (int)(e % K1);
-        const int t0 = r / T, t1 = c / T, lr = r % T, lc = c % T;
-        C acc{0, 0};
-        auto add_tile = [&](int tt0, int tt1, int rr, int cc) {
-            const int t = tt0 * nt1 + tt1;
-            const int f = tile_first[t], n = tile_n[t];
-            for (int k = 0; k < n; ++k) acc = cadd(acc, gpart[(int64_t)(f + k) * E * E + rr * E + cc]);
-        };
-        add_tile(t0, t1, lr, lc);
+    __shared__ int f_s[4], n_s[4];
+    constexpr int PARTS = 4;                       // CTAs per tile, T/PARTS rows each
+    const int t = active[blockIdx.x / PARTS];
+    const int part = blockIdx.x % PARTS;
+    const int t0 = t / nt1, t1 = t - t0 * nt1;
+    if (threadIdx.x < 4) {
         const int up = (t0 + nt0 - 1) % nt0, left = (t1 + nt1 - 1) % nt1;
-        if (lr < HALO) add_tile(up, t1, lr + T, lc);
-        if (lc < HALO) add_tile(t0, left, lr, lc + T);
-        if (lr < HALO && lc < HALO) add_tile(up, left, lr + T, lc + T);
-        grid[e] = acc;
+        const int tt = threadIdx.x == 0 ? t : threadIdx.x == 1 ? up * nt1 + t1
+                       : threadIdx.x == 2 ? t0 * nt1 + left : up * nt1 + left;
+        f_s[threadIdx.x] = tile_first[tt];
+        n_s[threadIdx.x] = tile_n[tt];
+    }
+    __syncthreads();
+    for (int e = part * (T * T / PARTS) + threadIdx.x; e < (part + 1) * (T * T / PARTS); e += 256) {
+        const int lr = e / T, lc = e % T;
+        C acc{0, 0};
+#pragma unroll 4
+        for (int k = 0; k < n_s[0]; ++k) acc = cadd(acc, gpart[(int64_t)(f_s[0] + k) * E * E + lr * E + lc]);
+        if (lr < HALO)
+            for (int k = 0; k < n_s[1]; ++k)
+                acc = cadd(acc, gpart[(int64_t)(f_s[1] + k) * E * E + (lr + T) * E + lc]);
+        if (lc < HALO)
+            for (int k = 0; k < n_s[2]; ++k)
+                acc = cadd(acc, gpart[(int64_t)(f_s[2] + k) * E * E + lr * E + lc + T]);
+        if (lr < HALO && lc < HALO)
+            for (int k = 0; k < n_s[3]; ++k)
+                acc = cadd(acc, gpart[(int64_t)(f_s[3] + k) * E * E + (lr + T) * E + lc + T]);
+        grid[(int64_t)(t0 * T + lr) * K1 + t1 * T + lc] = acc;
     }
 }
 
@@ -451,7 +510,11 @@ template <typename R> VisArgs<R> make_args(ppd_ctx *c) {
     A.p = static_cast<cplx_t<R> *>(c->p);
     A.mu = c->mu_d;
     A.scale = c->scale;
-    A.partials = c->partials;
+    A.partials = c->part_out;
+    A.part_in = c->part_in;
+    A.blk_ptr = c->ch.blk_ptr;
+    A.blk_list = c->ch.blk_list;
+    A.eps = c->eps_d;
     A.err = c->err;
     return A;
 }
@@ -511,10 +574,10 @@ int grid_t(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_
         else k_grid<R, T, GR_DUAL><<<nb, NT, sh, s>>>(A, gp);
         PPD_CHECK(launch_end(c, site, s));
     }
+    if (c->ch.n_active == 0) return PPD_OK;
     PPD_CHECK(launch_begin(c, "grid_combine", s, &site));
-    const int64_t cells = (int64_t)c->K0 * c->K1;
-    const int nblk = (int)std::min<int64_t>((cells + 255) / 256, 152 * 16);
-    k_combine<R, T><<<nblk, 256, 0, s>>>(gp, c->ch.tile_first, c->ch.tile_n, c->K0, c->K1, grid);
+    k_combine<R, T><<<(unsigned)c->ch.n_active * 4, 256, 0, s>>>(gp, c->ch.tile_first, c->ch.tile_n, c->ch.active,
+                                                            c->K1, c->K0 / T, c->K1 / T, grid);
     return launch_end(c, site, s);
 }
 
@@ -600,7 +663,7 @@ int block_norms(ppd_ctx *c, int with_resid, cudaStream_t s) {
     int site;
     PPD_CHECK(launch_begin(c, "block_norms", s, &site));
     const int wpb = 8;
-    k_block_norms<<<(c->d + wpb - 1) / wpb, wpb * 32, 0, s>>>(c->partials, c->ch.blk_ptr, c->ch.blk_list, c->eps_d,
+    k_block_norms<<<(c->d + wpb - 1) / wpb, wpb * 32, 0, s>>>(c->part_out, c->ch.blk_ptr, c->ch.blk_list, c->eps_d,
                                                                c->d, with_resid, c->scale, c->resid2, c->err);
     return launch_end(c, site, s);
 }

@@ -97,7 +97,7 @@ def test_bins_and_order_bit_exact(which):
     K = 2 * L
     ob0, ob1, _, _ = nufft.base_cells(om, K, K)
     _, ocnt = nufft.uniform_weights(om, K, K)
-    T = 32 if K >= 80 else 16
+    T = 16
     operm, _, _, _ = nufft.visibility_order(om, blk, K, K, T)
     assert np.array_equal(b0, ob0) and np.array_equal(b1, ob1)
     assert np.array_equal(cnt, ocnt)

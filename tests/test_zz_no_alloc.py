@@ -52,7 +52,7 @@ def test_noalloc_adjoint_matches_adjoint_on_two_calls(prec):
 
 def test_noalloc_refuses_problems_beyond_its_scratch():
     p = synth.make_problem("noalloc_big", L=64, M=60000, n_blocks=1, uv_sigma=0.2, seed=22, n_points=4, n_blobs=1)
-    s = ppd.Solver(p.L, 1, precision=ppd.PPD_FP32_FP64NORMS, eta=1.0, chunk=16)
+    s = ppd.Solver(p.L, 1, precision=ppd.PPD_FP32_FP64NORMS, eta=1.0, chunk=16, tile=32)
     s.set_problem(p.omega, p.y, p.block, theta=p.theta)
     E = s.params()["tile"] + 8
     assert s.params()["n_chunks"] * E * E * 8 > 32 * 2 ** 20
