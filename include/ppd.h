@@ -221,7 +221,9 @@ PPD_API int ppd_psi_synthesis(ppd_ctx *ctx, const void *c_dev, void *x_dev, void
 
 /* Per-kernel timing with CUDA events on the context stream.  enable = 1
  * records an event pair around every kernel the iteration launches (inside
- * the captured graph too); ppd_timing_collect() adds the durations of the
+ * the captured graph too) and runs the iteration's two independent branches
+ * one after the other, so each pair brackets one kernel only (the iteration
+ * is then slower than with timing off); ppd_timing_collect() adds the durations of the
  * launches completed since the last collect (synchronises) to running sums;
  * ppd_timing_read() returns, for up to n kernel names, the summed
  * milliseconds and launch counts.  names[i] points to static strings. */

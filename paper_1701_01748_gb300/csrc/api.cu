@@ -188,13 +188,15 @@ int check_err_word(ppd_ctx *c) {
 // prior branch (SARA analysis, clip, synthesis down to level 1) needs only
 // xt and u, so in the FP32 path it runs on a second stream beside the data
 // branch (FFT, degridding with the data step, gridding, inverse FFT); both
-// join before the fused level-0 synthesis + primal step.  The per-block P_B
+// join before the primal step.  The per-block P_B
 // scales are computed in the prologue of the kernel that uses them, from the
 // previous launch's chunk partials (two banks).
 template <typename R> int iteration_body(ppd_ctx *c, cudaStream_t s, bool first) {
     using C = cplx_t<R>;
     C *ga = static_cast<C *>(c->grid_a), *gv = static_cast<C *>(c->grid_v);
-    const bool fork = c->is_f32 && c->stream2;
+    // with per-kernel timing on, the branches run serialized so that every
+    // event pair brackets exactly one kernel
+    const bool fork = c->is_f32 && c->stream2 && !c->timing;
     cudaStream_t s2 = fork ? c->stream2 : s;
     if (fork) {
         PPD_CUDA(cudaEventRecord(c->ev_fork, s));
@@ -202,6 +204,7 @@ template <typename R> int iteration_body(ppd_ctx *c, cudaStream_t s, bool first)
     }
     const R *ll0 = nullptr;
     PPD_CHECK(sara_prior_branch<R>(c, &ll0, s2));
+    PPD_CHECK(sara_level0<R>(c, ll0, s2));
     if (fork) PPD_CUDA(cudaEventRecord(c->ev_join, s2));
 
     double *bank[2] = {c->partials, c->partials + NPART * c->ch.n};
@@ -224,7 +227,7 @@ template <typename R> int iteration_body(ppd_ctx *c, cudaStream_t s, bool first)
     PPD_CHECK(grid_vis<R>(c, GR_DUAL, nullptr, nullptr, gv, s));
     PPD_CHECK(fft_inverse<R>(c, gv, static_cast<R *>(c->g), s));
     if (fork) PPD_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
-    PPD_CHECK(sara_primal<R>(c, ll0, s));
+    PPD_CHECK(primal_step<R>(c, s));
     return PPD_OK;
 }
 
@@ -442,13 +445,15 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
         (st = dalloc_bytes(&c->u, N_BASES * N * rb)) || (st = dalloc_bytes(&c->wtmp, N_WAVELETS * N * rb)) ||
         (st = dalloc_bytes(&c->wtmp2, 4 * N * rb)) || (st = dalloc_bytes(&c->grid_a, G * cb)) ||
         (st = dalloc_bytes(&c->grid_v, G * cb)) || (st = dalloc_bytes(&c->fft_tmp, (int64_t)c->L0 * c->K1 * cb)) ||
+        (st = dalloc_bytes(&c->fft_tmp_inv, (int64_t)c->L0 * c->K1 * cb)) ||
+        (st = dalloc(&c->fwd_strips, c->K1)) || (st = dalloc(&c->inv_strips, c->K1)) ||
+        (st = dalloc(&c->row_fwd, c->K0)) || (st = dalloc(&c->row_inv, c->K0)) || (st = dalloc(&c->col_fwd, c->K1)) ||
         (st = dalloc_bytes(&c->tw0, c->K0 * cb)) || (st = dalloc_bytes(&c->deap0, c->L0 * rb)) ||
         (st = dalloc_bytes(&c->deap1, c->L1 * rb)) ||
         (st = dalloc_bytes(&c->kbpoly, (KB_DEG + 1) * KB_J * sizeof(float))) || (st = dalloc(&c->err, 1)) ||
         (st = dalloc(&c->stat_out, 3)))
         return bail(st);
-    // the primal step runs inside the finest SARA synthesis, one CTA per tile
-    c->n_prim_blocks = sara_primal_blocks(c);
+    c->n_prim_blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 4);
     if ((st = dalloc(&c->prim_part, 3 * (size_t)c->n_prim_blocks))) return bail(st);
     if ((st = make_twiddles(c)) || (st = make_deapodisation(c)) || (st = make_filters(c)) || (st = make_kb_poly(c)))
         return bail(st);
@@ -471,6 +476,9 @@ void ppd_destroy(ppd_ctx *c) {
     }
     for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
     free_vis(c);
+    for (void *p : {(void *)c->fwd_strips, (void *)c->inv_strips, (void *)c->row_fwd, (void *)c->row_inv,
+                    (void *)c->col_fwd, c->fft_tmp_inv})
+        dfree(p);
     for (void *p : {c->x, c->xt, c->g, c->ut, c->xtrue, c->u, c->wtmp, c->wtmp2, c->grid_a, c->grid_v, c->fft_tmp,
                     c->tw0, c->deap0, c->deap1, c->kbpoly, (void *)c->prim_part, (void *)c->stat_out, (void *)c->err})
         dfree(p);
@@ -586,6 +594,27 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
         for (int t = 0; t < ntiles; ++t)
             if (mark[t]) active.push_back(t);
     }
+    // FFT pruning: rows/columns the degridding reads (tiles with chunks plus
+    // their halo) and rows/columns the gridding can write (active tiles)
+    std::vector<char> rf(c->K0, 0), cf(c->K1, 0), ri(c->K0, 0), ci(c->K1, 0);
+    {
+        const int nt1 = c->K1 / c->T;
+        for (int t = 0; t < ntiles; ++t) {
+            if (!tn[t]) continue;
+            const int r0 = (t / nt1) * c->T, c0 = (t % nt1) * c->T;
+            for (int k = 0; k < c->T + HALO; ++k) {
+                rf[(r0 + k) % c->K0] = 1;
+                cf[(c0 + k) % c->K1] = 1;
+            }
+        }
+        for (int t : active) {
+            const int r0 = (t / nt1) * c->T, c0 = (t % nt1) * c->T;
+            for (int k = 0; k < c->T; ++k) {
+                ri[r0 + k] = 1;
+                ci[c0 + k] = 1;
+            }
+        }
+    }
     std::vector<int32_t> bptr(c->d + 1, 0), blist(nch);
     for (int64_t k = 0; k < nch; ++k) bptr[cbk[k] + 1]++;
     for (int j = 0; j < c->d; ++j) bptr[j + 1] += bptr[j];
@@ -645,6 +674,10 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
     if ((e = cudaMemset(c->grid_v, 0, (size_t)c->K0 * c->K1 * 2 * c->rsz))) {
         free_vis(c);
         return fail(PPD_ERR_CUDA, std::string("ppd_set_visibilities: clear: ") + cudaGetErrorString(e));
+    }
+    if ((st = fft_plan_pruning(c, rf, cf, ri, ci))) {
+        free_vis(c);
+        return st;
     }
     c->block_count_h.assign(c->d, 0);
     for (int64_t i = 0; i < M; ++i) c->block_count_h[block_id[i]]++;

@@ -106,7 +106,13 @@ struct ppd_ctx {
     // image side
     void *x = nullptr, *xt = nullptr, *g = nullptr, *ut = nullptr, *xtrue = nullptr;
     void *u = nullptr, *wtmp = nullptr, *wtmp2 = nullptr;
-    void *grid_a = nullptr, *grid_v = nullptr, *fft_tmp = nullptr;
+    void *grid_a = nullptr, *grid_v = nullptr, *fft_tmp = nullptr, *fft_tmp_inv = nullptr;
+    // FFT pruning (set by ppd_set_visibilities): column strips the forward /
+    // inverse column passes process, grid rows the degridding reads, grid
+    // rows the gridding can write, tmp columns the forward column pass reads
+    int32_t *fwd_strips = nullptr, *inv_strips = nullptr;
+    int n_fwd_strips = 0, n_inv_strips = 0;
+    uint8_t *row_fwd = nullptr, *row_inv = nullptr, *col_fwd = nullptr;
     void *tw0 = nullptr, *tw1 = nullptr, *deap0 = nullptr, *deap1 = nullptr;
     void *filt = nullptr;       // 8 x 16 reals (low-pass, zero padded)
     void *kbpoly = nullptr;     // (KB_DEG+1) x 8 floats
@@ -172,6 +178,8 @@ int launch_end(ppd_ctx *c, int site, cudaStream_t s);
 template <typename R> int fft_forward(ppd_ctx *c, const R *x, cplx_t<R> *grid, cudaStream_t s);
 template <typename R> int fft_inverse(ppd_ctx *c, const cplx_t<R> *grid, R *img, cudaStream_t s);
 int make_twiddles(ppd_ctx *c);
+int fft_plan_pruning(ppd_ctx *c, const std::vector<char> &rows_fwd, const std::vector<char> &cols_fwd,
+                     const std::vector<char> &rows_inv, const std::vector<char> &cols_inv);
 int make_deapodisation(ppd_ctx *c);
 
 // visibilities (vis.cu)
@@ -200,10 +208,10 @@ int make_filters(ppd_ctx *c);
 template <typename R> int psi_analysis(ppd_ctx *c, const R *x, R *coef, cudaStream_t s);
 template <typename R> int psi_synthesis(ppd_ctx *c, const R *coef, R *x, cudaStream_t s);
 template <typename R> int sara_prior_branch(ppd_ctx *c, const R **ll0, cudaStream_t s);
-template <typename R> int sara_primal(ppd_ctx *c, const R *ll0, cudaStream_t s);
-int sara_primal_blocks(ppd_ctx *c);
+template <typename R> int sara_level0(ppd_ctx *c, const R *ll0, cudaStream_t s);
 
 // image side (image.cu)
+template <typename R> int primal_step(ppd_ctx *c, cudaStream_t s);
 int reduce_primal_stats(ppd_ctx *c, cudaStream_t s);
 template <typename R> int scale_copy(ppd_ctx *c, const R *in, R *out, int64_t n, double a, cudaStream_t s);
 template <typename R> int sumsq(ppd_ctx *c, const R *in, int64_t n, double *out_dev, cudaStream_t s);

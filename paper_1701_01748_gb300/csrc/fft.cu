@@ -123,7 +123,7 @@ template <typename R> __host__ __device__ constexpr int cols_per_cta(int K) {
 template <typename R, int K>
 __global__ void __launch_bounds__(NT) k_rows_fwd(const R *__restrict__ x, cplx_t<R> *__restrict__ tmp,
                                                  const cplx_t<R> *__restrict__ tw, const R *__restrict__ s0,
-                                                 const R *__restrict__ s1, int L) {
+                                                 const R *__restrict__ s1, int L, const uint8_t *__restrict__ colmask) {
     using C = cplx_t<R>;
     constexpr int B = rows_per_cta<R>(K);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -144,21 +144,23 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(const R *__restrict__ x, cplx_t
     fft_smem<R, K, B, NT, false>(buf, tws);
     for (int e = threadIdx.x; e < B * K; e += NT) {
         int s = e / K, c = e % K, n0 = row0 + s;
-        if (n0 < L) tmp[(int64_t)n0 * K + c] = buf[s * K + ((c + K / 2) & (K - 1))];
+        if (n0 < L && colmask[c]) tmp[(int64_t)n0 * K + c] = buf[s * K + ((c + K / 2) & (K - 1))];
     }
 }
 
 // forward column pass: grid[r][c] = FFT_axis0(tmp padded)[(r + K/2) mod K][c]
 template <typename R, int K>
 __global__ void __launch_bounds__(NT) k_cols_fwd(const cplx_t<R> *__restrict__ tmp, cplx_t<R> *__restrict__ grid,
-                                                 const cplx_t<R> *__restrict__ tw, int L) {
+                                                 const cplx_t<R> *__restrict__ tw, int L,
+                                                 const int32_t *__restrict__ strips,
+                                                 const uint8_t *__restrict__ rowmask) {
     using C = cplx_t<R>;
     constexpr int W = cols_per_cta<R>(K);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
     C *tws = buf + W * K;   // twiddles staged in shared memory
     for (int e = threadIdx.x; e < K; e += NT) tws[e] = tw[e];
-    const int c0 = blockIdx.x * W;
+    const int c0 = strips[blockIdx.x];
     for (int e = threadIdx.x; e < W * K; e += NT) buf[e] = C{0, 0};
     __syncthreads();
     for (int e = threadIdx.x; e < W * L; e += NT) {
@@ -170,24 +172,26 @@ __global__ void __launch_bounds__(NT) k_cols_fwd(const cplx_t<R> *__restrict__ t
     fft_smem<R, K, W, NT, true>(buf, tws);
     for (int e = threadIdx.x; e < W * K; e += NT) {
         int s = e % W, r = e / W;
-        grid[(int64_t)r * K + c0 + s] = buf[((r + K / 2) & (K - 1)) * W + s];
+        if (rowmask[r]) grid[(int64_t)r * K + c0 + s] = buf[((r + K / 2) & (K - 1)) * W + s];
     }
 }
 
 // inverse column pass: tmp[n0][c] = (F^H along axis 0 of grid)[(n0 - L/2) mod K][c]
 template <typename R, int K>
 __global__ void __launch_bounds__(NT) k_cols_inv(const cplx_t<R> *__restrict__ grid, cplx_t<R> *__restrict__ tmp,
-                                                 const cplx_t<R> *__restrict__ tw, int L) {
+                                                 const cplx_t<R> *__restrict__ tw, int L,
+                                                 const int32_t *__restrict__ strips,
+                                                 const uint8_t *__restrict__ rowmask) {
     using C = cplx_t<R>;
     constexpr int W = cols_per_cta<R>(K);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
     C *tws = buf + W * K;   // twiddles staged in shared memory
     for (int e = threadIdx.x; e < K; e += NT) tws[e] = tw[e];
-    const int c0 = blockIdx.x * W;
+    const int c0 = strips[blockIdx.x];
     for (int e = threadIdx.x; e < W * K; e += NT) {
         int s = e % W, r = e / W;   // r: stored (centred) row; natural frequency (r + K/2) mod K
-        buf[((r + K / 2) & (K - 1)) * W + s] = cconj(grid[(int64_t)r * K + c0 + s]);
+        buf[((r + K / 2) & (K - 1)) * W + s] = rowmask[r] ? cconj(grid[(int64_t)r * K + c0 + s]) : C{0, 0};
     }
     __syncthreads();
     fft_smem<R, K, W, NT, true>(buf, tws);
@@ -242,11 +246,13 @@ template <typename R, int K> int fft_fwd_k(ppd_ctx *c, const R *x, cplx_t<R> *gr
     k_rows_fwd<R, K><<<(L + B - 1) / B, NT, shr, s>>>(x, static_cast<cplx_t<R> *>(c->fft_tmp),
                                                      static_cast<const cplx_t<R> *>(c->tw0),
                                                      static_cast<const R *>(c->deap0),
-                                                     static_cast<const R *>(c->deap1), L);
+                                                     static_cast<const R *>(c->deap1), L, c->col_fwd);
     PPD_CHECK(launch_end(c, site, s));
+    if (c->n_fwd_strips == 0) return PPD_OK;
     PPD_CHECK(launch_begin(c, "fft_fwd_cols", s, &site));
-    k_cols_fwd<R, K><<<K / W, NT, shc, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp), grid,
-                                            static_cast<const cplx_t<R> *>(c->tw0), L);
+    k_cols_fwd<R, K><<<c->n_fwd_strips, NT, shc, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp), grid,
+                                                      static_cast<const cplx_t<R> *>(c->tw0), L, c->fwd_strips,
+                                                      c->row_fwd);
     PPD_CHECK(launch_end(c, site, s));
     return PPD_OK;
 }
@@ -262,12 +268,15 @@ template <typename R, int K> int fft_inv_k(ppd_ctx *c, const cplx_t<R> *grid, R 
         attr = true;
     }
     int site;
-    PPD_CHECK(launch_begin(c, "fft_inv_cols", s, &site));
-    k_cols_inv<R, K><<<K / W, NT, shc, s>>>(grid, static_cast<cplx_t<R> *>(c->fft_tmp),
-                                            static_cast<const cplx_t<R> *>(c->tw0), L);
-    PPD_CHECK(launch_end(c, site, s));
+    if (c->n_inv_strips > 0) {
+        PPD_CHECK(launch_begin(c, "fft_inv_cols", s, &site));
+        k_cols_inv<R, K><<<c->n_inv_strips, NT, shc, s>>>(grid, static_cast<cplx_t<R> *>(c->fft_tmp_inv),
+                                                          static_cast<const cplx_t<R> *>(c->tw0), L, c->inv_strips,
+                                                          c->row_inv);
+        PPD_CHECK(launch_end(c, site, s));
+    }
     PPD_CHECK(launch_begin(c, "fft_inv_rows", s, &site));
-    k_rows_inv<R, K><<<(L + B - 1) / B, NT, shr, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp), img,
+    k_rows_inv<R, K><<<(L + B - 1) / B, NT, shr, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp_inv), img,
                                                      static_cast<const cplx_t<R> *>(c->tw0),
                                                      static_cast<const R *>(c->deap0),
                                                      static_cast<const R *>(c->deap1), L);
@@ -309,6 +318,38 @@ template int fft_forward<float>(ppd_ctx *, const float *, float2 *, cudaStream_t
 template int fft_forward<double>(ppd_ctx *, const double *, double2 *, cudaStream_t);
 template int fft_inverse<float>(ppd_ctx *, const float2 *, float *, cudaStream_t);
 template int fft_inverse<double>(ppd_ctx *, const double2 *, double *, cudaStream_t);
+
+// Column strips (W columns each, W as the column passes use) that contain a
+// marked column, and the row / column masks, uploaded for the pruned passes.
+int fft_plan_pruning(ppd_ctx *c, const std::vector<char> &rows_fwd, const std::vector<char> &cols_fwd,
+                     const std::vector<char> &rows_inv, const std::vector<char> &cols_inv) {
+    const int K = c->K0;
+    const int W = c->is_f32 ? cols_per_cta<float>(K) : cols_per_cta<double>(K);
+    std::vector<int32_t> fs, is;
+    for (int s0 = 0; s0 < K; s0 += W) {
+        bool f = false, i = false;
+        for (int j = s0; j < s0 + W; ++j) {
+            f = f || cols_fwd[j];
+            i = i || cols_inv[j];
+        }
+        if (f) fs.push_back(s0);
+        if (i) is.push_back(s0);
+    }
+    std::vector<uint8_t> rf(rows_fwd.begin(), rows_fwd.end()), ri(rows_inv.begin(), rows_inv.end()),
+        cf(cols_fwd.begin(), cols_fwd.end());
+    c->n_fwd_strips = (int)fs.size();
+    c->n_inv_strips = (int)is.size();
+    if (!fs.empty()) PPD_CUDA(cudaMemcpy(c->fwd_strips, fs.data(), fs.size() * 4, cudaMemcpyHostToDevice));
+    if (!is.empty()) PPD_CUDA(cudaMemcpy(c->inv_strips, is.data(), is.size() * 4, cudaMemcpyHostToDevice));
+    PPD_CUDA(cudaMemcpy(c->row_fwd, rf.data(), K, cudaMemcpyHostToDevice));
+    PPD_CUDA(cudaMemcpy(c->row_inv, ri.data(), K, cudaMemcpyHostToDevice));
+    PPD_CUDA(cudaMemcpy(c->col_fwd, cf.data(), K, cudaMemcpyHostToDevice));
+    // the inverse column pass writes only its strips: the rest of its output
+    // stays zero; the forward row pass writes only marked columns
+    PPD_CUDA(cudaMemset(c->fft_tmp_inv, 0, (size_t)c->L0 * K * 2 * c->rsz));
+    PPD_CUDA(cudaMemset(c->fft_tmp, 0, (size_t)c->L0 * K * 2 * c->rsz));
+    return PPD_OK;
+}
 
 // Twiddles exp(-2 pi i m / K), m < K, computed in double on the host.
 int make_twiddles(ppd_ctx *c) {

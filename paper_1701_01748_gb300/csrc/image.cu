@@ -1,6 +1,7 @@
-// Image-side helpers: deterministic FP64 reductions for the statistics and
-// the power iteration, and a scaled copy.  (The primal step of Algorithm 3
-// runs fused into the finest SARA synthesis, csrc/sara.cu.)
+// Image-side kernels: the primal step of Algorithm 3 (projection onto the
+// positive orthant, Section 3.3 Eq. "proj-plus") with the Dirac basis of the
+// prior step fused in, deterministic FP64 reductions for the statistics and
+// the power iteration, and a scaled copy.
 #include "common.cuh"
 
 namespace ppd {
@@ -37,6 +38,37 @@ template <int NTH> __device__ void cta_sum3(double a, double b, double c, double
     }
 }
 
+// Primal step of Algorithm 3 with the Dirac basis of the prior step:
+// u0 <- clip(u0 + xt/3, kappa); ut_all = (u0 + ut)/3;
+// xbar = P_C(x - tau (eta g + zeta ut_all)); xt = 2 xbar - x; x = xbar;
+// FP64 partials (||xbar - x||^2, ||xbar||^2, ||xbar - x0||^2) per CTA.
+template <typename R>
+__global__ void __launch_bounds__(NT) k_primal(R *__restrict__ x, R *__restrict__ xt, const R *__restrict__ g,
+                                               const R *__restrict__ ut, R *__restrict__ u0,
+                                               const R *__restrict__ xtrue, int64_t N, R tau, R eta, R zeta,
+                                               R kappa, double *__restrict__ part) {
+    double sd = 0, sx = 0, se = 0;
+    const R third = R(1.0 / 3.0);
+    for (int64_t e = blockIdx.x * (int64_t)NT + threadIdx.x; e < N; e += (int64_t)gridDim.x * NT) {
+        const R xo = x[e], xte = xt[e];
+        R un = u0[e] + xte * third;
+        un = fmin(fmax(un, -kappa), kappa);
+        u0[e] = un;
+        const R utot = (un + ut[e]) * third;
+        const R xb = fmax(R(0), xo - tau * (eta * g[e] + zeta * utot));
+        xt[e] = R(2) * xb - xo;
+        x[e] = xb;
+        const double dd = (double)xb - (double)xo;
+        sd += dd * dd;
+        sx += (double)xb * (double)xb;
+        if (xtrue) {
+            const double de = (double)xb - (double)xtrue[e];
+            se += de * de;
+        }
+    }
+    cta_sum3<NT>(sd, sx, se, part + 3 * (int64_t)blockIdx.x);
+}
+
 __global__ void k_reduce3(const double *__restrict__ part, int n, double *__restrict__ out) {
     double a = 0, b = 0, c = 0;
     for (int i = threadIdx.x; i < n; i += NT) {
@@ -63,6 +95,16 @@ template <typename R> __global__ void k_scale(const R *__restrict__ in, R *__res
 
 }  // namespace
 
+template <typename R> int primal_step(ppd_ctx *c, cudaStream_t s) {
+    int site;
+    PPD_CHECK(launch_begin(c, "primal", s, &site));
+    k_primal<R><<<c->n_prim_blocks, NT, 0, s>>>(static_cast<R *>(c->x), static_cast<R *>(c->xt),
+                                                static_cast<const R *>(c->g), static_cast<const R *>(c->ut),
+                                                static_cast<R *>(c->u), static_cast<const R *>(c->xtrue), c->N,
+                                                (R)c->tau, (R)c->eta, (R)c->zeta, (R)c->kappa, c->prim_part);
+    return launch_end(c, site, s);
+}
+
 int reduce_primal_stats(ppd_ctx *c, cudaStream_t s) {
     int site;
     PPD_CHECK(launch_begin(c, "stats", s, &site));
@@ -87,6 +129,8 @@ template <typename R> int scale_copy(ppd_ctx *c, const R *in, R *out, int64_t n,
     return launch_end(c, site, s);
 }
 
+template int primal_step<float>(ppd_ctx *, cudaStream_t);
+template int primal_step<double>(ppd_ctx *, cudaStream_t);
 template int sumsq<float>(ppd_ctx *, const float *, int64_t, double *, cudaStream_t);
 template int sumsq<double>(ppd_ctx *, const double *, int64_t, double *, cudaStream_t);
 template int scale_copy<float>(ppd_ctx *, const float *, float *, int64_t, double, cudaStream_t);

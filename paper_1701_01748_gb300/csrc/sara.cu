@@ -36,67 +36,66 @@ constexpr int TSA = 16;                       // analysis: quadrant positions pe
 constexpr int TS = 8;                         // synthesis: quadrant positions per tile side
 constexpr int AEXT = 2 * TSA + MAX_TAPS - 2;  // analysis input tile side (46)
 constexpr int SEXT = TS + MAX_TAPS / 2 - 1;   // synthesis quadrant tile side (15)
+static_assert(NT == 4 * TS * TS, "one synthesis output per thread");
 
 // periodic index for power-of-two n (two's complement makes the mask exact
 // for negative i)
 __device__ __forceinline__ int wrap(int i, int n) { return i & (n - 1); }
 
-// low-pass h and high-pass g[k] = (-1)^k h[F-1-k] of basis b, staged in shared memory
-template <typename R> __device__ __forceinline__ void stage_filters(R *fh, R *fg, int b, int F) {
-    if (threadIdx.x < MAX_TAPS) {
-        const int k = threadIdx.x;
-        fh[k] = k < F ? filt<R>(b, k) : R(0);
-        fg[k] = k < F ? hfilt<R>(b, F, k) : R(0);
+// Filter taps of basis b in registers: h[k] and g[k] = (-1)^k h[F-1-k].
+template <typename R, int F> struct Taps {
+    R h[F], g[F];
+    __device__ __forceinline__ explicit Taps(int b) {
+#pragma unroll
+        for (int k = 0; k < F; ++k) {
+            h[k] = filt<R>(b, k);
+            g[k] = hfilt<R>(b, F, k);
+        }
     }
-}
+};
 
-// One analysis level for all 8 wavelet bases (grid.y = basis), one tile of
-// ts x ts positions of each of the 4 quadrants per CTA.  Rows (axis 1) are
-// filtered into shared memory, then columns (axis 0).
-//   in:   level input, basis b at in + b*in_bstride, row pitch in_pitch
-//   LL:   next level's input (compact, pitch h) unless last
-//   coef: coefficient images (basis b+1 at coef + (b+1)*N, pitch L), written
-//         (mode 0: c = W x / 3) or clip-updated (mode 1: u = clip(u + W x / 3, kappa))
-template <typename R>
-__global__ void __launch_bounds__(NT) k_sara_ana(const R *__restrict__ in, int in_pitch, int64_t in_bstride, int n,
-                                                 int ts, R *__restrict__ ll, int64_t ll_bstride, int last,
-                                                 R *__restrict__ coef, int L, int64_t N, int mode, R kappa) {
-    __shared__ R tin[AEXT * AEXT];
-    __shared__ R rowf[AEXT * 2 * TSA];
-    __shared__ R fh[MAX_TAPS], fg[MAX_TAPS];
-    const int b = blockIdx.y, F = 2 * (b + 1);
-    const int h = n / 2, tpd = h / ts;
-    const int R0 = (blockIdx.x / tpd) * ts, C0 = (blockIdx.x % tpd) * ts;
-    const int ext = 2 * ts + F - 2;
-    const R *src = in + (int64_t)b * in_bstride;
-    stage_filters(fh, fg, b, F);
-    for (int e = threadIdx.x; e < ext * ext; e += NT) {
-        const int i = e / ext, j = e % ext;
-        tin[i * AEXT + j] = src[(int64_t)wrap(2 * R0 + i, n) * in_pitch + wrap(2 * C0 + j, n)];
+// ------------------------------------------------------------- analysis
+// One tile of TSA x TSA positions of each of the 4 quadrants of one level,
+// one basis (filter length F).  Rows (axis 1) are filtered into shared
+// memory, then columns (axis 0).  Levels with h < TSA use one tile and the
+// guards skip the wrapped duplicates.
+template <typename R, int F>
+__device__ __forceinline__ void ana_tile(const R *__restrict__ src, int in_pitch, int n, int R0, int C0,
+                                         R *__restrict__ ll, int last, R *__restrict__ cb, int L, int mode, R kappa,
+                                         int b, R *tin, R *rowf) {
+    constexpr int EXT = 2 * TSA + F - 2;
+    const Taps<R, F> f(b);
+    const int h = n >> 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = warp; i < EXT; i += NT / 32) {
+        const R *row = src + (int64_t)wrap(2 * R0 + i, n) * in_pitch;
+        for (int j = lane; j < EXT; j += 32) tin[i * AEXT + j] = row[wrap(2 * C0 + j, n)];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < ext * 2 * ts; e += NT) {
-        const int i = e / (2 * ts), q = e % (2 * ts);
-        const int cc = q % ts;
-        const bool hi = q >= ts;
-        const R *row = tin + i * AEXT + 2 * cc;
-        const R *f = hi ? fg : fh;
-        R acc = 0;
-        for (int k = 0; k < F; ++k) acc += f[k] * row[k];
-        rowf[i * 2 * TSA + q] = acc;
+    {   // rows: lane = output column q (low half, then high half)
+        const int cc = lane & (TSA - 1);
+        const bool hi = lane >= TSA;
+        for (int i = warp; i < EXT; i += NT / 32) {
+            const R *row = tin + i * AEXT + 2 * cc;
+            R acc = 0;
+#pragma unroll
+            for (int k = 0; k < F; ++k) acc += (hi ? f.g[k] : f.h[k]) * row[k];
+            rowf[i * 2 * TSA + lane] = acc;
+        }
     }
     __syncthreads();
-    R *cb = coef + (int64_t)(b + 1) * N;
-    for (int e = threadIdx.x; e < 4 * ts * ts; e += NT) {
-        const int rq = e / (2 * ts), q = e % (2 * ts);
-        const int rr = rq % ts, cc = q % ts;
-        const bool hi0 = rq >= ts, hi1 = q >= ts;
-        const R *f = hi0 ? fg : fh;
-        const R *col = rowf + 2 * rr * 2 * TSA + q;
+    const int cc = lane & (TSA - 1);
+    const bool hi1 = lane >= TSA;
+    for (int rq = warp; rq < 2 * TSA; rq += NT / 32) {   // columns: warp = output row
+        const int rr = rq & (TSA - 1);
+        const bool hi0 = rq >= TSA;
+        const R *col = rowf + 2 * rr * 2 * TSA + lane;
         R acc = 0;
-        for (int k = 0; k < F; ++k) acc += f[k] * col[k * 2 * TSA];
+#pragma unroll
+        for (int k = 0; k < F; ++k) acc += (hi0 ? f.g[k] : f.h[k]) * col[k * 2 * TSA];
+        if (rr >= h || cc >= h) continue;                // wrapped duplicate (h < TSA)
         if (!hi0 && !hi1 && !last) {
-            ll[(int64_t)b * ll_bstride + (R0 + rr) * h + C0 + cc] = acc;
+            ll[(R0 + rr) * h + C0 + cc] = acc;
         } else {
             R *dst = cb + (int64_t)((hi0 ? h : 0) + R0 + rr) * L + (hi1 ? h : 0) + C0 + cc;
             const R cv = acc * R(1.0 / 3.0);
@@ -110,15 +109,51 @@ __global__ void __launch_bounds__(NT) k_sara_ana(const R *__restrict__ in, int i
     }
 }
 
-// Load the four quadrant tiles of basis b for the synthesis of the tile whose
-// quadrant positions start at (R0, C0): rows/cols R0 - F/2 + 1 ... R0 + ts - 1.
+// One analysis level for all 8 wavelet bases (grid.y = basis).
+//   in:   level input, basis b at in + b*in_bstride, row pitch in_pitch
+//   ll:   next level's input (compact, pitch h) unless last
+//   coef: coefficient images (basis b+1 at coef + (b+1)*N, pitch L), written
+//         (mode 0: c = W x / 3) or clip-updated (mode 1: u = clip(u + W x / 3, kappa))
 template <typename R>
-__device__ __forceinline__ void syn_load(R *qs, const R *cb, const R *sl, int from_coef, int L, int h, int R0,
-                                         int C0, int ext, int F) {
-    for (int e = threadIdx.x; e < 4 * ext * ext; e += NT) {
-        const int qd = e / (ext * ext), r = e % (ext * ext);
-        const int i = r / ext, j = r % ext;
-        const int gi = wrap(R0 - F / 2 + 1 + i, h), gj = wrap(C0 - F / 2 + 1 + j, h);
+__global__ void __launch_bounds__(NT) k_sara_ana(const R *__restrict__ in, int in_pitch, int64_t in_bstride, int n,
+                                                 R *__restrict__ ll, int64_t ll_bstride, int last,
+                                                 R *__restrict__ coef, int L, int64_t N, int mode, R kappa) {
+    __shared__ R tin[AEXT * AEXT];
+    __shared__ R rowf[AEXT * 2 * TSA];
+    const int b = blockIdx.y;
+    const int h = n / 2, tpd = h > TSA ? h / TSA : 1;
+    const int R0 = (blockIdx.x / tpd) * TSA, C0 = (blockIdx.x % tpd) * TSA;
+    const R *src = in + (int64_t)b * in_bstride;
+    R *lb = ll + (int64_t)b * ll_bstride;
+    R *cb = coef + (int64_t)(b + 1) * N;
+    switch (b) {
+        case 0: ana_tile<R, 2>(src, in_pitch, n, R0, C0, lb, last, cb, L, mode, kappa, b, tin, rowf); break;
+        case 1: ana_tile<R, 4>(src, in_pitch, n, R0, C0, lb, last, cb, L, mode, kappa, b, tin, rowf); break;
+        case 2: ana_tile<R, 6>(src, in_pitch, n, R0, C0, lb, last, cb, L, mode, kappa, b, tin, rowf); break;
+        case 3: ana_tile<R, 8>(src, in_pitch, n, R0, C0, lb, last, cb, L, mode, kappa, b, tin, rowf); break;
+        case 4: ana_tile<R, 10>(src, in_pitch, n, R0, C0, lb, last, cb, L, mode, kappa, b, tin, rowf); break;
+        case 5: ana_tile<R, 12>(src, in_pitch, n, R0, C0, lb, last, cb, L, mode, kappa, b, tin, rowf); break;
+        case 6: ana_tile<R, 14>(src, in_pitch, n, R0, C0, lb, last, cb, L, mode, kappa, b, tin, rowf); break;
+        default: ana_tile<R, 16>(src, in_pitch, n, R0, C0, lb, last, cb, L, mode, kappa, b, tin, rowf); break;
+    }
+}
+
+// ------------------------------------------------------------- synthesis
+// Inverse of one level for one basis on one output tile of 2TS x 2TS samples
+// whose quadrant positions start at (R0, C0).  The quadrant tiles cover rows
+// and columns R0 - F/2 + 1 ... R0 + TS - 1 (mod h).  Returns this thread's
+// output (mm = tid / 2TS, nn = tid % 2TS; NT == 4 TS^2).
+template <typename R, int F>
+__device__ __forceinline__ R syn_tile(const R *__restrict__ cb, const R *__restrict__ sl, int from_coef, int L, int n,
+                                      int R0, int C0, int b, R *qs, R *tl, R *th) {
+    constexpr int EXT = TS + F / 2 - 1;
+    const Taps<R, F> f(b);
+    const int h = n >> 1;
+    const int base_r = R0 - F / 2 + 1, base_c = C0 - F / 2 + 1;
+    for (int e = threadIdx.x; e < 4 * EXT * EXT; e += NT) {
+        const int qd = e / (EXT * EXT), r = e % (EXT * EXT);
+        const int i = r / EXT, j = r % EXT;
+        const int gi = wrap(base_r + i, h), gj = wrap(base_c + j, h);
         R v;
         if (qd == 0) v = from_coef ? cb[(int64_t)gi * L + gj] : sl[gi * h + gj];
         else if (qd == 1) v = cb[(int64_t)gi * L + h + gj];
@@ -126,66 +161,70 @@ __device__ __forceinline__ void syn_load(R *qs, const R *cb, const R *sl, int fr
         else v = cb[(int64_t)(h + gi) * L + h + gj];
         qs[qd * SEXT * SEXT + i * SEXT + j] = v;
     }
-}
-
-// Inverse along axis 0: tl/th[mm][j] (mm < 2 ts, j < ext) from the quadrants.
-template <typename R>
-__device__ __forceinline__ void syn_cols(const R *qs, R *tl, R *th, const R *fh, const R *fg, int F, int n, int h,
-                                         int R0, int ts, int ext) {
-    for (int e = threadIdx.x; e < 2 * ts * ext; e += NT) {
-        const int mm = e / ext, j = e % ext;
-        const int m = 2 * R0 + mm;
-        R sl = 0, sh = 0;
-        for (int k = (m & 1); k < F; k += 2) {
-            const int ig = wrap(m - k, n) >> 1;
-            const int il = wrap(ig - (R0 - F / 2 + 1), h);
-            const R a = fh[k], c = fg[k];
-            sl += a * qs[0 * SEXT * SEXT + il * SEXT + j] + c * qs[2 * SEXT * SEXT + il * SEXT + j];
-            sh += a * qs[1 * SEXT * SEXT + il * SEXT + j] + c * qs[3 * SEXT * SEXT + il * SEXT + j];
+    __syncthreads();
+    for (int e = threadIdx.x; e < 2 * TS * EXT; e += NT) {   // inverse along axis 0
+        const int mm = e / EXT, j = e % EXT;
+        const int m = 2 * R0 + mm, par = mm & 1;
+        R sl0 = 0, sh0 = 0;
+#pragma unroll
+        for (int kk = 0; kk < F / 2; ++kk) {
+            const int k = 2 * kk + par;
+            const int il = wrap((wrap(m - k, n) >> 1) - base_r, h);
+            const R a = par ? f.h[2 * kk + 1] : f.h[2 * kk], c = par ? f.g[2 * kk + 1] : f.g[2 * kk];
+            sl0 += a * qs[0 * SEXT * SEXT + il * SEXT + j] + c * qs[2 * SEXT * SEXT + il * SEXT + j];
+            sh0 += a * qs[1 * SEXT * SEXT + il * SEXT + j] + c * qs[3 * SEXT * SEXT + il * SEXT + j];
         }
-        tl[mm * SEXT + j] = sl;
-        th[mm * SEXT + j] = sh;
+        tl[mm * SEXT + j] = sl0;
+        th[mm * SEXT + j] = sh0;
     }
+    __syncthreads();
+    const int mm = threadIdx.x / (2 * TS), nnl = threadIdx.x % (2 * TS);   // inverse along axis 1
+    const int nn = 2 * C0 + nnl, par = nnl & 1;
+    R out = 0;
+#pragma unroll
+    for (int kk = 0; kk < F / 2; ++kk) {
+        const int j = 2 * kk + par;
+        const int jl = wrap((wrap(nn - j, n) >> 1) - base_c, h);
+        const R a = par ? f.h[2 * kk + 1] : f.h[2 * kk], c = par ? f.g[2 * kk + 1] : f.g[2 * kk];
+        out += a * tl[mm * SEXT + jl] + c * th[mm * SEXT + jl];
+    }
+    __syncthreads();   // shared tiles are reused by the caller
+    return out;
 }
 
-// Inverse along axis 1 for output (mm, nn') of the tile.
 template <typename R>
-__device__ __forceinline__ R syn_row(const R *tl, const R *th, const R *fh, const R *fg, int F, int n, int h, int C0,
-                                     int mm, int nnl) {
-    const int nn = 2 * C0 + nnl;
-    R s = 0;
-    for (int j = (nn & 1); j < F; j += 2) {
-        const int jg = wrap(nn - j, n) >> 1;
-        const int jl = wrap(jg - (C0 - F / 2 + 1), h);
-        s += fh[j] * tl[mm * SEXT + jl] + fg[j] * th[mm * SEXT + jl];
+__device__ __forceinline__ R syn_tile_b(int b, const R *cb, const R *sl, int from_coef, int L, int n, int R0, int C0,
+                                        R *qs, R *tl, R *th) {
+    switch (b) {
+        case 0: return syn_tile<R, 2>(cb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 1: return syn_tile<R, 4>(cb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 2: return syn_tile<R, 6>(cb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 3: return syn_tile<R, 8>(cb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 4: return syn_tile<R, 10>(cb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 5: return syn_tile<R, 12>(cb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 6: return syn_tile<R, 14>(cb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        default: return syn_tile<R, 16>(cb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
     }
-    return s;
 }
 
-// One synthesis level l > 0 for all 8 bases: out_b (compact pitch n) = W_b^T of
-// (LL' block, detail quadrants).  LL' comes from the coefficients at the
-// coarsest level (from_coef) or from the coarser level's output sl.
+// One synthesis level l > 0 for all 8 bases (grid.y = basis): out_b (compact
+// pitch n) = W_b^T of (LL' block, detail quadrants).  LL' comes from the
+// coefficients at the coarsest level (from_coef) or from the coarser level's
+// output sll.
 template <typename R>
 __global__ void __launch_bounds__(NT) k_sara_syn(const R *__restrict__ coef, int L, int64_t N, const R *__restrict__ sll,
-                                                 int from_coef, int64_t sll_bstride, int n, int ts, R *__restrict__ out,
+                                                 int from_coef, int64_t sll_bstride, int n, R *__restrict__ out,
                                                  int64_t out_bstride) {
     __shared__ R qs[4 * SEXT * SEXT];
     __shared__ R tl[2 * TS * SEXT], th[2 * TS * SEXT];
-    __shared__ R fh[MAX_TAPS], fg[MAX_TAPS];
-    const int b = blockIdx.y, F = 2 * (b + 1);
-    const int h = n / 2, tpd = h / ts;
-    const int R0 = (blockIdx.x / tpd) * ts, C0 = (blockIdx.x % tpd) * ts;
-    const int ext = ts + F / 2 - 1;
-    stage_filters(fh, fg, b, F);
-    syn_load(qs, coef + (int64_t)(b + 1) * N, sll + (int64_t)b * sll_bstride, from_coef, L, h, R0, C0, ext, F);
-    __syncthreads();
-    syn_cols(qs, tl, th, fh, fg, F, n, h, R0, ts, ext);
-    __syncthreads();
-    R *o = out + (int64_t)b * out_bstride;
-    for (int e = threadIdx.x; e < 4 * ts * ts; e += NT) {
-        const int mm = e / (2 * ts), nnl = e % (2 * ts);
-        o[(int64_t)(2 * R0 + mm) * n + 2 * C0 + nnl] = syn_row(tl, th, fh, fg, F, n, h, C0, mm, nnl);
-    }
+    const int b = blockIdx.y;
+    const int h = n / 2, tpd = h > TS ? h / TS : 1;
+    const int R0 = (blockIdx.x / tpd) * TS, C0 = (blockIdx.x % tpd) * TS;
+    const R v = syn_tile_b<R>(b, coef + (int64_t)(b + 1) * N, sll + (int64_t)b * sll_bstride, from_coef, L, n, R0, C0,
+                              qs, tl, th);
+    const int mm = threadIdx.x / (2 * TS), nnl = threadIdx.x % (2 * TS);
+    if (2 * R0 + mm < n && 2 * C0 + nnl < n)
+        out[(int64_t)b * out_bstride + (int64_t)(2 * R0 + mm) * n + 2 * C0 + nnl] = v;
 }
 
 // Finest synthesis level, all 8 bases summed in order per output sample.
@@ -202,57 +241,42 @@ template <typename R> struct PrimalArgs {
 
 template <typename R>
 __global__ void __launch_bounds__(NT) k_sara_syn0(const R *__restrict__ coef, int L, int64_t N, const R *__restrict__ sll,
-                                                  int from_coef, int64_t sll_bstride, int ts, int mode,
+                                                  int from_coef, int64_t sll_bstride, int mode,
                                                   const R *__restrict__ dirac, R scale, R *__restrict__ out,
                                                   PrimalArgs<R> P) {
     __shared__ R qs[4 * SEXT * SEXT];
     __shared__ R tl[2 * TS * SEXT], th[2 * TS * SEXT];
-    __shared__ R fh[MAX_TAPS], fg[MAX_TAPS];
     __shared__ double red[3][NT / 32];
-    const int n = L, h = n / 2, tpd = h / ts;
-    const int R0 = (blockIdx.x / tpd) * ts, C0 = (blockIdx.x % tpd) * ts;
-    constexpr int PER = (4 * TS * TS + NT - 1) / NT;
-    R acc[PER];
+    const int n = L, h = n / 2, tpd = h > TS ? h / TS : 1;
+    const int R0 = (blockIdx.x / tpd) * TS, C0 = (blockIdx.x % tpd) * TS;
+    R acc = 0;
 #pragma unroll
-    for (int k = 0; k < PER; ++k) acc[k] = 0;
-    for (int b = 0; b < N_WAVELETS; ++b) {
-        const int F = 2 * (b + 1), ext = ts + F / 2 - 1;
-        stage_filters(fh, fg, b, F);
-        syn_load(qs, coef + (int64_t)(b + 1) * N, sll + (int64_t)b * sll_bstride, from_coef, L, h, R0, C0, ext, F);
-        __syncthreads();
-        syn_cols(qs, tl, th, fh, fg, F, n, h, R0, ts, ext);
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int e = threadIdx.x + k * NT;
-            if (e < 4 * ts * ts) acc[k] += syn_row(tl, th, fh, fg, F, n, h, C0, e / (2 * ts), e % (2 * ts));
-        }
-        __syncthreads();
-    }
+    for (int b = 0; b < N_WAVELETS; ++b)
+        acc += syn_tile_b<R>(b, coef + (int64_t)(b + 1) * N, sll + (int64_t)b * sll_bstride, from_coef, L, n, R0, C0,
+                             qs, tl, th);
+    const int mm = threadIdx.x / (2 * TS), nnl = threadIdx.x % (2 * TS);
+    const bool valid = (2 * R0 + mm < n) && (2 * C0 + nnl < n);
+    const int64_t idx = (int64_t)(2 * R0 + mm) * L + 2 * C0 + nnl;
     double sd = 0, sx = 0, se = 0;
-    const R third = R(1.0 / 3.0);
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int e = threadIdx.x + k * NT;
-        if (e >= 4 * ts * ts) continue;
-        const int64_t idx = (int64_t)(2 * R0 + e / (2 * ts)) * L + 2 * C0 + e % (2 * ts);
+    if (valid) {
         if (mode == 0) {
-            out[idx] = scale * ((dirac ? dirac[idx] : R(0)) + acc[k]);
+            out[idx] = scale * ((dirac ? dirac[idx] : R(0)) + acc);
         } else {
+            const R third = R(1.0 / 3.0);
             const R xo = P.x[idx], xte = P.xt[idx];
             R un = P.u0[idx] + xte * third;
             un = fmin(fmax(un, -P.kappa), P.kappa);
             P.u0[idx] = un;
-            const R utot = (un + acc[k]) * third;
+            const R utot = (un + acc) * third;
             const R xb = fmax(R(0), xo - P.tau * (P.eta * P.g[idx] + P.zeta * utot));
             P.xt[idx] = R(2) * xb - xo;
             P.x[idx] = xb;
             const double dd = (double)xb - (double)xo;
-            sd += dd * dd;
-            sx += (double)xb * (double)xb;
+            sd = dd * dd;
+            sx = (double)xb * (double)xb;
             if (P.xtrue) {
                 const double de = (double)xb - (double)P.xtrue[idx];
-                se += de * de;
+                se = de * de;
             }
         }
     }
@@ -289,9 +313,7 @@ template <typename R> __global__ void k_scale_copy(const R *__restrict__ in, R *
 }
 
 inline unsigned nblk(int64_t work) { return (unsigned)std::min<int64_t>((work + NT - 1) / NT, 152 * 8); }
-inline int tile_side(int h) { return h < TS ? h : TS; }
-
-inline int tile_side_ana(int h) { return h < TSA ? h : TSA; }
+inline int tiles(int h, int ts) { return h > ts ? (h / ts) * (h / ts) : 1; }
 
 // Analysis of all levels (tiled).  mode 0 writes c = W x / 3, mode 1
 // clip-updates u.
@@ -302,15 +324,14 @@ template <typename R> int analysis_all(ppd_ctx *c, const R *x, R *coef, int mode
     const int64_t ll_stride = (int64_t)(L / 2) * (L / 2);
     int site;
     for (int l = 0; l < c->levels; ++l) {
-        const int n = L >> l, h = n / 2, ts = tile_side_ana(h);
+        const int n = L >> l, h = n / 2;
         const bool last = (l == c->levels - 1);
         const R *in = l == 0 ? x : ll[(l - 1) & 1];
         const int pitch = l == 0 ? L : n;
         const int64_t bstride = l == 0 ? 0 : ll_stride;
         PPD_CHECK(launch_begin(c, "sara_analysis", s, &site));
-        k_sara_ana<R><<<dim3((h / ts) * (h / ts), N_WAVELETS), NT, 0, s>>>(in, pitch, bstride, n, ts, ll[l & 1],
-                                                                           ll_stride, last, coef, L, N, mode,
-                                                                           (R)c->kappa);
+        k_sara_ana<R><<<dim3(tiles(h, TSA), N_WAVELETS), NT, 0, s>>>(in, pitch, bstride, n, ll[l & 1], ll_stride, last,
+                                                                     coef, L, N, mode, (R)c->kappa);
         PPD_CHECK(launch_end(c, site, s));
     }
     return PPD_OK;
@@ -326,12 +347,11 @@ template <typename R> int synthesis_levels(ppd_ctx *c, const R *coef, const R **
     const R *prev = nullptr;
     int site, k = 0;
     for (int l = c->levels - 1; l >= 1; --l, ++k) {
-        const int n = L >> l, h = n / 2, ts = tile_side(h);
+        const int n = L >> l, h = n / 2;
         const bool coarsest = (l == c->levels - 1);
         PPD_CHECK(launch_begin(c, "sara_synthesis", s, &site));
-        k_sara_syn<R><<<dim3((h / ts) * (h / ts), N_WAVELETS), NT, 0, s>>>(coef, L, N, coarsest ? coef : prev,
-                                                                           coarsest ? 1 : 0, st, n, ts, buf[k & 1],
-                                                                           st);
+        k_sara_syn<R><<<dim3(tiles(h, TS), N_WAVELETS), NT, 0, s>>>(coef, L, N, coarsest ? coef : prev,
+                                                                    coarsest ? 1 : 0, st, n, buf[k & 1], st);
         PPD_CHECK(launch_end(c, site, s));
         prev = buf[k & 1];
     }
@@ -343,7 +363,7 @@ template <typename R>
 int synthesis_final(ppd_ctx *c, const R *coef, const R *ll0, int mode, const R *dirac, R scale, R *out,
                     cudaStream_t s) {
     const int L = c->L0;
-    const int h = L / 2, ts = tile_side(h);
+    const int h = L / 2;
     const int64_t st = (int64_t)(L / 2) * (L / 2);
     PrimalArgs<R> P{};
     if (mode == 1) {
@@ -361,8 +381,8 @@ int synthesis_final(ppd_ctx *c, const R *coef, const R *ll0, int mode, const R *
     const bool from_coef = ll0 == nullptr;   // levels == 1: LL' straight from the coefficients
     int site;
     PPD_CHECK(launch_begin(c, mode == 1 ? "sara_synthesis_primal" : "sara_synthesis", s, &site));
-    k_sara_syn0<R><<<(h / ts) * (h / ts), NT, 0, s>>>(coef, L, c->N, from_coef ? coef : ll0, from_coef ? 1 : 0, st, ts,
-                                                        mode, dirac, scale, out, P);
+    k_sara_syn0<R><<<tiles(h, TS), NT, 0, s>>>(coef, L, c->N, from_coef ? coef : ll0, from_coef ? 1 : 0, st, mode,
+                                                dirac, scale, out, P);
     return launch_end(c, site, s);
 }
 
@@ -486,16 +506,13 @@ template <typename R> int sara_prior_branch(ppd_ctx *c, const R **ll0, cudaStrea
     return synthesis_levels<R>(c, u, ll0, s);
 }
 
-// Level-0 synthesis summed over the bases with the Dirac basis, fused with
-// the primal step (needs g = Phi^dagger v from the data branch).
-template <typename R> int sara_primal(ppd_ctx *c, const R *ll0, cudaStream_t s) {
-    return synthesis_final<R>(c, static_cast<const R *>(c->u), ll0, 1, nullptr, R(1), nullptr, s);
+// Level-0 synthesis summed over the 8 wavelet bases: ut = sum_b W_b^T u_b
+// (the Dirac basis and the 1/3 are applied in the primal step).
+template <typename R> int sara_level0(ppd_ctx *c, const R *ll0, cudaStream_t s) {
+    return synthesis_final<R>(c, static_cast<const R *>(c->u), ll0, 0, nullptr, R(1), static_cast<R *>(c->ut), s);
 }
 
-int sara_primal_blocks(ppd_ctx *c) {
-    const int h = c->L0 / 2, ts = tile_side(h);
-    return (h / ts) * (h / ts);
-}
+
 
 template int psi_analysis<float>(ppd_ctx *, const float *, float *, cudaStream_t);
 template int psi_analysis<double>(ppd_ctx *, const double *, double *, cudaStream_t);
@@ -503,7 +520,7 @@ template int psi_synthesis<float>(ppd_ctx *, const float *, float *, cudaStream_
 template int psi_synthesis<double>(ppd_ctx *, const double *, double *, cudaStream_t);
 template int sara_prior_branch<float>(ppd_ctx *, const float **, cudaStream_t);
 template int sara_prior_branch<double>(ppd_ctx *, const double **, cudaStream_t);
-template int sara_primal<float>(ppd_ctx *, const float *, cudaStream_t);
-template int sara_primal<double>(ppd_ctx *, const double *, cudaStream_t);
+template int sara_level0<float>(ppd_ctx *, const float *, cudaStream_t);
+template int sara_level0<double>(ppd_ctx *, const double *, cudaStream_t);
 
 }  // namespace ppd

@@ -183,7 +183,7 @@ template <typename R> __device__ double block_scale(const VisArgs<R> &A, int blk
 // mode DG_FIRST: z = v/U + Theta G a;  w = z   (Algorithm 2 then starts from P_B(z))
 // partials[chunk] = (||w - y||^2, ||Theta G a - y||^2)
 template <typename R, int T, int MODE>
-__global__ void __launch_bounds__(DG_NT) k_degrid(const __grid_constant__ CUtensorMap tmap, int use_tma,
+__global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1) k_degrid(const __grid_constant__ CUtensorMap tmap, int use_tma,
                                                  const cplx_t<R> *__restrict__ grid, VisArgs<R> A) {
     using C = cplx_t<R>;
     constexpr int E = T + HALO;
