@@ -224,8 +224,8 @@ template <typename R> int iteration_body(ppd_ctx *c, cudaStream_t s, bool first)
     }
     c->part_in = bank[cur];
     c->part_out = bank[0];
-    PPD_CHECK(grid_vis<R>(c, GR_DUAL, nullptr, nullptr, gv, s));
-    PPD_CHECK(fft_inverse<R>(c, gv, static_cast<R *>(c->g), s));
+    PPD_CHECK(grid_vis<R>(c, GR_DUAL, nullptr, nullptr, gv, s, /*combine=*/false));
+    PPD_CHECK(fft_inverse_partials<R>(c, static_cast<R *>(c->g), s));
     if (fork) PPD_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
     PPD_CHECK(primal_step<R>(c, s));
     return PPD_OK;

@@ -177,6 +177,7 @@ int launch_end(ppd_ctx *c, int site, cudaStream_t s);
 // FFT (fft.cu)
 template <typename R> int fft_forward(ppd_ctx *c, const R *x, cplx_t<R> *grid, cudaStream_t s);
 template <typename R> int fft_inverse(ppd_ctx *c, const cplx_t<R> *grid, R *img, cudaStream_t s);
+template <typename R> int fft_inverse_partials(ppd_ctx *c, R *img, cudaStream_t s);
 int make_twiddles(ppd_ctx *c);
 int fft_plan_pruning(ppd_ctx *c, const std::vector<char> &rows_fwd, const std::vector<char> &cols_fwd,
                      const std::vector<char> &rows_inv, const std::vector<char> &cols_inv);
@@ -197,7 +198,7 @@ template <typename R> int subiter(ppd_ctx *c, cudaStream_t s);
 int block_norms(ppd_ctx *c, int which, cudaStream_t s);
 template <typename R>
 int grid_vis(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm_in, cplx_t<R> *grid,
-             cudaStream_t s);
+             cudaStream_t s, bool combine = true);
 
 template <typename R>
 int grid_vis_into(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_t<R> *grid, void *gpart,

@@ -202,6 +202,58 @@ __global__ void __launch_bounds__(NT) k_cols_inv(const cplx_t<R> *__restrict__ g
     }
 }
 
+// inverse column pass reading the gridding's per-chunk partial tiles
+// directly: each cell of the strip is the fixed-order sum that the combine
+// pass would write (its tile's chunks, then the halo rows/columns of the
+// tiles above, left and above-left), so the combined grid never goes to HBM.
+template <typename R, int K, int T>
+__global__ void __launch_bounds__(NT) k_cols_inv_part(const cplx_t<R> *__restrict__ gpart,
+                                                      const int32_t *__restrict__ tile_first,
+                                                      const int32_t *__restrict__ tile_n, cplx_t<R> *__restrict__ tmp,
+                                                      const cplx_t<R> *__restrict__ tw, int L,
+                                                      const int32_t *__restrict__ strips,
+                                                      const uint8_t *__restrict__ rowmask) {
+    using C = cplx_t<R>;
+    constexpr int W = cols_per_cta<R>(K);
+    constexpr int E = T + 8, NTL = K / T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    C *tws = buf + W * K;   // twiddles staged in shared memory
+    for (int e = threadIdx.x; e < K; e += NT) tws[e] = tw[e];
+    const int c0 = strips[blockIdx.x];
+    for (int e = threadIdx.x; e < W * K; e += NT) {
+        const int s = e % W, r = e / W;   // r: stored (centred) row
+        C acc{0, 0};
+        if (rowmask[r]) {
+            const int t0 = r / T, up = (t0 + NTL - 1) % NTL;
+            const int t1 = (c0 + s) / T, left = (t1 + NTL - 1) % NTL;
+            const int lr = r % T, lc = (c0 + s) % T;
+            auto add = [&](int tt0, int tt1, int rr, int cc) {
+                const int t = tt0 * NTL + tt1;
+                const int f = tile_first[t], n = tile_n[t];
+#pragma unroll 4
+                for (int k = 0; k < n; ++k) {
+                    const C g = gpart[(int64_t)(f + k) * E * E + rr * E + cc];
+                    acc.x += g.x;
+                    acc.y += g.y;
+                }
+            };
+            add(t0, t1, lr, lc);
+            if (lr < 8) add(up, t1, lr + T, lc);
+            if (lc < 8) add(t0, left, lr, lc + T);
+            if (lr < 8 && lc < 8) add(up, left, lr + T, lc + T);
+        }
+        buf[((r + K / 2) & (K - 1)) * W + s] = cconj(acc);
+    }
+    __syncthreads();
+    fft_smem<R, K, W, NT, true>(buf, tws);
+    for (int e = threadIdx.x; e < W * L; e += NT) {
+        int s = e % W, n0 = e / W;
+        int pos = (n0 - L / 2 + K) & (K - 1);
+        tmp[(int64_t)n0 * K + c0 + s] = cconj(buf[pos * W + s]);
+    }
+}
+
 // inverse row pass: img[n0][n1] = s0 s1 Re(F^H along axis 1 of tmp)[n0][(n1 - L/2) mod K]
 template <typename R, int K>
 __global__ void __launch_bounds__(NT) k_rows_inv(const cplx_t<R> *__restrict__ tmp, R *__restrict__ img,
@@ -284,7 +336,58 @@ template <typename R, int K> int fft_inv_k(ppd_ctx *c, const cplx_t<R> *grid, R 
     return PPD_OK;
 }
 
+template <typename R, int K, int T> int fft_inv_part_k(ppd_ctx *c, R *img, cudaStream_t s) {
+    constexpr int B = rows_per_cta<R>(K), W = cols_per_cta<R>(K);
+    const int L = c->L0;
+    size_t shr = (size_t)(B + 1) * K * sizeof(cplx_t<R>), shc = (size_t)(W + 1) * K * sizeof(cplx_t<R>);
+    static bool attr = false;
+    if (!attr) {
+        PPD_CUDA(cudaFuncSetAttribute(k_rows_inv<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shr));
+        PPD_CUDA(cudaFuncSetAttribute(k_cols_inv_part<R, K, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)shc));
+        attr = true;
+    }
+    int site;
+    if (c->n_inv_strips > 0) {
+        PPD_CHECK(launch_begin(c, "fft_inv_cols", s, &site));
+        k_cols_inv_part<R, K, T><<<c->n_inv_strips, NT, shc, s>>>(
+            static_cast<const cplx_t<R> *>(c->gpart), c->ch.tile_first, c->ch.tile_n,
+            static_cast<cplx_t<R> *>(c->fft_tmp_inv), static_cast<const cplx_t<R> *>(c->tw0), L, c->inv_strips,
+            c->row_inv);
+        PPD_CHECK(launch_end(c, site, s));
+    }
+    PPD_CHECK(launch_begin(c, "fft_inv_rows", s, &site));
+    k_rows_inv<R, K><<<(L + B - 1) / B, NT, shr, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp_inv), img,
+                                                     static_cast<const cplx_t<R> *>(c->tw0),
+                                                     static_cast<const R *>(c->deap0),
+                                                     static_cast<const R *>(c->deap1), L);
+    return launch_end(c, site, s);
+}
+
+template <typename R, int K> int fft_inv_part_t(ppd_ctx *c, R *img, cudaStream_t s) {
+    return c->T == 16 ? fft_inv_part_k<R, K, 16>(c, img, s) : fft_inv_part_k<R, K, 32>(c, img, s);
+}
+
 }  // namespace
+
+// Z^T F^H of the grid that the gridding's partial tiles sum to (the combine
+// pass fused into the inverse column FFT).
+template <typename R> int fft_inverse_partials(ppd_ctx *c, R *img, cudaStream_t s) {
+    switch (c->K0) {
+        case 32: return fft_inv_part_t<R, 32>(c, img, s);
+        case 64: return fft_inv_part_t<R, 64>(c, img, s);
+        case 128: return fft_inv_part_t<R, 128>(c, img, s);
+        case 256: return fft_inv_part_t<R, 256>(c, img, s);
+        case 512: return fft_inv_part_t<R, 512>(c, img, s);
+        case 1024: return fft_inv_part_t<R, 1024>(c, img, s);
+        case 2048: return fft_inv_part_t<R, 2048>(c, img, s);
+        case 4096: return fft_inv_part_t<R, 4096>(c, img, s);
+        default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
+    }
+}
+
+template int fft_inverse_partials<float>(ppd_ctx *, float *, cudaStream_t);
+template int fft_inverse_partials<double>(ppd_ctx *, double *, cudaStream_t);
 
 template <typename R> int fft_forward(ppd_ctx *c, const R *x, cplx_t<R> *grid, cudaStream_t s) {
     switch (c->K0) {

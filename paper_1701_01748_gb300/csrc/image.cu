@@ -47,7 +47,14 @@ __global__ void __launch_bounds__(NT) k_primal(R *__restrict__ x, R *__restrict_
                                                const R *__restrict__ ut, R *__restrict__ u0,
                                                const R *__restrict__ xtrue, int64_t N, R tau, R eta, R zeta,
                                                R kappa, double *__restrict__ part) {
-    double sd = 0, sx = 0, se = 0;
+    // per-thread sums in the working precision, Kahan-compensated, then a
+    // fixed-order FP64 reduction across the CTA
+    R sd = 0, sx = 0, se = 0, cd = 0, cx = 0, ce = 0;
+    auto kadd = [](R &s, R &c, R v) {
+        const R y = v - c, t = s + y;
+        c = (t - s) - y;
+        s = t;
+    };
     const R third = R(1.0 / 3.0);
     for (int64_t e = blockIdx.x * (int64_t)NT + threadIdx.x; e < N; e += (int64_t)gridDim.x * NT) {
         const R xo = x[e], xte = xt[e];
@@ -58,15 +65,16 @@ __global__ void __launch_bounds__(NT) k_primal(R *__restrict__ x, R *__restrict_
         const R xb = fmax(R(0), xo - tau * (eta * g[e] + zeta * utot));
         xt[e] = R(2) * xb - xo;
         x[e] = xb;
-        const double dd = (double)xb - (double)xo;
-        sd += dd * dd;
-        sx += (double)xb * (double)xb;
+        const R dd = xb - xo;
+        kadd(sd, cd, dd * dd);
+        kadd(sx, cx, xb * xb);
         if (xtrue) {
-            const double de = (double)xb - (double)xtrue[e];
-            se += de * de;
+            const R de = xb - xtrue[e];
+            kadd(se, ce, de * de);
         }
     }
-    cta_sum3<NT>(sd, sx, se, part + 3 * (int64_t)blockIdx.x);
+    cta_sum3<NT>((double)sd - (double)cd, (double)sx - (double)cx, (double)se - (double)ce,
+                 part + 3 * (int64_t)blockIdx.x);
 }
 
 __global__ void k_reduce3(const double *__restrict__ part, int n, double *__restrict__ out) {

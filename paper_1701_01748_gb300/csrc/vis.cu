@@ -75,12 +75,22 @@ __global__ void k_cell_count(const int32_t *__restrict__ cell, const int32_t *__
 // of psi(frac + 3 - j) made on the host); coefficients poly[k*8 + j].
 __device__ __forceinline__ void kb_weights(float frac, float (&w)[KB_J], const float *poly, double, double) {
     const float t = fmaf(2.0f, frac, -1.0f);
+    const float4 *p4 = reinterpret_cast<const float4 *>(poly);   // 16-byte aligned rows of 8 taps
+    float4 lo = p4[2 * KB_DEG], hi = p4[2 * KB_DEG + 1];
+    w[0] = lo.x, w[1] = lo.y, w[2] = lo.z, w[3] = lo.w, w[4] = hi.x, w[5] = hi.y, w[6] = hi.z, w[7] = hi.w;
 #pragma unroll
-    for (int j = 0; j < KB_J; ++j) w[j] = poly[KB_DEG * KB_J + j];
-#pragma unroll
-    for (int k = KB_DEG - 1; k >= 0; --k)
-#pragma unroll
-        for (int j = 0; j < KB_J; ++j) w[j] = fmaf(w[j], t, poly[k * KB_J + j]);
+    for (int k = KB_DEG - 1; k >= 0; --k) {
+        lo = p4[2 * k];
+        hi = p4[2 * k + 1];
+        w[0] = fmaf(w[0], t, lo.x);
+        w[1] = fmaf(w[1], t, lo.y);
+        w[2] = fmaf(w[2], t, lo.z);
+        w[3] = fmaf(w[3], t, lo.w);
+        w[4] = fmaf(w[4], t, hi.x);
+        w[5] = fmaf(w[5], t, hi.y);
+        w[6] = fmaf(w[6], t, hi.z);
+        w[7] = fmaf(w[7], t, hi.w);
+    }
 }
 
 // FP64: the kernel itself, psi(d) = I0(beta sqrt(1 - (d/4)^2)) / I0(beta), d = frac + 3 - j.
@@ -182,97 +192,150 @@ template <typename R> __device__ double block_scale(const VisArgs<R> &A, int blk
 // mode DG_DUAL:  z = v/U + Theta G a;  w = p - mu U (p - z)
 // mode DG_FIRST: z = v/U + Theta G a;  w = z   (Algorithm 2 then starts from P_B(z))
 // partials[chunk] = (||w - y||^2, ||Theta G a - y||^2)
+//
+// Persistent CTAs walk the chunks with a fixed stride.  The (T+8)^2 grid tile
+// of the next chunk is fetched by TMA into the other of two shared buffers
+// while the current chunk is computed (interior tiles; tiles that wrap
+// around the grid edge are loaded with plain loads when they are used).
+// Each thread loads its visibility data before waiting for the tile and one
+// visibility ahead inside the loop.
+template <typename R> struct VisIn {
+    VisRec<R> rc;
+    cplx_t<R> v, y, p;
+    R th;
+};
+
+template <typename R, int MODE>
+__device__ __forceinline__ void load_vis(const VisArgs<R> &A, int gi, VisIn<R> &o) {
+    o.rc = A.rec[gi];
+    o.th = A.theta_v ? A.theta_v[gi] : A.theta_s;
+    if (MODE != DG_OP) {
+        o.v = A.v[gi];
+        o.y = A.y[gi];
+        if (MODE == DG_DUAL) o.p = A.p[gi];
+    }
+}
+
 template <typename R, int T, int MODE>
-__global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1) k_degrid(const __grid_constant__ CUtensorMap tmap, int use_tma,
-                                                 const cplx_t<R> *__restrict__ grid, VisArgs<R> A) {
+__global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
+    k_degrid(const __grid_constant__ CUtensorMap tmap, int use_tma, const cplx_t<R> *__restrict__ grid, VisArgs<R> A,
+             int n_chunks) {
     using C = cplx_t<R>;
     constexpr int E = T + HALO;
+    constexpr int TILE_BYTES = E * E * (int)sizeof(C);
+    constexpr int TILE_STRIDE = (TILE_BYTES + 127) / 128 * 128;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    C *tile = reinterpret_cast<C *>(smem_raw);                       // E*E, 128-B aligned
-    float *poly = reinterpret_cast<float *>(smem_raw + E * E * sizeof(C));
-    __shared__ uint64_t bar;
+    float *poly = reinterpret_cast<float *>(smem_raw + 2 * TILE_STRIDE);
+    __shared__ uint64_t bar[2];
     __shared__ int ok_s;
 
-    const int ch = blockIdx.x;
-    const int start = A.ch_start[ch], count = A.ch_count[ch], tl = A.ch_tile[ch];
-    const int row0 = (tl / A.ntile1) * T, col0 = (tl % A.ntile1) * T;
-    const bool edge = (row0 + E > A.K0) || (col0 + E > A.K1);
-
     for (int i = threadIdx.x; i < (KB_DEG + 1) * KB_J; i += DG_NT) poly[i] = A.kbpoly ? A.kbpoly[i] : 0.f;
-    if (use_tma && !edge) {
-        if (threadIdx.x == 0) {
-            ok_s = 1;
-            mbar_init(&bar, 1);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            mbar_expect_tx(&bar, (uint32_t)(E * E * sizeof(C)));
-            tma_load_2d(tile, &tmap, 2 * col0, row0, &bar);
-        }
-        if (!mbar_wait(&bar, 0, SPIN_LIMIT)) {
-            atomicOr(A.err, ERR_TMA_TIMEOUT);
-            ok_s = 0;
-            mbar_wait(&bar, 0, SPIN_LIMIT);   // second bounded wait for the copy in flight
-        }
-        __syncthreads();
-        if (!ok_s) return;
-    } else {
-        for (int e = threadIdx.x; e < E * E; e += DG_NT) {
-            const int r = e / E, cc = e % E;
-            tile[e] = grid[(int64_t)((row0 + r) % A.K0) * A.K1 + (col0 + cc) % A.K1];
-        }
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        ok_s = 1;
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
     }
-
-    double mu = 0;
-    if (MODE != DG_OP) mu = A.mu[A.ch_block[ch]];
-    Acc<R> s_w, s_r;
-    for (int i = threadIdx.x; i < count; i += DG_NT) {
-        const int gi = start + i;
-        const VisRec<R> rc = A.rec[gi];
-        const int lb0 = (rc.packed & 0xffff) - row0, lb1 = ((rc.packed >> 16) & 0xffff) - col0;
-        R w0[KB_J], w1[KB_J];
-        kb_weights(rc.f0, w0, poly, A.beta, A.inv_i0b);
-        kb_weights(rc.f1, w1, poly, A.beta, A.inv_i0b);
-        C q{0, 0};
-#pragma unroll
-        for (int a = 0; a < KB_J; ++a) {
-            const C *row = tile + (lb0 + a) * E + lb1;
-            C r{0, 0};
-#pragma unroll
-            for (int b = 0; b < KB_J; ++b) {
-                const C g = row[b];
-                r.x += w1[b] * g.x;
-                r.y += w1[b] * g.y;
-            }
-            q.x += w0[a] * r.x;
-            q.y += w0[a] * r.y;
+    __syncthreads();
+    auto origin = [&](int ch, int &row0, int &col0) {
+        const int tl = A.ch_tile[ch];
+        row0 = (tl / A.ntile1) * T;
+        col0 = (tl % A.ntile1) * T;
+    };
+    auto interior = [&](int row0, int col0) { return use_tma && row0 + E <= A.K0 && col0 + E <= A.K1; };
+    auto issue = [&](int ch, int buf) {   // thread 0 only
+        int r0, c0;
+        origin(ch, r0, c0);
+        if (interior(r0, c0)) {
+            mbar_expect_tx(&bar[buf], (uint32_t)TILE_BYTES);
+            tma_load_2d(smem_raw + buf * TILE_STRIDE, &tmap, 2 * c0, r0, &bar[buf]);
         }
-        const R th = A.theta_v ? A.theta_v[gi] : A.theta_s;
-        const C phix{th * q.x, th * q.y};
-        if (MODE == DG_OP) {
-            A.op_out[A.perm ? A.perm[gi] : gi] = phix;
+    };
+    uint32_t ph = 0u;   // bit b: parity of the next completion of bar[b]
+    if (threadIdx.x == 0 && (int)blockIdx.x < n_chunks) issue(blockIdx.x, 0);
+    int it = 0;
+    for (int ch = blockIdx.x; ch < n_chunks; ch += gridDim.x, ++it) {
+        const int buf = it & 1;
+        C *tile = reinterpret_cast<C *>(smem_raw + buf * TILE_STRIDE);
+        const int nxt = ch + gridDim.x;
+        if (threadIdx.x == 0 && nxt < n_chunks) issue(nxt, buf ^ 1);
+        const int start = A.ch_start[ch], count = A.ch_count[ch];
+        int row0, col0;
+        origin(ch, row0, col0);
+        VisIn<R> cur;
+        if ((int)threadIdx.x < count) load_vis<R, MODE>(A, start + threadIdx.x, cur);
+        if (interior(row0, col0)) {
+            if (!mbar_wait(&bar[buf], (ph >> buf) & 1u, SPIN_LIMIT)) {
+                atomicOr(A.err, ERR_TMA_TIMEOUT);
+                ok_s = 0;
+                mbar_wait(&bar[buf], (ph >> buf) & 1u, SPIN_LIMIT);   // second bounded wait for the copy in flight
+            }
+            ph ^= 1u << buf;
+            __syncthreads();
+            if (!ok_s) {
+                // the next chunk's copy may be in flight: wait for it (bounded) before leaving
+                if (nxt < n_chunks) {
+                    int r1, c1;
+                    origin(nxt, r1, c1);
+                    if (interior(r1, c1)) mbar_wait(&bar[buf ^ 1], (ph >> (buf ^ 1)) & 1u, SPIN_LIMIT);
+                }
+                break;
+            }
         } else {
-            const C vv = A.v[gi], yy = A.y[gi];
-            const R invU = R(1) / rc.U;
-            const C zz{vv.x * invU + phix.x, vv.y * invU + phix.y};
-            A.z[gi] = zz;
-            C ww;
-            if (MODE == DG_FIRST) {
-                ww = zz;
-            } else {
-                const C pp = A.p[gi];
-                const R mu_u = (R)mu * rc.U;
-                ww = C{pp.x - mu_u * (pp.x - zz.x), pp.y - mu_u * (pp.y - zz.y)};
+            for (int e = threadIdx.x; e < E * E; e += DG_NT) {
+                const int r = e / E, cc = e % E;
+                tile[e] = grid[(int64_t)((row0 + r) % A.K0) * A.K1 + (col0 + cc) % A.K1];
             }
-            A.w[gi] = ww;
-            const R dx = ww.x - yy.x, dy = ww.y - yy.y;
-            s_w.add(dx * dx + dy * dy);
-            const R ex = phix.x - yy.x, ey = phix.y - yy.y;
-            s_r.add(ex * ex + ey * ey);
+            __syncthreads();
         }
+        const double mu = (MODE != DG_OP) ? A.mu[A.ch_block[ch]] : 0.0;
+        Acc<R> s_w, s_r;
+        for (int i = threadIdx.x; i < count; i += DG_NT) {
+            const int gi = start + i;
+            VisIn<R> nx;
+            if (i + DG_NT < count) load_vis<R, MODE>(A, gi + DG_NT, nx);
+            const int lb0 = (cur.rc.packed & 0xffff) - row0, lb1 = ((cur.rc.packed >> 16) & 0xffff) - col0;
+            R w0[KB_J], w1[KB_J];
+            kb_weights(cur.rc.f0, w0, poly, A.beta, A.inv_i0b);
+            kb_weights(cur.rc.f1, w1, poly, A.beta, A.inv_i0b);
+            C q{0, 0};
+#pragma unroll
+            for (int a = 0; a < KB_J; ++a) {
+                const C *row = tile + (lb0 + a) * E + lb1;
+                C r{0, 0};
+#pragma unroll
+                for (int b = 0; b < KB_J; ++b) {
+                    const C g = row[b];
+                    r.x += w1[b] * g.x;
+                    r.y += w1[b] * g.y;
+                }
+                q.x += w0[a] * r.x;
+                q.y += w0[a] * r.y;
+            }
+            const C phix{cur.th * q.x, cur.th * q.y};
+            if (MODE == DG_OP) {
+                A.op_out[A.perm ? A.perm[gi] : gi] = phix;
+            } else {
+                const R invU = R(1) / cur.rc.U;
+                const C zz{cur.v.x * invU + phix.x, cur.v.y * invU + phix.y};
+                A.z[gi] = zz;
+                C ww;
+                if (MODE == DG_FIRST) {
+                    ww = zz;
+                } else {
+                    const R mu_u = (R)mu * cur.rc.U;
+                    ww = C{cur.p.x - mu_u * (cur.p.x - zz.x), cur.p.y - mu_u * (cur.p.y - zz.y)};
+                }
+                A.w[gi] = ww;
+                const R dx = ww.x - cur.y.x, dy = ww.y - cur.y.y;
+                s_w.add(dx * dx + dy * dy);
+                const R ex = phix.x - cur.y.x, ey = phix.y - cur.y.y;
+                s_r.add(ex * ex + ey * ey);
+            }
+            cur = nx;
+        }
+        if (MODE != DG_OP) cta_sum2<DG_NT>(s_w.get(), s_r.get(), A.partials + NPART * (int64_t)ch);
+        __syncthreads();   // the tile buffer is refilled two chunks later
     }
-    if (MODE != DG_OP) cta_sum2<DG_NT>(s_w.get(), s_r.get(), A.partials + NPART * (int64_t)ch);
 }
 
 // ----------------------------------------------------------------- sub-iteration
@@ -531,7 +594,8 @@ int degrid_t(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const 
     A.op_out = out;
     A.perm = perm;
     constexpr int E = T + HALO;
-    const size_t sh = E * E * sizeof(cplx_t<R>) + (KB_DEG + 1) * KB_J * sizeof(float);
+    const size_t tile_stride = ((size_t)E * E * sizeof(cplx_t<R>) + 127) / 128 * 128;
+    const size_t sh = 2 * tile_stride + (KB_DEG + 1) * KB_J * sizeof(float);
     static bool attr = false;
     if (!attr) {
         PPD_CUDA(cudaFuncSetAttribute(k_degrid<R, T, DG_OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
@@ -541,17 +605,26 @@ int degrid_t(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const 
     }
     const int use_tma = (c->tma_ok && grid == c->grid_a) ? 1 : 0;
     if (c->ch.n == 0) return PPD_OK;
+    static int per_sm = 0;
+    if (!per_sm) {
+        PPD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_degrid<R, T, DG_DUAL>, DG_NT, sh));
+        if (per_sm < 1) per_sm = 1;
+    }
+    int sms = 0;
+    PPD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    const int nch = (int)c->ch.n;
+    const unsigned nb = (unsigned)std::min<int64_t>(nch, (int64_t)sms * per_sm);
     int site;
     PPD_CHECK(launch_begin(c, mode == DG_OP ? "degrid_op" : "degrid_dual", s, &site));
-    const unsigned nb = (unsigned)c->ch.n;
-    if (mode == DG_OP) k_degrid<R, T, DG_OP><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A);
-    else if (mode == DG_DUAL) k_degrid<R, T, DG_DUAL><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A);
-    else k_degrid<R, T, DG_FIRST><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A);
+    if (mode == DG_OP) k_degrid<R, T, DG_OP><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A, nch);
+    else if (mode == DG_DUAL) k_degrid<R, T, DG_DUAL><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A, nch);
+    else k_degrid<R, T, DG_FIRST><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A, nch);
     return launch_end(c, site, s);
 }
 
 template <typename R, int T>
-int grid_t(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_t<R> *grid, cudaStream_t s) {
+int grid_t(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_t<R> *grid, cudaStream_t s,
+           bool combine) {
     VisArgs<R> A = make_args<R>(c);
     A.op_in = in;
     A.perm = perm;
@@ -574,7 +647,7 @@ int grid_t(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_
         else k_grid<R, T, GR_DUAL><<<nb, NT, sh, s>>>(A, gp);
         PPD_CHECK(launch_end(c, site, s));
     }
-    if (c->ch.n_active == 0) return PPD_OK;
+    if (c->ch.n_active == 0 || !combine) return PPD_OK;
     PPD_CHECK(launch_begin(c, "grid_combine", s, &site));
     k_combine<R, T><<<(unsigned)c->ch.n_active * 4, 256, 0, s>>>(gp, c->ch.tile_first, c->ch.tile_n, c->ch.active,
                                                             c->K1, c->K0 / T, c->K1 / T, grid);
@@ -647,8 +720,10 @@ int degrid(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const in
 }
 
 template <typename R>
-int grid_vis(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_t<R> *grid, cudaStream_t s) {
-    return c->T == 16 ? grid_t<R, 16>(c, mode, in, perm, grid, s) : grid_t<R, 32>(c, mode, in, perm, grid, s);
+int grid_vis(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_t<R> *grid, cudaStream_t s,
+             bool combine) {
+    return c->T == 16 ? grid_t<R, 16>(c, mode, in, perm, grid, s, combine)
+                      : grid_t<R, 32>(c, mode, in, perm, grid, s, combine);
 }
 
 template <typename R> int subiter(ppd_ctx *c, cudaStream_t s) {
@@ -685,8 +760,8 @@ template int grid_vis_into<double>(ppd_ctx *, int, const double2 *, const int64_
                                    cudaStream_t);
 template int degrid<float>(ppd_ctx *, int, const float2 *, float2 *, const int64_t *, cudaStream_t);
 template int degrid<double>(ppd_ctx *, int, const double2 *, double2 *, const int64_t *, cudaStream_t);
-template int grid_vis<float>(ppd_ctx *, int, const float2 *, const int64_t *, float2 *, cudaStream_t);
-template int grid_vis<double>(ppd_ctx *, int, const double2 *, const int64_t *, double2 *, cudaStream_t);
+template int grid_vis<float>(ppd_ctx *, int, const float2 *, const int64_t *, float2 *, cudaStream_t, bool);
+template int grid_vis<double>(ppd_ctx *, int, const double2 *, const int64_t *, double2 *, cudaStream_t, bool);
 template int subiter<float>(ppd_ctx *, cudaStream_t);
 template int subiter<double>(ppd_ctx *, cudaStream_t);
 
