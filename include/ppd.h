@@ -110,6 +110,7 @@ typedef struct {
     int32_t  power_iters_done;
     int32_t  K0, K1;            /* oversampled grid */
     int32_t  tile;              /* gridding tile side */
+    int32_t  chunk;             /* max visibilities per work item */
     int64_t  n_chunks;          /* gridding work items */
     int64_t  M;                 /* visibilities */
     double   convergence_lhs;   /* tau*zeta*||Psi||^2 + tau*eta*||U^{1/2}Phi||^2 (Eq. "convergence-req-explicit-pd"), < 1 */
@@ -149,7 +150,7 @@ PPD_API int ppd_set_visibilities(ppd_ctx *ctx, int64_t M, const double *uv, cons
  *          precond = 1, all 1 when precond = 0)
  *   eps    n_blocks doubles > 0, l2 bounds on the whitened residual of each
  *          block (NULL => sqrt(M_j + 2 sqrt(M_j)), two chi^2 standard
- *          deviations above its mean)
+ *          deviations above its mean); ignored for blocks with no visibility
  * Then resolves eta (power iteration when config.eta = 0), mu_j =
  * 1/max(U_j)^2 (Algorithm 2) and resets the state to zero.
  * Errors: NOT_READY, INVALID_ARG, NONFINITE, OOM, CUDA. */
@@ -183,6 +184,30 @@ PPD_API int ppd_get_params(ppd_ctx *ctx, ppd_params *out);
  *            (floor(kappa + 0.5) mod K per axis) */
 PPD_API int ppd_get_bins(ppd_ctx *ctx, int64_t *perm, int32_t *base0, int32_t *base1, int32_t *count);
 
+/* Autotuner for the gridding work decomposition: for each tile side
+ * T in {16, 32} and work-item size C in {512, 1024, 2048} (visibilities per
+ * CTA, i.e. C/8 per warp), rebuilds the visibility order from the inputs of
+ * the last ppd_set_visibilities / ppd_set_weights calls, times `iters` PPD
+ * iterations with CUDA events and keeps the fastest; eta is kept, the solver
+ * state is reset to zero.  The chosen values are returned (either pointer may
+ * be NULL) and reported by ppd_get_params.
+ * Errors: NOT_READY, INVALID_ARG, OOM, CUDA. */
+PPD_API int ppd_autotune(ppd_ctx *ctx, int32_t iters, int32_t *tile_out, int32_t *chunk_out);
+
+/* Solver state for checkpoint / resume and warm starts (Algorithm 3 takes
+ * and returns x, xt, u_i, v_j; Algorithm 1 restarts Algorithm 3 from them):
+ * a self-describing blob holding x, xt, the 9 dual images u_i, the data
+ * duals v, the warm start p of Algorithm 2 (processing order) and the
+ * iteration count, tagged with the precision, sizes and a fingerprint of the
+ * visibility order.  ppd_get_state with blob = NULL sets *bytes to the size
+ * needed; otherwise *bytes must be at least that size and the blob is
+ * written (synchronises).  ppd_set_state accepts only a blob made by a
+ * context with the same precision, sizes and visibility order; resuming from
+ * it reproduces an uninterrupted run bit for bit.
+ * Errors: NOT_READY, INVALID_ARG (size, tag or fingerprint mismatch), CUDA. */
+PPD_API int ppd_get_state(ppd_ctx *ctx, void *blob, int64_t *bytes);
+PPD_API int ppd_set_state(ppd_ctx *ctx, const void *blob, int64_t bytes);
+
 /* Phi x = Theta G F Z x (Section 2): x_dev n0*n1 reals -> y_dev M complex
  * (caller order, whitened by theta).  Enqueued on stream.  Uses the
  * context's internal grid, so it must not overlap ppd_iterate on the same
@@ -192,6 +217,21 @@ PPD_API int ppd_op_forward(ppd_ctx *ctx, const void *x_dev, void *y_dev, void *s
 /* Phi^dagger y = Re(Z^T F^H G^H Theta^H y): y_dev M complex (caller order)
  * -> x_dev n0*n1 reals.  Same rules as ppd_op_forward. */
 PPD_API int ppd_op_adjoint(ppd_ctx *ctx, const void *y_dev, void *x_dev, void *stream);
+
+/* Batched independent problems (the paper's problems are independent once
+ * their data are fixed; the batch fills the GPU with several of them).  A
+ * group holds n FP32 contexts that have weights set; ppd_group_iterate
+ * advances every one of them by n_iters iterations of Algorithm 3, each
+ * iteration of the whole group being one launch of a CUDA graph captured from
+ * all the contexts' kernels on their own streams.  Results are identical to
+ * iterating each context alone.  The contexts must not be used elsewhere
+ * while the group runs; destroy the group before its contexts.
+ * Errors: INVALID_ARG (NULL, n < 1, FP64 context, per-kernel timing on),
+ * NOT_READY (a context without weights), CUDA. */
+typedef struct ppd_group ppd_group;
+PPD_API int ppd_group_create(ppd_group **out, ppd_ctx *const *ctxs, int32_t n);
+PPD_API int ppd_group_iterate(ppd_group *g, int32_t n_iters);
+PPD_API void ppd_group_destroy(ppd_group *g);
 
 /* Phi^dagger without allocating: the same result as ppd_op_adjoint (same
  * arguments, layouts and stream rules), for callers that cannot let the

@@ -681,6 +681,15 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
     }
     c->block_count_h.assign(c->d, 0);
     for (int64_t i = 0; i < M; ++i) c->block_count_h[block_id[i]]++;
+    if (c->in_uv.data() != uv) {   // (the autotuner passes the stored copies back in)
+        c->in_uv.assign(uv, uv + 2 * M);
+        c->in_y.assign(y, y + 2 * M);
+        c->in_block.assign(block_id, block_id + M);
+    }
+    if ((st = make_tmap(c))) {   // the TMA box depends on the tile side
+        free_vis(c);
+        return st;
+    }
     c->have_vis = true;
     c->have_weights = false;
     return PPD_OK;
@@ -690,6 +699,18 @@ int ppd_set_weights(ppd_ctx *c, const double *theta, const double *U, const doub
     if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_set_weights: NULL context");
     if (!c->have_vis) return fail(PPD_ERR_NOT_READY, "ppd_set_weights: call ppd_set_visibilities first");
     const int64_t M = c->M;
+    if (c->in_theta.data() != theta || !theta) {
+        c->has_theta = theta != nullptr;
+        if (theta) c->in_theta.assign(theta, theta + M);
+    }
+    if (c->in_U.data() != U || !U) {
+        c->has_U = U != nullptr;
+        if (U) c->in_U.assign(U, U + M);
+    }
+    if (c->in_eps.data() != eps || !eps) {
+        c->has_eps = eps != nullptr;
+        if (eps) c->in_eps.assign(eps, eps + c->d);
+    }
     std::vector<double> th(M), uu(M);
     bool uniform = true;
     for (int64_t i = 0; i < M; ++i) {
@@ -705,6 +726,10 @@ int ppd_set_weights(ppd_ctx *c, const double *theta, const double *U, const doub
     for (int j = 0; j < c->d; ++j) {
         const double Mj = (double)c->block_count_h[j];
         ep[j] = eps ? eps[j] : std::sqrt(Mj + 2.0 * std::sqrt(Mj));
+        if (Mj == 0) {   // an empty block has no constraint; its bound is never used
+            ep[j] = 1.0;
+            continue;
+        }
         if (!(ep[j] > 0) || !std::isfinite(ep[j]))
             return fail(PPD_ERR_INVALID_ARG, "ppd_set_weights: eps must be finite and > 0");
     }
@@ -855,6 +880,7 @@ int ppd_get_params(ppd_ctx *c, ppd_params *o) {
     o->K0 = c->K0;
     o->K1 = c->K1;
     o->tile = c->T;
+    o->chunk = c->C;
     o->n_chunks = c->ch.n;
     o->M = c->M;
     const double phi2 = c->op_norm_sq > 0 ? c->op_norm_sq : 1.0 / c->eta;
@@ -912,6 +938,263 @@ int ppd_psi_synthesis(ppd_ctx *c, const void *c_dev, void *x_dev, void *stream) 
     cudaStream_t s = pick(c, stream);
     if (c->is_f32) return psi_synthesis<float>(c, static_cast<const float *>(c_dev), static_cast<float *>(x_dev), s);
     return psi_synthesis<double>(c, static_cast<const double *>(c_dev), static_cast<double *>(x_dev), s);
+}
+
+int ppd_autotune(ppd_ctx *c, int32_t iters, int32_t *tile_out, int32_t *chunk_out) {
+    if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_autotune: NULL context");
+    if (!c->have_weights) return fail(PPD_ERR_NOT_READY, "ppd_autotune: call ppd_set_weights first");
+    if (iters < 1) return fail(PPD_ERR_INVALID_ARG, "ppd_autotune: iters < 1");
+    const double eta_cfg = c->cfg.eta;
+    c->cfg.eta = c->eta;   // keep the resolved eta: no power iteration per candidate
+    const std::vector<double> uv = c->in_uv, y = c->in_y, th = c->in_theta, U = c->in_U, ep = c->in_eps;
+    const std::vector<int32_t> blk = c->in_block;
+    const bool hth = c->has_theta, hU = c->has_U, hep = c->has_eps;
+    const bool timing = c->timing;
+    c->timing = false;
+    auto rebuild = [&](int T, int C) {
+        c->T = T;
+        c->C = C;
+        int st = ppd_set_visibilities(c, c->M, uv.data(), y.data(), blk.data());
+        if (st == PPD_OK) st = ppd_set_weights(c, hth ? th.data() : nullptr, hU ? U.data() : nullptr,
+                                               hep ? ep.data() : nullptr);
+        return st;
+    };
+    cudaEvent_t e0, e1;
+    PPD_CUDA(cudaEventCreate(&e0));
+    PPD_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bt = c->T, bc = c->C, st = PPD_OK;
+    for (int T : {16, 32}) {
+        if (c->K0 % T || c->K0 < 2 * T) continue;
+        for (int C : {512, 1024, 2048}) {
+            if ((st = rebuild(T, C))) break;
+            if ((st = ppd_iterate(c, 3, nullptr))) break;
+            cudaEventRecord(e0, c->stream);
+            if ((st = ppd_iterate(c, iters, nullptr))) break;
+            cudaEventRecord(e1, c->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bt = T;
+                bc = C;
+            }
+        }
+        if (st) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == PPD_OK) st = rebuild(bt, bc);
+    c->cfg.eta = eta_cfg;
+    c->timing = timing;
+    if (st) return st;
+    if (tile_out) *tile_out = bt;
+    if (chunk_out) *chunk_out = bc;
+    return PPD_OK;
+}
+
+struct ppd_group {
+    std::vector<ppd_ctx *> ctxs;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> joins;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int64_t> kernels;   // kernels each context contributes to one replay
+};
+
+void ppd_group_destroy(ppd_group *g) {
+    if (!g) return;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    for (cudaEvent_t e : g->joins) cudaEventDestroy(e);
+    if (g->fork) cudaEventDestroy(g->fork);
+    if (g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+}
+
+int ppd_group_create(ppd_group **out, ppd_ctx *const *ctxs, int32_t n) {
+    if (!out || !ctxs || n < 1) return fail(PPD_ERR_INVALID_ARG, "ppd_group_create: invalid argument");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return fail(PPD_ERR_INVALID_ARG, "ppd_group_create: NULL context");
+        if (!ctxs[i]->is_f32) return fail(PPD_ERR_INVALID_ARG, "ppd_group_create: groups hold FP32 contexts");
+        if (ctxs[i]->timing) return fail(PPD_ERR_INVALID_ARG, "ppd_group_create: per-kernel timing must be off");
+        if (!ctxs[i]->have_weights) return fail(PPD_ERR_NOT_READY, "ppd_group_create: context without weights");
+    }
+    ppd_group *g = new (std::nothrow) ppd_group();
+    if (!g) return fail(PPD_ERR_OOM, "ppd_group_create: host allocation");
+    g->ctxs.assign(ctxs, ctxs + n);
+    g->joins.resize(n, nullptr);
+    bool ok = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < n; ++i)
+        ok = cudaEventCreateWithFlags(&g->joins[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        ppd_group_destroy(g);
+        return fail(PPD_ERR_CUDA, "ppd_group_create: stream/event creation");
+    }
+    *out = g;
+    return PPD_OK;
+}
+
+int ppd_group_iterate(ppd_group *g, int32_t n_iters) {
+    if (!g) return fail(PPD_ERR_INVALID_ARG, "ppd_group_iterate: NULL group");
+    if (n_iters < 0) return fail(PPD_ERR_INVALID_ARG, "ppd_group_iterate: n_iters < 0");
+    if (n_iters == 0) return PPD_OK;
+    // a context's first iteration (Algorithm 2 starts from P_B(z)) differs
+    // from the captured one: if any context needs it, every context runs one
+    // iteration eagerly and the graph covers the remaining n_iters - 1
+    bool any_first = false;
+    for (ppd_ctx *c : g->ctxs) any_first = any_first || !c->p_valid;
+    if (any_first) {
+        for (ppd_ctx *c : g->ctxs) {
+            PPD_CHECK(iteration_body<float>(c, c->stream, !c->p_valid));
+            c->p_valid = true;
+            c->iters++;
+        }
+        if (--n_iters == 0) return PPD_OK;
+    }
+    if (!g->exec) {
+        std::vector<int64_t> before;
+        for (ppd_ctx *c : g->ctxs) before.push_back(c->launches);
+        PPD_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+        int st = PPD_OK;
+        cudaError_t e = cudaEventRecord(g->fork, g->stream);
+        for (size_t i = 0; st == PPD_OK && e == cudaSuccess && i < g->ctxs.size(); ++i) {
+            ppd_ctx *c = g->ctxs[i];
+            e = cudaStreamWaitEvent(c->stream, g->fork, 0);
+            if (e == cudaSuccess) st = iteration_body<float>(c, c->stream, false);
+            if (st == PPD_OK && e == cudaSuccess) e = cudaEventRecord(g->joins[i], c->stream);
+            if (st == PPD_OK && e == cudaSuccess) e = cudaStreamWaitEvent(g->stream, g->joins[i], 0);
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(g->stream, &graph);
+        g->kernels.clear();
+        for (size_t i = 0; i < g->ctxs.size(); ++i) {   // captured, not yet run
+            g->kernels.push_back(g->ctxs[i]->launches - before[i]);
+            g->ctxs[i]->launches = before[i];
+        }
+        if (st != PPD_OK || e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            if (st != PPD_OK) return st;
+            return fail(PPD_ERR_CUDA, std::string("ppd_group_iterate: capture: ") +
+                                          cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        g->graph = graph;
+        PPD_CUDA(cudaGraphInstantiate(&g->exec, graph, 0));
+    }
+    // order the group's stream after everything already queued on the contexts' streams
+    for (size_t i = 0; i < g->ctxs.size(); ++i) {
+        PPD_CUDA(cudaEventRecord(g->joins[i], g->ctxs[i]->stream));
+        PPD_CUDA(cudaStreamWaitEvent(g->stream, g->joins[i], 0));
+    }
+    for (int it = 0; it < n_iters; ++it) {
+        PPD_CUDA(cudaGraphLaunch(g->exec, g->stream));
+        for (size_t i = 0; i < g->ctxs.size(); ++i) {
+            g->ctxs[i]->iters++;
+            g->ctxs[i]->launches += g->kernels[i];
+        }
+    }
+    // keep each context's own stream ordered after the group's work
+    PPD_CUDA(cudaEventRecord(g->fork, g->stream));
+    for (ppd_ctx *c : g->ctxs) PPD_CUDA(cudaStreamWaitEvent(c->stream, g->fork, 0));
+    return PPD_OK;
+}
+
+namespace {
+struct StateHeader {
+    char magic[8];
+    int32_t version, precision, n0, n1;
+    int64_t M;
+    int32_t d, iters, p_valid, pad;
+    uint64_t order_hash;
+};
+
+uint64_t order_fingerprint(const ppd_ctx *c) {   // FNV-1a over the processing order
+    uint64_t h = 1469598103934665603ull;
+    for (int64_t v : c->perm_h) {
+        for (int k = 0; k < 8; ++k) {
+            h ^= (uint64_t)((v >> (8 * k)) & 0xff);
+            h *= 1099511628211ull;
+        }
+    }
+    return h;
+}
+
+int64_t state_bytes(const ppd_ctx *c) {
+    return (int64_t)sizeof(StateHeader) + (int64_t)c->rsz * (11 * c->N + 4 * c->M);
+}
+}  // namespace
+
+int ppd_get_state(ppd_ctx *c, void *blob, int64_t *bytes) {
+    if (!c || !bytes) return fail(PPD_ERR_INVALID_ARG, "ppd_get_state: NULL argument");
+    if (!c->have_weights) return fail(PPD_ERR_NOT_READY, "ppd_get_state: call ppd_set_weights first");
+    const int64_t need = state_bytes(c);
+    if (!blob) {
+        *bytes = need;
+        return PPD_OK;
+    }
+    if (*bytes < need) return fail(PPD_ERR_INVALID_ARG, "ppd_get_state: buffer too small");
+    StateHeader h{};
+    std::memcpy(h.magic, "PPDSTATE", 8);
+    h.version = 1;
+    h.precision = c->cfg.precision;
+    h.n0 = c->L0;
+    h.n1 = c->L1;
+    h.M = c->M;
+    h.d = c->d;
+    h.iters = c->iters;
+    h.p_valid = c->p_valid ? 1 : 0;
+    h.order_hash = order_fingerprint(c);
+    unsigned char *o = static_cast<unsigned char *>(blob);
+    std::memcpy(o, &h, sizeof(h));
+    o += sizeof(h);
+    const size_t rb = c->rsz;
+    PPD_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->stream2) PPD_CUDA(cudaStreamSynchronize(c->stream2));
+    PPD_CUDA(cudaMemcpy(o, c->x, c->N * rb, cudaMemcpyDeviceToHost));
+    o += c->N * rb;
+    PPD_CUDA(cudaMemcpy(o, c->xt, c->N * rb, cudaMemcpyDeviceToHost));
+    o += c->N * rb;
+    PPD_CUDA(cudaMemcpy(o, c->u, N_BASES * c->N * rb, cudaMemcpyDeviceToHost));
+    o += N_BASES * c->N * rb;
+    PPD_CUDA(cudaMemcpy(o, c->v, 2 * c->M * rb, cudaMemcpyDeviceToHost));
+    o += 2 * c->M * rb;
+    PPD_CUDA(cudaMemcpy(o, c->p, 2 * c->M * rb, cudaMemcpyDeviceToHost));
+    *bytes = need;
+    return PPD_OK;
+}
+
+int ppd_set_state(ppd_ctx *c, const void *blob, int64_t bytes) {
+    if (!c || !blob) return fail(PPD_ERR_INVALID_ARG, "ppd_set_state: NULL argument");
+    if (!c->have_weights) return fail(PPD_ERR_NOT_READY, "ppd_set_state: call ppd_set_weights first");
+    if (bytes != state_bytes(c)) return fail(PPD_ERR_INVALID_ARG, "ppd_set_state: size mismatch");
+    StateHeader h;
+    std::memcpy(&h, blob, sizeof(h));
+    if (std::memcmp(h.magic, "PPDSTATE", 8) != 0 || h.version != 1 || h.precision != c->cfg.precision ||
+        h.n0 != c->L0 || h.n1 != c->L1 || h.M != c->M || h.d != c->d)
+        return fail(PPD_ERR_INVALID_ARG, "ppd_set_state: blob made for another configuration");
+    if (h.order_hash != order_fingerprint(c))
+        return fail(PPD_ERR_INVALID_ARG, "ppd_set_state: blob made for another visibility order");
+    const unsigned char *o = static_cast<const unsigned char *>(blob) + sizeof(h);
+    const size_t rb = c->rsz;
+    PPD_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->stream2) PPD_CUDA(cudaStreamSynchronize(c->stream2));
+    PPD_CUDA(cudaMemcpy(c->x, o, c->N * rb, cudaMemcpyHostToDevice));
+    o += c->N * rb;
+    PPD_CUDA(cudaMemcpy(c->xt, o, c->N * rb, cudaMemcpyHostToDevice));
+    o += c->N * rb;
+    PPD_CUDA(cudaMemcpy(c->u, o, N_BASES * c->N * rb, cudaMemcpyHostToDevice));
+    o += N_BASES * c->N * rb;
+    PPD_CUDA(cudaMemcpy(c->v, o, 2 * c->M * rb, cudaMemcpyHostToDevice));
+    o += 2 * c->M * rb;
+    PPD_CUDA(cudaMemcpy(c->p, o, 2 * c->M * rb, cudaMemcpyHostToDevice));
+    c->iters = h.iters;
+    c->p_valid = h.p_valid != 0;
+    return PPD_OK;
 }
 
 int ppd_timing_enable(ppd_ctx *c, int32_t enable) {

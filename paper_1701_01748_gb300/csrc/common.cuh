@@ -129,6 +129,10 @@ struct ppd_ctx {
     std::vector<int64_t> perm_h;
     std::vector<int32_t> base0_h, base1_h, count_h, block_h, packed_h;
     std::vector<double> frac_h, eps_h, mu_h;
+    // host copies of the last inputs (the autotuner rebuilds the ordering)
+    std::vector<double> in_uv, in_y, in_theta, in_U, in_eps;
+    std::vector<int32_t> in_block;
+    bool has_theta = false, has_U = false, has_eps = false;
     std::vector<int64_t> block_count_h;
     int32_t *count_cell = nullptr;   // per visibility (sorted order), device
     ppd::Chunks ch;

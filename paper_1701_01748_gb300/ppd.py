@@ -48,7 +48,8 @@ class ppd_stats(ct.Structure):
 class ppd_params(ct.Structure):
     _fields_ = [("eta", ct.c_double), ("zeta", ct.c_double), ("tau", ct.c_double),
                 ("kappa", ct.c_double), ("op_norm_sq", ct.c_double), ("power_iters_done", ct.c_int32),
-                ("K0", ct.c_int32), ("K1", ct.c_int32), ("tile", ct.c_int32), ("n_chunks", ct.c_int64),
+                ("K0", ct.c_int32), ("K1", ct.c_int32), ("tile", ct.c_int32), ("chunk", ct.c_int32),
+                ("n_chunks", ct.c_int64),
                 ("M", ct.c_int64), ("convergence_lhs", ct.c_double)]
 
 
@@ -81,6 +82,12 @@ def _lib():
             "ppd_get_params": (I, [P, ct.POINTER(ppd_params)]),
             "ppd_get_bins": (I, [P, ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int32),
                                  ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32)]),
+            "ppd_autotune": (I, [P, I32, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32)]),
+            "ppd_get_state": (I, [P, P, ct.POINTER(ct.c_int64)]),
+            "ppd_group_create": (I, [ct.POINTER(P), ct.POINTER(P), I32]),
+            "ppd_group_iterate": (I, [P, I32]),
+            "ppd_group_destroy": (V, [P]),
+            "ppd_set_state": (I, [P, P, I64]),
             "ppd_op_forward": (I, [P, P, P, P]),
             "ppd_op_adjoint": (I, [P, P, P, P]),
             "ppd_op_adjoint_noalloc": (I, [P, P, P, P]),
@@ -201,6 +208,41 @@ def ppd_get_bins(ctx: int, M: int):
                                b1.ctypes.data_as(ct.POINTER(ct.c_int32)),
                                cnt.ctypes.data_as(ct.POINTER(ct.c_int32))), "ppd_get_bins")
     return perm, b0, b1, cnt
+
+
+def ppd_autotune(ctx: int, iters: int = 10):
+    t = ct.c_int32(0)
+    c = ct.c_int32(0)
+    _check(_lib().ppd_autotune(ctx, iters, ct.byref(t), ct.byref(c)), "ppd_autotune")
+    return int(t.value), int(c.value)
+
+
+def ppd_group_create(ctxs) -> int:
+    arr = (ct.c_void_p * len(ctxs))(*ctxs)
+    h = ct.c_void_p()
+    _check(_lib().ppd_group_create(ct.byref(h), arr, len(ctxs)), "ppd_group_create")
+    return h.value
+
+
+def ppd_group_iterate(group: int, n_iters: int) -> None:
+    _check(_lib().ppd_group_iterate(group, n_iters), "ppd_group_iterate")
+
+
+def ppd_group_destroy(group: int) -> None:
+    _lib().ppd_group_destroy(group)
+
+
+def ppd_get_state(ctx: int) -> bytes:
+    n = ct.c_int64(0)
+    _check(_lib().ppd_get_state(ctx, None, ct.byref(n)), "ppd_get_state")
+    buf = ct.create_string_buffer(n.value)
+    _check(_lib().ppd_get_state(ctx, ct.cast(buf, ct.c_void_p), ct.byref(n)), "ppd_get_state")
+    return buf.raw[: n.value]
+
+
+def ppd_set_state(ctx: int, blob: bytes) -> None:
+    buf = ct.create_string_buffer(blob, len(blob))
+    _check(_lib().ppd_set_state(ctx, ct.cast(buf, ct.c_void_p), len(blob)), "ppd_set_state")
 
 
 def ppd_op_forward(ctx: int, x_dev: int, y_dev: int, stream=None) -> None:

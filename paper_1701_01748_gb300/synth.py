@@ -148,6 +148,21 @@ def exact_visibilities(points, blob: np.ndarray, omega: np.ndarray,
     return y
 
 
+def make_batch(n: int = 8, seed: int = 1704, sides=(128, 256), ratio=(2.0, 8.0), blocks=(4, 32)):
+    """n independent problems of different sizes: side log-uniform over `sides`
+    (powers of two), M = r * L^2 with r log-uniform in `ratio`, block count
+    uniform in `blocks`, strongly non-uniform coverage (std 0.1 pi)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        L = int(sides[int(rng.integers(0, len(sides)))])
+        r = math.exp(rng.uniform(math.log(ratio[0]), math.log(ratio[1])))
+        d = int(rng.integers(blocks[0], blocks[1] + 1))
+        out.append(make_problem(f"batch_{i}", L=L, M=int(round(r * L * L)), n_blocks=d, uv_sigma=0.1,
+                                seed=seed * 100 + i))
+    return out
+
+
 def make_problem(name: str = "c1_128", *, L: int | None = None, M: int | None = None,
                  n_blocks: int | None = None, uv_sigma: float | None = None,
                  seed: int | None = None, isnr_db: float = 30.0,

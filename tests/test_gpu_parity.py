@@ -290,3 +290,72 @@ def test_error_codes():
     out = s.iterate(2)
     assert out["iters_done"] == 2 and math.isfinite(out["rel_var"])
     s.close()
+
+
+# ----------------------------------------------------------------- checkpoint / resume
+@pytest.mark.parametrize("prec", [F32, F64])
+def test_state_resume_is_bit_identical(prec):
+    p = problem("small", **SMALL)
+    s = solver(p, prec)                      # eta by the library's power iteration
+    s.iterate(7)
+    blob = ppd.ppd_get_state(s.ctx)
+    s.iterate(9)
+    x_run = s.image()
+    ppd.ppd_set_state(s.ctx, blob)
+    out = s.iterate(9)
+    assert out["iters_done"] == 16
+    assert np.array_equal(s.image(), x_run)
+    # a blob for another configuration is refused
+    s2 = solver(problem("c1_128"), prec, eta=1.0)
+    with pytest.raises(ppd.PPDError) as e:
+        ppd.ppd_set_state(s2.ctx, blob)
+    assert e.value.status == ppd.PPD_ERR_INVALID_ARG
+    s2.close()
+    s.close()
+
+
+# ----------------------------------------------------------------- autotuner
+def test_autotune_picks_a_candidate_and_keeps_parity():
+    p = problem("small", **SMALL)
+    S = oppd.make_setup(p.omega, p.y, p.theta, p.block, p.n_blocks, p.L, power_iters=400, x_true=p.x_true)
+    s = ppd.Solver(p.L, p.n_blocks, precision=F32, eta=S.eta)
+    s.set_problem(p.omega, p.y, p.block, theta=p.theta, x_true=p.x_true)
+    tile, chunk = ppd.ppd_autotune(s.ctx, 3)
+    prm = s.params()
+    assert tile in (16, 32) and chunk in (512, 1024, 2048)
+    assert prm["tile"] == tile and prm["chunk"] == chunk and abs(prm["eta"] - S.eta) <= 1e-12 * S.eta
+    st = oppd.init_state(S)
+    for _ in range(10):
+        oppd.iterate(st, S)
+    s.iterate(10)
+    assert rel(s.image(), st.x) <= 1e-4
+    perm, _, _, _ = ppd.ppd_get_bins(s.ctx, p.M)
+    assert np.array_equal(perm, nufft.visibility_order(p.omega, p.block, 2 * p.L, 2 * p.L, tile)[0])
+    s.close()
+
+
+# ----------------------------------------------------------------- batched group
+def test_group_matches_individual_runs():
+    probs = [synth.make_problem("grp", L=L, M=M, n_blocks=d, uv_sigma=0.15, seed=40 + i, n_points=6, n_blobs=1)
+             for i, (L, M, d) in enumerate([(32, 3000, 2), (64, 9000, 4), (32, 2000, 3)])]
+    solo, grouped = [], []
+    for p in probs:
+        a = ppd.Solver(p.L, p.n_blocks, precision=F32)   # eta by power iteration, shared below
+        a.set_problem(p.omega, p.y, p.block, theta=p.theta)
+        eta = a.params()["eta"]
+        a.close()
+        for dest in (solo, grouped):
+            s = ppd.Solver(p.L, p.n_blocks, precision=F32, eta=eta)
+            s.set_problem(p.omega, p.y, p.block, theta=p.theta)
+            dest.append(s)
+    for s in solo:
+        s.iterate(12, stats=False)
+    g = ppd.ppd_group_create([s.ctx for s in grouped])
+    ppd.ppd_group_iterate(g, 5)
+    ppd.ppd_group_iterate(g, 7)
+    ppd.ppd_group_destroy(g)
+    for a, b in zip(solo, grouped):
+        assert b.iterate(0)["iters_done"] == 12
+        assert np.array_equal(a.image(), b.image())
+        a.close()
+        b.close()
