@@ -204,6 +204,23 @@ def cpu_info():
     return model, os.cpu_count()
 
 
+# ------------------------------------------------------------------ replicas
+def max_over_ranks(seconds_per_step: float, dist=None, device=None) -> float:
+    """Slowest rank's seconds per step (each rank runs its own replica)."""
+    if dist is None:
+        return float(seconds_per_step)
+    import torch
+    t = torch.tensor([seconds_per_step], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(seconds_per_step: float, world: int) -> float:
+    """Whole-job iterations/s: every rank completes one iteration of its own
+    problem per step, the step lasting as long as the slowest rank's."""
+    return world / seconds_per_step
+
+
 # ------------------------------------------------------------------ batched problems
 def bench_batch(args, rank, world, local):
     """Independent problems of different sizes: each alone (one graph each,
@@ -395,16 +412,12 @@ def main():
     ips32 = args.steps / t32
     steps64 = max(3, args.steps // 4)
     ips64 = steps64 / t64
+    per_step = max_over_ranks(t32 / args.steps, dist, dev)
     if dist is not None:
-        t = torch.tensor([t32 / args.steps], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        per_step = float(t.item())
         dist.destroy_process_group()
-    else:
-        per_step = t32 / args.steps
     if rank != 0:
         return
-    value = world / per_step
+    value = replica_throughput(per_step, world)
     target = snr64[-1]
     it_to_target = None
     for i, v in enumerate(snr32):
