@@ -18,7 +18,8 @@ Readings (the paper is silent or its printed step is garbled):
   is the generalised Moreau identity with alpha = 1 after the rescaling
   v <- v/eta that puts eta in the primal step.
 * Algorithm 2 starts from the previous iteration's p (warm start) and, on
-  the first iteration, from P_B(z).  n_itr fixed (default 1).
+  the first iteration, from P_B(z); optionally from z itself every
+  iteration ("current").  n_itr fixed (default 1).
 * mu_j = 1/max_e(U_j,e)^2 (Algorithm 2, as printed).
 * Per-block bound eps_j^2 = M_j + 2 sqrt(M_j) in whitened units (the
   chi^2 rule applied per block; y whitened as Theta y).
@@ -78,6 +79,7 @@ class Setup:
     n_itr: int = 1
     levels: int = 4
     x_true: np.ndarray | None = None
+    inner_init: str = "warm"    # Algorithm 2 start: "warm" (previous p) or "current" (z)
 
     def __post_init__(self):
         self.members = [np.flatnonzero(self.block == j) for j in range(self.n_blocks)]
@@ -87,7 +89,7 @@ class Setup:
 def make_setup(omega, y, theta, block, n_blocks, L, *, precond: bool = True,
                eta: float | None = None, eps=None, U=None, n_itr: int = 1,
                tau: float = 0.49, kappa: float = 1e-4, x_true=None,
-               power_iters: int = 1000) -> Setup:
+               power_iters: int = 1000, inner_init: str = "warm") -> Setup:
     P = nufft.Plan(omega, L, L, theta=theta)
     if U is None:
         U = nufft.uniform_weights(omega, P.K0, P.K1)[0] if precond else np.ones(P.M)
@@ -103,7 +105,7 @@ def make_setup(omega, y, theta, block, n_blocks, L, *, precond: bool = True,
         eta = 1.0 / op_norm_sq(P, U, max_iter=power_iters)[0]
     return Setup(P=P, yw=np.asarray(theta) * np.asarray(y), U=U, block=block,
                  n_blocks=n_blocks, eps=eps, mu=mu, eta=float(eta), tau=tau, kappa=kappa,
-                 n_itr=n_itr, x_true=x_true)
+                 n_itr=n_itr, x_true=x_true, inner_init=inner_init)
 
 
 def convergence_lhs(S: Setup, psi_norm_sq: float = 1.0, phi_norm_sq: float | None = None):
@@ -141,7 +143,9 @@ def iterate(st: State, S: Setup) -> dict:
     for j, m in enumerate(S.members):
         if m.size == 0:
             continue
-        if st.p is None:
+        if S.inner_init == "current":
+            start = z[m]
+        elif st.p is None:
             start = prox.proj_l2ball(z[m], S.yw[m], S.eps[j])
         else:
             start = st.p[m]

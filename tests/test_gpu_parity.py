@@ -173,7 +173,8 @@ def run_both(p, prec, n_iter, **kw):
     precond = kw.pop("precond", 1)
     init = kw.pop("inner_init", ppd.PPD_INNER_WARM)
     S = oppd.make_setup(p.omega, p.y, p.theta, p.block, p.n_blocks, p.L, precond=bool(precond),
-                        n_itr=n_itr, power_iters=400, x_true=p.x_true)
+                        n_itr=n_itr, power_iters=400, x_true=p.x_true,
+                        inner_init="current" if init == ppd.PPD_INNER_CURRENT else "warm")
     s = ppd.Solver(p.L, p.n_blocks, precision=prec, eta=S.eta, n_itr=n_itr, precond=precond,
                    inner_init=init, **kw)
     s.set_problem(p.omega, p.y, p.block, theta=p.theta, x_true=p.x_true)
@@ -203,6 +204,13 @@ def test_ppd_multiblock_subiterations_weights(prec):
     p2 = synth.Problem(**{**p.__dict__})
     p2.theta = p.theta * np.random.default_rng(4).uniform(0.5, 2.0, size=p.M)   # non-uniform Theta
     xg, st, hist, stats, S = run_both(p2, prec, 30, n_itr=3)
+    assert rel(xg, st.x) <= TOL[prec]["img"], rel(xg, st.x)
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
+def test_inner_start_at_z(prec):
+    p = problem("small", **SMALL)
+    xg, st, hist, stats, S = run_both(p, prec, 20, n_itr=3, inner_init=ppd.PPD_INNER_CURRENT)
     assert rel(xg, st.x) <= TOL[prec]["img"], rel(xg, st.x)
 
 
