@@ -263,6 +263,37 @@ def bench_batch(args, rank, world, local):
         s.close()
 
 
+# ------------------------------------------------------------------ PD vs PPD study
+def study_ggd(args, local):
+    """Convergence speed of PPD (U = inverse sampling density) against PD
+    (U = I) on generalised-Gaussian coverages of shape beta (Section 5.3): SNR
+    every 10 iterations, and how many iterations PD needs to reach the SNR
+    that PPD has at iteration 100."""
+    import torch
+    from paper_1701_01748_gb300 import ppd, synth
+    torch.cuda.set_device(local)
+    iters = max(args.steps, 200)
+    out = {"metric": "iterations to reach PPD's SNR at iteration 100, PD vs PPD", "data": "synthetic",
+           "config": {"workload": "ggd", "image": "256x256", "visibilities": 65536, "blocks": 4,
+                      "uv_std": "0.15 pi", "isnr_db": args.isnr}, "results": []}
+    for beta in (2.0, 0.5, 0.25):
+        p = synth.make_problem("ggd", L=256, M=65536, n_blocks=4, uv_sigma=0.15, seed=1705,
+                               ggd_beta=beta, isnr_db=args.isnr)
+        curves = {}
+        for name, precond in (("ppd", 1), ("pd", 0)):
+            s = ppd.Solver(p.L, p.n_blocks, precision=ppd.PPD_FP32_FP64NORMS, precond=precond)
+            s.set_problem(p.omega, p.y, p.block, theta=p.theta, x_true=p.x_true)
+            curves[name] = [s.iterate(10)["snr_db"] for _ in range(iters // 10)]
+            s.close()
+        target = curves["ppd"][9]          # PPD at iteration 100
+        reach = next((10 * (i + 1) for i, v in enumerate(curves["pd"]) if v >= target), None)
+        out["results"].append({"beta": beta, "ppd_snr_at_100": target,
+                               "pd_iters_to_ppd_snr_at_100": reach,
+                               "speedup": (reach / 100.0) if reach else f">{iters / 100.0}",
+                               "ppd_snr": curves["ppd"][::5], "pd_snr": curves["pd"][::5]})
+    print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -277,6 +308,8 @@ def main():
     ap.add_argument("--oracle-steps", type=int, default=3)
     ap.add_argument("--tile", type=int, default=0, help="gridding tile side (0: library default)")
     ap.add_argument("--chunk", type=int, default=0, help="visibilities per work item (0: library default)")
+    ap.add_argument("--study", default="", help="ggd: PD vs PPD convergence on generalised-Gaussian coverages")
+    ap.add_argument("--isnr", type=float, default=30.0, help="input SNR (dB) of the study problems")
     ap.add_argument("--quick", action="store_true",
                     help="only the timed FP32 steps (for profiler launch lists); eta from 20 power steps")
     args = ap.parse_args()
@@ -284,6 +317,12 @@ def main():
         oracle_worker(args)
         return
     rank, world, local = _env_rank()
+    if args.study == "ggd":
+        from paper_1701_01748_gb300 import build
+        build.build()
+        if rank == 0:
+            study_ggd(args, local)
+        return
     from paper_1701_01748_gb300 import synth
     base_seed = synth.CONFIGS[args.workload]["seed"] if args.workload in synth.CONFIGS else 1704
     seed = (args.seed if args.seed is not None else base_seed) + 1000 * rank

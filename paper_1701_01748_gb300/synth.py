@@ -28,8 +28,8 @@ import math
 
 import numpy as np
 
-__all__ = ["Problem", "CONFIGS", "make_problem", "sky_image", "sample_uv",
-           "radial_blocks", "exact_visibilities"]
+__all__ = ["Problem", "CONFIGS", "make_problem", "make_batch", "sky_image", "sample_uv",
+           "sample_uv_ggd", "radial_blocks", "exact_visibilities"]
 
 
 @dataclasses.dataclass
@@ -105,6 +105,23 @@ def sample_uv(M: int, uv_sigma: float, rng: np.random.Generator) -> np.ndarray:
     return np.ascontiguousarray(out[:M])
 
 
+def sample_uv_ggd(M: int, beta: float, std: float, rng: np.random.Generator) -> np.ndarray:
+    """omega per axis from a zero-mean generalised Gaussian, density ~ exp(-|w/a|^beta),
+    scaled to standard deviation std*pi (Section 5's GGD coverages; beta = 2 is
+    Gaussian, smaller beta concentrates the samples at the centre), redrawn
+    until inside [-pi, pi)^2.  |w/a|^beta ~ Gamma(1/beta) with a random sign."""
+    a = std * math.pi * math.sqrt(math.gamma(1.0 / beta) / math.gamma(3.0 / beta))
+    out = np.empty((0, 2))
+    while out.shape[0] < M:
+        need = M - out.shape[0] + 16
+        g = rng.gamma(1.0 / beta, 1.0, size=(need, 2)) ** (1.0 / beta)
+        sgn = np.where(rng.random(size=(need, 2)) < 0.5, -1.0, 1.0)
+        w = a * sgn * g
+        ok = np.all((w >= -math.pi) & (w < math.pi), axis=1)
+        out = np.concatenate([out, w[ok]], axis=0)
+    return np.ascontiguousarray(out[:M])
+
+
 def radial_blocks(omega: np.ndarray, n_blocks: int) -> np.ndarray:
     """Uneven data blocks: equal-width radial bands of |omega| (FP64)."""
     r = np.hypot(omega[:, 0], omega[:, 1])
@@ -166,7 +183,7 @@ def make_batch(n: int = 8, seed: int = 1704, sides=(128, 256), ratio=(2.0, 8.0),
 def make_problem(name: str = "c1_128", *, L: int | None = None, M: int | None = None,
                  n_blocks: int | None = None, uv_sigma: float | None = None,
                  seed: int | None = None, isnr_db: float = 30.0,
-                 n_points: int = 20, n_blobs: int = 3) -> Problem:
+                 n_points: int = 20, n_blobs: int = 3, ggd_beta: float | None = None) -> Problem:
     """Build a seeded problem; keyword arguments override the named shape."""
     cfg = dict(CONFIGS.get(name, CONFIGS["c1_128"]))
     for k, v in dict(L=L, M=M, n_blocks=n_blocks, uv_sigma=uv_sigma, seed=seed).items():
@@ -178,7 +195,10 @@ def make_problem(name: str = "c1_128", *, L: int | None = None, M: int | None = 
     x = blob.copy()
     for (p0, p1, f) in points:
         x[p0, p1] += f
-    omega = sample_uv(int(cfg["M"]), float(cfg["uv_sigma"]), rng)
+    if ggd_beta is None:
+        omega = sample_uv(int(cfg["M"]), float(cfg["uv_sigma"]), rng)
+    else:
+        omega = sample_uv_ggd(int(cfg["M"]), float(ggd_beta), float(cfg["uv_sigma"]), rng)
     block = radial_blocks(omega, int(cfg["n_blocks"]))
     y0 = exact_visibilities(points, blob, omega)
     Mv = omega.shape[0]

@@ -1,0 +1,35 @@
+"""The seeded input generator: shapes, seeds and the u-v samplers."""
+import math
+
+import numpy as np
+
+from paper_1701_01748_gb300 import synth
+
+
+def test_problem_is_reproducible_and_well_formed():
+    a = synth.make_problem("t", L=32, M=500, n_blocks=3, uv_sigma=0.2, seed=3, n_points=4, n_blobs=1)
+    b = synth.make_problem("t", L=32, M=500, n_blocks=3, uv_sigma=0.2, seed=3, n_points=4, n_blobs=1)
+    assert np.array_equal(a.y, b.y) and np.array_equal(a.omega, b.omega)
+    assert a.x_true.min() >= 0 and a.omega.shape == (500, 2)
+    assert np.all((a.omega >= -math.pi) & (a.omega < math.pi))
+    assert set(np.unique(a.block)) <= {0, 1, 2}
+
+
+def test_exact_visibilities_match_a_direct_sum():
+    rng = np.random.default_rng(1)
+    pts, blob = synth.sky_image(16, rng, n_points=3, n_blobs=1)
+    x = blob.copy()
+    for p0, p1, f in pts:
+        x[p0, p1] += f
+    om = rng.uniform(-math.pi, math.pi, size=(40, 2))
+    n = np.arange(16) - 8
+    direct = np.array([np.sum(x * np.exp(-1j * (w0 * n[:, None] + w1 * n[None, :]))) for w0, w1 in om])
+    assert np.abs(synth.exact_visibilities(pts, blob, om) - direct).max() <= 1e-12 * np.abs(direct).max()
+
+
+def test_ggd_sampler_shape():
+    rng = np.random.default_rng(2)
+    g2 = synth.sample_uv_ggd(100000, 2.0, 0.15, rng)
+    assert abs(g2.std() / math.pi - 0.15) < 0.005          # beta = 2 is the Gaussian of that std
+    centre = [np.mean(np.abs(synth.sample_uv_ggd(50000, b, 0.15, rng)) < 0.05 * math.pi) for b in (2.0, 0.5, 0.25)]
+    assert centre[0] < centre[1] < centre[2]                # smaller beta: denser centre
