@@ -103,7 +103,9 @@ typedef struct {
     double  *block_residual;    /* optional caller buffer of n_blocks doubles: ||Phi_j xt - y_j|| (whitened) */
 } ppd_stats;
 
-/* Parameters resolved by ppd_set_weights. */
+/* Parameters resolved by ppd_set_weights (and ppd_set_prior_weights /
+ * ppd_reweight): zeta is the value the primal step uses, the configured zeta
+ * divided by ||Psi W||_S^2. */
 typedef struct {
     double   eta, zeta, tau, kappa;
     double   op_norm_sq;        /* ||U^{1/2} Phi||_S^2 (0 if eta was given) */
@@ -113,7 +115,9 @@ typedef struct {
     int32_t  chunk;             /* max visibilities per work item */
     int64_t  n_chunks;          /* gridding work items */
     int64_t  M;                 /* visibilities */
-    double   convergence_lhs;   /* tau*zeta*||Psi||^2 + tau*eta*||U^{1/2}Phi||^2 (Eq. "convergence-req-explicit-pd"), < 1 */
+    double   convergence_lhs;   /* tau*zeta*||Psi W||^2 + tau*eta*||U^{1/2}Phi||^2 (Eq. "convergence-req-explicit-pd"), < 1 */
+    double   psiw_norm_sq;      /* ||Psi W||_S^2 of the prior weights (1 when W = I) */
+    double   alpha;             /* clip level of the prior step, kappa * ||Psi W||_S^2 */
 } ppd_params;
 
 /* Fill *cfg with the paper's defaults (n0 = n1 = 0 must still be set). */
@@ -207,6 +211,34 @@ PPD_API int ppd_autotune(ppd_ctx *ctx, int32_t iters, int32_t *tile_out, int32_t
  * Errors: NOT_READY, INVALID_ARG (size, tag or fingerprint mismatch), CUDA. */
 PPD_API int ppd_get_state(ppd_ctx *ctx, void *blob, int64_t *bytes);
 PPD_API int ppd_set_state(ppd_ctx *ctx, const void *blob, int64_t bytes);
+
+/* Re-weighted l1 (Section 3.2, Algorithm 1, Eq. "reweighting").  The prior
+ * weights W_i are diagonal, one value per SARA coefficient, stored like the
+ * 9 dual images u_i: 9 * n0 * n1 values, basis-major (Dirac, db1 .. db8),
+ * each basis in the Mallat quadrant layout of ppd_psi_analysis.  With W set,
+ * the prior step of Algorithm 3 becomes u_i <- clip(u_i + W_i Psi_i^dagger xt,
+ * alpha), ut_i = Psi_i W_i u_i, with alpha = kappa ||Psi W||_S^2 and the primal
+ * step uses zeta / ||Psi W||_S^2 (so the convergence condition keeps its
+ * value); ||Psi W||_S^2 comes from a power iteration on Psi W^2 Psi^dagger
+ * (start all-ones, cfg power_iters / power_tol).  The solver state (x, xt,
+ * u, v) is kept, so the next ppd_iterate warm-starts from it as Algorithm 1
+ * asks.  Weights persist across ppd_set_weights and ppd_set_state; they are
+ * not part of the state blob.  A ppd_group holding the context re-captures
+ * its graph on its next ppd_group_iterate.
+ *
+ * ppd_set_prior_weights: w = host array of len = 9 n0 n1 doubles, finite and
+ *   >= 0, copied; w = NULL restores W = I.  Synchronises.
+ * ppd_reweight: W = omega / (omega + |Psi^dagger x|) from the current primal
+ *   iterate x, computed on the device (Eq. "reweighting"); omega > 0.
+ *   Algorithm 1's schedule is omega^(k) = 0.25^k omega^(0), omega^(0) = 1e-2
+ *   (Section 5.1).  Synchronises.
+ * ppd_get_prior_weights: host copy (FP64) of W, all ones when W = I.
+ * Errors: INVALID_ARG (NULL, len, negative or non-finite weight, omega),
+ * NONFINITE (||Psi W|| zero or not finite: the context is left with W = I),
+ * OOM, CUDA. */
+PPD_API int ppd_set_prior_weights(ppd_ctx *ctx, const double *w, int64_t len);
+PPD_API int ppd_reweight(ppd_ctx *ctx, double omega);
+PPD_API int ppd_get_prior_weights(ppd_ctx *ctx, double *w, int64_t len);
 
 /* Phi x = Theta G F Z x (Section 2): x_dev n0*n1 reals -> y_dev M complex
  * (caller order, whitened by theta).  Enqueued on stream.  Uses the

@@ -27,6 +27,9 @@ Readings (the paper is silent or its printed step is garbled):
 * Power iteration for ||U^{1/2} Phi||_S^2 on Phi^dagger U Phi from the
   all-ones vector, stopped at relative change < 1e-10 or 1000 steps.
 
+Prior weights W (Algorithm 1) enter the prior step as printed in Algorithm
+3; ``oracle/reweight.py`` sets them.
+
 Parity: the invariants of the whole iteration (feasibility, positivity,
 PPD and PD reaching the same minimiser, U = I reducing to PD) are pinned by
 tests; the trajectory itself is "parity unpinned" beyond them.
@@ -80,6 +83,8 @@ class Setup:
     levels: int = 4
     x_true: np.ndarray | None = None
     inner_init: str = "warm"    # Algorithm 2 start: "warm" (previous p) or "current" (z)
+    W: np.ndarray | None = None  # prior weights (9, L0, L1) of Algorithm 1; None = identity
+    psiw_sq: float = 1.0         # ||Psi W||_S^2 (1 for W = I)
 
     def __post_init__(self):
         self.members = [np.flatnonzero(self.block == j) for j in range(self.n_blocks)]
@@ -108,11 +113,13 @@ def make_setup(omega, y, theta, block, n_blocks, L, *, precond: bool = True,
                  n_itr=n_itr, x_true=x_true, inner_init=inner_init)
 
 
-def convergence_lhs(S: Setup, psi_norm_sq: float = 1.0, phi_norm_sq: float | None = None):
-    """tau zeta ||Psi||^2 + tau eta ||U^{1/2} Phi||^2 (must be < 1)."""
+def convergence_lhs(S: Setup, psi_norm_sq: float | None = None, phi_norm_sq: float | None = None):
+    """tau zeta_eff ||Psi W||^2 + tau eta ||U^{1/2} Phi||^2 (must be < 1)."""
     if phi_norm_sq is None:
         phi_norm_sq = 1.0 / S.eta
-    return S.tau * S.zeta * psi_norm_sq + S.tau * S.eta * phi_norm_sq
+    if psi_norm_sq is None:
+        psi_norm_sq = S.psiw_sq
+    return S.tau * (S.zeta / S.psiw_sq) * psi_norm_sq + S.tau * S.eta * phi_norm_sq
 
 
 @dataclasses.dataclass
@@ -153,12 +160,16 @@ def iterate(st: State, S: Setup) -> dict:
                                       start=start, mu=S.mu[j])
     v = S.U * (z - p)
     g = nufft.phi_adjoint(v, P)
-    # prior step: clip (I - S_kappa) of u + Psi^dagger xt, then synthesis
+    # prior step: clip (I - S_{kappa ||Psi W||^2}) of u + W Psi^dagger xt, then
+    # synthesis of W u; zeta = 1/||Psi W||^2 (W = I: ||Psi|| = 1)
     c = sara.psi_adjoint(st.xt, S.levels, S.hs)
-    u = prox.clip_complement(st.u + c, S.kappa * 1.0)
-    ut = sara.psi(u, S.levels, S.hs)
+    if S.W is not None:
+        c = S.W * c
+    u = prox.clip_complement(st.u + c, S.kappa * S.psiw_sq)
+    ut = sara.psi(u if S.W is None else S.W * u, S.levels, S.hs)
+    zeta = S.zeta / S.psiw_sq
     # primal step
-    xbar = prox.proj_positive(st.x - S.tau * (S.eta * g + S.zeta * ut))
+    xbar = prox.proj_positive(st.x - S.tau * (S.eta * g + zeta * ut))
     dx = float(np.linalg.norm(xbar - st.x))
     nx = float(np.linalg.norm(xbar))
     xt = 2.0 * xbar - st.x
@@ -171,6 +182,7 @@ def iterate(st: State, S: Setup) -> dict:
 
 
 def run(S: Setup, n_iters: int, st: State | None = None):
+    """n_iters iterations of Algorithm 3 from st (warm start) or from zero."""
     st = init_state(S) if st is None else st
     hist = []
     for _ in range(n_iters):

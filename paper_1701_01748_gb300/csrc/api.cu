@@ -116,6 +116,7 @@ void free_vis(ppd_ctx *c) {
 }
 
 void drop_graph(ppd_ctx *c) {
+    ++c->gen;
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     c->gexec = nullptr;
@@ -334,6 +335,58 @@ template <typename R> int upload_real(void *dst, const std::vector<double> &src)
     return PPD_OK;
 }
 
+// ||Psi W||_S^2 by power iteration on Psi W^2 Psi^dagger from the all-ones
+// image (same start and stop rule as the one for Phi).  The iterate lives in
+// g and ut, which every PPD iteration recomputes before use.
+template <typename R> int psiw_power_iteration(ppd_ctx *c) {
+    cudaStream_t s = c->stream;
+    const int64_t N = c->N;
+    R *v = static_cast<R *>(c->g), *y = static_cast<R *>(c->ut), *cw = static_cast<R *>(c->wcoef);
+    const R *w = static_cast<const R *>(c->wgt);
+    std::vector<R> ones(N, R(1.0 / std::sqrt((double)N)));
+    PPD_CUDA(cudaMemcpyAsync(v, ones.data(), N * sizeof(R), cudaMemcpyHostToDevice, s));
+    double prev = 0, val = 0;
+    const int maxit = c->cfg.power_iters > 0 ? c->cfg.power_iters : 1000;
+    const double tol = c->cfg.power_tol > 0 ? c->cfg.power_tol : 1e-10;
+    int it = 0;
+    for (it = 1; it <= maxit; ++it) {
+        PPD_CHECK(psi_analysis<R>(c, v, cw, s));
+        PPD_CHECK(mul_sq<R>(c, cw, w, N_BASES * N, s));
+        PPD_CHECK(psi_synthesis<R>(c, cw, y, s));
+        PPD_CHECK(sumsq<R>(c, y, N, c->stat_out, s));
+        double h[3];
+        PPD_CUDA(cudaMemcpyAsync(h, c->stat_out, sizeof(h), cudaMemcpyDeviceToHost, s));
+        PPD_CUDA(cudaStreamSynchronize(s));
+        val = std::sqrt(h[0]);
+        if (!std::isfinite(val) || val <= 0)
+            return fail(PPD_ERR_NONFINITE, "prior weights: ||Psi W|| is zero or not finite");
+        PPD_CHECK(scale_copy<R>(c, y, v, N, 1.0 / val, s));
+        if (std::abs(val - prev) <= tol * val) break;
+        prev = val;
+    }
+    c->psiw2 = val;
+    c->psiw_iters = std::min(it, maxit);
+    return PPD_OK;
+}
+
+int ensure_weight_buffers(ppd_ctx *c) {
+    const size_t bytes = (size_t)N_BASES * c->N * c->rsz;
+    if (!c->wgt) PPD_CHECK(dalloc_bytes(&c->wgt, bytes));
+    if (!c->wcoef) PPD_CHECK(dalloc_bytes(&c->wcoef, bytes));
+    return PPD_OK;
+}
+
+int finish_weights(ppd_ctx *c) {
+    drop_graph(c);
+    const int st = c->is_f32 ? psiw_power_iteration<float>(c) : psiw_power_iteration<double>(c);
+    if (st != PPD_OK) {   // leave the context unweighted rather than half-set
+        dfree(c->wgt);
+        c->wgt = nullptr;
+        c->psiw2 = 1.0;
+    }
+    return st;
+}
+
 }  // namespace
 
 // ======================================================================= ABI
@@ -478,6 +531,8 @@ void ppd_destroy(ppd_ctx *c) {
     free_vis(c);
     for (void *p : {(void *)c->fwd_strips, (void *)c->inv_strips, (void *)c->row_fwd, (void *)c->row_inv,
                     (void *)c->col_fwd, c->fft_tmp_inv})
+        dfree(p);
+    for (void *p : {c->wgt, c->wcoef})
         dfree(p);
     for (void *p : {c->x, c->xt, c->g, c->ut, c->xtrue, c->u, c->wtmp, c->wtmp2, c->grid_a, c->grid_v, c->fft_tmp,
                     c->tw0, c->deap0, c->deap1, c->kbpoly, (void *)c->prim_part, (void *)c->stat_out, (void *)c->err})
@@ -872,7 +927,7 @@ int ppd_get_params(ppd_ctx *c, ppd_params *o) {
     if (!c || !o) return fail(PPD_ERR_INVALID_ARG, "ppd_get_params: NULL argument");
     if (!c->have_weights) return fail(PPD_ERR_NOT_READY, "ppd_get_params: call ppd_set_weights first");
     o->eta = c->eta;
-    o->zeta = c->zeta;
+    o->zeta = c->zeta / c->psiw2;
     o->tau = c->tau;
     o->kappa = c->kappa;
     o->op_norm_sq = c->op_norm_sq;
@@ -883,8 +938,10 @@ int ppd_get_params(ppd_ctx *c, ppd_params *o) {
     o->chunk = c->C;
     o->n_chunks = c->ch.n;
     o->M = c->M;
+    o->psiw_norm_sq = c->psiw2;
+    o->alpha = c->kappa * c->psiw2;
     const double phi2 = c->op_norm_sq > 0 ? c->op_norm_sq : 1.0 / c->eta;
-    o->convergence_lhs = c->tau * c->zeta * 1.0 + c->tau * c->eta * phi2;
+    o->convergence_lhs = c->tau * (c->zeta / c->psiw2) * c->psiw2 + c->tau * c->eta * phi2;
     return PPD_OK;
 }
 
@@ -938,6 +995,64 @@ int ppd_psi_synthesis(ppd_ctx *c, const void *c_dev, void *x_dev, void *stream) 
     cudaStream_t s = pick(c, stream);
     if (c->is_f32) return psi_synthesis<float>(c, static_cast<const float *>(c_dev), static_cast<float *>(x_dev), s);
     return psi_synthesis<double>(c, static_cast<const double *>(c_dev), static_cast<double *>(x_dev), s);
+}
+
+int ppd_set_prior_weights(ppd_ctx *c, const double *w, int64_t len) {
+    if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_set_prior_weights: NULL context");
+    if (!w) {
+        PPD_CUDA(cudaStreamSynchronize(c->stream));
+        dfree(c->wgt);
+        c->wgt = nullptr;
+        c->psiw2 = 1.0;
+        c->psiw_iters = 0;
+        drop_graph(c);
+        return PPD_OK;
+    }
+    if (len != (int64_t)N_BASES * c->N) return fail(PPD_ERR_INVALID_ARG, "ppd_set_prior_weights: len != 9 n0 n1");
+    for (int64_t i = 0; i < len; ++i)
+        if (!(w[i] >= 0.0) || !std::isfinite(w[i]))
+            return fail(PPD_ERR_INVALID_ARG, "ppd_set_prior_weights: weights must be finite and >= 0");
+    PPD_CUDA(cudaStreamSynchronize(c->stream));
+    PPD_CHECK(ensure_weight_buffers(c));
+    if (c->is_f32) {
+        PPD_CHECK(upload_real<float>(c->wgt, std::vector<double>(w, w + len)));
+    } else {
+        PPD_CHECK(upload_real<double>(c->wgt, std::vector<double>(w, w + len)));
+    }
+    return finish_weights(c);
+}
+
+int ppd_reweight(ppd_ctx *c, double omega) {
+    if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_reweight: NULL context");
+    if (!(omega > 0) || !std::isfinite(omega)) return fail(PPD_ERR_INVALID_ARG, "ppd_reweight: omega must be > 0");
+    PPD_CHECK(ensure_weight_buffers(c));
+    cudaStream_t s = c->stream;
+    if (c->is_f32) {
+        PPD_CHECK(psi_analysis<float>(c, static_cast<const float *>(c->x), static_cast<float *>(c->wgt), s));
+        PPD_CHECK(reweight_from<float>(c, static_cast<float *>(c->wgt), N_BASES * c->N, omega, s));
+    } else {
+        PPD_CHECK(psi_analysis<double>(c, static_cast<const double *>(c->x), static_cast<double *>(c->wgt), s));
+        PPD_CHECK(reweight_from<double>(c, static_cast<double *>(c->wgt), N_BASES * c->N, omega, s));
+    }
+    return finish_weights(c);
+}
+
+int ppd_get_prior_weights(ppd_ctx *c, double *w, int64_t len) {
+    if (!c || !w) return fail(PPD_ERR_INVALID_ARG, "ppd_get_prior_weights: NULL argument");
+    if (len != (int64_t)N_BASES * c->N) return fail(PPD_ERR_INVALID_ARG, "ppd_get_prior_weights: len != 9 n0 n1");
+    if (!c->wgt) {
+        std::fill(w, w + len, 1.0);
+        return PPD_OK;
+    }
+    PPD_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->is_f32) {
+        std::vector<float> t(len);
+        PPD_CUDA(cudaMemcpy(t.data(), c->wgt, len * sizeof(float), cudaMemcpyDeviceToHost));
+        std::copy(t.begin(), t.end(), w);
+    } else {
+        PPD_CUDA(cudaMemcpy(w, c->wgt, len * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    return PPD_OK;
 }
 
 int ppd_autotune(ppd_ctx *c, int32_t iters, int32_t *tile_out, int32_t *chunk_out) {
@@ -1002,6 +1117,7 @@ struct ppd_group {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<int64_t> kernels;   // kernels each context contributes to one replay
+    std::vector<uint64_t> gens;     // the contexts' graph generations at capture
 };
 
 void ppd_group_destroy(ppd_group *g) {
@@ -1057,7 +1173,18 @@ int ppd_group_iterate(ppd_group *g, int32_t n_iters) {
         }
         if (--n_iters == 0) return PPD_OK;
     }
+    bool stale = g->gens.size() != g->ctxs.size();
+    for (size_t i = 0; !stale && i < g->ctxs.size(); ++i) stale = g->gens[i] != g->ctxs[i]->gen;
+    if (stale && g->exec) {   // a context's parameters, weights or buffers changed since the capture
+        PPD_CUDA(cudaStreamSynchronize(g->stream));
+        cudaGraphExecDestroy(g->exec);
+        cudaGraphDestroy(g->graph);
+        g->exec = nullptr;
+        g->graph = nullptr;
+    }
     if (!g->exec) {
+        g->gens.clear();
+        for (ppd_ctx *c : g->ctxs) g->gens.push_back(c->gen);
         std::vector<int64_t> before;
         for (ppd_ctx *c : g->ctxs) before.push_back(c->launches);
         PPD_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));

@@ -146,6 +146,14 @@ struct ppd_ctx {
     CUtensorMap tmap_a;              // TMA descriptor of grid_a
     bool tma_ok = false;
 
+    // prior weights of the re-weighted l1 scheme (Algorithm 1): W (9N reals,
+    // basis-major like u) or null for W = I; ||Psi W||_S^2 sets the clip
+    // level kappa ||Psi W||^2 and the primal step zeta / ||Psi W||^2
+    void *wgt = nullptr, *wcoef = nullptr;
+    double psiw2 = 1.0;
+    int psiw_iters = 0;
+    uint64_t gen = 0;   // bumped whenever captured graphs of this context go stale
+
     // parameters
     double eta = 0, zeta = 1, tau = 0.49, kappa = 1e-4, op_norm_sq = 0;
     int power_done = 0;
@@ -219,6 +227,8 @@ template <typename R> int sara_level0(ppd_ctx *c, const R *ll0, cudaStream_t s);
 template <typename R> int primal_step(ppd_ctx *c, cudaStream_t s);
 int reduce_primal_stats(ppd_ctx *c, cudaStream_t s);
 template <typename R> int scale_copy(ppd_ctx *c, const R *in, R *out, int64_t n, double a, cudaStream_t s);
+template <typename R> int reweight_from(ppd_ctx *c, R *coef_to_w, int64_t n, double omega, cudaStream_t s);
+template <typename R> int mul_sq(ppd_ctx *c, R *inout, const R *w, int64_t n, cudaStream_t s);
 template <typename R> int sumsq(ppd_ctx *c, const R *in, int64_t n, double *out_dev, cudaStream_t s);
 
 // host-side helpers

@@ -38,15 +38,17 @@ template <int NTH> __device__ void cta_sum3(double a, double b, double c, double
     }
 }
 
-// Primal step of Algorithm 3 with the Dirac basis of the prior step:
-// u0 <- clip(u0 + xt/3, kappa); ut_all = (u0 + ut)/3;
+// Primal step of Algorithm 3 with the Dirac basis of the prior step
+// (prior weights w0 of Algorithm 1, 1 when w0 is null; kappa here is the
+// clip level alpha = kappa ||Psi W||^2 and zeta the effective zeta / ||Psi W||^2):
+// u0 <- clip(u0 + w0 xt/3, kappa); ut_all = (w0 u0 + ut)/3;
 // xbar = P_C(x - tau (eta g + zeta ut_all)); xt = 2 xbar - x; x = xbar;
 // FP64 partials (||xbar - x||^2, ||xbar||^2, ||xbar - x0||^2) per CTA.
 template <typename R>
 __global__ void __launch_bounds__(NT) k_primal(R *__restrict__ x, R *__restrict__ xt, const R *__restrict__ g,
                                                const R *__restrict__ ut, R *__restrict__ u0,
-                                               const R *__restrict__ xtrue, int64_t N, R tau, R eta, R zeta,
-                                               R kappa, double *__restrict__ part) {
+                                               const R *__restrict__ w0, const R *__restrict__ xtrue, int64_t N,
+                                               R tau, R eta, R zeta, R kappa, double *__restrict__ part) {
     // per-thread sums in the working precision, Kahan-compensated, then a
     // fixed-order FP64 reduction across the CTA
     R sd = 0, sx = 0, se = 0, cd = 0, cx = 0, ce = 0;
@@ -58,10 +60,11 @@ __global__ void __launch_bounds__(NT) k_primal(R *__restrict__ x, R *__restrict_
     const R third = R(1.0 / 3.0);
     for (int64_t e = blockIdx.x * (int64_t)NT + threadIdx.x; e < N; e += (int64_t)gridDim.x * NT) {
         const R xo = x[e], xte = xt[e];
-        R un = u0[e] + xte * third;
+        const R wd = w0 ? w0[e] : R(1);
+        R un = u0[e] + wd * (xte * third);
         un = fmin(fmax(un, -kappa), kappa);
         u0[e] = un;
-        const R utot = (un + ut[e]) * third;
+        const R utot = (wd * un + ut[e]) * third;
         const R xb = fmax(R(0), xo - tau * (eta * g[e] + zeta * utot));
         xt[e] = R(2) * xb - xo;
         x[e] = xb;
@@ -101,6 +104,21 @@ template <typename R> __global__ void k_scale(const R *__restrict__ in, R *__res
     for (int64_t e = blockIdx.x * (int64_t)NT + threadIdx.x; e < n; e += (int64_t)gridDim.x * NT) out[e] = a * in[e];
 }
 
+// Weights of the re-weighted scheme (Eq. "reweighting"), in place over the
+// analysis coefficients: w = omega / (omega + |c|).
+template <typename R> __global__ void k_reweight(R *__restrict__ cw, int64_t n, R omega) {
+    for (int64_t e = blockIdx.x * (int64_t)NT + threadIdx.x; e < n; e += (int64_t)gridDim.x * NT)
+        cw[e] = omega / (omega + fabs(cw[e]));
+}
+
+// c <- w^2 c (one application of W^2 inside the power iteration on Psi W^2 Psi^dagger)
+template <typename R> __global__ void k_mul_sq(R *__restrict__ c, const R *__restrict__ w, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)NT + threadIdx.x; e < n; e += (int64_t)gridDim.x * NT) {
+        const R wv = w[e];
+        c[e] = (wv * wv) * c[e];
+    }
+}
+
 }  // namespace
 
 template <typename R> int primal_step(ppd_ctx *c, cudaStream_t s) {
@@ -108,8 +126,9 @@ template <typename R> int primal_step(ppd_ctx *c, cudaStream_t s) {
     PPD_CHECK(launch_begin(c, "primal", s, &site));
     k_primal<R><<<c->n_prim_blocks, NT, 0, s>>>(static_cast<R *>(c->x), static_cast<R *>(c->xt),
                                                 static_cast<const R *>(c->g), static_cast<const R *>(c->ut),
-                                                static_cast<R *>(c->u), static_cast<const R *>(c->xtrue), c->N,
-                                                (R)c->tau, (R)c->eta, (R)c->zeta, (R)c->kappa, c->prim_part);
+                                                static_cast<R *>(c->u), static_cast<const R *>(c->wgt),
+                                                static_cast<const R *>(c->xtrue), c->N, (R)c->tau, (R)c->eta,
+                                                (R)(c->zeta / c->psiw2), (R)(c->kappa * c->psiw2), c->prim_part);
     return launch_end(c, site, s);
 }
 
@@ -137,6 +156,24 @@ template <typename R> int scale_copy(ppd_ctx *c, const R *in, R *out, int64_t n,
     return launch_end(c, site, s);
 }
 
+template <typename R> int reweight_from(ppd_ctx *c, R *cw, int64_t n, double omega, cudaStream_t s) {
+    int site;
+    PPD_CHECK(launch_begin(c, "reweight", s, &site));
+    k_reweight<R><<<c->n_prim_blocks, NT, 0, s>>>(cw, n, (R)omega);
+    return launch_end(c, site, s);
+}
+
+template <typename R> int mul_sq(ppd_ctx *c, R *inout, const R *w, int64_t n, cudaStream_t s) {
+    int site;
+    PPD_CHECK(launch_begin(c, "reweight", s, &site));
+    k_mul_sq<R><<<c->n_prim_blocks, NT, 0, s>>>(inout, w, n);
+    return launch_end(c, site, s);
+}
+
+template int reweight_from<float>(ppd_ctx *, float *, int64_t, double, cudaStream_t);
+template int reweight_from<double>(ppd_ctx *, double *, int64_t, double, cudaStream_t);
+template int mul_sq<float>(ppd_ctx *, float *, const float *, int64_t, cudaStream_t);
+template int mul_sq<double>(ppd_ctx *, double *, const double *, int64_t, cudaStream_t);
 template int primal_step<float>(ppd_ctx *, cudaStream_t);
 template int primal_step<double>(ppd_ctx *, cudaStream_t);
 template int sumsq<float>(ppd_ctx *, const float *, int64_t, double *, cudaStream_t);

@@ -1,8 +1,10 @@
 // SARA dictionary Psi = (1/3) [Dirac, db1, ..., db8] (Section 2.2, Section
 // 5.1): separable periodic 2-D DWT, 4 levels, rows then columns per level,
 // Mallat quadrant layout per basis; and the prior dual step of Algorithm 3,
-// u_i <- (I - S_kappa)(u_i + Psi_i^dagger xt) = clip(u_i + Psi_i^dagger xt, +-kappa),
-// fused into the analysis output.
+// u_i <- (I - S_alpha)(u_i + W_i Psi_i^dagger xt) = clip(u_i + W_i Psi_i^dagger xt, +-alpha),
+// fused into the analysis output, with the prior weights W_i of the
+// re-weighted scheme (Algorithm 1; W = I unless set) and the clip level
+// alpha = kappa ||Psi W||_S^2.  D_b below is the orthonormal DWT of basis b.
 //
 // The eight wavelet bases run together (grid.z = basis); every pass maps one
 // thread to one output sample and reads its filter taps through the L1/L2.
@@ -61,8 +63,9 @@ template <typename R, int F> struct Taps {
 // guards skip the wrapped duplicates.
 template <typename R, int F>
 __device__ __forceinline__ void ana_tile(const R *__restrict__ src, int in_pitch, int n, int R0, int C0,
-                                         R *__restrict__ ll, int last, R *__restrict__ cb, int L, int mode, R kappa,
-                                         int b, R *tin, R *rowf) {
+                                         R *__restrict__ ll, int last, R *__restrict__ cb,
+                                         const R *__restrict__ wb, int L, int mode, R kappa, int b, R *tin,
+                                         R *rowf) {
     constexpr int EXT = 2 * TSA + F - 2;
     const Taps<R, F> f(b);
     const int h = n >> 1;
@@ -97,12 +100,13 @@ __device__ __forceinline__ void ana_tile(const R *__restrict__ src, int in_pitch
         if (!hi0 && !hi1 && !last) {
             ll[(R0 + rr) * h + C0 + cc] = acc;
         } else {
-            R *dst = cb + (int64_t)((hi0 ? h : 0) + R0 + rr) * L + (hi1 ? h : 0) + C0 + cc;
+            const int64_t off = (int64_t)((hi0 ? h : 0) + R0 + rr) * L + (hi1 ? h : 0) + C0 + cc;
+            R *dst = cb + off;
             const R cv = acc * R(1.0 / 3.0);
             if (mode == 0) {
                 *dst = cv;
             } else {
-                const R u = *dst + cv;
+                const R u = *dst + (wb ? wb[off] * cv : cv);
                 *dst = fmin(fmax(u, -kappa), kappa);
             }
         }
@@ -113,11 +117,13 @@ __device__ __forceinline__ void ana_tile(const R *__restrict__ src, int in_pitch
 //   in:   level input, basis b at in + b*in_bstride, row pitch in_pitch
 //   ll:   next level's input (compact, pitch h) unless last
 //   coef: coefficient images (basis b+1 at coef + (b+1)*N, pitch L), written
-//         (mode 0: c = W x / 3) or clip-updated (mode 1: u = clip(u + W x / 3, kappa))
+//         (mode 0: c = D x / 3) or clip-updated (mode 1: u = clip(u + w D x / 3, kappa))
+//   wgt:  prior weights (same layout as coef) or null (w = 1)
 template <typename R>
 __global__ void __launch_bounds__(NT) k_sara_ana(const R *__restrict__ in, int in_pitch, int64_t in_bstride, int n,
                                                  R *__restrict__ ll, int64_t ll_bstride, int last,
-                                                 R *__restrict__ coef, int L, int64_t N, int mode, R kappa) {
+                                                 R *__restrict__ coef, const R *__restrict__ wgt, int L, int64_t N,
+                                                 int mode, R kappa) {
     __shared__ R tin[AEXT * AEXT];
     __shared__ R rowf[AEXT * 2 * TSA];
     const int b = blockIdx.y;
@@ -126,15 +132,16 @@ __global__ void __launch_bounds__(NT) k_sara_ana(const R *__restrict__ in, int i
     const R *src = in + (int64_t)b * in_bstride;
     R *lb = ll + (int64_t)b * ll_bstride;
     R *cb = coef + (int64_t)(b + 1) * N;
+    const R *wb = wgt ? wgt + (int64_t)(b + 1) * N : nullptr;
     switch (b) {
-        case 0: ana_tile<R, 2>(src, in_pitch, n, R0, C0, lb, last, cb, L, mode, kappa, b, tin, rowf); break;
-        case 1: ana_tile<R, 4>(src, in_pitch, n, R0, C0, lb, last, cb, L, mode, kappa, b, tin, rowf); break;
-        case 2: ana_tile<R, 6>(src, in_pitch, n, R0, C0, lb, last, cb, L, mode, kappa, b, tin, rowf); break;
-        case 3: ana_tile<R, 8>(src, in_pitch, n, R0, C0, lb, last, cb, L, mode, kappa, b, tin, rowf); break;
-        case 4: ana_tile<R, 10>(src, in_pitch, n, R0, C0, lb, last, cb, L, mode, kappa, b, tin, rowf); break;
-        case 5: ana_tile<R, 12>(src, in_pitch, n, R0, C0, lb, last, cb, L, mode, kappa, b, tin, rowf); break;
-        case 6: ana_tile<R, 14>(src, in_pitch, n, R0, C0, lb, last, cb, L, mode, kappa, b, tin, rowf); break;
-        default: ana_tile<R, 16>(src, in_pitch, n, R0, C0, lb, last, cb, L, mode, kappa, b, tin, rowf); break;
+        case 0: ana_tile<R, 2>(src, in_pitch, n, R0, C0, lb, last, cb, wb, L, mode, kappa, b, tin, rowf); break;
+        case 1: ana_tile<R, 4>(src, in_pitch, n, R0, C0, lb, last, cb, wb, L, mode, kappa, b, tin, rowf); break;
+        case 2: ana_tile<R, 6>(src, in_pitch, n, R0, C0, lb, last, cb, wb, L, mode, kappa, b, tin, rowf); break;
+        case 3: ana_tile<R, 8>(src, in_pitch, n, R0, C0, lb, last, cb, wb, L, mode, kappa, b, tin, rowf); break;
+        case 4: ana_tile<R, 10>(src, in_pitch, n, R0, C0, lb, last, cb, wb, L, mode, kappa, b, tin, rowf); break;
+        case 5: ana_tile<R, 12>(src, in_pitch, n, R0, C0, lb, last, cb, wb, L, mode, kappa, b, tin, rowf); break;
+        case 6: ana_tile<R, 14>(src, in_pitch, n, R0, C0, lb, last, cb, wb, L, mode, kappa, b, tin, rowf); break;
+        default: ana_tile<R, 16>(src, in_pitch, n, R0, C0, lb, last, cb, wb, L, mode, kappa, b, tin, rowf); break;
     }
 }
 
@@ -144,8 +151,8 @@ __global__ void __launch_bounds__(NT) k_sara_ana(const R *__restrict__ in, int i
 // and columns R0 - F/2 + 1 ... R0 + TS - 1 (mod h).  Returns this thread's
 // output (mm = tid / 2TS, nn = tid % 2TS; NT == 4 TS^2).
 template <typename R, int F>
-__device__ __forceinline__ R syn_tile(const R *__restrict__ cb, const R *__restrict__ sl, int from_coef, int L, int n,
-                                      int R0, int C0, int b, R *qs, R *tl, R *th) {
+__device__ __forceinline__ R syn_tile(const R *__restrict__ cb, const R *__restrict__ wb, const R *__restrict__ sl,
+                                      int from_coef, int L, int n, int R0, int C0, int b, R *qs, R *tl, R *th) {
     constexpr int EXT = TS + F / 2 - 1;
     const Taps<R, F> f(b);
     const int h = n >> 1;
@@ -155,10 +162,13 @@ __device__ __forceinline__ R syn_tile(const R *__restrict__ cb, const R *__restr
         const int i = r / EXT, j = r % EXT;
         const int gi = wrap(base_r + i, h), gj = wrap(base_c + j, h);
         R v;
-        if (qd == 0) v = from_coef ? cb[(int64_t)gi * L + gj] : sl[gi * h + gj];
-        else if (qd == 1) v = cb[(int64_t)gi * L + h + gj];
-        else if (qd == 2) v = cb[(int64_t)(h + gi) * L + gj];
-        else v = cb[(int64_t)(h + gi) * L + h + gj];
+        if (qd == 0 && !from_coef) {
+            v = sl[gi * h + gj];
+        } else {
+            const int64_t off = (int64_t)((qd & 2) ? h + gi : gi) * L + ((qd & 1) ? h : 0) + gj;
+            v = cb[off];
+            if (wb) v *= wb[off];
+        }
         qs[qd * SEXT * SEXT + i * SEXT + j] = v;
     }
     __syncthreads();
@@ -193,118 +203,60 @@ __device__ __forceinline__ R syn_tile(const R *__restrict__ cb, const R *__restr
 }
 
 template <typename R>
-__device__ __forceinline__ R syn_tile_b(int b, const R *cb, const R *sl, int from_coef, int L, int n, int R0, int C0,
-                                        R *qs, R *tl, R *th) {
+__device__ __forceinline__ R syn_tile_b(int b, const R *cb, const R *wb, const R *sl, int from_coef, int L, int n,
+                                        int R0, int C0, R *qs, R *tl, R *th) {
     switch (b) {
-        case 0: return syn_tile<R, 2>(cb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
-        case 1: return syn_tile<R, 4>(cb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
-        case 2: return syn_tile<R, 6>(cb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
-        case 3: return syn_tile<R, 8>(cb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
-        case 4: return syn_tile<R, 10>(cb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
-        case 5: return syn_tile<R, 12>(cb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
-        case 6: return syn_tile<R, 14>(cb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
-        default: return syn_tile<R, 16>(cb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 0: return syn_tile<R, 2>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 1: return syn_tile<R, 4>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 2: return syn_tile<R, 6>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 3: return syn_tile<R, 8>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 4: return syn_tile<R, 10>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 5: return syn_tile<R, 12>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 6: return syn_tile<R, 14>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        default: return syn_tile<R, 16>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
     }
 }
 
 // One synthesis level l > 0 for all 8 bases (grid.y = basis): out_b (compact
-// pitch n) = W_b^T of (LL' block, detail quadrants).  LL' comes from the
-// coefficients at the coarsest level (from_coef) or from the coarser level's
-// output sll.
+// pitch n) = D_b^T of (LL' block, detail quadrants), coefficients times the
+// prior weights when wgt is set.  LL' comes from the coefficients at the
+// coarsest level (from_coef) or from the coarser level's output sll.
 template <typename R>
-__global__ void __launch_bounds__(NT) k_sara_syn(const R *__restrict__ coef, int L, int64_t N, const R *__restrict__ sll,
-                                                 int from_coef, int64_t sll_bstride, int n, R *__restrict__ out,
-                                                 int64_t out_bstride) {
+__global__ void __launch_bounds__(NT) k_sara_syn(const R *__restrict__ coef, const R *__restrict__ wgt, int L, int64_t N,
+                                                 const R *__restrict__ sll, int from_coef, int64_t sll_bstride, int n,
+                                                 R *__restrict__ out, int64_t out_bstride) {
     __shared__ R qs[4 * SEXT * SEXT];
     __shared__ R tl[2 * TS * SEXT], th[2 * TS * SEXT];
     const int b = blockIdx.y;
     const int h = n / 2, tpd = h > TS ? h / TS : 1;
     const int R0 = (blockIdx.x / tpd) * TS, C0 = (blockIdx.x % tpd) * TS;
-    const R v = syn_tile_b<R>(b, coef + (int64_t)(b + 1) * N, sll + (int64_t)b * sll_bstride, from_coef, L, n, R0, C0,
-                              qs, tl, th);
+    const R v = syn_tile_b<R>(b, coef + (int64_t)(b + 1) * N, wgt ? wgt + (int64_t)(b + 1) * N : nullptr,
+                              sll + (int64_t)b * sll_bstride, from_coef, L, n, R0, C0, qs, tl, th);
     const int mm = threadIdx.x / (2 * TS), nnl = threadIdx.x % (2 * TS);
     if (2 * R0 + mm < n && 2 * C0 + nnl < n)
         out[(int64_t)b * out_bstride + (int64_t)(2 * R0 + mm) * n + 2 * C0 + nnl] = v;
 }
 
-// Finest synthesis level, all 8 bases summed in order per output sample.
-// mode 0 (operator):  out = scale * (dirac + sum_b W_b^T c_b)
-// mode 1 (PPD step):  u0 <- clip(u0 + xt/3, kappa); ut = (u0 + sum_b W_b^T u_b)/3;
-//                     xbar = max(0, x - tau (eta g + zeta ut)); xt = 2 xbar - x; x = xbar
-//                     with FP64 partial sums (||dx||^2, ||xbar||^2, ||xbar - x0||^2) per CTA.
-template <typename R> struct PrimalArgs {
-    R *x, *xt, *u0;
-    const R *g, *xtrue;
-    R tau, eta, zeta, kappa;
-    double *part;
-};
-
+// Finest synthesis level, the 8 wavelet bases summed in order per output
+// sample: out = scale * (dirac + sum_b D_b^T (w_b c_b)) (dirac may be null).
 template <typename R>
-__global__ void __launch_bounds__(NT) k_sara_syn0(const R *__restrict__ coef, int L, int64_t N, const R *__restrict__ sll,
-                                                  int from_coef, int64_t sll_bstride, int mode,
-                                                  const R *__restrict__ dirac, R scale, R *__restrict__ out,
-                                                  PrimalArgs<R> P) {
+__global__ void __launch_bounds__(NT) k_sara_syn0(const R *__restrict__ coef, const R *__restrict__ wgt, int L,
+                                                  int64_t N, const R *__restrict__ sll, int from_coef,
+                                                  int64_t sll_bstride, const R *__restrict__ dirac, R scale,
+                                                  R *__restrict__ out) {
     __shared__ R qs[4 * SEXT * SEXT];
     __shared__ R tl[2 * TS * SEXT], th[2 * TS * SEXT];
-    __shared__ double red[3][NT / 32];
     const int n = L, h = n / 2, tpd = h > TS ? h / TS : 1;
     const int R0 = (blockIdx.x / tpd) * TS, C0 = (blockIdx.x % tpd) * TS;
     R acc = 0;
 #pragma unroll
     for (int b = 0; b < N_WAVELETS; ++b)
-        acc += syn_tile_b<R>(b, coef + (int64_t)(b + 1) * N, sll + (int64_t)b * sll_bstride, from_coef, L, n, R0, C0,
-                             qs, tl, th);
+        acc += syn_tile_b<R>(b, coef + (int64_t)(b + 1) * N, wgt ? wgt + (int64_t)(b + 1) * N : nullptr,
+                             sll + (int64_t)b * sll_bstride, from_coef, L, n, R0, C0, qs, tl, th);
     const int mm = threadIdx.x / (2 * TS), nnl = threadIdx.x % (2 * TS);
-    const bool valid = (2 * R0 + mm < n) && (2 * C0 + nnl < n);
-    const int64_t idx = (int64_t)(2 * R0 + mm) * L + 2 * C0 + nnl;
-    double sd = 0, sx = 0, se = 0;
-    if (valid) {
-        if (mode == 0) {
-            out[idx] = scale * ((dirac ? dirac[idx] : R(0)) + acc);
-        } else {
-            const R third = R(1.0 / 3.0);
-            const R xo = P.x[idx], xte = P.xt[idx];
-            R un = P.u0[idx] + xte * third;
-            un = fmin(fmax(un, -P.kappa), P.kappa);
-            P.u0[idx] = un;
-            const R utot = (un + acc) * third;
-            const R xb = fmax(R(0), xo - P.tau * (P.eta * P.g[idx] + P.zeta * utot));
-            P.xt[idx] = R(2) * xb - xo;
-            P.x[idx] = xb;
-            const double dd = (double)xb - (double)xo;
-            sd = dd * dd;
-            sx = (double)xb * (double)xb;
-            if (P.xtrue) {
-                const double de = (double)xb - (double)P.xtrue[idx];
-                se = de * de;
-            }
-        }
-    }
-    if (mode == 1) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            sd += __shfl_down_sync(0xffffffffu, sd, o);
-            sx += __shfl_down_sync(0xffffffffu, sx, o);
-            se += __shfl_down_sync(0xffffffffu, se, o);
-        }
-        const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        if (lane == 0) {
-            red[0][wid] = sd;
-            red[1][wid] = sx;
-            red[2][wid] = se;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double a0 = 0, a1 = 0, a2 = 0;
-            for (int i = 0; i < NT / 32; ++i) {
-                a0 += red[0][i];
-                a1 += red[1][i];
-                a2 += red[2][i];
-            }
-            P.part[3 * (int64_t)blockIdx.x] = a0;
-            P.part[3 * (int64_t)blockIdx.x + 1] = a1;
-            P.part[3 * (int64_t)blockIdx.x + 2] = a2;
-        }
+    if ((2 * R0 + mm < n) && (2 * C0 + nnl < n)) {
+        const int64_t idx = (int64_t)(2 * R0 + mm) * L + 2 * C0 + nnl;
+        out[idx] = scale * ((dirac ? dirac[idx] : R(0)) + acc);
     }
 }
 
@@ -315,9 +267,11 @@ template <typename R> __global__ void k_scale_copy(const R *__restrict__ in, R *
 inline unsigned nblk(int64_t work) { return (unsigned)std::min<int64_t>((work + NT - 1) / NT, 152 * 8); }
 inline int tiles(int h, int ts) { return h > ts ? (h / ts) * (h / ts) : 1; }
 
-// Analysis of all levels (tiled).  mode 0 writes c = W x / 3, mode 1
-// clip-updates u.
+// Analysis of all levels (tiled).  mode 0 writes c = D x / 3, mode 1
+// clip-updates u with the prior weights and the clip level kappa ||Psi W||^2.
 template <typename R> int analysis_all(ppd_ctx *c, const R *x, R *coef, int mode, cudaStream_t s) {
+    const R *wgt = mode == 1 ? static_cast<const R *>(c->wgt) : nullptr;
+    const R alpha = (R)(c->kappa * c->psiw2);
     const int L = c->L0;
     const int64_t N = c->N;
     R *ll[2] = {static_cast<R *>(c->wtmp), static_cast<R *>(c->wtmp) + (int64_t)N_WAVELETS * (L / 2) * (L / 2)};
@@ -331,7 +285,7 @@ template <typename R> int analysis_all(ppd_ctx *c, const R *x, R *coef, int mode
         const int64_t bstride = l == 0 ? 0 : ll_stride;
         PPD_CHECK(launch_begin(c, "sara_analysis", s, &site));
         k_sara_ana<R><<<dim3(tiles(h, TSA), N_WAVELETS), NT, 0, s>>>(in, pitch, bstride, n, ll[l & 1], ll_stride, last,
-                                                                     coef, L, N, mode, (R)c->kappa);
+                                                                     coef, wgt, L, N, mode, alpha);
         PPD_CHECK(launch_end(c, site, s));
     }
     return PPD_OK;
@@ -339,7 +293,8 @@ template <typename R> int analysis_all(ppd_ctx *c, const R *x, R *coef, int mode
 
 // Synthesis of the 8 wavelet bases, levels coarsest .. 1 (tiled); returns
 // the buffer holding the LL' block of level 0.
-template <typename R> int synthesis_levels(ppd_ctx *c, const R *coef, const R **ll0, cudaStream_t s) {
+template <typename R>
+int synthesis_levels(ppd_ctx *c, const R *coef, const R *wgt, const R **ll0, cudaStream_t s) {
     const int L = c->L0;
     const int64_t N = c->N;
     const int64_t st = (int64_t)(L / 2) * (L / 2);
@@ -350,7 +305,7 @@ template <typename R> int synthesis_levels(ppd_ctx *c, const R *coef, const R **
         const int n = L >> l, h = n / 2;
         const bool coarsest = (l == c->levels - 1);
         PPD_CHECK(launch_begin(c, "sara_synthesis", s, &site));
-        k_sara_syn<R><<<dim3(tiles(h, TS), N_WAVELETS), NT, 0, s>>>(coef, L, N, coarsest ? coef : prev,
+        k_sara_syn<R><<<dim3(tiles(h, TS), N_WAVELETS), NT, 0, s>>>(coef, wgt, L, N, coarsest ? coef : prev,
                                                                     coarsest ? 1 : 0, st, n, buf[k & 1], st);
         PPD_CHECK(launch_end(c, site, s));
         prev = buf[k & 1];
@@ -360,29 +315,16 @@ template <typename R> int synthesis_levels(ppd_ctx *c, const R *coef, const R **
 }
 
 template <typename R>
-int synthesis_final(ppd_ctx *c, const R *coef, const R *ll0, int mode, const R *dirac, R scale, R *out,
+int synthesis_final(ppd_ctx *c, const R *coef, const R *wgt, const R *ll0, const R *dirac, R scale, R *out,
                     cudaStream_t s) {
     const int L = c->L0;
     const int h = L / 2;
     const int64_t st = (int64_t)(L / 2) * (L / 2);
-    PrimalArgs<R> P{};
-    if (mode == 1) {
-        P.x = static_cast<R *>(c->x);
-        P.xt = static_cast<R *>(c->xt);
-        P.u0 = static_cast<R *>(c->u);
-        P.g = static_cast<const R *>(c->g);
-        P.xtrue = static_cast<const R *>(c->xtrue);
-        P.tau = (R)c->tau;
-        P.eta = (R)c->eta;
-        P.zeta = (R)c->zeta;
-        P.kappa = (R)c->kappa;
-        P.part = c->prim_part;
-    }
     const bool from_coef = ll0 == nullptr;   // levels == 1: LL' straight from the coefficients
     int site;
-    PPD_CHECK(launch_begin(c, mode == 1 ? "sara_synthesis_primal" : "sara_synthesis", s, &site));
-    k_sara_syn0<R><<<tiles(h, TS), NT, 0, s>>>(coef, L, c->N, from_coef ? coef : ll0, from_coef ? 1 : 0, st, mode,
-                                                dirac, scale, out, P);
+    PPD_CHECK(launch_begin(c, "sara_synthesis", s, &site));
+    k_sara_syn0<R><<<tiles(h, TS), NT, 0, s>>>(coef, wgt, L, c->N, from_coef ? coef : ll0, from_coef ? 1 : 0, st,
+                                                dirac, scale, out);
     return launch_end(c, site, s);
 }
 
@@ -492,24 +434,25 @@ template <typename R> int psi_analysis(ppd_ctx *c, const R *x, R *coef, cudaStre
 
 template <typename R> int psi_synthesis(ppd_ctx *c, const R *coef, R *x, cudaStream_t s) {
     const R *ll0 = nullptr;
-    PPD_CHECK(synthesis_levels<R>(c, coef, &ll0, s));
-    return synthesis_final<R>(c, coef, ll0, 0, coef, R(1.0 / 3.0), x, s);
+    PPD_CHECK(synthesis_levels<R>(c, coef, nullptr, &ll0, s));
+    return synthesis_final<R>(c, coef, nullptr, ll0, coef, R(1.0 / 3.0), x, s);
 }
 
 // Prior dual step of Algorithm 3 for the 8 wavelet bases up to the level-0
-// synthesis: u_b <- clip(u_b + Psi_b^dagger xt, kappa), then the synthesis of
-// levels coarsest .. 1.  Needs only xt and u, so it can run beside the data
-// branch of the iteration.
+// synthesis: u_b <- clip(u_b + W_b Psi_b^dagger xt, alpha), then the synthesis
+// of W_b u_b for levels coarsest .. 1.  Needs only xt and u, so it can run
+// beside the data branch of the iteration.
 template <typename R> int sara_prior_branch(ppd_ctx *c, const R **ll0, cudaStream_t s) {
     R *u = static_cast<R *>(c->u);
     PPD_CHECK(analysis_all<R>(c, static_cast<const R *>(c->xt), u, 1, s));
-    return synthesis_levels<R>(c, u, ll0, s);
+    return synthesis_levels<R>(c, u, static_cast<const R *>(c->wgt), ll0, s);
 }
 
-// Level-0 synthesis summed over the 8 wavelet bases: ut = sum_b W_b^T u_b
+// Level-0 synthesis summed over the 8 wavelet bases: ut = sum_b D_b^T (W_b u_b)
 // (the Dirac basis and the 1/3 are applied in the primal step).
 template <typename R> int sara_level0(ppd_ctx *c, const R *ll0, cudaStream_t s) {
-    return synthesis_final<R>(c, static_cast<const R *>(c->u), ll0, 0, nullptr, R(1), static_cast<R *>(c->ut), s);
+    return synthesis_final<R>(c, static_cast<const R *>(c->u), static_cast<const R *>(c->wgt), ll0, nullptr, R(1),
+                              static_cast<R *>(c->ut), s);
 }
 
 

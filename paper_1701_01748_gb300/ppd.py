@@ -50,7 +50,8 @@ class ppd_params(ct.Structure):
                 ("kappa", ct.c_double), ("op_norm_sq", ct.c_double), ("power_iters_done", ct.c_int32),
                 ("K0", ct.c_int32), ("K1", ct.c_int32), ("tile", ct.c_int32), ("chunk", ct.c_int32),
                 ("n_chunks", ct.c_int64),
-                ("M", ct.c_int64), ("convergence_lhs", ct.c_double)]
+                ("M", ct.c_int64), ("convergence_lhs", ct.c_double),
+                ("psiw_norm_sq", ct.c_double), ("alpha", ct.c_double)]
 
 
 class PPDError(RuntimeError):
@@ -88,6 +89,9 @@ def _lib():
             "ppd_group_iterate": (I, [P, I32]),
             "ppd_group_destroy": (V, [P]),
             "ppd_set_state": (I, [P, P, I64]),
+            "ppd_set_prior_weights": (I, [P, D, I64]),
+            "ppd_reweight": (I, [P, ct.c_double]),
+            "ppd_get_prior_weights": (I, [P, D, I64]),
             "ppd_op_forward": (I, [P, P, P, P]),
             "ppd_op_adjoint": (I, [P, P, P, P]),
             "ppd_op_adjoint_noalloc": (I, [P, P, P, P]),
@@ -245,6 +249,25 @@ def ppd_set_state(ctx: int, blob: bytes) -> None:
     _check(_lib().ppd_set_state(ctx, ct.cast(buf, ct.c_void_p), len(blob)), "ppd_set_state")
 
 
+def ppd_set_prior_weights(ctx: int, w) -> None:
+    """W of the re-weighted scheme (9 x n0 x n1, basis-major), or None for W = I."""
+    if w is None:
+        _check(_lib().ppd_set_prior_weights(ctx, None, 0), "ppd_set_prior_weights")
+        return
+    a = np.ascontiguousarray(w, dtype=np.float64).reshape(-1)
+    _check(_lib().ppd_set_prior_weights(ctx, _dptr(a), a.size), "ppd_set_prior_weights")
+
+
+def ppd_reweight(ctx: int, omega: float) -> None:
+    _check(_lib().ppd_reweight(ctx, float(omega)), "ppd_reweight")
+
+
+def ppd_get_prior_weights(ctx: int, n0: int, n1: int) -> np.ndarray:
+    out = np.empty(9 * n0 * n1)
+    _check(_lib().ppd_get_prior_weights(ctx, _dptr(out), out.size), "ppd_get_prior_weights")
+    return out.reshape(9, n0, n1)
+
+
 def ppd_op_forward(ctx: int, x_dev: int, y_dev: int, stream=None) -> None:
     _check(_lib().ppd_op_forward(ctx, x_dev, y_dev, _stream(stream)), "ppd_op_forward")
 
@@ -323,6 +346,23 @@ class Solver:
 
     def image(self) -> np.ndarray:
         return ppd_get_image(self.ctx, self.L, self.L)
+
+    def reweighted(self, n_reweights: int, iters: int, omega0: float = 1e-2, factor: float = 0.25,
+                   stats_every: int = 0):
+        """Algorithm 1: n_reweights + 1 warm-started PPD runs of `iters` iterations,
+        re-weighting with omega^(k) = factor^k omega0 between consecutive runs."""
+        hist = []
+        for k in range(n_reweights + 1):
+            if k > 0:
+                ppd_reweight(self.ctx, omega0 * factor ** k)
+            if stats_every > 0:
+                for _ in range(iters // stats_every):
+                    hist.append(self.iterate(stats_every))
+                if iters % stats_every:
+                    hist.append(self.iterate(iters % stats_every))
+            else:
+                self.iterate(iters, stats=False)
+        return hist
 
     def params(self) -> dict:
         return ppd_get_params(self.ctx)
