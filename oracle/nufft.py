@@ -131,16 +131,20 @@ def interpolate(grid: np.ndarray, P: Plan) -> np.ndarray:
 
 
 def interpolate_adjoint(v: np.ndarray, P: Plan) -> np.ndarray:
-    """G^H: scatter-add w0 w1 v onto the grid (the weights are real)."""
+    """G^H: scatter-add w0 w1 v onto the grid (the weights are real).
+
+    The 8 taps along axis 1 of one axis-0 tap go through one bincount (the
+    scatter of all (m, b) pairs for that a), so the K0 x K1 histogram is
+    built 2 J times rather than 2 J^2 times.
+    """
     K0, K1 = P.K0, P.K1
     re = np.zeros(K0 * K1)
     im = np.zeros(K0 * K1)
     for a in range(P.J):
-        for b in range(P.J):
-            c = P.w[0][:, a] * P.w[1][:, b] * v
-            lin = P.idx[0][:, a] * K1 + P.idx[1][:, b]
-            re += np.bincount(lin, weights=c.real, minlength=K0 * K1)
-            im += np.bincount(lin, weights=c.imag, minlength=K0 * K1)
+        c = (P.w[0][:, a] * v)[:, None] * P.w[1]                 # (M, J): w0[m,a] w1[m,b] v[m]
+        lin = (P.idx[0][:, a] * K1)[:, None] + P.idx[1]          # (M, J) linear cells
+        re += np.bincount(lin.ravel(), weights=c.real.ravel(), minlength=K0 * K1)
+        im += np.bincount(lin.ravel(), weights=c.imag.ravel(), minlength=K0 * K1)
     return (re + 1j * im).reshape(K0, K1)
 
 

@@ -30,6 +30,15 @@ Readings (the paper is silent or its printed step is garbled):
 Prior weights W (Algorithm 1) enter the prior step as printed in Algorithm
 3; ``oracle/reweight.py`` sets them.
 
+Randomised active sets (Algorithm 3, "generate sets P and D"; Section 4.4:
+nonzero probabilities, independent and identical draws along the
+iterations): the draws are inputs (``paper_1701_01748_gb300.synth.active_sets``
+makes seeded Bernoulli masks).  A data block j outside D keeps v_j (so its
+gridded contribution is unchanged) and its Algorithm 2 warm start p_j; a
+basis i outside P keeps u_i (so Psi_i u_i is unchanged).  Reading (the paper
+is silent): a block that has never been active starts Algorithm 2 from
+P_B(z), as every block does on the first iteration.
+
 Parity: the invariants of the whole iteration (feasibility, positivity,
 PPD and PD reaching the same minimiser, U = I reducing to PD) are pinned by
 tests; the trajectory itself is "parity unpinned" beyond them.
@@ -128,44 +137,58 @@ class State:
     xt: np.ndarray
     u: np.ndarray
     v: np.ndarray
-    p: np.ndarray | None = None
+    p: np.ndarray            # Algorithm 2 output of each block's last active iteration
+    seen: np.ndarray         # per block: has been active (p_j holds a prox output)
     t: int = 0
 
 
 def init_state(S: Setup) -> State:
     L0, L1 = S.P.L0, S.P.L1
     return State(x=np.zeros((L0, L1)), xt=np.zeros((L0, L1)),
-                 u=np.zeros((sara.N_BASES, L0, L1)), v=np.zeros(S.P.M, np.complex128))
+                 u=np.zeros((sara.N_BASES, L0, L1)), v=np.zeros(S.P.M, np.complex128),
+                 p=np.zeros(S.P.M, np.complex128), seen=np.zeros(S.n_blocks, dtype=bool))
 
 
-def iterate(st: State, S: Setup) -> dict:
-    """One iteration of Algorithm 3 (lambda = 1, all blocks and bases active)."""
+def iterate(st: State, S: Setup, active_blocks=None, active_bases=None) -> dict:
+    """One iteration of Algorithm 3 (lambda = 1).
+
+    active_blocks (d booleans, the set D) and active_bases (9 booleans, the
+    set P, Dirac first) select the dual variables updated this iteration;
+    None means all (no randomisation, Section 5.1).
+    """
     P = S.P
+    act_d = np.ones(S.n_blocks, bool) if active_blocks is None else np.asarray(active_blocks, bool)
+    act_p = np.ones(sara.N_BASES, bool) if active_bases is None else np.asarray(active_bases, bool)
     # forward: a = F Z xt, Theta G a
     phix = P.theta * nufft.interpolate(np.fft.fft2(nufft.zero_pad_scale(st.xt, P)), P)
     res = np.array([np.linalg.norm(phix[m] - S.yw[m]) for m in S.members])
-    # dual data step (Algorithm 2 inside the Moreau identity)
+    # dual data step (Algorithm 2 inside the Moreau identity) for the blocks in D;
+    # the others keep v_j and p_j
     z = st.v / S.U + phix
-    p = np.empty_like(z)
+    v = st.v.copy()
+    p = st.p.copy()
     for j, m in enumerate(S.members):
-        if m.size == 0:
+        if m.size == 0 or not act_d[j]:
             continue
         if S.inner_init == "current":
             start = z[m]
-        elif st.p is None:
+        elif not st.seen[j]:
             start = prox.proj_l2ball(z[m], S.yw[m], S.eps[j])
         else:
             start = st.p[m]
         p[m] = prox.ellipsoid_prox_fb(z[m], S.yw[m], S.eps[j], S.U[m], S.n_itr,
                                       start=start, mu=S.mu[j])
-    v = S.U * (z - p)
+        v[m] = S.U[m] * (z[m] - p[m])
     g = nufft.phi_adjoint(v, P)
-    # prior step: clip (I - S_{kappa ||Psi W||^2}) of u + W Psi^dagger xt, then
-    # synthesis of W u; zeta = 1/||Psi W||^2 (W = I: ||Psi|| = 1)
+    # prior step for the bases in P: clip (I - S_{kappa ||Psi W||^2}) of
+    # u + W Psi^dagger xt; the others keep u_i; then the synthesis of W u;
+    # zeta = 1/||Psi W||^2 (W = I: ||Psi|| = 1)
     c = sara.psi_adjoint(st.xt, S.levels, S.hs)
     if S.W is not None:
         c = S.W * c
     u = prox.clip_complement(st.u + c, S.kappa * S.psiw_sq)
+    if not act_p.all():
+        u = np.where(act_p[:, None, None], u, st.u)
     ut = sara.psi(u if S.W is None else S.W * u, S.levels, S.hs)
     zeta = S.zeta / S.psiw_sq
     # primal step
@@ -174,6 +197,7 @@ def iterate(st: State, S: Setup) -> dict:
     nx = float(np.linalg.norm(xbar))
     xt = 2.0 * xbar - st.x
     st.x, st.xt, st.u, st.v, st.p = xbar, xt, u, v, p
+    st.seen = st.seen | act_d
     st.t += 1
     stats = dict(residual=res, rel_var=dx / nx if nx > 0 else float("inf"))
     if S.x_true is not None:

@@ -28,8 +28,9 @@ import math
 
 import numpy as np
 
-__all__ = ["Problem", "CONFIGS", "make_problem", "make_batch", "sky_image", "sample_uv",
-           "sample_uv_ggd", "radial_blocks", "exact_visibilities"]
+__all__ = ["Problem", "CONFIGS", "make_problem", "make_batch", "make_batch32", "sky_image", "sample_uv",
+           "sample_uv_ggd", "radial_blocks", "exact_visibilities", "gaussian_visibilities",
+           "point_visibilities", "active_sets"]
 
 
 @dataclasses.dataclass
@@ -60,11 +61,13 @@ CONFIGS = {
     "c2_512": dict(L=512, M=524288, n_blocks=16, uv_sigma=0.1, seed=1702),
     # 1024x1024, 4M visibilities, 64 radial blocks
     "c3_1024": dict(L=1024, M=4194304, n_blocks=64, uv_sigma=0.1, seed=1703),
+    # 4096x4096, 64M visibilities, 256 radial blocks (compact blobs, analytic blob spectra)
+    "c5_4096": dict(L=4096, M=67108864, n_blocks=256, uv_sigma=0.1, seed=1705, compact=True),
 }
 
 
 def sky_image(L: int, rng: np.random.Generator, n_points: int = 20,
-              n_blobs: int = 3):
+              n_blobs: int = 3, compact: bool = False, params_out: list | None = None):
     """Positive test sky: point sources plus elliptical Gaussian blobs.
 
     Returns (points, blob_image): points is a list of (row, col, flux) with
@@ -72,7 +75,11 @@ def sky_image(L: int, rng: np.random.Generator, n_points: int = 20,
     Point fluxes are log-uniform in [1e-3, 1]; blob centres uniform in the
     central half, major-axis std uniform in [0.02L, 0.08L], axis ratio uniform
     in [0.3, 1], position angle uniform in [0, pi), peak log-uniform in
-    [1e-2, 1e-1].
+    [1e-2, 1e-1].  compact=True keeps every blob at least 6 standard
+    deviations inside the image (centres in [0.3L, 0.7L], major-axis std in
+    [0.03L, 0.05L]) so that its spectrum is the analytic Gaussian one to
+    ~1e-8 (see gaussian_visibilities); the draws are the same.  params_out,
+    if given, receives (c0, c1, smaj, smin, angle, peak) per blob.
     """
     pos = rng.integers(0, L, size=(n_points, 2))
     flux = 10.0 ** rng.uniform(-3.0, 0.0, size=n_points)
@@ -80,12 +87,16 @@ def sky_image(L: int, rng: np.random.Generator, n_points: int = 20,
     r = np.arange(L, dtype=np.float64)
     R0, R1 = np.meshgrid(r, r, indexing="ij")
     blob = np.zeros((L, L))
+    clo, chi = (0.3 * L, 0.7 * L) if compact else (L / 4, 3 * L / 4)
+    slo, shi = (0.03 * L, 0.05 * L) if compact else (0.02 * L, 0.08 * L)
     for _ in range(n_blobs):
-        c0, c1 = rng.uniform(L / 4, 3 * L / 4, size=2)
-        smaj = rng.uniform(0.02 * L, 0.08 * L)
+        c0, c1 = rng.uniform(clo, chi, size=2)
+        smaj = rng.uniform(slo, shi)
         smin = smaj * rng.uniform(0.3, 1.0)
         ang = rng.uniform(0.0, math.pi)
         peak = 10.0 ** rng.uniform(-2.0, -1.0)
+        if params_out is not None:
+            params_out.append((c0, c1, smaj, smin, ang, peak))
         ca, sa = math.cos(ang), math.sin(ang)
         d0, d1 = R0 - c0, R1 - c1
         a = ca * d0 + sa * d1
@@ -165,7 +176,38 @@ def exact_visibilities(points, blob: np.ndarray, omega: np.ndarray,
     return y
 
 
-def make_batch(n: int = 8, seed: int = 1704, sides=(128, 256), ratio=(2.0, 8.0), blocks=(4, 32)):
+def gaussian_visibilities(params, omega: np.ndarray, L: int, chunk: int = 1 << 22) -> np.ndarray:
+    """Spectra of the Gaussian blobs at omega (sign and origin of exact_visibilities):
+    for a blob A exp(-(a^2/smaj^2 + b^2/smin^2)/2) centred at c, the sum over the
+    integer lattice is A 2 pi smaj smin exp(-omega^T S omega / 2) exp(-i <omega, c - L/2>)
+    with omega^T S omega = smaj^2 (cos t w0 + sin t w1)^2 + smin^2 (-sin t w0 + cos t w1)^2
+    (Poisson summation; the aliased terms and the part of the blob outside
+    the image are below 1e-8 for compact blobs)."""
+    M = omega.shape[0]
+    y = np.zeros(M, dtype=np.complex128)
+    for i in range(0, M, chunk):
+        w0, w1 = omega[i:i + chunk, 0], omega[i:i + chunk, 1]
+        for (c0, c1, smaj, smin, ang, peak) in params:
+            ca, sa = math.cos(ang), math.sin(ang)
+            q = (smaj * (ca * w0 + sa * w1)) ** 2 + (smin * (-sa * w0 + ca * w1)) ** 2
+            amp = peak * 2.0 * math.pi * smaj * smin * np.exp(-0.5 * q)
+            y[i:i + chunk] += amp * np.exp(-1j * (w0 * (c0 - L / 2) + w1 * (c1 - L / 2)))
+    return y
+
+
+def point_visibilities(points, omega: np.ndarray, L: int, chunk: int = 1 << 22) -> np.ndarray:
+    """Exact spectra of the point sources (chunked)."""
+    M = omega.shape[0]
+    y = np.zeros(M, dtype=np.complex128)
+    for i in range(0, M, chunk):
+        w0, w1 = omega[i:i + chunk, 0], omega[i:i + chunk, 1]
+        for (p0, p1, f) in points:
+            y[i:i + chunk] += f * np.exp(-1j * (w0 * (p0 - L / 2) + w1 * (p1 - L / 2)))
+    return y
+
+
+def make_batch(n: int = 8, seed: int = 1704, sides=(128, 256), ratio=(2.0, 8.0), blocks=(4, 32),
+               compact: bool = False):
     """n independent problems of different sizes: side log-uniform over `sides`
     (powers of two), M = r * L^2 with r log-uniform in `ratio`, block count
     uniform in `blocks`, strongly non-uniform coverage (std 0.1 pi)."""
@@ -176,22 +218,33 @@ def make_batch(n: int = 8, seed: int = 1704, sides=(128, 256), ratio=(2.0, 8.0),
         r = math.exp(rng.uniform(math.log(ratio[0]), math.log(ratio[1])))
         d = int(rng.integers(blocks[0], blocks[1] + 1))
         out.append(make_problem(f"batch_{i}", L=L, M=int(round(r * L * L)), n_blocks=d, uv_sigma=0.1,
-                                seed=seed * 100 + i))
+                                seed=seed * 100 + i, compact=compact))
     return out
+
+
+def make_batch32(seed: int = 1704):
+    """32 independent problems, sides 256, 512 or 1024 (log-uniform), M = 2-8 x
+    the pixel count, 4-32 blocks: the batched workload of independent problems."""
+    return make_batch(32, seed=seed, sides=(256, 512, 1024), ratio=(2.0, 8.0), blocks=(4, 32), compact=True)
 
 
 def make_problem(name: str = "c1_128", *, L: int | None = None, M: int | None = None,
                  n_blocks: int | None = None, uv_sigma: float | None = None,
                  seed: int | None = None, isnr_db: float = 30.0,
-                 n_points: int = 20, n_blobs: int = 3, ggd_beta: float | None = None) -> Problem:
-    """Build a seeded problem; keyword arguments override the named shape."""
+                 n_points: int = 20, n_blobs: int = 3, ggd_beta: float | None = None,
+                 compact: bool | None = None) -> Problem:
+    """Build a seeded problem; keyword arguments override the named shape.
+    compact: blobs kept well inside the image and their visibilities taken
+    from the analytic Gaussian spectra (large problems; see sky_image)."""
     cfg = dict(CONFIGS.get(name, CONFIGS["c1_128"]))
-    for k, v in dict(L=L, M=M, n_blocks=n_blocks, uv_sigma=uv_sigma, seed=seed).items():
+    for k, v in dict(L=L, M=M, n_blocks=n_blocks, uv_sigma=uv_sigma, seed=seed, compact=compact).items():
         if v is not None:
             cfg[k] = v
+    is_compact = bool(cfg.get("compact", False))
     rng = np.random.default_rng(cfg["seed"])
     Lv = int(cfg["L"])
-    points, blob = sky_image(Lv, rng, n_points=n_points, n_blobs=n_blobs)
+    params = []
+    points, blob = sky_image(Lv, rng, n_points=n_points, n_blobs=n_blobs, compact=is_compact, params_out=params)
     x = blob.copy()
     for (p0, p1, f) in points:
         x[p0, p1] += f
@@ -200,10 +253,28 @@ def make_problem(name: str = "c1_128", *, L: int | None = None, M: int | None = 
     else:
         omega = sample_uv_ggd(int(cfg["M"]), float(ggd_beta), float(cfg["uv_sigma"]), rng)
     block = radial_blocks(omega, int(cfg["n_blocks"]))
-    y0 = exact_visibilities(points, blob, omega)
+    if is_compact:
+        y0 = point_visibilities(points, omega, Lv) + gaussian_visibilities(params, omega, Lv)
+    else:
+        y0 = exact_visibilities(points, blob, omega)
     Mv = omega.shape[0]
     sigma = math.sqrt(float(np.vdot(y0, y0).real) / Mv * 10.0 ** (-isnr_db / 10.0))
     noise = sigma * (rng.normal(size=Mv) + 1j * rng.normal(size=Mv)) / math.sqrt(2.0)
     return Problem(name=name, L=Lv, x_true=x, omega=omega, y=y0 + noise, sigma=sigma,
                    theta=np.full(Mv, 1.0 / sigma), block=block,
                    n_blocks=int(cfg["n_blocks"]), isnr_db=isnr_db, seed=int(cfg["seed"]))
+
+
+def active_sets(n_iters: int, n_blocks: int, p_data: float, p_prior: float, seed: int = 1706,
+                n_bases: int = 9):
+    """Seeded draws of the randomised active sets of Algorithm 3: every data
+    block is in D with probability p_data and every basis (Dirac first) in P
+    with probability p_prior, independently and identically along the
+    iterations (Section 4.4 asks for nonzero probabilities and i.i.d. draws).
+    Returns uint8 masks of shapes (n_iters, n_blocks) and (n_iters, n_bases)."""
+    if not (0.0 < p_data <= 1.0 and 0.0 < p_prior <= 1.0):
+        raise ValueError("activation probabilities must lie in (0, 1]")
+    rng = np.random.default_rng(seed)
+    blocks = (rng.random((n_iters, n_blocks)) < p_data).astype(np.uint8)
+    bases = (rng.random((n_iters, n_bases)) < p_prior).astype(np.uint8)
+    return blocks, bases

@@ -33,3 +33,24 @@ def test_ggd_sampler_shape():
     assert abs(g2.std() / math.pi - 0.15) < 0.005          # beta = 2 is the Gaussian of that std
     centre = [np.mean(np.abs(synth.sample_uv_ggd(50000, b, 0.15, rng)) < 0.05 * math.pi) for b in (2.0, 0.5, 0.25)]
     assert centre[0] < centre[1] < centre[2]                # smaller beta: denser centre
+
+
+def test_compact_blobs_analytic_spectra_match_the_exact_sum():
+    """For compact blobs (L >= 256) the analytic Gaussian spectra equal the exact
+    pixel sum (truncated SVD route) to ~1e-8."""
+    rng = np.random.default_rng(77)
+    L = 256
+    params = []
+    points, blob = synth.sky_image(L, rng, n_points=3, n_blobs=3, compact=True, params_out=params)
+    omega = rng.uniform(-np.pi, np.pi, size=(1500, 2))
+    exact = synth.exact_visibilities(points, blob, omega)
+    fast = synth.point_visibilities(points, omega, L) + synth.gaussian_visibilities(params, omega, L)
+    assert np.linalg.norm(fast - exact) <= 1e-8 * np.linalg.norm(exact)
+
+
+def test_batch_shapes_stay_in_their_ranges():
+    probs = synth.make_batch(6, seed=9, sides=(16, 32), ratio=(2.0, 8.0), blocks=(2, 5))
+    assert {p.L for p in probs} <= {16, 32}
+    for p in probs:
+        assert 2.0 * p.L ** 2 - 1 <= p.M <= 8.0 * p.L ** 2 + 1
+        assert 2 <= p.n_blocks <= 5 and p.block.max() < p.n_blocks
