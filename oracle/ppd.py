@@ -19,7 +19,8 @@ Readings (the paper is silent or its printed step is garbled):
   v <- v/eta that puts eta in the primal step.
 * Algorithm 2 starts from the previous iteration's p (warm start) and, on
   the first iteration, from P_B(z); optionally from z itself every
-  iteration ("current").  n_itr fixed (default 1).
+  iteration ("current").  n_itr fixed (default 1).  Optionally its
+  accelerated (FISTA) form, which Section 4.1 points to (Tseng 2008).
 * mu_j = 1/max_e(U_j,e)^2 (Algorithm 2, as printed).
 * Per-block bound eps_j^2 = M_j + 2 sqrt(M_j) in whitened units (the
   chi^2 rule applied per block; y whitened as Theta y).
@@ -92,6 +93,7 @@ class Setup:
     levels: int = 4
     x_true: np.ndarray | None = None
     inner_init: str = "warm"    # Algorithm 2 start: "warm" (previous p) or "current" (z)
+    inner_solver: str = "fb"     # "fb": Algorithm 2; "fista": its accelerated form (Section 4.1)
     W: np.ndarray | None = None  # prior weights (9, L0, L1) of Algorithm 1; None = identity
     psiw_sq: float = 1.0         # ||Psi W||_S^2 (1 for W = I)
 
@@ -103,7 +105,7 @@ class Setup:
 def make_setup(omega, y, theta, block, n_blocks, L, *, precond: bool = True,
                eta: float | None = None, eps=None, U=None, n_itr: int = 1,
                tau: float = 0.49, kappa: float = 1e-4, x_true=None,
-               power_iters: int = 1000, inner_init: str = "warm") -> Setup:
+               power_iters: int = 1000, inner_init: str = "warm", inner_solver: str = "fb") -> Setup:
     P = nufft.Plan(omega, L, L, theta=theta)
     if U is None:
         U = nufft.uniform_weights(omega, P.K0, P.K1)[0] if precond else np.ones(P.M)
@@ -119,7 +121,7 @@ def make_setup(omega, y, theta, block, n_blocks, L, *, precond: bool = True,
         eta = 1.0 / op_norm_sq(P, U, max_iter=power_iters)[0]
     return Setup(P=P, yw=np.asarray(theta) * np.asarray(y), U=U, block=block,
                  n_blocks=n_blocks, eps=eps, mu=mu, eta=float(eta), tau=tau, kappa=kappa,
-                 n_itr=n_itr, x_true=x_true, inner_init=inner_init)
+                 n_itr=n_itr, x_true=x_true, inner_init=inner_init, inner_solver=inner_solver)
 
 
 def convergence_lhs(S: Setup, psi_norm_sq: float | None = None, phi_norm_sq: float | None = None):
@@ -176,8 +178,8 @@ def iterate(st: State, S: Setup, active_blocks=None, active_bases=None) -> dict:
             start = prox.proj_l2ball(z[m], S.yw[m], S.eps[j])
         else:
             start = st.p[m]
-        p[m] = prox.ellipsoid_prox_fb(z[m], S.yw[m], S.eps[j], S.U[m], S.n_itr,
-                                      start=start, mu=S.mu[j])
+        solve = prox.ellipsoid_prox_fista if S.inner_solver == "fista" else prox.ellipsoid_prox_fb
+        p[m] = solve(z[m], S.yw[m], S.eps[j], S.U[m], S.n_itr, start=start, mu=S.mu[j])
         v[m] = S.U[m] * (z[m] - p[m])
     g = nufft.phi_adjoint(v, P)
     # prior step for the bases in P: clip (I - S_{kappa ||Psi W||^2}) of

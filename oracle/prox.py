@@ -56,6 +56,29 @@ def ellipsoid_prox_fb(z, y, eps: float, U, n_itr: int, start=None, mu=None):
     return zb
 
 
+def ellipsoid_prox_fista(z, y, eps: float, U, n_itr: int, start=None, mu=None):
+    """Accelerated Algorithm 2 (Section 4.1 points to faster proximal gradient
+    methods, Tseng 2008): the same projected gradient step on
+    (zbar - z)^H U (zbar - z) / 2 taken at an extrapolated point,
+        zbar_k = P_B(q_k - mu U (q_k - z)),
+        t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2,  t_1 = 1,
+        q_{k+1} = zbar_k + ((t_k - 1) / t_{k+1}) (zbar_k - zbar_{k-1}),
+    with q_1 = zbar_0 = start (FISTA, Beck & Teboulle 2009).  The first two
+    steps coincide with Algorithm 2 (t_1 = 1 gives no extrapolation).
+    """
+    U = np.asarray(U, dtype=np.float64)
+    mu = 1.0 / float(np.max(U)) ** 2 if mu is None else mu
+    prev = np.array(z if start is None else start, dtype=np.complex128, copy=True)
+    q = prev.copy()
+    t = 1.0
+    for _ in range(n_itr):
+        cur = proj_l2ball(q - mu * U * (q - z), y, eps)
+        t_next = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
+        q = cur + ((t - 1.0) / t_next) * (cur - prev)
+        prev, t = cur, t_next
+    return prev
+
+
 def ellipsoid_prox_exact(z, y, eps: float, U, tol: float = 1e-15):
     """Exact prox^U_h(z) through its optimality conditions (used to pin Algorithm 2).
 

@@ -129,3 +129,18 @@ def test_more_subiterations_approach_the_exact_prox():
     z = np.zeros(S.P.M, np.complex128)   # at t=1 xt = 0 and v = 0, so z = 0
     p_exact, _ = prox.ellipsoid_prox_exact(z, S.yw, S.eps[0], S.U)
     assert np.abs(st.p - p_exact).max() <= 1e-8 * np.abs(p_exact).max()
+
+
+def test_accelerated_inner_solver_in_the_iteration():
+    """With one or two sub-iterations the accelerated inner solver is Algorithm 2;
+    with many, both give the exact prox, so the iterates agree."""
+    p = _tiny(seed=9, M=300, n_blocks=2)
+    runs = {}
+    for solver in ("fb", "fista"):
+        for n_itr in (2, 400):
+            S = ppd.make_setup(p.omega, p.y, p.theta, p.block, p.n_blocks, p.L, power_iters=200,
+                               n_itr=n_itr, inner_solver=solver)
+            st, _ = ppd.run(S, 4)
+            runs[(solver, n_itr)] = st.x
+    assert np.array_equal(runs[("fb", 2)], runs[("fista", 2)])
+    assert np.abs(runs[("fb", 400)] - runs[("fista", 400)]).max() <= 1e-8 * np.abs(runs[("fb", 400)]).max()

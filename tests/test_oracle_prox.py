@@ -89,3 +89,47 @@ def test_inside_the_ball_the_prox_is_the_point():
     assert np.array_equal(p, z)
     p2 = prox.ellipsoid_prox_fb(z, y, 1.0, U, n_itr=4000, start=y)
     assert np.abs(p2 - z).max() <= 1e-12
+
+
+# ----------------------------------------------------------------- accelerated Algorithm 2
+def _weak_block(seed, m=64, cond=3.0, out=1.05, eps=4.0):
+    """z just outside the ball (small Lagrange multiplier) and U spread over
+    `cond` decades: the regime where the plain step is slow."""
+    rng = np.random.default_rng(seed)
+    y = rng.normal(size=m) + 1j * rng.normal(size=m)
+    d = rng.normal(size=m) + 1j * rng.normal(size=m)
+    z = y + out * eps * d / np.linalg.norm(d)
+    U = 10.0 ** (-cond * rng.random(m))
+    U[0] = 1.0
+    return z, y, U, eps
+
+
+def test_fista_first_two_steps_are_algorithm2():
+    z, y, U = _block(8, m=32, cond=3.0)
+    for n in (1, 2):
+        assert np.array_equal(prox.ellipsoid_prox_fista(z, y, 4.0, U, n_itr=n, start=y),
+                              prox.ellipsoid_prox_fb(z, y, 4.0, U, n_itr=n, start=y))
+
+
+@pytest.mark.parametrize("seed", [5, 6, 7])
+def test_fista_converges_to_exact_prox(seed):
+    z, y, U = _block(seed, m=64, cond=3.0)
+    p_exact, _ = prox.ellipsoid_prox_exact(z, y, 4.0, U)
+    p = prox.ellipsoid_prox_fista(z, y, 4.0, U, n_itr=5000)
+    assert np.abs(p - p_exact).max() <= 1e-8 * np.abs(p_exact).max()
+    z, y, U, eps = _weak_block(seed)
+    p_exact, _ = prox.ellipsoid_prox_exact(z, y, eps, U)
+    p = prox.ellipsoid_prox_fista(z, y, eps, U, n_itr=20000)
+    assert np.abs(p - p_exact).max() <= 1e-8 * np.abs(p_exact).max()
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_fista_is_faster_when_the_constraint_is_weakly_active(seed):
+    """O(1/k^2) against O(1/k): after 100 steps the accelerated iterate is
+    several times closer to the exact prox than Algorithm 2's."""
+    z, y, U, eps = _weak_block(seed)
+    p_exact, _ = prox.ellipsoid_prox_exact(z, y, eps, U)
+    err = lambda p: np.abs(p - p_exact).max() / np.abs(p_exact).max()
+    e_fb = err(prox.ellipsoid_prox_fb(z, y, eps, U, n_itr=100))
+    e_fa = err(prox.ellipsoid_prox_fista(z, y, eps, U, n_itr=100))
+    assert e_fa <= 0.2 * e_fb, (e_fa, e_fb)
