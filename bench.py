@@ -10,7 +10,7 @@ SARA prior step, primal step) on inputs resident in HBM; L2 is flushed
 
 Printed JSON line (rank 0): PPD iterations per second of the FP32-batched
 path (FP32 arrays, FP64 norms, one CUDA graph per iteration), with the FP64
-plain path, the SNR reached after 500 iterations by each, the iterations and
+plain path, the SNR reached after 500 iterations (100 at 4096^2) by each, the iterations and
 seconds the FP32 path needs to reach the FP64 path's SNR, an end-to-end
 number through the host API, the roofline of the dominant kernel and the
 FP64 oracle timed on the host cores.
@@ -36,7 +36,20 @@ import numpy as np  # noqa: E402
 METRIC = "PPD iters/s and time-to-target-SNR, FP32-batched vs FP64-plain on 1 GB300"
 UNIT = "iters/s"
 SNR_ITERS = 500
+# iterations of the SNR comparison per workload (the FP64 plain path at 4096^2 runs a few iterations/s)
+SNR_ITERS_BY_WORKLOAD = {"c5_4096": 100}
+# workloads whose FP64 oracle iteration does not fit a bounded CPU sample (64M-visibility plans)
+NO_ORACLE = {"c5_4096": "one oracle iteration at 4096^2 with 64M visibilities holds > 16 GB of FP64 tap tables "
+                        "and runs for minutes on one core; the CPU baseline is reported on c2_512 and c3_1024"}
 WORKLOAD = "c2_512"
+
+
+_T0 = time.time()
+
+
+def _log(msg: str):
+    """Progress line on stderr (phase and elapsed seconds)."""
+    print(f"[bench {time.time() - _T0:7.1f}s] {msg}", file=sys.stderr, flush=True)
 
 
 def _env_rank():
@@ -45,40 +58,32 @@ def _env_rank():
 
 
 # ------------------------------------------------------------------ roofline model
-def coarse_level(L: int, levels: int = 4, rsz: int = 4) -> int:
-    """First SARA level the library runs inside one CTA per basis (mirrors csrc/sara.cu)."""
-    for l in range(1, levels):
-        nc = L >> l
-        if 2 * nc * nc * rsz <= 192 * 1024:
-            return l
-    return levels
-
-
-def algorithmic_bytes_per_step(L: int, M: int, levels: int = 4, rsz: int = 4) -> dict:
+def algorithmic_bytes_per_step(L: int, M: int, levels: int = 4, rsz: int = 4, xtrue: bool = True) -> dict:
     """Algorithmic HBM bytes per PPD iteration for each kernel name (all its launches).
 
     Complex = 2 * rsz bytes.  Every input read once and every output written
     once; halos, partial tiles and re-reads are implementation overhead and
     not counted.  N = L^2 pixels, K^2 = 4N grid cells, M visibilities.
+    SARA analysis, level l (8 wavelet bases): the level input (xt once at
+    level 0, the previous LL per basis after), the 3 detail quadrants of u
+    read and written, the LL written (read and written in u at the last
+    level).  Synthesis, level l >= 1: LL' and 3 detail quadrants read, the
+    2h x 2h output written; level 0 (all bases summed): LL' and details read,
+    ut written.  Primal: x, xt, g, ut, u_Dirac (and x_true for the SNR) read;
+    x, xt, u_Dirac written.
     """
     N, K2, c = L * L, 4 * L * L, 2 * rsz
-    lc = coarse_level(L, levels, rsz)
     det = lambda l: 3 * N / 4 ** (l + 1)       # detail coefficients of level l, per basis
     ll = lambda l: N / 4 ** (l + 1)            # LL of level l, per basis
     ana = rsz * N                               # xt read once for all bases
-    for l in range(min(lc, levels)):
+    for l in range(levels):
         inp = 0 if l == 0 else ll(l - 1)
-        out_ll = ll(l) if l < levels - 1 else 0
-        coarse_ll = ll(l) if l == levels - 1 else 0
-        ana += 8 * rsz * (inp + 2 * det(l) + 2 * coarse_ll + out_ll)
-    coarse = 0.0
-    if lc < levels:
-        coefs = sum(det(l) for l in range(lc, levels)) + ll(levels - 1)
-        coarse = 8 * rsz * (ll(lc - 1) + 3 * coefs + ll(lc - 1))
+        last = l == levels - 1
+        ana += 8 * rsz * (inp + 2 * det(l) + (2 * ll(l) if last else ll(l)))
     syn = 0.0
-    for l in range(min(lc, levels) - 1, 0, -1):
+    for l in range(levels - 1, 0, -1):
         syn += 8 * rsz * (ll(l) + det(l) + 4 * ll(l))
-    syn0 = 8 * rsz * (ll(0) + det(0)) + rsz * N * (5 + 3)
+    syn += 8 * rsz * (ll(0) + det(0)) + rsz * N
     return {
         "degrid_dual": (16 + 5 * c) * M + c * K2,     # record, v, y, p in; z, w out; grid once
         "grid_dual": (16 + 5 * c) * M + c * K2,       # record, y, w, z in; v, p out; grid once
@@ -89,9 +94,8 @@ def algorithmic_bytes_per_step(L: int, M: int, levels: int = 4, rsz: int = 4) ->
         "fft_inv_cols": c * K2 + c * 2 * N,
         "fft_inv_rows": c * 2 * N + rsz * N,
         "sara_analysis": ana,
-        "sara_coarse": coarse,
         "sara_synthesis": syn,
-        "sara_synthesis_primal": syn0,
+        "primal": rsz * N * (8 + (1 if xtrue else 0)),
         "block_norms": 0.0,
     }
 
@@ -295,6 +299,32 @@ def study_ggd(args, local):
 
 
 # ------------------------------------------------------------------ main
+def cufft_compare(K: int, dev, stream, flush, reps: int = 20) -> dict:
+    """cuFFT (through torch.fft) on the full K x K complex64 grid, timed with CUDA
+    events on the bench stream after 3 warm-ups, L2 flushed before each call:
+    the comparison for the library's own forward and inverse 2-D FFT passes."""
+    import torch
+    a = torch.randn((K, K), dtype=torch.complex64, device=dev)
+    out = {}
+    with torch.cuda.stream(stream):
+        for name, fn in (("cufft_fft2_us", lambda t: torch.fft.fft2(t)),
+                         ("cufft_ifft2_us", lambda t: torch.fft.ifft2(t, norm="forward"))):
+            for _ in range(3):
+                fn(a)
+            tot = 0.0
+            for _ in range(reps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn(a)
+                e1.record(stream)
+                e1.synchronize()
+                tot += e0.elapsed_time(e1)
+            out[name] = 1e3 * tot / reps
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -306,6 +336,7 @@ def main():
     ap.add_argument("--oracle-worker", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-steps", type=int, default=3)
+    ap.add_argument("--snr-iters", type=int, default=0, help="iterations of the SNR comparison (0: per workload)")
     ap.add_argument("--tile", type=int, default=0, help="gridding tile side (0: library default)")
     ap.add_argument("--chunk", type=int, default=0, help="visibilities per work item (0: library default)")
     ap.add_argument("--study", default="", help="ggd: PD vs PPD convergence on generalised-Gaussian coverages")
@@ -357,7 +388,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     dev = torch.device("cuda", local)
+    _log(f"generating {args.workload}")
     p = synth.make_problem(args.workload, seed=seed)
+    _log("problem ready")
+    snr_iters = args.snr_iters or SNR_ITERS_BY_WORKLOAD.get(args.workload, SNR_ITERS)
     stream = torch.cuda.Stream(dev)
     sp = stream.cuda_stream
 
@@ -370,12 +404,17 @@ def main():
     if args.quick:
         s32 = make(ppd.PPD_FP32_FP64NORMS, power_iters=20)
     else:
+        _log("set-up FP32 (eta by power iteration)")
         s32 = make(ppd.PPD_FP32_FP64NORMS)
+        _log("set-up FP64 (eta by power iteration)")
         s64 = make(ppd.PPD_FP64_PLAIN)
+    # the zero state of each solver, restored before every measured run (the
+    # state blob resets x, xt, u, v and the warm start without a new eta)
+    zero = {s.ctx: ppd.ppd_get_state(s.ctx) for s in ([s32] if args.quick else [s32, s64])}
 
     def timed_steps(s, steps, warmup, kernel_timing):
         ppd.ppd_timing_enable(s.ctx, kernel_timing)
-        ppd.ppd_set_weights(s.ctx, p.theta, None, None)   # reset state (eta recomputed) - untimed
+        ppd.ppd_set_state(s.ctx, zero[s.ctx])             # reset to the zero state - untimed
         for _ in range(warmup):
             ppd.ppd_iterate(s.ctx, 1, stats=False)
         torch.cuda.synchronize(dev)
@@ -401,7 +440,7 @@ def main():
 
     def snr_run(s, iters):
         ppd.ppd_timing_enable(s.ctx, False)
-        ppd.ppd_set_weights(s.ctx, p.theta, None, None)
+        ppd.ppd_set_state(s.ctx, zero[s.ctx])
         snr = []
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -428,25 +467,36 @@ def main():
         dist.barrier()
     with Clocks(local) as clk:
         # timed region: FP32-batched, no per-kernel event nodes in the graph
+        _log("timed FP32 steps")
         t32, launches, _ = timed_steps(s32, args.steps, max(args.warmup, 3), False)
         # same protocol again with an event pair around every kernel (roofline)
+        _log("per-kernel timed FP32 steps")
         t32k, _, kt = timed_steps(s32, args.steps, max(args.warmup, 3), True)
         # FP64 plain, same protocol
+        _log("timed FP64 steps")
         t64, _, _ = timed_steps(s64, max(3, args.steps // 4), 3, False)
-        snr32, wall32 = snr_run(s32, SNR_ITERS)
-        snr64, wall64 = snr_run(s64, SNR_ITERS)
-        # end to end through the host API: upload, set-up, 500 iterations with per-10 stats, image back
+        _log("SNR runs")
+        snr32, wall32 = snr_run(s32, snr_iters)
+        snr64, wall64 = snr_run(s64, snr_iters)
+        # end to end through the host API: context, upload, set-up, snr_iters iterations with
+        # per-10 stats, image back
+        _log("end to end")
         e2e_t = []
         for _ in range(2):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            ppd.ppd_set_visibilities(s32.ctx, p.omega, p.y, p.block)
-            ppd.ppd_set_weights(s32.ctx, p.theta, None, None)
-            for _ in range(SNR_ITERS // 10):
-                ppd.ppd_iterate(s32.ctx, 10, p.n_blocks)
-            img = ppd.ppd_get_image(s32.ctx, p.L, p.L)
+            se = ppd.Solver(p.L, p.n_blocks, precision=ppd.PPD_FP32_FP64NORMS, stream=sp)
+            ppd.ppd_set_visibilities(se.ctx, p.omega, p.y, p.block)
+            ppd.ppd_set_weights(se.ctx, p.theta, None, None)
+            ppd.ppd_set_ground_truth(se.ctx, p.x_true)
+            for _ in range(snr_iters // 10):
+                ppd.ppd_iterate(se.ctx, 10, p.n_blocks)
+            img = ppd.ppd_get_image(se.ctx, p.L, p.L)
+            se.close()
             e2e_t.append(time.perf_counter() - t0)
     clocks = clk.summary()
+    _log("cuFFT comparison")
+    cufft = cufft_compare(2 * p.L, dev, stream, flush) if rank == 0 else {}
 
     ips32 = args.steps / t32
     steps64 = max(3, args.steps // 4)
@@ -483,10 +533,19 @@ def main():
                 "algorithmic_bytes_per_launch": ab.get(name, 0.0) * args.steps / n,
                 "avg_launch_us": 1e3 * ms / n, "share_of_kernel_time": ms / ktot,
                 "ms_per_step_with_kernel_events": 1e3 * t32k / args.steps}
-    in_bytes = p.M * (16 + 16 + 4 + 8)
+    fft_cmp = None
+    if kt and cufft:
+        def avg(k):
+            return kern[k]["avg_us"] if k in kern else 0.0
+        fft_cmp = {"ours_forward_us": avg("fft_fwd_rows") + avg("fft_fwd_cols"),
+                   "ours_inverse_us": avg("fft_inv_cols") + avg("fft_inv_rows"), **cufft,
+                   "note": "ours: zero-padding, deapodisation and coverage pruning fused (forward), "
+                           "partial-tile sum, crop and real part fused (inverse), event-timed per kernel; "
+                           "cuFFT: plain full-grid complex-to-complex transform"}
+    in_bytes = p.M * (16 + 16 + 4 + 8) + p.L * p.L * 8   # uv, y, block, theta; x_true
     out_bytes = p.L * p.L * 8
-    stats_bytes = (SNR_ITERS // 10) * (3 * 8 + p.n_blocks * 8 + 4)
-    e2e_v = SNR_ITERS / min(e2e_t)
+    stats_bytes = (snr_iters // 10) * (3 * 8 + p.n_blocks * 8 + 4)
+    e2e_v = snr_iters / min(e2e_t)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * per_step, "higher_is_better": True,
@@ -495,21 +554,27 @@ def main():
                    "blocks": p.n_blocks, "uv_density": "gaussian sigma=0.1pi", "isnr_db": 30,
                    "l2": "flushed (256 MiB write) between timed steps", "graph": "one CUDA graph per iteration",
                    "replicas": world},
-        "fp64_plain": {"iters_per_s": ips64, "snr_db_at_500": target, "seconds_500": wall64},
-        "fp32_batched": {"iters_per_s": ips32, "snr_db_at_500": snr32[-1], "seconds_500": wall32,
+        "snr_iters": snr_iters,
+        "fp64_plain": {"iters_per_s": ips64, "snr_db_at_end": target, "seconds_all": wall64},
+        "fp32_batched": {"iters_per_s": ips32, "snr_db_at_end": snr32[-1], "seconds_all": wall32,
                          "iters_to_target_snr": it_to_target,
-                         "seconds_to_target_snr": (wall32 * it_to_target / SNR_ITERS) if it_to_target else None},
+                         "seconds_to_target_snr": (wall32 * it_to_target / snr_iters) if it_to_target else None},
         "speedup_iters_per_s": ips32 / ips64,
-        "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": in_bytes / SNR_ITERS,
-                "d2h_bytes_per_step": (out_bytes + stats_bytes) / SNR_ITERS,
-                "what": "ppd_set_visibilities + ppd_set_weights (eta by power iteration) + 500 iterations "
+        "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": in_bytes / snr_iters,
+                "d2h_bytes_per_step": (out_bytes + stats_bytes) / snr_iters,
+                "what": f"ppd_create + ppd_set_visibilities + ppd_set_weights (eta by power iteration) + "
+                        f"{snr_iters} iterations "
                         "with stats every 10 + ppd_get_image, from host buffers"},
         "gpu_launches": launches,
+        "fft_vs_cufft": fft_cmp,
         "roofline": roof,
         "kernels": kern,
         "clocks": clocks,
     }
-    if not args.no_cpu_baseline and world == 1:
+    if args.workload in NO_ORACLE and world == 1:
+        line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "not run: " + NO_ORACLE[args.workload]}
+    elif not args.no_cpu_baseline and world == 1:
         times = run_oracle(args.workload, seed, args.oracle_steps, 0)
         model, ncpu = cpu_info()
         line["cpu_baseline"] = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -70,7 +70,7 @@ typedef struct ppd_ctx ppd_ctx;
  * (Section 5.1: tau = 0.49, lambda = 1, kappa = 1e-4, n_itr = 1, no
  * randomisation; Section 5: oversampling 2 per axis, 8 x 8 Kaiser-Bessel). */
 typedef struct {
-    int32_t  n0, n1;            /* image rows / columns: powers of two, 16 <= n <= 2048 */
+    int32_t  n0, n1;            /* image rows / columns: powers of two, 16 <= n <= 4096 */
     int32_t  oversample;        /* grid K = oversample * n per axis; must be 2 */
     int32_t  kernel_width;      /* interpolation support J; must be 8 */
     double   kb_beta;           /* Kaiser-Bessel shape; 0 => 2.34 * J */

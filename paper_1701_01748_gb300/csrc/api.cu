@@ -438,8 +438,8 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
     *out = nullptr;
     const ppd_config &k = *cfg;
     if (k.n0 != k.n1) return fail(PPD_ERR_UNSUPPORTED, "ppd_create: only square images (n0 == n1)");
-    if (!is_pow2(k.n0) || k.n0 < 16 || k.n0 > 2048)
-        return fail(PPD_ERR_UNSUPPORTED, "ppd_create: image side must be a power of two in [16, 2048]");
+    if (!is_pow2(k.n0) || k.n0 < 16 || k.n0 > 4096)
+        return fail(PPD_ERR_UNSUPPORTED, "ppd_create: image side must be a power of two in [16, 4096]");
     if (k.oversample != 2 || k.kernel_width != 8 || k.wavelet_levels != 4)
         return fail(PPD_ERR_UNSUPPORTED, "ppd_create: oversample 2, kernel width 8 and 4 levels are required");
     if (k.n_blocks < 1 || k.n_itr < 1 || !(k.tau > 0) || k.lambda != 1.0 || !(k.kappa > 0) || k.eta < 0 ||

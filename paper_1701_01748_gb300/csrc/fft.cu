@@ -113,10 +113,37 @@ constexpr int NT = 256;
 
 // rows per CTA in a row pass: enough butterflies for 256 threads
 template <typename R> __host__ __device__ constexpr int rows_per_cta(int K) { return 1024 / K > 0 ? 1024 / K : 1; }
-// columns per CTA in a column pass (32 KB of shared memory), at most K
+// columns per CTA in a column pass.  K <= 2048: the strips are read from
+// L2 (grid and row-pass output of these sizes stay cached between the
+// passes), so the fewest columns the 256-thread butterfly split allows
+// (1024 / K, at least 1) give the most CTAs for these latency-bound passes.
+// Larger K: at least 32 contiguous bytes per grid row (one DRAM sector:
+// 4 float / 2 double columns), at most 128 KB of strip.
 template <typename R> __host__ __device__ constexpr int cols_per_cta(int K) {
-    return (sizeof(R) == 4 ? 4096 : 2048) / K < 1 ? 1
-           : (sizeof(R) == 4 ? 4096 : 2048) / K < K ? (sizeof(R) == 4 ? 4096 : 2048) / K : K;
+    constexpr int csz = 2 * (int)sizeof(R);
+    if (K <= 2048) return 1024 / K > 1 ? 1024 / K : 1;
+    const int w32 = (32 * 1024) / (K * csz), wmin = 32 / csz;
+    int w = w32 > wmin ? w32 : wmin;
+    while (w > 1 && (long long)w * K * csz > 128 * 1024) w /= 2;
+    return w < K ? w : K;
+}
+// twiddles go to shared memory beside nseq sequences when they fit (200 KB in
+// all), else they are read through the L1 from global memory
+template <typename R> __host__ __device__ constexpr bool tw_smem(int nseq, int K) {
+    return (long long)(nseq + 1) * K * 2 * (int)sizeof(R) <= 200 * 1024;
+}
+template <typename R> constexpr size_t pass_smem(int nseq, int K) {
+    return (size_t)(nseq + (tw_smem<R>(nseq, K) ? 1 : 0)) * K * 2 * sizeof(R);
+}
+template <typename R, int NSEQ, int K>
+__device__ __forceinline__ const cplx_t<R> *stage_twiddles(cplx_t<R> *buf, const cplx_t<R> *__restrict__ tw) {
+    if constexpr (tw_smem<R>(NSEQ, K)) {
+        cplx_t<R> *tws = buf + NSEQ * K;
+        for (int e = threadIdx.x; e < K; e += NT) tws[e] = tw[e];
+        return tws;
+    } else {
+        return tw;
+    }
 }
 
 // forward row pass: tmp[n0][c] = FFT_axis1(Z x)[n0][(c + K/2) mod K]
@@ -128,8 +155,7 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(const R *__restrict__ x, cplx_t
     constexpr int B = rows_per_cta<R>(K);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
-    C *tws = buf + B * K;   // twiddles staged in shared memory
-    for (int e = threadIdx.x; e < K; e += NT) tws[e] = tw[e];
+    const C *tws = stage_twiddles<R, B, K>(buf, tw);
     const int row0 = blockIdx.x * B;
     for (int e = threadIdx.x; e < B * K; e += NT) buf[e] = C{0, 0};
     __syncthreads();
@@ -158,8 +184,7 @@ __global__ void __launch_bounds__(NT) k_cols_fwd(const cplx_t<R> *__restrict__ t
     constexpr int W = cols_per_cta<R>(K);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
-    C *tws = buf + W * K;   // twiddles staged in shared memory
-    for (int e = threadIdx.x; e < K; e += NT) tws[e] = tw[e];
+    const C *tws = stage_twiddles<R, W, K>(buf, tw);
     const int c0 = strips[blockIdx.x];
     for (int e = threadIdx.x; e < W * K; e += NT) buf[e] = C{0, 0};
     __syncthreads();
@@ -186,8 +211,7 @@ __global__ void __launch_bounds__(NT) k_cols_inv(const cplx_t<R> *__restrict__ g
     constexpr int W = cols_per_cta<R>(K);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
-    C *tws = buf + W * K;   // twiddles staged in shared memory
-    for (int e = threadIdx.x; e < K; e += NT) tws[e] = tw[e];
+    const C *tws = stage_twiddles<R, W, K>(buf, tw);
     const int c0 = strips[blockIdx.x];
     for (int e = threadIdx.x; e < W * K; e += NT) {
         int s = e % W, r = e / W;   // r: stored (centred) row; natural frequency (r + K/2) mod K
@@ -218,8 +242,7 @@ __global__ void __launch_bounds__(NT) k_cols_inv_part(const cplx_t<R> *__restric
     constexpr int E = T + 8, NTL = K / T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
-    C *tws = buf + W * K;   // twiddles staged in shared memory
-    for (int e = threadIdx.x; e < K; e += NT) tws[e] = tw[e];
+    const C *tws = stage_twiddles<R, W, K>(buf, tw);
     const int c0 = strips[blockIdx.x];
     for (int e = threadIdx.x; e < W * K; e += NT) {
         const int s = e % W, r = e / W;   // r: stored (centred) row
@@ -263,8 +286,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(const cplx_t<R> *__restrict__ t
     constexpr int B = rows_per_cta<R>(K);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
-    C *tws = buf + B * K;   // twiddles staged in shared memory
-    for (int e = threadIdx.x; e < K; e += NT) tws[e] = tw[e];
+    const C *tws = stage_twiddles<R, B, K>(buf, tw);
     const int row0 = blockIdx.x * B;
     for (int e = threadIdx.x; e < B * K; e += NT) {
         int s = e / K, c = e % K, n0 = row0 + s;
@@ -286,7 +308,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(const cplx_t<R> *__restrict__ t
 template <typename R, int K> int fft_fwd_k(ppd_ctx *c, const R *x, cplx_t<R> *grid, cudaStream_t s) {
     constexpr int B = rows_per_cta<R>(K), W = cols_per_cta<R>(K);
     const int L = c->L0;
-    size_t shr = (size_t)(B + 1) * K * sizeof(cplx_t<R>), shc = (size_t)(W + 1) * K * sizeof(cplx_t<R>);
+    size_t shr = pass_smem<R>(B, K), shc = pass_smem<R>(W, K);
     static bool attr = false;
     if (!attr) {
         PPD_CUDA(cudaFuncSetAttribute(k_rows_fwd<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shr));
@@ -312,7 +334,7 @@ template <typename R, int K> int fft_fwd_k(ppd_ctx *c, const R *x, cplx_t<R> *gr
 template <typename R, int K> int fft_inv_k(ppd_ctx *c, const cplx_t<R> *grid, R *img, cudaStream_t s) {
     constexpr int B = rows_per_cta<R>(K), W = cols_per_cta<R>(K);
     const int L = c->L0;
-    size_t shr = (size_t)(B + 1) * K * sizeof(cplx_t<R>), shc = (size_t)(W + 1) * K * sizeof(cplx_t<R>);
+    size_t shr = pass_smem<R>(B, K), shc = pass_smem<R>(W, K);
     static bool attr = false;
     if (!attr) {
         PPD_CUDA(cudaFuncSetAttribute(k_rows_inv<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shr));
@@ -339,7 +361,7 @@ template <typename R, int K> int fft_inv_k(ppd_ctx *c, const cplx_t<R> *grid, R 
 template <typename R, int K, int T> int fft_inv_part_k(ppd_ctx *c, R *img, cudaStream_t s) {
     constexpr int B = rows_per_cta<R>(K), W = cols_per_cta<R>(K);
     const int L = c->L0;
-    size_t shr = (size_t)(B + 1) * K * sizeof(cplx_t<R>), shc = (size_t)(W + 1) * K * sizeof(cplx_t<R>);
+    size_t shr = pass_smem<R>(B, K), shc = pass_smem<R>(W, K);
     static bool attr = false;
     if (!attr) {
         PPD_CUDA(cudaFuncSetAttribute(k_rows_inv<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shr));
@@ -382,6 +404,7 @@ template <typename R> int fft_inverse_partials(ppd_ctx *c, R *img, cudaStream_t 
         case 1024: return fft_inv_part_t<R, 1024>(c, img, s);
         case 2048: return fft_inv_part_t<R, 2048>(c, img, s);
         case 4096: return fft_inv_part_t<R, 4096>(c, img, s);
+        case 8192: return fft_inv_part_t<R, 8192>(c, img, s);
         default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
     }
 }
@@ -399,6 +422,7 @@ template <typename R> int fft_forward(ppd_ctx *c, const R *x, cplx_t<R> *grid, c
         case 1024: return fft_fwd_k<R, 1024>(c, x, grid, s);
         case 2048: return fft_fwd_k<R, 2048>(c, x, grid, s);
         case 4096: return fft_fwd_k<R, 4096>(c, x, grid, s);
+        case 8192: return fft_fwd_k<R, 8192>(c, x, grid, s);
         default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
     }
 }
@@ -413,6 +437,7 @@ template <typename R> int fft_inverse(ppd_ctx *c, const cplx_t<R> *grid, R *img,
         case 1024: return fft_inv_k<R, 1024>(c, grid, img, s);
         case 2048: return fft_inv_k<R, 2048>(c, grid, img, s);
         case 4096: return fft_inv_k<R, 4096>(c, grid, img, s);
+        case 8192: return fft_inv_k<R, 8192>(c, grid, img, s);
         default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
     }
 }

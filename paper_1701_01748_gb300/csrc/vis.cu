@@ -400,6 +400,7 @@ __global__ void k_block_norms(const double *__restrict__ partials, const int32_t
 // footprint into the warp's private (T+8)^2 tile; phase 3 sums the private
 // tiles in warp order and writes the chunk's partial tile.  GR_DUAL fuses the
 // end of the data step: p = P_B(w) = y + c (w - y), v = U (z - p).
+constexpr int GRID_MINV = 16;   // least visibilities per scattering warp
 template <typename R> struct GridCfg;
 template <> struct GridCfg<float> { static constexpr int NWARP = 8; };
 template <> struct GridCfg<double> { static constexpr int NWARP = 4; };
@@ -421,8 +422,11 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
     const int start = A.ch_start[ch], count = A.ch_count[ch], tl = A.ch_tile[ch];
     const int row0 = (tl / A.ntile1) * T, col0 = (tl % A.ntile1) * T;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // warps that scatter: at least GRID_MINV visibilities each, so that a
+    // small chunk clears and sums only as many private tiles as it fills
+    const int nwu = min(NW, max(1, (count + GRID_MINV - 1) / GRID_MINV));
     for (int i = threadIdx.x; i < (KB_DEG + 1) * KB_J; i += NT) poly[i] = A.kbpoly ? A.kbpoly[i] : 0.f;
-    for (int e = threadIdx.x; e < NW * E * P; e += NT) priv[e] = C{0, 0};
+    for (int e = threadIdx.x; e < nwu * E * P; e += NT) priv[e] = C{0, 0};
     R c = 0;
     if (MODE == GR_DUAL) c = (R)block_scale(A, A.ch_block[ch]);
     __syncthreads();
@@ -463,8 +467,8 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
         // sort order makes runs of visibilities share a first tap, so each
         // lane accumulates its two footprint cells in registers and writes
         // the warp's private tile only when the base cell changes.
-        const int seg = (n + NW - 1) / NW;
-        const int i0 = warp * seg, i1 = min(n, i0 + seg);
+        const int seg = (n + nwu - 1) / nwu;
+        const int i0 = warp < nwu ? warp * seg : n, i1 = min(n, i0 + seg);
         int cur = -1;
         C acc0{0, 0}, acc1{0, 0};
         for (int i = i0; i < i1; ++i) {
@@ -500,8 +504,7 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
     for (int e = threadIdx.x; e < E * E; e += NT) {
         const int r = e / E, cc = e % E;
         C s{0, 0};
-#pragma unroll
-        for (int k = 0; k < NW; ++k) s = cadd(s, priv[k * E * P + r * P + cc]);
+        for (int k = 0; k < nwu; ++k) s = cadd(s, priv[k * E * P + r * P + cc]);
         out[e] = s;
     }
 }

@@ -1,0 +1,133 @@
+"""Full-size parity through the C ABI: the 1024 x 1024 workload (4,194,304
+visibilities, 64 blocks) and the 4096 x 4096 workload (67,108,864
+visibilities, 256 blocks), in the FP32 launch configuration the benchmark
+times.
+
+At these sizes the oracle computes sampled outputs one by one: Phi on a
+random sample of visibilities (each visibility depends only on the grid),
+Phi^dagger of a measurement vector that is zero outside a random sample
+(the library still grids every visibility), Psi^dagger of the whole image.
+Properties that hold at any size cover the rest: the adjoint identity of
+the library's own Phi and Phi^dagger, and perfect reconstruction
+Psi Psi^dagger x = x.  At 1024^2 the oracle also runs two whole PPD
+iterations (Algorithm 3) for an element-wise image comparison.
+
+Tolerances (relative l2): operators <= 1e-5, image after a fixed number of
+iterations <= 1e-4 (FP32 path against the FP64 oracle).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import nufft, ppd as oppd, sara  # noqa: E402
+from paper_1701_01748_gb300 import build, ppd, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+F32 = ppd.PPD_FP32_FP64NORMS
+SAMPLE = 4096
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    build.build()
+    assert torch.cuda.is_available()
+    return ppd._lib()
+
+
+_cache = {}
+
+
+def problem(name):
+    if name not in _cache:
+        _cache.clear()          # one large problem in host memory at a time
+        _cache[name] = synth.make_problem(name)
+    return _cache[name]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def gpu_forward(s, x):
+    xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+    yd = torch.empty((s.M, 2), dtype=torch.float32, device="cuda")
+    ppd.ppd_op_forward(s.ctx, xd.data_ptr(), yd.data_ptr(), stream())
+    torch.cuda.synchronize()
+    out = yd.cpu().double().numpy()
+    del xd, yd
+    return out[:, 0] + 1j * out[:, 1]
+
+
+def gpu_adjoint(s, y):
+    yd = torch.tensor(np.stack([y.real, y.imag], 1), dtype=torch.float32, device="cuda")
+    xd = torch.empty((s.L, s.L), dtype=torch.float32, device="cuda")
+    ppd.ppd_op_adjoint(s.ctx, yd.data_ptr(), xd.data_ptr(), stream())
+    torch.cuda.synchronize()
+    out = xd.cpu().double().numpy()
+    del xd, yd
+    return out
+
+
+def test_ppd_two_iterations_at_1024():
+    p = problem("c3_1024")
+    # 1 / ||U^{1/2} Phi||_S^2 of this problem to 3 digits (the oracle's power
+    # iteration gives 7.81e5); the power iteration itself is checked at small sizes
+    eta = 1.28e-6
+    S = oppd.make_setup(p.omega, p.y, p.theta, p.block, p.n_blocks, p.L, eta=eta, x_true=p.x_true)
+    st = oppd.init_state(S)
+    for _ in range(2):
+        hist = oppd.iterate(st, S)
+    s = ppd.Solver(p.L, p.n_blocks, precision=F32, eta=eta)
+    s.set_problem(p.omega, p.y, p.block, theta=p.theta, x_true=p.x_true)
+    stats = s.iterate(2)
+    assert rel(s.image(), st.x) <= 1e-4
+    assert np.allclose(stats["block_residual"], hist["residual"], rtol=1e-4)
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["c3_1024", "c5_4096"])
+def test_operators_at_full_size(name):
+    p = problem(name)
+    s = ppd.Solver(p.L, p.n_blocks, precision=F32, eta=1.0)
+    s.set_problem(p.omega, p.y, p.block, theta=p.theta)
+    idx = np.sort(np.random.default_rng(17).choice(p.M, size=SAMPLE, replace=False))
+    Ps = nufft.Plan(p.omega[idx], p.L, theta=p.theta[idx])
+    # Phi on sampled visibilities (Section 2: Phi = Theta G F Z)
+    y_gpu = gpu_forward(s, p.x_true)
+    assert rel(y_gpu[idx], nufft.phi(p.x_true, Ps)) <= 1e-5
+    # Phi^dagger of data supported on the sample
+    yv = np.zeros(p.M, np.complex128)
+    rng = np.random.default_rng(18)
+    yv[idx] = rng.normal(size=SAMPLE) + 1j * rng.normal(size=SAMPLE)
+    assert rel(gpu_adjoint(s, yv), nufft.phi_adjoint(yv[idx], Ps)) <= 1e-5
+    # adjoint identity of the library's own operators on all visibilities
+    yw = p.theta * p.y
+    a = float(np.vdot(y_gpu, yw).real)
+    b = float(np.sum(p.x_true * gpu_adjoint(s, yw)))
+    assert abs(a - b) <= 1e-5 * abs(a)
+    s.close()
+
+
+def test_psi_at_4096():
+    p = problem("c5_4096")
+    s = ppd.Solver(p.L, p.n_blocks, precision=F32, eta=1.0)
+    xd = torch.tensor(p.x_true, dtype=torch.float32, device="cuda")
+    cd = torch.empty((sara.N_BASES, p.L, p.L), dtype=torch.float32, device="cuda")
+    ppd.ppd_psi_analysis(s.ctx, xd.data_ptr(), cd.data_ptr(), stream())
+    torch.cuda.synchronize()
+    ref = sara.psi_adjoint(p.x_true, 4)
+    got = cd.cpu().double().numpy()
+    for b in range(sara.N_BASES):
+        assert rel(got[b], ref[b]) <= 1e-5, b
+    del ref, got
+    rd = torch.empty_like(xd)
+    ppd.ppd_psi_synthesis(s.ctx, cd.data_ptr(), rd.data_ptr(), stream())
+    torch.cuda.synchronize()
+    assert rel(rd.cpu().double().numpy(), p.x_true) <= 1e-5     # Psi Psi^dagger = I
+    s.close()
