@@ -298,6 +298,62 @@ def study_ggd(args, local):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------------ randomised active sets
+def study_random(args, local):
+    """Randomised active sets (Algorithm 3, sets P and D) on the bench
+    workload: iterations/s of the FP32 path with every data block and basis
+    active with probability p (seeded i.i.d. draws, Section 4.4), and the SNR
+    after a fixed number of iterations, for p = 1 (plain), 0.75, 0.5."""
+    import torch
+    from paper_1701_01748_gb300 import ppd, synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = synth.make_problem(args.workload)
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    s = ppd.Solver(p.L, p.n_blocks, precision=ppd.PPD_FP32_FP64NORMS, stream=stream.cuda_stream)
+    s.set_problem(p.omega, p.y, p.block, theta=p.theta, x_true=p.x_true)
+    zero = ppd.ppd_get_state(s.ctx)
+    iters = args.snr_iters or SNR_ITERS
+    out = {"metric": "PPD iterations/s and SNR with randomised active sets", "unit": "iters/s", "data": "synthetic",
+           "dtype": "f32", "steps": args.steps, "warmup": args.warmup,
+           "config": {"workload": args.workload, "image": f"{p.L}x{p.L}", "visibilities": p.M,
+                      "blocks": p.n_blocks, "l2": "flushed (256 MiB write) between timed steps"},
+           "results": []}
+    for prob in (1.0, 0.75, 0.5):
+        n_all = args.warmup + args.steps
+        B, P = synth.active_sets(max(n_all, iters), p.n_blocks, prob, prob, seed=1706)
+
+        def restart():
+            ppd.ppd_set_state(s.ctx, zero)
+            if prob < 1.0:
+                ppd.ppd_set_active_sets(s.ctx, B, P)
+            else:
+                ppd.ppd_set_active_sets(s.ctx, n_iters=0)
+        restart()
+        for _ in range(args.warmup):
+            ppd.ppd_iterate(s.ctx, 1, stats=False)
+        torch.cuda.synchronize(dev)
+        tot = 0.0
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ppd.ppd_iterate(s.ctx, 1, stats=False)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        restart()             # SNR after `iters` iterations from zero with the same draws
+        snr = [ppd.ppd_iterate(s.ctx, 10, p.n_blocks)["snr_db"] for _ in range(iters // 10)]
+        out["results"].append({"p_active": prob, "iters_per_s": args.steps / (tot / 1e3),
+                               "ms_per_iter": tot / args.steps, "snr_db_at_end": snr[-1],
+                               "snr_db_every_50": snr[4::5]})
+    print(json.dumps(out), flush=True)
+    s.close()
+
+
 # ------------------------------------------------------------------ main
 def cufft_compare(K: int, dev, stream, flush, reps: int = 20) -> dict:
     """cuFFT (through torch.fft) on the full K x K complex64 grid, timed with CUDA
@@ -339,7 +395,8 @@ def main():
     ap.add_argument("--snr-iters", type=int, default=0, help="iterations of the SNR comparison (0: per workload)")
     ap.add_argument("--tile", type=int, default=0, help="gridding tile side (0: library default)")
     ap.add_argument("--chunk", type=int, default=0, help="visibilities per work item (0: library default)")
-    ap.add_argument("--study", default="", help="ggd: PD vs PPD convergence on generalised-Gaussian coverages")
+    ap.add_argument("--study", default="", help="ggd: PD vs PPD convergence on generalised-Gaussian coverages; "
+                                                "random: randomised active sets")
     ap.add_argument("--isnr", type=float, default=30.0, help="input SNR (dB) of the study problems")
     ap.add_argument("--quick", action="store_true",
                     help="only the timed FP32 steps (for profiler launch lists); eta from 20 power steps")
@@ -348,11 +405,11 @@ def main():
         oracle_worker(args)
         return
     rank, world, local = _env_rank()
-    if args.study == "ggd":
+    if args.study in ("ggd", "random"):
         from paper_1701_01748_gb300 import build
         build.build()
         if rank == 0:
-            study_ggd(args, local)
+            (study_ggd if args.study == "ggd" else study_random)(args, local)
         return
     from paper_1701_01748_gb300 import synth
     base_seed = synth.CONFIGS[args.workload]["seed"] if args.workload in synth.CONFIGS else 1704

@@ -64,6 +64,12 @@ extern "C" {
 #define PPD_INNER_WARM          0   /* previous iteration's prox output (P_B(z) on the first iteration) */
 #define PPD_INNER_CURRENT       1   /* zbar^(0) = z */
 
+/* Algorithm 2 iteration (config.inner_solver) */
+#define PPD_INNER_FB            0   /* Algorithm 2 as printed: zbar <- P_B(zbar - mu U (zbar - z)) */
+#define PPD_INNER_FISTA         1   /* the same step at an extrapolated point, FISTA t-sequence
+                                       (Section 4.1: faster proximal gradient methods, Tseng 2008);
+                                       identical to PPD_INNER_FB for n_itr <= 2 */
+
 typedef struct ppd_ctx ppd_ctx;
 
 /* Solver configuration.  ppd_config_default() fills the paper's values
@@ -91,6 +97,7 @@ typedef struct {
     int32_t  power_iters;       /* power-iteration cap for eta; 0 => 1000 */
     double   power_tol;         /* power-iteration relative stop; 0 => 1e-10 */
     void    *stream;            /* cudaStream_t for all work; NULL => library-created stream */
+    int32_t  inner_solver;      /* PPD_INNER_FB (default) or PPD_INNER_FISTA */
 } ppd_config;
 
 /* Per-call statistics (ppd_iterate).  All norms are computed in double. */
@@ -201,7 +208,8 @@ PPD_API int ppd_autotune(ppd_ctx *ctx, int32_t iters, int32_t *tile_out, int32_t
 /* Solver state for checkpoint / resume and warm starts (Algorithm 3 takes
  * and returns x, xt, u_i, v_j; Algorithm 1 restarts Algorithm 3 from them):
  * a self-describing blob holding x, xt, the 9 dual images u_i, the data
- * duals v, the warm start p of Algorithm 2 (processing order) and the
+ * duals v, the warm start p of Algorithm 2 (processing order), the per-block
+ * flags of which blocks have been active (randomised active sets) and the
  * iteration count, tagged with the precision, sizes and a fingerprint of the
  * visibility order.  ppd_get_state with blob = NULL sets *bytes to the size
  * needed; otherwise *bytes must be at least that size and the blob is
@@ -239,6 +247,27 @@ PPD_API int ppd_set_state(ppd_ctx *ctx, const void *blob, int64_t bytes);
 PPD_API int ppd_set_prior_weights(ppd_ctx *ctx, const double *w, int64_t len);
 PPD_API int ppd_reweight(ppd_ctx *ctx, double omega);
 PPD_API int ppd_get_prior_weights(ppd_ctx *ctx, double *w, int64_t len);
+
+/* Randomised active sets (Algorithm 3, "generate sets P and D"; Section 4.2:
+ * only the dual variables in the sets are updated; Section 4.4: the sets are
+ * drawn with nonzero probabilities, independently and identically along the
+ * iterations).  Queues the sets of the next n_iters iterations:
+ *   blocks  host array n_iters x n_blocks bytes, row t = the set D of the
+ *           t-th next iteration (nonzero = data block j updated), or NULL
+ *           (every block, every iteration)
+ *   bases   host array n_iters x 9 bytes, row t = the set P (Dirac, db1 ..
+ *           db8; nonzero = basis i updated), or NULL (every basis)
+ * Both are copied.  A block outside D keeps v_j and its Algorithm 2 warm
+ * start (its gridded contribution is reused without recomputation); a basis
+ * outside P keeps u_i.  A block that has never been active starts
+ * Algorithm 2 from P_B(z), as every block does on the first iteration.  The
+ * rows are consumed one per iteration by ppd_iterate and ppd_group_iterate;
+ * once they are used up every set is full until the next call.  n_iters = 0
+ * drops the queue and returns to the plain iteration.  The draws are the
+ * caller's (e.g. Bernoulli masks from a seeded generator); the queue position
+ * is not part of the state blob.  Synchronises.
+ * Errors: INVALID_ARG (NULL context, n_iters < 0), OOM, CUDA. */
+PPD_API int ppd_set_active_sets(ppd_ctx *ctx, int32_t n_iters, const uint8_t *blocks, const uint8_t *bases);
 
 /* Phi x = Theta G F Z x (Section 2): x_dev n0*n1 reals -> y_dev M complex
  * (caller order, whitened by theta).  Enqueued on stream.  Uses the

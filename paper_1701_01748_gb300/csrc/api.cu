@@ -113,6 +113,7 @@ void free_vis(ppd_ctx *c) {
     c->ch = Chunks{};
     c->partials = c->scale = c->resid2 = c->eps_d = c->mu_d = nullptr;
     c->have_vis = c->have_weights = false;
+    c->gpart_stale = true;
 }
 
 void drop_graph(ppd_ctx *c) {
@@ -212,15 +213,33 @@ template <typename R> int iteration_body(ppd_ctx *c, cudaStream_t s, bool first)
     int cur = 0;
     PPD_CHECK(fft_forward<R>(c, static_cast<const R *>(c->xt), ga, s));
     const bool current = c->cfg.inner_init == PPD_INNER_CURRENT;
+    // with randomised active sets the warm start is decided per block on
+    // the device (blocks without a prox output start from z, then one extra
+    // step gives P_B(z)), so the captured iteration is the same every time
+    const bool rnd = c->rand_on;
     c->part_out = bank[0];
     c->part_in = bank[1];
-    PPD_CHECK(degrid<R>(c, (current || first) ? DG_FIRST : DG_DUAL, ga, nullptr, nullptr, s));
-    // warm start at t = 1: zbar^(0) = P_B(z), then the first step; plus n_itr - 1 steps
-    const int steps = c->cfg.n_itr - 1 + ((first && !current) ? 1 : 0);
-    for (int k = 0; k < steps; ++k) {
+    PPD_CHECK(degrid<R>(c, (current || (first && !rnd)) ? DG_FIRST : DG_DUAL, ga, nullptr, nullptr, s));
+    // warm start at t = 1: zbar^(0) = P_B(z) (an extra step from z), then
+    // the n_itr - 1 steps between the degridding and the gridding; the
+    // accelerated solver extrapolates with beta_k = (t_k - 1) / t_{k+1},
+    // t_1 = 1, from the second of them on
+    const bool extra = !current && (rnd || first);
+    if (extra) {
         c->part_in = bank[cur];
         c->part_out = bank[cur ^ 1];
-        PPD_CHECK(subiter<R>(c, s));
+        PPD_CHECK(subiter<R>(c, s, /*only_first=*/rnd ? 1 : 0));
+        cur ^= 1;
+    }
+    const bool fista = c->cfg.inner_solver == PPD_INNER_FISTA;
+    double t_k = 1.0;
+    for (int k = 1; k < c->cfg.n_itr; ++k) {
+        const double t_next = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t_k * t_k));
+        const double beta = fista ? (t_k - 1.0) / t_next : 0.0;
+        t_k = t_next;
+        c->part_in = bank[cur];
+        c->part_out = bank[cur ^ 1];
+        PPD_CHECK(subiter<R>(c, s, 0, beta, fista ? 1 : 0));
         cur ^= 1;
     }
     c->part_in = bank[cur];
@@ -232,10 +251,34 @@ template <typename R> int iteration_body(ppd_ctx *c, cudaStream_t s, bool first)
     return PPD_OK;
 }
 
+// Before an iteration with randomised active sets: the iteration's masks
+// (the next queued row, or all ones once the queue is used up) and, when the
+// partial tiles may hold other data, the flag that regrids inactive blocks.
+int rand_prepare(ppd_ctx *c, cudaStream_t s) {
+    if (!c->rand_on) return PPD_OK;
+    const size_t row = (size_t)c->d + N_BASES;
+    if (c->rand_next < c->rand_n) {
+        PPD_CUDA(cudaMemcpyAsync(c->mask_cur, c->mask_all + (size_t)c->rand_next * row, row, cudaMemcpyDeviceToDevice, s));
+        c->rand_next++;
+    } else {
+        PPD_CUDA(cudaMemsetAsync(c->mask_cur, 1, row, s));
+    }
+    if (c->gpart_stale) PPD_CUDA(cudaMemsetAsync(c->regrid_d, 1, sizeof(int), s));
+    return PPD_OK;
+}
+
+int rand_finish(ppd_ctx *c, cudaStream_t s) {
+    if (!c->rand_on || !c->gpart_stale) return PPD_OK;
+    PPD_CUDA(cudaMemsetAsync(c->regrid_d, 0, sizeof(int), s));
+    c->gpart_stale = false;
+    return PPD_OK;
+}
+
 template <typename R> int run_iterations(ppd_ctx *c, int n) {
     cudaStream_t s = c->stream;
     for (int it = 0; it < n; ++it) {
         const bool first = !c->p_valid;
+        PPD_CHECK(rand_prepare(c, s));
         if (first || !c->cfg.use_graph || !c->is_f32) {
             PPD_CHECK(iteration_body<R>(c, s, first));
         } else {
@@ -276,6 +319,7 @@ template <typename R> int run_iterations(ppd_ctx *c, int n) {
             c->launches += c->graph_kernels;
             c->graph_ran_since_collect = true;
         }
+        PPD_CHECK(rand_finish(c, s));
         c->p_valid = true;
         c->iters++;
     }
@@ -310,6 +354,7 @@ template <typename R> int power_iteration(ppd_ctx *c) {
     }
     c->op_norm_sq = val;
     c->power_done = std::min(it, maxit);
+    c->gpart_stale = true;
     return PPD_OK;
 }
 
@@ -323,8 +368,10 @@ int reset_state(ppd_ctx *c) {
         PPD_CUDA(cudaMemsetAsync(c->p, 0, 2 * c->M * rb, c->stream));
     }
     PPD_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    if (c->blk_seen) PPD_CUDA(cudaMemsetAsync(c->blk_seen, 0, c->d, c->stream));
     c->p_valid = false;
     c->iters = 0;
+    c->gpart_stale = true;
     drop_graph(c);
     return PPD_OK;
 }
@@ -415,6 +462,7 @@ void ppd_config_default(ppd_config *cfg) {
     cfg->power_iters = 0;
     cfg->power_tol = 0.0;
     cfg->stream = nullptr;
+    cfg->inner_solver = PPD_INNER_FB;
 }
 
 const char *ppd_status_string(int status) {
@@ -449,6 +497,8 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
         return fail(PPD_ERR_INVALID_ARG, "ppd_create: unknown precision");
     if (k.inner_init != PPD_INNER_WARM && k.inner_init != PPD_INNER_CURRENT)
         return fail(PPD_ERR_INVALID_ARG, "ppd_create: unknown inner_init");
+    if (k.inner_solver != PPD_INNER_FB && k.inner_solver != PPD_INNER_FISTA)
+        return fail(PPD_ERR_INVALID_ARG, "ppd_create: unknown inner_solver");
     if (k.tile != 0 && k.tile != 16 && k.tile != 32) return fail(PPD_ERR_INVALID_ARG, "ppd_create: tile must be 16 or 32");
     if (k.chunk < 0) return fail(PPD_ERR_INVALID_ARG, "ppd_create: chunk must be >= 0");
 
@@ -508,6 +558,13 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
         return bail(st);
     c->n_prim_blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 4);
     if ((st = dalloc(&c->prim_part, 3 * (size_t)c->n_prim_blocks))) return bail(st);
+    if ((st = dalloc(&c->mask_cur, (size_t)c->d + N_BASES)) || (st = dalloc(&c->blk_seen, (size_t)c->d)) ||
+        (st = dalloc(&c->regrid_d, 1)))
+        return bail(st);
+    if (cudaMemsetAsync(c->mask_cur, 1, (size_t)c->d + N_BASES, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->blk_seen, 0, (size_t)c->d, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->regrid_d, 0, sizeof(int), c->stream) != cudaSuccess)
+        return bail(fail(PPD_ERR_CUDA, "ppd_create: initialisation"));
     if ((st = make_twiddles(c)) || (st = make_deapodisation(c)) || (st = make_filters(c)) || (st = make_kb_poly(c)))
         return bail(st);
     if (cudaMemsetAsync(c->grid_a, 0, G * cb, c->stream) != cudaSuccess ||
@@ -532,7 +589,8 @@ void ppd_destroy(ppd_ctx *c) {
     for (void *p : {(void *)c->fwd_strips, (void *)c->inv_strips, (void *)c->row_fwd, (void *)c->row_inv,
                     (void *)c->col_fwd, c->fft_tmp_inv})
         dfree(p);
-    for (void *p : {c->wgt, c->wcoef})
+    for (void *p : {c->wgt, c->wcoef, (void *)c->mask_all, (void *)c->mask_cur, (void *)c->blk_seen,
+                    (void *)c->regrid_d})
         dfree(p);
     for (void *p : {c->x, c->xt, c->g, c->ut, c->xtrue, c->u, c->wtmp, c->wtmp2, c->grid_a, c->grid_v, c->fft_tmp,
                     c->tw0, c->deap0, c->deap1, c->kbpoly, (void *)c->prim_part, (void *)c->stat_out, (void *)c->err})
@@ -973,6 +1031,7 @@ int ppd_op_adjoint(ppd_ctx *c, const void *y_dev, void *x_dev, void *stream) {
     if (!c || !x_dev || !y_dev) return fail(PPD_ERR_INVALID_ARG, "ppd_op_adjoint: NULL argument");
     if (!c->have_weights) return fail(PPD_ERR_NOT_READY, "ppd_op_adjoint: call ppd_set_weights first");
     cudaStream_t s = pick(c, stream);
+    c->gpart_stale = true;   // the partial tiles now hold this call's data
     if (c->is_f32) {
         PPD_CHECK(grid_vis<float>(c, GR_OP, static_cast<const float2 *>(y_dev), c->perm,
                                   static_cast<float2 *>(c->grid_v), s));
@@ -1035,6 +1094,39 @@ int ppd_reweight(ppd_ctx *c, double omega) {
         PPD_CHECK(reweight_from<double>(c, static_cast<double *>(c->wgt), N_BASES * c->N, omega, s));
     }
     return finish_weights(c);
+}
+
+int ppd_set_active_sets(ppd_ctx *c, int32_t n_iters, const uint8_t *blocks, const uint8_t *bases) {
+    if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_set_active_sets: NULL context");
+    if (n_iters < 0) return fail(PPD_ERR_INVALID_ARG, "ppd_set_active_sets: n_iters < 0");
+    PPD_CUDA(cudaStreamSynchronize(c->stream));
+    dfree(c->mask_all);
+    c->mask_all = nullptr;
+    c->rand_n = c->rand_next = 0;
+    if (n_iters == 0) {
+        if (c->rand_on) {
+            c->rand_on = false;
+            drop_graph(c);
+        }
+        return PPD_OK;
+    }
+    const size_t row = (size_t)c->d + N_BASES;
+    std::vector<uint8_t> h((size_t)n_iters * row);
+    for (int32_t t = 0; t < n_iters; ++t) {
+        for (int j = 0; j < c->d; ++j) h[t * row + j] = blocks ? (blocks[(size_t)t * c->d + j] != 0) : 1;
+        for (int i = 0; i < N_BASES; ++i) h[t * row + c->d + i] = bases ? (bases[(size_t)t * N_BASES + i] != 0) : 1;
+    }
+    PPD_CHECK(dalloc(&c->mask_all, h.size()));
+    PPD_CUDA(cudaMemcpy(c->mask_all, h.data(), h.size(), cudaMemcpyHostToDevice));
+    if (!c->rand_on) {
+        // after plain iterations every block holds a prox output
+        PPD_CUDA(cudaMemset(c->blk_seen, c->p_valid ? 1 : 0, c->d));
+        c->rand_on = true;
+        c->gpart_stale = true;
+        drop_graph(c);
+    }
+    c->rand_n = n_iters;
+    return PPD_OK;
 }
 
 int ppd_get_prior_weights(ppd_ctx *c, double *w, int64_t len) {
@@ -1167,7 +1259,9 @@ int ppd_group_iterate(ppd_group *g, int32_t n_iters) {
     for (ppd_ctx *c : g->ctxs) any_first = any_first || !c->p_valid;
     if (any_first) {
         for (ppd_ctx *c : g->ctxs) {
+            PPD_CHECK(rand_prepare(c, c->stream));
             PPD_CHECK(iteration_body<float>(c, c->stream, !c->p_valid));
+            PPD_CHECK(rand_finish(c, c->stream));
             c->p_valid = true;
             c->iters++;
         }
@@ -1219,7 +1313,9 @@ int ppd_group_iterate(ppd_group *g, int32_t n_iters) {
         PPD_CUDA(cudaStreamWaitEvent(g->stream, g->joins[i], 0));
     }
     for (int it = 0; it < n_iters; ++it) {
+        for (ppd_ctx *c : g->ctxs) PPD_CHECK(rand_prepare(c, g->stream));
         PPD_CUDA(cudaGraphLaunch(g->exec, g->stream));
+        for (ppd_ctx *c : g->ctxs) PPD_CHECK(rand_finish(c, g->stream));
         for (size_t i = 0; i < g->ctxs.size(); ++i) {
             g->ctxs[i]->iters++;
             g->ctxs[i]->launches += g->kernels[i];
@@ -1252,7 +1348,7 @@ uint64_t order_fingerprint(const ppd_ctx *c) {   // FNV-1a over the processing o
 }
 
 int64_t state_bytes(const ppd_ctx *c) {
-    return (int64_t)sizeof(StateHeader) + (int64_t)c->rsz * (11 * c->N + 4 * c->M);
+    return (int64_t)sizeof(StateHeader) + (int64_t)c->rsz * (11 * c->N + 4 * c->M) + c->d;
 }
 }  // namespace
 
@@ -1267,7 +1363,7 @@ int ppd_get_state(ppd_ctx *c, void *blob, int64_t *bytes) {
     if (*bytes < need) return fail(PPD_ERR_INVALID_ARG, "ppd_get_state: buffer too small");
     StateHeader h{};
     std::memcpy(h.magic, "PPDSTATE", 8);
-    h.version = 1;
+    h.version = 2;
     h.precision = c->cfg.precision;
     h.n0 = c->L0;
     h.n1 = c->L1;
@@ -1291,6 +1387,8 @@ int ppd_get_state(ppd_ctx *c, void *blob, int64_t *bytes) {
     PPD_CUDA(cudaMemcpy(o, c->v, 2 * c->M * rb, cudaMemcpyDeviceToHost));
     o += 2 * c->M * rb;
     PPD_CUDA(cudaMemcpy(o, c->p, 2 * c->M * rb, cudaMemcpyDeviceToHost));
+    o += 2 * c->M * rb;
+    PPD_CUDA(cudaMemcpy(o, c->blk_seen, c->d, cudaMemcpyDeviceToHost));
     *bytes = need;
     return PPD_OK;
 }
@@ -1301,7 +1399,7 @@ int ppd_set_state(ppd_ctx *c, const void *blob, int64_t bytes) {
     if (bytes != state_bytes(c)) return fail(PPD_ERR_INVALID_ARG, "ppd_set_state: size mismatch");
     StateHeader h;
     std::memcpy(&h, blob, sizeof(h));
-    if (std::memcmp(h.magic, "PPDSTATE", 8) != 0 || h.version != 1 || h.precision != c->cfg.precision ||
+    if (std::memcmp(h.magic, "PPDSTATE", 8) != 0 || h.version != 2 || h.precision != c->cfg.precision ||
         h.n0 != c->L0 || h.n1 != c->L1 || h.M != c->M || h.d != c->d)
         return fail(PPD_ERR_INVALID_ARG, "ppd_set_state: blob made for another configuration");
     if (h.order_hash != order_fingerprint(c))
@@ -1319,8 +1417,11 @@ int ppd_set_state(ppd_ctx *c, const void *blob, int64_t bytes) {
     PPD_CUDA(cudaMemcpy(c->v, o, 2 * c->M * rb, cudaMemcpyHostToDevice));
     o += 2 * c->M * rb;
     PPD_CUDA(cudaMemcpy(c->p, o, 2 * c->M * rb, cudaMemcpyHostToDevice));
+    o += 2 * c->M * rb;
+    PPD_CUDA(cudaMemcpy(c->blk_seen, o, c->d, cudaMemcpyHostToDevice));
     c->iters = h.iters;
     c->p_valid = h.p_valid != 0;
+    c->gpart_stale = true;   // the partial tiles belong to the replaced dual
     return PPD_OK;
 }
 

@@ -154,6 +154,18 @@ struct ppd_ctx {
     int psiw_iters = 0;
     uint64_t gen = 0;   // bumped whenever captured graphs of this context go stale
 
+    // randomised active sets of Algorithm 3 (ppd_set_active_sets): masks for
+    // the next rand_n iterations, rand_n x (d + 9) bytes (d block flags, then
+    // 9 basis flags, Dirac first); the current iteration's row; per block
+    // whether it has a prox output (Algorithm 2 warm start); and a device
+    // flag that makes the gridding recompute the partial tiles of inactive
+    // blocks (set while gpart may hold other data than their last tiles)
+    bool rand_on = false;
+    uint8_t *mask_all = nullptr, *mask_cur = nullptr, *blk_seen = nullptr;
+    int32_t rand_n = 0, rand_next = 0;
+    int *regrid_d = nullptr;
+    bool gpart_stale = true;
+
     // parameters
     double eta = 0, zeta = 1, tau = 0.49, kappa = 1e-4, op_norm_sq = 0;
     int power_done = 0;
@@ -206,7 +218,8 @@ enum GridMode { GR_OP = 0, GR_OP_U = 1, GR_DUAL = 2 };
 template <typename R>
 int degrid(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const int64_t *perm_out,
            cudaStream_t s);
-template <typename R> int subiter(ppd_ctx *c, cudaStream_t s);
+template <typename R>
+int subiter(ppd_ctx *c, cudaStream_t s, int only_first = 0, double beta = 0.0, int write_p = 0);
 int block_norms(ppd_ctx *c, int which, cudaStream_t s);
 template <typename R>
 int grid_vis(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm_in, cplx_t<R> *grid,

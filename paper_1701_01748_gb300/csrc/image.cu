@@ -44,11 +44,14 @@ template <int NTH> __device__ void cta_sum3(double a, double b, double c, double
 // u0 <- clip(u0 + w0 xt/3, kappa); ut_all = (w0 u0 + ut)/3;
 // xbar = P_C(x - tau (eta g + zeta ut_all)); xt = 2 xbar - x; x = xbar;
 // FP64 partials (||xbar - x||^2, ||xbar||^2, ||xbar - x0||^2) per CTA.
+// pmask: active set P of Algorithm 3 (Dirac flag first) or null; a Dirac
+// basis outside P keeps u0.
 template <typename R>
 __global__ void __launch_bounds__(NT) k_primal(R *__restrict__ x, R *__restrict__ xt, const R *__restrict__ g,
                                                const R *__restrict__ ut, R *__restrict__ u0,
                                                const R *__restrict__ w0, const R *__restrict__ xtrue, int64_t N,
-                                               R tau, R eta, R zeta, R kappa, double *__restrict__ part) {
+                                               R tau, R eta, R zeta, R kappa, double *__restrict__ part,
+                                               const uint8_t *__restrict__ pmask) {
     // per-thread sums in the working precision, Kahan-compensated, then a
     // fixed-order FP64 reduction across the CTA
     R sd = 0, sx = 0, se = 0, cd = 0, cx = 0, ce = 0;
@@ -58,12 +61,15 @@ __global__ void __launch_bounds__(NT) k_primal(R *__restrict__ x, R *__restrict_
         s = t;
     };
     const R third = R(1.0 / 3.0);
+    const bool dirac_on = !pmask || pmask[0];
     for (int64_t e = blockIdx.x * (int64_t)NT + threadIdx.x; e < N; e += (int64_t)gridDim.x * NT) {
         const R xo = x[e], xte = xt[e];
         const R wd = w0 ? w0[e] : R(1);
-        R un = u0[e] + wd * (xte * third);
-        un = fmin(fmax(un, -kappa), kappa);
-        u0[e] = un;
+        R un = u0[e];
+        if (dirac_on) {
+            un = fmin(fmax(un + wd * (xte * third), -kappa), kappa);
+            u0[e] = un;
+        }
         const R utot = (wd * un + ut[e]) * third;
         const R xb = fmax(R(0), xo - tau * (eta * g[e] + zeta * utot));
         xt[e] = R(2) * xb - xo;
@@ -128,7 +134,8 @@ template <typename R> int primal_step(ppd_ctx *c, cudaStream_t s) {
                                                 static_cast<const R *>(c->g), static_cast<const R *>(c->ut),
                                                 static_cast<R *>(c->u), static_cast<const R *>(c->wgt),
                                                 static_cast<const R *>(c->xtrue), c->N, (R)c->tau, (R)c->eta,
-                                                (R)(c->zeta / c->psiw2), (R)(c->kappa * c->psiw2), c->prim_part);
+                                                (R)(c->zeta / c->psiw2), (R)(c->kappa * c->psiw2), c->prim_part,
+                                                c->rand_on ? c->mask_cur + c->d : nullptr);
     return launch_end(c, site, s);
 }
 

@@ -119,14 +119,17 @@ __device__ __forceinline__ void ana_tile(const R *__restrict__ src, int in_pitch
 //   coef: coefficient images (basis b+1 at coef + (b+1)*N, pitch L), written
 //         (mode 0: c = D x / 3) or clip-updated (mode 1: u = clip(u + w D x / 3, kappa))
 //   wgt:  prior weights (same layout as coef) or null (w = 1)
+//   pmask: active set P of Algorithm 3 (9 flags, Dirac first) or null; in
+//         mode 1 a basis outside P keeps u_b and is skipped at every level
 template <typename R>
 __global__ void __launch_bounds__(NT) k_sara_ana(const R *__restrict__ in, int in_pitch, int64_t in_bstride, int n,
                                                  R *__restrict__ ll, int64_t ll_bstride, int last,
                                                  R *__restrict__ coef, const R *__restrict__ wgt, int L, int64_t N,
-                                                 int mode, R kappa) {
+                                                 int mode, R kappa, const uint8_t *__restrict__ pmask) {
     __shared__ R tin[AEXT * AEXT];
     __shared__ R rowf[AEXT * 2 * TSA];
     const int b = blockIdx.y;
+    if (mode == 1 && pmask && !pmask[b + 1]) return;
     const int h = n / 2, tpd = h > TSA ? h / TSA : 1;
     const int R0 = (blockIdx.x / tpd) * TSA, C0 = (blockIdx.x % tpd) * TSA;
     const R *src = in + (int64_t)b * in_bstride;
@@ -271,6 +274,7 @@ inline int tiles(int h, int ts) { return h > ts ? (h / ts) * (h / ts) : 1; }
 // clip-updates u with the prior weights and the clip level kappa ||Psi W||^2.
 template <typename R> int analysis_all(ppd_ctx *c, const R *x, R *coef, int mode, cudaStream_t s) {
     const R *wgt = mode == 1 ? static_cast<const R *>(c->wgt) : nullptr;
+    const uint8_t *pmask = (mode == 1 && c->rand_on) ? c->mask_cur + c->d : nullptr;
     const R alpha = (R)(c->kappa * c->psiw2);
     const int L = c->L0;
     const int64_t N = c->N;
@@ -285,7 +289,7 @@ template <typename R> int analysis_all(ppd_ctx *c, const R *x, R *coef, int mode
         const int64_t bstride = l == 0 ? 0 : ll_stride;
         PPD_CHECK(launch_begin(c, "sara_analysis", s, &site));
         k_sara_ana<R><<<dim3(tiles(h, TSA), N_WAVELETS), NT, 0, s>>>(in, pitch, bstride, n, ll[l & 1], ll_stride, last,
-                                                                     coef, wgt, L, N, mode, alpha);
+                                                                     coef, wgt, L, N, mode, alpha, pmask);
         PPD_CHECK(launch_end(c, site, s));
     }
     return PPD_OK;

@@ -120,6 +120,12 @@ template <typename R> struct VisArgs {
     const int32_t *blk_ptr, *blk_list;
     const double *eps;
     int *err;
+    // randomised active sets (null: every block active): the current
+    // iteration's block flags, per-block "has a prox output" flags, and the
+    // flag that makes the gridding redo the partial tiles of inactive blocks
+    const uint8_t *bmask;
+    uint8_t *seen;
+    const int *regrid;
     // operator mode I/O (caller order through perm when non-null)
     const cplx_t<R> *op_in;
     cplx_t<R> *op_out;
@@ -287,7 +293,13 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
             }
             __syncthreads();
         }
-        const double mu = (MODE != DG_OP) ? A.mu[A.ch_block[ch]] : 0.0;
+        const int blk = A.ch_block[ch];
+        const double mu = (MODE != DG_OP) ? A.mu[blk] : 0.0;
+        // block outside the active set D: z, w untouched (only the residual
+        // statistic is formed); block without a prox output yet: w = z, so
+        // that the next Algorithm 2 step starts from P_B(z)
+        const bool act = MODE == DG_OP || !A.bmask || A.bmask[blk];
+        const bool first_blk = MODE == DG_FIRST || (A.seen && !A.seen[blk]);
         Acc<R> s_w, s_r;
         for (int i = threadIdx.x; i < count; i += DG_NT) {
             const int gi = start + i;
@@ -315,19 +327,21 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
             if (MODE == DG_OP) {
                 A.op_out[A.perm ? A.perm[gi] : gi] = phix;
             } else {
-                const R invU = R(1) / cur.rc.U;
-                const C zz{cur.v.x * invU + phix.x, cur.v.y * invU + phix.y};
-                A.z[gi] = zz;
-                C ww;
-                if (MODE == DG_FIRST) {
-                    ww = zz;
-                } else {
-                    const R mu_u = (R)mu * cur.rc.U;
-                    ww = C{cur.p.x - mu_u * (cur.p.x - zz.x), cur.p.y - mu_u * (cur.p.y - zz.y)};
+                if (act) {
+                    const R invU = R(1) / cur.rc.U;
+                    const C zz{cur.v.x * invU + phix.x, cur.v.y * invU + phix.y};
+                    A.z[gi] = zz;
+                    C ww;
+                    if (first_blk) {
+                        ww = zz;
+                    } else {
+                        const R mu_u = (R)mu * cur.rc.U;
+                        ww = C{cur.p.x - mu_u * (cur.p.x - zz.x), cur.p.y - mu_u * (cur.p.y - zz.y)};
+                    }
+                    A.w[gi] = ww;
+                    const R dx = ww.x - cur.y.x, dy = ww.y - cur.y.y;
+                    s_w.add(dx * dx + dy * dy);
                 }
-                A.w[gi] = ww;
-                const R dx = ww.x - cur.y.x, dy = ww.y - cur.y.y;
-                s_w.add(dx * dx + dy * dy);
                 const R ex = phix.x - cur.y.x, ey = phix.y - cur.y.y;
                 s_r.add(ex * ex + ey * ey);
             }
@@ -340,12 +354,24 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
 
 // ----------------------------------------------------------------- sub-iteration
 // Algorithm 2 step with the block scale c of the previous step:
-//   p = P_B(w) = y + c (w - y);  w = p - mu U (p - z);  partial ||w - y||^2
+//   p = P_B(w) = y + c (w - y);  w = q - mu U (q - z);  partial ||w - y||^2
+// with q = p (Algorithm 2) or, for the accelerated form, the extrapolated
+// point q = p + beta (p - p_prev), p_prev read from and p written to the
+// warm-start array (beta = 0: p_prev is not read; write_p = 0: p not written).
+// only_first: the extra step that moves the start of a block with no prox
+// output yet from z to P_B(z) (randomised active sets); chunks of other
+// blocks, and of blocks outside D, pass their partial through unchanged.
 template <typename R>
-__global__ void __launch_bounds__(DG_NT) k_subiter(VisArgs<R> A) {
+__global__ void __launch_bounds__(DG_NT) k_subiter(VisArgs<R> A, int only_first, R beta, int write_p) {
     using C = cplx_t<R>;
     const int ch = blockIdx.x;
     const int start = A.ch_start[ch], count = A.ch_count[ch], blk = A.ch_block[ch];
+    const bool act = !A.bmask || A.bmask[blk];
+    const bool first_blk = A.seen && !A.seen[blk];
+    if (!act || (only_first && !first_blk)) {
+        if (threadIdx.x == 0) A.partials[NPART * (int64_t)ch] = A.part_in[NPART * (int64_t)ch];
+        return;
+    }
     const R c = (R)block_scale(A, blk), mu = (R)A.mu[blk];
     Acc<R> s_w;
     for (int i = threadIdx.x; i < count; i += DG_NT) {
@@ -353,8 +379,14 @@ __global__ void __launch_bounds__(DG_NT) k_subiter(VisArgs<R> A) {
         const R U = A.rec[gi].U;
         const C yy = A.y[gi], ww = A.w[gi], zz = A.z[gi];
         const C pp{yy.x + c * (ww.x - yy.x), yy.y + c * (ww.y - yy.y)};
+        C q = pp;
+        if (beta != R(0)) {
+            const C pm = A.p[gi];
+            q = C{pp.x + beta * (pp.x - pm.x), pp.y + beta * (pp.y - pm.y)};
+        }
+        if (write_p) A.p[gi] = pp;
         const R mu_u = mu * U;
-        const C wn{pp.x - mu_u * (pp.x - zz.x), pp.y - mu_u * (pp.y - zz.y)};
+        const C wn{q.x - mu_u * (q.x - zz.x), q.y - mu_u * (q.y - zz.y)};
         A.w[gi] = wn;
         const R dx = wn.x - yy.x, dy = wn.y - yy.y;
         s_w.add(dx * dx + dy * dy);
@@ -422,13 +454,19 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
     const int start = A.ch_start[ch], count = A.ch_count[ch], tl = A.ch_tile[ch];
     const int row0 = (tl / A.ntile1) * T, col0 = (tl % A.ntile1) * T;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // a block outside the active set D keeps v_j, so its chunks' partial
+    // tiles from the last gridding still hold G^dagger Theta^dagger v_j
+    const int blk = A.ch_block[ch];
+    const bool act = MODE != GR_DUAL || !A.bmask || A.bmask[blk];
+    if (!act && !(A.regrid && *A.regrid)) return;
     // warps that scatter: at least GRID_MINV visibilities each, so that a
     // small chunk clears and sums only as many private tiles as it fills
     const int nwu = min(NW, max(1, (count + GRID_MINV - 1) / GRID_MINV));
     for (int i = threadIdx.x; i < (KB_DEG + 1) * KB_J; i += NT) poly[i] = A.kbpoly ? A.kbpoly[i] : 0.f;
     for (int e = threadIdx.x; e < nwu * E * P; e += NT) priv[e] = C{0, 0};
     R c = 0;
-    if (MODE == GR_DUAL) c = (R)block_scale(A, A.ch_block[ch]);
+    if (MODE == GR_DUAL && act) c = (R)block_scale(A, blk);
+    if (MODE == GR_DUAL && act && A.seen && threadIdx.x == 0) A.seen[blk] = 1;
     __syncthreads();
 
     C *mine = priv + warp * E * P;
@@ -439,12 +477,14 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
             const int gi = start + base + threadIdx.x;
             const VisRec<R> rc = A.rec[gi];
             C vv;
-            if (MODE == GR_DUAL) {
+            if (MODE == GR_DUAL && act) {
                 const C yy = A.y[gi], ww = A.w[gi], zz = A.z[gi];
                 const C pp{yy.x + c * (ww.x - yy.x), yy.y + c * (ww.y - yy.y)};
                 vv = C{rc.U * (zz.x - pp.x), rc.U * (zz.y - pp.y)};
                 A.v[gi] = vv;
                 A.p[gi] = pp;
+            } else if (MODE == GR_DUAL) {
+                vv = A.v[gi];
             } else {
                 vv = A.op_in[A.perm ? A.perm[gi] : gi];
                 if (MODE == GR_OP_U) vv = C{rc.U * vv.x, rc.U * vv.y};
@@ -582,6 +622,9 @@ template <typename R> VisArgs<R> make_args(ppd_ctx *c) {
     A.blk_list = c->ch.blk_list;
     A.eps = c->eps_d;
     A.err = c->err;
+    A.bmask = c->rand_on ? c->mask_cur : nullptr;
+    A.seen = c->rand_on ? c->blk_seen : nullptr;
+    A.regrid = c->rand_on ? c->regrid_d : nullptr;
     return A;
 }
 
@@ -729,11 +772,11 @@ int grid_vis(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cpl
                       : grid_t<R, 32>(c, mode, in, perm, grid, s, combine);
 }
 
-template <typename R> int subiter(ppd_ctx *c, cudaStream_t s) {
+template <typename R> int subiter(ppd_ctx *c, cudaStream_t s, int only_first, double beta, int write_p) {
     if (c->ch.n == 0) return PPD_OK;
     int site;
     PPD_CHECK(launch_begin(c, "subiter", s, &site));
-    k_subiter<R><<<(unsigned)c->ch.n, DG_NT, 0, s>>>(make_args<R>(c));
+    k_subiter<R><<<(unsigned)c->ch.n, DG_NT, 0, s>>>(make_args<R>(c), only_first, (R)beta, write_p);
     return launch_end(c, site, s);
 }
 
@@ -765,7 +808,7 @@ template int degrid<float>(ppd_ctx *, int, const float2 *, float2 *, const int64
 template int degrid<double>(ppd_ctx *, int, const double2 *, double2 *, const int64_t *, cudaStream_t);
 template int grid_vis<float>(ppd_ctx *, int, const float2 *, const int64_t *, float2 *, cudaStream_t, bool);
 template int grid_vis<double>(ppd_ctx *, int, const double2 *, const int64_t *, double2 *, cudaStream_t, bool);
-template int subiter<float>(ppd_ctx *, cudaStream_t);
-template int subiter<double>(ppd_ctx *, cudaStream_t);
+template int subiter<float>(ppd_ctx *, cudaStream_t, int, double, int);
+template int subiter<double>(ppd_ctx *, cudaStream_t, int, double, int);
 
 }  // namespace ppd

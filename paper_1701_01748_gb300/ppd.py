@@ -26,6 +26,8 @@ PPD_FP64_PLAIN = 0
 PPD_FP32_FP64NORMS = 1
 PPD_INNER_WARM = 0
 PPD_INNER_CURRENT = 1
+PPD_INNER_FB = 0
+PPD_INNER_FISTA = 1
 
 
 class ppd_config(ct.Structure):
@@ -36,7 +38,7 @@ class ppd_config(ct.Structure):
                 ("zeta", ct.c_double), ("precision", ct.c_int32), ("precond", ct.c_int32),
                 ("inner_init", ct.c_int32), ("use_graph", ct.c_int32), ("tile", ct.c_int32),
                 ("chunk", ct.c_int32), ("power_iters", ct.c_int32), ("power_tol", ct.c_double),
-                ("stream", ct.c_void_p)]
+                ("stream", ct.c_void_p), ("inner_solver", ct.c_int32)]
 
 
 class ppd_stats(ct.Structure):
@@ -92,6 +94,7 @@ def _lib():
             "ppd_set_prior_weights": (I, [P, D, I64]),
             "ppd_reweight": (I, [P, ct.c_double]),
             "ppd_get_prior_weights": (I, [P, D, I64]),
+            "ppd_set_active_sets": (I, [P, I32, ct.POINTER(ct.c_uint8), ct.POINTER(ct.c_uint8)]),
             "ppd_op_forward": (I, [P, P, P, P]),
             "ppd_op_adjoint": (I, [P, P, P, P]),
             "ppd_op_adjoint_noalloc": (I, [P, P, P, P]),
@@ -266,6 +269,18 @@ def ppd_get_prior_weights(ctx: int, n0: int, n1: int) -> np.ndarray:
     out = np.empty(9 * n0 * n1)
     _check(_lib().ppd_get_prior_weights(ctx, _dptr(out), out.size), "ppd_get_prior_weights")
     return out.reshape(9, n0, n1)
+
+
+def ppd_set_active_sets(ctx: int, blocks=None, bases=None, n_iters: int | None = None) -> None:
+    """Queue the sets D (n_iters x n_blocks) and P (n_iters x 9) of the next
+    iterations; None = full sets; n_iters = 0 returns to the plain iteration."""
+    b = None if blocks is None else np.ascontiguousarray(blocks, dtype=np.uint8)
+    p = None if bases is None else np.ascontiguousarray(bases, dtype=np.uint8)
+    if n_iters is None:
+        n_iters = b.shape[0] if b is not None else (p.shape[0] if p is not None else 0)
+    u8 = ct.POINTER(ct.c_uint8)
+    _check(_lib().ppd_set_active_sets(ctx, int(n_iters), None if b is None else b.ctypes.data_as(u8),
+                                      None if p is None else p.ctypes.data_as(u8)), "ppd_set_active_sets")
 
 
 def ppd_op_forward(ctx: int, x_dev: int, y_dev: int, stream=None) -> None:

@@ -172,11 +172,13 @@ def run_both(p, prec, n_iter, **kw):
     n_itr = kw.pop("n_itr", 1)
     precond = kw.pop("precond", 1)
     init = kw.pop("inner_init", ppd.PPD_INNER_WARM)
+    solver_kind = kw.pop("inner_solver", ppd.PPD_INNER_FB)
     S = oppd.make_setup(p.omega, p.y, p.theta, p.block, p.n_blocks, p.L, precond=bool(precond),
                         n_itr=n_itr, power_iters=400, x_true=p.x_true,
-                        inner_init="current" if init == ppd.PPD_INNER_CURRENT else "warm")
+                        inner_init="current" if init == ppd.PPD_INNER_CURRENT else "warm",
+                        inner_solver="fista" if solver_kind == ppd.PPD_INNER_FISTA else "fb")
     s = ppd.Solver(p.L, p.n_blocks, precision=prec, eta=S.eta, n_itr=n_itr, precond=precond,
-                   inner_init=init, **kw)
+                   inner_init=init, inner_solver=solver_kind, **kw)
     s.set_problem(p.omega, p.y, p.block, theta=p.theta, x_true=p.x_true)
     st = oppd.init_state(S)
     for _ in range(n_iter):
@@ -211,6 +213,16 @@ def test_ppd_multiblock_subiterations_weights(prec):
 def test_inner_start_at_z(prec):
     p = problem("small", **SMALL)
     xg, st, hist, stats, S = run_both(p, prec, 20, n_itr=3, inner_init=ppd.PPD_INNER_CURRENT)
+    assert rel(xg, st.x) <= TOL[prec]["img"], rel(xg, st.x)
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
+@pytest.mark.parametrize("init", ["warm", "current"])
+def test_accelerated_inner_solver(prec, init):
+    """Accelerated Algorithm 2 (FISTA t-sequence) with 6 sub-iterations."""
+    p = problem("small", **SMALL)
+    xg, st, hist, stats, S = run_both(p, prec, 20, n_itr=6, inner_solver=ppd.PPD_INNER_FISTA,
+                                      inner_init=ppd.PPD_INNER_CURRENT if init == "current" else ppd.PPD_INNER_WARM)
     assert rel(xg, st.x) <= TOL[prec]["img"], rel(xg, st.x)
 
 
