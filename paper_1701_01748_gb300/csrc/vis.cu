@@ -226,6 +226,10 @@ template <typename R, int T, int MODE>
 __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
     k_degrid(const __grid_constant__ CUtensorMap tmap, int use_tma, const cplx_t<R> *__restrict__ grid, VisArgs<R> A,
              int n_chunks) {
+    pdl_enter();
+    // the grid was written through the generic proxy by the previous kernel;
+    // order those writes before this kernel's TMA (async proxy) reads
+    asm volatile("fence.proxy.async.global;" ::: "memory");
     using C = cplx_t<R>;
     constexpr int E = T + HALO;
     constexpr int TILE_BYTES = E * E * (int)sizeof(C);
@@ -363,6 +367,7 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
 // blocks, and of blocks outside D, pass their partial through unchanged.
 template <typename R>
 __global__ void __launch_bounds__(DG_NT) k_subiter(VisArgs<R> A, int only_first, R beta, int write_p) {
+    pdl_enter();
     using C = cplx_t<R>;
     const int ch = blockIdx.x;
     const int start = A.ch_start[ch], count = A.ch_count[ch], blk = A.ch_block[ch];
@@ -439,6 +444,7 @@ template <> struct GridCfg<double> { static constexpr int NWARP = 4; };
 
 template <typename R, int T, int MODE>
 __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, cplx_t<R> *__restrict__ gpart) {
+    pdl_enter();
     using C = cplx_t<R>;
     constexpr int NW = GridCfg<R>::NWARP, NT = NW * 32;
     constexpr int E = T + HALO, P = E + 1;   // P: padded pitch of the private tiles
@@ -561,6 +567,7 @@ __global__ void __launch_bounds__(256) k_combine(const cplx_t<R> *__restrict__ g
                                                  const int32_t *__restrict__ tile_n,
                                                  const int32_t *__restrict__ active, int K1, int nt0, int nt1,
                                                  cplx_t<R> *__restrict__ grid) {
+    pdl_enter();
     using C = cplx_t<R>;
     constexpr int E = T + HALO;
     __shared__ int f_s[4], n_s[4];
@@ -662,9 +669,9 @@ int degrid_t(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const 
     const unsigned nb = (unsigned)std::min<int64_t>(nch, (int64_t)sms * per_sm);
     int site;
     PPD_CHECK(launch_begin(c, mode == DG_OP ? "degrid_op" : "degrid_dual", s, &site));
-    if (mode == DG_OP) k_degrid<R, T, DG_OP><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A, nch);
-    else if (mode == DG_DUAL) k_degrid<R, T, DG_DUAL><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A, nch);
-    else k_degrid<R, T, DG_FIRST><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A, nch);
+    if (mode == DG_OP) PPD_CUDA(launch_pdl(k_degrid<R, T, DG_OP>, dim3(nb), dim3(DG_NT), sh, s, c->tmap_a, use_tma, grid, A, nch));
+    else if (mode == DG_DUAL) PPD_CUDA(launch_pdl(k_degrid<R, T, DG_DUAL>, dim3(nb), dim3(DG_NT), sh, s, c->tmap_a, use_tma, grid, A, nch));
+    else PPD_CUDA(launch_pdl(k_degrid<R, T, DG_FIRST>, dim3(nb), dim3(DG_NT), sh, s, c->tmap_a, use_tma, grid, A, nch));
     return launch_end(c, site, s);
 }
 
@@ -688,15 +695,15 @@ int grid_t(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_
     if (c->ch.n > 0) {
         PPD_CHECK(launch_begin(c, mode == GR_DUAL ? "grid_dual" : "grid_op", s, &site));
         const unsigned nb = (unsigned)c->ch.n;
-        if (mode == GR_OP) k_grid<R, T, GR_OP><<<nb, NT, sh, s>>>(A, gp);
-        else if (mode == GR_OP_U) k_grid<R, T, GR_OP_U><<<nb, NT, sh, s>>>(A, gp);
-        else k_grid<R, T, GR_DUAL><<<nb, NT, sh, s>>>(A, gp);
+        if (mode == GR_OP) PPD_CUDA(launch_pdl(k_grid<R, T, GR_OP>, dim3(nb), dim3(NT), sh, s, A, gp));
+        else if (mode == GR_OP_U) PPD_CUDA(launch_pdl(k_grid<R, T, GR_OP_U>, dim3(nb), dim3(NT), sh, s, A, gp));
+        else PPD_CUDA(launch_pdl(k_grid<R, T, GR_DUAL>, dim3(nb), dim3(NT), sh, s, A, gp));
         PPD_CHECK(launch_end(c, site, s));
     }
     if (c->ch.n_active == 0 || !combine) return PPD_OK;
     PPD_CHECK(launch_begin(c, "grid_combine", s, &site));
-    k_combine<R, T><<<(unsigned)c->ch.n_active * 4, 256, 0, s>>>(gp, c->ch.tile_first, c->ch.tile_n, c->ch.active,
-                                                            c->K1, c->K0 / T, c->K1 / T, grid);
+    PPD_CUDA(launch_pdl(k_combine<R, T>, dim3((unsigned)c->ch.n_active * 4), dim3(256), 0, s, gp, c->ch.tile_first, c->ch.tile_n, c->ch.active,
+                                                            c->K1, c->K0 / T, c->K1 / T, grid));
     return launch_end(c, site, s);
 }
 
@@ -776,7 +783,7 @@ template <typename R> int subiter(ppd_ctx *c, cudaStream_t s, int only_first, do
     if (c->ch.n == 0) return PPD_OK;
     int site;
     PPD_CHECK(launch_begin(c, "subiter", s, &site));
-    k_subiter<R><<<(unsigned)c->ch.n, DG_NT, 0, s>>>(make_args<R>(c), only_first, (R)beta, write_p);
+    PPD_CUDA(launch_pdl(k_subiter<R>, dim3((unsigned)c->ch.n), dim3(DG_NT), 0, s, make_args<R>(c), only_first, (R)beta, write_p));
     return launch_end(c, site, s);
 }
 
