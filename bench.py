@@ -232,13 +232,18 @@ def bench_batch(args, rank, world, local):
     import torch
     from paper_1701_01748_gb300 import ppd, synth
     n = int(args.workload[len("batch"):] or 8)
-    probs = synth.make_batch(n, seed=1704 + 1000 * rank)
+    # batch32: 32 problems of 256^2-1024^2, M = 2-8 x pixels, 4-32 blocks; other sizes: 128^2-256^2
+    probs = synth.make_batch32(seed=1704 + 1000 * rank) if n == 32 else synth.make_batch(n, seed=1704 + 1000 * rank)
     dev = torch.device("cuda", local)
-    solvers = []
+    solvers, tuned = [], []
+    _log(f"{n} problems, {sum(p.M for p in probs)} visibilities in all")
     for p in probs:
         s = ppd.Solver(p.L, p.n_blocks, precision=ppd.PPD_FP32_FP64NORMS)
         s.set_problem(p.omega, p.y, p.block, theta=p.theta, x_true=p.x_true)
+        if args.autotune:
+            tuned.append(ppd.ppd_autotune(s.ctx, 5))
         solvers.append(s)
+    _log("set-up done")
     for s in solvers:
         s.iterate(max(args.warmup, 3), stats=False)
     torch.cuda.synchronize(dev)
@@ -261,7 +266,10 @@ def bench_batch(args, rank, world, local):
             "metric": "PPD iterations/s summed over a batch of independent problems", "unit": "iters/s",
             "value": total / t_grp, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "problems": [[p.L, p.M, p.n_blocks] for p in probs]},
+            "config": {"workload": args.workload, "problems": [[p.L, p.M, p.n_blocks] for p in probs],
+                       "visibilities": int(sum(p.M for p in probs)),
+                       "gridding_tile_and_chunk": tuned if tuned else "library default (16, 1024)",
+                       "timing": "wall clock between device synchronisations, one group graph launch per iteration"},
             "sequential_iters_per_s": total / t_seq, "batching_speedup": t_seq / t_grp}), flush=True)
     for s in solvers:
         s.close()
@@ -398,6 +406,7 @@ def main():
     ap.add_argument("--study", default="", help="ggd: PD vs PPD convergence on generalised-Gaussian coverages; "
                                                 "random: randomised active sets")
     ap.add_argument("--isnr", type=float, default=30.0, help="input SNR (dB) of the study problems")
+    ap.add_argument("--autotune", action="store_true", help="batch workloads: autotune each problem's gridding")
     ap.add_argument("--quick", action="store_true",
                     help="only the timed FP32 steps (for profiler launch lists); eta from 20 power steps")
     args = ap.parse_args()

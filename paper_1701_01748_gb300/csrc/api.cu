@@ -244,8 +244,16 @@ template <typename R> int iteration_body(ppd_ctx *c, cudaStream_t s, bool first)
     }
     c->part_in = bank[cur];
     c->part_out = bank[0];
-    PPD_CHECK(grid_vis<R>(c, GR_DUAL, nullptr, nullptr, gv, s, /*combine=*/false));
-    PPD_CHECK(fft_inverse_partials<R>(c, static_cast<R *>(c->g), s));
+    // small grids: the inverse column pass sums the partial tiles itself (no
+    // combined grid in memory); from K = 4096 on, a combine pass with one CTA
+    // group per tile reads them contiguously and the column pass reads the grid
+    if (c->K0 >= 4096) {
+        PPD_CHECK(grid_vis<R>(c, GR_DUAL, nullptr, nullptr, gv, s, /*combine=*/true));
+        PPD_CHECK(fft_inverse<R>(c, gv, static_cast<R *>(c->g), s));
+    } else {
+        PPD_CHECK(grid_vis<R>(c, GR_DUAL, nullptr, nullptr, gv, s, /*combine=*/false));
+        PPD_CHECK(fft_inverse_partials<R>(c, static_cast<R *>(c->g), s));
+    }
     if (fork) PPD_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
     PPD_CHECK(primal_step<R>(c, s));
     return PPD_OK;

@@ -37,7 +37,7 @@ template <> struct __align__(16) VisRec<float> { int packed; float f0, f1, U; };
 template <> struct __align__(16) VisRec<double> { int packed; int pad; double f0, f1, U; };
 
 constexpr int KB_J = 8;          // interpolation taps per axis
-constexpr int KB_DEG = 9;        // degree of the per-tap FP32 weight polynomial
+constexpr int KB_DEG = 7;        // degree of the per-tap FP32 weight polynomial (fit error 4e-8)
 constexpr int HALO = 8;          // extended tile = (T + HALO)^2 cells
 constexpr int N_BASES = 9;       // Dirac + db1..db8
 constexpr int N_WAVELETS = 8;
@@ -52,34 +52,6 @@ constexpr int ERR_BOUNDS = 4;
 
 // bounded spin for mbarrier waits (iterations of try_wait)
 constexpr long long SPIN_LIMIT = 1ll << 21;
-
-// ---------------------------------------------------------------- launches
-// Programmatic dependent launch (sm_90 and later): the iteration's kernels
-// are launched with programmatic stream serialisation, so a kernel's CTAs
-// can be scheduled while its predecessor in the stream drains.  Every such
-// kernel starts with pdl_enter(): wait until the predecessor has completed
-// and its writes are visible (nothing is read or written before that), then
-// let the successor be scheduled.  Launched normally, both are no-ops.
-__device__ __forceinline__ void pdl_enter() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
-template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                              Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
-}
 
 // ---------------------------------------------------------------- status
 struct Error {

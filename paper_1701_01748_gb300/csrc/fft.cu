@@ -152,7 +152,6 @@ template <typename R, int K>
 __global__ void __launch_bounds__(NT) k_rows_fwd(const R *__restrict__ x, cplx_t<R> *__restrict__ tmp,
                                                  const cplx_t<R> *__restrict__ tw, const R *__restrict__ s0,
                                                  const R *__restrict__ s1, int L, const uint8_t *__restrict__ colmask) {
-    pdl_enter();
     using C = cplx_t<R>;
     constexpr int B = rows_per_cta<R>(K);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -182,7 +181,6 @@ __global__ void __launch_bounds__(NT) k_cols_fwd(const cplx_t<R> *__restrict__ t
                                                  const cplx_t<R> *__restrict__ tw, int L,
                                                  const int32_t *__restrict__ strips,
                                                  const uint8_t *__restrict__ rowmask) {
-    pdl_enter();
     using C = cplx_t<R>;
     constexpr int W = cols_per_cta<R>(K);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -210,7 +208,6 @@ __global__ void __launch_bounds__(NT) k_cols_inv(const cplx_t<R> *__restrict__ g
                                                  const cplx_t<R> *__restrict__ tw, int L,
                                                  const int32_t *__restrict__ strips,
                                                  const uint8_t *__restrict__ rowmask) {
-    pdl_enter();
     using C = cplx_t<R>;
     constexpr int W = cols_per_cta<R>(K);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -241,7 +238,6 @@ __global__ void __launch_bounds__(NT) k_cols_inv_part(const cplx_t<R> *__restric
                                                       const cplx_t<R> *__restrict__ tw, int L,
                                                       const int32_t *__restrict__ strips,
                                                       const uint8_t *__restrict__ rowmask) {
-    pdl_enter();
     using C = cplx_t<R>;
     constexpr int W = cols_per_cta<R>(K);
     constexpr int E = T + 8, NTL = K / T;
@@ -287,7 +283,6 @@ template <typename R, int K>
 __global__ void __launch_bounds__(NT) k_rows_inv(const cplx_t<R> *__restrict__ tmp, R *__restrict__ img,
                                                  const cplx_t<R> *__restrict__ tw, const R *__restrict__ s0,
                                                  const R *__restrict__ s1, int L) {
-    pdl_enter();
     using C = cplx_t<R>;
     constexpr int B = rows_per_cta<R>(K);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -323,16 +318,16 @@ template <typename R, int K> int fft_fwd_k(ppd_ctx *c, const R *x, cplx_t<R> *gr
     }
     int site;
     PPD_CHECK(launch_begin(c, "fft_fwd_rows", s, &site));
-    PPD_CUDA(launch_pdl(k_rows_fwd<R, K>, dim3((L + B - 1) / B), dim3(NT), shr, s, x, static_cast<cplx_t<R> *>(c->fft_tmp),
+    k_rows_fwd<R, K><<<(L + B - 1) / B, NT, shr, s>>>(x, static_cast<cplx_t<R> *>(c->fft_tmp),
                                                      static_cast<const cplx_t<R> *>(c->tw0),
                                                      static_cast<const R *>(c->deap0),
-                                                     static_cast<const R *>(c->deap1), L, c->col_fwd));
+                                                     static_cast<const R *>(c->deap1), L, c->col_fwd);
     PPD_CHECK(launch_end(c, site, s));
     if (c->n_fwd_strips == 0) return PPD_OK;
     PPD_CHECK(launch_begin(c, "fft_fwd_cols", s, &site));
-    PPD_CUDA(launch_pdl(k_cols_fwd<R, K>, dim3(c->n_fwd_strips), dim3(NT), shc, s, static_cast<const cplx_t<R> *>(c->fft_tmp), grid,
+    k_cols_fwd<R, K><<<c->n_fwd_strips, NT, shc, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp), grid,
                                                       static_cast<const cplx_t<R> *>(c->tw0), L, c->fwd_strips,
-                                                      c->row_fwd));
+                                                      c->row_fwd);
     PPD_CHECK(launch_end(c, site, s));
     return PPD_OK;
 }
@@ -350,16 +345,16 @@ template <typename R, int K> int fft_inv_k(ppd_ctx *c, const cplx_t<R> *grid, R 
     int site;
     if (c->n_inv_strips > 0) {
         PPD_CHECK(launch_begin(c, "fft_inv_cols", s, &site));
-        PPD_CUDA(launch_pdl(k_cols_inv<R, K>, dim3(c->n_inv_strips), dim3(NT), shc, s, grid, static_cast<cplx_t<R> *>(c->fft_tmp_inv),
+        k_cols_inv<R, K><<<c->n_inv_strips, NT, shc, s>>>(grid, static_cast<cplx_t<R> *>(c->fft_tmp_inv),
                                                           static_cast<const cplx_t<R> *>(c->tw0), L, c->inv_strips,
-                                                          c->row_inv));
+                                                          c->row_inv);
         PPD_CHECK(launch_end(c, site, s));
     }
     PPD_CHECK(launch_begin(c, "fft_inv_rows", s, &site));
-    PPD_CUDA(launch_pdl(k_rows_inv<R, K>, dim3((L + B - 1) / B), dim3(NT), shr, s, static_cast<const cplx_t<R> *>(c->fft_tmp_inv), img,
+    k_rows_inv<R, K><<<(L + B - 1) / B, NT, shr, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp_inv), img,
                                                      static_cast<const cplx_t<R> *>(c->tw0),
                                                      static_cast<const R *>(c->deap0),
-                                                     static_cast<const R *>(c->deap1), L));
+                                                     static_cast<const R *>(c->deap1), L);
     PPD_CHECK(launch_end(c, site, s));
     return PPD_OK;
 }
@@ -378,17 +373,16 @@ template <typename R, int K, int T> int fft_inv_part_k(ppd_ctx *c, R *img, cudaS
     int site;
     if (c->n_inv_strips > 0) {
         PPD_CHECK(launch_begin(c, "fft_inv_cols", s, &site));
-        PPD_CUDA(launch_pdl(k_cols_inv_part<R, K, T>, dim3(c->n_inv_strips), dim3(NT), shc, s, 
-            static_cast<const cplx_t<R> *>(c->gpart), c->ch.tile_first, c->ch.tile_n,
+        k_cols_inv_part<R, K, T><<<c->n_inv_strips, NT, shc, s>>>(static_cast<const cplx_t<R> *>(c->gpart), c->ch.tile_first, c->ch.tile_n,
             static_cast<cplx_t<R> *>(c->fft_tmp_inv), static_cast<const cplx_t<R> *>(c->tw0), L, c->inv_strips,
-            c->row_inv));
+            c->row_inv);
         PPD_CHECK(launch_end(c, site, s));
     }
     PPD_CHECK(launch_begin(c, "fft_inv_rows", s, &site));
-    PPD_CUDA(launch_pdl(k_rows_inv<R, K>, dim3((L + B - 1) / B), dim3(NT), shr, s, static_cast<const cplx_t<R> *>(c->fft_tmp_inv), img,
+    k_rows_inv<R, K><<<(L + B - 1) / B, NT, shr, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp_inv), img,
                                                      static_cast<const cplx_t<R> *>(c->tw0),
                                                      static_cast<const R *>(c->deap0),
-                                                     static_cast<const R *>(c->deap1), L));
+                                                     static_cast<const R *>(c->deap1), L);
     return launch_end(c, site, s);
 }
 

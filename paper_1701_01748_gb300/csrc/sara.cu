@@ -13,7 +13,6 @@
 #include <cmath>
 #include <algorithm>
 #include <complex>
-#include <type_traits>
 
 #include "common.cuh"
 
@@ -127,7 +126,6 @@ __global__ void __launch_bounds__(NT) k_sara_ana(const R *__restrict__ in, int i
                                                  R *__restrict__ ll, int64_t ll_bstride, int last,
                                                  R *__restrict__ coef, const R *__restrict__ wgt, int L, int64_t N,
                                                  int mode, R kappa, const uint8_t *__restrict__ pmask) {
-    pdl_enter();
     __shared__ R tin[AEXT * AEXT];
     __shared__ R rowf[AEXT * 2 * TSA];
     const int b = blockIdx.y;
@@ -152,15 +150,14 @@ __global__ void __launch_bounds__(NT) k_sara_ana(const R *__restrict__ in, int i
 
 // ------------------------------------------------------------- synthesis
 // Inverse of one level for one basis on one output tile of 2TS x 2TS samples
-// whose quadrant positions start at (R0, C0), in three phases separated by
-// barriers: stage the quadrant tiles (rows and columns R0 - F/2 + 1 ...
-// R0 + TS - 1, mod h) in shared memory, inverse along axis 0, inverse along
-// axis 1 (this thread's output mm = tid / 2TS, nn = tid % 2TS; NT == 4 TS^2).
+// whose quadrant positions start at (R0, C0).  The quadrant tiles cover rows
+// and columns R0 - F/2 + 1 ... R0 + TS - 1 (mod h).  Returns this thread's
+// output (mm = tid / 2TS, nn = tid % 2TS; NT == 4 TS^2).
 template <typename R, int F>
-__device__ __forceinline__ void syn_stage(const R *__restrict__ cb, const R *__restrict__ wb,
-                                          const R *__restrict__ sl, int from_coef, int L, int n, int R0, int C0,
-                                          R *qs) {
+__device__ __forceinline__ R syn_tile(const R *__restrict__ cb, const R *__restrict__ wb, const R *__restrict__ sl,
+                                      int from_coef, int L, int n, int R0, int C0, int b, R *qs, R *tl, R *th) {
     constexpr int EXT = TS + F / 2 - 1;
+    const Taps<R, F> f(b);
     const int h = n >> 1;
     const int base_r = R0 - F / 2 + 1, base_c = C0 - F / 2 + 1;
     for (int e = threadIdx.x; e < 4 * EXT * EXT; e += NT) {
@@ -177,14 +174,7 @@ __device__ __forceinline__ void syn_stage(const R *__restrict__ cb, const R *__r
         }
         qs[qd * SEXT * SEXT + i * SEXT + j] = v;
     }
-}
-
-template <typename R, int F>
-__device__ __forceinline__ void syn_cols(int n, int R0, int b, const R *qs, R *tl, R *th) {
-    constexpr int EXT = TS + F / 2 - 1;
-    const Taps<R, F> f(b);
-    const int h = n >> 1;
-    const int base_r = R0 - F / 2 + 1;
+    __syncthreads();
     for (int e = threadIdx.x; e < 2 * TS * EXT; e += NT) {   // inverse along axis 0
         const int mm = e / EXT, j = e % EXT;
         const int m = 2 * R0 + mm, par = mm & 1;
@@ -200,13 +190,7 @@ __device__ __forceinline__ void syn_cols(int n, int R0, int b, const R *qs, R *t
         tl[mm * SEXT + j] = sl0;
         th[mm * SEXT + j] = sh0;
     }
-}
-
-template <typename R, int F>
-__device__ __forceinline__ R syn_rows(int n, int C0, int b, const R *tl, const R *th) {
-    const Taps<R, F> f(b);
-    const int h = n >> 1;
-    const int base_c = C0 - F / 2 + 1;
+    __syncthreads();
     const int mm = threadIdx.x / (2 * TS), nnl = threadIdx.x % (2 * TS);   // inverse along axis 1
     const int nn = 2 * C0 + nnl, par = nnl & 1;
     R out = 0;
@@ -217,37 +201,23 @@ __device__ __forceinline__ R syn_rows(int n, int C0, int b, const R *tl, const R
         const R a = par ? f.h[2 * kk + 1] : f.h[2 * kk], c = par ? f.g[2 * kk + 1] : f.g[2 * kk];
         out += a * tl[mm * SEXT + jl] + c * th[mm * SEXT + jl];
     }
+    __syncthreads();   // shared tiles are reused by the caller
     return out;
-}
-
-// Filter length of wavelet basis b (db(b+1): 2b + 2 taps) as a compile-time
-// constant for fn.
-template <typename Fn> __device__ __forceinline__ auto by_taps(int b, Fn fn) {
-    switch (b) {
-        case 0: return fn(std::integral_constant<int, 2>{});
-        case 1: return fn(std::integral_constant<int, 4>{});
-        case 2: return fn(std::integral_constant<int, 6>{});
-        case 3: return fn(std::integral_constant<int, 8>{});
-        case 4: return fn(std::integral_constant<int, 10>{});
-        case 5: return fn(std::integral_constant<int, 12>{});
-        case 6: return fn(std::integral_constant<int, 14>{});
-        default: return fn(std::integral_constant<int, 16>{});
-    }
 }
 
 template <typename R>
 __device__ __forceinline__ R syn_tile_b(int b, const R *cb, const R *wb, const R *sl, int from_coef, int L, int n,
                                         int R0, int C0, R *qs, R *tl, R *th) {
-    return by_taps(b, [&](auto Fc) {
-        constexpr int F = decltype(Fc)::value;
-        syn_stage<R, F>(cb, wb, sl, from_coef, L, n, R0, C0, qs);
-        __syncthreads();
-        syn_cols<R, F>(n, R0, b, qs, tl, th);
-        __syncthreads();
-        const R out = syn_rows<R, F>(n, C0, b, tl, th);
-        __syncthreads();   // shared tiles are reused by the caller
-        return out;
-    });
+    switch (b) {
+        case 0: return syn_tile<R, 2>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 1: return syn_tile<R, 4>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 2: return syn_tile<R, 6>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 3: return syn_tile<R, 8>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 4: return syn_tile<R, 10>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 5: return syn_tile<R, 12>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 6: return syn_tile<R, 14>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        default: return syn_tile<R, 16>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+    }
 }
 
 // One synthesis level l > 0 for all 8 bases (grid.y = basis): out_b (compact
@@ -258,7 +228,6 @@ template <typename R>
 __global__ void __launch_bounds__(NT) k_sara_syn(const R *__restrict__ coef, const R *__restrict__ wgt, int L, int64_t N,
                                                  const R *__restrict__ sll, int from_coef, int64_t sll_bstride, int n,
                                                  R *__restrict__ out, int64_t out_bstride) {
-    pdl_enter();
     __shared__ R qs[4 * SEXT * SEXT];
     __shared__ R tl[2 * TS * SEXT], th[2 * TS * SEXT];
     const int b = blockIdx.y;
@@ -273,43 +242,20 @@ __global__ void __launch_bounds__(NT) k_sara_syn(const R *__restrict__ coef, con
 
 // Finest synthesis level, the 8 wavelet bases summed in order per output
 // sample: out = scale * (dirac + sum_b D_b^T (w_b c_b)) (dirac may be null).
-// The quadrant tiles of all 8 bases are staged at once (one barrier per
-// phase for the whole sum): dynamic shared memory syn0_smem<R>().
-template <typename R> constexpr size_t syn0_smem() {
-    return (size_t)N_WAVELETS * (4 * SEXT * SEXT + 4 * TS * SEXT) * sizeof(R);
-}
-
 template <typename R>
-__global__ void __launch_bounds__(NT, 2) k_sara_syn0(const R *__restrict__ coef, const R *__restrict__ wgt, int L,
+__global__ void __launch_bounds__(NT) k_sara_syn0(const R *__restrict__ coef, const R *__restrict__ wgt, int L,
                                                   int64_t N, const R *__restrict__ sll, int from_coef,
                                                   int64_t sll_bstride, const R *__restrict__ dirac, R scale,
                                                   R *__restrict__ out) {
-    pdl_enter();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *qs = reinterpret_cast<R *>(smem_raw);                  // 8 x 4 SEXT^2
-    R *tl = qs + N_WAVELETS * 4 * SEXT * SEXT;                 // 8 x 2TS SEXT
-    R *th = tl + N_WAVELETS * 2 * TS * SEXT;                   // 8 x 2TS SEXT
+    __shared__ R qs[4 * SEXT * SEXT];
+    __shared__ R tl[2 * TS * SEXT], th[2 * TS * SEXT];
     const int n = L, h = n / 2, tpd = h > TS ? h / TS : 1;
     const int R0 = (blockIdx.x / tpd) * TS, C0 = (blockIdx.x % tpd) * TS;
-    for (int b = 0; b < N_WAVELETS; ++b)
-        by_taps(b, [&](auto Fc) {
-            syn_stage<R, decltype(Fc)::value>(coef + (int64_t)(b + 1) * N, wgt ? wgt + (int64_t)(b + 1) * N : nullptr,
-                                              sll + (int64_t)b * sll_bstride, from_coef, L, n, R0, C0,
-                                              qs + b * 4 * SEXT * SEXT);
-        });
-    __syncthreads();
-    for (int b = 0; b < N_WAVELETS; ++b)
-        by_taps(b, [&](auto Fc) {
-            syn_cols<R, decltype(Fc)::value>(n, R0, b, qs + b * 4 * SEXT * SEXT, tl + b * 2 * TS * SEXT,
-                                             th + b * 2 * TS * SEXT);
-        });
-    __syncthreads();
     R acc = 0;
 #pragma unroll
     for (int b = 0; b < N_WAVELETS; ++b)
-        acc += by_taps(b, [&](auto Fc) {
-            return syn_rows<R, decltype(Fc)::value>(n, C0, b, tl + b * 2 * TS * SEXT, th + b * 2 * TS * SEXT);
-        });
+        acc += syn_tile_b<R>(b, coef + (int64_t)(b + 1) * N, wgt ? wgt + (int64_t)(b + 1) * N : nullptr,
+                             sll + (int64_t)b * sll_bstride, from_coef, L, n, R0, C0, qs, tl, th);
     const int mm = threadIdx.x / (2 * TS), nnl = threadIdx.x % (2 * TS);
     if ((2 * R0 + mm < n) && (2 * C0 + nnl < n)) {
         const int64_t idx = (int64_t)(2 * R0 + mm) * L + 2 * C0 + nnl;
@@ -342,8 +288,8 @@ template <typename R> int analysis_all(ppd_ctx *c, const R *x, R *coef, int mode
         const int pitch = l == 0 ? L : n;
         const int64_t bstride = l == 0 ? 0 : ll_stride;
         PPD_CHECK(launch_begin(c, "sara_analysis", s, &site));
-        PPD_CUDA(launch_pdl(k_sara_ana<R>, dim3(dim3(tiles(h, TSA), N_WAVELETS)), dim3(NT), 0, s, in, pitch, bstride, n, ll[l & 1], ll_stride, last,
-                                                                     coef, wgt, L, N, mode, alpha, pmask));
+        k_sara_ana<R><<<dim3(tiles(h, TSA), N_WAVELETS), NT, 0, s>>>(in, pitch, bstride, n, ll[l & 1], ll_stride, last,
+                                                                     coef, wgt, L, N, mode, alpha, pmask);
         PPD_CHECK(launch_end(c, site, s));
     }
     return PPD_OK;
@@ -363,8 +309,8 @@ int synthesis_levels(ppd_ctx *c, const R *coef, const R *wgt, const R **ll0, cud
         const int n = L >> l, h = n / 2;
         const bool coarsest = (l == c->levels - 1);
         PPD_CHECK(launch_begin(c, "sara_synthesis", s, &site));
-        PPD_CUDA(launch_pdl(k_sara_syn<R>, dim3(dim3(tiles(h, TS), N_WAVELETS)), dim3(NT), 0, s, coef, wgt, L, N, coarsest ? coef : prev,
-                                                                    coarsest ? 1 : 0, st, n, buf[k & 1], st));
+        k_sara_syn<R><<<dim3(tiles(h, TS), N_WAVELETS), NT, 0, s>>>(coef, wgt, L, N, coarsest ? coef : prev,
+                                                                    coarsest ? 1 : 0, st, n, buf[k & 1], st);
         PPD_CHECK(launch_end(c, site, s));
         prev = buf[k & 1];
     }
@@ -379,16 +325,10 @@ int synthesis_final(ppd_ctx *c, const R *coef, const R *wgt, const R *ll0, const
     const int h = L / 2;
     const int64_t st = (int64_t)(L / 2) * (L / 2);
     const bool from_coef = ll0 == nullptr;   // levels == 1: LL' straight from the coefficients
-    static bool attr = false;
-    if (!attr) {
-        PPD_CUDA(cudaFuncSetAttribute(k_sara_syn0<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)syn0_smem<R>()));
-        attr = true;
-    }
     int site;
     PPD_CHECK(launch_begin(c, "sara_synthesis", s, &site));
-    PPD_CUDA(launch_pdl(k_sara_syn0<R>, dim3(tiles(h, TS)), dim3(NT), syn0_smem<R>(), s, coef, wgt, L, c->N, from_coef ? coef : ll0, from_coef ? 1 : 0, st,
-                                                dirac, scale, out));
+    k_sara_syn0<R><<<tiles(h, TS), NT, 0, s>>>(coef, wgt, L, c->N, from_coef ? coef : ll0, from_coef ? 1 : 0, st,
+                                                dirac, scale, out);
     return launch_end(c, site, s);
 }
 

@@ -226,10 +226,6 @@ template <typename R, int T, int MODE>
 __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
     k_degrid(const __grid_constant__ CUtensorMap tmap, int use_tma, const cplx_t<R> *__restrict__ grid, VisArgs<R> A,
              int n_chunks) {
-    pdl_enter();
-    // the grid was written through the generic proxy by the previous kernel;
-    // order those writes before this kernel's TMA (async proxy) reads
-    asm volatile("fence.proxy.async.global;" ::: "memory");
     using C = cplx_t<R>;
     constexpr int E = T + HALO;
     constexpr int TILE_BYTES = E * E * (int)sizeof(C);
@@ -367,7 +363,6 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
 // blocks, and of blocks outside D, pass their partial through unchanged.
 template <typename R>
 __global__ void __launch_bounds__(DG_NT) k_subiter(VisArgs<R> A, int only_first, R beta, int write_p) {
-    pdl_enter();
     using C = cplx_t<R>;
     const int ch = blockIdx.x;
     const int start = A.ch_start[ch], count = A.ch_count[ch], blk = A.ch_block[ch];
@@ -444,7 +439,6 @@ template <> struct GridCfg<double> { static constexpr int NWARP = 4; };
 
 template <typename R, int T, int MODE>
 __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, cplx_t<R> *__restrict__ gpart) {
-    pdl_enter();
     using C = cplx_t<R>;
     constexpr int NW = GridCfg<R>::NWARP, NT = NW * 32;
     constexpr int E = T + HALO, P = E + 1;   // P: padded pitch of the private tiles
@@ -477,56 +471,89 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
 
     C *mine = priv + warp * E * P;
     const int a = lane & 7, bb = (lane >> 3) * 2;
+    // this thread's visibility of the current round, loaded one round ahead
+    // so that the loads of round r + 1 are in flight during the scatter of r
+    struct In {
+        VisRec<R> rc;
+        C a, b, z;   // GR_DUAL active: y, w, z; inactive: v; operator modes: input
+        R th;
+    };
+    auto load_in = [&](int gi, In &o) {
+        o.rc = A.rec[gi];
+        if (MODE == GR_DUAL && act) {
+            o.a = A.y[gi];
+            o.b = A.w[gi];
+            o.z = A.z[gi];
+        } else if (MODE == GR_DUAL) {
+            o.a = A.v[gi];
+        } else {
+            o.a = A.op_in[A.perm ? A.perm[gi] : gi];
+        }
+        o.th = A.theta_v ? A.theta_v[gi] : A.theta_s;
+    };
+    In cur;
+    if ((int)threadIdx.x < count) load_in(start + threadIdx.x, cur);
     for (int base = 0; base < count; base += NT) {
         const int n = min(NT, count - base);
         if (threadIdx.x < n) {
             const int gi = start + base + threadIdx.x;
-            const VisRec<R> rc = A.rec[gi];
+            const VisRec<R> rc = cur.rc;
             C vv;
             if (MODE == GR_DUAL && act) {
-                const C yy = A.y[gi], ww = A.w[gi], zz = A.z[gi];
+                const C yy = cur.a, ww = cur.b, zz = cur.z;
                 const C pp{yy.x + c * (ww.x - yy.x), yy.y + c * (ww.y - yy.y)};
                 vv = C{rc.U * (zz.x - pp.x), rc.U * (zz.y - pp.y)};
                 A.v[gi] = vv;
                 A.p[gi] = pp;
             } else if (MODE == GR_DUAL) {
-                vv = A.v[gi];
+                vv = cur.a;
             } else {
-                vv = A.op_in[A.perm ? A.perm[gi] : gi];
+                vv = cur.a;
                 if (MODE == GR_OP_U) vv = C{rc.U * vv.x, rc.U * vv.y};
             }
-            const R th = A.theta_v ? A.theta_v[gi] : A.theta_s;
+            const R th = cur.th;
             sv[threadIdx.x] = C{th * vv.x, th * vv.y};
             R w0[KB_J], w1[KB_J];
             kb_weights(rc.f0, w0, poly, A.beta, A.inv_i0b);
             kb_weights(rc.f1, w1, poly, A.beta, A.inv_i0b);
+            if constexpr (sizeof(R) == 4) {   // 16-byte stores: 2-way instead of 8-way bank conflicts
+                float4 *d0 = reinterpret_cast<float4 *>(sw0 + threadIdx.x * KB_J);
+                float4 *d1 = reinterpret_cast<float4 *>(sw1 + threadIdx.x * KB_J);
+                d0[0] = make_float4(w0[0], w0[1], w0[2], w0[3]);
+                d0[1] = make_float4(w0[4], w0[5], w0[6], w0[7]);
+                d1[0] = make_float4(w1[0], w1[1], w1[2], w1[3]);
+                d1[1] = make_float4(w1[4], w1[5], w1[6], w1[7]);
+            } else {
 #pragma unroll
-            for (int j = 0; j < KB_J; ++j) {
-                sw0[threadIdx.x * KB_J + j] = w0[j];
-                sw1[threadIdx.x * KB_J + j] = w1[j];
+                for (int j = 0; j < KB_J; ++j) {
+                    sw0[threadIdx.x * KB_J + j] = w0[j];
+                    sw1[threadIdx.x * KB_J + j] = w1[j];
+                }
             }
             const int lb0 = (rc.packed & 0xffff) - row0, lb1 = ((rc.packed >> 16) & 0xffff) - col0;
             slb[threadIdx.x] = lb0 | (lb1 << 16);
         }
         __syncthreads();
+        In nxt;
+        if (base + NT + (int)threadIdx.x < count) load_in(start + base + NT + threadIdx.x, nxt);
         // warp w takes a contiguous segment of the staged visibilities; the
         // sort order makes runs of visibilities share a first tap, so each
         // lane accumulates its two footprint cells in registers and writes
         // the warp's private tile only when the base cell changes.
         const int seg = (n + nwu - 1) / nwu;
         const int i0 = warp < nwu ? warp * seg : n, i1 = min(n, i0 + seg);
-        int cur = -1;
+        int run = -1;
         C acc0{0, 0}, acc1{0, 0};
         for (int i = i0; i < i1; ++i) {
             const int lb = slb[i];
-            if (lb != cur) {
-                if (cur >= 0) {
-                    C *cell = mine + ((cur & 0xffff) + a) * P + (cur >> 16) + bb;
+            if (lb != run) {
+                if (run >= 0) {
+                    C *cell = mine + ((run & 0xffff) + a) * P + (run >> 16) + bb;
                     C g0 = cell[0], g1 = cell[1];
                     cell[0] = cadd(g0, acc0);
                     cell[1] = cadd(g1, acc1);
                 }
-                cur = lb;
+                run = lb;
                 acc0 = C{0, 0};
                 acc1 = C{0, 0};
             }
@@ -538,13 +565,14 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
             acc1.x += wb1 * tv.x;
             acc1.y += wb1 * tv.y;
         }
-        if (cur >= 0) {
-            C *cell = mine + ((cur & 0xffff) + a) * P + (cur >> 16) + bb;
+        if (run >= 0) {
+            C *cell = mine + ((run & 0xffff) + a) * P + (run >> 16) + bb;
             C g0 = cell[0], g1 = cell[1];
             cell[0] = cadd(g0, acc0);
             cell[1] = cadd(g1, acc1);
         }
         __syncthreads();
+        cur = nxt;
     }
     C *out = gpart + (int64_t)ch * E * E;
     for (int e = threadIdx.x; e < E * E; e += NT) {
@@ -567,7 +595,6 @@ __global__ void __launch_bounds__(256) k_combine(const cplx_t<R> *__restrict__ g
                                                  const int32_t *__restrict__ tile_n,
                                                  const int32_t *__restrict__ active, int K1, int nt0, int nt1,
                                                  cplx_t<R> *__restrict__ grid) {
-    pdl_enter();
     using C = cplx_t<R>;
     constexpr int E = T + HALO;
     __shared__ int f_s[4], n_s[4];
@@ -669,9 +696,9 @@ int degrid_t(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const 
     const unsigned nb = (unsigned)std::min<int64_t>(nch, (int64_t)sms * per_sm);
     int site;
     PPD_CHECK(launch_begin(c, mode == DG_OP ? "degrid_op" : "degrid_dual", s, &site));
-    if (mode == DG_OP) PPD_CUDA(launch_pdl(k_degrid<R, T, DG_OP>, dim3(nb), dim3(DG_NT), sh, s, c->tmap_a, use_tma, grid, A, nch));
-    else if (mode == DG_DUAL) PPD_CUDA(launch_pdl(k_degrid<R, T, DG_DUAL>, dim3(nb), dim3(DG_NT), sh, s, c->tmap_a, use_tma, grid, A, nch));
-    else PPD_CUDA(launch_pdl(k_degrid<R, T, DG_FIRST>, dim3(nb), dim3(DG_NT), sh, s, c->tmap_a, use_tma, grid, A, nch));
+    if (mode == DG_OP) k_degrid<R, T, DG_OP><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A, nch);
+    else if (mode == DG_DUAL) k_degrid<R, T, DG_DUAL><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A, nch);
+    else k_degrid<R, T, DG_FIRST><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A, nch);
     return launch_end(c, site, s);
 }
 
@@ -695,15 +722,15 @@ int grid_t(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_
     if (c->ch.n > 0) {
         PPD_CHECK(launch_begin(c, mode == GR_DUAL ? "grid_dual" : "grid_op", s, &site));
         const unsigned nb = (unsigned)c->ch.n;
-        if (mode == GR_OP) PPD_CUDA(launch_pdl(k_grid<R, T, GR_OP>, dim3(nb), dim3(NT), sh, s, A, gp));
-        else if (mode == GR_OP_U) PPD_CUDA(launch_pdl(k_grid<R, T, GR_OP_U>, dim3(nb), dim3(NT), sh, s, A, gp));
-        else PPD_CUDA(launch_pdl(k_grid<R, T, GR_DUAL>, dim3(nb), dim3(NT), sh, s, A, gp));
+        if (mode == GR_OP) k_grid<R, T, GR_OP><<<nb, NT, sh, s>>>(A, gp);
+        else if (mode == GR_OP_U) k_grid<R, T, GR_OP_U><<<nb, NT, sh, s>>>(A, gp);
+        else k_grid<R, T, GR_DUAL><<<nb, NT, sh, s>>>(A, gp);
         PPD_CHECK(launch_end(c, site, s));
     }
     if (c->ch.n_active == 0 || !combine) return PPD_OK;
     PPD_CHECK(launch_begin(c, "grid_combine", s, &site));
-    PPD_CUDA(launch_pdl(k_combine<R, T>, dim3((unsigned)c->ch.n_active * 4), dim3(256), 0, s, gp, c->ch.tile_first, c->ch.tile_n, c->ch.active,
-                                                            c->K1, c->K0 / T, c->K1 / T, grid));
+    k_combine<R, T><<<(unsigned)c->ch.n_active * 4, 256, 0, s>>>(gp, c->ch.tile_first, c->ch.tile_n, c->ch.active,
+                                                            c->K1, c->K0 / T, c->K1 / T, grid);
     return launch_end(c, site, s);
 }
 
@@ -783,7 +810,7 @@ template <typename R> int subiter(ppd_ctx *c, cudaStream_t s, int only_first, do
     if (c->ch.n == 0) return PPD_OK;
     int site;
     PPD_CHECK(launch_begin(c, "subiter", s, &site));
-    PPD_CUDA(launch_pdl(k_subiter<R>, dim3((unsigned)c->ch.n), dim3(DG_NT), 0, s, make_args<R>(c), only_first, (R)beta, write_p));
+    k_subiter<R><<<(unsigned)c->ch.n, DG_NT, 0, s>>>(make_args<R>(c), only_first, (R)beta, write_p);
     return launch_end(c, site, s);
 }
 

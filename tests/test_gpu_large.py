@@ -9,8 +9,9 @@ Phi^dagger of a measurement vector that is zero outside a random sample
 (the library still grids every visibility), Psi^dagger of the whole image.
 Properties that hold at any size cover the rest: the adjoint identity of
 the library's own Phi and Phi^dagger, and perfect reconstruction
-Psi Psi^dagger x = x.  At 1024^2 the oracle also runs two whole PPD
-iterations (Algorithm 3) for an element-wise image comparison.
+Psi Psi^dagger x = x.  At 1024^2 and 2048^2 (200k visibilities) the
+oracle also runs whole PPD iterations (Algorithm 3) for an element-wise
+image comparison.
 
 Tolerances (relative l2): operators <= 1e-5, image after a fixed number of
 iterations <= 1e-4 (FP32 path against the FP64 oracle).
@@ -88,6 +89,23 @@ def test_ppd_two_iterations_at_1024():
     stats = s.iterate(2)
     assert rel(s.image(), st.x) <= 1e-4
     assert np.allclose(stats["block_residual"], hist["residual"], rtol=1e-4)
+    s.close()
+
+
+def test_ppd_iterations_at_2048_with_the_combine_pass():
+    """From K = 4096 on the iteration sums the gridding's partial tiles in a
+    separate combine pass before the inverse column FFT: 2048^2 image, 200k
+    visibilities in 8 blocks, three iterations against the oracle."""
+    p = synth.make_problem("c2048", L=2048, M=200_000, n_blocks=8, uv_sigma=0.1, seed=1710, compact=True)
+    eta = 2.09e-7              # 1 / ||U^{1/2} Phi||_S^2 (the oracle's power iteration gives 4.78e6)
+    S = oppd.make_setup(p.omega, p.y, p.theta, p.block, p.n_blocks, p.L, eta=eta, x_true=p.x_true)
+    st = oppd.init_state(S)
+    for _ in range(3):
+        oppd.iterate(st, S)
+    s = ppd.Solver(p.L, p.n_blocks, precision=F32, eta=eta)
+    s.set_problem(p.omega, p.y, p.block, theta=p.theta, x_true=p.x_true)
+    s.iterate(3)
+    assert rel(s.image(), st.x) <= 1e-4, rel(s.image(), st.x)
     s.close()
 
 
