@@ -100,6 +100,38 @@ def algorithmic_bytes_per_step(L: int, M: int, levels: int = 4, rsz: int = 4, xt
     }
 
 
+def source_digest() -> str:
+    """sha256 over the library's CUDA sources (name and contents, sorted)."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1701_01748_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def dram_traffic(workload: str) -> tuple[dict, str]:
+    """DRAM bytes per launch by kernel from the committed ncu summary of this
+    workload (profiles/ncu_dram_<workload>.txt), if it was taken on the
+    current sources; else ({}, why)."""
+    path = os.path.join(ROOT, "profiles", f"ncu_dram_{workload}.txt")
+    if not os.path.exists(path):
+        return {}, "no ncu capture for this workload"
+    out, digest = {}, None
+    for line in open(path):
+        line = line.strip()
+        if line.startswith("sources sha256:"):
+            digest = line.split(":", 1)[1].strip()
+        elif line and not line.startswith("#") and ":" not in line:
+            k, v = line.split()[:2]
+            out[k] = float(v)
+    if digest != source_digest():
+        return {}, "kernels changed since the ncu capture"
+    return out, "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, " + os.path.basename(path)
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -407,6 +439,7 @@ def main():
                                                 "random: randomised active sets")
     ap.add_argument("--isnr", type=float, default=30.0, help="input SNR (dB) of the study problems")
     ap.add_argument("--autotune", action="store_true", help="batch workloads: autotune each problem's gridding")
+    ap.add_argument("--no-autotune", action="store_true", help="main bench: keep the library's default gridding")
     ap.add_argument("--quick", action="store_true",
                     help="only the timed FP32 steps (for profiler launch lists); eta from 20 power steps")
     args = ap.parse_args()
@@ -472,11 +505,15 @@ def main():
     else:
         _log("set-up FP32 (eta by power iteration)")
         s32 = make(ppd.PPD_FP32_FP64NORMS)
+        if not args.no_autotune and args.tile == 0 and args.chunk == 0:
+            _log("autotuning the gridding work decomposition")
+            ppd.ppd_autotune(s32.ctx, 10)
         _log("set-up FP64 (eta by power iteration)")
         s64 = make(ppd.PPD_FP64_PLAIN)
     # the zero state of each solver, restored before every measured run (the
     # state blob resets x, xt, u, v and the warm start without a new eta)
     zero = {s.ctx: ppd.ppd_get_state(s.ctx) for s in ([s32] if args.quick else [s32, s64])}
+    prm32 = s32.params()
 
     def timed_steps(s, steps, warmup, kernel_timing):
         ppd.ppd_timing_enable(s.ctx, kernel_timing)
@@ -551,7 +588,8 @@ def main():
         for _ in range(2):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            se = ppd.Solver(p.L, p.n_blocks, precision=ppd.PPD_FP32_FP64NORMS, stream=sp)
+            se = ppd.Solver(p.L, p.n_blocks, precision=ppd.PPD_FP32_FP64NORMS, stream=sp,
+                            tile=prm32["tile"], chunk=prm32["chunk"])
             ppd.ppd_set_visibilities(se.ctx, p.omega, p.y, p.block)
             ppd.ppd_set_weights(se.ctx, p.theta, None, None)
             ppd.ppd_set_ground_truth(se.ctx, p.x_true)
@@ -594,8 +632,10 @@ def main():
         name, (ms, n) = max(kt.items(), key=lambda kv: kv[1][0])
         per_step_s = ms / args.steps / 1e3
         ach = ab.get(name, 0.0) / per_step_s / 1e9 if ab.get(name) else None
+        traffic, why = dram_traffic(args.workload)
         roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": (ach / peak if ach else None), "traffic": None, "peak_source": peak_kind,
+                "frac": (ach / peak if ach else None), "traffic": traffic.get(name), "traffic_source": why,
+                "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": ab.get(name, 0.0) * args.steps / n,
                 "avg_launch_us": 1e3 * ms / n, "share_of_kernel_time": ms / ktot,
                 "ms_per_step_with_kernel_events": 1e3 * t32k / args.steps}
@@ -619,7 +659,9 @@ def main():
         "config": {"workload": args.workload, "image": f"{p.L}x{p.L}", "visibilities": p.M,
                    "blocks": p.n_blocks, "uv_density": "gaussian sigma=0.1pi", "isnr_db": 30,
                    "l2": "flushed (256 MiB write) between timed steps", "graph": "one CUDA graph per iteration",
-                   "replicas": world},
+                   "replicas": world,
+                   "gridding": {"tile": prm32["tile"], "chunk": prm32["chunk"], "work_items": prm32["n_chunks"],
+                                "autotuned": not args.no_autotune and args.tile == 0 and args.chunk == 0}},
         "snr_iters": snr_iters,
         "fp64_plain": {"iters_per_s": ips64, "snr_db_at_end": target, "seconds_all": wall64},
         "fp32_batched": {"iters_per_s": ips32, "snr_db_at_end": snr32[-1], "seconds_all": wall32,
