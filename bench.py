@@ -70,7 +70,8 @@ def algorithmic_bytes_per_step(L: int, M: int, levels: int = 4, rsz: int = 4, xt
     level).  Synthesis, level l >= 1: LL' and 3 detail quadrants read, the
     2h x 2h output written; level 0 (all bases summed): LL' and details read,
     ut written.  Primal: x, xt, g, ut, u_Dirac (and x_true for the SNR) read;
-    x, xt, u_Dirac written.
+    x, xt, u_Dirac written; fused with the inverse and the next forward row
+    pass (rows_primal), g never leaves the chip.
     """
     N, K2, c = L * L, 4 * L * L, 2 * rsz
     det = lambda l: 3 * N / 4 ** (l + 1)       # detail coefficients of level l, per basis
@@ -96,6 +97,9 @@ def algorithmic_bytes_per_step(L: int, M: int, levels: int = 4, rsz: int = 4, xt
         "sara_analysis": ana,
         "sara_synthesis": syn,
         "primal": rsz * N * (8 + (1 if xtrue else 0)),
+        # inverse row pass (tmp_inv read), primal (x, xt, ut, u_Dirac [, x_true] read; x, xt,
+        # u_Dirac written; g stays on chip) and the next forward row pass (tmp written)
+        "rows_primal": c * 2 * N + rsz * N * (7 + (1 if xtrue else 0)) + c * 2 * N,
         "block_norms": 0.0,
     }
 

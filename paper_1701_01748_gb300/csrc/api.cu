@@ -211,7 +211,9 @@ template <typename R> int iteration_body(ppd_ctx *c, cudaStream_t s, bool first)
 
     double *bank[2] = {c->partials, c->partials + NPART * c->ch.n};
     int cur = 0;
-    PPD_CHECK(fft_forward<R>(c, static_cast<const R *>(c->xt), ga, s));
+    // the forward row pass of xt was done by the previous iteration's last
+    // kernel (or by run_iterations before the first one)
+    PPD_CHECK(fft_forward_cols<R>(c, ga, s));
     const bool current = c->cfg.inner_init == PPD_INNER_CURRENT;
     // with randomised active sets the warm start is decided per block on
     // the device (blocks without a prox output start from z, then one extra
@@ -249,13 +251,14 @@ template <typename R> int iteration_body(ppd_ctx *c, cudaStream_t s, bool first)
     // group per tile reads them contiguously and the column pass reads the grid
     if (c->K0 >= 4096) {
         PPD_CHECK(grid_vis<R>(c, GR_DUAL, nullptr, nullptr, gv, s, /*combine=*/true));
-        PPD_CHECK(fft_inverse<R>(c, gv, static_cast<R *>(c->g), s));
+        PPD_CHECK(fft_inverse_cols<R>(c, gv, s));
     } else {
         PPD_CHECK(grid_vis<R>(c, GR_DUAL, nullptr, nullptr, gv, s, /*combine=*/false));
-        PPD_CHECK(fft_inverse_partials<R>(c, static_cast<R *>(c->g), s));
+        PPD_CHECK(fft_inverse_cols_partials<R>(c, s));
     }
     if (fork) PPD_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
-    PPD_CHECK(primal_step<R>(c, s));
+    // inverse row pass, primal step and the next iteration's forward row pass
+    PPD_CHECK(rows_primal<R>(c, s));
     return PPD_OK;
 }
 
@@ -282,11 +285,23 @@ int rand_finish(ppd_ctx *c, cudaStream_t s) {
     return PPD_OK;
 }
 
+// The iteration starts at the forward column pass: its row pass of xt is
+// the last step of the previous iteration.  When the FFT temporary holds
+// anything else (a reset, a restored state, an operator call, the power
+// iteration) the row pass runs on its own first.
+template <typename R> int xt_rows_ready(ppd_ctx *c, cudaStream_t s) {
+    if (c->xt_rows_valid) return PPD_OK;
+    PPD_CHECK(fft_forward_rows<R>(c, static_cast<const R *>(c->xt), s));
+    c->xt_rows_valid = true;
+    return PPD_OK;
+}
+
 template <typename R> int run_iterations(ppd_ctx *c, int n) {
     cudaStream_t s = c->stream;
     for (int it = 0; it < n; ++it) {
         const bool first = !c->p_valid;
         PPD_CHECK(rand_prepare(c, s));
+        PPD_CHECK(xt_rows_ready<R>(c, s));
         if (first || !c->cfg.use_graph || !c->is_f32) {
             PPD_CHECK(iteration_body<R>(c, s, first));
         } else {
@@ -328,6 +343,7 @@ template <typename R> int run_iterations(ppd_ctx *c, int n) {
             c->graph_ran_since_collect = true;
         }
         PPD_CHECK(rand_finish(c, s));
+        c->xt_rows_valid = true;
         c->p_valid = true;
         c->iters++;
     }
@@ -380,6 +396,7 @@ int reset_state(ppd_ctx *c) {
     c->p_valid = false;
     c->iters = 0;
     c->gpart_stale = true;
+    c->xt_rows_valid = false;
     drop_graph(c);
     return PPD_OK;
 }
@@ -565,7 +582,7 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
         (st = dalloc(&c->stat_out, 3)))
         return bail(st);
     c->n_prim_blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 4);
-    if ((st = dalloc(&c->prim_part, 3 * (size_t)c->n_prim_blocks))) return bail(st);
+    if ((st = dalloc(&c->prim_part, 3 * (size_t)std::max(c->n_prim_blocks, c->L0)))) return bail(st);
     if ((st = dalloc(&c->mask_cur, (size_t)c->d + N_BASES)) || (st = dalloc(&c->blk_seen, (size_t)c->d)) ||
         (st = dalloc(&c->regrid_d, 1)))
         return bail(st);
@@ -1268,8 +1285,10 @@ int ppd_group_iterate(ppd_group *g, int32_t n_iters) {
     if (any_first) {
         for (ppd_ctx *c : g->ctxs) {
             PPD_CHECK(rand_prepare(c, c->stream));
+            PPD_CHECK(xt_rows_ready<float>(c, c->stream));
             PPD_CHECK(iteration_body<float>(c, c->stream, !c->p_valid));
             PPD_CHECK(rand_finish(c, c->stream));
+            c->xt_rows_valid = true;
             c->p_valid = true;
             c->iters++;
         }
@@ -1321,9 +1340,15 @@ int ppd_group_iterate(ppd_group *g, int32_t n_iters) {
         PPD_CUDA(cudaStreamWaitEvent(g->stream, g->joins[i], 0));
     }
     for (int it = 0; it < n_iters; ++it) {
-        for (ppd_ctx *c : g->ctxs) PPD_CHECK(rand_prepare(c, g->stream));
+        for (ppd_ctx *c : g->ctxs) {
+            PPD_CHECK(rand_prepare(c, g->stream));
+            PPD_CHECK(xt_rows_ready<float>(c, g->stream));
+        }
         PPD_CUDA(cudaGraphLaunch(g->exec, g->stream));
-        for (ppd_ctx *c : g->ctxs) PPD_CHECK(rand_finish(c, g->stream));
+        for (ppd_ctx *c : g->ctxs) {
+            PPD_CHECK(rand_finish(c, g->stream));
+            c->xt_rows_valid = true;
+        }
         for (size_t i = 0; i < g->ctxs.size(); ++i) {
             g->ctxs[i]->iters++;
             g->ctxs[i]->launches += g->kernels[i];
@@ -1430,6 +1455,7 @@ int ppd_set_state(ppd_ctx *c, const void *blob, int64_t bytes) {
     c->iters = h.iters;
     c->p_valid = h.p_valid != 0;
     c->gpart_stale = true;   // the partial tiles belong to the replaced dual
+    c->xt_rows_valid = false;
     return PPD_OK;
 }
 

@@ -118,6 +118,8 @@ struct ppd_ctx {
     void *kbpoly = nullptr;     // (KB_DEG+1) x 8 floats
     double *prim_part = nullptr;
     int n_prim_blocks = 0;
+    int n_stat_parts = 0;        // primal statistics partials the last primal launch wrote
+    bool xt_rows_valid = false;  // fft_tmp holds the forward row pass of xt
     double *stat_out = nullptr; // 3 doubles
 
     // visibility side
@@ -201,7 +203,6 @@ int launch_end(ppd_ctx *c, int site, cudaStream_t s);
 // FFT (fft.cu)
 template <typename R> int fft_forward(ppd_ctx *c, const R *x, cplx_t<R> *grid, cudaStream_t s);
 template <typename R> int fft_inverse(ppd_ctx *c, const cplx_t<R> *grid, R *img, cudaStream_t s);
-template <typename R> int fft_inverse_partials(ppd_ctx *c, R *img, cudaStream_t s);
 int make_twiddles(ppd_ctx *c);
 int fft_plan_pruning(ppd_ctx *c, const std::vector<char> &rows_fwd, const std::vector<char> &cols_fwd,
                      const std::vector<char> &rows_inv, const std::vector<char> &cols_inv);
@@ -237,7 +238,95 @@ template <typename R> int sara_prior_branch(ppd_ctx *c, const R **ll0, cudaStrea
 template <typename R> int sara_level0(ppd_ctx *c, const R *ll0, cudaStream_t s);
 
 // image side (image.cu)
-template <typename R> int primal_step(ppd_ctx *c, cudaStream_t s);
+// Deterministic CTA sum of three doubles per thread (fixed shuffle tree, then
+// warps in order); thread 0 writes out3[0..2].
+template <int NTH> __device__ __forceinline__ void cta_sum3(double a, double b, double c, double *out3) {
+    __shared__ double red[3][NTH / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[0][wid] = a;
+        red[1][wid] = b;
+        red[2][wid] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0, s1 = 0, s2 = 0;
+        for (int i = 0; i < NTH / 32; ++i) {
+            s0 += red[0][i];
+            s1 += red[1][i];
+            s2 += red[2][i];
+        }
+        out3[0] = s0;
+        out3[1] = s1;
+        out3[2] = s2;
+    }
+}
+
+// Primal step of Algorithm 3 on one pixel, with the Dirac basis of the
+// prior step (prior weight w0 of Algorithm 1, 1 when w0 is null; kappa is
+// the clip level alpha = kappa ||Psi W||^2, zeta the effective zeta /
+// ||Psi W||^2; a Dirac basis outside the active set P keeps u0):
+//   u0 <- clip(u0 + w0 xt/3, kappa); ut_all = (w0 u0 + ut)/3;
+//   xbar = P_C(x - tau (eta g + zeta ut_all)); xt = 2 xbar - x; x = xbar.
+// Kahan-compensated per-thread sums of ||xbar - x||^2, ||xbar||^2 and
+// ||xbar - x_true||^2 in the working precision.  Returns the new xt.
+template <typename R> struct PrimalArgs {
+    R *x, *xt, *u0;
+    const R *ut, *w0, *xtrue;
+    R tau, eta, zeta, kappa;
+    const uint8_t *pmask;
+};
+
+template <typename R> struct PrimalSums {
+    R sd = 0, cd = 0, sx = 0, cx = 0, se = 0, ce = 0;
+    __device__ __forceinline__ static void kadd(R &s, R &c, R v) {
+        const R y = v - c, t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ void write(double *part3) const {
+        cta_sum3<256>((double)sd - (double)cd, (double)sx - (double)cx, (double)se - (double)ce, part3);
+    }
+};
+
+template <typename R>
+__device__ __forceinline__ R primal_pixel(const PrimalArgs<R> &P, int64_t e, R g, PrimalSums<R> &acc) {
+    const R third = R(1.0 / 3.0);
+    const R xo = P.x[e], xte = P.xt[e];
+    const R wd = P.w0 ? P.w0[e] : R(1);
+    R un = P.u0[e];
+    if (!P.pmask || P.pmask[0]) {
+        un = fmin(fmax(un + wd * (xte * third), -P.kappa), P.kappa);
+        P.u0[e] = un;
+    }
+    const R utot = (wd * un + P.ut[e]) * third;
+    const R xb = fmax(R(0), xo - P.tau * (P.eta * g + P.zeta * utot));
+    const R xtn = R(2) * xb - xo;
+    P.xt[e] = xtn;
+    P.x[e] = xb;
+    const R dd = xb - xo;
+    PrimalSums<R>::kadd(acc.sd, acc.cd, dd * dd);
+    PrimalSums<R>::kadd(acc.sx, acc.cx, xb * xb);
+    if (P.xtrue) {
+        const R de = xb - P.xtrue[e];
+        PrimalSums<R>::kadd(acc.se, acc.ce, de * de);
+    }
+    return xtn;
+}
+
+template <typename R> PrimalArgs<R> primal_args(ppd_ctx *c);
+// inverse row pass + primal step + the next iteration's forward row pass (fft.cu)
+template <typename R> int rows_primal(ppd_ctx *c, cudaStream_t s);
+template <typename R> int fft_forward_rows(ppd_ctx *c, const R *x, cudaStream_t s);
+template <typename R> int fft_forward_cols(ppd_ctx *c, cplx_t<R> *grid, cudaStream_t s);
+template <typename R> int fft_inverse_cols_partials(ppd_ctx *c, cudaStream_t s);
+template <typename R> int fft_inverse_cols(ppd_ctx *c, const cplx_t<R> *grid, cudaStream_t s);
 int reduce_primal_stats(ppd_ctx *c, cudaStream_t s);
 template <typename R> int scale_copy(ppd_ctx *c, const R *in, R *out, int64_t n, double a, cudaStream_t s);
 template <typename R> int reweight_from(ppd_ctx *c, R *coef_to_w, int64_t n, double omega, cudaStream_t s);

@@ -306,146 +306,229 @@ __global__ void __launch_bounds__(NT) k_rows_inv(const cplx_t<R> *__restrict__ t
     }
 }
 
-template <typename R, int K> int fft_fwd_k(ppd_ctx *c, const R *x, cplx_t<R> *grid, cudaStream_t s) {
-    constexpr int B = rows_per_cta<R>(K), W = cols_per_cta<R>(K);
-    const int L = c->L0;
-    size_t shr = pass_smem<R>(B, K), shc = pass_smem<R>(W, K);
-    static bool attr = false;
-    if (!attr) {
-        PPD_CUDA(cudaFuncSetAttribute(k_rows_fwd<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shr));
-        PPD_CUDA(cudaFuncSetAttribute(k_cols_fwd<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shc));
-        attr = true;
+// The end of one PPD iteration and the start of the next, B rows per CTA:
+// the inverse row pass g = s0 s1 Re(F^H along axis 1 of tmp_inv) (the rows'
+// Phi^dagger v, kept on chip), the primal step of Algorithm 3 on those
+// pixels (primal_pixel), and the forward row pass of the new xt into
+// tmp_fwd (the next iteration's first FFT pass), with the FP64 statistics
+// partials of the CTA.  The join of the prior branch precedes it (ut, u0).
+template <typename R, int K>
+__global__ void __launch_bounds__(NT) k_rows_primal(const cplx_t<R> *__restrict__ tmp_inv, cplx_t<R> *__restrict__ tmp_fwd,
+                                                    const cplx_t<R> *__restrict__ tw, const R *__restrict__ s0,
+                                                    const R *__restrict__ s1, const uint8_t *__restrict__ colmask,
+                                                    PrimalArgs<R> P, double *__restrict__ part) {
+    using C = cplx_t<R>;
+    constexpr int B = rows_per_cta<R>(K), L = K / 2, PER = B * L / NT;
+    static_assert(B * L % NT == 0, "pixels per thread");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const C *tws = stage_twiddles<R, B, K>(buf, tw);
+    const int row0 = blockIdx.x * B;
+    for (int e = threadIdx.x; e < B * K; e += NT) {
+        const int s = e / K, c = e % K, n0 = row0 + s;
+        buf[s * K + ((c + K / 2) & (K - 1))] = n0 < L ? cconj(tmp_inv[(int64_t)n0 * K + c]) : C{0, 0};
     }
-    int site;
-    PPD_CHECK(launch_begin(c, "fft_fwd_rows", s, &site));
-    k_rows_fwd<R, K><<<(L + B - 1) / B, NT, shr, s>>>(x, static_cast<cplx_t<R> *>(c->fft_tmp),
-                                                     static_cast<const cplx_t<R> *>(c->tw0),
-                                                     static_cast<const R *>(c->deap0),
-                                                     static_cast<const R *>(c->deap1), L, c->col_fwd);
-    PPD_CHECK(launch_end(c, site, s));
-    if (c->n_fwd_strips == 0) return PPD_OK;
-    PPD_CHECK(launch_begin(c, "fft_fwd_cols", s, &site));
-    k_cols_fwd<R, K><<<c->n_fwd_strips, NT, shc, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp), grid,
-                                                      static_cast<const cplx_t<R> *>(c->tw0), L, c->fwd_strips,
-                                                      c->row_fwd);
-    PPD_CHECK(launch_end(c, site, s));
-    return PPD_OK;
+    __syncthreads();
+    fft_smem<R, K, B, NT, false>(buf, tws);
+    PrimalSums<R> acc;
+    R xtn[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int e = threadIdx.x + k * NT, s = e / L, n1 = e % L, n0 = row0 + s;
+        xtn[k] = R(0);
+        if (n0 < L) {
+            const R g = s0[n0] * s1[n1] * buf[s * K + ((n1 - L / 2 + K) & (K - 1))].x;
+            xtn[k] = primal_pixel(P, (int64_t)n0 * L + n1, g, acc);
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < B * K; e += NT) buf[e] = C{0, 0};
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int e = threadIdx.x + k * NT, s = e / L, n1 = e % L, n0 = row0 + s;
+        if (n0 < L) buf[s * K + ((n1 - L / 2 + K) & (K - 1))] = C{s0[n0] * s1[n1] * xtn[k], R(0)};
+    }
+    __syncthreads();
+    fft_smem<R, K, B, NT, false>(buf, tws);
+    for (int e = threadIdx.x; e < B * K; e += NT) {
+        const int s = e / K, c = e % K, n0 = row0 + s;
+        if (n0 < L && colmask[c]) tmp_fwd[(int64_t)n0 * K + c] = buf[s * K + ((c + K / 2) & (K - 1))];
+    }
+    acc.write(part + 3 * (int64_t)blockIdx.x);
 }
 
-template <typename R, int K> int fft_inv_k(ppd_ctx *c, const cplx_t<R> *grid, R *img, cudaStream_t s) {
-    constexpr int B = rows_per_cta<R>(K), W = cols_per_cta<R>(K);
-    const int L = c->L0;
-    size_t shr = pass_smem<R>(B, K), shc = pass_smem<R>(W, K);
-    static bool attr = false;
-    if (!attr) {
-        PPD_CUDA(cudaFuncSetAttribute(k_rows_inv<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shr));
-        PPD_CUDA(cudaFuncSetAttribute(k_cols_inv<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shc));
-        attr = true;
+template <typename R, int K> struct Pass {
+    static constexpr int B = rows_per_cta<R>(K), W = cols_per_cta<R>(K);
+    // dynamic shared memory of the row and column passes, set once per instantiation
+    static int attrs() {
+        static bool done = false;
+        if (done) return PPD_OK;
+        const int shr = (int)pass_smem<R>(B, K), shc = (int)pass_smem<R>(W, K);
+        PPD_CUDA(cudaFuncSetAttribute(k_rows_fwd<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, shr));
+        PPD_CUDA(cudaFuncSetAttribute(k_rows_inv<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, shr));
+        PPD_CUDA(cudaFuncSetAttribute(k_rows_primal<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, shr));
+        PPD_CUDA(cudaFuncSetAttribute(k_cols_fwd<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, shc));
+        PPD_CUDA(cudaFuncSetAttribute(k_cols_inv<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, shc));
+        PPD_CUDA(cudaFuncSetAttribute(k_cols_inv_part<R, K, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, shc));
+        PPD_CUDA(cudaFuncSetAttribute(k_cols_inv_part<R, K, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, shc));
+        done = true;
+        return PPD_OK;
     }
-    int site;
-    if (c->n_inv_strips > 0) {
+    static int rows_fwd(ppd_ctx *c, const R *x, cudaStream_t s) {
+        PPD_CHECK(attrs());
+        int site;
+        PPD_CHECK(launch_begin(c, "fft_fwd_rows", s, &site));
+        k_rows_fwd<R, K><<<(c->L0 + B - 1) / B, NT, pass_smem<R>(B, K), s>>>(
+            x, static_cast<cplx_t<R> *>(c->fft_tmp), static_cast<const cplx_t<R> *>(c->tw0),
+            static_cast<const R *>(c->deap0), static_cast<const R *>(c->deap1), c->L0, c->col_fwd);
+        return launch_end(c, site, s);
+    }
+    static int cols_fwd(ppd_ctx *c, cplx_t<R> *grid, cudaStream_t s) {
+        PPD_CHECK(attrs());
+        if (c->n_fwd_strips == 0) return PPD_OK;
+        int site;
+        PPD_CHECK(launch_begin(c, "fft_fwd_cols", s, &site));
+        k_cols_fwd<R, K><<<c->n_fwd_strips, NT, pass_smem<R>(W, K), s>>>(
+            static_cast<const cplx_t<R> *>(c->fft_tmp), grid, static_cast<const cplx_t<R> *>(c->tw0), c->L0,
+            c->fwd_strips, c->row_fwd);
+        return launch_end(c, site, s);
+    }
+    static int cols_inv(ppd_ctx *c, const cplx_t<R> *grid, cudaStream_t s) {
+        PPD_CHECK(attrs());
+        if (c->n_inv_strips == 0) return PPD_OK;
+        int site;
         PPD_CHECK(launch_begin(c, "fft_inv_cols", s, &site));
-        k_cols_inv<R, K><<<c->n_inv_strips, NT, shc, s>>>(grid, static_cast<cplx_t<R> *>(c->fft_tmp_inv),
-                                                          static_cast<const cplx_t<R> *>(c->tw0), L, c->inv_strips,
-                                                          c->row_inv);
-        PPD_CHECK(launch_end(c, site, s));
+        k_cols_inv<R, K><<<c->n_inv_strips, NT, pass_smem<R>(W, K), s>>>(
+            grid, static_cast<cplx_t<R> *>(c->fft_tmp_inv), static_cast<const cplx_t<R> *>(c->tw0), c->L0,
+            c->inv_strips, c->row_inv);
+        return launch_end(c, site, s);
     }
-    PPD_CHECK(launch_begin(c, "fft_inv_rows", s, &site));
-    k_rows_inv<R, K><<<(L + B - 1) / B, NT, shr, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp_inv), img,
-                                                     static_cast<const cplx_t<R> *>(c->tw0),
-                                                     static_cast<const R *>(c->deap0),
-                                                     static_cast<const R *>(c->deap1), L);
-    PPD_CHECK(launch_end(c, site, s));
-    return PPD_OK;
-}
-
-template <typename R, int K, int T> int fft_inv_part_k(ppd_ctx *c, R *img, cudaStream_t s) {
-    constexpr int B = rows_per_cta<R>(K), W = cols_per_cta<R>(K);
-    const int L = c->L0;
-    size_t shr = pass_smem<R>(B, K), shc = pass_smem<R>(W, K);
-    static bool attr = false;
-    if (!attr) {
-        PPD_CUDA(cudaFuncSetAttribute(k_rows_inv<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shr));
-        PPD_CUDA(cudaFuncSetAttribute(k_cols_inv_part<R, K, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)shc));
-        attr = true;
-    }
-    int site;
-    if (c->n_inv_strips > 0) {
+    static int cols_inv_part(ppd_ctx *c, cudaStream_t s) {
+        PPD_CHECK(attrs());
+        if (c->n_inv_strips == 0) return PPD_OK;
+        int site;
         PPD_CHECK(launch_begin(c, "fft_inv_cols", s, &site));
-        k_cols_inv_part<R, K, T><<<c->n_inv_strips, NT, shc, s>>>(static_cast<const cplx_t<R> *>(c->gpart), c->ch.tile_first, c->ch.tile_n,
-            static_cast<cplx_t<R> *>(c->fft_tmp_inv), static_cast<const cplx_t<R> *>(c->tw0), L, c->inv_strips,
-            c->row_inv);
-        PPD_CHECK(launch_end(c, site, s));
+        const cplx_t<R> *gp = static_cast<const cplx_t<R> *>(c->gpart);
+        cplx_t<R> *out = static_cast<cplx_t<R> *>(c->fft_tmp_inv);
+        const cplx_t<R> *tw = static_cast<const cplx_t<R> *>(c->tw0);
+        if (c->T == 16)
+            k_cols_inv_part<R, K, 16><<<c->n_inv_strips, NT, pass_smem<R>(W, K), s>>>(
+                gp, c->ch.tile_first, c->ch.tile_n, out, tw, c->L0, c->inv_strips, c->row_inv);
+        else
+            k_cols_inv_part<R, K, 32><<<c->n_inv_strips, NT, pass_smem<R>(W, K), s>>>(
+                gp, c->ch.tile_first, c->ch.tile_n, out, tw, c->L0, c->inv_strips, c->row_inv);
+        return launch_end(c, site, s);
     }
-    PPD_CHECK(launch_begin(c, "fft_inv_rows", s, &site));
-    k_rows_inv<R, K><<<(L + B - 1) / B, NT, shr, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp_inv), img,
-                                                     static_cast<const cplx_t<R> *>(c->tw0),
-                                                     static_cast<const R *>(c->deap0),
-                                                     static_cast<const R *>(c->deap1), L);
-    return launch_end(c, site, s);
-}
-
-template <typename R, int K> int fft_inv_part_t(ppd_ctx *c, R *img, cudaStream_t s) {
-    return c->T == 16 ? fft_inv_part_k<R, K, 16>(c, img, s) : fft_inv_part_k<R, K, 32>(c, img, s);
-}
+    static int rows_inv(ppd_ctx *c, R *img, cudaStream_t s) {
+        PPD_CHECK(attrs());
+        int site;
+        PPD_CHECK(launch_begin(c, "fft_inv_rows", s, &site));
+        k_rows_inv<R, K><<<(c->L0 + B - 1) / B, NT, pass_smem<R>(B, K), s>>>(
+            static_cast<const cplx_t<R> *>(c->fft_tmp_inv), img, static_cast<const cplx_t<R> *>(c->tw0),
+            static_cast<const R *>(c->deap0), static_cast<const R *>(c->deap1), c->L0);
+        return launch_end(c, site, s);
+    }
+    static int rows_primal(ppd_ctx *c, cudaStream_t s) {
+        PPD_CHECK(attrs());
+        int site;
+        PPD_CHECK(launch_begin(c, "rows_primal", s, &site));
+        const int n = (c->L0 + B - 1) / B;
+        k_rows_primal<R, K><<<n, NT, pass_smem<R>(B, K), s>>>(
+            static_cast<const cplx_t<R> *>(c->fft_tmp_inv), static_cast<cplx_t<R> *>(c->fft_tmp),
+            static_cast<const cplx_t<R> *>(c->tw0), static_cast<const R *>(c->deap0),
+            static_cast<const R *>(c->deap1), c->col_fwd, primal_args<R>(c), c->prim_part);
+        c->n_stat_parts = n;
+        return launch_end(c, site, s);
+    }
+};
 
 }  // namespace
 
-// Z^T F^H of the grid that the gridding's partial tiles sum to (the combine
-// pass fused into the inverse column FFT).
-template <typename R> int fft_inverse_partials(ppd_ctx *c, R *img, cudaStream_t s) {
+#define PPD_FFT_SIZES(X) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
+#define PPD_FFT_CASE(KK, CALL) case KK: return Pass<R, KK>::CALL;
+
+// forward row pass of x into the FFT temporary (first half of F Z x)
+template <typename R> int fft_forward_rows(ppd_ctx *c, const R *x, cudaStream_t s) {
+    c->xt_rows_valid = false;
     switch (c->K0) {
-        case 32: return fft_inv_part_t<R, 32>(c, img, s);
-        case 64: return fft_inv_part_t<R, 64>(c, img, s);
-        case 128: return fft_inv_part_t<R, 128>(c, img, s);
-        case 256: return fft_inv_part_t<R, 256>(c, img, s);
-        case 512: return fft_inv_part_t<R, 512>(c, img, s);
-        case 1024: return fft_inv_part_t<R, 1024>(c, img, s);
-        case 2048: return fft_inv_part_t<R, 2048>(c, img, s);
-        case 4096: return fft_inv_part_t<R, 4096>(c, img, s);
-        case 8192: return fft_inv_part_t<R, 8192>(c, img, s);
+#define X(KK) PPD_FFT_CASE(KK, rows_fwd(c, x, s))
+        PPD_FFT_SIZES(X)
+#undef X
         default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
     }
 }
 
-template int fft_inverse_partials<float>(ppd_ctx *, float *, cudaStream_t);
-template int fft_inverse_partials<double>(ppd_ctx *, double *, cudaStream_t);
-
-template <typename R> int fft_forward(ppd_ctx *c, const R *x, cplx_t<R> *grid, cudaStream_t s) {
+// forward column pass from the FFT temporary to the grid (second half of F Z x)
+template <typename R> int fft_forward_cols(ppd_ctx *c, cplx_t<R> *grid, cudaStream_t s) {
     switch (c->K0) {
-        case 32: return fft_fwd_k<R, 32>(c, x, grid, s);
-        case 64: return fft_fwd_k<R, 64>(c, x, grid, s);
-        case 128: return fft_fwd_k<R, 128>(c, x, grid, s);
-        case 256: return fft_fwd_k<R, 256>(c, x, grid, s);
-        case 512: return fft_fwd_k<R, 512>(c, x, grid, s);
-        case 1024: return fft_fwd_k<R, 1024>(c, x, grid, s);
-        case 2048: return fft_fwd_k<R, 2048>(c, x, grid, s);
-        case 4096: return fft_fwd_k<R, 4096>(c, x, grid, s);
-        case 8192: return fft_fwd_k<R, 8192>(c, x, grid, s);
+#define X(KK) PPD_FFT_CASE(KK, cols_fwd(c, grid, s))
+        PPD_FFT_SIZES(X)
+#undef X
         default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
     }
+}
+
+// inverse column pass of a combined grid into the inverse temporary
+template <typename R> int fft_inverse_cols(ppd_ctx *c, const cplx_t<R> *grid, cudaStream_t s) {
+    switch (c->K0) {
+#define X(KK) PPD_FFT_CASE(KK, cols_inv(c, grid, s))
+        PPD_FFT_SIZES(X)
+#undef X
+        default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
+    }
+}
+
+// inverse column pass summing the gridding's partial tiles while loading
+// (the combine pass fused in)
+template <typename R> int fft_inverse_cols_partials(ppd_ctx *c, cudaStream_t s) {
+    switch (c->K0) {
+#define X(KK) PPD_FFT_CASE(KK, cols_inv_part(c, s))
+        PPD_FFT_SIZES(X)
+#undef X
+        default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
+    }
+}
+
+// inverse row pass + primal step + forward row pass of the new xt
+template <typename R> int rows_primal(ppd_ctx *c, cudaStream_t s) {
+    switch (c->K0) {
+#define X(KK) PPD_FFT_CASE(KK, rows_primal(c, s))
+        PPD_FFT_SIZES(X)
+#undef X
+        default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
+    }
+}
+
+template <typename R> int fft_forward(ppd_ctx *c, const R *x, cplx_t<R> *grid, cudaStream_t s) {
+    PPD_CHECK(fft_forward_rows<R>(c, x, s));
+    return fft_forward_cols<R>(c, grid, s);
 }
 
 template <typename R> int fft_inverse(ppd_ctx *c, const cplx_t<R> *grid, R *img, cudaStream_t s) {
+    PPD_CHECK(fft_inverse_cols<R>(c, grid, s));
     switch (c->K0) {
-        case 32: return fft_inv_k<R, 32>(c, grid, img, s);
-        case 64: return fft_inv_k<R, 64>(c, grid, img, s);
-        case 128: return fft_inv_k<R, 128>(c, grid, img, s);
-        case 256: return fft_inv_k<R, 256>(c, grid, img, s);
-        case 512: return fft_inv_k<R, 512>(c, grid, img, s);
-        case 1024: return fft_inv_k<R, 1024>(c, grid, img, s);
-        case 2048: return fft_inv_k<R, 2048>(c, grid, img, s);
-        case 4096: return fft_inv_k<R, 4096>(c, grid, img, s);
-        case 8192: return fft_inv_k<R, 8192>(c, grid, img, s);
+#define X(KK) PPD_FFT_CASE(KK, rows_inv(c, img, s))
+        PPD_FFT_SIZES(X)
+#undef X
         default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
     }
 }
 
-template int fft_forward<float>(ppd_ctx *, const float *, float2 *, cudaStream_t);
-template int fft_forward<double>(ppd_ctx *, const double *, double2 *, cudaStream_t);
-template int fft_inverse<float>(ppd_ctx *, const float2 *, float *, cudaStream_t);
-template int fft_inverse<double>(ppd_ctx *, const double2 *, double *, cudaStream_t);
+#undef PPD_FFT_CASE
+#undef PPD_FFT_SIZES
+
+#define PPD_FFT_INST(R)                                                                                         \
+    template int fft_forward<R>(ppd_ctx *, const R *, cplx_t<R> *, cudaStream_t);                              \
+    template int fft_inverse<R>(ppd_ctx *, const cplx_t<R> *, R *, cudaStream_t);                              \
+    template int fft_forward_rows<R>(ppd_ctx *, const R *, cudaStream_t);                                       \
+    template int fft_forward_cols<R>(ppd_ctx *, cplx_t<R> *, cudaStream_t);                                     \
+    template int fft_inverse_cols<R>(ppd_ctx *, const cplx_t<R> *, cudaStream_t);                              \
+    template int fft_inverse_cols_partials<R>(ppd_ctx *, cudaStream_t);                                         \
+    template int rows_primal<R>(ppd_ctx *, cudaStream_t);
+PPD_FFT_INST(float)
+PPD_FFT_INST(double)
+#undef PPD_FFT_INST
 
 // Column strips (W columns each, W as the column passes use) that contain a
 // marked column, and the row / column masks, uploaded for the pruned passes.
