@@ -263,184 +263,6 @@ __global__ void __launch_bounds__(NT) k_sara_syn0(const R *__restrict__ coef, co
     }
 }
 
-// ------------------------------------------------------------- coarse levels
-// Levels whose input (analysis) or output (synthesis) side is at most
-// coarse_max<R>() run with one CTA per basis, every level in shared memory,
-// in one launch: a level of a small image costs one launch ramp and a few
-// barriers instead of a full grid of tiles.
-constexpr int NTC = 512;
-template <typename R> constexpr int coarse_max() { return sizeof(R) == 4 ? 128 : 64; }
-template <typename R> constexpr size_t coarse_smem() {
-    return (size_t)2 * coarse_max<R>() * coarse_max<R>() * sizeof(R);
-}
-
-// Analysis of levels l0 .. levels-1 for one basis: X holds the level input
-// (n x n), Tm the row-filtered image; the LL quadrant becomes the next
-// level's input in X; detail quadrants (and the last LL) go to the
-// coefficient image exactly as in ana_tile.
-template <typename R, int F>
-__device__ __forceinline__ void ana_coarse(const R *__restrict__ src, int in_pitch, int n, int nlev,
-                                           R *__restrict__ cb, const R *__restrict__ wb, int L, int mode, R kappa,
-                                           int b, R *X, R *Tm) {
-    const Taps<R, F> f(b);
-    for (int e = threadIdx.x; e < n * n; e += NTC) X[e] = src[(int64_t)(e / n) * in_pitch + e % n];
-    __syncthreads();
-    for (int lev = 0; lev < nlev; ++lev, n >>= 1) {
-        const int h = n >> 1;
-        const bool last = lev == nlev - 1;
-        for (int e = threadIdx.x; e < n * n; e += NTC) {   // rows: low half, then high half
-            const int i = e / n, q = e % n;
-            const bool hi = q >= h;
-            const int qq = hi ? q - h : q;
-            const R *row = X + i * n;
-            R acc = 0;
-#pragma unroll
-            for (int k = 0; k < F; ++k) acc += (hi ? f.g[k] : f.h[k]) * row[wrap(2 * qq + k, n)];
-            Tm[e] = acc;
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < n * n; e += NTC) {   // columns
-            const int r = e / n, q = e % n;
-            const bool hi0 = r >= h, hi1 = q >= h;
-            const int rr = hi0 ? r - h : r;
-            R acc = 0;
-#pragma unroll
-            for (int k = 0; k < F; ++k) acc += (hi0 ? f.g[k] : f.h[k]) * Tm[wrap(2 * rr + k, n) * n + q];
-            if (!hi0 && !hi1 && !last) {
-                X[rr * h + q] = acc;                       // next level's input (X no longer read)
-            } else {
-                const int64_t off = (int64_t)r * L + q;
-                R *dst = cb + off;
-                const R cv = acc * R(1.0 / 3.0);
-                if (mode == 0) {
-                    *dst = cv;
-                } else {
-                    const R u = *dst + (wb ? wb[off] * cv : cv);
-                    *dst = fmin(fmax(u, -kappa), kappa);
-                }
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// grid.x = basis; in: level-l0 input (basis b at in + b*in_bstride, pitch
-// in_pitch); other arguments as k_sara_ana.
-template <typename R>
-__global__ void __launch_bounds__(NTC) k_sara_ana_coarse(const R *__restrict__ in, int in_pitch, int64_t in_bstride,
-                                                         int n, int nlev, R *__restrict__ coef,
-                                                         const R *__restrict__ wgt, int L, int64_t N, int mode,
-                                                         R kappa, const uint8_t *__restrict__ pmask) {
-    const int b = blockIdx.x;
-    if (mode == 1 && pmask && !pmask[b + 1]) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *X = reinterpret_cast<R *>(smem_raw);
-    R *Tm = X + coarse_max<R>() * coarse_max<R>();
-    const R *src = in + (int64_t)b * in_bstride;
-    R *cb = coef + (int64_t)(b + 1) * N;
-    const R *wb = wgt ? wgt + (int64_t)(b + 1) * N : nullptr;
-    switch (b) {
-        case 0: ana_coarse<R, 2>(src, in_pitch, n, nlev, cb, wb, L, mode, kappa, b, X, Tm); break;
-        case 1: ana_coarse<R, 4>(src, in_pitch, n, nlev, cb, wb, L, mode, kappa, b, X, Tm); break;
-        case 2: ana_coarse<R, 6>(src, in_pitch, n, nlev, cb, wb, L, mode, kappa, b, X, Tm); break;
-        case 3: ana_coarse<R, 8>(src, in_pitch, n, nlev, cb, wb, L, mode, kappa, b, X, Tm); break;
-        case 4: ana_coarse<R, 10>(src, in_pitch, n, nlev, cb, wb, L, mode, kappa, b, X, Tm); break;
-        case 5: ana_coarse<R, 12>(src, in_pitch, n, nlev, cb, wb, L, mode, kappa, b, X, Tm); break;
-        case 6: ana_coarse<R, 14>(src, in_pitch, n, nlev, cb, wb, L, mode, kappa, b, X, Tm); break;
-        default: ana_coarse<R, 16>(src, in_pitch, n, nlev, cb, wb, L, mode, kappa, b, X, Tm); break;
-    }
-}
-
-// Synthesis of levels levels-1 .. l1 for one basis (output sides n_c ..
-// n_1): P0 holds the four quadrants of the level (LL' first: the
-// coefficients at the coarsest level, else the previous level's output,
-// already in place), P1 the column-inverted halves; the output overwrites
-// P0 and is the next level's LL'.  The last output goes to out (pitch n_1).
-template <typename R, int F>
-__device__ __forceinline__ void syn_coarse(const R *__restrict__ cb, const R *__restrict__ wb, int L, int n,
-                                           int n_last, int b, R *__restrict__ out, R *P0, R *P1) {
-    const Taps<R, F> f(b);
-    bool coarsest = true;
-    for (; n <= n_last; n <<= 1) {
-        const int h = n >> 1, hh = h * h;
-        for (int e = threadIdx.x; e < 4 * hh; e += NTC) {   // quadrants (LL' from the coefficients only at first)
-            const int qd = e / hh, r = e % hh, i = r / h, j = r % h;
-            if (qd == 0 && !coarsest) continue;
-            const int64_t off = (int64_t)((qd & 2) ? h + i : i) * L + ((qd & 1) ? h : 0) + j;
-            R v = cb[off];
-            if (wb) v *= wb[off];
-            P0[e] = v;
-        }
-        __syncthreads();
-        const R *Q0 = P0, *Q1 = P0 + hh, *Q2 = P0 + 2 * hh, *Q3 = P0 + 3 * hh;
-        R *tl = P1, *th = P1 + n * h;
-        for (int e = threadIdx.x; e < n * h; e += NTC) {   // inverse along axis 0
-            const int m = e / h, j = e % h, par = m & 1;
-            R sl0 = 0, sh0 = 0;
-#pragma unroll
-            for (int kk = 0; kk < F / 2; ++kk) {
-                const int k = 2 * kk + par;
-                const int il = wrap(m - k, n) >> 1;
-                const R a = par ? f.h[2 * kk + 1] : f.h[2 * kk], c = par ? f.g[2 * kk + 1] : f.g[2 * kk];
-                sl0 += a * Q0[il * h + j] + c * Q2[il * h + j];
-                sh0 += a * Q1[il * h + j] + c * Q3[il * h + j];
-            }
-            tl[m * h + j] = sl0;
-            th[m * h + j] = sh0;
-        }
-        __syncthreads();
-        const bool final_level = n == n_last;
-        for (int e = threadIdx.x; e < n * n; e += NTC) {   // inverse along axis 1
-            const int m = e / n, nn = e % n, par = nn & 1;
-            R o = 0;
-#pragma unroll
-            for (int kk = 0; kk < F / 2; ++kk) {
-                const int j = 2 * kk + par;
-                const int jl = wrap(nn - j, n) >> 1;
-                const R a = par ? f.h[2 * kk + 1] : f.h[2 * kk], c = par ? f.g[2 * kk + 1] : f.g[2 * kk];
-                o += a * tl[m * h + jl] + c * th[m * h + jl];
-            }
-            if (final_level) out[e] = o;
-            else P0[e] = o;                                  // the next level's LL' (quadrants no longer read)
-        }
-        __syncthreads();
-        coarsest = false;
-    }
-}
-
-// grid.x = basis: synthesis of levels levels-1 .. l1, coarsest output side
-// n_c, last output side n_last written to out (basis b at out + b*out_bstride).
-template <typename R>
-__global__ void __launch_bounds__(NTC) k_sara_syn_coarse(const R *__restrict__ coef, const R *__restrict__ wgt, int L,
-                                                         int64_t N, int n_c, int n_last, R *__restrict__ out,
-                                                         int64_t out_bstride) {
-    const int b = blockIdx.x;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *P0 = reinterpret_cast<R *>(smem_raw);
-    R *P1 = P0 + coarse_max<R>() * coarse_max<R>();
-    const R *cb = coef + (int64_t)(b + 1) * N;
-    const R *wb = wgt ? wgt + (int64_t)(b + 1) * N : nullptr;
-    R *ob = out + (int64_t)b * out_bstride;
-    switch (b) {
-        case 0: syn_coarse<R, 2>(cb, wb, L, n_c, n_last, b, ob, P0, P1); break;
-        case 1: syn_coarse<R, 4>(cb, wb, L, n_c, n_last, b, ob, P0, P1); break;
-        case 2: syn_coarse<R, 6>(cb, wb, L, n_c, n_last, b, ob, P0, P1); break;
-        case 3: syn_coarse<R, 8>(cb, wb, L, n_c, n_last, b, ob, P0, P1); break;
-        case 4: syn_coarse<R, 10>(cb, wb, L, n_c, n_last, b, ob, P0, P1); break;
-        case 5: syn_coarse<R, 12>(cb, wb, L, n_c, n_last, b, ob, P0, P1); break;
-        case 6: syn_coarse<R, 14>(cb, wb, L, n_c, n_last, b, ob, P0, P1); break;
-        default: syn_coarse<R, 16>(cb, wb, L, n_c, n_last, b, ob, P0, P1); break;
-    }
-}
-
-// First level handled by the coarse kernels: the smallest l whose side
-// L >> l fits (levels when none does).
-inline int coarse_level(int L, int levels, int cmax) {
-    for (int l = 0; l < levels; ++l)
-        if ((L >> l) <= cmax) return l;
-    return levels;
-}
-
 template <typename R> __global__ void k_scale_copy(const R *__restrict__ in, R *__restrict__ out, int64_t n, R a) {
     for (int64_t e = blockIdx.x * (int64_t)NT + threadIdx.x; e < n; e += (int64_t)gridDim.x * NT) out[e] = a * in[e];
 }
@@ -458,9 +280,8 @@ template <typename R> int analysis_all(ppd_ctx *c, const R *x, R *coef, int mode
     const int64_t N = c->N;
     R *ll[2] = {static_cast<R *>(c->wtmp), static_cast<R *>(c->wtmp) + (int64_t)N_WAVELETS * (L / 2) * (L / 2)};
     const int64_t ll_stride = (int64_t)(L / 2) * (L / 2);
-    const int lc = coarse_level(L, c->levels, coarse_max<R>());
     int site;
-    for (int l = 0; l < lc; ++l) {
+    for (int l = 0; l < c->levels; ++l) {
         const int n = L >> l, h = n / 2;
         const bool last = (l == c->levels - 1);
         const R *in = l == 0 ? x : ll[(l - 1) & 1];
@@ -469,21 +290,6 @@ template <typename R> int analysis_all(ppd_ctx *c, const R *x, R *coef, int mode
         PPD_CHECK(launch_begin(c, "sara_analysis", s, &site));
         k_sara_ana<R><<<dim3(tiles(h, TSA), N_WAVELETS), NT, 0, s>>>(in, pitch, bstride, n, ll[l & 1], ll_stride, last,
                                                                      coef, wgt, L, N, mode, alpha, pmask);
-        PPD_CHECK(launch_end(c, site, s));
-    }
-    if (lc < c->levels) {   // levels lc .. levels-1 in one launch, one CTA per basis
-        static bool attr = false;
-        if (!attr) {
-            PPD_CUDA(cudaFuncSetAttribute(k_sara_ana_coarse<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)coarse_smem<R>()));
-            attr = true;
-        }
-        const int n = L >> lc;
-        const R *in = lc == 0 ? x : ll[(lc - 1) & 1];
-        PPD_CHECK(launch_begin(c, "sara_analysis", s, &site));
-        k_sara_ana_coarse<R><<<N_WAVELETS, NTC, coarse_smem<R>(), s>>>(in, lc == 0 ? L : n, lc == 0 ? 0 : ll_stride, n,
-                                                                         c->levels - lc, coef, wgt, L, N, mode, alpha,
-                                                                         pmask);
         PPD_CHECK(launch_end(c, site, s));
     }
     return PPD_OK;
@@ -499,27 +305,9 @@ int synthesis_levels(ppd_ctx *c, const R *coef, const R *wgt, const R **ll0, cud
     R *buf[2] = {static_cast<R *>(c->wtmp2), static_cast<R *>(c->wtmp2) + (int64_t)N_WAVELETS * st};
     const R *prev = nullptr;
     int site, k = 0;
-    // levels levels-1 .. lcs (output sides up to the coarse limit) in one launch
-    const int lcs = std::max(1, coarse_level(L, c->levels, coarse_max<R>()));
-    int l_top = c->levels - 1;
-    if (lcs <= c->levels - 1) {
-        static bool attr = false;
-        if (!attr) {
-            PPD_CUDA(cudaFuncSetAttribute(k_sara_syn_coarse<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)coarse_smem<R>()));
-            attr = true;
-        }
-        PPD_CHECK(launch_begin(c, "sara_synthesis", s, &site));
-        k_sara_syn_coarse<R><<<N_WAVELETS, NTC, coarse_smem<R>(), s>>>(coef, wgt, L, N, L >> (c->levels - 1), L >> lcs,
-                                                                         buf[0], st);
-        PPD_CHECK(launch_end(c, site, s));
-        prev = buf[0];
-        k = 1;
-        l_top = lcs - 1;
-    }
-    for (int l = l_top; l >= 1; --l, ++k) {
+    for (int l = c->levels - 1; l >= 1; --l, ++k) {
         const int n = L >> l, h = n / 2;
-        const bool coarsest = (l == c->levels - 1);   // (never after the coarse launch)
+        const bool coarsest = (l == c->levels - 1);
         PPD_CHECK(launch_begin(c, "sara_synthesis", s, &site));
         k_sara_syn<R><<<dim3(tiles(h, TS), N_WAVELETS), NT, 0, s>>>(coef, wgt, L, N, coarsest ? coef : prev,
                                                                     coarsest ? 1 : 0, st, n, buf[k & 1], st);
