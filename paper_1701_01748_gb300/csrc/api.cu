@@ -211,8 +211,9 @@ template <typename R> int iteration_body(ppd_ctx *c, cudaStream_t s, bool first)
 
     double *bank[2] = {c->partials, c->partials + NPART * c->ch.n};
     int cur = 0;
-    // the forward row pass of xt was done by the previous iteration's last
-    // kernel (or by run_iterations before the first one)
+    // with the fused row kernel the forward row pass of xt was done by the
+    // previous iteration's last kernel (or by run_iterations before the first)
+    if (!fused_rows(c)) PPD_CHECK(fft_forward_rows<R>(c, static_cast<const R *>(c->xt), s));
     PPD_CHECK(fft_forward_cols<R>(c, ga, s));
     const bool current = c->cfg.inner_init == PPD_INNER_CURRENT;
     // with randomised active sets the warm start is decided per block on
@@ -256,9 +257,15 @@ template <typename R> int iteration_body(ppd_ctx *c, cudaStream_t s, bool first)
         PPD_CHECK(grid_vis<R>(c, GR_DUAL, nullptr, nullptr, gv, s, /*combine=*/false));
         PPD_CHECK(fft_inverse_cols_partials<R>(c, s));
     }
-    if (fork) PPD_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
-    // inverse row pass, primal step and the next iteration's forward row pass
-    PPD_CHECK(rows_primal<R>(c, s));
+    if (fused_rows(c)) {
+        if (fork) PPD_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
+        // inverse row pass, primal step and the next iteration's forward row pass
+        PPD_CHECK(rows_primal<R>(c, s));
+    } else {
+        PPD_CHECK(fft_inverse_rows<R>(c, static_cast<R *>(c->g), s));
+        if (fork) PPD_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
+        PPD_CHECK(primal_step<R>(c, s));
+    }
     return PPD_OK;
 }
 
@@ -290,7 +297,7 @@ int rand_finish(ppd_ctx *c, cudaStream_t s) {
 // anything else (a reset, a restored state, an operator call, the power
 // iteration) the row pass runs on its own first.
 template <typename R> int xt_rows_ready(ppd_ctx *c, cudaStream_t s) {
-    if (c->xt_rows_valid) return PPD_OK;
+    if (c->xt_rows_valid || !fused_rows(c)) return PPD_OK;
     PPD_CHECK(fft_forward_rows<R>(c, static_cast<const R *>(c->xt), s));
     c->xt_rows_valid = true;
     return PPD_OK;
@@ -343,7 +350,7 @@ template <typename R> int run_iterations(ppd_ctx *c, int n) {
             c->graph_ran_since_collect = true;
         }
         PPD_CHECK(rand_finish(c, s));
-        c->xt_rows_valid = true;
+        c->xt_rows_valid = fused_rows(c);
         c->p_valid = true;
         c->iters++;
     }
@@ -1288,7 +1295,7 @@ int ppd_group_iterate(ppd_group *g, int32_t n_iters) {
             PPD_CHECK(xt_rows_ready<float>(c, c->stream));
             PPD_CHECK(iteration_body<float>(c, c->stream, !c->p_valid));
             PPD_CHECK(rand_finish(c, c->stream));
-            c->xt_rows_valid = true;
+            c->xt_rows_valid = fused_rows(c);
             c->p_valid = true;
             c->iters++;
         }
@@ -1347,7 +1354,7 @@ int ppd_group_iterate(ppd_group *g, int32_t n_iters) {
         PPD_CUDA(cudaGraphLaunch(g->exec, g->stream));
         for (ppd_ctx *c : g->ctxs) {
             PPD_CHECK(rand_finish(c, g->stream));
-            c->xt_rows_valid = true;
+            c->xt_rows_valid = fused_rows(c);
         }
         for (size_t i = 0; i < g->ctxs.size(); ++i) {
             g->ctxs[i]->iters++;

@@ -321,6 +321,12 @@ __device__ __forceinline__ R primal_pixel(const PrimalArgs<R> &P, int64_t e, R g
 }
 
 template <typename R> PrimalArgs<R> primal_args(ppd_ctx *c);
+template <typename R> int primal_step(ppd_ctx *c, cudaStream_t s);   // from g = Phi^dagger v in memory
+template <typename R> int fft_inverse_rows(ppd_ctx *c, R *img, cudaStream_t s);
+// Grids up to K = 2048 end the iteration with the fused row kernel; larger
+// grids with the plain inverse row pass and the primal kernel (an 8192-point
+// row pair per CTA costs more registers than the two launches it saves).
+inline bool fused_rows(const ppd_ctx *c) { return c->K0 <= 2048; }
 // inverse row pass + primal step + the next iteration's forward row pass (fft.cu)
 template <typename R> int rows_primal(ppd_ctx *c, cudaStream_t s);
 template <typename R> int fft_forward_rows(ppd_ctx *c, const R *x, cudaStream_t s);

@@ -490,6 +490,16 @@ template <typename R> int fft_inverse_cols_partials(ppd_ctx *c, cudaStream_t s) 
     }
 }
 
+// inverse row pass into an image (second half of Z^T F^H)
+template <typename R> int fft_inverse_rows(ppd_ctx *c, R *img, cudaStream_t s) {
+    switch (c->K0) {
+#define X(KK) PPD_FFT_CASE(KK, rows_inv(c, img, s))
+        PPD_FFT_SIZES(X)
+#undef X
+        default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
+    }
+}
+
 // inverse row pass + primal step + forward row pass of the new xt
 template <typename R> int rows_primal(ppd_ctx *c, cudaStream_t s) {
     switch (c->K0) {
@@ -507,12 +517,7 @@ template <typename R> int fft_forward(ppd_ctx *c, const R *x, cplx_t<R> *grid, c
 
 template <typename R> int fft_inverse(ppd_ctx *c, const cplx_t<R> *grid, R *img, cudaStream_t s) {
     PPD_CHECK(fft_inverse_cols<R>(c, grid, s));
-    switch (c->K0) {
-#define X(KK) PPD_FFT_CASE(KK, rows_inv(c, img, s))
-        PPD_FFT_SIZES(X)
-#undef X
-        default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
-    }
+    return fft_inverse_rows<R>(c, img, s);
 }
 
 #undef PPD_FFT_CASE
@@ -525,6 +530,7 @@ template <typename R> int fft_inverse(ppd_ctx *c, const cplx_t<R> *grid, R *img,
     template int fft_forward_cols<R>(ppd_ctx *, cplx_t<R> *, cudaStream_t);                                     \
     template int fft_inverse_cols<R>(ppd_ctx *, const cplx_t<R> *, cudaStream_t);                              \
     template int fft_inverse_cols_partials<R>(ppd_ctx *, cudaStream_t);                                         \
+    template int fft_inverse_rows<R>(ppd_ctx *, R *, cudaStream_t);                                             \
     template int rows_primal<R>(ppd_ctx *, cudaStream_t);
 PPD_FFT_INST(float)
 PPD_FFT_INST(double)

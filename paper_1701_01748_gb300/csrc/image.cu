@@ -11,6 +11,17 @@ namespace {
 
 constexpr int NT = 256;
 
+// Primal step of Algorithm 3 (primal_pixel) over all pixels, grid-stride,
+// from g = Phi^dagger v in memory, with FP64 partials per CTA.
+template <typename R>
+__global__ void __launch_bounds__(NT) k_primal(PrimalArgs<R> P, const R *__restrict__ g, int64_t N,
+                                               double *__restrict__ part) {
+    PrimalSums<R> acc;
+    for (int64_t e = blockIdx.x * (int64_t)NT + threadIdx.x; e < N; e += (int64_t)gridDim.x * NT)
+        primal_pixel(P, e, g[e], acc);
+    acc.write(part + 3 * (int64_t)blockIdx.x);
+}
+
 __global__ void k_reduce3(const double *__restrict__ part, int n, double *__restrict__ out) {
     double a = 0, b = 0, c = 0;
     for (int i = threadIdx.x; i < n; i += NT) {
@@ -68,6 +79,14 @@ template <typename R> PrimalArgs<R> primal_args(ppd_ctx *c) {
     return P;
 }
 
+template <typename R> int primal_step(ppd_ctx *c, cudaStream_t s) {
+    int site;
+    PPD_CHECK(launch_begin(c, "primal", s, &site));
+    k_primal<R><<<c->n_prim_blocks, NT, 0, s>>>(primal_args<R>(c), static_cast<const R *>(c->g), c->N, c->prim_part);
+    c->n_stat_parts = c->n_prim_blocks;
+    return launch_end(c, site, s);
+}
+
 int reduce_primal_stats(ppd_ctx *c, cudaStream_t s) {
     int site;
     PPD_CHECK(launch_begin(c, "stats", s, &site));
@@ -112,6 +131,8 @@ template int mul_sq<float>(ppd_ctx *, float *, const float *, int64_t, cudaStrea
 template int mul_sq<double>(ppd_ctx *, double *, const double *, int64_t, cudaStream_t);
 template PrimalArgs<float> primal_args<float>(ppd_ctx *);
 template PrimalArgs<double> primal_args<double>(ppd_ctx *);
+template int primal_step<float>(ppd_ctx *, cudaStream_t);
+template int primal_step<double>(ppd_ctx *, cudaStream_t);
 template int sumsq<float>(ppd_ctx *, const float *, int64_t, double *, cudaStream_t);
 template int sumsq<double>(ppd_ctx *, const double *, int64_t, double *, cudaStream_t);
 template int scale_copy<float>(ppd_ctx *, const float *, float *, int64_t, double, cudaStream_t);
