@@ -1,0 +1,48 @@
+"""Host-side logic of the benchmark: the algorithmic byte model behind the
+roofline figures and the rule that ties an ncu DRAM summary to the sources
+it was captured on (traffic is reported only for unchanged kernels)."""
+import os
+import shutil
+
+import pytest
+
+import bench
+
+
+def test_byte_model_counts_each_array_once():
+    L, M = 512, 524288
+    N, K2 = L * L, 4 * L * L
+    b = bench.algorithmic_bytes_per_step(L, M)
+    # degridding: 16-byte record, v, y, p read; z, w written (8 bytes each); the grid read once
+    assert b["degrid_dual"] == 16 * M + 5 * 8 * M + 8 * K2
+    # fused row kernel: inverse temporary read, forward temporary written (L x K complex each),
+    # x, xt, ut, u_Dirac, x_true read and x, xt, u_Dirac written (4 bytes each)
+    assert b["rows_primal"] == 2 * (8 * 2 * N) + 4 * N * 8
+    # SARA analysis: xt once, then per level and basis the input LL, the three detail
+    # quadrants read and written, the LL written (read and written in u at the last level)
+    ana = 4 * N
+    for lev in range(4):
+        q = N / 4 ** (lev + 1)
+        ana += 8 * 4 * ((0 if lev == 0 else 4 * q) + 2 * 3 * q + (2 * q if lev == 3 else q))
+    assert b["sara_analysis"] == pytest.approx(ana)
+    # FP64 doubles every term
+    b64 = bench.algorithmic_bytes_per_step(L, M, rsz=8)
+    assert b64["fft_fwd_cols"] == 2 * b["fft_fwd_cols"]
+
+
+def test_traffic_only_for_the_sources_it_was_captured_on(tmp_path, monkeypatch):
+    root = tmp_path / "repo"
+    shutil.copytree(os.path.join(bench.ROOT, "paper_1701_01748_gb300", "csrc"),
+                    root / "paper_1701_01748_gb300" / "csrc")
+    (root / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.dram_traffic("w")[0] == {}                 # no capture
+    digest = bench.source_digest()
+    (root / "profiles" / "ncu_dram_w.txt").write_text(
+        "# header\nsources sha256: " + digest + "\nsara_analysis 3075904 12 14.2\ngrid_dual 21047723 3 48.6\n")
+    traffic, why = bench.dram_traffic("w")
+    assert traffic == {"sara_analysis": 3075904.0, "grid_dual": 21047723.0} and "ncu" in why
+    # any change to a kernel source voids the capture
+    f = root / "paper_1701_01748_gb300" / "csrc" / "vis.cu"
+    f.write_text(f.read_text() + "\n// changed\n")
+    assert bench.dram_traffic("w") == ({}, "kernels changed since the ncu capture")
