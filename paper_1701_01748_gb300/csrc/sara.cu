@@ -39,6 +39,7 @@ constexpr int TS = 8;                         // synthesis: quadrant positions p
 constexpr int AEXT = 2 * TSA + MAX_TAPS - 2;  // analysis input tile side (46)
 constexpr int SEXT = TS + MAX_TAPS / 2 - 1;   // synthesis quadrant tile side (15)
 static_assert(NT == 4 * TS * TS, "one synthesis output per thread");
+static_assert(2 * TSA % (NT / 32) == 0, "analysis column rows per warp");
 
 // periodic index for power-of-two n (two's complement makes the mask exact
 // for negative i)
@@ -67,29 +68,45 @@ __device__ __forceinline__ void ana_tile(const R *__restrict__ src, int in_pitch
                                          const R *__restrict__ wb, int L, int mode, R kappa, int b, R *tin,
                                          R *rowf) {
     constexpr int EXT = 2 * TSA + F - 2;
+    constexpr int NQ = 2 * TSA / (NT / 32);   // output rows per warp in the column pass
     const Taps<R, F> f(b);
     const int h = n >> 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cc = lane & (TSA - 1);
+    const bool hi1 = lane >= TSA;
+    // the coefficients this thread clip-updates (and their weights) are
+    // loaded before the input tile, so both global round trips overlap
+    R pu[NQ], pw[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+        const int rq = warp + k * (NT / 32), rr = rq & (TSA - 1);
+        const bool hi0 = rq >= TSA;
+        pu[k] = R(0);
+        pw[k] = R(1);
+        if (mode != 0 && rr < h && cc < h && (hi0 || hi1 || last)) {
+            const int64_t off = (int64_t)((hi0 ? h : 0) + R0 + rr) * L + (hi1 ? h : 0) + C0 + cc;
+            pu[k] = cb[off];
+            if (wb) pw[k] = wb[off];
+        }
+    }
     for (int i = warp; i < EXT; i += NT / 32) {
         const R *row = src + (int64_t)wrap(2 * R0 + i, n) * in_pitch;
         for (int j = lane; j < EXT; j += 32) tin[i * AEXT + j] = row[wrap(2 * C0 + j, n)];
     }
     __syncthreads();
     {   // rows: lane = output column q (low half, then high half)
-        const int cc = lane & (TSA - 1);
-        const bool hi = lane >= TSA;
         for (int i = warp; i < EXT; i += NT / 32) {
             const R *row = tin + i * AEXT + 2 * cc;
             R acc = 0;
 #pragma unroll
-            for (int k = 0; k < F; ++k) acc += (hi ? f.g[k] : f.h[k]) * row[k];
+            for (int k = 0; k < F; ++k) acc += (hi1 ? f.g[k] : f.h[k]) * row[k];
             rowf[i * 2 * TSA + lane] = acc;
         }
     }
     __syncthreads();
-    const int cc = lane & (TSA - 1);
-    const bool hi1 = lane >= TSA;
-    for (int rq = warp; rq < 2 * TSA; rq += NT / 32) {   // columns: warp = output row
+#pragma unroll
+    for (int kq = 0; kq < NQ; ++kq) {   // columns: warp = output row
+        const int rq = warp + kq * (NT / 32);
         const int rr = rq & (TSA - 1);
         const bool hi0 = rq >= TSA;
         const R *col = rowf + 2 * rr * 2 * TSA + lane;
@@ -106,7 +123,7 @@ __device__ __forceinline__ void ana_tile(const R *__restrict__ src, int in_pitch
             if (mode == 0) {
                 *dst = cv;
             } else {
-                const R u = *dst + (wb ? wb[off] * cv : cv);
+                const R u = pu[kq] + (wb ? pw[kq] * cv : cv);
                 *dst = fmin(fmax(u, -kappa), kappa);
             }
         }
