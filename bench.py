@@ -207,31 +207,85 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ CPU oracle leg
-def oracle_worker(args):
-    """Run in a fresh single-threaded interpreter: time oracle PPD iterations."""
+GOLDEN_NORMS = os.path.join(ROOT, "tests", "golden", "op_norms.json")
+
+
+def oracle_op_norm(p, P, U):
+    """||U^{1/2} Phi||_S^2 of problem p for the oracle: the value stored by
+    tests/golden/make_op_norms.py (the oracle's Lanczos routine, run offline)
+    when it was made for this workload, seed and size, else the same routine
+    now.  Returns (value, source)."""
     from oracle import ppd as oppd
+    try:
+        with open(GOLDEN_NORMS) as f:
+            rec = json.load(f).get(p.name)
+    except (OSError, ValueError):
+        rec = None
+    if rec and rec["seed"] == p.seed and rec["L"] == p.L and rec["M"] == p.M:
+        return float(rec["op_norm_sq"]), "tests/golden/op_norms.json (oracle Lanczos, stored)"
+    val, _ = oppd.op_norm_sq_lanczos(P, U, tol=1e-8)
+    return val, "oracle Lanczos at set-up"
+
+
+def oracle_setup(workload: str, seed: int):
+    """The oracle's set-up of the workload (never timed): eta = 1/||U^{1/2} Phi||^2
+    as Section 5.1 asks, so that the convergence condition holds."""
+    from oracle import nufft, ppd as oppd
     from paper_1701_01748_gb300 import synth
-    p = synth.make_problem(args.workload, seed=args.seed)
-    S = oppd.make_setup(p.omega, p.y, p.theta, p.block, p.n_blocks, p.L, eta=1.0, x_true=p.x_true)
+    p = synth.make_problem(workload, seed=seed)
+    P = nufft.Plan(p.omega, p.L, p.L, theta=p.theta)
+    U = nufft.uniform_weights(p.omega, P.K0, P.K1)[0]
+    norm, src = oracle_op_norm(p, P, U)
+    S = oppd.make_setup(p.omega, p.y, p.theta, p.block, p.n_blocks, p.L, eta=1.0 / norm, U=U,
+                        x_true=p.x_true)
+    return p, S, {"op_norm_sq": norm, "eta_source": src, "convergence_lhs": oppd.convergence_lhs(S, 1.0, norm)}
+
+
+def oracle_worker(args):
+    """Run in a fresh single-threaded interpreter: time oracle PPD iterations,
+    args.steps of them after args.warmup, or, with --oracle-seconds, as many
+    as fit in that many seconds (at least 3)."""
+    from oracle import ppd as oppd
+    p, S, info = oracle_setup(args.workload, args.seed)
     st = oppd.init_state(S)
-    times = []
-    for i in range(args.warmup + args.steps):
+    times, snr = [], None
+    budget = args.oracle_seconds
+    i = 0
+    while True:
         t0 = time.perf_counter()
-        oppd.iterate(st, S)
+        h = oppd.iterate(st, S)
         dt = time.perf_counter() - t0
+        if not all(math.isfinite(r) for r in h["residual"]):
+            raise RuntimeError(f"oracle iteration {i + 1} is not finite")
+        snr = h.get("snr")
         if i >= args.warmup:
             times.append(dt)
-    print(json.dumps({"times": times}))
+        i += 1
+        if budget > 0:
+            if len(times) >= 3 and sum(times) >= budget:
+                break
+        elif len(times) >= args.steps:
+            break
+    print(json.dumps({"times": times, "snr_db": snr, **info}))
 
 
-def run_oracle(workload: str, seed: int, steps: int, warmup: int):
+def run_oracle(workload: str, seed: int, steps: int, warmup: int, seconds: float = 0.0):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", "--workload", workload,
-           "--seed", str(seed), "--steps", str(steps), "--warmup", str(warmup)]
+           "--seed", str(seed), "--steps", str(steps), "--warmup", str(warmup),
+           "--oracle-seconds", str(seconds)]
     r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])["times"]
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def workload_config(workload: str) -> dict:
+    """The `config` block of a single-problem workload, from its generator settings."""
+    from paper_1701_01748_gb300 import synth
+    cfg = synth.CONFIGS[workload]
+    return {"workload": workload, "image": f"{cfg['L']}x{cfg['L']}", "visibilities": cfg["M"],
+            "blocks": cfg["n_blocks"], "uv_density": f"gaussian sigma={cfg['uv_sigma']}pi", "isnr_db": 30}
 
 
 def cpu_info():
@@ -436,7 +490,8 @@ def main():
     ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--oracle-worker", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--oracle-steps", type=int, default=3)
+    ap.add_argument("--oracle-seconds", type=float, default=20.0,
+                    help="CPU baseline: oracle iterations until this many seconds (at least 3)")
     ap.add_argument("--snr-iters", type=int, default=0, help="iterations of the SNR comparison (0: per workload)")
     ap.add_argument("--tile", type=int, default=0, help="gridding tile side (0: library default)")
     ap.add_argument("--chunk", type=int, default=0, help="visibilities per work item (0: library default)")
@@ -465,18 +520,24 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        times = run_oracle(args.workload, seed, args.steps, max(args.warmup, 0))
-        v = len(times) / sum(times)
         model, ncpu = cpu_info()
+        if args.workload not in synth.CONFIGS or args.workload in NO_ORACLE:
+            why = NO_ORACLE.get(args.workload, "the oracle runs single-problem workloads only")
+            print(json.dumps({"impl": "reference", "unavailable": why}), flush=True)
+            return
+        r = run_oracle(args.workload, seed, args.steps, max(args.warmup, 0))
+        times = r["times"]
+        v = len(times) / sum(times)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic",
-                "config": {"workload": args.workload, "image": "512x512", "visibilities": 524288,
-                           "blocks": 16, "uv_density": "gaussian sigma=0.1pi", "isnr_db": 30},
+                "data": "synthetic", "config": workload_config(args.workload),
+                "oracle": {"eta_source": r["eta_source"], "op_norm_sq": r["op_norm_sq"],
+                           "convergence_lhs": r["convergence_lhs"], "snr_db_at_end": r["snr_db"]},
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": f"{len(times)} oracle PPD iterations of the workload "
-                                           f"(FP64 NumPy, 1 thread) on {model} ({ncpu} cores)"},
+                                 "sample": f"{len(times)} oracle PPD iterations of the workload after "
+                                           f"{args.warmup} untimed (FP64 NumPy, 1 thread) on {model} "
+                                           f"({ncpu} cores)"},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
@@ -661,8 +722,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "image": f"{p.L}x{p.L}", "visibilities": p.M,
-                   "blocks": p.n_blocks, "uv_density": "gaussian sigma=0.1pi", "isnr_db": 30,
+        "config": {**workload_config(args.workload),
                    "l2": "flushed (256 MiB write) between timed steps", "graph": "one CUDA graph per iteration",
                    "replicas": world,
                    "gridding": {"tile": prm32["tile"], "chunk": prm32["chunk"], "work_items": prm32["n_chunks"],
@@ -673,6 +733,8 @@ def main():
                          "iters_to_target_snr": it_to_target,
                          "seconds_to_target_snr": (wall32 * it_to_target / snr_iters) if it_to_target else None},
         "speedup_iters_per_s": ips32 / ips64,
+        "eta": {name: {k: prm[k] for k in ("op_norm_sq", "power_iters_done", "convergence_lhs")}
+                for name, prm in (("fp32", prm32), ("fp64", s64.params()))},
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": in_bytes / snr_iters,
                 "d2h_bytes_per_step": (out_bytes + stats_bytes) / snr_iters,
                 "what": f"ppd_create + ppd_set_visibilities + ppd_set_weights (eta by power iteration) + "
@@ -688,11 +750,14 @@ def main():
         line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "not run: " + NO_ORACLE[args.workload]}
     elif not args.no_cpu_baseline and world == 1:
-        times = run_oracle(args.workload, seed, args.oracle_steps, 0)
+        r = run_oracle(args.workload, seed, 0, 0, seconds=args.oracle_seconds)
+        times = r["times"]
         model, ncpu = cpu_info()
         line["cpu_baseline"] = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{len(times)} oracle PPD iterations of the same workload "
-                                          f"(FP64 NumPy, 1 thread) on {model} ({ncpu} cores)"}
+                                "sample": f"{len(times)} oracle PPD iterations of the same workload from x = 0 "
+                                          f"(about {args.oracle_seconds:.0f} s; FP64 NumPy, 1 thread) on "
+                                          f"{model} ({ncpu} cores)",
+                                "convergence_lhs": r["convergence_lhs"], "eta_source": r["eta_source"]}
     print(json.dumps(line), flush=True)
     s32.close()
     s64.close()

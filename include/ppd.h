@@ -30,6 +30,10 @@
  *   Calling ppd_set_visibilities or ppd_set_weights again resets the solver
  *   state to x = 0.
  * - A context is not thread-safe; use one context per host thread.
+ * - A context lives on the device that was current at ppd_create.  Every
+ *   entry point makes that device current while it runs and gives the
+ *   caller's current device back on return; *_dev pointers and streams
+ *   must belong to that device.
  */
 #ifndef PPD_H
 #define PPD_H
@@ -303,8 +307,10 @@ PPD_API void ppd_group_destroy(ppd_group *g);
  * The gridding scratch (one (T+8)^2 complex tile per work item, see
  * ppd_params.n_chunks) comes from one fixed device array of
  * PPD_NOALLOC_SCRATCH_BYTES that the library holds on every GPU it is loaded
- * on until the process exits.  The first call on a device looks up that
- * array's device address, so make the first call before any stream capture.
+ * on until the process exits.  The call runs on the context's device (see
+ * the conventions above) and uses that device's copy of the array.  The
+ * first call on a device looks up that array's device address, so make the
+ * first call before any stream capture.
  * All calls share the array: calls that overlap on the GPU race and give
  * wrong results.  No cudaMalloc, cudaFree or other allocating routine is
  * called.  Errors: NOT_READY, INVALID_ARG, UNSUPPORTED (scratch needed above

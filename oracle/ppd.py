@@ -27,6 +27,12 @@ Readings (the paper is silent or its printed step is garbled):
 * Initial state x = xt = 0, u = 0, v = 0.
 * Power iteration for ||U^{1/2} Phi||_S^2 on Phi^dagger U Phi from the
   all-ones vector, stopped at relative change < 1e-10 or 1000 steps.
+* Algorithm 2's "until convergence": optionally stop at the first step t
+  with ||zbar^t - zbar^(t-1)||_2 <= inner_tol ||zbar^t||_2 (FP64, per
+  block), capped at n_itr steps; inner_tol = 0 keeps the fixed n_itr.
+* Algorithm 3's "until convergence": optionally stop once the relative
+  variation ||x^t - x^(t-1)|| / ||x^t|| is below a tolerance and every block
+  residual is within 1.005 eps_j (``converged`` / ``run_until``).
 
 Prior weights W (Algorithm 1) enter the prior step as printed in Algorithm
 3; ``oracle/reweight.py`` sets them.
@@ -76,6 +82,27 @@ def op_norm_sq(P: nufft.Plan, U: np.ndarray, max_iter: int = 1000, tol: float = 
     return val, max_iter
 
 
+def op_norm_sq_lanczos(P: nufft.Plan, U: np.ndarray, tol: float = 1e-8, ncv: int = 12):
+    """||U^{1/2} Phi||_S^2 as the largest eigenvalue of Phi^dagger U Phi by
+    implicitly restarted Lanczos (ARPACK through scipy's eigsh) from the
+    all-ones vector.  The same quantity as op_norm_sq; used where the
+    power iteration converges too slowly for a CPU run (strongly
+    non-uniform coverages, where the two largest eigenvalues are close).
+    Returns (value, operator applications)."""
+    from scipy.sparse.linalg import LinearOperator, eigsh
+    n = P.L0 * P.L1
+    count = [0]
+
+    def matvec(v):
+        count[0] += 1
+        return nufft.phi_adjoint(U * nufft.phi(np.reshape(v, (P.L0, P.L1)), P), P).ravel()
+
+    A = LinearOperator((n, n), matvec=matvec, dtype=np.float64)
+    w = eigsh(A, k=1, which="LA", tol=tol, v0=np.ones(n), ncv=min(ncv, n - 1),
+              return_eigenvectors=False)
+    return float(w[0]), count[0]
+
+
 @dataclasses.dataclass
 class Setup:
     P: nufft.Plan
@@ -96,6 +123,7 @@ class Setup:
     inner_solver: str = "fb"     # "fb": Algorithm 2; "fista": its accelerated form (Section 4.1)
     W: np.ndarray | None = None  # prior weights (9, L0, L1) of Algorithm 1; None = identity
     psiw_sq: float = 1.0         # ||Psi W||_S^2 (1 for W = I)
+    inner_tol: float = 0.0       # Algorithm 2 stop: ||zbar^t - zbar^(t-1)|| <= inner_tol ||zbar^t|| (0: n_itr steps)
 
     def __post_init__(self):
         self.members = [np.flatnonzero(self.block == j) for j in range(self.n_blocks)]
@@ -105,7 +133,8 @@ class Setup:
 def make_setup(omega, y, theta, block, n_blocks, L, *, precond: bool = True,
                eta: float | None = None, eps=None, U=None, n_itr: int = 1,
                tau: float = 0.49, kappa: float = 1e-4, x_true=None,
-               power_iters: int = 1000, inner_init: str = "warm", inner_solver: str = "fb") -> Setup:
+               power_iters: int = 1000, inner_init: str = "warm", inner_solver: str = "fb",
+               inner_tol: float = 0.0) -> Setup:
     P = nufft.Plan(omega, L, L, theta=theta)
     if U is None:
         U = nufft.uniform_weights(omega, P.K0, P.K1)[0] if precond else np.ones(P.M)
@@ -121,7 +150,8 @@ def make_setup(omega, y, theta, block, n_blocks, L, *, precond: bool = True,
         eta = 1.0 / op_norm_sq(P, U, max_iter=power_iters)[0]
     return Setup(P=P, yw=np.asarray(theta) * np.asarray(y), U=U, block=block,
                  n_blocks=n_blocks, eps=eps, mu=mu, eta=float(eta), tau=tau, kappa=kappa,
-                 n_itr=n_itr, x_true=x_true, inner_init=inner_init, inner_solver=inner_solver)
+                 n_itr=n_itr, x_true=x_true, inner_init=inner_init, inner_solver=inner_solver,
+                 inner_tol=float(inner_tol))
 
 
 def convergence_lhs(S: Setup, psi_norm_sq: float | None = None, phi_norm_sq: float | None = None):
@@ -169,6 +199,7 @@ def iterate(st: State, S: Setup, active_blocks=None, active_bases=None) -> dict:
     z = st.v / S.U + phix
     v = st.v.copy()
     p = st.p.copy()
+    inner_steps = np.zeros(S.n_blocks, np.int64)
     for j, m in enumerate(S.members):
         if m.size == 0 or not act_d[j]:
             continue
@@ -179,7 +210,10 @@ def iterate(st: State, S: Setup, active_blocks=None, active_bases=None) -> dict:
         else:
             start = st.p[m]
         solve = prox.ellipsoid_prox_fista if S.inner_solver == "fista" else prox.ellipsoid_prox_fb
-        p[m] = solve(z[m], S.yw[m], S.eps[j], S.U[m], S.n_itr, start=start, mu=S.mu[j])
+        info = {}
+        p[m] = solve(z[m], S.yw[m], S.eps[j], S.U[m], S.n_itr, start=start, mu=S.mu[j], tol=S.inner_tol,
+                     info=info)
+        inner_steps[j] = info["steps"]
         v[m] = S.U[m] * (z[m] - p[m])
     g = nufft.phi_adjoint(v, P)
     # prior step for the bases in P: clip (I - S_{kappa ||Psi W||^2}) of
@@ -201,7 +235,7 @@ def iterate(st: State, S: Setup, active_blocks=None, active_bases=None) -> dict:
     st.x, st.xt, st.u, st.v, st.p = xbar, xt, u, v, p
     st.seen = st.seen | act_d
     st.t += 1
-    stats = dict(residual=res, rel_var=dx / nx if nx > 0 else float("inf"))
+    stats = dict(residual=res, rel_var=dx / nx if nx > 0 else float("inf"), inner_steps=inner_steps)
     if S.x_true is not None:
         stats["snr"] = snr(S.x_true, xbar)
     return stats
@@ -214,6 +248,28 @@ def run(S: Setup, n_iters: int, st: State | None = None):
     for _ in range(n_iters):
         hist.append(iterate(st, S))
     return st, hist
+
+
+def converged(S: Setup, stats: dict, rel_var_tol: float, eps_factor: float = 1.005) -> bool:
+    """Global stopping rule of Algorithm 3 ("until convergence"; reading, the
+    paper gives no test): the relative variation of x is below rel_var_tol and
+    every block residual ||Phi_j xt - y_j|| of the iteration's data step is
+    within eps_factor eps_j."""
+    return stats["rel_var"] < rel_var_tol and bool(np.all(stats["residual"] <= eps_factor * S.eps))
+
+
+def run_until(S: Setup, max_iters: int, rel_var_tol: float, eps_factor: float = 1.005,
+              check_every: int = 1, st: State | None = None):
+    """Algorithm 3 until the global stopping rule holds (tested after every
+    check_every-th iteration) or max_iters iterations.  Returns (state,
+    history, stopped)."""
+    st = init_state(S) if st is None else st
+    hist = []
+    for t in range(1, max_iters + 1):
+        hist.append(iterate(st, S))
+        if t % check_every == 0 and converged(S, hist[-1], rel_var_tol, eps_factor):
+            return st, hist, True
+    return st, hist, False
 
 
 def snr(x_true: np.ndarray, x: np.ndarray) -> float:

@@ -42,21 +42,40 @@ def proj_l2ball(z, y, eps: float):
     return np.array(z, copy=True)
 
 
-def ellipsoid_prox_fb(z, y, eps: float, U, n_itr: int, start=None, mu=None):
-    """Algorithm 2: zbar <- P_B(zbar - mu U (zbar - z)), n_itr times.
+def _inner_converged(cur, prev, tol: float) -> bool:
+    """Algorithm 2's stopping test (the paper says only "until convergence";
+    reading): ||zbar^t - zbar^(t-1)||_2 <= tol ||zbar^t||_2, in FP64."""
+    return float(np.linalg.norm(cur - prev)) <= tol * float(np.linalg.norm(cur))
+
+
+def ellipsoid_prox_fb(z, y, eps: float, U, n_itr: int, start=None, mu=None, tol: float = 0.0,
+                      info: dict | None = None):
+    """Algorithm 2: zbar <- P_B(zbar - mu U (zbar - z)), at most n_itr times.
 
     Computes prox^U_h(z) = argmin_{||p - y|| <= eps} (z-p)^H U (z-p) / 2.
-    start is zbar^(0) (defaults to z); mu defaults to 1/max(U)^2.
+    start is zbar^(0) (defaults to z); mu defaults to 1/max(U)^2.  tol > 0
+    stops after the first step t with ||zbar^t - zbar^(t-1)|| <= tol
+    ||zbar^t||; tol = 0 runs all n_itr steps.  info, if given, receives
+    info["steps"] = the number of steps taken.
     """
     U = np.asarray(U, dtype=np.float64)
     mu = 1.0 / float(np.max(U)) ** 2 if mu is None else mu
     zb = np.array(z if start is None else start, dtype=np.complex128, copy=True)
+    steps = 0
     for _ in range(n_itr):
-        zb = proj_l2ball(zb - mu * U * (zb - z), y, eps)
+        nxt = proj_l2ball(zb - mu * U * (zb - z), y, eps)
+        steps += 1
+        done = tol > 0.0 and _inner_converged(nxt, zb, tol)
+        zb = nxt
+        if done:
+            break
+    if info is not None:
+        info["steps"] = steps
     return zb
 
 
-def ellipsoid_prox_fista(z, y, eps: float, U, n_itr: int, start=None, mu=None):
+def ellipsoid_prox_fista(z, y, eps: float, U, n_itr: int, start=None, mu=None, tol: float = 0.0,
+                         info: dict | None = None):
     """Accelerated Algorithm 2 (Section 4.1 points to faster proximal gradient
     methods, Tseng 2008): the same projected gradient step on
     (zbar - z)^H U (zbar - z) / 2 taken at an extrapolated point,
@@ -64,18 +83,26 @@ def ellipsoid_prox_fista(z, y, eps: float, U, n_itr: int, start=None, mu=None):
         t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2,  t_1 = 1,
         q_{k+1} = zbar_k + ((t_k - 1) / t_{k+1}) (zbar_k - zbar_{k-1}),
     with q_1 = zbar_0 = start (FISTA, Beck & Teboulle 2009).  The first two
-    steps coincide with Algorithm 2 (t_1 = 1 gives no extrapolation).
+    steps coincide with Algorithm 2 (t_1 = 1 gives no extrapolation).  tol
+    and info as in ellipsoid_prox_fb (the test compares zbar_k with zbar_{k-1}).
     """
     U = np.asarray(U, dtype=np.float64)
     mu = 1.0 / float(np.max(U)) ** 2 if mu is None else mu
     prev = np.array(z if start is None else start, dtype=np.complex128, copy=True)
     q = prev.copy()
     t = 1.0
+    steps = 0
     for _ in range(n_itr):
         cur = proj_l2ball(q - mu * U * (q - z), y, eps)
+        steps += 1
+        done = tol > 0.0 and _inner_converged(cur, prev, tol)
         t_next = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
         q = cur + ((t - 1.0) / t_next) * (cur - prev)
         prev, t = cur, t_next
+        if done:
+            break
+    if info is not None:
+        info["steps"] = steps
     return prev
 
 

@@ -7,7 +7,10 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <mutex>
+#include <set>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -21,6 +24,18 @@ void set_last_error(const std::string &msg) { g_last_error = msg; }
 int fail(int code, const std::string &msg) {
     g_last_error = msg;
     return code;
+}
+
+int smem_attr(const void *fn, int bytes) {
+    static std::mutex mu;
+    static std::set<std::tuple<int, const void *, int>> done;
+    int dev = 0;
+    PPD_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count(std::make_tuple(dev, fn, bytes))) return PPD_OK;
+    PPD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done.insert(std::make_tuple(dev, fn, bytes));
+    return PPD_OK;
 }
 
 // ----------------------------------------------------------------- launches and timing
@@ -610,6 +625,7 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
 
 void ppd_destroy(ppd_ctx *c) {
     if (!c) return;
+    DeviceGuard dg_(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     drop_graph(c);
     for (auto &t : c->sites_eager) {
@@ -639,6 +655,7 @@ void ppd_destroy(ppd_ctx *c) {
 
 int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *y, const int32_t *block_id) {
     if (!c || !uv || !y || !block_id) return fail(PPD_ERR_INVALID_ARG, "ppd_set_visibilities: NULL argument");
+    DeviceGuard dg_(c->device);
     if (M < 1 || M >= (int64_t)1 << 31) return fail(PPD_ERR_INVALID_ARG, "ppd_set_visibilities: M out of range");
     for (int64_t i = 0; i < 2 * M; ++i)
         if (!std::isfinite(y[i])) return fail(PPD_ERR_INVALID_ARG, "ppd_set_visibilities: non-finite visibility");
@@ -842,6 +859,7 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
 
 int ppd_set_weights(ppd_ctx *c, const double *theta, const double *U, const double *eps) {
     if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_set_weights: NULL context");
+    DeviceGuard dg_(c->device);
     if (!c->have_vis) return fail(PPD_ERR_NOT_READY, "ppd_set_weights: call ppd_set_visibilities first");
     const int64_t M = c->M;
     if (c->in_theta.data() != theta || !theta) {
@@ -942,6 +960,7 @@ int ppd_set_weights(ppd_ctx *c, const double *theta, const double *U, const doub
 
 int ppd_set_ground_truth(ppd_ctx *c, const double *x_true, int64_t len) {
     if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_set_ground_truth: NULL context");
+    DeviceGuard dg_(c->device);
     if (!x_true) {
         dfree(c->xtrue);
         c->xtrue = nullptr;
@@ -963,6 +982,7 @@ int ppd_set_ground_truth(ppd_ctx *c, const double *x_true, int64_t len) {
 
 int ppd_iterate(ppd_ctx *c, int32_t n_iters, ppd_stats *stats) {
     if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_iterate: NULL context");
+    DeviceGuard dg_(c->device);
     if (!c->have_weights) return fail(PPD_ERR_NOT_READY, "ppd_iterate: call ppd_set_weights first");
     if (n_iters < 0) return fail(PPD_ERR_INVALID_ARG, "ppd_iterate: n_iters < 0");
     int st = c->is_f32 ? run_iterations<float>(c, n_iters) : run_iterations<double>(c, n_iters);
@@ -1000,6 +1020,7 @@ int ppd_iterate(ppd_ctx *c, int32_t n_iters, ppd_stats *stats) {
 
 int ppd_get_image(ppd_ctx *c, double *x_out, int64_t len) {
     if (!c || !x_out) return fail(PPD_ERR_INVALID_ARG, "ppd_get_image: NULL argument");
+    DeviceGuard dg_(c->device);
     if (len != c->N) return fail(PPD_ERR_INVALID_ARG, "ppd_get_image: len must be n0*n1");
     if (c->is_f32) {
         std::vector<float> t(c->N);
@@ -1049,6 +1070,7 @@ int ppd_get_bins(ppd_ctx *c, int64_t *perm, int32_t *base0, int32_t *base1, int3
 
 int ppd_op_forward(ppd_ctx *c, const void *x_dev, void *y_dev, void *stream) {
     if (!c || !x_dev || !y_dev) return fail(PPD_ERR_INVALID_ARG, "ppd_op_forward: NULL argument");
+    DeviceGuard dg_(c->device);
     if (!c->have_weights) return fail(PPD_ERR_NOT_READY, "ppd_op_forward: call ppd_set_weights first");
     cudaStream_t s = pick(c, stream);
     if (c->is_f32) {
@@ -1061,6 +1083,7 @@ int ppd_op_forward(ppd_ctx *c, const void *x_dev, void *y_dev, void *stream) {
 
 int ppd_op_adjoint(ppd_ctx *c, const void *y_dev, void *x_dev, void *stream) {
     if (!c || !x_dev || !y_dev) return fail(PPD_ERR_INVALID_ARG, "ppd_op_adjoint: NULL argument");
+    DeviceGuard dg_(c->device);
     if (!c->have_weights) return fail(PPD_ERR_NOT_READY, "ppd_op_adjoint: call ppd_set_weights first");
     cudaStream_t s = pick(c, stream);
     c->gpart_stale = true;   // the partial tiles now hold this call's data
@@ -1076,6 +1099,7 @@ int ppd_op_adjoint(ppd_ctx *c, const void *y_dev, void *x_dev, void *stream) {
 
 int ppd_psi_analysis(ppd_ctx *c, const void *x_dev, void *c_dev, void *stream) {
     if (!c || !x_dev || !c_dev) return fail(PPD_ERR_INVALID_ARG, "ppd_psi_analysis: NULL argument");
+    DeviceGuard dg_(c->device);
     cudaStream_t s = pick(c, stream);
     if (c->is_f32) return psi_analysis<float>(c, static_cast<const float *>(x_dev), static_cast<float *>(c_dev), s);
     return psi_analysis<double>(c, static_cast<const double *>(x_dev), static_cast<double *>(c_dev), s);
@@ -1083,6 +1107,7 @@ int ppd_psi_analysis(ppd_ctx *c, const void *x_dev, void *c_dev, void *stream) {
 
 int ppd_psi_synthesis(ppd_ctx *c, const void *c_dev, void *x_dev, void *stream) {
     if (!c || !x_dev || !c_dev) return fail(PPD_ERR_INVALID_ARG, "ppd_psi_synthesis: NULL argument");
+    DeviceGuard dg_(c->device);
     cudaStream_t s = pick(c, stream);
     if (c->is_f32) return psi_synthesis<float>(c, static_cast<const float *>(c_dev), static_cast<float *>(x_dev), s);
     return psi_synthesis<double>(c, static_cast<const double *>(c_dev), static_cast<double *>(x_dev), s);
@@ -1090,6 +1115,7 @@ int ppd_psi_synthesis(ppd_ctx *c, const void *c_dev, void *x_dev, void *stream) 
 
 int ppd_set_prior_weights(ppd_ctx *c, const double *w, int64_t len) {
     if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_set_prior_weights: NULL context");
+    DeviceGuard dg_(c->device);
     if (!w) {
         PPD_CUDA(cudaStreamSynchronize(c->stream));
         dfree(c->wgt);
@@ -1115,6 +1141,7 @@ int ppd_set_prior_weights(ppd_ctx *c, const double *w, int64_t len) {
 
 int ppd_reweight(ppd_ctx *c, double omega) {
     if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_reweight: NULL context");
+    DeviceGuard dg_(c->device);
     if (!(omega > 0) || !std::isfinite(omega)) return fail(PPD_ERR_INVALID_ARG, "ppd_reweight: omega must be > 0");
     PPD_CHECK(ensure_weight_buffers(c));
     cudaStream_t s = c->stream;
@@ -1130,6 +1157,7 @@ int ppd_reweight(ppd_ctx *c, double omega) {
 
 int ppd_set_active_sets(ppd_ctx *c, int32_t n_iters, const uint8_t *blocks, const uint8_t *bases) {
     if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_set_active_sets: NULL context");
+    DeviceGuard dg_(c->device);
     if (n_iters < 0) return fail(PPD_ERR_INVALID_ARG, "ppd_set_active_sets: n_iters < 0");
     PPD_CUDA(cudaStreamSynchronize(c->stream));
     dfree(c->mask_all);
@@ -1163,6 +1191,7 @@ int ppd_set_active_sets(ppd_ctx *c, int32_t n_iters, const uint8_t *blocks, cons
 
 int ppd_get_prior_weights(ppd_ctx *c, double *w, int64_t len) {
     if (!c || !w) return fail(PPD_ERR_INVALID_ARG, "ppd_get_prior_weights: NULL argument");
+    DeviceGuard dg_(c->device);
     if (len != (int64_t)N_BASES * c->N) return fail(PPD_ERR_INVALID_ARG, "ppd_get_prior_weights: len != 9 n0 n1");
     if (!c->wgt) {
         std::fill(w, w + len, 1.0);
@@ -1181,6 +1210,7 @@ int ppd_get_prior_weights(ppd_ctx *c, double *w, int64_t len) {
 
 int ppd_autotune(ppd_ctx *c, int32_t iters, int32_t *tile_out, int32_t *chunk_out) {
     if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_autotune: NULL context");
+    DeviceGuard dg_(c->device);
     if (!c->have_weights) return fail(PPD_ERR_NOT_READY, "ppd_autotune: call ppd_set_weights first");
     if (iters < 1) return fail(PPD_ERR_INVALID_ARG, "ppd_autotune: iters < 1");
     const double eta_cfg = c->cfg.eta;
@@ -1246,6 +1276,7 @@ struct ppd_group {
 
 void ppd_group_destroy(ppd_group *g) {
     if (!g) return;
+    DeviceGuard dg_(g->ctxs.empty() ? 0 : g->ctxs[0]->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
@@ -1263,7 +1294,10 @@ int ppd_group_create(ppd_group **out, ppd_ctx *const *ctxs, int32_t n) {
         if (!ctxs[i]->is_f32) return fail(PPD_ERR_INVALID_ARG, "ppd_group_create: groups hold FP32 contexts");
         if (ctxs[i]->timing) return fail(PPD_ERR_INVALID_ARG, "ppd_group_create: per-kernel timing must be off");
         if (!ctxs[i]->have_weights) return fail(PPD_ERR_NOT_READY, "ppd_group_create: context without weights");
+        if (ctxs[i]->device != ctxs[0]->device)
+            return fail(PPD_ERR_INVALID_ARG, "ppd_group_create: contexts on different devices");
     }
+    DeviceGuard dg_(ctxs[0]->device);
     ppd_group *g = new (std::nothrow) ppd_group();
     if (!g) return fail(PPD_ERR_OOM, "ppd_group_create: host allocation");
     g->ctxs.assign(ctxs, ctxs + n);
@@ -1283,6 +1317,7 @@ int ppd_group_create(ppd_group **out, ppd_ctx *const *ctxs, int32_t n) {
 int ppd_group_iterate(ppd_group *g, int32_t n_iters) {
     if (!g) return fail(PPD_ERR_INVALID_ARG, "ppd_group_iterate: NULL group");
     if (n_iters < 0) return fail(PPD_ERR_INVALID_ARG, "ppd_group_iterate: n_iters < 0");
+    DeviceGuard dg_(g->ctxs[0]->device);
     if (n_iters == 0) return PPD_OK;
     // a context's first iteration (Algorithm 2 starts from P_B(z)) differs
     // from the captured one: if any context needs it, every context runs one
@@ -1394,6 +1429,7 @@ int64_t state_bytes(const ppd_ctx *c) {
 
 int ppd_get_state(ppd_ctx *c, void *blob, int64_t *bytes) {
     if (!c || !bytes) return fail(PPD_ERR_INVALID_ARG, "ppd_get_state: NULL argument");
+    DeviceGuard dg_(c->device);
     if (!c->have_weights) return fail(PPD_ERR_NOT_READY, "ppd_get_state: call ppd_set_weights first");
     const int64_t need = state_bytes(c);
     if (!blob) {
@@ -1435,6 +1471,7 @@ int ppd_get_state(ppd_ctx *c, void *blob, int64_t *bytes) {
 
 int ppd_set_state(ppd_ctx *c, const void *blob, int64_t bytes) {
     if (!c || !blob) return fail(PPD_ERR_INVALID_ARG, "ppd_set_state: NULL argument");
+    DeviceGuard dg_(c->device);
     if (!c->have_weights) return fail(PPD_ERR_NOT_READY, "ppd_set_state: call ppd_set_weights first");
     if (bytes != state_bytes(c)) return fail(PPD_ERR_INVALID_ARG, "ppd_set_state: size mismatch");
     StateHeader h;
@@ -1478,6 +1515,7 @@ int ppd_timing_enable(ppd_ctx *c, int32_t enable) {
 
 int ppd_timing_collect(ppd_ctx *c) {
     if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_timing_collect: NULL context");
+    DeviceGuard dg_(c->device);
     PPD_CUDA(cudaStreamSynchronize(c->stream));
     for (auto &t : c->sites_eager) {
         float ms = 0;

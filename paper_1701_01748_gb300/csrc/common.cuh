@@ -69,6 +69,23 @@ int fail(int code, const std::string &msg);
                                std::string(#call) + ": " + cudaGetErrorString(e_));     \
     } while (0)
 
+// Makes a context's device current for the duration of an entry point and
+// gives the caller's current device back on return.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess || prev == dev || cudaSetDevice(dev) != cudaSuccess) prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// Lets kernel `fn` launch with `bytes` of dynamic shared memory on the
+// current device (the attribute is per device: it is set once for every
+// device, kernel and size seen).
+int smem_attr(const void *fn, int bytes);
+
 #define PPD_CHECK(call)                 \
     do {                                \
         int s_ = (call);                \

@@ -360,20 +360,16 @@ __global__ void __launch_bounds__(NT) k_rows_primal(const cplx_t<R> *__restrict_
 
 template <typename R, int K> struct Pass {
     static constexpr int B = rows_per_cta<R>(K), W = cols_per_cta<R>(K);
-    // dynamic shared memory of the row and column passes, set once per instantiation
+    // dynamic shared memory of the row and column passes (per device)
     static int attrs() {
-        static bool done = false;
-        if (done) return PPD_OK;
         const int shr = (int)pass_smem<R>(B, K), shc = (int)pass_smem<R>(W, K);
-        PPD_CUDA(cudaFuncSetAttribute(k_rows_fwd<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, shr));
-        PPD_CUDA(cudaFuncSetAttribute(k_rows_inv<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, shr));
-        PPD_CUDA(cudaFuncSetAttribute(k_rows_primal<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, shr));
-        PPD_CUDA(cudaFuncSetAttribute(k_cols_fwd<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, shc));
-        PPD_CUDA(cudaFuncSetAttribute(k_cols_inv<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, shc));
-        PPD_CUDA(cudaFuncSetAttribute(k_cols_inv_part<R, K, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, shc));
-        PPD_CUDA(cudaFuncSetAttribute(k_cols_inv_part<R, K, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, shc));
-        done = true;
-        return PPD_OK;
+        PPD_CHECK(smem_attr((const void *)k_rows_fwd<R, K>, shr));
+        PPD_CHECK(smem_attr((const void *)k_rows_inv<R, K>, shr));
+        PPD_CHECK(smem_attr((const void *)k_rows_primal<R, K>, shr));
+        PPD_CHECK(smem_attr((const void *)k_cols_fwd<R, K>, shc));
+        PPD_CHECK(smem_attr((const void *)k_cols_inv<R, K>, shc));
+        PPD_CHECK(smem_attr((const void *)k_cols_inv_part<R, K, 16>, shc));
+        return smem_attr((const void *)k_cols_inv_part<R, K, 32>, shc);
     }
     static int rows_fwd(ppd_ctx *c, const R *x, cudaStream_t s) {
         PPD_CHECK(attrs());

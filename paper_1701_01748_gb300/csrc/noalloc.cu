@@ -12,7 +12,9 @@
 // library holds its PPD_NOALLOC_SCRATCH_BYTES until the process exits.  In
 // host code its name is only a host-side stand-in, never a device address:
 // the device address is obtained once per device with cudaGetSymbolAddress
-// (with that device current) on the first call made on that device.
+// (with that device current) on the first call made on that device.  The
+// call runs on the device the context was created on, whichever device the
+// caller has current.
 // Every call shares the array and it keeps the last call's contents; the
 // kernel writes every partial tile it later reads, so nothing needs clearing.
 // Calls that overlap on the GPU (other streams, other contexts on the same
@@ -30,10 +32,9 @@ constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 void *g_scratch_dev[MAX_DEVICES] = {};
 
-// Device address of g_grid_scratch on the current device (set-up on first use).
-int scratch_address(void **out) {
-    int dev = 0;
-    PPD_CUDA(cudaGetDevice(&dev));
+// Device address of g_grid_scratch on device `dev`, which must be current
+// (set-up on the first call made on that device).
+int scratch_address(int dev, void **out) {
     if (dev < 0 || dev >= MAX_DEVICES) return fail(PPD_ERR_UNSUPPORTED, "ppd_op_adjoint_noalloc: device index");
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch_dev[dev]) {
@@ -63,8 +64,11 @@ extern "C" int ppd_op_adjoint_noalloc(ppd_ctx *c, const void *y_dev, void *x_dev
                     "ppd_op_adjoint_noalloc: problem needs " + std::to_string(need) +
                         " bytes of gridding scratch, above the fixed " +
                         std::to_string((size_t)PPD_NOALLOC_SCRATCH_BYTES) + " bytes");
+    // the context's device is current for the call, so the scratch address
+    // and the kernels below belong to the GPU that holds the context's memory
+    DeviceGuard dg_(c->device);
     void *scratch = nullptr;
-    PPD_CHECK(scratch_address(&scratch));
+    PPD_CHECK(scratch_address(c->device, &scratch));
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : c->stream;
     if (c->is_f32) {
         PPD_CHECK(grid_vis_into<float>(c, GR_OP, static_cast<const float2 *>(y_dev), c->perm,

@@ -676,20 +676,14 @@ int degrid_t(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const 
     constexpr int E = T + HALO;
     const size_t tile_stride = ((size_t)E * E * sizeof(cplx_t<R>) + 127) / 128 * 128;
     const size_t sh = 2 * tile_stride + (KB_DEG + 1) * KB_J * sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-        PPD_CUDA(cudaFuncSetAttribute(k_degrid<R, T, DG_OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-        PPD_CUDA(cudaFuncSetAttribute(k_degrid<R, T, DG_DUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-        PPD_CUDA(cudaFuncSetAttribute(k_degrid<R, T, DG_FIRST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-        attr = true;
-    }
+    PPD_CHECK(smem_attr((const void *)k_degrid<R, T, DG_OP>, (int)sh));
+    PPD_CHECK(smem_attr((const void *)k_degrid<R, T, DG_DUAL>, (int)sh));
+    PPD_CHECK(smem_attr((const void *)k_degrid<R, T, DG_FIRST>, (int)sh));
     const int use_tma = (c->tma_ok && grid == c->grid_a) ? 1 : 0;
     if (c->ch.n == 0) return PPD_OK;
-    static int per_sm = 0;
-    if (!per_sm) {
-        PPD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_degrid<R, T, DG_DUAL>, DG_NT, sh));
-        if (per_sm < 1) per_sm = 1;
-    }
+    int per_sm = 0;
+    PPD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_degrid<R, T, DG_DUAL>, DG_NT, sh));
+    if (per_sm < 1) per_sm = 1;
     int sms = 0;
     PPD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     const int nch = (int)c->ch.n;
@@ -709,13 +703,9 @@ int grid_t(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_
     A.op_in = in;
     A.perm = perm;
     const size_t sh = grid_smem<R, T>();
-    static bool attr = false;
-    if (!attr) {
-        PPD_CUDA(cudaFuncSetAttribute(k_grid<R, T, GR_OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-        PPD_CUDA(cudaFuncSetAttribute(k_grid<R, T, GR_OP_U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-        PPD_CUDA(cudaFuncSetAttribute(k_grid<R, T, GR_DUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-        attr = true;
-    }
+    PPD_CHECK(smem_attr((const void *)k_grid<R, T, GR_OP>, (int)sh));
+    PPD_CHECK(smem_attr((const void *)k_grid<R, T, GR_OP_U>, (int)sh));
+    PPD_CHECK(smem_attr((const void *)k_grid<R, T, GR_DUAL>, (int)sh));
     constexpr int NT = GridCfg<R>::NWARP * 32;
     cplx_t<R> *gp = static_cast<cplx_t<R> *>(c->gpart);
     int site;

@@ -63,4 +63,39 @@ def test_reference_arm_prints_the_contract_line():
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
     assert line["config"]["workload"] == bench.WORKLOAD
+    assert line["config"] == bench.workload_config(bench.WORKLOAD)
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+    # the oracle runs Algorithm 3 with the paper's eta (stored, not recomputed) and converges
+    assert line["oracle"]["eta_source"].startswith("tests/golden/op_norms.json")
+    assert line["oracle"]["convergence_lhs"] < 1.0
+
+
+def test_oracle_setup_meets_the_convergence_condition_and_stays_finite():
+    """The set-up the benchmark's oracle arm builds: eta = 1/||U^{1/2} Phi||^2 with
+    the norm from the oracle's Lanczos routine, so tau eta ||U^{1/2} Phi||^2 +
+    tau zeta ||Psi||^2 < 1 (Eq. "convergence-req-explicit-pd"), and the driver's
+    steps + warm-up iterations (25) run without overflow."""
+    import math
+    from oracle import ppd as oppd
+    p, S, info = bench.oracle_setup("c1_128", 1701)
+    assert info["convergence_lhs"] < 1.0
+    # the power iteration approaches the norm from below (a Rayleigh quotient)
+    lo, _ = oppd.op_norm_sq(S.P, S.U, max_iter=30)
+    assert lo <= info["op_norm_sq"] * (1 + 1e-9)
+    st = oppd.init_state(S)
+    for _ in range(25):
+        h = oppd.iterate(st, S)
+    assert all(math.isfinite(r) for r in h["residual"]) and math.isfinite(h["snr"]) and h["snr"] > 0
+
+
+def test_stored_operator_norms_belong_to_the_benchmark_workloads():
+    """tests/golden/op_norms.json was written for the workloads' current seeds and sizes."""
+    import json
+    from paper_1701_01748_gb300 import synth
+    table = json.load(open(bench.GOLDEN_NORMS))
+    for name in ("c2_512", "c3_1024"):
+        cfg = synth.CONFIGS[name]
+        rec = table[name]
+        assert (rec["seed"], rec["L"], rec["M"], rec["n_blocks"]) == (cfg["seed"], cfg["L"], cfg["M"],
+                                                                     cfg["n_blocks"])
+        assert rec["op_norm_sq"] > 0

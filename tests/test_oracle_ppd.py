@@ -42,6 +42,8 @@ def test_power_iteration_matches_dense_spectral_norm():
     dense = np.linalg.norm(A, 2) ** 2
     got, it = ppd.op_norm_sq(P, U, max_iter=5000, tol=1e-13)
     assert abs(got - dense) <= 1e-8 * dense
+    lz, _ = ppd.op_norm_sq_lanczos(P, U, tol=1e-12)
+    assert abs(lz - dense) <= 1e-9 * dense
 
 
 def test_dual_step_is_the_conjugate_prox_in_metric_U_inverse():
@@ -144,3 +146,45 @@ def test_accelerated_inner_solver_in_the_iteration():
             runs[(solver, n_itr)] = st.x
     assert np.array_equal(runs[("fb", 2)], runs[("fista", 2)])
     assert np.abs(runs[("fb", 400)] - runs[("fista", 400)]).max() <= 1e-8 * np.abs(runs[("fb", 400)]).max()
+
+
+def test_inner_stopping_test_in_the_iteration():
+    """Algorithm 2 stopped by its test inside PPD: per-block step counts lie in
+    [1, n_itr]; with a tight test and a high cap each block's prox is the exact
+    one (so the iterates equal those of a run to convergence), and a looser test
+    takes fewer steps."""
+    p = _tiny(seed=10, M=300, n_blocks=3)
+    kw = dict(power_iters=200, n_itr=20000)
+    S_exact = ppd.make_setup(p.omega, p.y, p.theta, p.block, p.n_blocks, p.L, **kw)
+    S_tol = ppd.make_setup(p.omega, p.y, p.theta, p.block, p.n_blocks, p.L, inner_tol=1e-11, **kw)
+    S_loose = ppd.make_setup(p.omega, p.y, p.theta, p.block, p.n_blocks, p.L, inner_tol=1e-3, **kw)
+    st_e, st_t, st_l = ppd.init_state(S_exact), ppd.init_state(S_tol), ppd.init_state(S_loose)
+    for _ in range(3):
+        he = ppd.iterate(st_e, S_exact)
+        ht = ppd.iterate(st_t, S_tol)
+        hl = ppd.iterate(st_l, S_loose)
+        assert np.all(he["inner_steps"] == 20000)
+        assert np.all((ht["inner_steps"] >= 1) & (ht["inner_steps"] < 20000))
+        assert np.all(hl["inner_steps"] <= ht["inner_steps"])
+    assert np.abs(st_t.x - st_e.x).max() <= 1e-7 * np.abs(st_e.x).max()
+
+
+def test_global_stopping_rule_stops_near_the_minimiser():
+    """Algorithm 3 stopped by the rule (relative variation below tol, every block
+    residual within 1.005 eps_j): the rule holds where it stopped, a looser
+    tolerance stops no later, and the stopped image is close to the minimiser of
+    a long run."""
+    p = _tiny()
+    S = ppd.make_setup(p.omega, p.y, p.theta, p.block, p.n_blocks, p.L, x_true=p.x_true, power_iters=300)
+    x_min, _ = ppd.run(S, 1500)
+    stops = []
+    for tol in (1e-2, 1e-3, 1e-4):
+        st, hist, stopped = ppd.run_until(S, 1500, tol)
+        assert stopped
+        assert hist[-1]["rel_var"] < tol and np.all(hist[-1]["residual"] <= 1.005 * S.eps)
+        stops.append(len(hist))
+    assert stops == sorted(stops) and stops[0] < stops[-1]
+    assert np.linalg.norm(st.x - x_min.x) <= 5e-2 * np.linalg.norm(x_min.x)
+    # checked every 5th iteration only: stops at a multiple of 5, no earlier than every-iteration checks
+    _, hist5, stopped5 = ppd.run_until(S, 1500, 1e-3, check_every=5)
+    assert stopped5 and len(hist5) % 5 == 0 and len(hist5) >= stops[1]

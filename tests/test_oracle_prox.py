@@ -133,3 +133,49 @@ def test_fista_is_faster_when_the_constraint_is_weakly_active(seed):
     e_fb = err(prox.ellipsoid_prox_fb(z, y, eps, U, n_itr=100))
     e_fa = err(prox.ellipsoid_prox_fista(z, y, eps, U, n_itr=100))
     assert e_fa <= 0.2 * e_fb, (e_fa, e_fb)
+
+
+# ----------------------------------------------------------------- Algorithm 2 stopping test
+def test_stopping_test_with_identity_metric_stops_at_the_second_step():
+    """U = I, mu = 1: every step lands on P_B(z) (the textbook l2-ball projection),
+    so zbar^2 = zbar^1 and the test ||zbar^t - zbar^(t-1)|| <= tol ||zbar^t|| first
+    holds at t = 2 from any other start, at t = 1 from P_B(z) itself."""
+    z, y, _ = _block(8, m=16)
+    U = np.ones(16)
+    ball = prox.proj_l2ball(z, y, 1.0)
+    for solve in (prox.ellipsoid_prox_fb, prox.ellipsoid_prox_fista):
+        info = {}
+        p = solve(z, y, 1.0, U, n_itr=50, start=y + 100.0, tol=1e-12, info=info)
+        assert info["steps"] == 2 and np.allclose(p, ball, rtol=0, atol=1e-14)
+        info = {}
+        solve(z, y, 1.0, U, n_itr=50, start=ball, tol=1e-12, info=info)
+        assert info["steps"] == 1
+        info = {}
+        solve(z, y, 1.0, U, n_itr=7, start=y + 100.0, tol=0.0, info=info)
+        assert info["steps"] == 7          # tol = 0: the fixed number of steps
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13])
+def test_stopping_test_bounds_the_distance_to_the_exact_prox(seed):
+    """With max U = 1 and mu = 1 the step zbar -> P_B(zbar - U (zbar - z)) is a
+    contraction of factor q = 1 - min U (P_B is non-expansive), so at the stop
+    ||zbar^t - p*|| <= q/(1-q) ||zbar^t - zbar^(t-1)|| <= q/(1-q) tol ||zbar^t||
+    (the a-posteriori bound of Banach's fixed-point theorem), p* the exact prox."""
+    rng = np.random.default_rng(seed)
+    m = 48
+    y = rng.normal(size=m) + 1j * rng.normal(size=m)
+    z = y + 6.0 * (rng.normal(size=m) + 1j * rng.normal(size=m)) / np.sqrt(m)
+    U = rng.uniform(0.2, 1.0, size=m)
+    U[0] = 1.0
+    q = 1.0 - U.min()
+    p_exact, lam = prox.ellipsoid_prox_exact(z, y, 2.0, U)
+    assert lam > 0
+    steps = []
+    for tol in (1e-3, 1e-5, 1e-7, 1e-9):
+        info = {}
+        p = prox.ellipsoid_prox_fb(z, y, 2.0, U, n_itr=100000, start=y, tol=tol, info=info)
+        bound = q / (1.0 - q) * tol * np.linalg.norm(p)
+        assert np.linalg.norm(p - p_exact) <= bound * (1 + 1e-6) + 1e-13 * np.linalg.norm(p)
+        assert info["steps"] < 100000
+        steps.append(info["steps"])
+    assert steps == sorted(steps) and steps[0] < steps[-1]   # tighter tolerance, more steps
