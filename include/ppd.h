@@ -68,6 +68,10 @@ extern "C" {
 #define PPD_INNER_WARM          0   /* previous iteration's prox output (P_B(z) on the first iteration) */
 #define PPD_INNER_CURRENT       1   /* zbar^(0) = z */
 
+/* estimate of ||U^{1/2} Phi||_S^2 for eta (config.norm_method) */
+#define PPD_NORM_LANCZOS        0   /* largest eigenvalue of Phi^dagger U Phi by the Lanczos process */
+#define PPD_NORM_POWER          1   /* power iteration on Phi^dagger U Phi */
+
 /* Algorithm 2 iteration (config.inner_solver) */
 #define PPD_INNER_FB            0   /* Algorithm 2 as printed: zbar <- P_B(zbar - mu U (zbar - z)) */
 #define PPD_INNER_FISTA         1   /* the same step at an extrapolated point, FISTA t-sequence
@@ -90,7 +94,7 @@ typedef struct {
     double   tau;               /* primal step (0.49) */
     double   lambda;            /* relaxation; must be 1 */
     double   kappa;             /* normalised soft-threshold (1e-4) */
-    double   eta;               /* 0 => 1/||U^{1/2} Phi||_S^2 by power iteration */
+    double   eta;               /* 0 => 1/||U^{1/2} Phi||_S^2 (norm_method) */
     double   zeta;              /* 0 => 1/||Psi||_S^2 = 1 */
     int32_t  precision;         /* PPD_FP64_PLAIN or PPD_FP32_FP64NORMS */
     int32_t  precond;           /* 1: PPD with U = inverse sampling density; 0: U = I (PD) */
@@ -98,10 +102,29 @@ typedef struct {
     int32_t  use_graph;         /* 1: replay each iteration from a captured CUDA graph */
     int32_t  tile;              /* gridding tile side T (16 or 32); 0 => 16 */
     int32_t  chunk;             /* max visibilities per gridding work item; 0 => 1024 */
-    int32_t  power_iters;       /* power-iteration cap for eta; 0 => 1000 */
-    double   power_tol;         /* power-iteration relative stop; 0 => 1e-10 */
+    int32_t  power_iters;       /* cap on the operator applications of the norm estimate; 0 => 1000 */
+    double   power_tol;         /* relative change of the estimate that stops it; 0 => 1e-10
+                                   (Lanczos in FP32: at least 2e-6) */
     void    *stream;            /* cudaStream_t for all work; NULL => library-created stream */
     int32_t  inner_solver;      /* PPD_INNER_FB (default) or PPD_INNER_FISTA */
+    /* Stopping tests ("until convergence" in Algorithms 2 and 3; the paper
+     * gives no test, these are the library's readings, evaluated in FP64 on
+     * the device in both precisions): */
+    double   inner_tol;         /* Algorithm 2: a block stops at the first step t with
+                                   ||zbar^t - zbar^(t-1)|| <= inner_tol ||zbar^t||, at most
+                                   n_itr steps; 0 => always n_itr steps */
+    double   stop_tol;          /* Algorithm 3: ppd_iterate returns early once the relative
+                                   variation of x is < stop_tol and every block residual
+                                   ||Phi_j xt - y_j|| <= stop_eps_factor eps_j; 0 => off */
+    double   stop_eps_factor;   /* 0 => 1.005 */
+    int32_t  stop_every;        /* test the rule after every stop_every-th iteration of a
+                                   ppd_iterate call (one host synchronisation each); 0 => 1 */
+    int32_t  pad0;
+    uint64_t seed;              /* start vector of the norm estimate: 0 => all ones; otherwise
+                                   x_i = 0.5 + 2^-53 (s_i >> 11), s_i the SplitMix64 output
+                                   for counter seed + (i + 1) * 0x9E3779B97F4A7C15 */
+    int32_t  norm_method;       /* PPD_NORM_LANCZOS (default) or PPD_NORM_POWER */
+    int32_t  pad1;
 } ppd_config;
 
 /* Per-call statistics (ppd_iterate).  All norms are computed in double. */
@@ -112,6 +135,10 @@ typedef struct {
     double   snr_db;            /* 20 log10(||x0|| / ||x0 - x||) if ppd_set_ground_truth was called, else NaN */
     double   max_res_over_eps;  /* max_j ||Phi_j xt - y_j|| / eps_j at the last iteration's data step */
     double  *block_residual;    /* optional caller buffer of n_blocks doubles: ||Phi_j xt - y_j|| (whitened) */
+    int32_t *inner_steps;       /* optional caller buffer of n_blocks int32: Algorithm 2 steps each
+                                   block took in the last iteration (0: outside the active set) */
+    int32_t  stopped;           /* 1 if the stop_tol rule ended the call before n_iters */
+    int32_t  iters_run;         /* iterations this call ran */
 } ppd_stats;
 
 /* Parameters resolved by ppd_set_weights (and ppd_set_prior_weights /
@@ -120,7 +147,7 @@ typedef struct {
 typedef struct {
     double   eta, zeta, tau, kappa;
     double   op_norm_sq;        /* ||U^{1/2} Phi||_S^2 (0 if eta was given) */
-    int32_t  power_iters_done;
+    int32_t  power_iters_done;  /* operator applications of the norm estimate */
     int32_t  K0, K1;            /* oversampled grid */
     int32_t  tile;              /* gridding tile side */
     int32_t  chunk;             /* max visibilities per work item */
@@ -166,7 +193,7 @@ PPD_API int ppd_set_visibilities(ppd_ctx *ctx, int64_t M, const double *uv, cons
  *   eps    n_blocks doubles > 0, l2 bounds on the whitened residual of each
  *          block (NULL => sqrt(M_j + 2 sqrt(M_j)), two chi^2 standard
  *          deviations above its mean); ignored for blocks with no visibility
- * Then resolves eta (power iteration when config.eta = 0), mu_j =
+ * Then resolves eta (config.norm_method when config.eta = 0), mu_j =
  * 1/max(U_j)^2 (Algorithm 2) and resets the state to zero.
  * Errors: NOT_READY, INVALID_ARG, NONFINITE, OOM, CUDA. */
 PPD_API int ppd_set_weights(ppd_ctx *ctx, const double *theta, const double *U, const double *eps);
@@ -177,7 +204,10 @@ PPD_API int ppd_set_ground_truth(ppd_ctx *ctx, const double *x_true, int64_t len
 
 /* Run n_iters iterations of Algorithm 3 (lambda = 1, all blocks and bases
  * every iteration).  Work is enqueued on the context stream; if stats is
- * non-NULL the call synchronises and fills it.  n_iters >= 0.
+ * non-NULL the call synchronises and fills it.  n_iters >= 0.  With
+ * config.stop_tol > 0 the call tests the global stopping rule (see
+ * ppd_config) after every stop_every-th iteration, synchronising each time,
+ * and returns as soon as it holds (stats->stopped = 1).
  * Errors: NOT_READY, INVALID_ARG, NONFINITE, TIMEOUT, CUDA. */
 PPD_API int ppd_iterate(ppd_ctx *ctx, int32_t n_iters, ppd_stats *stats);
 
@@ -338,6 +368,19 @@ PPD_API int ppd_timing_enable(ppd_ctx *ctx, int32_t enable);
 PPD_API int ppd_timing_collect(ppd_ctx *ctx);
 PPD_API int ppd_timing_read(ppd_ctx *ctx, int32_t n, const char **names, double *ms, int64_t *launches,
                     int32_t *n_out);
+
+/* Failure detection of the bounded device waits.  The degridding kernel waits
+ * on an mbarrier for each TMA tile copy; the wait gives up after `polls`
+ * polls (default PPD_WAIT_LIMIT_DEFAULT), sets the context's device error
+ * word and, with the copies it started waited for under the default bound,
+ * leaves the kernel; the next synchronising call (ppd_iterate with stats,
+ * ppd_set_weights) returns PPD_ERR_TIMEOUT and clears the word, and the
+ * context stays usable.  Setting a smaller limit (0: give up at once) makes
+ * the first wait of every tile run out, which tests that path without any
+ * fault; the results of the launches it affects are not defined.  Synchronises.
+ * Errors: INVALID_ARG (NULL, polls < 0), CUDA. */
+#define PPD_WAIT_LIMIT_DEFAULT (1ll << 21)
+PPD_API int ppd_set_wait_limit(ppd_ctx *ctx, int64_t polls);
 
 /* Kernel launches enqueued by this context since creation (all entry points). */
 PPD_API int64_t ppd_launch_count(ppd_ctx *ctx);

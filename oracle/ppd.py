@@ -134,8 +134,9 @@ def make_setup(omega, y, theta, block, n_blocks, L, *, precond: bool = True,
                eta: float | None = None, eps=None, U=None, n_itr: int = 1,
                tau: float = 0.49, kappa: float = 1e-4, x_true=None,
                power_iters: int = 1000, inner_init: str = "warm", inner_solver: str = "fb",
-               inner_tol: float = 0.0) -> Setup:
-    P = nufft.Plan(omega, L, L, theta=theta)
+               inner_tol: float = 0.0, L1: int | None = None) -> Setup:
+    """The solver's inputs and parameters for an L x L1 image (L1 = L by default)."""
+    P = nufft.Plan(omega, L, L if L1 is None else L1, theta=theta)
     if U is None:
         U = nufft.uniform_weights(omega, P.K0, P.K1)[0] if precond else np.ones(P.M)
     U = np.asarray(U, dtype=np.float64)

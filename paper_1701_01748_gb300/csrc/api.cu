@@ -146,8 +146,6 @@ void drop_graph(ppd_ctx *c) {
 
 cudaStream_t pick(ppd_ctx *c, void *s) { return s ? static_cast<cudaStream_t>(s) : c->stream; }
 
-bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
-
 // Stable LSD radix sort of indices by 64-bit key (16-bit digits).
 void radix_sort(const std::vector<uint64_t> &key, std::vector<int64_t> &perm) {
     const int64_t M = (int64_t)key.size();
@@ -192,13 +190,29 @@ int make_tmap(ppd_ctx *c) {
     return PPD_OK;
 }
 
+// Reads the device error word and clears it, so that a failure is reported
+// once, by the call that observes it, and the context stays usable.
 int check_err_word(ppd_ctx *c) {
     int h = 0;
     PPD_CUDA(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     PPD_CUDA(cudaStreamSynchronize(c->stream));
+    if (h) PPD_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
     if (h & ERR_TMA_TIMEOUT) return fail(PPD_ERR_TIMEOUT, "a bounded TMA wait in the degridding kernel gave up");
     if (h & ERR_NONFINITE) return fail(PPD_ERR_NONFINITE, "non-finite block norm");
     return PPD_OK;
+}
+
+// Global stopping rule of Algorithm 3 on the last iteration: relative
+// variation of x below tol and every block residual within fac eps_j,
+// evaluated in FP64 on the device; *flag = 1 when it holds (synchronises).
+int stop_rule(ppd_ctx *c, double tol, double fac, int *flag) {
+    c->part_out = c->partials;   // bank 0: the data step's residual partials
+    PPD_CHECK(block_norms(c, 1, c->stream));
+    PPD_CHECK(reduce_primal_stats(c, c->stream));
+    PPD_CHECK(stop_flag(c, tol, fac, c->stream));
+    PPD_CUDA(cudaMemcpyAsync(flag, c->stop_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PPD_CUDA(cudaStreamSynchronize(c->stream));
+    return check_err_word(c);
 }
 
 // One PPD iteration (Algorithm 3, lambda = 1, all blocks and bases).  The
@@ -246,6 +260,8 @@ template <typename R> int iteration_body(ppd_ctx *c, cudaStream_t s, bool first)
     if (extra) {
         c->part_in = bank[cur];
         c->part_out = bank[cur ^ 1];
+        c->next_step = 0;
+        c->next_test_in = 0;
         PPD_CHECK(subiter<R>(c, s, /*only_first=*/rnd ? 1 : 0));
         cur ^= 1;
     }
@@ -257,11 +273,15 @@ template <typename R> int iteration_body(ppd_ctx *c, cudaStream_t s, bool first)
         t_k = t_next;
         c->part_in = bank[cur];
         c->part_out = bank[cur ^ 1];
+        c->next_step = k;
+        c->next_test_in = k >= 2;   // step k - 1 >= 1 left the test partials
         PPD_CHECK(subiter<R>(c, s, 0, beta, fista ? 1 : 0));
         cur ^= 1;
     }
     c->part_in = bank[cur];
     c->part_out = bank[0];
+    c->next_step = c->cfg.n_itr;
+    c->next_test_in = c->cfg.n_itr >= 2;
     // small grids: the inverse column pass sums the partial tiles itself (no
     // combined grid in memory); from K = 4096 on, a combine pass with one CTA
     // group per tile reads them contiguously and the column pass reads the grid
@@ -372,12 +392,36 @@ template <typename R> int run_iterations(ppd_ctx *c, int n) {
     return PPD_OK;
 }
 
+// Start vector of the power iteration, normalised: all ones for seed 0,
+// else x_i = 0.5 + 2^-53 (s_i >> 11) with s_i = SplitMix64(seed + (i+1) g),
+// g = 0x9E3779B97F4A7C15 (Steele, Lea & Flood 2014, the generator's
+// published finaliser), i the row-major pixel index.
+std::vector<double> power_start(int n0, int n1, uint64_t seed) {
+    const size_t n = (size_t)n0 * n1;
+    std::vector<double> x(n, 1.0);
+    if (seed != 0) {
+        for (size_t i = 0; i < n; ++i) {
+            uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            x[i] = 0.5 + (double)(z >> 11) * 0x1.0p-53;
+        }
+    }
+    double s2 = 0;
+    for (double v : x) s2 += v * v;
+    const double inv = 1.0 / std::sqrt(s2);
+    for (double &v : x) v *= inv;
+    return x;
+}
+
 template <typename R> int power_iteration(ppd_ctx *c) {
     using C = cplx_t<R>;
     cudaStream_t s = c->stream;
     const int64_t N = c->N;
-    std::vector<R> ones(N, R(1.0 / std::sqrt((double)N)));
-    PPD_CUDA(cudaMemcpy(c->x, ones.data(), N * sizeof(R), cudaMemcpyHostToDevice));
+    std::vector<double> x0 = power_start(c->L0, c->L1, c->cfg.seed);
+    std::vector<R> start(x0.begin(), x0.end());
+    PPD_CUDA(cudaMemcpy(c->x, start.data(), N * sizeof(R), cudaMemcpyHostToDevice));
     double *nrm = c->stat_out;
     double prev = 0, val = 0;
     const int maxit = c->cfg.power_iters > 0 ? c->cfg.power_iters : 1000;
@@ -404,6 +448,93 @@ template <typename R> int power_iteration(ppd_ctx *c) {
     return PPD_OK;
 }
 
+// Largest eigenvalue of the symmetric tridiagonal matrix with diagonal a and
+// off-diagonal b (|b| = |a| - 1) by bisection on the Sturm sequence, FP64.
+double tridiag_max_eig(const std::vector<double> &a, const std::vector<double> &b) {
+    const int m = (int)a.size();
+    double lo = std::numeric_limits<double>::infinity(), hi = -lo;
+    for (int i = 0; i < m; ++i) {   // Gershgorin interval
+        const double r = (i > 0 ? std::abs(b[i - 1]) : 0.0) + (i + 1 < m ? std::abs(b[i]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    auto below = [&](double x) {   // eigenvalues < x
+        int cnt = 0;
+        double d = 1.0;
+        for (int i = 0; i < m; ++i) {
+            d = a[i] - x - (i > 0 ? b[i - 1] * b[i - 1] / d : 0.0);
+            if (d == 0.0) d = -1e-300;
+            if (d < 0) ++cnt;
+        }
+        return cnt;
+    };
+    for (int it = 0; it < 400 && hi - lo > 1e-16 * std::max(std::abs(lo), std::abs(hi)); ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (below(mid) >= m) hi = mid;
+        else lo = mid;
+    }
+    return hi;
+}
+
+// ||U^{1/2} Phi||_S^2 as the largest eigenvalue of Phi^dagger U Phi by the
+// Lanczos process (Lanczos 1950) from the same start as the power iteration:
+// w = A v_j - beta_{j-1} v_{j-1}, alpha_j = <w, v_j>, w -= alpha_j v_j,
+// beta_j = ||w||, v_{j+1} = w / beta_j, with the inner products in FP64; the
+// estimate is the largest eigenvalue of the tridiagonal (alpha, beta) after
+// each step, stopped when it has changed by at most tol (relative; at least
+// 2e-6 in FP32, where the operator itself is accurate to ~1e-7) in three
+// consecutive steps, or after maxit steps.  On strongly non-uniform coverages the two largest eigenvalues are
+// close and the power iteration needs thousands of steps; Lanczos converges
+// in tens.  Vectors: v_{j-1} in xt, v_j in x, w in g.
+template <typename R> int lanczos(ppd_ctx *c) {
+    using C = cplx_t<R>;
+    cudaStream_t s = c->stream;
+    const int64_t N = c->N;
+    R *v = static_cast<R *>(c->x), *vp = static_cast<R *>(c->xt), *w = static_cast<R *>(c->g);
+    std::vector<double> x0 = power_start(c->L0, c->L1, c->cfg.seed);
+    std::vector<R> start(x0.begin(), x0.end());
+    PPD_CUDA(cudaMemcpy(v, start.data(), N * sizeof(R), cudaMemcpyHostToDevice));
+    PPD_CUDA(cudaMemsetAsync(vp, 0, N * sizeof(R), s));
+    const int maxit = c->cfg.power_iters > 0 ? c->cfg.power_iters : 1000;
+    double tol = c->cfg.power_tol > 0 ? c->cfg.power_tol : 1e-10;
+    if (sizeof(R) == 4) tol = std::max(tol, 2e-6);
+    std::vector<double> al, be;
+    double theta = 0, beta = 0;
+    int it = 0, calm = 0;
+    for (it = 1; it <= maxit; ++it) {
+        PPD_CHECK(fft_forward<R>(c, v, static_cast<C *>(c->grid_a), s));
+        PPD_CHECK(degrid<R>(c, DG_OP, static_cast<C *>(c->grid_a), static_cast<C *>(c->z), nullptr, s));
+        PPD_CHECK(grid_vis<R>(c, GR_OP_U, static_cast<const C *>(c->z), nullptr, static_cast<C *>(c->grid_v), s));
+        PPD_CHECK(fft_inverse<R>(c, static_cast<const C *>(c->grid_v), w, s));
+        double h[3];
+        PPD_CHECK(lanczos_dot(c, w, vp, v, beta, c->stat_out, s));   // w -= beta v_{j-1}; <w, v_j>
+        PPD_CUDA(cudaMemcpyAsync(h, c->stat_out, sizeof(h), cudaMemcpyDeviceToHost, s));
+        PPD_CUDA(cudaStreamSynchronize(s));
+        const double alpha = h[0];
+        PPD_CHECK(lanczos_orth(c, w, v, alpha, c->stat_out, s));     // w -= alpha v_j; ||w||^2
+        PPD_CUDA(cudaMemcpyAsync(h, c->stat_out, sizeof(h), cudaMemcpyDeviceToHost, s));
+        PPD_CUDA(cudaStreamSynchronize(s));
+        if (!std::isfinite(alpha) || !std::isfinite(h[0]))
+            return fail(PPD_ERR_NONFINITE, "Lanczos: non-finite inner product");
+        al.push_back(alpha);
+        const double prev = theta;
+        theta = tridiag_max_eig(al, be);
+        // stop after three consecutive steps within the tolerance
+        calm = (it > 1 && std::abs(theta - prev) <= tol * theta) ? calm + 1 : 0;
+        if (calm >= 3) break;
+        beta = std::sqrt(std::max(h[0], 0.0));
+        if (beta <= 1e-300) break;   // invariant subspace: theta is exact
+        be.push_back(beta);
+        PPD_CHECK(scale_copy<R>(c, v, vp, N, 1.0, s));          // v_{j-1} <- v_j
+        PPD_CHECK(scale_copy<R>(c, w, v, N, 1.0 / beta, s));    // v_j <- w / beta_j
+    }
+    if (!(theta > 0) || !std::isfinite(theta)) return fail(PPD_ERR_NONFINITE, "Lanczos: non-positive norm");
+    c->op_norm_sq = theta;
+    c->power_done = std::min(it, maxit);
+    c->gpart_stale = true;
+    return PPD_OK;
+}
+
 int reset_state(ppd_ctx *c) {
     const size_t rb = c->rsz;
     PPD_CUDA(cudaMemsetAsync(c->x, 0, c->N * rb, c->stream));
@@ -415,6 +546,8 @@ int reset_state(ppd_ctx *c) {
     }
     PPD_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
     if (c->blk_seen) PPD_CUDA(cudaMemsetAsync(c->blk_seen, 0, c->d, c->stream));
+    if (c->inner_state) PPD_CUDA(cudaMemsetAsync(c->inner_state, 0, c->d * sizeof(int), c->stream));
+    if (c->inner_steps) PPD_CUDA(cudaMemsetAsync(c->inner_steps, 0, c->d * sizeof(int), c->stream));
     c->p_valid = false;
     c->iters = 0;
     c->gpart_stale = true;
@@ -510,6 +643,12 @@ void ppd_config_default(ppd_config *cfg) {
     cfg->power_tol = 0.0;
     cfg->stream = nullptr;
     cfg->inner_solver = PPD_INNER_FB;
+    cfg->inner_tol = 0.0;
+    cfg->stop_tol = 0.0;
+    cfg->stop_eps_factor = 1.005;
+    cfg->stop_every = 1;
+    cfg->seed = 0;
+    cfg->norm_method = PPD_NORM_LANCZOS;
 }
 
 const char *ppd_status_string(int status) {
@@ -532,9 +671,13 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
     if (!out || !cfg) return fail(PPD_ERR_INVALID_ARG, "ppd_create: NULL argument");
     *out = nullptr;
     const ppd_config &k = *cfg;
-    if (k.n0 != k.n1) return fail(PPD_ERR_UNSUPPORTED, "ppd_create: only square images (n0 == n1)");
-    if (!is_pow2(k.n0) || k.n0 < 16 || k.n0 > 4096)
-        return fail(PPD_ERR_UNSUPPORTED, "ppd_create: image side must be a power of two in [16, 4096]");
+    if (k.n0 < 16 || k.n1 < 16 || k.n0 > 4096 || k.n1 > 4096 || k.n0 % 16 || k.n1 % 16)
+        return fail(PPD_ERR_UNSUPPORTED, "ppd_create: image sides must be multiples of 16 in [16, 4096]");
+    const bool fp64 = k.precision == PPD_FP64_PLAIN;
+    if (!fft_length_supported(2 * k.n0, fp64) || !fft_length_supported(2 * k.n1, fp64))
+        return fail(PPD_ERR_UNSUPPORTED,
+                    "ppd_create: the oversampled grid sides 2 n0, 2 n1 must have no prime factor above 5 "
+                    "(and be powers of two above 4096 in FP64)");
     if (k.oversample != 2 || k.kernel_width != 8 || k.wavelet_levels != 4)
         return fail(PPD_ERR_UNSUPPORTED, "ppd_create: oversample 2, kernel width 8 and 4 levels are required");
     if (k.n_blocks < 1 || k.n_itr < 1 || !(k.tau > 0) || k.lambda != 1.0 || !(k.kappa > 0) || k.eta < 0 ||
@@ -546,8 +689,13 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
         return fail(PPD_ERR_INVALID_ARG, "ppd_create: unknown inner_init");
     if (k.inner_solver != PPD_INNER_FB && k.inner_solver != PPD_INNER_FISTA)
         return fail(PPD_ERR_INVALID_ARG, "ppd_create: unknown inner_solver");
+    if (k.norm_method != PPD_NORM_LANCZOS && k.norm_method != PPD_NORM_POWER)
+        return fail(PPD_ERR_INVALID_ARG, "ppd_create: unknown norm_method");
     if (k.tile != 0 && k.tile != 16 && k.tile != 32) return fail(PPD_ERR_INVALID_ARG, "ppd_create: tile must be 16 or 32");
     if (k.chunk < 0) return fail(PPD_ERR_INVALID_ARG, "ppd_create: chunk must be >= 0");
+    if (!(k.inner_tol >= 0) || !(k.stop_tol >= 0) || !(k.stop_eps_factor >= 0) || k.stop_every < 0 ||
+        !std::isfinite(k.inner_tol) || !std::isfinite(k.stop_tol) || !std::isfinite(k.stop_eps_factor))
+        return fail(PPD_ERR_INVALID_ARG, "ppd_create: invalid stopping-test parameter");
 
     ppd_ctx *c = new (std::nothrow) ppd_ctx();
     if (!c) return fail(PPD_ERR_OOM, "ppd_create: host allocation");
@@ -562,7 +710,7 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
     c->d = k.n_blocks;
     c->levels = k.wavelet_levels;
     c->T = k.tile ? k.tile : 16;
-    if (c->K0 % c->T) c->T = 16;
+    if (c->K0 % c->T || c->K1 % c->T) c->T = 16;
     c->C = k.chunk ? k.chunk : 1024;
     c->beta = k.kb_beta > 0 ? k.kb_beta : 2.34 * KB_J;
     c->tau = k.tau;
@@ -598,7 +746,8 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
         (st = dalloc_bytes(&c->fft_tmp_inv, (int64_t)c->L0 * c->K1 * cb)) ||
         (st = dalloc(&c->fwd_strips, c->K1)) || (st = dalloc(&c->inv_strips, c->K1)) ||
         (st = dalloc(&c->row_fwd, c->K0)) || (st = dalloc(&c->row_inv, c->K0)) || (st = dalloc(&c->col_fwd, c->K1)) ||
-        (st = dalloc_bytes(&c->tw0, c->K0 * cb)) || (st = dalloc_bytes(&c->deap0, c->L0 * rb)) ||
+        (st = dalloc_bytes(&c->tw0, c->K0 * cb)) || (st = dalloc_bytes(&c->tw1, c->K1 * cb)) ||
+        (st = dalloc_bytes(&c->deap0, c->L0 * rb)) ||
         (st = dalloc_bytes(&c->deap1, c->L1 * rb)) ||
         (st = dalloc_bytes(&c->kbpoly, (KB_DEG + 1) * KB_J * sizeof(float))) || (st = dalloc(&c->err, 1)) ||
         (st = dalloc(&c->stat_out, 3)))
@@ -606,7 +755,8 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
     c->n_prim_blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 4);
     if ((st = dalloc(&c->prim_part, 3 * (size_t)std::max(c->n_prim_blocks, c->L0)))) return bail(st);
     if ((st = dalloc(&c->mask_cur, (size_t)c->d + N_BASES)) || (st = dalloc(&c->blk_seen, (size_t)c->d)) ||
-        (st = dalloc(&c->regrid_d, 1)))
+        (st = dalloc(&c->regrid_d, 1)) || (st = dalloc(&c->inner_state, (size_t)c->d)) ||
+        (st = dalloc(&c->inner_steps, (size_t)c->d)) || (st = dalloc(&c->stop_flag, 1)))
         return bail(st);
     if (cudaMemsetAsync(c->mask_cur, 1, (size_t)c->d + N_BASES, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->blk_seen, 0, (size_t)c->d, c->stream) != cudaSuccess ||
@@ -638,10 +788,11 @@ void ppd_destroy(ppd_ctx *c) {
                     (void *)c->col_fwd, c->fft_tmp_inv})
         dfree(p);
     for (void *p : {c->wgt, c->wcoef, (void *)c->mask_all, (void *)c->mask_cur, (void *)c->blk_seen,
-                    (void *)c->regrid_d})
+                    (void *)c->regrid_d, (void *)c->inner_state, (void *)c->inner_steps, (void *)c->stop_flag})
         dfree(p);
     for (void *p : {c->x, c->xt, c->g, c->ut, c->xtrue, c->u, c->wtmp, c->wtmp2, c->grid_a, c->grid_v, c->fft_tmp,
-                    c->tw0, c->deap0, c->deap1, c->kbpoly, (void *)c->prim_part, (void *)c->stat_out, (void *)c->err})
+                    c->tw0, c->tw1, c->deap0, c->deap1, c->kbpoly, (void *)c->prim_part, (void *)c->stat_out,
+                    (void *)c->err})
         dfree(p);
     if (c->stream2) {
         cudaStreamSynchronize(c->stream2);
@@ -950,7 +1101,11 @@ int ppd_set_weights(ppd_ctx *c, const double *theta, const double *U, const doub
         c->op_norm_sq = 0;
         c->power_done = 0;
     } else {
-        if ((st = c->is_f32 ? power_iteration<float>(c) : power_iteration<double>(c))) return st;
+        if (c->cfg.norm_method == PPD_NORM_POWER)
+            st = c->is_f32 ? power_iteration<float>(c) : power_iteration<double>(c);
+        else
+            st = c->is_f32 ? lanczos<float>(c) : lanczos<double>(c);
+        if (st) return st;
         c->eta = 1.0 / c->op_norm_sq;
     }
     if ((st = reset_state(c))) return st;
@@ -985,7 +1140,30 @@ int ppd_iterate(ppd_ctx *c, int32_t n_iters, ppd_stats *stats) {
     DeviceGuard dg_(c->device);
     if (!c->have_weights) return fail(PPD_ERR_NOT_READY, "ppd_iterate: call ppd_set_weights first");
     if (n_iters < 0) return fail(PPD_ERR_INVALID_ARG, "ppd_iterate: n_iters < 0");
-    int st = c->is_f32 ? run_iterations<float>(c, n_iters) : run_iterations<double>(c, n_iters);
+    int st = PPD_OK, ran = 0, stopped = 0;
+    if (c->cfg.stop_tol > 0 && n_iters > 0) {
+        // Algorithm 3 until its stopping rule holds: the rule is evaluated on
+        // the device in FP64 after every `every`-th iteration of this call
+        const int every = c->cfg.stop_every > 0 ? c->cfg.stop_every : 1;
+        const double fac = c->cfg.stop_eps_factor > 0 ? c->cfg.stop_eps_factor : 1.005;
+        while (ran < n_iters && st == PPD_OK) {
+            const int n = std::min(every, n_iters - ran);
+            st = c->is_f32 ? run_iterations<float>(c, n) : run_iterations<double>(c, n);
+            if (st != PPD_OK) break;
+            ran += n;
+            if (ran % every == 0) {
+                int flag = 0;
+                st = stop_rule(c, c->cfg.stop_tol, fac, &flag);
+                if (st == PPD_OK && flag) {
+                    stopped = 1;
+                    break;
+                }
+            }
+        }
+    } else {
+        st = c->is_f32 ? run_iterations<float>(c, n_iters) : run_iterations<double>(c, n_iters);
+        ran = n_iters;
+    }
     if (st != PPD_OK) {
         if (stats) stats->status = st;
         return st;
@@ -996,11 +1174,16 @@ int ppd_iterate(ppd_ctx *c, int32_t n_iters, ppd_stats *stats) {
         PPD_CHECK(reduce_primal_stats(c, c->stream));
         double h[3];
         std::vector<double> r2(c->d);
+        std::vector<int32_t> steps(c->d);
         PPD_CUDA(cudaMemcpyAsync(h, c->stat_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
         PPD_CUDA(cudaMemcpyAsync(r2.data(), c->resid2, c->d * 8, cudaMemcpyDeviceToHost, c->stream));
+        if (stats->inner_steps)
+            PPD_CUDA(cudaMemcpyAsync(steps.data(), c->inner_steps, c->d * 4, cudaMemcpyDeviceToHost, c->stream));
         PPD_CUDA(cudaStreamSynchronize(c->stream));
         st = check_err_word(c);
         stats->iters_done = c->iters;
+        stats->iters_run = ran;
+        stats->stopped = stopped;
         stats->status = st;
         stats->rel_var = h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::numeric_limits<double>::infinity();
         stats->snr_db = c->xtrue_set && h[2] > 0 ? 20.0 * std::log10(std::sqrt(c->xtrue_norm2 / h[2]))
@@ -1009,6 +1192,7 @@ int ppd_iterate(ppd_ctx *c, int32_t n_iters, ppd_stats *stats) {
         for (int j = 0; j < c->d; ++j) {
             const double rj = std::sqrt(r2[j]);
             if (stats->block_residual) stats->block_residual[j] = rj;
+            if (stats->inner_steps) stats->inner_steps[j] = steps[j];
             mx = std::max(mx, rj / c->eps_h[j]);
         }
         stats->max_res_over_eps = mx;
@@ -1234,7 +1418,7 @@ int ppd_autotune(ppd_ctx *c, int32_t iters, int32_t *tile_out, int32_t *chunk_ou
     float best = 1e30f;
     int bt = c->T, bc = c->C, st = PPD_OK;
     for (int T : {16, 32}) {
-        if (c->K0 % T || c->K0 < 2 * T) continue;
+        if (c->K0 % T || c->K1 % T || c->K0 < 2 * T || c->K1 < 2 * T) continue;
         for (int C : {512, 1024, 2048}) {
             if ((st = rebuild(T, C))) break;
             if ((st = ppd_iterate(c, 3, nullptr))) break;
@@ -1549,5 +1733,15 @@ int ppd_timing_read(ppd_ctx *c, int32_t n, const char **names, double *ms, int64
 }
 
 int64_t ppd_launch_count(ppd_ctx *c) { return c ? c->launches : 0; }
+
+int ppd_set_wait_limit(ppd_ctx *c, int64_t polls) {
+    if (!c) return fail(PPD_ERR_INVALID_ARG, "ppd_set_wait_limit: NULL context");
+    if (polls < 0) return fail(PPD_ERR_INVALID_ARG, "ppd_set_wait_limit: polls < 0");
+    DeviceGuard dg_(c->device);
+    PPD_CUDA(cudaStreamSynchronize(c->stream));
+    c->wait_first = polls;
+    drop_graph(c);   // the limit is a kernel argument of the captured iteration
+    return PPD_OK;
+}
 
 }  // extern "C"

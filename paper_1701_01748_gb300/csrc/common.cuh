@@ -42,7 +42,9 @@ constexpr int HALO = 8;          // extended tile = (T + HALO)^2 cells
 constexpr int N_BASES = 9;       // Dirac + db1..db8
 constexpr int N_WAVELETS = 8;
 constexpr int MAX_TAPS = 16;     // db8
-constexpr int NPART = 2;         // per-chunk norm partials: ||w-y||^2, ||Theta q - y||^2
+// per-chunk norm partials: ||w-y||^2, ||Theta q - y||^2 and, for the
+// Algorithm 2 stopping test, ||zbar^t - zbar^(t-1)||^2, ||zbar^t||^2
+constexpr int NPART = 4;
 constexpr double INV_TWO_PI = 0.15915494309189535;
 
 // device error word bits
@@ -98,6 +100,18 @@ struct TimingSite {
     cudaEvent_t start, stop;
 };
 
+// Stages of a mixed-radix FFT of length K (radices 2, 3, 4, 5; ns = 0 when
+// K has another prime factor).
+struct FftPlan {
+    static constexpr int MAX_STAGES = 16;
+    int K = 0, ns = 0;
+    int rad[MAX_STAGES] = {};
+};
+FftPlan make_fft_plan(int K);
+// lengths the FFT passes handle: 32 <= K <= 8192 with prime factors 2, 3, 5
+// (lengths that are not powers of two up to 4096 in FP64)
+bool fft_length_supported(int K, bool fp64);
+
 struct Chunks {
     int64_t n = 0;
     int32_t *start = nullptr, *count = nullptr, *tile = nullptr, *block = nullptr;   // device
@@ -130,7 +144,8 @@ struct ppd_ctx {
     int32_t *fwd_strips = nullptr, *inv_strips = nullptr;
     int n_fwd_strips = 0, n_inv_strips = 0;
     uint8_t *row_fwd = nullptr, *row_inv = nullptr, *col_fwd = nullptr;
-    void *tw0 = nullptr, *tw1 = nullptr, *deap0 = nullptr, *deap1 = nullptr;
+    void *tw0 = nullptr, *tw1 = nullptr, *deap0 = nullptr, *deap1 = nullptr;   // twiddles of K0 / K1, Z's scalings
+    ppd::FftPlan plan0, plan1;                                               // FFT plans of K0 (columns), K1 (rows)
     void *filt = nullptr;       // 8 x 16 reals (low-pass, zero padded)
     void *kbpoly = nullptr;     // (KB_DEG+1) x 8 floats
     double *prim_part = nullptr;
@@ -158,10 +173,19 @@ struct ppd_ctx {
     double *partials = nullptr, *scale = nullptr, *resid2 = nullptr, *eps_d = nullptr,
            *mu_d = nullptr;
     double *part_in = nullptr, *part_out = nullptr;   // chunk-partial banks for the next launch
+    // Algorithm 2 stopping test (cfg.inner_tol > 0): per block the step at
+    // which the test held in the current iteration (0 = still running) and
+    // the steps taken in the last iteration; the arguments of the next
+    // sub-iteration / gridding launch: its step number and whether its input
+    // bank holds the test partials of the previous step
+    int *inner_state = nullptr, *inner_steps = nullptr;
+    int next_step = 0, next_test_in = 0;
+    int *stop_flag = nullptr;                          // global stopping rule (device, 1 int)
     cudaStream_t stream2 = nullptr;                   // prior (SARA) branch of the iteration
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     void *gpart = nullptr;           // n_chunks x (T+HALO)^2 complex
     int *err = nullptr;              // device error word
+    long long wait_first = ppd::SPIN_LIMIT;   // polls of the degridding's first TMA wait (ppd_set_wait_limit)
     CUtensorMap tmap_a;              // TMA descriptor of grid_a
     bool tma_ok = false;
 
@@ -343,7 +367,7 @@ template <typename R> int fft_inverse_rows(ppd_ctx *c, R *img, cudaStream_t s);
 // Grids up to K = 2048 end the iteration with the fused row kernel; larger
 // grids with the plain inverse row pass and the primal kernel (an 8192-point
 // row pair per CTA costs more registers than the two launches it saves).
-inline bool fused_rows(const ppd_ctx *c) { return c->K0 <= 2048; }
+inline bool fused_rows(const ppd_ctx *c) { return c->K1 <= 2048; }
 // inverse row pass + primal step + the next iteration's forward row pass (fft.cu)
 template <typename R> int rows_primal(ppd_ctx *c, cudaStream_t s);
 template <typename R> int fft_forward_rows(ppd_ctx *c, const R *x, cudaStream_t s);
@@ -351,7 +375,13 @@ template <typename R> int fft_forward_cols(ppd_ctx *c, cplx_t<R> *grid, cudaStre
 template <typename R> int fft_inverse_cols_partials(ppd_ctx *c, cudaStream_t s);
 template <typename R> int fft_inverse_cols(ppd_ctx *c, const cplx_t<R> *grid, cudaStream_t s);
 int reduce_primal_stats(ppd_ctx *c, cudaStream_t s);
+// stop_flag = (sqrt(stat_out[0] / stat_out[1]) < tol && every sqrt(resid2_j) <= fac eps_j)
+int stop_flag(ppd_ctx *c, double tol, double fac, cudaStream_t s);
 template <typename R> int scale_copy(ppd_ctx *c, const R *in, R *out, int64_t n, double a, cudaStream_t s);
+// Lanczos steps (image.cu): w -= beta vp, out_dev[0] = <w, v>; w -= alpha v, out_dev[0] = ||w||^2
+template <typename R>
+int lanczos_dot(ppd_ctx *c, R *w, const R *vp, const R *v, double beta, double *out_dev, cudaStream_t s);
+template <typename R> int lanczos_orth(ppd_ctx *c, R *w, const R *v, double alpha, double *out_dev, cudaStream_t s);
 template <typename R> int reweight_from(ppd_ctx *c, R *coef_to_w, int64_t n, double omega, cudaStream_t s);
 template <typename R> int mul_sq(ppd_ctx *c, R *inout, const R *w, int64_t n, cudaStream_t s);
 template <typename R> int sumsq(ppd_ctx *c, const R *in, int64_t n, double *out_dev, cudaStream_t s);

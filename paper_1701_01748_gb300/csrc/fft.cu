@@ -1,18 +1,25 @@
 // Oversampled 2-D FFT with the zero-padding / scaling operator Z fused in
 // (Section 2: Phi = Theta G F Z; F is the unnormalised n-oversampled DFT).
 //
-// Forward  a = F Z x:  row pass   x (L x L real)  -> tmp (L x K complex)
-//                      column pass tmp            -> grid (K x K complex)
+// Image L0 x L1 (rows x columns), grid K0 x K1 (K = 2L per axis).
+// Forward  a = F Z x:  row pass    x (L0 x L1 real) -> tmp (L0 x K1 complex)
+//                      column pass tmp              -> grid (K0 x K1 complex)
 // Inverse  Re(Z^T F^H grid): column pass grid -> tmp, row pass tmp -> image.
 //
-// Every pass is a batched Stockham radix-4 (one radix-2 stage when log2 K is
-// odd) FFT in shared memory: a CTA loads B whole rows (row pass) or a strip of
-// W columns (column pass), runs log K stages with one shared buffer (each
-// thread keeps its butterflies in registers between the read and the write
-// half of a stage) and writes the result.  Only the L nonzero rows/columns of
-// the padded image are read or produced; the grid is stored with the zero
-// frequency at the centre (plain index k at (k + K/2) mod K).
+// Every pass is a batched Stockham FFT in shared memory: a CTA loads B whole
+// rows (row pass, length K1) or a strip of W columns (column pass, length
+// K0), runs the stages and writes the result.  Only the L nonzero rows /
+// columns of the padded image are read or produced; the grid is stored with
+// the zero frequency at the centre (plain index k at (k + K/2) mod K).
+//
+// Two cores: lengths that are powers of two use a compile-time radix-4 (and
+// one radix-2) core with one shared buffer; any other length whose prime
+// factors are 2, 3 and 5 uses a run-time mixed-radix core (radices 5, 3, 4,
+// 2 from a plan made on the host) that ping-pongs between two buffers.  The
+// pass kernels are templated on KT = the length for the first core, 0 for
+// the second.
 #include <cmath>
+#include <vector>
 
 #include "common.cuh"
 
@@ -29,10 +36,16 @@ template <typename C> __device__ __forceinline__ C cconj(C a) { return C{a.x, -a
 
 __host__ __device__ constexpr int ilog2_(int k) { return k <= 1 ? 0 : 1 + ilog2_(k / 2); }
 
+// v mod K for v in [0, 2K)
+__device__ __forceinline__ int wrapK(int v, int K) { return v >= K ? v - K : v; }
+
+constexpr int NT = 256;
+
+// ------------------------------------------------------------ power-of-two core
 // In-place batched Stockham FFT (forward sign) of NSEQ sequences of length K
 // held in shared memory.  INTERLEAVED: element (s, i) at i*NSEQ + s;
 // otherwise at s*K + i.  tw[m] = exp(-2 pi i m / K).
-template <typename R, int K, int NSEQ, int NT, bool INTERLEAVED>
+template <typename R, int K, int NSEQ, bool INTERLEAVED>
 __device__ void fft_smem(cplx_t<R> *buf, const cplx_t<R> *tw) {
     using C = cplx_t<R>;
     const int tid = threadIdx.x;
@@ -109,16 +122,111 @@ __device__ void fft_smem(cplx_t<R> *buf, const cplx_t<R> *tw) {
     }
 }
 
-constexpr int NT = 256;
+// ------------------------------------------------------------ mixed-radix core
+// Forward DFT of RAD points in place (sign -), written out per radix.
+template <typename C> __device__ __forceinline__ void dft(C (&a)[2]) {
+    const C t = a[0];
+    a[0] = cadd(t, a[1]);
+    a[1] = csub(t, a[1]);
+}
+template <typename C> __device__ __forceinline__ void dft(C (&a)[3]) {
+    using R = decltype(a[0].x);
+    const R h = R(0.8660254037844386);   // sin(2 pi / 3)
+    const C s = cadd(a[1], a[2]), d = csub(a[1], a[2]);
+    const C m{a[0].x - R(0.5) * s.x, a[0].y - R(0.5) * s.y};
+    const C e{h * d.y, -h * d.x};   // -i sin(2 pi/3) (a1 - a2)
+    a[0] = cadd(a[0], s);
+    a[1] = cadd(m, e);
+    a[2] = csub(m, e);
+}
+template <typename C> __device__ __forceinline__ void dft(C (&a)[4]) {
+    const C t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
+    const C t2 = cadd(a[1], a[3]), t3 = csub(a[1], a[3]);
+    a[0] = cadd(t0, t2);
+    a[1] = C{t1.x + t3.y, t1.y - t3.x};
+    a[2] = csub(t0, t2);
+    a[3] = C{t1.x - t3.y, t1.y + t3.x};
+}
+template <typename C> __device__ __forceinline__ void dft(C (&a)[5]) {
+    using R = decltype(a[0].x);
+    const R c1 = R(0.30901699437494745), c2 = R(-0.8090169943749475);   // cos(2 pi/5), cos(4 pi/5)
+    const R s1 = R(0.9510565162951535), s2 = R(0.5877852522924731);     // sin(2 pi/5), sin(4 pi/5)
+    const C t1 = cadd(a[1], a[4]), t2 = cadd(a[2], a[3]);
+    const C t3 = csub(a[1], a[4]), t4 = csub(a[2], a[3]);
+    const C u1{a[0].x + c1 * t1.x + c2 * t2.x, a[0].y + c1 * t1.y + c2 * t2.y};
+    const C u2{a[0].x + c2 * t1.x + c1 * t2.x, a[0].y + c2 * t1.y + c1 * t2.y};
+    const C v1{s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y};
+    const C v2{s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y};
+    a[0] = cadd(a[0], cadd(t1, t2));
+    a[1] = C{u1.x + v1.y, u1.y - v1.x};   // u1 - i v1
+    a[4] = C{u1.x - v1.y, u1.y + v1.x};   // u1 + i v1
+    a[2] = C{u2.x + v2.y, u2.y - v2.x};
+    a[3] = C{u2.x - v2.y, u2.y + v2.x};
+}
 
-// rows per CTA in a row pass: enough butterflies for 256 threads
+// One Stockham stage of radix RAD from src to dst: for butterfly j (k = j mod
+// Ns) the inputs j + q K/RAD, twiddled by w^(q k K/(Ns RAD)), go to
+// (j - k) RAD + k + p Ns.
+template <typename R, int RAD, bool INTERLEAVED>
+__device__ __forceinline__ void stage_any(const cplx_t<R> *__restrict__ src, cplx_t<R> *__restrict__ dst, int K,
+                                          int nseq, int Ns, const cplx_t<R> *__restrict__ tw) {
+    using C = cplx_t<R>;
+    const int m = K / RAD, tstep = K / (Ns * RAD), nbf = nseq * m;
+    for (int bf = threadIdx.x; bf < nbf; bf += NT) {
+        int s, j;
+        if (INTERLEAVED) {
+            j = bf / nseq;
+            s = bf - j * nseq;
+        } else {
+            s = bf / m;
+            j = bf - s * m;
+        }
+        const int k = j % Ns;
+        C a[RAD];
+#pragma unroll
+        for (int q = 0; q < RAD; ++q) a[q] = src[INTERLEAVED ? (j + q * m) * nseq + s : s * K + j + q * m];
+        if (Ns > 1) {
+#pragma unroll
+            for (int q = 1; q < RAD; ++q) a[q] = cmul(a[q], tw[q * k * tstep]);
+        }
+        dft(a);
+        const int d = (j - k) * RAD + k;
+#pragma unroll
+        for (int p = 0; p < RAD; ++p) dst[INTERLEAVED ? (d + p * Ns) * nseq + s : s * K + d + p * Ns] = a[p];
+    }
+}
+
+// Batched mixed-radix FFT of nseq sequences of length pl.K in a (layout as
+// fft_smem), ping-ponging with b; returns the buffer holding the result.
+// Callers synchronise before (the input is complete) and the last stage
+// ends with a barrier.
+template <typename R, bool INTERLEAVED>
+__device__ cplx_t<R> *fft_any(cplx_t<R> *a, cplx_t<R> *b, int nseq, const FftPlan &pl, const cplx_t<R> *tw) {
+    int Ns = 1;
+    for (int st = 0; st < pl.ns; ++st) {
+        const int r = pl.rad[st];
+        if (r == 4) stage_any<R, 4, INTERLEAVED>(a, b, pl.K, nseq, Ns, tw);
+        else if (r == 2) stage_any<R, 2, INTERLEAVED>(a, b, pl.K, nseq, Ns, tw);
+        else if (r == 3) stage_any<R, 3, INTERLEAVED>(a, b, pl.K, nseq, Ns, tw);
+        else stage_any<R, 5, INTERLEAVED>(a, b, pl.K, nseq, Ns, tw);
+        __syncthreads();
+        Ns *= r;
+        cplx_t<R> *t = a;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// ------------------------------------------------------------ pass geometry
+// rows per CTA in a row pass of the power-of-two core: enough butterflies for 256 threads
 template <typename R> __host__ __device__ constexpr int rows_per_cta(int K) { return 1024 / K > 0 ? 1024 / K : 1; }
-// columns per CTA in a column pass.  K <= 2048: the strips are read from
-// L2 (grid and row-pass output of these sizes stay cached between the
-// passes), so the fewest columns the 256-thread butterfly split allows
-// (1024 / K, at least 1) give the most CTAs for these latency-bound passes.
-// Larger K: at least 32 contiguous bytes per grid row (one DRAM sector:
-// 4 float / 2 double columns), at most 128 KB of strip.
+// columns per CTA in a column pass of the power-of-two core.  K <= 2048:
+// the strips are read from L2 (grid and row-pass output of these sizes stay
+// cached between the passes), so the fewest columns the 256-thread
+// butterfly split allows (1024 / K, at least 1) give the most CTAs for these
+// latency-bound passes.  Larger K: at least 32 contiguous bytes per grid row
+// (one DRAM sector: 4 float / 2 double columns), at most 128 KB of strip.
 template <typename R> __host__ __device__ constexpr int cols_per_cta(int K) {
     constexpr int csz = 2 * (int)sizeof(R);
     if (K <= 2048) return 1024 / K > 1 ? 1024 / K : 1;
@@ -146,84 +254,109 @@ __device__ __forceinline__ const cplx_t<R> *stage_twiddles(cplx_t<R> *buf, const
         return tw;
     }
 }
+// sequences per CTA as a compile-time constant (power-of-two core) or 1
+template <typename R, int KT> constexpr int rows_ct() { return KT ? rows_per_cta<R>(KT) : 1; }
+template <typename R, int KT> constexpr int cols_ct() { return KT ? cols_per_cta<R>(KT) : 1; }
 
-// forward row pass: tmp[n0][c] = FFT_axis1(Z x)[n0][(c + K/2) mod K]
-template <typename R, int K>
+// The FFT of a pass: the compile-time core in place, or the mixed-radix core
+// (buf2 the second buffer); returns the buffer holding the result.
+template <typename R, int KT, int NSEQ, bool IL>
+__device__ __forceinline__ cplx_t<R> *run_fft(cplx_t<R> *buf, cplx_t<R> *buf2, const cplx_t<R> *tws, int nseq,
+                                              const FftPlan &pl, const cplx_t<R> *tw) {
+    if constexpr (KT != 0) {
+        fft_smem<R, KT, NSEQ, IL>(buf, tws);
+        return buf;
+    } else {
+        return fft_any<R, IL>(buf, buf2, nseq, pl, tw);
+    }
+}
+
+// Run-time arguments of a pass: the FFT plan of its length and the
+// sequences per CTA (used by the mixed-radix core only).
+struct PassArgs {
+    FftPlan pl;
+    int nseq;
+};
+
+// forward row pass: tmp[n0][c] = FFT_axis1(Z x)[n0][(c + K1/2) mod K1]
+template <typename R, int KT>
 __global__ void __launch_bounds__(NT) k_rows_fwd(const R *__restrict__ x, cplx_t<R> *__restrict__ tmp,
                                                  const cplx_t<R> *__restrict__ tw, const R *__restrict__ s0,
-                                                 const R *__restrict__ s1, int L, const uint8_t *__restrict__ colmask) {
+                                                 const R *__restrict__ s1, int L0, int L1,
+                                                 const uint8_t *__restrict__ colmask, PassArgs pa) {
     using C = cplx_t<R>;
-    constexpr int B = rows_per_cta<R>(K);
+    constexpr int BT = rows_ct<R, KT>();
+    const int K = KT ? KT : pa.pl.K, B = KT ? BT : pa.nseq;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
-    const C *tws = stage_twiddles<R, B, K>(buf, tw);
+    C *buf2 = buf + B * K;
+    const C *tws = KT ? stage_twiddles<R, BT, KT ? KT : 1>(buf, tw) : tw;
     const int row0 = blockIdx.x * B;
     for (int e = threadIdx.x; e < B * K; e += NT) buf[e] = C{0, 0};
     __syncthreads();
-    for (int e = threadIdx.x; e < B * L; e += NT) {
-        int s = e / L, n1 = e % L, n0 = row0 + s;
-        if (n0 < L) {
-            int pos = (n1 - L / 2 + K) & (K - 1);
-            buf[s * K + pos] = C{s0[n0] * s1[n1] * x[(int64_t)n0 * L + n1], R(0)};
-        }
+    for (int e = threadIdx.x; e < B * L1; e += NT) {
+        const int s = e / L1, n1 = e - s * L1, n0 = row0 + s;
+        if (n0 < L0) buf[s * K + wrapK(n1 - L1 / 2 + K, K)] = C{s0[n0] * s1[n1] * x[(int64_t)n0 * L1 + n1], R(0)};
     }
     __syncthreads();
-    fft_smem<R, K, B, NT, false>(buf, tws);
+    const C *out = run_fft<R, KT, BT, false>(buf, buf2, tws, B, pa.pl, tw);
     for (int e = threadIdx.x; e < B * K; e += NT) {
-        int s = e / K, c = e % K, n0 = row0 + s;
-        if (n0 < L && colmask[c]) tmp[(int64_t)n0 * K + c] = buf[s * K + ((c + K / 2) & (K - 1))];
+        const int s = e / K, c = e - s * K, n0 = row0 + s;
+        if (n0 < L0 && colmask[c]) tmp[(int64_t)n0 * K + c] = out[s * K + wrapK(c + K / 2, K)];
     }
 }
 
-// forward column pass: grid[r][c] = FFT_axis0(tmp padded)[(r + K/2) mod K][c]
-template <typename R, int K>
+// forward column pass: grid[r][c] = FFT_axis0(tmp padded)[(r + K0/2) mod K0][c]
+template <typename R, int KT>
 __global__ void __launch_bounds__(NT) k_cols_fwd(const cplx_t<R> *__restrict__ tmp, cplx_t<R> *__restrict__ grid,
-                                                 const cplx_t<R> *__restrict__ tw, int L,
+                                                 const cplx_t<R> *__restrict__ tw, int L0, int K1,
                                                  const int32_t *__restrict__ strips,
-                                                 const uint8_t *__restrict__ rowmask) {
+                                                 const uint8_t *__restrict__ rowmask, PassArgs pa) {
     using C = cplx_t<R>;
-    constexpr int W = cols_per_cta<R>(K);
+    constexpr int WT = cols_ct<R, KT>();
+    const int K = KT ? KT : pa.pl.K, W = KT ? WT : pa.nseq;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
-    const C *tws = stage_twiddles<R, W, K>(buf, tw);
+    C *buf2 = buf + W * K;
+    const C *tws = KT ? stage_twiddles<R, WT, KT ? KT : 1>(buf, tw) : tw;
     const int c0 = strips[blockIdx.x];
     for (int e = threadIdx.x; e < W * K; e += NT) buf[e] = C{0, 0};
     __syncthreads();
-    for (int e = threadIdx.x; e < W * L; e += NT) {
-        int s = e % W, n0 = e / W;
-        int pos = (n0 - L / 2 + K) & (K - 1);
-        buf[pos * W + s] = tmp[(int64_t)n0 * K + c0 + s];
+    for (int e = threadIdx.x; e < W * L0; e += NT) {
+        const int n0 = e / W, s = e - n0 * W;
+        buf[wrapK(n0 - L0 / 2 + K, K) * W + s] = tmp[(int64_t)n0 * K1 + c0 + s];
     }
     __syncthreads();
-    fft_smem<R, K, W, NT, true>(buf, tws);
+    const C *out = run_fft<R, KT, WT, true>(buf, buf2, tws, W, pa.pl, tw);
     for (int e = threadIdx.x; e < W * K; e += NT) {
-        int s = e % W, r = e / W;
-        if (rowmask[r]) grid[(int64_t)r * K + c0 + s] = buf[((r + K / 2) & (K - 1)) * W + s];
+        const int r = e / W, s = e - r * W;
+        if (rowmask[r]) grid[(int64_t)r * K1 + c0 + s] = out[wrapK(r + K / 2, K) * W + s];
     }
 }
 
-// inverse column pass: tmp[n0][c] = (F^H along axis 0 of grid)[(n0 - L/2) mod K][c]
-template <typename R, int K>
+// inverse column pass: tmp[n0][c] = (F^H along axis 0 of grid)[(n0 - L0/2) mod K0][c]
+template <typename R, int KT>
 __global__ void __launch_bounds__(NT) k_cols_inv(const cplx_t<R> *__restrict__ grid, cplx_t<R> *__restrict__ tmp,
-                                                 const cplx_t<R> *__restrict__ tw, int L,
+                                                 const cplx_t<R> *__restrict__ tw, int L0, int K1,
                                                  const int32_t *__restrict__ strips,
-                                                 const uint8_t *__restrict__ rowmask) {
+                                                 const uint8_t *__restrict__ rowmask, PassArgs pa) {
     using C = cplx_t<R>;
-    constexpr int W = cols_per_cta<R>(K);
+    constexpr int WT = cols_ct<R, KT>();
+    const int K = KT ? KT : pa.pl.K, W = KT ? WT : pa.nseq;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
-    const C *tws = stage_twiddles<R, W, K>(buf, tw);
+    C *buf2 = buf + W * K;
+    const C *tws = KT ? stage_twiddles<R, WT, KT ? KT : 1>(buf, tw) : tw;
     const int c0 = strips[blockIdx.x];
     for (int e = threadIdx.x; e < W * K; e += NT) {
-        int s = e % W, r = e / W;   // r: stored (centred) row; natural frequency (r + K/2) mod K
-        buf[((r + K / 2) & (K - 1)) * W + s] = rowmask[r] ? cconj(grid[(int64_t)r * K + c0 + s]) : C{0, 0};
+        const int r = e / W, s = e - r * W;   // r: stored (centred) row; natural frequency (r + K/2) mod K
+        buf[wrapK(r + K / 2, K) * W + s] = rowmask[r] ? cconj(grid[(int64_t)r * K1 + c0 + s]) : C{0, 0};
     }
     __syncthreads();
-    fft_smem<R, K, W, NT, true>(buf, tws);
-    for (int e = threadIdx.x; e < W * L; e += NT) {
-        int s = e % W, n0 = e / W;
-        int pos = (n0 - L / 2 + K) & (K - 1);
-        tmp[(int64_t)n0 * K + c0 + s] = cconj(buf[pos * W + s]);
+    const C *out = run_fft<R, KT, WT, true>(buf, buf2, tws, W, pa.pl, tw);
+    for (int e = threadIdx.x; e < W * L0; e += NT) {
+        const int n0 = e / W, s = e - n0 * W;
+        tmp[(int64_t)n0 * K1 + c0 + s] = cconj(out[wrapK(n0 - L0 / 2 + K, K) * W + s]);
     }
 }
 
@@ -231,29 +364,32 @@ __global__ void __launch_bounds__(NT) k_cols_inv(const cplx_t<R> *__restrict__ g
 // directly: each cell of the strip is the fixed-order sum that the combine
 // pass would write (its tile's chunks, then the halo rows/columns of the
 // tiles above, left and above-left), so the combined grid never goes to HBM.
-template <typename R, int K, int T>
+template <typename R, int KT, int T>
 __global__ void __launch_bounds__(NT) k_cols_inv_part(const cplx_t<R> *__restrict__ gpart,
                                                       const int32_t *__restrict__ tile_first,
                                                       const int32_t *__restrict__ tile_n, cplx_t<R> *__restrict__ tmp,
-                                                      const cplx_t<R> *__restrict__ tw, int L,
+                                                      const cplx_t<R> *__restrict__ tw, int L0, int K1,
                                                       const int32_t *__restrict__ strips,
-                                                      const uint8_t *__restrict__ rowmask) {
+                                                      const uint8_t *__restrict__ rowmask, PassArgs pa) {
     using C = cplx_t<R>;
-    constexpr int W = cols_per_cta<R>(K);
-    constexpr int E = T + 8, NTL = K / T;
+    constexpr int WT = cols_ct<R, KT>();
+    constexpr int E = T + 8;
+    const int K = KT ? KT : pa.pl.K, W = KT ? WT : pa.nseq;
+    const int nt0 = K / T, nt1 = K1 / T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
-    const C *tws = stage_twiddles<R, W, K>(buf, tw);
+    C *buf2 = buf + W * K;
+    const C *tws = KT ? stage_twiddles<R, WT, KT ? KT : 1>(buf, tw) : tw;
     const int c0 = strips[blockIdx.x];
     for (int e = threadIdx.x; e < W * K; e += NT) {
-        const int s = e % W, r = e / W;   // r: stored (centred) row
+        const int r = e / W, s = e - r * W;   // r: stored (centred) row
         C acc{0, 0};
         if (rowmask[r]) {
-            const int t0 = r / T, up = (t0 + NTL - 1) % NTL;
-            const int t1 = (c0 + s) / T, left = (t1 + NTL - 1) % NTL;
-            const int lr = r % T, lc = (c0 + s) % T;
+            const int t0 = r / T, up = t0 == 0 ? nt0 - 1 : t0 - 1;
+            const int t1 = (c0 + s) / T, left = t1 == 0 ? nt1 - 1 : t1 - 1;
+            const int lr = r - t0 * T, lc = c0 + s - t1 * T;
             auto add = [&](int tt0, int tt1, int rr, int cc) {
-                const int t = tt0 * NTL + tt1;
+                const int t = tt0 * nt1 + tt1;
                 const int f = tile_first[t], n = tile_n[t];
 #pragma unroll 4
                 for (int k = 0; k < n; ++k) {
@@ -267,42 +403,38 @@ __global__ void __launch_bounds__(NT) k_cols_inv_part(const cplx_t<R> *__restric
             if (lc < 8) add(t0, left, lr, lc + T);
             if (lr < 8 && lc < 8) add(up, left, lr + T, lc + T);
         }
-        buf[((r + K / 2) & (K - 1)) * W + s] = cconj(acc);
+        buf[wrapK(r + K / 2, K) * W + s] = cconj(acc);
     }
     __syncthreads();
-    fft_smem<R, K, W, NT, true>(buf, tws);
-    for (int e = threadIdx.x; e < W * L; e += NT) {
-        int s = e % W, n0 = e / W;
-        int pos = (n0 - L / 2 + K) & (K - 1);
-        tmp[(int64_t)n0 * K + c0 + s] = cconj(buf[pos * W + s]);
+    const C *out = run_fft<R, KT, WT, true>(buf, buf2, tws, W, pa.pl, tw);
+    for (int e = threadIdx.x; e < W * L0; e += NT) {
+        const int n0 = e / W, s = e - n0 * W;
+        tmp[(int64_t)n0 * K1 + c0 + s] = cconj(out[wrapK(n0 - L0 / 2 + K, K) * W + s]);
     }
 }
 
-// inverse row pass: img[n0][n1] = s0 s1 Re(F^H along axis 1 of tmp)[n0][(n1 - L/2) mod K]
-template <typename R, int K>
+// inverse row pass: img[n0][n1] = s0 s1 Re(F^H along axis 1 of tmp)[n0][(n1 - L1/2) mod K1]
+template <typename R, int KT>
 __global__ void __launch_bounds__(NT) k_rows_inv(const cplx_t<R> *__restrict__ tmp, R *__restrict__ img,
                                                  const cplx_t<R> *__restrict__ tw, const R *__restrict__ s0,
-                                                 const R *__restrict__ s1, int L) {
+                                                 const R *__restrict__ s1, int L0, int L1, PassArgs pa) {
     using C = cplx_t<R>;
-    constexpr int B = rows_per_cta<R>(K);
+    constexpr int BT = rows_ct<R, KT>();
+    const int K = KT ? KT : pa.pl.K, B = KT ? BT : pa.nseq;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
-    const C *tws = stage_twiddles<R, B, K>(buf, tw);
+    C *buf2 = buf + B * K;
+    const C *tws = KT ? stage_twiddles<R, BT, KT ? KT : 1>(buf, tw) : tw;
     const int row0 = blockIdx.x * B;
     for (int e = threadIdx.x; e < B * K; e += NT) {
-        int s = e / K, c = e % K, n0 = row0 + s;
-        C val = C{0, 0};
-        if (n0 < L) val = cconj(tmp[(int64_t)n0 * K + c]);
-        buf[s * K + ((c + K / 2) & (K - 1))] = val;
+        const int s = e / K, c = e - s * K, n0 = row0 + s;
+        buf[s * K + wrapK(c + K / 2, K)] = n0 < L0 ? cconj(tmp[(int64_t)n0 * K + c]) : C{0, 0};
     }
     __syncthreads();
-    fft_smem<R, K, B, NT, false>(buf, tws);
-    for (int e = threadIdx.x; e < B * L; e += NT) {
-        int s = e / L, n1 = e % L, n0 = row0 + s;
-        if (n0 < L) {
-            int pos = (n1 - L / 2 + K) & (K - 1);
-            img[(int64_t)n0 * L + n1] = s0[n0] * s1[n1] * buf[s * K + pos].x;
-        }
+    const C *out = run_fft<R, KT, BT, false>(buf, buf2, tws, B, pa.pl, tw);
+    for (int e = threadIdx.x; e < B * L1; e += NT) {
+        const int s = e / L1, n1 = e - s * L1, n0 = row0 + s;
+        if (n0 < L0) img[(int64_t)n0 * L1 + n1] = s0[n0] * s1[n1] * out[s * K + wrapK(n1 - L1 / 2 + K, K)].x;
     }
 }
 
@@ -312,198 +444,227 @@ __global__ void __launch_bounds__(NT) k_rows_inv(const cplx_t<R> *__restrict__ t
 // pixels (primal_pixel), and the forward row pass of the new xt into
 // tmp_fwd (the next iteration's first FFT pass), with the FP64 statistics
 // partials of the CTA.  The join of the prior branch precedes it (ut, u0).
-template <typename R, int K>
-__global__ void __launch_bounds__(NT) k_rows_primal(const cplx_t<R> *__restrict__ tmp_inv, cplx_t<R> *__restrict__ tmp_fwd,
-                                                    const cplx_t<R> *__restrict__ tw, const R *__restrict__ s0,
-                                                    const R *__restrict__ s1, const uint8_t *__restrict__ colmask,
-                                                    PrimalArgs<R> P, double *__restrict__ part) {
+template <typename R, int KT>
+__global__ void __launch_bounds__(NT) k_rows_primal(const cplx_t<R> *__restrict__ tmp_inv,
+                                                    cplx_t<R> *__restrict__ tmp_fwd, const cplx_t<R> *__restrict__ tw,
+                                                    const R *__restrict__ s0, const R *__restrict__ s1,
+                                                    const uint8_t *__restrict__ colmask, PrimalArgs<R> P,
+                                                    double *__restrict__ part, int L0, int L1, PassArgs pa) {
     using C = cplx_t<R>;
-    constexpr int B = rows_per_cta<R>(K), L = K / 2, PER = B * L / NT;
-    static_assert(B * L % NT == 0, "pixels per thread");
+    constexpr int BT = rows_ct<R, KT>();
+    const int K = KT ? KT : pa.pl.K, B = KT ? BT : pa.nseq;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
-    const C *tws = stage_twiddles<R, B, K>(buf, tw);
+    C *buf2 = buf + B * K;
+    const C *tws = KT ? stage_twiddles<R, BT, KT ? KT : 1>(buf, tw) : tw;
     const int row0 = blockIdx.x * B;
     for (int e = threadIdx.x; e < B * K; e += NT) {
-        const int s = e / K, c = e % K, n0 = row0 + s;
-        buf[s * K + ((c + K / 2) & (K - 1))] = n0 < L ? cconj(tmp_inv[(int64_t)n0 * K + c]) : C{0, 0};
+        const int s = e / K, c = e - s * K, n0 = row0 + s;
+        buf[s * K + wrapK(c + K / 2, K)] = n0 < L0 ? cconj(tmp_inv[(int64_t)n0 * K + c]) : C{0, 0};
     }
     __syncthreads();
-    fft_smem<R, K, B, NT, false>(buf, tws);
+    C *out = run_fft<R, KT, BT, false>(buf, buf2, tws, B, pa.pl, tw);
     PrimalSums<R> acc;
-    R xtn[PER];
+    if constexpr (KT != 0) {
+        // the new xt stays in registers while the buffer is cleared
+        constexpr int LT = KT / 2, PER = BT * LT / NT;
+        static_assert(BT * LT % NT == 0, "pixels per thread");
+        R xtn[PER];
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int e = threadIdx.x + k * NT, s = e / L, n1 = e % L, n0 = row0 + s;
-        xtn[k] = R(0);
-        if (n0 < L) {
-            const R g = s0[n0] * s1[n1] * buf[s * K + ((n1 - L / 2 + K) & (K - 1))].x;
-            xtn[k] = primal_pixel(P, (int64_t)n0 * L + n1, g, acc);
+        for (int k = 0; k < PER; ++k) {
+            const int e = threadIdx.x + k * NT, s = e / LT, n1 = e % LT, n0 = row0 + s;
+            xtn[k] = R(0);
+            if (n0 < L0) {
+                const R g = s0[n0] * s1[n1] * out[s * K + ((n1 - LT / 2 + K) & (K - 1))].x;
+                xtn[k] = primal_pixel(P, (int64_t)n0 * LT + n1, g, acc);
+            }
         }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < B * K; e += NT) buf[e] = C{0, 0};
-    __syncthreads();
+        __syncthreads();
+        for (int e = threadIdx.x; e < B * K; e += NT) buf[e] = C{0, 0};
+        __syncthreads();
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int e = threadIdx.x + k * NT, s = e / L, n1 = e % L, n0 = row0 + s;
-        if (n0 < L) buf[s * K + ((n1 - L / 2 + K) & (K - 1))] = C{s0[n0] * s1[n1] * xtn[k], R(0)};
+        for (int k = 0; k < PER; ++k) {
+            const int e = threadIdx.x + k * NT, s = e / LT, n1 = e % LT, n0 = row0 + s;
+            if (n0 < L0) buf[s * K + ((n1 - LT / 2 + K) & (K - 1))] = C{s0[n0] * s1[n1] * xtn[k], R(0)};
+        }
+        __syncthreads();
+    } else {
+        // the mixed-radix core leaves the result in one buffer: the forward
+        // input is built in the other one
+        C *fin = out == buf ? buf2 : buf;
+        for (int e = threadIdx.x; e < B * K; e += NT) fin[e] = C{0, 0};
+        __syncthreads();
+        for (int e = threadIdx.x; e < B * L1; e += NT) {
+            const int s = e / L1, n1 = e - s * L1, n0 = row0 + s;
+            if (n0 < L0) {
+                const int pos = wrapK(n1 - L1 / 2 + K, K);
+                const R g = s0[n0] * s1[n1] * out[s * K + pos].x;
+                const R xtn = primal_pixel(P, (int64_t)n0 * L1 + n1, g, acc);
+                fin[s * K + pos] = C{s0[n0] * s1[n1] * xtn, R(0)};
+            }
+        }
+        __syncthreads();
+        buf = fin;
+        buf2 = out;
     }
-    __syncthreads();
-    fft_smem<R, K, B, NT, false>(buf, tws);
+    const C *res = run_fft<R, KT, BT, false>(buf, buf2, tws, B, pa.pl, tw);
     for (int e = threadIdx.x; e < B * K; e += NT) {
-        const int s = e / K, c = e % K, n0 = row0 + s;
-        if (n0 < L && colmask[c]) tmp_fwd[(int64_t)n0 * K + c] = buf[s * K + ((c + K / 2) & (K - 1))];
+        const int s = e / K, c = e - s * K, n0 = row0 + s;
+        if (n0 < L0 && colmask[c]) tmp_fwd[(int64_t)n0 * K + c] = res[s * K + wrapK(c + K / 2, K)];
     }
     acc.write(part + 3 * (int64_t)blockIdx.x);
 }
 
-template <typename R, int K> struct Pass {
-    static constexpr int B = rows_per_cta<R>(K), W = cols_per_cta<R>(K);
-    // dynamic shared memory of the row and column passes (per device)
-    static int attrs() {
-        const int shr = (int)pass_smem<R>(B, K), shc = (int)pass_smem<R>(W, K);
-        PPD_CHECK(smem_attr((const void *)k_rows_fwd<R, K>, shr));
-        PPD_CHECK(smem_attr((const void *)k_rows_inv<R, K>, shr));
-        PPD_CHECK(smem_attr((const void *)k_rows_primal<R, K>, shr));
-        PPD_CHECK(smem_attr((const void *)k_cols_fwd<R, K>, shc));
-        PPD_CHECK(smem_attr((const void *)k_cols_inv<R, K>, shc));
-        PPD_CHECK(smem_attr((const void *)k_cols_inv_part<R, K, 16>, shc));
-        return smem_attr((const void *)k_cols_inv_part<R, K, 32>, shc);
+// ------------------------------------------------------------ launchers
+// Sequences per CTA of the mixed-radix passes: rows: enough for ~1024
+// points; columns: the largest power of two <= 1024 / K (at most 32, so
+// that it divides K1, a multiple of 32).
+int any_rows(int K) { return std::max(1, 1024 / K); }
+int any_cols(int K) {
+    int w = 1;
+    while (w < 32 && 2 * w * K <= 1024) w *= 2;
+    return w;
+}
+
+// Row passes have the row length K1, column passes the column length K0.
+// RowPass / ColPass hold the launches of one core (KT) and precision.
+template <typename R, int KT> struct RowPass {
+    static constexpr int BT = rows_ct<R, KT>();
+    static int nseq(const ppd_ctx *c) { return KT ? BT : any_rows(c->K1); }
+    static size_t smem(const ppd_ctx *c) {
+        return KT ? pass_smem<R>(BT, KT) : (size_t)2 * nseq(c) * c->K1 * 2 * sizeof(R);
     }
-    static int rows_fwd(ppd_ctx *c, const R *x, cudaStream_t s) {
-        PPD_CHECK(attrs());
+    static PassArgs args(const ppd_ctx *c) { return PassArgs{c->plan1, nseq(c)}; }
+    static unsigned blocks(const ppd_ctx *c) { return (unsigned)((c->L0 + nseq(c) - 1) / nseq(c)); }
+    static const cplx_t<R> *tw(const ppd_ctx *c) { return static_cast<const cplx_t<R> *>(c->tw1); }
+    static int fwd(ppd_ctx *c, const R *x, cudaStream_t s) {
+        const int sh = (int)smem(c);
+        PPD_CHECK(smem_attr((const void *)k_rows_fwd<R, KT>, sh));
         int site;
         PPD_CHECK(launch_begin(c, "fft_fwd_rows", s, &site));
-        k_rows_fwd<R, K><<<(c->L0 + B - 1) / B, NT, pass_smem<R>(B, K), s>>>(
-            x, static_cast<cplx_t<R> *>(c->fft_tmp), static_cast<const cplx_t<R> *>(c->tw0),
-            static_cast<const R *>(c->deap0), static_cast<const R *>(c->deap1), c->L0, c->col_fwd);
+        k_rows_fwd<R, KT><<<blocks(c), NT, sh, s>>>(x, static_cast<cplx_t<R> *>(c->fft_tmp), tw(c),
+                                                   static_cast<const R *>(c->deap0),
+                                                   static_cast<const R *>(c->deap1), c->L0, c->L1, c->col_fwd,
+                                                   args(c));
         return launch_end(c, site, s);
     }
-    static int cols_fwd(ppd_ctx *c, cplx_t<R> *grid, cudaStream_t s) {
-        PPD_CHECK(attrs());
-        if (c->n_fwd_strips == 0) return PPD_OK;
-        int site;
-        PPD_CHECK(launch_begin(c, "fft_fwd_cols", s, &site));
-        k_cols_fwd<R, K><<<c->n_fwd_strips, NT, pass_smem<R>(W, K), s>>>(
-            static_cast<const cplx_t<R> *>(c->fft_tmp), grid, static_cast<const cplx_t<R> *>(c->tw0), c->L0,
-            c->fwd_strips, c->row_fwd);
-        return launch_end(c, site, s);
-    }
-    static int cols_inv(ppd_ctx *c, const cplx_t<R> *grid, cudaStream_t s) {
-        PPD_CHECK(attrs());
-        if (c->n_inv_strips == 0) return PPD_OK;
-        int site;
-        PPD_CHECK(launch_begin(c, "fft_inv_cols", s, &site));
-        k_cols_inv<R, K><<<c->n_inv_strips, NT, pass_smem<R>(W, K), s>>>(
-            grid, static_cast<cplx_t<R> *>(c->fft_tmp_inv), static_cast<const cplx_t<R> *>(c->tw0), c->L0,
-            c->inv_strips, c->row_inv);
-        return launch_end(c, site, s);
-    }
-    static int cols_inv_part(ppd_ctx *c, cudaStream_t s) {
-        PPD_CHECK(attrs());
-        if (c->n_inv_strips == 0) return PPD_OK;
-        int site;
-        PPD_CHECK(launch_begin(c, "fft_inv_cols", s, &site));
-        const cplx_t<R> *gp = static_cast<const cplx_t<R> *>(c->gpart);
-        cplx_t<R> *out = static_cast<cplx_t<R> *>(c->fft_tmp_inv);
-        const cplx_t<R> *tw = static_cast<const cplx_t<R> *>(c->tw0);
-        if (c->T == 16)
-            k_cols_inv_part<R, K, 16><<<c->n_inv_strips, NT, pass_smem<R>(W, K), s>>>(
-                gp, c->ch.tile_first, c->ch.tile_n, out, tw, c->L0, c->inv_strips, c->row_inv);
-        else
-            k_cols_inv_part<R, K, 32><<<c->n_inv_strips, NT, pass_smem<R>(W, K), s>>>(
-                gp, c->ch.tile_first, c->ch.tile_n, out, tw, c->L0, c->inv_strips, c->row_inv);
-        return launch_end(c, site, s);
-    }
-    static int rows_inv(ppd_ctx *c, R *img, cudaStream_t s) {
-        PPD_CHECK(attrs());
+    static int inv(ppd_ctx *c, R *img, cudaStream_t s) {
+        const int sh = (int)smem(c);
+        PPD_CHECK(smem_attr((const void *)k_rows_inv<R, KT>, sh));
         int site;
         PPD_CHECK(launch_begin(c, "fft_inv_rows", s, &site));
-        k_rows_inv<R, K><<<(c->L0 + B - 1) / B, NT, pass_smem<R>(B, K), s>>>(
-            static_cast<const cplx_t<R> *>(c->fft_tmp_inv), img, static_cast<const cplx_t<R> *>(c->tw0),
-            static_cast<const R *>(c->deap0), static_cast<const R *>(c->deap1), c->L0);
+        k_rows_inv<R, KT><<<blocks(c), NT, sh, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp_inv), img, tw(c),
+                                                   static_cast<const R *>(c->deap0),
+                                                   static_cast<const R *>(c->deap1), c->L0, c->L1, args(c));
         return launch_end(c, site, s);
     }
-    static int rows_primal(ppd_ctx *c, cudaStream_t s) {
-        PPD_CHECK(attrs());
+    static int primal(ppd_ctx *c, cudaStream_t s) {
+        const int sh = (int)smem(c);
+        PPD_CHECK(smem_attr((const void *)k_rows_primal<R, KT>, sh));
         int site;
         PPD_CHECK(launch_begin(c, "rows_primal", s, &site));
-        const int n = (c->L0 + B - 1) / B;
-        k_rows_primal<R, K><<<n, NT, pass_smem<R>(B, K), s>>>(
-            static_cast<const cplx_t<R> *>(c->fft_tmp_inv), static_cast<cplx_t<R> *>(c->fft_tmp),
-            static_cast<const cplx_t<R> *>(c->tw0), static_cast<const R *>(c->deap0),
-            static_cast<const R *>(c->deap1), c->col_fwd, primal_args<R>(c), c->prim_part);
-        c->n_stat_parts = n;
+        const unsigned n = blocks(c);
+        k_rows_primal<R, KT><<<n, NT, sh, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp_inv),
+                                               static_cast<cplx_t<R> *>(c->fft_tmp), tw(c),
+                                               static_cast<const R *>(c->deap0), static_cast<const R *>(c->deap1),
+                                               c->col_fwd, primal_args<R>(c), c->prim_part, c->L0, c->L1, args(c));
+        c->n_stat_parts = (int)n;
         return launch_end(c, site, s);
+    }
+};
+
+template <typename R, int KT> struct ColPass {
+    static constexpr int WT = cols_ct<R, KT>();
+    static int nseq(const ppd_ctx *c) { return KT ? WT : any_cols(c->K0); }
+    static size_t smem(const ppd_ctx *c) {
+        return KT ? pass_smem<R>(WT, KT) : (size_t)2 * nseq(c) * c->K0 * 2 * sizeof(R);
+    }
+    static PassArgs args(const ppd_ctx *c) { return PassArgs{c->plan0, nseq(c)}; }
+    static const cplx_t<R> *tw(const ppd_ctx *c) { return static_cast<const cplx_t<R> *>(c->tw0); }
+    static int fwd(ppd_ctx *c, cplx_t<R> *grid, cudaStream_t s) {
+        if (c->n_fwd_strips == 0) return PPD_OK;
+        const int sh = (int)smem(c);
+        PPD_CHECK(smem_attr((const void *)k_cols_fwd<R, KT>, sh));
+        int site;
+        PPD_CHECK(launch_begin(c, "fft_fwd_cols", s, &site));
+        k_cols_fwd<R, KT><<<c->n_fwd_strips, NT, sh, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp), grid, tw(c),
+                                                         c->L0, c->K1, c->fwd_strips, c->row_fwd, args(c));
+        return launch_end(c, site, s);
+    }
+    static int inv(ppd_ctx *c, const cplx_t<R> *grid, cudaStream_t s) {
+        if (c->n_inv_strips == 0) return PPD_OK;
+        const int sh = (int)smem(c);
+        PPD_CHECK(smem_attr((const void *)k_cols_inv<R, KT>, sh));
+        int site;
+        PPD_CHECK(launch_begin(c, "fft_inv_cols", s, &site));
+        k_cols_inv<R, KT><<<c->n_inv_strips, NT, sh, s>>>(grid, static_cast<cplx_t<R> *>(c->fft_tmp_inv), tw(c),
+                                                         c->L0, c->K1, c->inv_strips, c->row_inv, args(c));
+        return launch_end(c, site, s);
+    }
+    template <int T> static int inv_part_t(ppd_ctx *c, cudaStream_t s) {
+        const int sh = (int)smem(c);
+        PPD_CHECK(smem_attr((const void *)k_cols_inv_part<R, KT, T>, sh));
+        int site;
+        PPD_CHECK(launch_begin(c, "fft_inv_cols", s, &site));
+        k_cols_inv_part<R, KT, T><<<c->n_inv_strips, NT, sh, s>>>(
+            static_cast<const cplx_t<R> *>(c->gpart), c->ch.tile_first, c->ch.tile_n,
+            static_cast<cplx_t<R> *>(c->fft_tmp_inv), tw(c), c->L0, c->K1, c->inv_strips, c->row_inv, args(c));
+        return launch_end(c, site, s);
+    }
+    static int inv_part(ppd_ctx *c, cudaStream_t s) {
+        if (c->n_inv_strips == 0) return PPD_OK;
+        return c->T == 16 ? inv_part_t<16>(c, s) : inv_part_t<32>(c, s);
     }
 };
 
 }  // namespace
 
-#define PPD_FFT_SIZES(X) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
-#define PPD_FFT_CASE(KK, CALL) case KK: return Pass<R, KK>::CALL;
+// Power-of-two lengths take the compile-time core; other 5-smooth lengths
+// the mixed-radix one (KT = 0).
+#define PPD_FFT_DISPATCH(KLEN, PASS, CALL)                  \
+    switch (KLEN) {                                         \
+        case 32: return PASS<R, 32>::CALL;                  \
+        case 64: return PASS<R, 64>::CALL;                  \
+        case 128: return PASS<R, 128>::CALL;                \
+        case 256: return PASS<R, 256>::CALL;                \
+        case 512: return PASS<R, 512>::CALL;                \
+        case 1024: return PASS<R, 1024>::CALL;              \
+        case 2048: return PASS<R, 2048>::CALL;              \
+        case 4096: return PASS<R, 4096>::CALL;              \
+        case 8192: return PASS<R, 8192>::CALL;              \
+        default: return PASS<R, 0>::CALL;                   \
+    }
 
 // forward row pass of x into the FFT temporary (first half of F Z x)
 template <typename R> int fft_forward_rows(ppd_ctx *c, const R *x, cudaStream_t s) {
     c->xt_rows_valid = false;
-    switch (c->K0) {
-#define X(KK) PPD_FFT_CASE(KK, rows_fwd(c, x, s))
-        PPD_FFT_SIZES(X)
-#undef X
-        default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
-    }
+    PPD_FFT_DISPATCH(c->K1, RowPass, fwd(c, x, s))
 }
 
 // forward column pass from the FFT temporary to the grid (second half of F Z x)
 template <typename R> int fft_forward_cols(ppd_ctx *c, cplx_t<R> *grid, cudaStream_t s) {
-    switch (c->K0) {
-#define X(KK) PPD_FFT_CASE(KK, cols_fwd(c, grid, s))
-        PPD_FFT_SIZES(X)
-#undef X
-        default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
-    }
+    PPD_FFT_DISPATCH(c->K0, ColPass, fwd(c, grid, s))
 }
 
 // inverse column pass of a combined grid into the inverse temporary
 template <typename R> int fft_inverse_cols(ppd_ctx *c, const cplx_t<R> *grid, cudaStream_t s) {
-    switch (c->K0) {
-#define X(KK) PPD_FFT_CASE(KK, cols_inv(c, grid, s))
-        PPD_FFT_SIZES(X)
-#undef X
-        default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
-    }
+    PPD_FFT_DISPATCH(c->K0, ColPass, inv(c, grid, s))
 }
 
 // inverse column pass summing the gridding's partial tiles while loading
 // (the combine pass fused in)
 template <typename R> int fft_inverse_cols_partials(ppd_ctx *c, cudaStream_t s) {
-    switch (c->K0) {
-#define X(KK) PPD_FFT_CASE(KK, cols_inv_part(c, s))
-        PPD_FFT_SIZES(X)
-#undef X
-        default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
-    }
+    PPD_FFT_DISPATCH(c->K0, ColPass, inv_part(c, s))
 }
 
 // inverse row pass into an image (second half of Z^T F^H)
 template <typename R> int fft_inverse_rows(ppd_ctx *c, R *img, cudaStream_t s) {
-    switch (c->K0) {
-#define X(KK) PPD_FFT_CASE(KK, rows_inv(c, img, s))
-        PPD_FFT_SIZES(X)
-#undef X
-        default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
-    }
+    PPD_FFT_DISPATCH(c->K1, RowPass, inv(c, img, s))
 }
 
 // inverse row pass + primal step + forward row pass of the new xt
 template <typename R> int rows_primal(ppd_ctx *c, cudaStream_t s) {
-    switch (c->K0) {
-#define X(KK) PPD_FFT_CASE(KK, rows_primal(c, s))
-        PPD_FFT_SIZES(X)
-#undef X
-        default: return fail(PPD_ERR_UNSUPPORTED, "FFT size not supported");
-    }
+    PPD_FFT_DISPATCH(c->K1, RowPass, primal(c, s))
 }
 
 template <typename R> int fft_forward(ppd_ctx *c, const R *x, cplx_t<R> *grid, cudaStream_t s) {
@@ -516,8 +677,7 @@ template <typename R> int fft_inverse(ppd_ctx *c, const cplx_t<R> *grid, R *img,
     return fft_inverse_rows<R>(c, img, s);
 }
 
-#undef PPD_FFT_CASE
-#undef PPD_FFT_SIZES
+#undef PPD_FFT_DISPATCH
 
 #define PPD_FFT_INST(R)                                                                                         \
     template int fft_forward<R>(ppd_ctx *, const R *, cplx_t<R> *, cudaStream_t);                              \
@@ -532,16 +692,47 @@ PPD_FFT_INST(float)
 PPD_FFT_INST(double)
 #undef PPD_FFT_INST
 
+// FFT plan of length K: radices 5, 3, then 4, then a last 2 (an empty plan
+// if K has another prime factor).
+FftPlan make_fft_plan(int K) {
+    FftPlan p{};
+    p.K = K;
+    int k = K;
+    for (int r : {5, 3})
+        while (k % r == 0 && p.ns < FftPlan::MAX_STAGES) {
+            p.rad[p.ns++] = r;
+            k /= r;
+        }
+    while (k % 4 == 0 && p.ns < FftPlan::MAX_STAGES) {
+        p.rad[p.ns++] = 4;
+        k /= 4;
+    }
+    if (k == 2 && p.ns < FftPlan::MAX_STAGES) {
+        p.rad[p.ns++] = 2;
+        k = 1;
+    }
+    if (k != 1) p.ns = 0;
+    return p;
+}
+
+bool fft_length_supported(int K, bool fp64) {
+    if (K < 32 || K > 8192 || make_fft_plan(K).ns == 0) return false;
+    const bool pow2 = (K & (K - 1)) == 0;
+    // two buffers of the mixed-radix core per CTA: at most 128 KB
+    return pow2 || (size_t)2 * K * 2 * (fp64 ? 8 : 4) <= 128 * 1024;
+}
+
 // Column strips (W columns each, W as the column passes use) that contain a
 // marked column, and the row / column masks, uploaded for the pruned passes.
 int fft_plan_pruning(ppd_ctx *c, const std::vector<char> &rows_fwd, const std::vector<char> &cols_fwd,
                      const std::vector<char> &rows_inv, const std::vector<char> &cols_inv) {
-    const int K = c->K0;
-    const int W = c->is_f32 ? cols_per_cta<float>(K) : cols_per_cta<double>(K);
+    const int K0 = c->K0, K1 = c->K1;
+    const bool p2 = (K0 & (K0 - 1)) == 0;
+    const int W = !p2 ? any_cols(K0) : c->is_f32 ? cols_per_cta<float>(K0) : cols_per_cta<double>(K0);
     std::vector<int32_t> fs, is;
-    for (int s0 = 0; s0 < K; s0 += W) {
+    for (int s0 = 0; s0 < K1; s0 += W) {
         bool f = false, i = false;
-        for (int j = s0; j < s0 + W; ++j) {
+        for (int j = s0; j < s0 + W && j < K1; ++j) {
             f = f || cols_fwd[j];
             i = i || cols_inv[j];
         }
@@ -554,19 +745,19 @@ int fft_plan_pruning(ppd_ctx *c, const std::vector<char> &rows_fwd, const std::v
     c->n_inv_strips = (int)is.size();
     if (!fs.empty()) PPD_CUDA(cudaMemcpy(c->fwd_strips, fs.data(), fs.size() * 4, cudaMemcpyHostToDevice));
     if (!is.empty()) PPD_CUDA(cudaMemcpy(c->inv_strips, is.data(), is.size() * 4, cudaMemcpyHostToDevice));
-    PPD_CUDA(cudaMemcpy(c->row_fwd, rf.data(), K, cudaMemcpyHostToDevice));
-    PPD_CUDA(cudaMemcpy(c->row_inv, ri.data(), K, cudaMemcpyHostToDevice));
-    PPD_CUDA(cudaMemcpy(c->col_fwd, cf.data(), K, cudaMemcpyHostToDevice));
+    PPD_CUDA(cudaMemcpy(c->row_fwd, rf.data(), K0, cudaMemcpyHostToDevice));
+    PPD_CUDA(cudaMemcpy(c->row_inv, ri.data(), K0, cudaMemcpyHostToDevice));
+    PPD_CUDA(cudaMemcpy(c->col_fwd, cf.data(), K1, cudaMemcpyHostToDevice));
     // the inverse column pass writes only its strips: the rest of its output
     // stays zero; the forward row pass writes only marked columns
-    PPD_CUDA(cudaMemset(c->fft_tmp_inv, 0, (size_t)c->L0 * K * 2 * c->rsz));
-    PPD_CUDA(cudaMemset(c->fft_tmp, 0, (size_t)c->L0 * K * 2 * c->rsz));
+    PPD_CUDA(cudaMemset(c->fft_tmp_inv, 0, (size_t)c->L0 * K1 * 2 * c->rsz));
+    PPD_CUDA(cudaMemset(c->fft_tmp, 0, (size_t)c->L0 * K1 * 2 * c->rsz));
     return PPD_OK;
 }
 
-// Twiddles exp(-2 pi i m / K), m < K, computed in double on the host.
-int make_twiddles(ppd_ctx *c) {
-    const int K = c->K0;
+// Twiddles exp(-2 pi i m / K), m < K, computed in double on the host, for
+// the column length K0 (tw0) and the row length K1 (tw1).
+static int upload_twiddles(ppd_ctx *c, int K, void *dst) {
     std::vector<double> t(2 * (size_t)K);
     for (int m = 0; m < K; ++m) {
         double a = -2.0 * M_PI * (double)m / (double)K;
@@ -575,17 +766,23 @@ int make_twiddles(ppd_ctx *c) {
     }
     if (c->is_f32) {
         std::vector<float> f(t.begin(), t.end());
-        PPD_CUDA(cudaMemcpy(c->tw0, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+        PPD_CUDA(cudaMemcpy(dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
     } else {
-        PPD_CUDA(cudaMemcpy(c->tw0, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
+        PPD_CUDA(cudaMemcpy(dst, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
     return PPD_OK;
 }
 
+int make_twiddles(ppd_ctx *c) {
+    c->plan0 = make_fft_plan(c->K0);
+    c->plan1 = make_fft_plan(c->K1);
+    PPD_CHECK(upload_twiddles(c, c->K0, c->tw0));
+    return upload_twiddles(c, c->K1, c->tw1);
+}
+
 // Z's scaling s(n) = 1 / psi_hat((n - L/2)/K), psi_hat(f) = (J / I0(beta)) sinh(q)/q,
 // q = sqrt(beta^2 - (pi J f)^2): the Fourier transform of the Kaiser-Bessel kernel.
-int make_deapodisation(ppd_ctx *c) {
-    const int L = c->L0, K = c->K0;
+static int upload_deapodisation(ppd_ctx *c, int L, int K, void *dst) {
     const double J = KB_J, beta = c->beta, i0b = std::cyl_bessel_i(0.0, beta);
     std::vector<double> s(L);
     for (int n = 0; n < L; ++n) {
@@ -595,13 +792,16 @@ int make_deapodisation(ppd_ctx *c) {
     }
     if (c->is_f32) {
         std::vector<float> f(s.begin(), s.end());
-        PPD_CUDA(cudaMemcpy(c->deap0, f.data(), L * sizeof(float), cudaMemcpyHostToDevice));
-        PPD_CUDA(cudaMemcpy(c->deap1, f.data(), L * sizeof(float), cudaMemcpyHostToDevice));
+        PPD_CUDA(cudaMemcpy(dst, f.data(), L * sizeof(float), cudaMemcpyHostToDevice));
     } else {
-        PPD_CUDA(cudaMemcpy(c->deap0, s.data(), L * sizeof(double), cudaMemcpyHostToDevice));
-        PPD_CUDA(cudaMemcpy(c->deap1, s.data(), L * sizeof(double), cudaMemcpyHostToDevice));
+        PPD_CUDA(cudaMemcpy(dst, s.data(), L * sizeof(double), cudaMemcpyHostToDevice));
     }
     return PPD_OK;
+}
+
+int make_deapodisation(ppd_ctx *c) {
+    PPD_CHECK(upload_deapodisation(c, c->L0, c->K0, c->deap0));
+    return upload_deapodisation(c, c->L1, c->K1, c->deap1);
 }
 
 }  // namespace ppd

@@ -32,12 +32,52 @@ __global__ void k_reduce3(const double *__restrict__ part, int n, double *__rest
     cta_sum3<NT>(a, b, c, out);
 }
 
+// Global stopping rule of Algorithm 3 in FP64: relative variation
+// sqrt(||x - x_prev||^2 / ||x||^2) below tol and every block residual
+// sqrt(resid2_j) within fac eps_j.  One warp.
+__global__ void k_stop_flag(const double *__restrict__ stat, const double *__restrict__ resid2,
+                            const double *__restrict__ eps, int d, double tol, double fac, int *__restrict__ flag) {
+    bool ok = true;
+    for (int j = threadIdx.x; j < d; j += 32) ok = ok && sqrt(resid2[j]) <= fac * eps[j];
+    ok = __all_sync(0xffffffffu, ok);
+    if (threadIdx.x == 0) {
+        const bool rv = stat[1] > 0 && sqrt(stat[0] / stat[1]) < tol;
+        *flag = (ok && rv) ? 1 : 0;
+    }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(NT) k_sumsq(const R *__restrict__ in, int64_t n, double *__restrict__ part) {
     double s = 0;
     for (int64_t e = blockIdx.x * (int64_t)NT + threadIdx.x; e < n; e += (int64_t)gridDim.x * NT) {
         const double v = (double)in[e];
         s += v * v;
+    }
+    cta_sum3<NT>(s, 0.0, 0.0, part + 3 * (int64_t)blockIdx.x);
+}
+
+// Lanczos steps: w -= beta vp with the partials of <w, v>; w -= alpha v
+// with the partials of ||w||^2 (FP64 per-CTA sums, fixed order).
+template <typename R>
+__global__ void __launch_bounds__(NT) k_lz_dot(R *__restrict__ w, const R *__restrict__ vp, const R *__restrict__ v,
+                                               int64_t n, R beta, double *__restrict__ part) {
+    double s = 0;
+    for (int64_t e = blockIdx.x * (int64_t)NT + threadIdx.x; e < n; e += (int64_t)gridDim.x * NT) {
+        const R we = w[e] - beta * vp[e];
+        w[e] = we;
+        s += (double)we * (double)v[e];
+    }
+    cta_sum3<NT>(s, 0.0, 0.0, part + 3 * (int64_t)blockIdx.x);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(NT) k_lz_orth(R *__restrict__ w, const R *__restrict__ v, int64_t n, R alpha,
+                                                double *__restrict__ part) {
+    double s = 0;
+    for (int64_t e = blockIdx.x * (int64_t)NT + threadIdx.x; e < n; e += (int64_t)gridDim.x * NT) {
+        const R we = w[e] - alpha * v[e];
+        w[e] = we;
+        s += (double)we * (double)we;
     }
     cta_sum3<NT>(s, 0.0, 0.0, part + 3 * (int64_t)blockIdx.x);
 }
@@ -94,6 +134,13 @@ int reduce_primal_stats(ppd_ctx *c, cudaStream_t s) {
     return launch_end(c, site, s);
 }
 
+int stop_flag(ppd_ctx *c, double tol, double fac, cudaStream_t s) {
+    int site;
+    PPD_CHECK(launch_begin(c, "stop_rule", s, &site));
+    k_stop_flag<<<1, 32, 0, s>>>(c->stat_out, c->resid2, c->eps_d, c->d, tol, fac, c->stop_flag);
+    return launch_end(c, site, s);
+}
+
 template <typename R> int sumsq(ppd_ctx *c, const R *in, int64_t n, double *out_dev, cudaStream_t s) {
     int site;
     PPD_CHECK(launch_begin(c, "sumsq", s, &site));
@@ -103,6 +150,32 @@ template <typename R> int sumsq(ppd_ctx *c, const R *in, int64_t n, double *out_
     k_reduce3<<<1, NT, 0, s>>>(c->prim_part, c->n_prim_blocks, out_dev);
     return launch_end(c, site, s);
 }
+
+template <typename R> int lanczos_dot(ppd_ctx *c, R *w, const R *vp, const R *v, double beta, double *out_dev,
+                                      cudaStream_t s) {
+    int site;
+    PPD_CHECK(launch_begin(c, "lanczos", s, &site));
+    k_lz_dot<R><<<c->n_prim_blocks, NT, 0, s>>>(w, vp, v, c->N, (R)beta, c->prim_part);
+    PPD_CHECK(launch_end(c, site, s));
+    PPD_CHECK(launch_begin(c, "stats", s, &site));
+    k_reduce3<<<1, NT, 0, s>>>(c->prim_part, c->n_prim_blocks, out_dev);
+    return launch_end(c, site, s);
+}
+
+template <typename R> int lanczos_orth(ppd_ctx *c, R *w, const R *v, double alpha, double *out_dev, cudaStream_t s) {
+    int site;
+    PPD_CHECK(launch_begin(c, "lanczos", s, &site));
+    k_lz_orth<R><<<c->n_prim_blocks, NT, 0, s>>>(w, v, c->N, (R)alpha, c->prim_part);
+    PPD_CHECK(launch_end(c, site, s));
+    PPD_CHECK(launch_begin(c, "stats", s, &site));
+    k_reduce3<<<1, NT, 0, s>>>(c->prim_part, c->n_prim_blocks, out_dev);
+    return launch_end(c, site, s);
+}
+
+template int lanczos_dot<float>(ppd_ctx *, float *, const float *, const float *, double, double *, cudaStream_t);
+template int lanczos_dot<double>(ppd_ctx *, double *, const double *, const double *, double, double *, cudaStream_t);
+template int lanczos_orth<float>(ppd_ctx *, float *, const float *, double, double *, cudaStream_t);
+template int lanczos_orth<double>(ppd_ctx *, double *, const double *, double, double *, cudaStream_t);
 
 template <typename R> int scale_copy(ppd_ctx *c, const R *in, R *out, int64_t n, double a, cudaStream_t s) {
     int site;

@@ -41,9 +41,13 @@ constexpr int SEXT = TS + MAX_TAPS / 2 - 1;   // synthesis quadrant tile side (1
 static_assert(NT == 4 * TS * TS, "one synthesis output per thread");
 static_assert(2 * TSA % (NT / 32) == 0, "analysis column rows per warp");
 
-// periodic index for power-of-two n (two's complement makes the mask exact
-// for negative i)
-__device__ __forceinline__ int wrap(int i, int n) { return i & (n - 1); }
+// periodic index i mod n (i may be negative); indices inside [0, n) are
+// the common case and skip the division
+__device__ __forceinline__ int wrap(int i, int n) {
+    if ((unsigned)i < (unsigned)n) return i;
+    const int r = i % n;
+    return r < 0 ? r + n : r;
+}
 
 // Filter taps of basis b in registers: h[k] and g[k] = (-1)^k h[F-1-k].
 template <typename R, int F> struct Taps {
@@ -59,18 +63,19 @@ template <typename R, int F> struct Taps {
 
 // ------------------------------------------------------------- analysis
 // One tile of TSA x TSA positions of each of the 4 quadrants of one level,
-// one basis (filter length F).  Rows (axis 1) are filtered into shared
-// memory, then columns (axis 0).  Levels with h < TSA use one tile and the
-// guards skip the wrapped duplicates.
+// one basis (filter length F); the level input is n0 x n1, its quadrants
+// h0 x h1.  Rows (axis 1) are filtered into shared memory, then columns
+// (axis 0).  Tiles reaching past h0 or h1 (levels smaller than a tile, or
+// sides that are not multiples of TSA) skip the positions outside.
 template <typename R, int F>
-__device__ __forceinline__ void ana_tile(const R *__restrict__ src, int in_pitch, int n, int R0, int C0,
+__device__ __forceinline__ void ana_tile(const R *__restrict__ src, int in_pitch, int n0, int n1, int R0, int C0,
                                          R *__restrict__ ll, int last, R *__restrict__ cb,
-                                         const R *__restrict__ wb, int L, int mode, R kappa, int b, R *tin,
+                                         const R *__restrict__ wb, int L1, int mode, R kappa, int b, R *tin,
                                          R *rowf) {
     constexpr int EXT = 2 * TSA + F - 2;
     constexpr int NQ = 2 * TSA / (NT / 32);   // output rows per warp in the column pass
     const Taps<R, F> f(b);
-    const int h = n >> 1;
+    const int h0 = n0 >> 1, h1 = n1 >> 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cc = lane & (TSA - 1);
     const bool hi1 = lane >= TSA;
@@ -83,15 +88,32 @@ __device__ __forceinline__ void ana_tile(const R *__restrict__ src, int in_pitch
         const bool hi0 = rq >= TSA;
         pu[k] = R(0);
         pw[k] = R(1);
-        if (mode != 0 && rr < h && cc < h && (hi0 || hi1 || last)) {
-            const int64_t off = (int64_t)((hi0 ? h : 0) + R0 + rr) * L + (hi1 ? h : 0) + C0 + cc;
+        if (mode != 0 && R0 + rr < h0 && C0 + cc < h1 && (hi0 || hi1 || last)) {
+            const int64_t off = (int64_t)((hi0 ? h0 : 0) + R0 + rr) * L1 + (hi1 ? h1 : 0) + C0 + cc;
             pu[k] = cb[off];
             if (wb) pw[k] = wb[off];
         }
     }
-    for (int i = warp; i < EXT; i += NT / 32) {
-        const R *row = src + (int64_t)wrap(2 * R0 + i, n) * in_pitch;
-        for (int j = lane; j < EXT; j += 32) tin[i * AEXT + j] = row[wrap(2 * C0 + j, n)];
+    // the input tile: every load issued before the first store
+    constexpr int NR = (EXT + NT / 32 - 1) / (NT / 32);
+    R tv[NR][2];
+    const int j1 = wrap(2 * C0 + lane, n1), j2 = wrap(2 * C0 + lane + 32, n1);
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const int i = warp + k * (NT / 32);
+        if (i < EXT) {
+            const R *row = src + (int64_t)wrap(2 * R0 + i, n0) * in_pitch;
+            tv[k][0] = row[j1];
+            if (lane + 32 < EXT) tv[k][1] = row[j2];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const int i = warp + k * (NT / 32);
+        if (i < EXT) {
+            tin[i * AEXT + lane] = tv[k][0];
+            if (lane + 32 < EXT) tin[i * AEXT + lane + 32] = tv[k][1];
+        }
     }
     __syncthreads();
     {   // rows: lane = output column q (low half, then high half)
@@ -113,11 +135,11 @@ __device__ __forceinline__ void ana_tile(const R *__restrict__ src, int in_pitch
         R acc = 0;
 #pragma unroll
         for (int k = 0; k < F; ++k) acc += (hi0 ? f.g[k] : f.h[k]) * col[k * 2 * TSA];
-        if (rr >= h || cc >= h) continue;                // wrapped duplicate (h < TSA)
+        if (R0 + rr >= h0 || C0 + cc >= h1) continue;   // outside the quadrant
         if (!hi0 && !hi1 && !last) {
-            ll[(R0 + rr) * h + C0 + cc] = acc;
+            ll[(R0 + rr) * h1 + C0 + cc] = acc;
         } else {
-            const int64_t off = (int64_t)((hi0 ? h : 0) + R0 + rr) * L + (hi1 ? h : 0) + C0 + cc;
+            const int64_t off = (int64_t)((hi0 ? h0 : 0) + R0 + rr) * L1 + (hi1 ? h1 : 0) + C0 + cc;
             R *dst = cb + off;
             const R cv = acc * R(1.0 / 3.0);
             if (mode == 0) {
@@ -131,66 +153,91 @@ __device__ __forceinline__ void ana_tile(const R *__restrict__ src, int in_pitch
 }
 
 // One analysis level for all 8 wavelet bases (grid.y = basis).
-//   in:   level input, basis b at in + b*in_bstride, row pitch in_pitch
-//   ll:   next level's input (compact, pitch h) unless last
-//   coef: coefficient images (basis b+1 at coef + (b+1)*N, pitch L), written
+//   in:   level input n0 x n1, basis b at in + b*in_bstride, row pitch in_pitch
+//   ll:   next level's input (compact, pitch h1) unless last
+//   coef: coefficient images (basis b+1 at coef + (b+1)*N, pitch L1), written
 //         (mode 0: c = D x / 3) or clip-updated (mode 1: u = clip(u + w D x / 3, kappa))
 //   wgt:  prior weights (same layout as coef) or null (w = 1)
 //   pmask: active set P of Algorithm 3 (9 flags, Dirac first) or null; in
 //         mode 1 a basis outside P keeps u_b and is skipped at every level
 template <typename R>
-__global__ void __launch_bounds__(NT) k_sara_ana(const R *__restrict__ in, int in_pitch, int64_t in_bstride, int n,
-                                                 R *__restrict__ ll, int64_t ll_bstride, int last,
-                                                 R *__restrict__ coef, const R *__restrict__ wgt, int L, int64_t N,
+__global__ void __launch_bounds__(NT) k_sara_ana(const R *__restrict__ in, int in_pitch, int64_t in_bstride, int n0,
+                                                 int n1, R *__restrict__ ll, int64_t ll_bstride, int last,
+                                                 R *__restrict__ coef, const R *__restrict__ wgt, int L1, int64_t N,
                                                  int mode, R kappa, const uint8_t *__restrict__ pmask) {
     __shared__ R tin[AEXT * AEXT];
     __shared__ R rowf[AEXT * 2 * TSA];
     const int b = blockIdx.y;
     if (mode == 1 && pmask && !pmask[b + 1]) return;
-    const int h = n / 2, tpd = h > TSA ? h / TSA : 1;
-    const int R0 = (blockIdx.x / tpd) * TSA, C0 = (blockIdx.x % tpd) * TSA;
+    const int tpd1 = (n1 / 2 + TSA - 1) / TSA;
+    const int R0 = (blockIdx.x / tpd1) * TSA, C0 = (blockIdx.x % tpd1) * TSA;
     const R *src = in + (int64_t)b * in_bstride;
     R *lb = ll + (int64_t)b * ll_bstride;
     R *cb = coef + (int64_t)(b + 1) * N;
     const R *wb = wgt ? wgt + (int64_t)(b + 1) * N : nullptr;
     switch (b) {
-        case 0: ana_tile<R, 2>(src, in_pitch, n, R0, C0, lb, last, cb, wb, L, mode, kappa, b, tin, rowf); break;
-        case 1: ana_tile<R, 4>(src, in_pitch, n, R0, C0, lb, last, cb, wb, L, mode, kappa, b, tin, rowf); break;
-        case 2: ana_tile<R, 6>(src, in_pitch, n, R0, C0, lb, last, cb, wb, L, mode, kappa, b, tin, rowf); break;
-        case 3: ana_tile<R, 8>(src, in_pitch, n, R0, C0, lb, last, cb, wb, L, mode, kappa, b, tin, rowf); break;
-        case 4: ana_tile<R, 10>(src, in_pitch, n, R0, C0, lb, last, cb, wb, L, mode, kappa, b, tin, rowf); break;
-        case 5: ana_tile<R, 12>(src, in_pitch, n, R0, C0, lb, last, cb, wb, L, mode, kappa, b, tin, rowf); break;
-        case 6: ana_tile<R, 14>(src, in_pitch, n, R0, C0, lb, last, cb, wb, L, mode, kappa, b, tin, rowf); break;
-        default: ana_tile<R, 16>(src, in_pitch, n, R0, C0, lb, last, cb, wb, L, mode, kappa, b, tin, rowf); break;
+        case 0: ana_tile<R, 2>(src, in_pitch, n0, n1, R0, C0, lb, last, cb, wb, L1, mode, kappa, b, tin, rowf); break;
+        case 1: ana_tile<R, 4>(src, in_pitch, n0, n1, R0, C0, lb, last, cb, wb, L1, mode, kappa, b, tin, rowf); break;
+        case 2: ana_tile<R, 6>(src, in_pitch, n0, n1, R0, C0, lb, last, cb, wb, L1, mode, kappa, b, tin, rowf); break;
+        case 3: ana_tile<R, 8>(src, in_pitch, n0, n1, R0, C0, lb, last, cb, wb, L1, mode, kappa, b, tin, rowf); break;
+        case 4: ana_tile<R, 10>(src, in_pitch, n0, n1, R0, C0, lb, last, cb, wb, L1, mode, kappa, b, tin, rowf); break;
+        case 5: ana_tile<R, 12>(src, in_pitch, n0, n1, R0, C0, lb, last, cb, wb, L1, mode, kappa, b, tin, rowf); break;
+        case 6: ana_tile<R, 14>(src, in_pitch, n0, n1, R0, C0, lb, last, cb, wb, L1, mode, kappa, b, tin, rowf); break;
+        default: ana_tile<R, 16>(src, in_pitch, n0, n1, R0, C0, lb, last, cb, wb, L1, mode, kappa, b, tin, rowf); break;
     }
 }
 
 // ------------------------------------------------------------- synthesis
-// Inverse of one level for one basis on one output tile of 2TS x 2TS samples
-// whose quadrant positions start at (R0, C0).  The quadrant tiles cover rows
-// and columns R0 - F/2 + 1 ... R0 + TS - 1 (mod h).  Returns this thread's
-// output (mm = tid / 2TS, nn = tid % 2TS; NT == 4 TS^2).
+// Inverse of one level (output n0 x n1, quadrants h0 x h1) for one basis on
+// one output tile of 2TS x 2TS samples whose quadrant positions start at
+// (R0, C0).  The quadrant tiles cover rows R0 - F/2 + 1 ... R0 + TS - 1
+// (mod h0) and the same columns (mod h1), EXT = TS + F/2 - 1 <= 15 of each:
+// thread t holds tile position (t / 16, t % 16) of the 4 quadrants.  An
+// output sample m of a row takes quadrant row (m - k)/2 for its taps k of the
+// same parity, so the tile row is (m - k)/2 - (R0 - F/2 + 1) with no wrap.
+static_assert(NT == 16 * 16 && SEXT <= 16, "one quadrant-tile position per thread");
+
+// This thread's quadrant-tile values of basis filter length F (loads only;
+// the prior weights multiply them when they are stored).
+template <typename R> struct SynVals {
+    R v[4], w[4];
+};
+
+template <typename R>
+__device__ __forceinline__ void syn_load(SynVals<R> &o, const R *__restrict__ cb, const R *__restrict__ wb,
+                                         const R *__restrict__ sl, int from_coef, int L1, int h0, int h1, int R0,
+                                         int C0, int F) {
+    const int ext = TS + F / 2 - 1, i = threadIdx.x >> 4, j = threadIdx.x & 15;
+    if (i >= ext || j >= ext) return;
+    const int gi = wrap(R0 - F / 2 + 1 + i, h0), gj = wrap(C0 - F / 2 + 1 + j, h1);
+#pragma unroll
+    for (int qd = 0; qd < 4; ++qd) {
+        o.w[qd] = R(1);
+        if (qd == 0 && !from_coef) {
+            o.v[qd] = sl[gi * h1 + gj];
+        } else {
+            const int64_t off = (int64_t)((qd & 2) ? h0 + gi : gi) * L1 + ((qd & 1) ? h1 : 0) + gj;
+            o.v[qd] = cb[off];
+            if (wb) o.w[qd] = wb[off];
+        }
+    }
+}
+
+template <typename R> __device__ __forceinline__ void syn_store(const SynVals<R> &o, R *qs, int F) {
+    const int ext = TS + F / 2 - 1, i = threadIdx.x >> 4, j = threadIdx.x & 15;
+    if (i >= ext || j >= ext) return;
+#pragma unroll
+    for (int qd = 0; qd < 4; ++qd) qs[qd * SEXT * SEXT + i * SEXT + j] = o.v[qd] * o.w[qd];
+}
+
+// The two filter passes over the stored quadrant tiles (barrier first);
+// returns this thread's output (mm = tid / 2TS, nn = tid % 2TS; NT == 4 TS^2)
+// and leaves the shared tiles free for reuse.
 template <typename R, int F>
-__device__ __forceinline__ R syn_tile(const R *__restrict__ cb, const R *__restrict__ wb, const R *__restrict__ sl,
-                                      int from_coef, int L, int n, int R0, int C0, int b, R *qs, R *tl, R *th) {
+__device__ __forceinline__ R syn_compute(int R0, int C0, int b, const R *qs, R *tl, R *th) {
     constexpr int EXT = TS + F / 2 - 1;
     const Taps<R, F> f(b);
-    const int h = n >> 1;
     const int base_r = R0 - F / 2 + 1, base_c = C0 - F / 2 + 1;
-    for (int e = threadIdx.x; e < 4 * EXT * EXT; e += NT) {
-        const int qd = e / (EXT * EXT), r = e % (EXT * EXT);
-        const int i = r / EXT, j = r % EXT;
-        const int gi = wrap(base_r + i, h), gj = wrap(base_c + j, h);
-        R v;
-        if (qd == 0 && !from_coef) {
-            v = sl[gi * h + gj];
-        } else {
-            const int64_t off = (int64_t)((qd & 2) ? h + gi : gi) * L + ((qd & 1) ? h : 0) + gj;
-            v = cb[off];
-            if (wb) v *= wb[off];
-        }
-        qs[qd * SEXT * SEXT + i * SEXT + j] = v;
-    }
     __syncthreads();
     for (int e = threadIdx.x; e < 2 * TS * EXT; e += NT) {   // inverse along axis 0
         const int mm = e / EXT, j = e % EXT;
@@ -199,7 +246,7 @@ __device__ __forceinline__ R syn_tile(const R *__restrict__ cb, const R *__restr
 #pragma unroll
         for (int kk = 0; kk < F / 2; ++kk) {
             const int k = 2 * kk + par;
-            const int il = wrap((wrap(m - k, n) >> 1) - base_r, h);
+            const int il = ((m - k) >> 1) - base_r;
             const R a = par ? f.h[2 * kk + 1] : f.h[2 * kk], c = par ? f.g[2 * kk + 1] : f.g[2 * kk];
             sl0 += a * qs[0 * SEXT * SEXT + il * SEXT + j] + c * qs[2 * SEXT * SEXT + il * SEXT + j];
             sh0 += a * qs[1 * SEXT * SEXT + il * SEXT + j] + c * qs[3 * SEXT * SEXT + il * SEXT + j];
@@ -214,68 +261,81 @@ __device__ __forceinline__ R syn_tile(const R *__restrict__ cb, const R *__restr
 #pragma unroll
     for (int kk = 0; kk < F / 2; ++kk) {
         const int j = 2 * kk + par;
-        const int jl = wrap((wrap(nn - j, n) >> 1) - base_c, h);
+        const int jl = ((nn - j) >> 1) - base_c;
         const R a = par ? f.h[2 * kk + 1] : f.h[2 * kk], c = par ? f.g[2 * kk + 1] : f.g[2 * kk];
         out += a * tl[mm * SEXT + jl] + c * th[mm * SEXT + jl];
     }
-    __syncthreads();   // shared tiles are reused by the caller
+    __syncthreads();
     return out;
 }
 
-template <typename R>
-__device__ __forceinline__ R syn_tile_b(int b, const R *cb, const R *wb, const R *sl, int from_coef, int L, int n,
-                                        int R0, int C0, R *qs, R *tl, R *th) {
+template <typename R> __device__ __forceinline__ R syn_compute_b(int b, int R0, int C0, const R *qs, R *tl, R *th) {
     switch (b) {
-        case 0: return syn_tile<R, 2>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
-        case 1: return syn_tile<R, 4>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
-        case 2: return syn_tile<R, 6>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
-        case 3: return syn_tile<R, 8>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
-        case 4: return syn_tile<R, 10>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
-        case 5: return syn_tile<R, 12>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
-        case 6: return syn_tile<R, 14>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
-        default: return syn_tile<R, 16>(cb, wb, sl, from_coef, L, n, R0, C0, b, qs, tl, th);
+        case 0: return syn_compute<R, 2>(R0, C0, b, qs, tl, th);
+        case 1: return syn_compute<R, 4>(R0, C0, b, qs, tl, th);
+        case 2: return syn_compute<R, 6>(R0, C0, b, qs, tl, th);
+        case 3: return syn_compute<R, 8>(R0, C0, b, qs, tl, th);
+        case 4: return syn_compute<R, 10>(R0, C0, b, qs, tl, th);
+        case 5: return syn_compute<R, 12>(R0, C0, b, qs, tl, th);
+        case 6: return syn_compute<R, 14>(R0, C0, b, qs, tl, th);
+        default: return syn_compute<R, 16>(R0, C0, b, qs, tl, th);
     }
 }
 
-// One synthesis level l > 0 for all 8 bases (grid.y = basis): out_b (compact
-// pitch n) = D_b^T of (LL' block, detail quadrants), coefficients times the
-// prior weights when wgt is set.  LL' comes from the coefficients at the
-// coarsest level (from_coef) or from the coarser level's output sll.
+// One synthesis level l > 0 for all 8 bases (grid.y = basis): out_b (n0 x n1,
+// compact pitch n1) = D_b^T of (LL' block, detail quadrants), coefficients
+// times the prior weights when wgt is set.  LL' comes from the coefficients
+// at the coarsest level (from_coef) or from the coarser level's output sll.
 template <typename R>
-__global__ void __launch_bounds__(NT) k_sara_syn(const R *__restrict__ coef, const R *__restrict__ wgt, int L, int64_t N,
-                                                 const R *__restrict__ sll, int from_coef, int64_t sll_bstride, int n,
-                                                 R *__restrict__ out, int64_t out_bstride) {
+__global__ void __launch_bounds__(NT) k_sara_syn(const R *__restrict__ coef, const R *__restrict__ wgt, int L1,
+                                                 int64_t N, const R *__restrict__ sll, int from_coef,
+                                                 int64_t sll_bstride, int n0, int n1, R *__restrict__ out,
+                                                 int64_t out_bstride) {
     __shared__ R qs[4 * SEXT * SEXT];
     __shared__ R tl[2 * TS * SEXT], th[2 * TS * SEXT];
     const int b = blockIdx.y;
-    const int h = n / 2, tpd = h > TS ? h / TS : 1;
-    const int R0 = (blockIdx.x / tpd) * TS, C0 = (blockIdx.x % tpd) * TS;
-    const R v = syn_tile_b<R>(b, coef + (int64_t)(b + 1) * N, wgt ? wgt + (int64_t)(b + 1) * N : nullptr,
-                              sll + (int64_t)b * sll_bstride, from_coef, L, n, R0, C0, qs, tl, th);
+    const int tpd1 = (n1 / 2 + TS - 1) / TS;
+    const int R0 = (blockIdx.x / tpd1) * TS, C0 = (blockIdx.x % tpd1) * TS;
+    SynVals<R> q;
+    syn_load(q, coef + (int64_t)(b + 1) * N, wgt ? wgt + (int64_t)(b + 1) * N : nullptr,
+             sll + (int64_t)b * sll_bstride, from_coef, L1, n0 >> 1, n1 >> 1, R0, C0, 2 * b + 2);
+    syn_store(q, qs, 2 * b + 2);
+    const R v = syn_compute_b<R>(b, R0, C0, qs, tl, th);
     const int mm = threadIdx.x / (2 * TS), nnl = threadIdx.x % (2 * TS);
-    if (2 * R0 + mm < n && 2 * C0 + nnl < n)
-        out[(int64_t)b * out_bstride + (int64_t)(2 * R0 + mm) * n + 2 * C0 + nnl] = v;
+    if (2 * R0 + mm < n0 && 2 * C0 + nnl < n1)
+        out[(int64_t)b * out_bstride + (int64_t)(2 * R0 + mm) * n1 + 2 * C0 + nnl] = v;
 }
 
 // Finest synthesis level, the 8 wavelet bases summed in order per output
 // sample: out = scale * (dirac + sum_b D_b^T (w_b c_b)) (dirac may be null).
+// The quadrant tiles of basis b + 1 are loaded into registers while basis b
+// is filtered.
 template <typename R>
-__global__ void __launch_bounds__(NT) k_sara_syn0(const R *__restrict__ coef, const R *__restrict__ wgt, int L,
-                                                  int64_t N, const R *__restrict__ sll, int from_coef,
+__global__ void __launch_bounds__(NT) k_sara_syn0(const R *__restrict__ coef, const R *__restrict__ wgt, int L0,
+                                                  int L1, int64_t N, const R *__restrict__ sll, int from_coef,
                                                   int64_t sll_bstride, const R *__restrict__ dirac, R scale,
                                                   R *__restrict__ out) {
     __shared__ R qs[4 * SEXT * SEXT];
     __shared__ R tl[2 * TS * SEXT], th[2 * TS * SEXT];
-    const int n = L, h = n / 2, tpd = h > TS ? h / TS : 1;
-    const int R0 = (blockIdx.x / tpd) * TS, C0 = (blockIdx.x % tpd) * TS;
+    const int tpd1 = (L1 / 2 + TS - 1) / TS;
+    const int R0 = (blockIdx.x / tpd1) * TS, C0 = (blockIdx.x % tpd1) * TS;
+    const int h0 = L0 >> 1, h1 = L1 >> 1;
+    auto load = [&](SynVals<R> &q, int b) {
+        syn_load(q, coef + (int64_t)(b + 1) * N, wgt ? wgt + (int64_t)(b + 1) * N : nullptr,
+                 sll + (int64_t)b * sll_bstride, from_coef, L1, h0, h1, R0, C0, 2 * b + 2);
+    };
+    SynVals<R> q;
+    load(q, 0);
     R acc = 0;
 #pragma unroll
-    for (int b = 0; b < N_WAVELETS; ++b)
-        acc += syn_tile_b<R>(b, coef + (int64_t)(b + 1) * N, wgt ? wgt + (int64_t)(b + 1) * N : nullptr,
-                             sll + (int64_t)b * sll_bstride, from_coef, L, n, R0, C0, qs, tl, th);
+    for (int b = 0; b < N_WAVELETS; ++b) {
+        syn_store(q, qs, 2 * b + 2);
+        if (b + 1 < N_WAVELETS) load(q, b + 1);
+        acc += syn_compute_b<R>(b, R0, C0, qs, tl, th);
+    }
     const int mm = threadIdx.x / (2 * TS), nnl = threadIdx.x % (2 * TS);
-    if ((2 * R0 + mm < n) && (2 * C0 + nnl < n)) {
-        const int64_t idx = (int64_t)(2 * R0 + mm) * L + 2 * C0 + nnl;
+    if ((2 * R0 + mm < L0) && (2 * C0 + nnl < L1)) {
+        const int64_t idx = (int64_t)(2 * R0 + mm) * L1 + 2 * C0 + nnl;
         out[idx] = scale * ((dirac ? dirac[idx] : R(0)) + acc);
     }
 }
@@ -285,7 +345,8 @@ template <typename R> __global__ void k_scale_copy(const R *__restrict__ in, R *
 }
 
 inline unsigned nblk(int64_t work) { return (unsigned)std::min<int64_t>((work + NT - 1) / NT, 152 * 8); }
-inline int tiles(int h, int ts) { return h > ts ? (h / ts) * (h / ts) : 1; }
+// tiles of ts x ts quadrant positions covering an h0 x h1 quadrant
+inline unsigned tiles(int h0, int h1, int ts) { return (unsigned)(((h0 + ts - 1) / ts) * ((h1 + ts - 1) / ts)); }
 
 // Analysis of all levels (tiled).  mode 0 writes c = D x / 3, mode 1
 // clip-updates u with the prior weights and the clip level kappa ||Psi W||^2.
@@ -293,20 +354,20 @@ template <typename R> int analysis_all(ppd_ctx *c, const R *x, R *coef, int mode
     const R *wgt = mode == 1 ? static_cast<const R *>(c->wgt) : nullptr;
     const uint8_t *pmask = (mode == 1 && c->rand_on) ? c->mask_cur + c->d : nullptr;
     const R alpha = (R)(c->kappa * c->psiw2);
-    const int L = c->L0;
+    const int L0 = c->L0, L1 = c->L1;
     const int64_t N = c->N;
-    R *ll[2] = {static_cast<R *>(c->wtmp), static_cast<R *>(c->wtmp) + (int64_t)N_WAVELETS * (L / 2) * (L / 2)};
-    const int64_t ll_stride = (int64_t)(L / 2) * (L / 2);
+    const int64_t ll_stride = (int64_t)(L0 / 2) * (L1 / 2);
+    R *ll[2] = {static_cast<R *>(c->wtmp), static_cast<R *>(c->wtmp) + (int64_t)N_WAVELETS * ll_stride};
     int site;
     for (int l = 0; l < c->levels; ++l) {
-        const int n = L >> l, h = n / 2;
+        const int n0 = L0 >> l, n1 = L1 >> l;
         const bool last = (l == c->levels - 1);
         const R *in = l == 0 ? x : ll[(l - 1) & 1];
-        const int pitch = l == 0 ? L : n;
+        const int pitch = l == 0 ? L1 : n1;
         const int64_t bstride = l == 0 ? 0 : ll_stride;
         PPD_CHECK(launch_begin(c, "sara_analysis", s, &site));
-        k_sara_ana<R><<<dim3(tiles(h, TSA), N_WAVELETS), NT, 0, s>>>(in, pitch, bstride, n, ll[l & 1], ll_stride, last,
-                                                                     coef, wgt, L, N, mode, alpha, pmask);
+        k_sara_ana<R><<<dim3(tiles(n0 / 2, n1 / 2, TSA), N_WAVELETS), NT, 0, s>>>(
+            in, pitch, bstride, n0, n1, ll[l & 1], ll_stride, last, coef, wgt, L1, N, mode, alpha, pmask);
         PPD_CHECK(launch_end(c, site, s));
     }
     return PPD_OK;
@@ -316,18 +377,18 @@ template <typename R> int analysis_all(ppd_ctx *c, const R *x, R *coef, int mode
 // the buffer holding the LL' block of level 0.
 template <typename R>
 int synthesis_levels(ppd_ctx *c, const R *coef, const R *wgt, const R **ll0, cudaStream_t s) {
-    const int L = c->L0;
+    const int L0 = c->L0, L1 = c->L1;
     const int64_t N = c->N;
-    const int64_t st = (int64_t)(L / 2) * (L / 2);
+    const int64_t st = (int64_t)(L0 / 2) * (L1 / 2);
     R *buf[2] = {static_cast<R *>(c->wtmp2), static_cast<R *>(c->wtmp2) + (int64_t)N_WAVELETS * st};
     const R *prev = nullptr;
     int site, k = 0;
     for (int l = c->levels - 1; l >= 1; --l, ++k) {
-        const int n = L >> l, h = n / 2;
+        const int n0 = L0 >> l, n1 = L1 >> l;
         const bool coarsest = (l == c->levels - 1);
         PPD_CHECK(launch_begin(c, "sara_synthesis", s, &site));
-        k_sara_syn<R><<<dim3(tiles(h, TS), N_WAVELETS), NT, 0, s>>>(coef, wgt, L, N, coarsest ? coef : prev,
-                                                                    coarsest ? 1 : 0, st, n, buf[k & 1], st);
+        k_sara_syn<R><<<dim3(tiles(n0 / 2, n1 / 2, TS), N_WAVELETS), NT, 0, s>>>(
+            coef, wgt, L1, N, coarsest ? coef : prev, coarsest ? 1 : 0, st, n0, n1, buf[k & 1], st);
         PPD_CHECK(launch_end(c, site, s));
         prev = buf[k & 1];
     }
@@ -338,14 +399,13 @@ int synthesis_levels(ppd_ctx *c, const R *coef, const R *wgt, const R **ll0, cud
 template <typename R>
 int synthesis_final(ppd_ctx *c, const R *coef, const R *wgt, const R *ll0, const R *dirac, R scale, R *out,
                     cudaStream_t s) {
-    const int L = c->L0;
-    const int h = L / 2;
-    const int64_t st = (int64_t)(L / 2) * (L / 2);
+    const int L0 = c->L0, L1 = c->L1;
+    const int64_t st = (int64_t)(L0 / 2) * (L1 / 2);
     const bool from_coef = ll0 == nullptr;   // levels == 1: LL' straight from the coefficients
     int site;
     PPD_CHECK(launch_begin(c, "sara_synthesis", s, &site));
-    k_sara_syn0<R><<<tiles(h, TS), NT, 0, s>>>(coef, wgt, L, c->N, from_coef ? coef : ll0, from_coef ? 1 : 0, st,
-                                                dirac, scale, out);
+    k_sara_syn0<R><<<tiles(L0 / 2, L1 / 2, TS), NT, 0, s>>>(coef, wgt, L0, L1, c->N, from_coef ? coef : ll0,
+                                                           from_coef ? 1 : 0, st, dirac, scale, out);
     return launch_end(c, site, s);
 }
 

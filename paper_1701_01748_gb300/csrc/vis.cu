@@ -130,6 +130,14 @@ template <typename R> struct VisArgs {
     const cplx_t<R> *op_in;
     cplx_t<R> *op_out;
     const int64_t *perm;
+    // Algorithm 2 stopping test (inner_tol > 0): this launch's step number
+    // (0: the step that forms the start P_B(z); 1 .. n_itr - 1: sub-iterations;
+    // n_itr: the gridding), whether part_in holds the previous step's test
+    // partials, per block the step at which the test held (0: running) and
+    // the steps taken
+    double inner_tol;
+    int step, test_in, n_itr;
+    int *inner_state, *inner_steps;
 };
 
 // Deterministic CTA sum of two doubles per thread (fixed shuffle tree, then
@@ -175,22 +183,48 @@ constexpr int DG_NT = 256;
 // P_B scale of block `blk` (Section 3.3, Eq. "proj-L2" as a radial scale):
 // eps / ||w - y|| if that norm exceeds eps, else 1, from the previous step's
 // chunk partials summed in a fixed order (the same result in every CTA).
-template <typename R> __device__ double block_scale(const VisArgs<R> &A, int blk) {
+// With `test`, *stop also receives Algorithm 2's stopping test of the
+// previous step, ||zbar^t - zbar^(t-1)|| <= inner_tol ||zbar^t||, in FP64.
+template <typename R> __device__ double block_scale(const VisArgs<R> &A, int blk, bool test = false,
+                                                   bool *stop = nullptr) {
     __shared__ double sc_s;
+    __shared__ int st_s;
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
-        double a = 0;
-        for (int k = A.blk_ptr[blk] + lane; k < A.blk_ptr[blk + 1]; k += 32) a += A.part_in[NPART * A.blk_list[k]];
+        double a = 0, dd = 0, nn = 0;
+        for (int k = A.blk_ptr[blk] + lane; k < A.blk_ptr[blk + 1]; k += 32) {
+            const double *q = A.part_in + NPART * (int64_t)A.blk_list[k];
+            a += q[0];
+            if (test) {
+                dd += q[2];
+                nn += q[3];
+            }
+        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            dd += __shfl_down_sync(0xffffffffu, dd, o);
+            nn += __shfl_down_sync(0xffffffffu, nn, o);
+        }
         if (lane == 0) {
             const double nrm = sqrt(a);
             if (!isfinite(nrm)) atomicOr(A.err, ERR_NONFINITE);
             sc_s = (nrm > A.eps[blk]) ? A.eps[blk] / nrm : 1.0;
+            st_s = test && sqrt(dd) <= A.inner_tol * sqrt(nn);
         }
     }
     __syncthreads();
+    if (stop) *stop = st_s != 0;
     return sc_s;
+}
+
+// Step at which block `blk` stopped Algorithm 2 in this iteration (0: still
+// running), read once per CTA so that every thread takes the same branch.
+template <typename R> __device__ int inner_stopped(const VisArgs<R> &A, int blk) {
+    __shared__ int s_state;
+    if (threadIdx.x == 0) s_state = (A.inner_tol > 0) ? *(volatile const int *)(A.inner_state + blk) : 0;
+    __syncthreads();
+    return s_state;
 }
 
 // ----------------------------------------------------------------- degrid
@@ -225,7 +259,7 @@ __device__ __forceinline__ void load_vis(const VisArgs<R> &A, int gi, VisIn<R> &
 template <typename R, int T, int MODE>
 __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
     k_degrid(const __grid_constant__ CUtensorMap tmap, int use_tma, const cplx_t<R> *__restrict__ grid, VisArgs<R> A,
-             int n_chunks) {
+             int n_chunks, long long spin_first) {
     using C = cplx_t<R>;
     constexpr int E = T + HALO;
     constexpr int TILE_BYTES = E * E * (int)sizeof(C);
@@ -270,7 +304,9 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
         VisIn<R> cur;
         if ((int)threadIdx.x < count) load_vis<R, MODE>(A, start + threadIdx.x, cur);
         if (interior(row0, col0)) {
-            if (!mbar_wait(&bar[buf], (ph >> buf) & 1u, SPIN_LIMIT)) {
+            // spin_first bounds the first wait (SPIN_LIMIT unless a test shortens
+            // it); the waits for copies in flight before leaving keep SPIN_LIMIT
+            if (!mbar_wait(&bar[buf], (ph >> buf) & 1u, spin_first)) {
                 atomicOr(A.err, ERR_TMA_TIMEOUT);
                 ok_s = 0;
                 mbar_wait(&bar[buf], (ph >> buf) & 1u, SPIN_LIMIT);   // second bounded wait for the copy in flight
@@ -300,6 +336,13 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
         // that the next Algorithm 2 step starts from P_B(z)
         const bool act = MODE == DG_OP || !A.bmask || A.bmask[blk];
         const bool first_blk = MODE == DG_FIRST || (A.seen && !A.seen[blk]);
+        if (MODE != DG_OP && threadIdx.x == 0) {
+            if (A.inner_tol > 0) A.inner_state[blk] = 0;
+            if (A.inner_steps) A.inner_steps[blk] = act ? A.n_itr : 0;
+        }
+        // with the stopping test the start zbar^(0) = z of a block without a
+        // prox output is kept in p, the previous point of the first test
+        const bool keep_start = first_blk && A.inner_tol > 0;
         Acc<R> s_w, s_r;
         for (int i = threadIdx.x; i < count; i += DG_NT) {
             const int gi = start + i;
@@ -334,6 +377,7 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
                     C ww;
                     if (first_blk) {
                         ww = zz;
+                        if (keep_start) A.p[gi] = zz;
                     } else {
                         const R mu_u = (R)mu * cur.rc.U;
                         ww = C{cur.p.x - mu_u * (cur.p.x - zz.x), cur.p.y - mu_u * (cur.p.y - zz.y)};
@@ -361,6 +405,9 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
 // only_first: the extra step that moves the start of a block with no prox
 // output yet from z to P_B(z) (randomised active sets); chunks of other
 // blocks, and of blocks outside D, pass their partial through unchanged.
+// Stopping test (inner_tol > 0): p is kept every step; a step k >= 1 also
+// forms the partials ||p - p_prev||^2 and ||p||^2; a block whose test held
+// for the previous step (or earlier) stops, its p being the prox output.
 template <typename R>
 __global__ void __launch_bounds__(DG_NT) k_subiter(VisArgs<R> A, int only_first, R beta, int write_p) {
     using C = cplx_t<R>;
@@ -372,28 +419,48 @@ __global__ void __launch_bounds__(DG_NT) k_subiter(VisArgs<R> A, int only_first,
         if (threadIdx.x == 0) A.partials[NPART * (int64_t)ch] = A.part_in[NPART * (int64_t)ch];
         return;
     }
-    const R c = (R)block_scale(A, blk), mu = (R)A.mu[blk];
-    Acc<R> s_w;
+    const bool tol_on = A.inner_tol > 0;
+    if (inner_stopped(A, blk)) return;   // stopped at an earlier step of this iteration
+    bool stop = false;
+    const R c = (R)block_scale(A, blk, tol_on && A.test_in, &stop);
+    if (stop) {   // the previous step's output is the prox
+        if (threadIdx.x == 0) A.inner_state[blk] = A.step - 1;
+        return;
+    }
+    const R mu = (R)A.mu[blk];
+    const bool test_out = tol_on && A.step > 0;
+    const bool keep = write_p || tol_on;
+    Acc<R> s_w, s_d, s_n;
     for (int i = threadIdx.x; i < count; i += DG_NT) {
         const int gi = start + i;
         const R U = A.rec[gi].U;
         const C yy = A.y[gi], ww = A.w[gi], zz = A.z[gi];
         const C pp{yy.x + c * (ww.x - yy.x), yy.y + c * (ww.y - yy.y)};
         C q = pp;
-        if (beta != R(0)) {
+        if (beta != R(0) || test_out) {
             const C pm = A.p[gi];
-            q = C{pp.x + beta * (pp.x - pm.x), pp.y + beta * (pp.y - pm.y)};
+            if (beta != R(0)) q = C{pp.x + beta * (pp.x - pm.x), pp.y + beta * (pp.y - pm.y)};
+            if (test_out) {
+                const R ex = pp.x - pm.x, ey = pp.y - pm.y;
+                s_d.add(ex * ex + ey * ey);
+                s_n.add(pp.x * pp.x + pp.y * pp.y);
+            }
         }
-        if (write_p) A.p[gi] = pp;
+        if (keep) A.p[gi] = pp;
         const R mu_u = mu * U;
         const C wn{q.x - mu_u * (q.x - zz.x), q.y - mu_u * (q.y - zz.y)};
         A.w[gi] = wn;
         const R dx = wn.x - yy.x, dy = wn.y - yy.y;
         s_w.add(dx * dx + dy * dy);
     }
-    __shared__ double o2[2];
-    cta_sum2<DG_NT>(s_w.get(), 0.0, o2);
-    if (threadIdx.x == 0) A.partials[NPART * (int64_t)ch] = o2[0];
+    __shared__ double o3[3];
+    cta_sum3<DG_NT>(s_w.get(), s_d.get(), s_n.get(), o3);
+    if (threadIdx.x == 0) {
+        double *out = A.partials + NPART * (int64_t)ch;
+        out[0] = o3[0];
+        out[2] = o3[1];
+        out[3] = o3[2];
+    }
 }
 
 // ----------------------------------------------------------------- block norms
@@ -432,6 +499,10 @@ __global__ void k_block_norms(const double *__restrict__ partials, const int32_t
 // footprint into the warp's private (T+8)^2 tile; phase 3 sums the private
 // tiles in warp order and writes the chunk's partial tile.  GR_DUAL fuses the
 // end of the data step: p = P_B(w) = y + c (w - y), v = U (z - p).
+// Lane l of the scattering warp owns footprint column l mod 8 of rows l/8
+// and l/8 + 4; with the private-tile pitch T + 8 = 8 mod 16 (in 8-byte
+// words) the two rows a half-warp touches fall in disjoint bank halves, so
+// the read-modify-write of the tile is free of bank conflicts.
 constexpr int GRID_MINV = 16;   // least visibilities per scattering warp
 template <typename R> struct GridCfg;
 template <> struct GridCfg<float> { static constexpr int NWARP = 8; };
@@ -441,7 +512,8 @@ template <typename R, int T, int MODE>
 __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, cplx_t<R> *__restrict__ gpart) {
     using C = cplx_t<R>;
     constexpr int NW = GridCfg<R>::NWARP, NT = NW * 32;
-    constexpr int E = T + HALO, P = E + 1;   // P: padded pitch of the private tiles
+    constexpr int E = T + HALO, P = E;   // P: pitch of the private tiles (8 mod 16 words)
+    static_assert(P % 16 == 8, "private-tile pitch");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     C *priv = reinterpret_cast<C *>(smem_raw);                          // NW * E * P
     R *sw0 = reinterpret_cast<R *>(priv + NW * E * P);                  // NT * 8
@@ -465,24 +537,47 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
     for (int i = threadIdx.x; i < (KB_DEG + 1) * KB_J; i += NT) poly[i] = A.kbpoly ? A.kbpoly[i] : 0.f;
     for (int e = threadIdx.x; e < nwu * E * P; e += NT) priv[e] = C{0, 0};
     R c = 0;
-    if (MODE == GR_DUAL && act) c = (R)block_scale(A, blk);
+    // Algorithm 2 stopped early (stopping test): the prox output is the p
+    // the stopping step kept, not P_B of the current w
+    bool done = false;
+    if (MODE == GR_DUAL && act) {
+        const bool tol_on = A.inner_tol > 0 && A.n_itr > 1;
+        int steps = A.n_itr;
+        const int stopped = tol_on ? inner_stopped(A, blk) : 0;
+        if (stopped) {
+            done = true;
+            steps = stopped;
+        } else {
+            bool stop = false;
+            c = (R)block_scale(A, blk, tol_on && A.test_in, &stop);
+            if (stop) {
+                done = true;
+                steps = A.n_itr - 1;
+            }
+        }
+        if (threadIdx.x == 0 && A.inner_steps) A.inner_steps[blk] = steps;
+    }
     if (MODE == GR_DUAL && act && A.seen && threadIdx.x == 0) A.seen[blk] = 1;
     __syncthreads();
 
     C *mine = priv + warp * E * P;
-    const int a = lane & 7, bb = (lane >> 3) * 2;
+    const int bcol = lane & 7, a0 = lane >> 3, a1 = a0 + 4;
     // this thread's visibility of the current round, loaded one round ahead
     // so that the loads of round r + 1 are in flight during the scatter of r
     struct In {
         VisRec<R> rc;
-        C a, b, z;   // GR_DUAL active: y, w, z; inactive: v; operator modes: input
+        C a, b, z;   // GR_DUAL active: y, w, z (stopped early: p, -, z); inactive: v; operator modes: input
         R th;
     };
     auto load_in = [&](int gi, In &o) {
         o.rc = A.rec[gi];
         if (MODE == GR_DUAL && act) {
-            o.a = A.y[gi];
-            o.b = A.w[gi];
+            if (done) {
+                o.a = A.p[gi];
+            } else {
+                o.a = A.y[gi];
+                o.b = A.w[gi];
+            }
             o.z = A.z[gi];
         } else if (MODE == GR_DUAL) {
             o.a = A.v[gi];
@@ -500,11 +595,17 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
             const VisRec<R> rc = cur.rc;
             C vv;
             if (MODE == GR_DUAL && act) {
-                const C yy = cur.a, ww = cur.b, zz = cur.z;
-                const C pp{yy.x + c * (ww.x - yy.x), yy.y + c * (ww.y - yy.y)};
+                const C zz = cur.z;
+                C pp;
+                if (done) {
+                    pp = cur.a;
+                } else {
+                    const C yy = cur.a, ww = cur.b;
+                    pp = C{yy.x + c * (ww.x - yy.x), yy.y + c * (ww.y - yy.y)};
+                    A.p[gi] = pp;
+                }
                 vv = C{rc.U * (zz.x - pp.x), rc.U * (zz.y - pp.y)};
                 A.v[gi] = vv;
-                A.p[gi] = pp;
             } else if (MODE == GR_DUAL) {
                 vv = cur.a;
             } else {
@@ -548,28 +649,28 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
             const int lb = slb[i];
             if (lb != run) {
                 if (run >= 0) {
-                    C *cell = mine + ((run & 0xffff) + a) * P + (run >> 16) + bb;
-                    C g0 = cell[0], g1 = cell[1];
+                    C *cell = mine + ((run & 0xffff) + a0) * P + (run >> 16) + bcol;
+                    C g0 = cell[0], g1 = cell[4 * P];
                     cell[0] = cadd(g0, acc0);
-                    cell[1] = cadd(g1, acc1);
+                    cell[4 * P] = cadd(g1, acc1);
                 }
                 run = lb;
                 acc0 = C{0, 0};
                 acc1 = C{0, 0};
             }
             const C tv = sv[i];
-            const R wa = sw0[i * KB_J + a];
-            const R wb0 = wa * sw1[i * KB_J + bb], wb1 = wa * sw1[i * KB_J + bb + 1];
-            acc0.x += wb0 * tv.x;
-            acc0.y += wb0 * tv.y;
-            acc1.x += wb1 * tv.x;
-            acc1.y += wb1 * tv.y;
+            const R wb = sw1[i * KB_J + bcol];
+            const R w0 = sw0[i * KB_J + a0] * wb, w1 = sw0[i * KB_J + a1] * wb;
+            acc0.x += w0 * tv.x;
+            acc0.y += w0 * tv.y;
+            acc1.x += w1 * tv.x;
+            acc1.y += w1 * tv.y;
         }
         if (run >= 0) {
-            C *cell = mine + ((run & 0xffff) + a) * P + (run >> 16) + bb;
-            C g0 = cell[0], g1 = cell[1];
+            C *cell = mine + ((run & 0xffff) + a0) * P + (run >> 16) + bcol;
+            C g0 = cell[0], g1 = cell[4 * P];
             cell[0] = cadd(g0, acc0);
-            cell[1] = cadd(g1, acc1);
+            cell[4 * P] = cadd(g1, acc1);
         }
         __syncthreads();
         cur = nxt;
@@ -659,11 +760,17 @@ template <typename R> VisArgs<R> make_args(ppd_ctx *c) {
     A.bmask = c->rand_on ? c->mask_cur : nullptr;
     A.seen = c->rand_on ? c->blk_seen : nullptr;
     A.regrid = c->rand_on ? c->regrid_d : nullptr;
+    A.inner_tol = c->cfg.inner_tol;
+    A.step = c->next_step;
+    A.test_in = c->next_test_in;
+    A.n_itr = c->cfg.n_itr;
+    A.inner_state = c->inner_state;
+    A.inner_steps = c->inner_steps;
     return A;
 }
 
 template <typename R, int T> size_t grid_smem() {
-    constexpr int NW = GridCfg<R>::NWARP, NT = NW * 32, E = T + HALO, P = E + 1;
+    constexpr int NW = GridCfg<R>::NWARP, NT = NW * 32, E = T + HALO, P = E;
     return (size_t)NW * E * P * sizeof(cplx_t<R>) + 2 * NT * KB_J * sizeof(R) + NT * sizeof(cplx_t<R>) +
            NT * sizeof(int) + (KB_DEG + 1) * KB_J * sizeof(float);
 }
@@ -690,9 +797,10 @@ int degrid_t(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const 
     const unsigned nb = (unsigned)std::min<int64_t>(nch, (int64_t)sms * per_sm);
     int site;
     PPD_CHECK(launch_begin(c, mode == DG_OP ? "degrid_op" : "degrid_dual", s, &site));
-    if (mode == DG_OP) k_degrid<R, T, DG_OP><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A, nch);
-    else if (mode == DG_DUAL) k_degrid<R, T, DG_DUAL><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A, nch);
-    else k_degrid<R, T, DG_FIRST><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A, nch);
+    const long long sf = c->wait_first;
+    if (mode == DG_OP) k_degrid<R, T, DG_OP><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A, nch, sf);
+    else if (mode == DG_DUAL) k_degrid<R, T, DG_DUAL><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A, nch, sf);
+    else k_degrid<R, T, DG_FIRST><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A, nch, sf);
     return launch_end(c, site, s);
 }
 

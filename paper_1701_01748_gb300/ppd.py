@@ -28,6 +28,8 @@ PPD_INNER_WARM = 0
 PPD_INNER_CURRENT = 1
 PPD_INNER_FB = 0
 PPD_INNER_FISTA = 1
+PPD_NORM_LANCZOS = 0
+PPD_NORM_POWER = 1
 
 
 class ppd_config(ct.Structure):
@@ -38,13 +40,16 @@ class ppd_config(ct.Structure):
                 ("zeta", ct.c_double), ("precision", ct.c_int32), ("precond", ct.c_int32),
                 ("inner_init", ct.c_int32), ("use_graph", ct.c_int32), ("tile", ct.c_int32),
                 ("chunk", ct.c_int32), ("power_iters", ct.c_int32), ("power_tol", ct.c_double),
-                ("stream", ct.c_void_p), ("inner_solver", ct.c_int32)]
+                ("stream", ct.c_void_p), ("inner_solver", ct.c_int32), ("inner_tol", ct.c_double),
+                ("stop_tol", ct.c_double), ("stop_eps_factor", ct.c_double), ("stop_every", ct.c_int32),
+                ("pad0", ct.c_int32), ("seed", ct.c_uint64), ("norm_method", ct.c_int32), ("pad1", ct.c_int32)]
 
 
 class ppd_stats(ct.Structure):
     _fields_ = [("iters_done", ct.c_int32), ("status", ct.c_int32), ("rel_var", ct.c_double),
                 ("snr_db", ct.c_double), ("max_res_over_eps", ct.c_double),
-                ("block_residual", ct.POINTER(ct.c_double))]
+                ("block_residual", ct.POINTER(ct.c_double)), ("inner_steps", ct.POINTER(ct.c_int32)),
+                ("stopped", ct.c_int32), ("iters_run", ct.c_int32)]
 
 
 class ppd_params(ct.Structure):
@@ -105,6 +110,7 @@ def _lib():
             "ppd_timing_read": (I, [P, I32, ct.POINTER(ct.c_char_p), D, ct.POINTER(ct.c_int64),
                                     ct.POINTER(ct.c_int32)]),
             "ppd_launch_count": (I64, [P]),
+            "ppd_set_wait_limit": (I, [P, I64]),
             "ppd_status_string": (ct.c_char_p, [I]),
             "ppd_last_error": (ct.c_char_p, []),
         }
@@ -184,13 +190,16 @@ def ppd_iterate(ctx: int, n_iters: int, n_blocks: int | None = None, stats: bool
         _check(_lib().ppd_iterate(ctx, n_iters, None), "ppd_iterate")
         return None
     st = ppd_stats()
-    res = None
+    res = steps = None
     if n_blocks:
         res = np.zeros(n_blocks)
+        steps = np.zeros(n_blocks, np.int32)
         st.block_residual = _dptr(res)
+        st.inner_steps = steps.ctypes.data_as(ct.POINTER(ct.c_int32))
     _check(_lib().ppd_iterate(ctx, n_iters, ct.byref(st)), "ppd_iterate")
     return dict(iters_done=st.iters_done, rel_var=st.rel_var, snr_db=st.snr_db,
-                max_res_over_eps=st.max_res_over_eps, block_residual=res)
+                max_res_over_eps=st.max_res_over_eps, block_residual=res, inner_steps=steps,
+                stopped=bool(st.stopped), iters_run=st.iters_run)
 
 
 def ppd_get_image(ctx: int, n0: int, n1: int) -> np.ndarray:
@@ -323,6 +332,13 @@ def ppd_timing_read(ctx: int) -> dict:
     return {names[i].decode(): (float(ms[i]), int(cnt[i])) for i in range(k)}
 
 
+PPD_WAIT_LIMIT_DEFAULT = 1 << 21
+
+
+def ppd_set_wait_limit(ctx: int, polls: int) -> None:
+    _check(_lib().ppd_set_wait_limit(ctx, int(polls)), "ppd_set_wait_limit")
+
+
 def ppd_launch_count(ctx: int) -> int:
     return int(_lib().ppd_launch_count(ctx))
 
@@ -337,14 +353,17 @@ def ppd_last_error() -> str:
 
 # --------------------------------------------------------------- convenience
 class Solver:
-    """One library context for one imaging problem (owns the handle)."""
+    """One library context for one imaging problem (owns the handle): an
+    L x L1 image (L1 = L by default)."""
 
-    def __init__(self, L: int, n_blocks: int = 1, precision: int = PPD_FP32_FP64NORMS, **cfg):
+    def __init__(self, L: int, n_blocks: int = 1, precision: int = PPD_FP32_FP64NORMS, L1: int | None = None,
+                 **cfg):
         self.L = L
+        self.L1 = L if L1 is None else L1
         self.n_blocks = n_blocks
         if "stream" in cfg:
             cfg["stream"] = _stream(cfg["stream"])
-        self.cfg = ppd_config_default(n0=L, n1=L, n_blocks=n_blocks, precision=precision, **cfg)
+        self.cfg = ppd_config_default(n0=L, n1=self.L1, n_blocks=n_blocks, precision=precision, **cfg)
         self.ctx = ppd_create(self.cfg)
         self.M = 0
 
@@ -360,7 +379,7 @@ class Solver:
         return ppd_iterate(self.ctx, n, self.n_blocks, stats)
 
     def image(self) -> np.ndarray:
-        return ppd_get_image(self.ctx, self.L, self.L)
+        return ppd_get_image(self.ctx, self.L, self.L1)
 
     def reweighted(self, n_reweights: int, iters: int, omega0: float = 1e-2, factor: float = 0.25,
                    stats_every: int = 0):

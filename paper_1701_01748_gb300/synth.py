@@ -30,15 +30,15 @@ import numpy as np
 
 __all__ = ["Problem", "CONFIGS", "make_problem", "make_batch", "make_batch32", "sky_image", "sample_uv",
            "sample_uv_ggd", "radial_blocks", "exact_visibilities", "gaussian_visibilities",
-           "point_visibilities", "active_sets"]
+           "point_visibilities", "active_sets", "power_start", "splitmix64", "smooth_sides"]
 
 
 @dataclasses.dataclass
 class Problem:
     """One synthetic imaging problem (all arrays FP64 / int32, host)."""
     name: str
-    L: int                    # image side (square images, L x L)
-    x_true: np.ndarray        # (L, L) float64, >= 0
+    L: int                    # image rows (an L x L1 image)
+    x_true: np.ndarray        # (L, L1) float64, >= 0
     omega: np.ndarray         # (M, 2) float64 in [-pi, pi); col 0 -> image rows
     y: np.ndarray             # (M,) complex128, raw (un-whitened) visibilities
     sigma: float              # noise standard deviation of each complex visibility
@@ -47,6 +47,11 @@ class Problem:
     n_blocks: int
     isnr_db: float
     seed: int
+    L1: int | None = None     # image columns (None: square, L1 = L)
+
+    def __post_init__(self):
+        if self.L1 is None:
+            self.L1 = self.L
 
     @property
     def M(self) -> int:
@@ -67,7 +72,8 @@ CONFIGS = {
 
 
 def sky_image(L: int, rng: np.random.Generator, n_points: int = 20,
-              n_blobs: int = 3, compact: bool = False, params_out: list | None = None):
+              n_blobs: int = 3, compact: bool = False, params_out: list | None = None,
+              L1: int | None = None):
     """Positive test sky: point sources plus elliptical Gaussian blobs.
 
     Returns (points, blob_image): points is a list of (row, col, flux) with
@@ -78,19 +84,29 @@ def sky_image(L: int, rng: np.random.Generator, n_points: int = 20,
     [1e-2, 1e-1].  compact=True keeps every blob at least 6 standard
     deviations inside the image (centres in [0.3L, 0.7L], major-axis std in
     [0.03L, 0.05L]) so that its spectrum is the analytic Gaussian one to
-    ~1e-8 (see gaussian_visibilities); the draws are the same.  params_out,
+    ~1e-8 (see gaussian_visibilities); the draws are the same.  L1 (default
+    L) gives an L x L1 image: positions and centres scale with each axis,
+    blob widths with the shorter side.  params_out,
     if given, receives (c0, c1, smaj, smin, angle, peak) per blob.
     """
-    pos = rng.integers(0, L, size=(n_points, 2))
+    L1 = L if L1 is None else L1
+    if L1 == L:
+        pos = rng.integers(0, L, size=(n_points, 2))
+    else:
+        pos = np.stack([rng.integers(0, L, size=n_points), rng.integers(0, L1, size=n_points)], axis=1)
     flux = 10.0 ** rng.uniform(-3.0, 0.0, size=n_points)
     points = [(int(p[0]), int(p[1]), float(f)) for p, f in zip(pos, flux)]
-    r = np.arange(L, dtype=np.float64)
-    R0, R1 = np.meshgrid(r, r, indexing="ij")
-    blob = np.zeros((L, L))
+    R0, R1 = np.meshgrid(np.arange(L, dtype=np.float64), np.arange(L1, dtype=np.float64), indexing="ij")
+    blob = np.zeros((L, L1))
+    Ls = min(L, L1)
     clo, chi = (0.3 * L, 0.7 * L) if compact else (L / 4, 3 * L / 4)
-    slo, shi = (0.03 * L, 0.05 * L) if compact else (0.02 * L, 0.08 * L)
+    slo, shi = (0.03 * Ls, 0.05 * Ls) if compact else (0.02 * Ls, 0.08 * Ls)
     for _ in range(n_blobs):
-        c0, c1 = rng.uniform(clo, chi, size=2)
+        if L1 == L:
+            c0, c1 = rng.uniform(clo, chi, size=2)
+        else:
+            f0, f1 = (0.3, 0.7) if compact else (0.25, 0.75)
+            c0, c1 = rng.uniform(f0, f1, size=2) * np.array([L, L1], dtype=np.float64)
         smaj = rng.uniform(slo, shi)
         smin = smaj * rng.uniform(0.3, 1.0)
         ang = rng.uniform(0.0, math.pi)
@@ -157,12 +173,12 @@ def _phase_rows(w: np.ndarray, L: int) -> np.ndarray:
 
 def exact_visibilities(points, blob: np.ndarray, omega: np.ndarray,
                        chunk: int = 8192) -> np.ndarray:
-    """Exact y_m = sum_n x[n] exp(-i <omega_m, n - L/2>) of the pixel sky."""
-    L = blob.shape[0]
+    """Exact y_m = sum_n x[n] exp(-i <omega_m, n - L/2>) of the pixel sky (L = (L0, L1))."""
+    L0, L1 = blob.shape
     M = omega.shape[0]
     y = np.zeros(M, dtype=np.complex128)
     for (p0, p1, f) in points:
-        y += f * np.exp(-1j * (omega[:, 0] * (p0 - L / 2) + omega[:, 1] * (p1 - L / 2)))
+        y += f * np.exp(-1j * (omega[:, 0] * (p0 - L0 / 2) + omega[:, 1] * (p1 - L1 / 2)))
     if np.any(blob):
         U, s, Vt = np.linalg.svd(blob)
         r = int(np.sum(s > s[0] * 1e-15))
@@ -170,19 +186,21 @@ def exact_visibilities(points, blob: np.ndarray, omega: np.ndarray,
         V = Vt[:r, :].T
         for i in range(0, M, chunk):
             w = omega[i:i + chunk]
-            e0 = _phase_rows(w[:, 0], L) @ Us
-            e1 = _phase_rows(w[:, 1], L) @ V
+            e0 = _phase_rows(w[:, 0], L0) @ Us
+            e1 = _phase_rows(w[:, 1], L1) @ V
             y[i:i + chunk] += np.sum(e0 * e1, axis=1)
     return y
 
 
-def gaussian_visibilities(params, omega: np.ndarray, L: int, chunk: int = 1 << 22) -> np.ndarray:
+def gaussian_visibilities(params, omega: np.ndarray, L: int, chunk: int = 1 << 22,
+                          L1: int | None = None) -> np.ndarray:
     """Spectra of the Gaussian blobs at omega (sign and origin of exact_visibilities):
     for a blob A exp(-(a^2/smaj^2 + b^2/smin^2)/2) centred at c, the sum over the
     integer lattice is A 2 pi smaj smin exp(-omega^T S omega / 2) exp(-i <omega, c - L/2>)
     with omega^T S omega = smaj^2 (cos t w0 + sin t w1)^2 + smin^2 (-sin t w0 + cos t w1)^2
     (Poisson summation; the aliased terms and the part of the blob outside
     the image are below 1e-8 for compact blobs)."""
+    L1 = L if L1 is None else L1
     M = omega.shape[0]
     y = np.zeros(M, dtype=np.complex128)
     for i in range(0, M, chunk):
@@ -191,30 +209,53 @@ def gaussian_visibilities(params, omega: np.ndarray, L: int, chunk: int = 1 << 2
             ca, sa = math.cos(ang), math.sin(ang)
             q = (smaj * (ca * w0 + sa * w1)) ** 2 + (smin * (-sa * w0 + ca * w1)) ** 2
             amp = peak * 2.0 * math.pi * smaj * smin * np.exp(-0.5 * q)
-            y[i:i + chunk] += amp * np.exp(-1j * (w0 * (c0 - L / 2) + w1 * (c1 - L / 2)))
+            y[i:i + chunk] += amp * np.exp(-1j * (w0 * (c0 - L / 2) + w1 * (c1 - L1 / 2)))
     return y
 
 
-def point_visibilities(points, omega: np.ndarray, L: int, chunk: int = 1 << 22) -> np.ndarray:
+def point_visibilities(points, omega: np.ndarray, L: int, chunk: int = 1 << 22,
+                       L1: int | None = None) -> np.ndarray:
     """Exact spectra of the point sources (chunked)."""
+    L1 = L if L1 is None else L1
     M = omega.shape[0]
     y = np.zeros(M, dtype=np.complex128)
     for i in range(0, M, chunk):
         w0, w1 = omega[i:i + chunk, 0], omega[i:i + chunk, 1]
         for (p0, p1, f) in points:
-            y[i:i + chunk] += f * np.exp(-1j * (w0 * (p0 - L / 2) + w1 * (p1 - L / 2)))
+            y[i:i + chunk] += f * np.exp(-1j * (w0 * (p0 - L / 2) + w1 * (p1 - L1 / 2)))
     return y
 
 
+def smooth_sides(lo: int, hi: int) -> list:
+    """Image sides 16 * 2^a 3^b 5^c in [lo, hi]: multiples of 16 whose
+    oversampled grid side 2 L has no prime factor above 5."""
+    out = []
+    for L in range(16 * ((lo + 15) // 16), hi + 1, 16):
+        m = L // 16
+        for f in (2, 3, 5):
+            while m % f == 0:
+                m //= f
+        if m == 1:
+            out.append(L)
+    return out
+
+
 def make_batch(n: int = 8, seed: int = 1704, sides=(128, 256), ratio=(2.0, 8.0), blocks=(4, 32),
-               compact: bool = False):
-    """n independent problems of different sizes: side log-uniform over `sides`
-    (powers of two), M = r * L^2 with r log-uniform in `ratio`, block count
-    uniform in `blocks`, strongly non-uniform coverage (std 0.1 pi)."""
+               compact: bool = False, side_range: tuple | None = None):
+    """n independent problems of different sizes: side drawn from `sides`
+    (uniformly), or, with side_range = (lo, hi), log-uniform in [lo, hi] and
+    rounded to the nearest 16 * 2^a 3^b 5^c; M = r * L^2 with r log-uniform in
+    `ratio`, block count uniform in `blocks`, strongly non-uniform coverage
+    (std 0.1 pi)."""
     rng = np.random.default_rng(seed)
+    grid = smooth_sides(*side_range) if side_range else None
     out = []
     for i in range(n):
-        L = int(sides[int(rng.integers(0, len(sides)))])
+        if grid:
+            t = math.exp(rng.uniform(math.log(side_range[0]), math.log(side_range[1])))
+            L = min(grid, key=lambda v: (abs(v - t), v))
+        else:
+            L = int(sides[int(rng.integers(0, len(sides)))])
         r = math.exp(rng.uniform(math.log(ratio[0]), math.log(ratio[1])))
         d = int(rng.integers(blocks[0], blocks[1] + 1))
         out.append(make_problem(f"batch_{i}", L=L, M=int(round(r * L * L)), n_blocks=d, uv_sigma=0.1,
@@ -223,19 +264,21 @@ def make_batch(n: int = 8, seed: int = 1704, sides=(128, 256), ratio=(2.0, 8.0),
 
 
 def make_batch32(seed: int = 1704):
-    """32 independent problems, sides 256, 512 or 1024 (log-uniform), M = 2-8 x
-    the pixel count, 4-32 blocks: the batched workload of independent problems."""
-    return make_batch(32, seed=seed, sides=(256, 512, 1024), ratio=(2.0, 8.0), blocks=(4, 32), compact=True)
+    """32 independent problems, sides log-uniform in [256, 1024] rounded to the
+    nearest 16 * 2^a 3^b 5^c, M = 2-8 x the pixel count, 4-32 blocks: the
+    batched workload of independent problems."""
+    return make_batch(32, seed=seed, ratio=(2.0, 8.0), blocks=(4, 32), compact=True, side_range=(256, 1024))
 
 
 def make_problem(name: str = "c1_128", *, L: int | None = None, M: int | None = None,
                  n_blocks: int | None = None, uv_sigma: float | None = None,
                  seed: int | None = None, isnr_db: float = 30.0,
                  n_points: int = 20, n_blobs: int = 3, ggd_beta: float | None = None,
-                 compact: bool | None = None) -> Problem:
+                 compact: bool | None = None, L1: int | None = None) -> Problem:
     """Build a seeded problem; keyword arguments override the named shape.
     compact: blobs kept well inside the image and their visibilities taken
-    from the analytic Gaussian spectra (large problems; see sky_image)."""
+    from the analytic Gaussian spectra (large problems; see sky_image).
+    L1: number of image columns when it differs from L (rows)."""
     cfg = dict(CONFIGS.get(name, CONFIGS["c1_128"]))
     for k, v in dict(L=L, M=M, n_blocks=n_blocks, uv_sigma=uv_sigma, seed=seed, compact=compact).items():
         if v is not None:
@@ -243,8 +286,10 @@ def make_problem(name: str = "c1_128", *, L: int | None = None, M: int | None = 
     is_compact = bool(cfg.get("compact", False))
     rng = np.random.default_rng(cfg["seed"])
     Lv = int(cfg["L"])
+    L1v = Lv if L1 is None else int(L1)
     params = []
-    points, blob = sky_image(Lv, rng, n_points=n_points, n_blobs=n_blobs, compact=is_compact, params_out=params)
+    points, blob = sky_image(Lv, rng, n_points=n_points, n_blobs=n_blobs, compact=is_compact, params_out=params,
+                             L1=L1v)
     x = blob.copy()
     for (p0, p1, f) in points:
         x[p0, p1] += f
@@ -254,7 +299,7 @@ def make_problem(name: str = "c1_128", *, L: int | None = None, M: int | None = 
         omega = sample_uv_ggd(int(cfg["M"]), float(ggd_beta), float(cfg["uv_sigma"]), rng)
     block = radial_blocks(omega, int(cfg["n_blocks"]))
     if is_compact:
-        y0 = point_visibilities(points, omega, Lv) + gaussian_visibilities(params, omega, Lv)
+        y0 = point_visibilities(points, omega, Lv, L1=L1v) + gaussian_visibilities(params, omega, Lv, L1=L1v)
     else:
         y0 = exact_visibilities(points, blob, omega)
     Mv = omega.shape[0]
@@ -262,7 +307,7 @@ def make_problem(name: str = "c1_128", *, L: int | None = None, M: int | None = 
     noise = sigma * (rng.normal(size=Mv) + 1j * rng.normal(size=Mv)) / math.sqrt(2.0)
     return Problem(name=name, L=Lv, x_true=x, omega=omega, y=y0 + noise, sigma=sigma,
                    theta=np.full(Mv, 1.0 / sigma), block=block,
-                   n_blocks=int(cfg["n_blocks"]), isnr_db=isnr_db, seed=int(cfg["seed"]))
+                   n_blocks=int(cfg["n_blocks"]), isnr_db=isnr_db, seed=int(cfg["seed"]), L1=L1v)
 
 
 def active_sets(n_iters: int, n_blocks: int, p_data: float, p_prior: float, seed: int = 1706,
@@ -278,3 +323,31 @@ def active_sets(n_iters: int, n_blocks: int, p_data: float, p_prior: float, seed
     blocks = (rng.random((n_iters, n_blocks)) < p_data).astype(np.uint8)
     bases = (rng.random((n_iters, n_bases)) < p_prior).astype(np.uint8)
     return blocks, bases
+
+
+def splitmix64(counter: np.ndarray) -> np.ndarray:
+    """SplitMix64 finaliser (Steele, Lea & Flood 2014) of uint64 counters:
+    the generator's output for a state that has just been advanced to
+    `counter`."""
+    z = np.asarray(counter, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def power_start(n0: int, n1: int, seed: int) -> np.ndarray:
+    """Seeded start image of a power iteration (an input, like the data):
+    all ones for seed 0, else x_i = 0.5 + 2^-53 (s_i >> 11) with s_i the
+    SplitMix64 output for the counter seed + (i + 1) * 0x9E3779B97F4A7C15,
+    i the row-major pixel index; normalised to unit l2 norm."""
+    n = n0 * n1
+    if seed == 0:
+        x = np.ones(n)
+    else:
+        i = np.arange(1, n + 1, dtype=np.uint64)
+        with np.errstate(over="ignore"):
+            ctr = np.uint64(seed) + i * np.uint64(0x9E3779B97F4A7C15)
+        x = 0.5 + (splitmix64(ctr) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    x = x.reshape(n0, n1)
+    return x / np.linalg.norm(x)

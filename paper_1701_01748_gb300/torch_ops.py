@@ -31,7 +31,7 @@ class PhiFunction(torch.autograd.Function):
     def backward(ctx, g: torch.Tensor):
         solver = ctx.solver
         gr = torch.view_as_real(g.contiguous()).contiguous()
-        out = torch.empty((solver.L, solver.L), dtype=gr.dtype, device=gr.device)
+        out = torch.empty((solver.L, solver.L1), dtype=gr.dtype, device=gr.device)
         s = torch.cuda.current_stream(gr.device).cuda_stream
         ppd.ppd_op_adjoint(solver.ctx, gr.data_ptr(), out.data_ptr(), s)
         return out, None

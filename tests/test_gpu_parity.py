@@ -155,15 +155,40 @@ def test_psi_analysis_synthesis(prec):
 
 
 @pytest.mark.parametrize("prec", [F32, F64])
-def test_eta_power_iteration(prec):
+@pytest.mark.parametrize("method", ["lanczos", "power"])
+def test_eta_operator_norm(prec, method):
+    """||U^{1/2} Phi||_S^2 by the library's Lanczos process (default) or power
+    iteration, against the oracle's routine of the same name."""
     p = problem("small", **SMALL)
     P = nufft.Plan(p.omega, p.L, theta=p.theta)
     U = nufft.uniform_weights(p.omega, 2 * p.L, 2 * p.L)[0]
-    ref, _ = oppd.op_norm_sq(P, U, max_iter=1000, tol=1e-10)
-    s = solver(p, prec)
+    if method == "power":
+        ref, _ = oppd.op_norm_sq(P, U, max_iter=1000, tol=1e-10)
+        s = solver(p, prec, norm_method=ppd.PPD_NORM_POWER)
+    else:
+        ref, _ = oppd.op_norm_sq_lanczos(P, U, tol=1e-12)
+        s = solver(p, prec)
     got = s.params()
     assert abs(got["op_norm_sq"] - ref) <= (1e-5 if prec == F32 else 1e-8) * ref
     assert got["convergence_lhs"] < 1.0
+    if method == "lanczos":
+        assert got["power_iters_done"] < 200
+    s.close()
+
+
+def test_lanczos_gets_the_norm_the_power_iteration_misses():
+    """The 512^2 workload (strongly non-uniform coverage): the library's
+    Lanczos estimate equals the oracle's stored Lanczos value, which 20 power
+    steps underestimate by >10 %."""
+    import json
+    import os
+    p = problem("c2_512")
+    rec = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "op_norms.json")))["c2_512"]
+    assert rec["seed"] == p.seed and rec["M"] == p.M
+    s = solver(p, F32)
+    got = s.params()
+    assert abs(got["op_norm_sq"] - rec["op_norm_sq"]) <= 1e-4 * rec["op_norm_sq"]
+    assert got["power_iters_done"] < 300
     s.close()
 
 

@@ -1,0 +1,136 @@
+"""Stopping tests of Algorithms 2 and 3 and the seeded power iteration: CUDA
+path against the FP64 oracle through the C ABI.
+
+Algorithm 2 with inner_tol: the per-block step counts of every iteration must
+equal the oracle's and the image must match within the fixed-count tolerance
+(1e-4 relative in FP32, 1e-8 in FP64).  Algorithm 3 with stop_tol: the
+iteration at which ppd_iterate stops must equal the oracle's run_until.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import nufft, ppd as oppd  # noqa: E402
+from paper_1701_01748_gb300 import build, ppd, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+F32, F64 = ppd.PPD_FP32_FP64NORMS, ppd.PPD_FP64_PLAIN
+IMG = {F32: 1e-4, F64: 1e-8}
+SMALL = dict(L=32, M=3000, n_blocks=3, uv_sigma=0.3, seed=11, n_points=6, n_blobs=1)
+
+
+@pytest.fixture(scope="session", autouse=True)
+def lib():
+    build.build()
+    assert torch.cuda.is_available()
+    return ppd._lib()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def pair(p, prec, **kw):
+    S = oppd.make_setup(p.omega, p.y, p.theta, p.block, p.n_blocks, p.L, power_iters=400, x_true=p.x_true,
+                        n_itr=kw.get("n_itr", 1), inner_tol=kw.get("inner_tol", 0.0),
+                        inner_init="current" if kw.get("inner_init") == ppd.PPD_INNER_CURRENT else "warm",
+                        inner_solver="fista" if kw.get("inner_solver") == ppd.PPD_INNER_FISTA else "fb")
+    s = ppd.Solver(p.L, p.n_blocks, precision=prec, eta=S.eta, **kw)
+    s.set_problem(p.omega, p.y, p.block, theta=p.theta, x_true=p.x_true)
+    return S, s
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
+@pytest.mark.parametrize("variant", ["warm", "current", "fista"])
+def test_inner_stopping_test_matches_oracle(prec, variant):
+    """Algorithm 2 stopped by ||zbar^t - zbar^(t-1)|| <= tol ||zbar^t|| (cap 12
+    steps): same per-block step counts as the oracle at every iteration, blocks
+    stopping at different steps, same image."""
+    p = synth.make_problem("small", **SMALL)
+    kw = dict(n_itr=12, inner_tol=2e-3)
+    if variant == "current":
+        kw["inner_init"] = ppd.PPD_INNER_CURRENT
+    if variant == "fista":
+        kw["inner_solver"] = ppd.PPD_INNER_FISTA
+    S, s = pair(p, prec, **kw)
+    st = oppd.init_state(S)
+    distinct = False
+    for it in range(15):
+        h = oppd.iterate(st, S)
+        out = s.iterate(1)
+        assert np.array_equal(out["inner_steps"], h["inner_steps"]), (it, out["inner_steps"], h["inner_steps"])
+        distinct = distinct or len(set(h["inner_steps"].tolist())) > 1
+    assert distinct, "every block stopped at the same step: the case of a block stopping early is not covered"
+    assert rel(s.image(), st.x) <= IMG[prec], rel(s.image(), st.x)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
+def test_inner_stopping_test_in_the_graph_and_without(prec):
+    """The stopping test inside the captured graph gives what the eager launches give."""
+    p = synth.make_problem("small", **SMALL)
+    imgs = []
+    for graph in (1, 0):
+        S, s = pair(p, prec, n_itr=8, inner_tol=1e-3, use_graph=graph)
+        s.iterate(20, stats=False)
+        imgs.append(s.image())
+        s.close()
+    assert np.array_equal(imgs[0], imgs[1])
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
+@pytest.mark.parametrize("every", [1, 5])
+def test_global_stopping_rule_matches_oracle(prec, every):
+    """ppd_iterate with stop_tol stops at the oracle's iteration (relative
+    variation below stop_tol and every block residual within 1.005 eps_j,
+    tested after every `every`-th iteration) with the same image."""
+    p = synth.make_problem("small", **SMALL)
+    tol = 3e-3
+    S, s = pair(p, prec, stop_tol=tol, stop_every=every)
+    st, hist, stopped = oppd.run_until(S, 400, tol, check_every=every)
+    assert stopped
+    out = s.iterate(400)
+    assert out["stopped"] and out["iters_run"] == len(hist) and out["iters_done"] == len(hist)
+    assert rel(s.image(), st.x) <= IMG[prec]
+    # stopped: a further call stops after its first tested iteration (the rule still holds)
+    again = s.iterate(400)
+    assert again["stopped"] and again["iters_run"] == every
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
+def test_seeded_power_iteration_start(prec):
+    """config.seed picks the power iteration's start vector; after a fixed
+    number of steps the norm equals the oracle's from synth.power_start."""
+    p = synth.make_problem("small", **SMALL)
+    P = nufft.Plan(p.omega, p.L, theta=p.theta)
+    U = nufft.uniform_weights(p.omega, 2 * p.L, 2 * p.L)[0]
+    vals = {}
+    for seed in (0, 99991):
+        ref, it = oppd.op_norm_sq(P, U, max_iter=6, tol=1e-300, start=synth.power_start(p.L, p.L, seed))
+        s = ppd.Solver(p.L, p.n_blocks, precision=prec, seed=seed, power_iters=6, power_tol=1e-300,
+                       norm_method=ppd.PPD_NORM_POWER)
+        s.set_problem(p.omega, p.y, p.block, theta=p.theta)
+        got = s.params()
+        assert got["power_iters_done"] == 6 == it
+        assert abs(got["op_norm_sq"] - ref) <= (2e-6 if prec == F32 else 1e-12) * ref
+        vals[seed] = ref
+        s.close()
+    assert vals[0] != vals[99991]
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
+def test_seeded_lanczos_start(prec):
+    """The Lanczos estimate from a seeded start equals the oracle's value (the
+    largest eigenvalue does not depend on the start)."""
+    p = synth.make_problem("small", **SMALL)
+    P = nufft.Plan(p.omega, p.L, theta=p.theta)
+    U = nufft.uniform_weights(p.omega, 2 * p.L, 2 * p.L)[0]
+    ref, _ = oppd.op_norm_sq_lanczos(P, U, tol=1e-12)
+    for seed in (0, 4242):
+        s = ppd.Solver(p.L, p.n_blocks, precision=prec, seed=seed)
+        s.set_problem(p.omega, p.y, p.block, theta=p.theta)
+        assert abs(s.params()["op_norm_sq"] - ref) <= (1e-5 if prec == F32 else 1e-8) * ref
+        s.close()

@@ -54,3 +54,40 @@ def test_batch_shapes_stay_in_their_ranges():
     for p in probs:
         assert 2.0 * p.L ** 2 - 1 <= p.M <= 8.0 * p.L ** 2 + 1
         assert 2 <= p.n_blocks <= 5 and p.block.max() < p.n_blocks
+
+
+def test_splitmix64_published_outputs_and_power_start():
+    """SplitMix64 from state 0 gives 0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4
+    (the generator's published first outputs); power_start draws in [0.5, 1.5)
+    before normalisation and is all ones for seed 0."""
+    import numpy as np
+    g = np.uint64(0x9E3779B97F4A7C15)
+    with np.errstate(over="ignore"):
+        out = synth.splitmix64(np.array([g, g * np.uint64(2)], dtype=np.uint64))
+    assert [int(v) for v in out] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4]
+    x = synth.power_start(8, 6, 1234)
+    assert x.shape == (8, 6) and abs(np.linalg.norm(x) - 1.0) < 1e-15
+    r = x / x.max()
+    assert r.min() > 0.5 / 1.5 - 1e-12
+    assert np.array_equal(synth.power_start(4, 4, 0), np.full((4, 4), 0.25))
+
+
+def test_batch_sides_are_five_smooth_multiples_of_16():
+    """The batched workload's sides: log-uniform draws rounded to the nearest
+    16 * 2^a 3^b 5^c, so every oversampled grid side 2 L is 5-smooth."""
+    assert synth.smooth_sides(256, 1024) == [256, 288, 320, 384, 400, 432, 480, 512, 576, 640, 720, 768, 800,
+                                             864, 960, 1024]
+    probs = synth.make_batch(5, seed=3, side_range=(16, 96), ratio=(2.0, 3.0), blocks=(2, 3))
+    for p in probs:
+        assert p.L in synth.smooth_sides(16, 96) and p.x_true.shape == (p.L, p.L)
+        assert 2 * p.L * p.L <= p.M <= 3 * p.L * p.L + 1
+
+
+def test_rectangular_problem_data_are_the_exact_measurement():
+    """An L x L1 problem: noise-free data equal the direct DTFT of the pixel sky."""
+    import numpy as np
+    from oracle import nufft
+    p = synth.make_problem("rect", L=32, L1=48, M=300, n_blocks=2, uv_sigma=0.3, seed=4, isnr_db=300.0)
+    assert p.x_true.shape == (32, 48) and p.L1 == 48
+    y = nufft.nudft(p.x_true, p.omega)
+    assert np.abs(p.y - y).max() <= 1e-9 * np.abs(y).max()
