@@ -149,3 +149,47 @@ def test_psi_at_4096():
     torch.cuda.synchronize()
     assert rel(rd.cpu().double().numpy(), p.x_true) <= 1e-5     # Psi Psi^dagger = I
     s.close()
+
+
+def test_phi_gradient_at_1024():
+    """Phi as a torch.autograd.Function at the 1024^2 / 4M-visibility size:
+    the gradient of 1/2 ||y - Phi x||^2 (backward = the library's Phi^dagger)
+    in FP32 and FP64 against the oracle's FP64 gradient Phi^dagger(Phi x - y),
+    and against central finite differences of the loss along random
+    directions (loss through the library's FP64 Phi, whose parity with the
+    oracle is checked above)."""
+    from paper_1701_01748_gb300 import torch_ops
+    p = problem("c3_1024")
+    P = nufft.Plan(p.omega, p.L, theta=p.theta)
+    yw = p.theta * p.y
+    x0 = p.x_true
+    g_ref = nufft.phi_adjoint(nufft.phi(x0, P) - yw, P)
+    del P
+    rng = np.random.default_rng(23)
+    dirs = [rng.normal(size=x0.shape) for _ in range(3)]
+    s64 = ppd.Solver(p.L, p.n_blocks, precision=ppd.PPD_FP64_PLAIN, eta=1.0)
+    s64.set_problem(p.omega, p.y, p.block, theta=p.theta)
+    yt64 = torch.tensor(yw, dtype=torch.complex128, device="cuda")
+
+    def loss64(x):
+        xt = torch.tensor(x, dtype=torch.float64, device="cuda")
+        with torch.no_grad():
+            return 0.5 * float((torch_ops.phi(xt, s64) - yt64).abs().pow(2).sum())
+
+    for prec, dt, ct, tol in ((F32, torch.float32, torch.complex64, 1e-4),
+                              (ppd.PPD_FP64_PLAIN, torch.float64, torch.complex128, 1e-9)):
+        s = s64 if prec == ppd.PPD_FP64_PLAIN else ppd.Solver(p.L, p.n_blocks, precision=prec, eta=1.0)
+        if s is not s64:
+            s.set_problem(p.omega, p.y, p.block, theta=p.theta)
+        x = torch.tensor(x0, dtype=dt, device="cuda", requires_grad=True)
+        loss = 0.5 * (torch_ops.phi(x, s) - torch.tensor(yw, dtype=ct, device="cuda")).abs().pow(2).sum()
+        loss.backward()
+        g = x.grad.cpu().double().numpy()
+        assert rel(g, g_ref) <= tol, (prec, rel(g, g_ref))
+        for d in dirs:
+            h = 1e-3
+            fd = (loss64(x0 + h * d) - loss64(x0 - h * d)) / (2 * h)
+            assert abs(fd - float(np.sum(g * d))) <= 1e-3 * abs(fd), (prec, fd, float(np.sum(g * d)))
+        if s is not s64:
+            s.close()
+    s64.close()
