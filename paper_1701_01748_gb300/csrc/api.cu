@@ -119,7 +119,7 @@ void free_vis(ppd_ctx *c) {
     for (void *p : {c->rec, c->theta_v, c->y, c->v, c->z, c->w, c->p, c->y_raw, (void *)c->perm,
                     (void *)c->count_cell, (void *)c->ch.start, (void *)c->ch.count, (void *)c->ch.tile,
                     (void *)c->ch.block, (void *)c->ch.tile_first, (void *)c->ch.tile_n, (void *)c->ch.blk_ptr,
-                    (void *)c->ch.blk_list, (void *)c->ch.active, (void *)c->partials, (void *)c->scale, (void *)c->resid2,
+                    (void *)c->ch.blk_pos, (void *)c->ch.active, (void *)c->partials, (void *)c->scale, (void *)c->resid2,
                     (void *)c->eps_d, (void *)c->mu_d, c->gpart})
         dfree(p);
     c->rec = c->theta_v = c->y = c->v = c->z = c->w = c->p = c->y_raw = c->gpart = nullptr;
@@ -928,12 +928,14 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
             }
         }
     }
-    std::vector<int32_t> bptr(c->d + 1, 0), blist(nch);
+    // block-major partial slots: block b owns slots bptr[b] .. bptr[b+1] - 1,
+    // chunk k writes slot bpos[k] (chunks of a block in processing order)
+    std::vector<int32_t> bptr(c->d + 1, 0), bpos(nch);
     for (int64_t k = 0; k < nch; ++k) bptr[cbk[k] + 1]++;
     for (int j = 0; j < c->d; ++j) bptr[j + 1] += bptr[j];
     {
         std::vector<int32_t> fill(bptr.begin(), bptr.end() - 1);
-        for (int64_t k = 0; k < nch; ++k) blist[fill[cbk[k]]++] = (int32_t)k;
+        for (int64_t k = 0; k < nch; ++k) bpos[k] = fill[cbk[k]]++;
     }
     c->ch.n = nch;
     c->ch.n_active = (int64_t)active.size();
@@ -942,7 +944,7 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
     if ((st = dalloc(&c->ch.start, nch)) || (st = dalloc(&c->ch.count, nch)) || (st = dalloc(&c->ch.tile, nch)) ||
         (st = dalloc(&c->ch.block, nch)) || (st = dalloc(&c->ch.tile_first, ntiles)) ||
         (st = dalloc(&c->ch.tile_n, ntiles)) || (st = dalloc(&c->ch.blk_ptr, c->d + 1)) ||
-        (st = dalloc(&c->ch.blk_list, nch)) || (st = dalloc(&c->ch.active, active.size())) ||
+        (st = dalloc(&c->ch.blk_pos, nch)) || (st = dalloc(&c->ch.active, active.size())) ||
         (st = dalloc(&c->partials, 2 * NPART * (size_t)nch)) ||
         (st = dalloc(&c->scale, c->d)) || (st = dalloc(&c->resid2, c->d)) || (st = dalloc(&c->eps_d, c->d)) ||
         (st = dalloc(&c->mu_d, c->d)) || (st = dalloc_bytes(&c->gpart, (size_t)nch * E * E * cbsz)) ||
@@ -976,7 +978,7 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
         (e = cudaMemcpy(c->ch.tile_first, tfirst.data(), ntiles * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->ch.tile_n, tn.data(), ntiles * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->ch.blk_ptr, bptr.data(), (c->d + 1) * 4, cudaMemcpyHostToDevice)) ||
-        (e = cudaMemcpy(c->ch.blk_list, blist.data(), nch * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->ch.blk_pos, bpos.data(), nch * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->ch.active, active.data(), active.size() * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->perm, c->perm_h.data(), M * 8, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->y_raw, yraw_sorted.data(), 2 * M * 8, cudaMemcpyHostToDevice))) {

@@ -116,7 +116,7 @@ struct Chunks {
     int64_t n = 0;
     int32_t *start = nullptr, *count = nullptr, *tile = nullptr, *block = nullptr;   // device
     int32_t *tile_first = nullptr, *tile_n = nullptr;                                // device, n_tiles
-    int32_t *blk_ptr = nullptr, *blk_list = nullptr;                                 // device CSR
+    int32_t *blk_ptr = nullptr, *blk_pos = nullptr;   // device: block b's partial slots, slot of each chunk
     int32_t *active = nullptr;   // tiles the combine pass writes (device)
     int64_t n_active = 0;
 };

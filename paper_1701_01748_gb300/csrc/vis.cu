@@ -117,7 +117,9 @@ template <typename R> struct VisArgs {
     const double *mu, *scale;
     double *partials;            // this launch's chunk partials
     const double *part_in;       // previous step's chunk partials (P_B scale)
-    const int32_t *blk_ptr, *blk_list;
+    // chunk partials live in block-major slots: chunk ch writes slot
+    // blk_pos[ch]; block b's slots are blk_ptr[b] .. blk_ptr[b+1] - 1
+    const int32_t *blk_ptr, *blk_pos;
     const double *eps;
     int *err;
     // randomised active sets (null: every block active): the current
@@ -185,33 +187,46 @@ constexpr int DG_NT = 256;
 // chunk partials summed in a fixed order (the same result in every CTA).
 // With `test`, *stop also receives Algorithm 2's stopping test of the
 // previous step, ||zbar^t - zbar^(t-1)|| <= inner_tol ||zbar^t||, in FP64.
+// Every thread of the CTA loads a strided share of the block's contiguous
+// slots (one round trip), then a fixed-order tree and warp order sum them.
 template <typename R> __device__ double block_scale(const VisArgs<R> &A, int blk, bool test = false,
                                                    bool *stop = nullptr) {
     __shared__ double sc_s;
     __shared__ int st_s;
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        double a = 0, dd = 0, nn = 0;
-        for (int k = A.blk_ptr[blk] + lane; k < A.blk_ptr[blk + 1]; k += 32) {
-            const double *q = A.part_in + NPART * (int64_t)A.blk_list[k];
-            a += q[0];
-            if (test) {
-                dd += q[2];
-                nn += q[3];
-            }
+    __shared__ double red[3][32];
+    double a = 0, dd = 0, nn = 0;
+    for (int k = A.blk_ptr[blk] + threadIdx.x; k < A.blk_ptr[blk + 1]; k += blockDim.x) {
+        const double *q = A.part_in + NPART * (int64_t)k;
+        a += q[0];
+        if (test) {
+            dd += q[2];
+            nn += q[3];
         }
+    }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_down_sync(0xffffffffu, a, o);
-            dd += __shfl_down_sync(0xffffffffu, dd, o);
-            nn += __shfl_down_sync(0xffffffffu, nn, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        dd += __shfl_down_sync(0xffffffffu, dd, o);
+        nn += __shfl_down_sync(0xffffffffu, nn, o);
+    }
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[0][wid] = a;
+        red[1][wid] = dd;
+        red[2][wid] = nn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0, sd = 0, sn = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            sa += red[0][w];
+            sd += red[1][w];
+            sn += red[2][w];
         }
-        if (lane == 0) {
-            const double nrm = sqrt(a);
-            if (!isfinite(nrm)) atomicOr(A.err, ERR_NONFINITE);
-            sc_s = (nrm > A.eps[blk]) ? A.eps[blk] / nrm : 1.0;
-            st_s = test && sqrt(dd) <= A.inner_tol * sqrt(nn);
-        }
+        const double nrm = sqrt(sa);
+        if (!isfinite(nrm)) atomicOr(A.err, ERR_NONFINITE);
+        sc_s = (nrm > A.eps[blk]) ? A.eps[blk] / nrm : 1.0;
+        st_s = test && sqrt(sd) <= A.inner_tol * sqrt(sn);
     }
     __syncthreads();
     if (stop) *stop = st_s != 0;
@@ -391,7 +406,7 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
             }
             cur = nx;
         }
-        if (MODE != DG_OP) cta_sum2<DG_NT>(s_w.get(), s_r.get(), A.partials + NPART * (int64_t)ch);
+        if (MODE != DG_OP) cta_sum2<DG_NT>(s_w.get(), s_r.get(), A.partials + NPART * (int64_t)A.blk_pos[ch]);
         __syncthreads();   // the tile buffer is refilled two chunks later
     }
 }
@@ -416,7 +431,10 @@ __global__ void __launch_bounds__(DG_NT) k_subiter(VisArgs<R> A, int only_first,
     const bool act = !A.bmask || A.bmask[blk];
     const bool first_blk = A.seen && !A.seen[blk];
     if (!act || (only_first && !first_blk)) {
-        if (threadIdx.x == 0) A.partials[NPART * (int64_t)ch] = A.part_in[NPART * (int64_t)ch];
+        if (threadIdx.x == 0) {
+            const int64_t slot = NPART * (int64_t)A.blk_pos[ch];
+            A.partials[slot] = A.part_in[slot];
+        }
         return;
     }
     const bool tol_on = A.inner_tol > 0;
@@ -456,7 +474,7 @@ __global__ void __launch_bounds__(DG_NT) k_subiter(VisArgs<R> A, int only_first,
     __shared__ double o3[3];
     cta_sum3<DG_NT>(s_w.get(), s_d.get(), s_n.get(), o3);
     if (threadIdx.x == 0) {
-        double *out = A.partials + NPART * (int64_t)ch;
+        double *out = A.partials + NPART * (int64_t)A.blk_pos[ch];
         out[0] = o3[0];
         out[2] = o3[1];
         out[3] = o3[2];
@@ -468,7 +486,7 @@ __global__ void __launch_bounds__(DG_NT) k_subiter(VisArgs<R> A, int only_first,
 // scale_j = eps_j / ||w_j - y_j|| if that norm exceeds eps_j, else 1 (the
 // l2-ball projection P_B of Section 3.3 as a radial scale).
 __global__ void k_block_norms(const double *__restrict__ partials, const int32_t *__restrict__ blk_ptr,
-                              const int32_t *__restrict__ blk_list, const double *__restrict__ eps, int d,
+                              const double *__restrict__ eps, int d,
                               int with_resid, double *__restrict__ scale, double *__restrict__ resid2,
                               int *__restrict__ err) {
     const int j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
@@ -476,9 +494,8 @@ __global__ void k_block_norms(const double *__restrict__ partials, const int32_t
     if (j >= d) return;
     double a = 0, b = 0;
     for (int k = blk_ptr[j] + lane; k < blk_ptr[j + 1]; k += 32) {
-        const int ch = blk_list[k];
-        a += partials[NPART * (int64_t)ch];
-        if (with_resid) b += partials[NPART * (int64_t)ch + 1];
+        a += partials[NPART * (int64_t)k];
+        if (with_resid) b += partials[NPART * (int64_t)k + 1];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -494,9 +511,10 @@ __global__ void k_block_norms(const double *__restrict__ partials, const int32_t
 }
 
 // ----------------------------------------------------------------- gridding
-// Per CTA: phase 1 (thread per visibility) forms Theta v and the 16 weights
-// into a staging area; phase 2 (warp per visibility) adds the 8 x 8
-// footprint into the warp's private (T+8)^2 tile; phase 3 sums the private
+// Per CTA: phase 1 (thread per visibility) forms Theta v, the 8 products
+// w0[a] Theta v and the 8 weights w1[b] into a staging area; phase 2 (warp
+// per visibility) adds the 8 x 8 footprint w1[b] (w0[a] Theta v) into the
+// warp's private (T+8)^2 tile; phase 3 sums the private
 // tiles in warp order and writes the chunk's partial tile.  GR_DUAL fuses the
 // end of the data step: p = P_B(w) = y + c (w - y), v = U (z - p).
 // Lane l of the scattering warp owns footprint column l mod 8 of rows l/8
@@ -516,11 +534,10 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
     static_assert(P % 16 == 8, "private-tile pitch");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     C *priv = reinterpret_cast<C *>(smem_raw);                          // NW * E * P
-    R *sw0 = reinterpret_cast<R *>(priv + NW * E * P);                  // NT * 8
-    R *sw1 = sw0 + NT * KB_J;                                           // NT * 8
-    C *sv = reinterpret_cast<C *>(sw1 + NT * KB_J);                     // NT
-    int *slb = reinterpret_cast<int *>(sv + NT);                        // NT
-    float *poly = reinterpret_cast<float *>(slb + NT);                  // 80
+    C *sa = priv + NW * E * P;                                          // NT * 8: w0[a] Theta v, pairs (a, a+4)
+    R *sb = reinterpret_cast<R *>(sa + NT * KB_J);                      // NT * 8: w1[b]
+    int *slb = reinterpret_cast<int *>(sb + NT * KB_J);                 // NT
+    float *poly = reinterpret_cast<float *>(slb + NT);                  // 64
 
     const int ch = blockIdx.x;
     const int start = A.ch_start[ch], count = A.ch_count[ch], tl = A.ch_tile[ch];
@@ -561,7 +578,7 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
     __syncthreads();
 
     C *mine = priv + warp * E * P;
-    const int bcol = lane & 7, a0 = lane >> 3, a1 = a0 + 4;
+    const int bcol = lane & 7, a0 = lane >> 3;   // rows a0 and a0 + 4
     // this thread's visibility of the current round, loaded one round ahead
     // so that the loads of round r + 1 are in flight during the scatter of r
     struct In {
@@ -613,23 +630,23 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
                 if (MODE == GR_OP_U) vv = C{rc.U * vv.x, rc.U * vv.y};
             }
             const R th = cur.th;
-            sv[threadIdx.x] = C{th * vv.x, th * vv.y};
+            const C tv{th * vv.x, th * vv.y};
             R w0[KB_J], w1[KB_J];
             kb_weights(rc.f0, w0, poly, A.beta, A.inv_i0b);
             kb_weights(rc.f1, w1, poly, A.beta, A.inv_i0b);
-            if constexpr (sizeof(R) == 4) {   // 16-byte stores: 2-way instead of 8-way bank conflicts
-                float4 *d0 = reinterpret_cast<float4 *>(sw0 + threadIdx.x * KB_J);
-                float4 *d1 = reinterpret_cast<float4 *>(sw1 + threadIdx.x * KB_J);
-                d0[0] = make_float4(w0[0], w0[1], w0[2], w0[3]);
-                d0[1] = make_float4(w0[4], w0[5], w0[6], w0[7]);
-                d1[0] = make_float4(w1[0], w1[1], w1[2], w1[3]);
-                d1[1] = make_float4(w1[4], w1[5], w1[6], w1[7]);
+            C *da = sa + threadIdx.x * KB_J;
+#pragma unroll
+            for (int a = 0; a < KB_J / 2; ++a) {   // lane pair (a, a+4) reads one 2-complex word
+                da[2 * a] = C{w0[a] * tv.x, w0[a] * tv.y};
+                da[2 * a + 1] = C{w0[a + 4] * tv.x, w0[a + 4] * tv.y};
+            }
+            if constexpr (sizeof(R) == 4) {
+                float4 *db = reinterpret_cast<float4 *>(sb + threadIdx.x * KB_J);
+                db[0] = make_float4(w1[0], w1[1], w1[2], w1[3]);
+                db[1] = make_float4(w1[4], w1[5], w1[6], w1[7]);
             } else {
 #pragma unroll
-                for (int j = 0; j < KB_J; ++j) {
-                    sw0[threadIdx.x * KB_J + j] = w0[j];
-                    sw1[threadIdx.x * KB_J + j] = w1[j];
-                }
+                for (int j = 0; j < KB_J; ++j) sb[threadIdx.x * KB_J + j] = w1[j];
             }
             const int lb0 = (rc.packed & 0xffff) - row0, lb1 = ((rc.packed >> 16) & 0xffff) - col0;
             slb[threadIdx.x] = lb0 | (lb1 << 16);
@@ -658,13 +675,12 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
                 acc0 = C{0, 0};
                 acc1 = C{0, 0};
             }
-            const C tv = sv[i];
-            const R wb = sw1[i * KB_J + bcol];
-            const R w0 = sw0[i * KB_J + a0] * wb, w1 = sw0[i * KB_J + a1] * wb;
-            acc0.x += w0 * tv.x;
-            acc0.y += w0 * tv.y;
-            acc1.x += w1 * tv.x;
-            acc1.y += w1 * tv.y;
+            const C pa = sa[i * KB_J + 2 * a0], pb = sa[i * KB_J + 2 * a0 + 1];   // w0[a0] Theta v, w0[a1] Theta v
+            const R wb = sb[i * KB_J + bcol];
+            acc0.x += wb * pa.x;
+            acc0.y += wb * pa.y;
+            acc1.x += wb * pb.x;
+            acc1.y += wb * pb.y;
         }
         if (run >= 0) {
             C *cell = mine + ((run & 0xffff) + a0) * P + (run >> 16) + bcol;
@@ -754,7 +770,7 @@ template <typename R> VisArgs<R> make_args(ppd_ctx *c) {
     A.partials = c->part_out;
     A.part_in = c->part_in;
     A.blk_ptr = c->ch.blk_ptr;
-    A.blk_list = c->ch.blk_list;
+    A.blk_pos = c->ch.blk_pos;
     A.eps = c->eps_d;
     A.err = c->err;
     A.bmask = c->rand_on ? c->mask_cur : nullptr;
@@ -771,7 +787,7 @@ template <typename R> VisArgs<R> make_args(ppd_ctx *c) {
 
 template <typename R, int T> size_t grid_smem() {
     constexpr int NW = GridCfg<R>::NWARP, NT = NW * 32, E = T + HALO, P = E;
-    return (size_t)NW * E * P * sizeof(cplx_t<R>) + 2 * NT * KB_J * sizeof(R) + NT * sizeof(cplx_t<R>) +
+    return (size_t)NW * E * P * sizeof(cplx_t<R>) + NT * KB_J * sizeof(cplx_t<R>) + NT * KB_J * sizeof(R) +
            NT * sizeof(int) + (KB_DEG + 1) * KB_J * sizeof(float);
 }
 
@@ -916,7 +932,7 @@ int block_norms(ppd_ctx *c, int with_resid, cudaStream_t s) {
     int site;
     PPD_CHECK(launch_begin(c, "block_norms", s, &site));
     const int wpb = 8;
-    k_block_norms<<<(c->d + wpb - 1) / wpb, wpb * 32, 0, s>>>(c->part_out, c->ch.blk_ptr, c->ch.blk_list, c->eps_d,
+    k_block_norms<<<(c->d + wpb - 1) / wpb, wpb * 32, 0, s>>>(c->part_out, c->ch.blk_ptr, c->eps_d,
                                                                c->d, with_resid, c->scale, c->resid2, c->err);
     return launch_end(c, site, s);
 }
