@@ -119,7 +119,7 @@ void free_vis(ppd_ctx *c) {
     for (void *p : {c->rec, c->theta_v, c->y, c->v, c->z, c->w, c->p, c->y_raw, (void *)c->perm,
                     (void *)c->count_cell, (void *)c->ch.start, (void *)c->ch.count, (void *)c->ch.tile,
                     (void *)c->ch.block, (void *)c->ch.tile_first, (void *)c->ch.tile_n, (void *)c->ch.blk_ptr,
-                    (void *)c->ch.blk_pos, (void *)c->ch.active, (void *)c->partials, (void *)c->scale, (void *)c->resid2,
+                    (void *)c->ch.u_start, (void *)c->ch.u_count, (void *)c->ch.u_chunk, (void *)c->ch.u_pos, (void *)c->ch.active, (void *)c->partials, (void *)c->scale, (void *)c->resid2,
                     (void *)c->eps_d, (void *)c->mu_d, c->gpart})
         dfree(p);
     c->rec = c->theta_v = c->y = c->v = c->z = c->w = c->p = c->y_raw = c->gpart = nullptr;
@@ -238,7 +238,7 @@ template <typename R> int iteration_body(ppd_ctx *c, cudaStream_t s, bool first)
     PPD_CHECK(sara_level0<R>(c, ll0, s2));
     if (fork) PPD_CUDA(cudaEventRecord(c->ev_join, s2));
 
-    double *bank[2] = {c->partials, c->partials + NPART * c->ch.n};
+    double *bank[2] = {c->partials, c->partials + NPART * c->ch.nu};
     int cur = 0;
     // with the fused row kernel the forward row pass of xt was done by the
     // previous iteration's last kernel (or by run_iterations before the first)
@@ -747,6 +747,7 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
         (st = dalloc(&c->fwd_strips, c->K1)) || (st = dalloc(&c->inv_strips, c->K1)) ||
         (st = dalloc(&c->row_fwd, c->K0)) || (st = dalloc(&c->row_inv, c->K0)) || (st = dalloc(&c->col_fwd, c->K1)) ||
         (st = dalloc_bytes(&c->tw0, c->K0 * cb)) || (st = dalloc_bytes(&c->tw1, c->K1 * cb)) ||
+        (st = dalloc_bytes(&c->twst0, c->K0 * cb)) || (st = dalloc_bytes(&c->twst1, c->K1 * cb)) ||
         (st = dalloc_bytes(&c->deap0, c->L0 * rb)) ||
         (st = dalloc_bytes(&c->deap1, c->L1 * rb)) ||
         (st = dalloc_bytes(&c->kbpoly, (KB_DEG + 1) * KB_J * sizeof(float))) || (st = dalloc(&c->err, 1)) ||
@@ -791,7 +792,7 @@ void ppd_destroy(ppd_ctx *c) {
                     (void *)c->regrid_d, (void *)c->inner_state, (void *)c->inner_steps, (void *)c->stop_flag})
         dfree(p);
     for (void *p : {c->x, c->xt, c->g, c->ut, c->xtrue, c->u, c->wtmp, c->wtmp2, c->grid_a, c->grid_v, c->fft_tmp,
-                    c->tw0, c->tw1, c->deap0, c->deap1, c->kbpoly, (void *)c->prim_part, (void *)c->stat_out,
+                    c->tw0, c->tw1, c->twst0, c->twst1, c->deap0, c->deap1, c->kbpoly, (void *)c->prim_part, (void *)c->stat_out,
                     (void *)c->err})
         dfree(p);
     if (c->stream2) {
@@ -810,6 +811,11 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
     if (M < 1 || M >= (int64_t)1 << 31) return fail(PPD_ERR_INVALID_ARG, "ppd_set_visibilities: M out of range");
     for (int64_t i = 0; i < 2 * M; ++i)
         if (!std::isfinite(y[i])) return fail(PPD_ERR_INVALID_ARG, "ppd_set_visibilities: non-finite visibility");
+    for (int64_t i = 0; i < M; ++i)
+        if (!(uv[2 * i] >= -M_PI && uv[2 * i] <= M_PI && uv[2 * i + 1] >= -M_PI && uv[2 * i + 1] <= M_PI) ||
+            block_id[i] < 0 || block_id[i] >= c->d)
+            return fail(PPD_ERR_INVALID_ARG,
+                        "ppd_set_visibilities: omega outside [-pi, pi] or block id out of range");
     free_vis(c);
     drop_graph(c);
     c->M = M;
@@ -928,24 +934,35 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
             }
         }
     }
-    // block-major partial slots: block b owns slots bptr[b] .. bptr[b+1] - 1,
-    // chunk k writes slot bpos[k] (chunks of a block in processing order)
-    std::vector<int32_t> bptr(c->d + 1, 0), bpos(nch);
-    for (int64_t k = 0; k < nch; ++k) bptr[cbk[k] + 1]++;
+    // work units of the degridding and sub-iterations (runs of at most UNIT
+    // visibilities of one chunk) and their block-major partial slots: block
+    // b owns slots bptr[b] .. bptr[b+1] - 1, unit u writes slot upos[u]
+    std::vector<int32_t> us, un, uc;
+    for (int64_t k = 0; k < nch; ++k)
+        for (int32_t o = 0; o < cn[k]; o += UNIT) {
+            us.push_back(cs[k] + o);
+            un.push_back(std::min<int32_t>(UNIT, cn[k] - o));
+            uc.push_back((int32_t)k);
+        }
+    const int64_t nu = (int64_t)us.size();
+    std::vector<int32_t> bptr(c->d + 1, 0), upos(nu);
+    for (int64_t u = 0; u < nu; ++u) bptr[cbk[uc[u]] + 1]++;
     for (int j = 0; j < c->d; ++j) bptr[j + 1] += bptr[j];
     {
         std::vector<int32_t> fill(bptr.begin(), bptr.end() - 1);
-        for (int64_t k = 0; k < nch; ++k) bpos[k] = fill[cbk[k]]++;
+        for (int64_t u = 0; u < nu; ++u) upos[u] = fill[cbk[uc[u]]]++;
     }
     c->ch.n = nch;
+    c->ch.nu = nu;
     c->ch.n_active = (int64_t)active.size();
     const size_t cbsz = 2 * c->rsz;
     const int E = c->T + HALO;
     if ((st = dalloc(&c->ch.start, nch)) || (st = dalloc(&c->ch.count, nch)) || (st = dalloc(&c->ch.tile, nch)) ||
         (st = dalloc(&c->ch.block, nch)) || (st = dalloc(&c->ch.tile_first, ntiles)) ||
         (st = dalloc(&c->ch.tile_n, ntiles)) || (st = dalloc(&c->ch.blk_ptr, c->d + 1)) ||
-        (st = dalloc(&c->ch.blk_pos, nch)) || (st = dalloc(&c->ch.active, active.size())) ||
-        (st = dalloc(&c->partials, 2 * NPART * (size_t)nch)) ||
+        (st = dalloc(&c->ch.u_start, nu)) ||
+        (st = dalloc(&c->ch.u_count, nu)) || (st = dalloc(&c->ch.u_chunk, nu)) || (st = dalloc(&c->ch.u_pos, nu)) || (st = dalloc(&c->ch.active, active.size())) ||
+        (st = dalloc(&c->partials, 2 * NPART * (size_t)nu)) ||
         (st = dalloc(&c->scale, c->d)) || (st = dalloc(&c->resid2, c->d)) || (st = dalloc(&c->eps_d, c->d)) ||
         (st = dalloc(&c->mu_d, c->d)) || (st = dalloc_bytes(&c->gpart, (size_t)nch * E * E * cbsz)) ||
         (st = dalloc(&c->perm, M)) || (st = dalloc_bytes(&c->rec, M * (c->is_f32 ? 16 : 32))) ||
@@ -978,7 +995,10 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
         (e = cudaMemcpy(c->ch.tile_first, tfirst.data(), ntiles * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->ch.tile_n, tn.data(), ntiles * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->ch.blk_ptr, bptr.data(), (c->d + 1) * 4, cudaMemcpyHostToDevice)) ||
-        (e = cudaMemcpy(c->ch.blk_pos, bpos.data(), nch * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->ch.u_start, us.data(), nu * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->ch.u_count, un.data(), nu * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->ch.u_chunk, uc.data(), nu * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->ch.u_pos, upos.data(), nu * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->ch.active, active.data(), active.size() * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->perm, c->perm_h.data(), M * 8, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->y_raw, yraw_sorted.data(), 2 * M * 8, cudaMemcpyHostToDevice))) {

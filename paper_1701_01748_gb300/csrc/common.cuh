@@ -45,6 +45,7 @@ constexpr int MAX_TAPS = 16;     // db8
 // per-chunk norm partials: ||w-y||^2, ||Theta q - y||^2 and, for the
 // Algorithm 2 stopping test, ||zbar^t - zbar^(t-1)||^2, ||zbar^t||^2
 constexpr int NPART = 4;
+constexpr int UNIT = 256;        // visibilities per work unit of the degridding / sub-iterations
 constexpr double INV_TWO_PI = 0.15915494309189535;
 
 // device error word bits
@@ -116,7 +117,13 @@ struct Chunks {
     int64_t n = 0;
     int32_t *start = nullptr, *count = nullptr, *tile = nullptr, *block = nullptr;   // device
     int32_t *tile_first = nullptr, *tile_n = nullptr;                                // device, n_tiles
-    int32_t *blk_ptr = nullptr, *blk_pos = nullptr;   // device: block b's partial slots, slot of each chunk
+    // work units of the degridding and sub-iterations: runs of at most 256
+    // visibilities of one chunk (device arrays of nu entries); unit u writes
+    // its norm partials to slot u_pos[u], block b owns slots blk_ptr[b] ..
+    // blk_ptr[b+1] - 1
+    int64_t nu = 0;
+    int32_t *u_start = nullptr, *u_count = nullptr, *u_chunk = nullptr, *u_pos = nullptr;
+    int32_t *blk_ptr = nullptr;
     int32_t *active = nullptr;   // tiles the combine pass writes (device)
     int64_t n_active = 0;
 };
@@ -146,6 +153,7 @@ struct ppd_ctx {
     uint8_t *row_fwd = nullptr, *row_inv = nullptr, *col_fwd = nullptr;
     void *tw0 = nullptr, *tw1 = nullptr, *deap0 = nullptr, *deap1 = nullptr;   // twiddles of K0 / K1, Z's scalings
     ppd::FftPlan plan0, plan1;                                               // FFT plans of K0 (columns), K1 (rows)
+    void *twst0 = nullptr, *twst1 = nullptr;   // twiddles of the power-of-two core, stage by stage
     void *filt = nullptr;       // 8 x 16 reals (low-pass, zero padded)
     void *kbpoly = nullptr;     // (KB_DEG+1) x 8 floats
     double *prim_part = nullptr;

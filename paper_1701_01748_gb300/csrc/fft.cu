@@ -44,7 +44,9 @@ constexpr int NT = 256;
 // ------------------------------------------------------------ power-of-two core
 // In-place batched Stockham FFT (forward sign) of NSEQ sequences of length K
 // held in shared memory.  INTERLEAVED: element (s, i) at i*NSEQ + s;
-// otherwise at s*K + i.  tw[m] = exp(-2 pi i m / K).
+// otherwise at s*K + i.  tw: the twiddles stage by stage (upload_stage_twiddles):
+// for the radix-4 stage of span Ns, w^(q k K / (4 Ns)) at (q - 1) Ns + k, so
+// that the butterflies of a warp (consecutive k) read consecutive words.
 template <typename R, int K, int NSEQ, bool INTERLEAVED>
 __device__ void fft_smem(cplx_t<R> *buf, const cplx_t<R> *tw) {
     using C = cplx_t<R>;
@@ -79,9 +81,9 @@ __device__ void fft_smem(cplx_t<R> *buf, const cplx_t<R> *tw) {
     }
     constexpr int NB = NSEQ * K / 4 / NT;
     static_assert(NB >= 1 && NSEQ * K / 4 % NT == 0, "radix-4 work split");
+    const C *tws = tw;   // this stage's table (stages with Ns = 1 have none)
     for (; Ns < K; Ns *= 4) {
         C v[NB][4];
-        const int twstep = K / (Ns * 4);
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             int bf = tid + b * NT;
@@ -93,9 +95,9 @@ __device__ void fft_smem(cplx_t<R> *buf, const cplx_t<R> *tw) {
             C a2 = buf[idx(s, j + K / 2)];
             C a3 = buf[idx(s, j + 3 * K / 4)];
             if (Ns > 1) {
-                a1 = cmul(a1, tw[(1 * k * twstep) & (K - 1)]);
-                a2 = cmul(a2, tw[(2 * k * twstep) & (K - 1)]);
-                a3 = cmul(a3, tw[(3 * k * twstep) & (K - 1)]);
+                a1 = cmul(a1, tws[k]);
+                a2 = cmul(a2, tws[Ns + k]);
+                a3 = cmul(a3, tws[2 * Ns + k]);
             }
             C t0 = cadd(a0, a2), t1 = csub(a0, a2);
             C t2 = cadd(a1, a3), t3 = csub(a1, a3);
@@ -119,6 +121,7 @@ __device__ void fft_smem(cplx_t<R> *buf, const cplx_t<R> *tw) {
             buf[idx(s, d + 3 * Ns)] = v[b][3];
         }
         __syncthreads();
+        if (Ns > 1) tws += 3 * Ns;
     }
 }
 
@@ -536,7 +539,9 @@ template <typename R, int KT> struct RowPass {
     }
     static PassArgs args(const ppd_ctx *c) { return PassArgs{c->plan1, nseq(c)}; }
     static unsigned blocks(const ppd_ctx *c) { return (unsigned)((c->L0 + nseq(c) - 1) / nseq(c)); }
-    static const cplx_t<R> *tw(const ppd_ctx *c) { return static_cast<const cplx_t<R> *>(c->tw1); }
+    static const cplx_t<R> *tw(const ppd_ctx *c) {
+        return static_cast<const cplx_t<R> *>(KT ? c->twst1 : c->tw1);
+    }
     static int fwd(ppd_ctx *c, const R *x, cudaStream_t s) {
         const int sh = (int)smem(c);
         PPD_CHECK(smem_attr((const void *)k_rows_fwd<R, KT>, sh));
@@ -580,7 +585,9 @@ template <typename R, int KT> struct ColPass {
         return KT ? pass_smem<R>(WT, KT) : (size_t)2 * nseq(c) * c->K0 * 2 * sizeof(R);
     }
     static PassArgs args(const ppd_ctx *c) { return PassArgs{c->plan0, nseq(c)}; }
-    static const cplx_t<R> *tw(const ppd_ctx *c) { return static_cast<const cplx_t<R> *>(c->tw0); }
+    static const cplx_t<R> *tw(const ppd_ctx *c) {
+        return static_cast<const cplx_t<R> *>(KT ? c->twst0 : c->tw0);
+    }
     static int fwd(ppd_ctx *c, cplx_t<R> *grid, cudaStream_t s) {
         if (c->n_fwd_strips == 0) return PPD_OK;
         const int sh = (int)smem(c);
@@ -773,11 +780,37 @@ static int upload_twiddles(ppd_ctx *c, int K, void *dst) {
     return PPD_OK;
 }
 
+// Twiddles of the power-of-two core stage by stage (K entries, zero padded):
+// the radix-4 stages of span Ns = 2 or 4, then x4 up to K/4, each with
+// w^(q k K / (4 Ns)) at (q - 1) Ns + k, q = 1..3, k < Ns.
+static int upload_stage_twiddles(ppd_ctx *c, int K, void *dst) {
+    std::vector<double> t(2 * (size_t)K, 0.0);
+    if ((K & (K - 1)) == 0) {
+        size_t off = 0;
+        for (int Ns = (ilog2_(K) & 1) ? 2 : 4; Ns < K; Ns *= 4)
+            for (int q = 1; q <= 3; ++q)
+                for (int k = 0; k < Ns; ++k, ++off) {
+                    const double a = -2.0 * M_PI * (double)q * k / (4.0 * Ns);
+                    t[2 * off] = std::cos(a);
+                    t[2 * off + 1] = std::sin(a);
+                }
+    }
+    if (c->is_f32) {
+        std::vector<float> f(t.begin(), t.end());
+        PPD_CUDA(cudaMemcpy(dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+    } else {
+        PPD_CUDA(cudaMemcpy(dst, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    return PPD_OK;
+}
+
 int make_twiddles(ppd_ctx *c) {
     c->plan0 = make_fft_plan(c->K0);
     c->plan1 = make_fft_plan(c->K1);
     PPD_CHECK(upload_twiddles(c, c->K0, c->tw0));
-    return upload_twiddles(c, c->K1, c->tw1);
+    PPD_CHECK(upload_twiddles(c, c->K1, c->tw1));
+    PPD_CHECK(upload_stage_twiddles(c, c->K0, c->twst0));
+    return upload_stage_twiddles(c, c->K1, c->twst1);
 }
 
 // Z's scaling s(n) = 1 / psi_hat((n - L/2)/K), psi_hat(f) = (J / I0(beta)) sinh(q)/q,

@@ -41,6 +41,9 @@ __global__ void k_bin(const double *__restrict__ uv, const int32_t *__restrict__
         if (!(om0 >= -M_PI && om0 <= M_PI && om1 >= -M_PI && om1 <= M_PI) || b < 0 || b >= d) {
             atomicOr(bad, 1);
             key[i] = 0;
+            base[2 * i] = base[2 * i + 1] = 0;
+            frac[2 * i] = frac[2 * i + 1] = 0.0;
+            cell[i] = 0;   // a valid cell for k_cell_count; the call fails on `bad`
             continue;
         }
         const double k0 = __dmul_rn(__dmul_rn(om0, (double)K0), INV_TWO_PI);
@@ -109,6 +112,9 @@ template <typename R> struct VisArgs {
     const R *theta_v;
     R theta_s;
     const int32_t *ch_start, *ch_count, *ch_tile, *ch_block;
+    // work units of the degridding and sub-iteration kernels: runs of at
+    // most DG_NT visibilities of one chunk, each with its partial slot
+    const int32_t *u_start, *u_count, *u_chunk;
     int K0, K1, ntile1;
     const float *kbpoly;
     double beta, inv_i0b;
@@ -117,9 +123,9 @@ template <typename R> struct VisArgs {
     const double *mu, *scale;
     double *partials;            // this launch's chunk partials
     const double *part_in;       // previous step's chunk partials (P_B scale)
-    // chunk partials live in block-major slots: chunk ch writes slot
-    // blk_pos[ch]; block b's slots are blk_ptr[b] .. blk_ptr[b+1] - 1
-    const int32_t *blk_ptr, *blk_pos;
+    // partials live in block-major slots: work unit u writes slot
+    // u_pos[u]; block b's slots are blk_ptr[b] .. blk_ptr[b+1] - 1
+    const int32_t *blk_ptr, *u_pos;
     const double *eps;
     int *err;
     // randomised active sets (null: every block active): the current
@@ -246,14 +252,16 @@ template <typename R> __device__ int inner_stopped(const VisArgs<R> &A, int blk)
 // mode DG_OP:    op_out[perm[i]] = Theta G a
 // mode DG_DUAL:  z = v/U + Theta G a;  w = p - mu U (p - z)
 // mode DG_FIRST: z = v/U + Theta G a;  w = z   (Algorithm 2 then starts from P_B(z))
-// partials[chunk] = (||w - y||^2, ||Theta G a - y||^2)
+// partial slot of the unit = (||w - y||^2, ||Theta G a - y||^2)
 //
-// Persistent CTAs walk the chunks with a fixed stride.  The (T+8)^2 grid tile
-// of the next chunk is fetched by TMA into the other of two shared buffers
-// while the current chunk is computed (interior tiles; tiles that wrap
-// around the grid edge are loaded with plain loads when they are used).
-// Each thread loads its visibility data before waiting for the tile and one
-// visibility ahead inside the loop.
+// Persistent CTAs walk the work units (at most DG_NT visibilities of one
+// chunk, one per thread) with a fixed stride, so that the dense centre of the
+// coverage, split into many full units, spreads evenly over the GPU.  The
+// (T+8)^2 grid tile of the next unit is fetched by TMA into the other of two
+// shared buffers while the current unit is computed (interior tiles; tiles
+// that wrap around the grid edge are loaded with plain loads when they are
+// used), and each thread loads its visibility of the next unit before the
+// current one is computed.
 template <typename R> struct VisIn {
     VisRec<R> rc;
     cplx_t<R> v, y, p;
@@ -274,7 +282,7 @@ __device__ __forceinline__ void load_vis(const VisArgs<R> &A, int gi, VisIn<R> &
 template <typename R, int T, int MODE>
 __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
     k_degrid(const __grid_constant__ CUtensorMap tmap, int use_tma, const cplx_t<R> *__restrict__ grid, VisArgs<R> A,
-             int n_chunks, long long spin_first) {
+             int n_units, long long spin_first) {
     using C = cplx_t<R>;
     constexpr int E = T + HALO;
     constexpr int TILE_BYTES = E * E * (int)sizeof(C);
@@ -291,33 +299,36 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
         mbar_init(&bar[1], 1);
     }
     __syncthreads();
-    auto origin = [&](int ch, int &row0, int &col0) {
-        const int tl = A.ch_tile[ch];
+    auto origin = [&](int u, int &row0, int &col0) {
+        const int tl = A.ch_tile[A.u_chunk[u]];
         row0 = (tl / A.ntile1) * T;
         col0 = (tl % A.ntile1) * T;
     };
     auto interior = [&](int row0, int col0) { return use_tma && row0 + E <= A.K0 && col0 + E <= A.K1; };
-    auto issue = [&](int ch, int buf) {   // thread 0 only
+    auto issue = [&](int u, int buf) {   // thread 0 only
         int r0, c0;
-        origin(ch, r0, c0);
+        origin(u, r0, c0);
         if (interior(r0, c0)) {
             mbar_expect_tx(&bar[buf], (uint32_t)TILE_BYTES);
             tma_load_2d(smem_raw + buf * TILE_STRIDE, &tmap, 2 * c0, r0, &bar[buf]);
         }
     };
     uint32_t ph = 0u;   // bit b: parity of the next completion of bar[b]
-    if (threadIdx.x == 0 && (int)blockIdx.x < n_chunks) issue(blockIdx.x, 0);
+    if (threadIdx.x == 0 && (int)blockIdx.x < n_units) issue(blockIdx.x, 0);
+    VisIn<R> cur;
+    if ((int)blockIdx.x < n_units && (int)threadIdx.x < A.u_count[blockIdx.x])
+        load_vis<R, MODE>(A, A.u_start[blockIdx.x] + threadIdx.x, cur);
     int it = 0;
-    for (int ch = blockIdx.x; ch < n_chunks; ch += gridDim.x, ++it) {
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++it) {
         const int buf = it & 1;
         C *tile = reinterpret_cast<C *>(smem_raw + buf * TILE_STRIDE);
-        const int nxt = ch + gridDim.x;
-        if (threadIdx.x == 0 && nxt < n_chunks) issue(nxt, buf ^ 1);
-        const int start = A.ch_start[ch], count = A.ch_count[ch];
+        const int nxt = u + gridDim.x;
+        if (threadIdx.x == 0 && nxt < n_units) issue(nxt, buf ^ 1);
+        const int start = A.u_start[u], count = A.u_count[u], ch = A.u_chunk[u];
+        VisIn<R> nx;
+        if (nxt < n_units && (int)threadIdx.x < A.u_count[nxt]) load_vis<R, MODE>(A, A.u_start[nxt] + threadIdx.x, nx);
         int row0, col0;
-        origin(ch, row0, col0);
-        VisIn<R> cur;
-        if ((int)threadIdx.x < count) load_vis<R, MODE>(A, start + threadIdx.x, cur);
+        origin(u, row0, col0);
         if (interior(row0, col0)) {
             // spin_first bounds the first wait (SPIN_LIMIT unless a test shortens
             // it); the waits for copies in flight before leaving keep SPIN_LIMIT
@@ -329,8 +340,8 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
             ph ^= 1u << buf;
             __syncthreads();
             if (!ok_s) {
-                // the next chunk's copy may be in flight: wait for it (bounded) before leaving
-                if (nxt < n_chunks) {
+                // the next unit's copy may be in flight: wait for it (bounded) before leaving
+                if (nxt < n_units) {
                     int r1, c1;
                     origin(nxt, r1, c1);
                     if (interior(r1, c1)) mbar_wait(&bar[buf ^ 1], (ph >> (buf ^ 1)) & 1u, SPIN_LIMIT);
@@ -359,10 +370,8 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
         // prox output is kept in p, the previous point of the first test
         const bool keep_start = first_blk && A.inner_tol > 0;
         Acc<R> s_w, s_r;
-        for (int i = threadIdx.x; i < count; i += DG_NT) {
-            const int gi = start + i;
-            VisIn<R> nx;
-            if (i + DG_NT < count) load_vis<R, MODE>(A, gi + DG_NT, nx);
+        if ((int)threadIdx.x < count) {
+            const int gi = start + threadIdx.x;
             const int lb0 = (cur.rc.packed & 0xffff) - row0, lb1 = ((cur.rc.packed >> 16) & 0xffff) - col0;
             R w0[KB_J], w1[KB_J];
             kb_weights(cur.rc.f0, w0, poly, A.beta, A.inv_i0b);
@@ -404,10 +413,10 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
                 const R ex = phix.x - cur.y.x, ey = phix.y - cur.y.y;
                 s_r.add(ex * ex + ey * ey);
             }
-            cur = nx;
         }
-        if (MODE != DG_OP) cta_sum2<DG_NT>(s_w.get(), s_r.get(), A.partials + NPART * (int64_t)A.blk_pos[ch]);
-        __syncthreads();   // the tile buffer is refilled two chunks later
+        if (MODE != DG_OP) cta_sum2<DG_NT>(s_w.get(), s_r.get(), A.partials + NPART * (int64_t)A.u_pos[u]);
+        __syncthreads();   // the tile buffer is refilled two units later
+        cur = nx;
     }
 }
 
@@ -426,13 +435,13 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
 template <typename R>
 __global__ void __launch_bounds__(DG_NT) k_subiter(VisArgs<R> A, int only_first, R beta, int write_p) {
     using C = cplx_t<R>;
-    const int ch = blockIdx.x;
-    const int start = A.ch_start[ch], count = A.ch_count[ch], blk = A.ch_block[ch];
+    const int u = blockIdx.x;   // one work unit (at most DG_NT visibilities)
+    const int start = A.u_start[u], count = A.u_count[u], blk = A.ch_block[A.u_chunk[u]];
     const bool act = !A.bmask || A.bmask[blk];
     const bool first_blk = A.seen && !A.seen[blk];
     if (!act || (only_first && !first_blk)) {
         if (threadIdx.x == 0) {
-            const int64_t slot = NPART * (int64_t)A.blk_pos[ch];
+            const int64_t slot = NPART * (int64_t)A.u_pos[u];
             A.partials[slot] = A.part_in[slot];
         }
         return;
@@ -474,7 +483,7 @@ __global__ void __launch_bounds__(DG_NT) k_subiter(VisArgs<R> A, int only_first,
     __shared__ double o3[3];
     cta_sum3<DG_NT>(s_w.get(), s_d.get(), s_n.get(), o3);
     if (threadIdx.x == 0) {
-        double *out = A.partials + NPART * (int64_t)A.blk_pos[ch];
+        double *out = A.partials + NPART * (int64_t)A.u_pos[u];
         out[0] = o3[0];
         out[2] = o3[1];
         out[3] = o3[2];
@@ -533,10 +542,14 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
     constexpr int E = T + HALO, P = E;   // P: pitch of the private tiles (8 mod 16 words)
     static_assert(P % 16 == 8, "private-tile pitch");
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    // staging, component-major with a pitch of NT + 1 so that the stores of
+    // consecutive threads and the reads of one visibility by a warp's lanes
+    // both hit distinct banks
+    constexpr int SP = NT + 1;
     C *priv = reinterpret_cast<C *>(smem_raw);                          // NW * E * P
-    C *sa = priv + NW * E * P;                                          // NT * 8: w0[a] Theta v, pairs (a, a+4)
-    R *sb = reinterpret_cast<R *>(sa + NT * KB_J);                      // NT * 8: w1[b]
-    int *slb = reinterpret_cast<int *>(sb + NT * KB_J);                 // NT
+    C *sa = priv + NW * E * P;                                          // 4 x SP pairs (w0[a] Theta v, w0[a+4] Theta v)
+    R *sb = reinterpret_cast<R *>(sa + 2 * 4 * SP);                     // 8 x SP: w1[b]
+    int *slb = reinterpret_cast<int *>(sb + KB_J * SP);                 // NT
     float *poly = reinterpret_cast<float *>(slb + NT);                  // 64
 
     const int ch = blockIdx.x;
@@ -634,20 +647,19 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
             R w0[KB_J], w1[KB_J];
             kb_weights(rc.f0, w0, poly, A.beta, A.inv_i0b);
             kb_weights(rc.f1, w1, poly, A.beta, A.inv_i0b);
-            C *da = sa + threadIdx.x * KB_J;
 #pragma unroll
-            for (int a = 0; a < KB_J / 2; ++a) {   // lane pair (a, a+4) reads one 2-complex word
-                da[2 * a] = C{w0[a] * tv.x, w0[a] * tv.y};
-                da[2 * a + 1] = C{w0[a + 4] * tv.x, w0[a + 4] * tv.y};
+            for (int a = 0; a < KB_J / 2; ++a) {   // lane rows (a, a+4) read one pair
+                C *da = sa + 2 * (a * SP + threadIdx.x);
+                if constexpr (sizeof(R) == 4) {
+                    *reinterpret_cast<float4 *>(da) =
+                        make_float4(w0[a] * tv.x, w0[a] * tv.y, w0[a + 4] * tv.x, w0[a + 4] * tv.y);
+                } else {
+                    da[0] = C{w0[a] * tv.x, w0[a] * tv.y};
+                    da[1] = C{w0[a + 4] * tv.x, w0[a + 4] * tv.y};
+                }
             }
-            if constexpr (sizeof(R) == 4) {
-                float4 *db = reinterpret_cast<float4 *>(sb + threadIdx.x * KB_J);
-                db[0] = make_float4(w1[0], w1[1], w1[2], w1[3]);
-                db[1] = make_float4(w1[4], w1[5], w1[6], w1[7]);
-            } else {
 #pragma unroll
-                for (int j = 0; j < KB_J; ++j) sb[threadIdx.x * KB_J + j] = w1[j];
-            }
+            for (int j = 0; j < KB_J; ++j) sb[j * SP + threadIdx.x] = w1[j];
             const int lb0 = (rc.packed & 0xffff) - row0, lb1 = ((rc.packed >> 16) & 0xffff) - col0;
             slb[threadIdx.x] = lb0 | (lb1 << 16);
         }
@@ -675,8 +687,16 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
                 acc0 = C{0, 0};
                 acc1 = C{0, 0};
             }
-            const C pa = sa[i * KB_J + 2 * a0], pb = sa[i * KB_J + 2 * a0 + 1];   // w0[a0] Theta v, w0[a1] Theta v
-            const R wb = sb[i * KB_J + bcol];
+            C pa, pb;   // w0[a0] Theta v, w0[a0+4] Theta v
+            if constexpr (sizeof(R) == 4) {
+                const float4 q = *reinterpret_cast<const float4 *>(sa + 2 * (a0 * SP + i));
+                pa = C{q.x, q.y};
+                pb = C{q.z, q.w};
+            } else {
+                pa = sa[2 * (a0 * SP + i)];
+                pb = sa[2 * (a0 * SP + i) + 1];
+            }
+            const R wb = sb[bcol * SP + i];
             acc0.x += wb * pa.x;
             acc0.y += wb * pa.y;
             acc1.x += wb * pb.x;
@@ -770,7 +790,10 @@ template <typename R> VisArgs<R> make_args(ppd_ctx *c) {
     A.partials = c->part_out;
     A.part_in = c->part_in;
     A.blk_ptr = c->ch.blk_ptr;
-    A.blk_pos = c->ch.blk_pos;
+    A.u_pos = c->ch.u_pos;
+    A.u_start = c->ch.u_start;
+    A.u_count = c->ch.u_count;
+    A.u_chunk = c->ch.u_chunk;
     A.eps = c->eps_d;
     A.err = c->err;
     A.bmask = c->rand_on ? c->mask_cur : nullptr;
@@ -786,8 +809,8 @@ template <typename R> VisArgs<R> make_args(ppd_ctx *c) {
 }
 
 template <typename R, int T> size_t grid_smem() {
-    constexpr int NW = GridCfg<R>::NWARP, NT = NW * 32, E = T + HALO, P = E;
-    return (size_t)NW * E * P * sizeof(cplx_t<R>) + NT * KB_J * sizeof(cplx_t<R>) + NT * KB_J * sizeof(R) +
+    constexpr int NW = GridCfg<R>::NWARP, NT = NW * 32, E = T + HALO, P = E, SP = NT + 1;
+    return (size_t)NW * E * P * sizeof(cplx_t<R>) + 8 * SP * sizeof(cplx_t<R>) + KB_J * SP * sizeof(R) +
            NT * sizeof(int) + (KB_DEG + 1) * KB_J * sizeof(float);
 }
 
@@ -803,13 +826,13 @@ int degrid_t(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const 
     PPD_CHECK(smem_attr((const void *)k_degrid<R, T, DG_DUAL>, (int)sh));
     PPD_CHECK(smem_attr((const void *)k_degrid<R, T, DG_FIRST>, (int)sh));
     const int use_tma = (c->tma_ok && grid == c->grid_a) ? 1 : 0;
-    if (c->ch.n == 0) return PPD_OK;
+    if (c->ch.nu == 0) return PPD_OK;
     int per_sm = 0;
     PPD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_degrid<R, T, DG_DUAL>, DG_NT, sh));
     if (per_sm < 1) per_sm = 1;
     int sms = 0;
     PPD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    const int nch = (int)c->ch.n;
+    const int nch = (int)c->ch.nu;   // work units
     const unsigned nb = (unsigned)std::min<int64_t>(nch, (int64_t)sms * per_sm);
     int site;
     PPD_CHECK(launch_begin(c, mode == DG_OP ? "degrid_op" : "degrid_dual", s, &site));
@@ -921,10 +944,10 @@ int grid_vis(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cpl
 }
 
 template <typename R> int subiter(ppd_ctx *c, cudaStream_t s, int only_first, double beta, int write_p) {
-    if (c->ch.n == 0) return PPD_OK;
+    if (c->ch.nu == 0) return PPD_OK;
     int site;
     PPD_CHECK(launch_begin(c, "subiter", s, &site));
-    k_subiter<R><<<(unsigned)c->ch.n, DG_NT, 0, s>>>(make_args<R>(c), only_first, (R)beta, write_p);
+    k_subiter<R><<<(unsigned)c->ch.nu, DG_NT, 0, s>>>(make_args<R>(c), only_first, (R)beta, write_p);
     return launch_end(c, site, s);
 }
 
