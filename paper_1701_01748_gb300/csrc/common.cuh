@@ -45,7 +45,7 @@ constexpr int MAX_TAPS = 16;     // db8
 // per-chunk norm partials: ||w-y||^2, ||Theta q - y||^2 and, for the
 // Algorithm 2 stopping test, ||zbar^t - zbar^(t-1)||^2, ||zbar^t||^2
 constexpr int NPART = 4;
-constexpr int UNIT = 256;        // visibilities per work unit of the degridding / sub-iterations
+constexpr int UNIT = 1 << 30;    // visibilities per work unit of the degridding / sub-iterations (no split: a unit is a chunk)
 constexpr double INV_TWO_PI = 0.15915494309189535;
 
 // device error word bits
@@ -117,12 +117,13 @@ struct Chunks {
     int64_t n = 0;
     int32_t *start = nullptr, *count = nullptr, *tile = nullptr, *block = nullptr;   // device
     int32_t *tile_first = nullptr, *tile_n = nullptr;                                // device, n_tiles
-    // work units of the degridding and sub-iterations: runs of at most 256
+    // work units of the degridding and sub-iterations: runs of at most UNIT
     // visibilities of one chunk (device arrays of nu entries); unit u writes
     // its norm partials to slot u_pos[u], block b owns slots blk_ptr[b] ..
-    // blk_ptr[b+1] - 1
+    // blk_ptr[b+1] - 1; u_order lists the units by decreasing size (the
+    // degridding's visiting order)
     int64_t nu = 0;
-    int32_t *u_start = nullptr, *u_count = nullptr, *u_chunk = nullptr, *u_pos = nullptr;
+    int32_t *u_start = nullptr, *u_count = nullptr, *u_chunk = nullptr, *u_pos = nullptr, *u_order = nullptr;
     int32_t *blk_ptr = nullptr;
     int32_t *active = nullptr;   // tiles the combine pass writes (device)
     int64_t n_active = 0;

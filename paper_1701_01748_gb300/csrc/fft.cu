@@ -295,11 +295,12 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(const R *__restrict__ x, cplx_t
     C *buf2 = buf + B * K;
     const C *tws = KT ? stage_twiddles<R, BT, KT ? KT : 1>(buf, tw) : tw;
     const int row0 = blockIdx.x * B;
-    for (int e = threadIdx.x; e < B * K; e += NT) buf[e] = C{0, 0};
-    __syncthreads();
-    for (int e = threadIdx.x; e < B * L1; e += NT) {
-        const int s = e / L1, n1 = e - s * L1, n0 = row0 + s;
-        if (n0 < L0) buf[s * K + wrapK(n1 - L1 / 2 + K, K)] = C{s0[n0] * s1[n1] * x[(int64_t)n0 * L1 + n1], R(0)};
+    // one pass over the padded rows: position p holds pixel p + L1/2 (p <
+    // L1/2) or p - K + L1/2 (p >= K - L1/2), zero in between
+    for (int e = threadIdx.x; e < B * K; e += NT) {
+        const int s = e / K, p = e - s * K, n0 = row0 + s;
+        const int n1 = p < L1 / 2 ? p + L1 / 2 : (p >= K - L1 / 2 ? p - K + L1 / 2 : -1);
+        buf[e] = (n1 >= 0 && n0 < L0) ? C{s0[n0] * s1[n1] * x[(int64_t)n0 * L1 + n1], R(0)} : C{0, 0};
     }
     __syncthreads();
     const C *out = run_fft<R, KT, BT, false>(buf, buf2, tws, B, pa.pl, tw);
@@ -323,11 +324,12 @@ __global__ void __launch_bounds__(NT) k_cols_fwd(const cplx_t<R> *__restrict__ t
     C *buf2 = buf + W * K;
     const C *tws = KT ? stage_twiddles<R, WT, KT ? KT : 1>(buf, tw) : tw;
     const int c0 = strips[blockIdx.x];
-    for (int e = threadIdx.x; e < W * K; e += NT) buf[e] = C{0, 0};
-    __syncthreads();
-    for (int e = threadIdx.x; e < W * L0; e += NT) {
-        const int n0 = e / W, s = e - n0 * W;
-        buf[wrapK(n0 - L0 / 2 + K, K) * W + s] = tmp[(int64_t)n0 * K1 + c0 + s];
+    // one pass over the padded strip: position p holds image row p + L0/2
+    // (p < L0/2) or p - K + L0/2 (p >= K - L0/2), zero in between
+    for (int e = threadIdx.x; e < W * K; e += NT) {
+        const int p = e / W, s = e - p * W;
+        const int n0 = p < L0 / 2 ? p + L0 / 2 : (p >= K - L0 / 2 ? p - K + L0 / 2 : -1);
+        buf[e] = n0 >= 0 ? tmp[(int64_t)n0 * K1 + c0 + s] : C{0, 0};
     }
     __syncthreads();
     const C *out = run_fft<R, KT, WT, true>(buf, buf2, tws, W, pa.pl, tw);
@@ -483,12 +485,14 @@ __global__ void __launch_bounds__(NT) k_rows_primal(const cplx_t<R> *__restrict_
             }
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < B * K; e += NT) buf[e] = C{0, 0};
-        __syncthreads();
+        // the new row in place, each thread also clearing the padding
+        // position K/2 away from its pixel's (the padding is [LT/2, K - LT/2))
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
             const int e = threadIdx.x + k * NT, s = e / LT, n1 = e % LT, n0 = row0 + s;
-            if (n0 < L0) buf[s * K + ((n1 - LT / 2 + K) & (K - 1))] = C{s0[n0] * s1[n1] * xtn[k], R(0)};
+            const int pos = (n1 - LT / 2 + K) & (K - 1);
+            buf[s * K + pos] = C{n0 < L0 ? s0[n0] * s1[n1] * xtn[k] : R(0), R(0)};
+            buf[s * K + ((pos + LT) & (K - 1))] = C{0, 0};
         }
         __syncthreads();
     } else {

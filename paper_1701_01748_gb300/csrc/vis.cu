@@ -114,7 +114,7 @@ template <typename R> struct VisArgs {
     const int32_t *ch_start, *ch_count, *ch_tile, *ch_block;
     // work units of the degridding and sub-iteration kernels: runs of at
     // most DG_NT visibilities of one chunk, each with its partial slot
-    const int32_t *u_start, *u_count, *u_chunk;
+    const int32_t *u_start, *u_count, *u_chunk, *u_order;
     int K0, K1, ntile1;
     const float *kbpoly;
     double beta, inv_i0b;
@@ -254,14 +254,14 @@ template <typename R> __device__ int inner_stopped(const VisArgs<R> &A, int blk)
 // mode DG_FIRST: z = v/U + Theta G a;  w = z   (Algorithm 2 then starts from P_B(z))
 // partial slot of the unit = (||w - y||^2, ||Theta G a - y||^2)
 //
-// Persistent CTAs walk the work units (at most DG_NT visibilities of one
-// chunk, one per thread) with a fixed stride, so that the dense centre of the
-// coverage, split into many full units, spreads evenly over the GPU.  The
-// (T+8)^2 grid tile of the next unit is fetched by TMA into the other of two
-// shared buffers while the current unit is computed (interior tiles; tiles
-// that wrap around the grid edge are loaded with plain loads when they are
-// used), and each thread loads its visibility of the next unit before the
-// current one is computed.
+// Persistent CTAs walk the work units (the chunks) in the order u_order
+// (largest first) with a fixed stride, so that every CTA gets one of the
+// heavy units of the dense centre of the coverage before the light ones.
+// The (T+8)^2 grid tile of the next unit is fetched by TMA into the other of
+// two shared buffers while the current unit is computed (interior tiles;
+// tiles that wrap around the grid edge are loaded with plain loads when they
+// are used); each thread loads its first visibility of the next unit before
+// the current one is computed, and one visibility ahead inside a unit.
 template <typename R> struct VisIn {
     VisRec<R> rc;
     cplx_t<R> v, y, p;
@@ -314,19 +314,19 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
         }
     };
     uint32_t ph = 0u;   // bit b: parity of the next completion of bar[b]
-    if (threadIdx.x == 0 && (int)blockIdx.x < n_units) issue(blockIdx.x, 0);
+    const int32_t *ord = A.u_order;
+    if (threadIdx.x == 0 && (int)blockIdx.x < n_units) issue(ord[blockIdx.x], 0);
     VisIn<R> cur;
-    if ((int)blockIdx.x < n_units && (int)threadIdx.x < A.u_count[blockIdx.x])
-        load_vis<R, MODE>(A, A.u_start[blockIdx.x] + threadIdx.x, cur);
+    if ((int)blockIdx.x < n_units && (int)threadIdx.x < A.u_count[ord[blockIdx.x]])
+        load_vis<R, MODE>(A, A.u_start[ord[blockIdx.x]] + threadIdx.x, cur);
     int it = 0;
-    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++it) {
+    for (int iu = blockIdx.x; iu < n_units; iu += gridDim.x, ++it) {
         const int buf = it & 1;
         C *tile = reinterpret_cast<C *>(smem_raw + buf * TILE_STRIDE);
-        const int nxt = u + gridDim.x;
+        const int u = ord[iu];
+        const int nxt = iu + gridDim.x < n_units ? ord[iu + gridDim.x] : n_units;
         if (threadIdx.x == 0 && nxt < n_units) issue(nxt, buf ^ 1);
         const int start = A.u_start[u], count = A.u_count[u], ch = A.u_chunk[u];
-        VisIn<R> nx;
-        if (nxt < n_units && (int)threadIdx.x < A.u_count[nxt]) load_vis<R, MODE>(A, A.u_start[nxt] + threadIdx.x, nx);
         int row0, col0;
         origin(u, row0, col0);
         if (interior(row0, col0)) {
@@ -370,8 +370,10 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
         // prox output is kept in p, the previous point of the first test
         const bool keep_start = first_blk && A.inner_tol > 0;
         Acc<R> s_w, s_r;
-        if ((int)threadIdx.x < count) {
-            const int gi = start + threadIdx.x;
+        for (int i = threadIdx.x; i < count; i += DG_NT) {
+            const int gi = start + i;
+            VisIn<R> nx;   // the next visibility: of this unit, else the next unit's first
+            if (i + DG_NT < count) load_vis<R, MODE>(A, gi + DG_NT, nx);
             const int lb0 = (cur.rc.packed & 0xffff) - row0, lb1 = ((cur.rc.packed >> 16) & 0xffff) - col0;
             R w0[KB_J], w1[KB_J];
             kb_weights(cur.rc.f0, w0, poly, A.beta, A.inv_i0b);
@@ -413,10 +415,13 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
                 const R ex = phix.x - cur.y.x, ey = phix.y - cur.y.y;
                 s_r.add(ex * ex + ey * ey);
             }
+            if (i + DG_NT < count) cur = nx;
         }
+        // this thread's first visibility of the next unit (loaded during the
+        // unit's reduction and barrier below)
+        if (nxt < n_units && (int)threadIdx.x < A.u_count[nxt]) load_vis<R, MODE>(A, A.u_start[nxt] + threadIdx.x, cur);
         if (MODE != DG_OP) cta_sum2<DG_NT>(s_w.get(), s_r.get(), A.partials + NPART * (int64_t)A.u_pos[u]);
         __syncthreads();   // the tile buffer is refilled two units later
-        cur = nx;
     }
 }
 
@@ -674,8 +679,29 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
         const int i0 = warp < nwu ? warp * seg : n, i1 = min(n, i0 + seg);
         int run = -1;
         C acc0{0, 0}, acc1{0, 0};
+        // the staged operands of visibility i + 1 are read while visibility i
+        // is accumulated (the staging is not written during the scatter)
+        auto fetch = [&](int i, int &lb, C &pa, C &pb, R &wb) {
+            lb = slb[i];
+            if constexpr (sizeof(R) == 4) {
+                const float4 q = *reinterpret_cast<const float4 *>(sa + 2 * (a0 * SP + i));
+                pa = C{q.x, q.y};
+                pb = C{q.z, q.w};
+            } else {
+                pa = sa[2 * (a0 * SP + i)];
+                pb = sa[2 * (a0 * SP + i) + 1];
+            }
+            wb = sb[bcol * SP + i];
+        };
+        int lbn = 0;
+        C pan{0, 0}, pbn{0, 0};   // w0[a0] Theta v, w0[a0+4] Theta v
+        R wbn = 0;
+        if (i0 < i1) fetch(i0, lbn, pan, pbn, wbn);
         for (int i = i0; i < i1; ++i) {
-            const int lb = slb[i];
+            const int lb = lbn;
+            const C pa = pan, pb = pbn;
+            const R wb = wbn;
+            if (i + 1 < i1) fetch(i + 1, lbn, pan, pbn, wbn);
             if (lb != run) {
                 if (run >= 0) {
                     C *cell = mine + ((run & 0xffff) + a0) * P + (run >> 16) + bcol;
@@ -687,16 +713,6 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
                 acc0 = C{0, 0};
                 acc1 = C{0, 0};
             }
-            C pa, pb;   // w0[a0] Theta v, w0[a0+4] Theta v
-            if constexpr (sizeof(R) == 4) {
-                const float4 q = *reinterpret_cast<const float4 *>(sa + 2 * (a0 * SP + i));
-                pa = C{q.x, q.y};
-                pb = C{q.z, q.w};
-            } else {
-                pa = sa[2 * (a0 * SP + i)];
-                pb = sa[2 * (a0 * SP + i) + 1];
-            }
-            const R wb = sb[bcol * SP + i];
             acc0.x += wb * pa.x;
             acc0.y += wb * pa.y;
             acc1.x += wb * pb.x;
@@ -794,6 +810,7 @@ template <typename R> VisArgs<R> make_args(ppd_ctx *c) {
     A.u_start = c->ch.u_start;
     A.u_count = c->ch.u_count;
     A.u_chunk = c->ch.u_chunk;
+    A.u_order = c->ch.u_order;
     A.eps = c->eps_d;
     A.err = c->err;
     A.bmask = c->rand_on ? c->mask_cur : nullptr;

@@ -68,6 +68,9 @@ CONFIGS = {
     "c3_1024": dict(L=1024, M=4194304, n_blocks=64, uv_sigma=0.1, seed=1703),
     # 4096x4096, 64M visibilities, 256 radial blocks (compact blobs, analytic blob spectra)
     "c5_4096": dict(L=4096, M=67108864, n_blocks=256, uv_sigma=0.1, seed=1705, compact=True),
+    # the 4096x4096 image with 8M visibilities: the 4096^2 workload at a size a
+    # multi-pass profiler capture can replay (visibility-side traffic scales with M)
+    "c5m8_4096": dict(L=4096, M=8388608, n_blocks=256, uv_sigma=0.1, seed=1705, compact=True),
 }
 
 
