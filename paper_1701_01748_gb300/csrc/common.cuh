@@ -157,6 +157,7 @@ struct ppd_ctx {
     void *twst0 = nullptr, *twst1 = nullptr;   // twiddles of the power-of-two core, stage by stage
     void *filt = nullptr;       // 8 x 16 reals (low-pass, zero padded)
     void *kbpoly = nullptr;     // (KB_DEG+1) x 8 floats
+    std::vector<float> kbpoly_h;   // host copy (kernel argument of the visibility kernels)
     double *prim_part = nullptr;
     int n_prim_blocks = 0;
     int n_stat_parts = 0;        // primal statistics partials the last primal launch wrote

@@ -281,6 +281,72 @@ struct PassArgs {
     int nseq;
 };
 
+// Row passes of the power-of-two core transform two real rows (a, b) as one
+// complex sequence.  Forward: z = a + i b, and after the FFT
+// A[k] = (Z[k] + conj(Z[-k]))/2, B[k] = (Z[k] - conj(Z[-k]))/(2i).
+template <typename C> __device__ __forceinline__ void split_two_real(C z, C zr, C &A, C &B) {
+    using R = decltype(z.x);
+    A = C{R(0.5) * (z.x + zr.x), R(0.5) * (z.y - zr.y)};
+    B = C{R(0.5) * (z.y + zr.y), R(0.5) * (zr.x - z.x)};
+}
+// Inverse to real parts: Re(F^H X) = F^H H with H[k] = (X[k] + conj(X[-k]))/2
+// (the Hermitian part of X), so the pair is Y = Ha + i Hb, F^H Y = ha + i hb;
+// returns Y[k] and Y[-k] from Xa[k], Xa[-k], Xb[k], Xb[-k].
+template <typename C> __device__ __forceinline__ void pack_two_real(C xa, C xar, C xb, C xbr, C &y, C &yr) {
+    using R = decltype(xa.x);
+    const C ha{R(0.5) * (xa.x + xar.x), R(0.5) * (xa.y - xar.y)};
+    const C hb{R(0.5) * (xb.x + xbr.x), R(0.5) * (xb.y - xbr.y)};
+    y = C{ha.x - hb.y, ha.y + hb.x};    // ha + i hb
+    yr = C{ha.x + hb.y, hb.x - ha.y};   // conj(ha) + i conj(hb)
+}
+
+// Loads the spectra of rows (row0 + 2s, row0 + 2s + 1), s < NSEQ, of tmp
+// (stored centred: natural frequency k at column (k + K/2) mod K) and writes
+// conj(Y) in natural order into buf, so that the forward FFT of buf gives
+// conj(F^H Y): row a's real inverse in .x, row b's in -.y.
+template <typename R, int K, int NSEQ>
+__device__ __forceinline__ void load_two_real_inverse(const cplx_t<R> *__restrict__ tmp, int row0, int L0,
+                                                      cplx_t<R> *buf) {
+    using C = cplx_t<R>;
+    constexpr int H = K / 2 + 1;   // pairs (k, -k), k = 0 .. K/2
+    for (int e = threadIdx.x; e < NSEQ * H; e += NT) {
+        const int s = e / H, k = e - s * H, kr = (K - k) & (K - 1);
+        const int ra = row0 + 2 * s, rb = ra + 1;
+        const int ck = (k + K / 2) & (K - 1), ckr = (kr + K / 2) & (K - 1);
+        C xa{0, 0}, xar{0, 0}, xb{0, 0}, xbr{0, 0};
+        if (ra < L0) {
+            xa = tmp[(int64_t)ra * K + ck];
+            xar = tmp[(int64_t)ra * K + ckr];
+        }
+        if (rb < L0) {
+            xb = tmp[(int64_t)rb * K + ck];
+            xbr = tmp[(int64_t)rb * K + ckr];
+        }
+        C y, yr;
+        pack_two_real(xa, xar, xb, xbr, y, yr);
+        buf[s * K + k] = cconj(y);
+        buf[s * K + kr] = cconj(yr);
+    }
+}
+
+// Writes the spectra of rows (row0 + 2s, row0 + 2s + 1) from the FFT of
+// a + i b in buf (natural order) to tmp (stored centred, marked columns).
+template <typename R, int K, int NSEQ>
+__device__ __forceinline__ void store_two_real_forward(const cplx_t<R> *out, int row0, int L0,
+                                                       const uint8_t *__restrict__ colmask,
+                                                       cplx_t<R> *__restrict__ tmp) {
+    using C = cplx_t<R>;
+    for (int e = threadIdx.x; e < NSEQ * K; e += NT) {
+        const int s = e / K, c = e % K, ra = row0 + 2 * s, rb = ra + 1;
+        if (!colmask[c]) continue;
+        const int kk = (c + K / 2) & (K - 1), kr = (K - kk) & (K - 1);
+        C A, B;
+        split_two_real(out[s * K + kk], out[s * K + kr], A, B);
+        if (ra < L0) tmp[(int64_t)ra * K + c] = A;
+        if (rb < L0) tmp[(int64_t)rb * K + c] = B;
+    }
+}
+
 // forward row pass: tmp[n0][c] = FFT_axis1(Z x)[n0][(c + K1/2) mod K1]
 template <typename R, int KT>
 __global__ void __launch_bounds__(NT) k_rows_fwd(const R *__restrict__ x, cplx_t<R> *__restrict__ tmp,
@@ -294,6 +360,21 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(const R *__restrict__ x, cplx_t
     C *buf = reinterpret_cast<C *>(smem_raw);
     C *buf2 = buf + B * K;
     const C *tws = KT ? stage_twiddles<R, BT, KT ? KT : 1>(buf, tw) : tw;
+    if constexpr (KT != 0) {   // two rows per sequence
+        const int row0 = blockIdx.x * 2 * BT;
+        for (int e = threadIdx.x; e < BT * KT; e += NT) {
+            const int s = e / KT, p = e % KT, ra = row0 + 2 * s, rb = ra + 1;
+            const int n1 = p < L1 / 2 ? p + L1 / 2 : (p >= KT - L1 / 2 ? p - KT + L1 / 2 : -1);
+            R va = 0, vb = 0;
+            if (n1 >= 0 && ra < L0) va = s0[ra] * s1[n1] * x[(int64_t)ra * L1 + n1];
+            if (n1 >= 0 && rb < L0) vb = s0[rb] * s1[n1] * x[(int64_t)rb * L1 + n1];
+            buf[e] = C{va, vb};
+        }
+        __syncthreads();
+        fft_smem<R, KT ? KT : 1, BT, false>(buf, tws);
+        store_two_real_forward<R, KT ? KT : 1, BT>(buf, row0, L0, colmask, tmp);
+        return;
+    }
     const int row0 = blockIdx.x * B;
     // one pass over the padded rows: position p holds pixel p + L1/2 (p <
     // L1/2) or p - K + L1/2 (p >= K - L1/2), zero in between
@@ -430,6 +511,19 @@ __global__ void __launch_bounds__(NT) k_rows_inv(const cplx_t<R> *__restrict__ t
     C *buf = reinterpret_cast<C *>(smem_raw);
     C *buf2 = buf + B * K;
     const C *tws = KT ? stage_twiddles<R, BT, KT ? KT : 1>(buf, tw) : tw;
+    if constexpr (KT != 0) {   // two rows per sequence
+        const int row0 = blockIdx.x * 2 * BT;
+        load_two_real_inverse<R, KT ? KT : 1, BT>(tmp, row0, L0, buf);
+        __syncthreads();
+        fft_smem<R, KT ? KT : 1, BT, false>(buf, tws);
+        for (int e = threadIdx.x; e < BT * L1; e += NT) {
+            const int s = e / L1, n1 = e % L1, ra = row0 + 2 * s, rb = ra + 1;
+            const C v = buf[s * KT + ((n1 - L1 / 2 + KT) & (KT - 1))];
+            if (ra < L0) img[(int64_t)ra * L1 + n1] = s0[ra] * s1[n1] * v.x;
+            if (rb < L0) img[(int64_t)rb * L1 + n1] = -s0[rb] * s1[n1] * v.y;
+        }
+        return;
+    }
     const int row0 = blockIdx.x * B;
     for (int e = threadIdx.x; e < B * K; e += NT) {
         const int s = e / K, c = e - s * K, n0 = row0 + s;
@@ -462,6 +556,41 @@ __global__ void __launch_bounds__(NT) k_rows_primal(const cplx_t<R> *__restrict_
     C *buf = reinterpret_cast<C *>(smem_raw);
     C *buf2 = buf + B * K;
     const C *tws = KT ? stage_twiddles<R, BT, KT ? KT : 1>(buf, tw) : tw;
+    PrimalSums<R> acc;
+    if constexpr (KT != 0) {
+        // two rows per sequence (rows row0 + 2s and row0 + 2s + 1)
+        constexpr int KK = KT ? KT : 1, LT = KK / 2, PER = BT * LT / NT;
+        static_assert(BT * LT % NT == 0, "pixel pairs per thread");
+        const int row0 = blockIdx.x * 2 * BT;
+        load_two_real_inverse<R, KK, BT>(tmp_inv, row0, L0, buf);
+        __syncthreads();
+        fft_smem<R, KK, BT, false>(buf, tws);
+        // the new xt of both rows stays in registers while the buffer is rewritten
+        R xa[PER], xb[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = threadIdx.x + k * NT, s = e / LT, n1 = e % LT, ra = row0 + 2 * s, rb = ra + 1;
+            const C v = buf[s * KK + ((n1 - LT / 2 + KK) & (KK - 1))];
+            xa[k] = xb[k] = R(0);
+            if (ra < L0) xa[k] = primal_pixel(P, (int64_t)ra * LT + n1, s0[ra] * s1[n1] * v.x, acc);
+            if (rb < L0) xb[k] = primal_pixel(P, (int64_t)rb * LT + n1, -s0[rb] * s1[n1] * v.y, acc);
+        }
+        __syncthreads();
+        // the new rows a + i b in place, each thread also clearing the padding
+        // position K/2 away from its pixel's (the padding is [LT/2, K - LT/2))
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = threadIdx.x + k * NT, s = e / LT, n1 = e % LT, ra = row0 + 2 * s, rb = ra + 1;
+            const int pos = (n1 - LT / 2 + KK) & (KK - 1);
+            buf[s * KK + pos] = C{ra < L0 ? s0[ra] * s1[n1] * xa[k] : R(0), rb < L0 ? s0[rb] * s1[n1] * xb[k] : R(0)};
+            buf[s * KK + ((pos + LT) & (KK - 1))] = C{0, 0};
+        }
+        __syncthreads();
+        fft_smem<R, KK, BT, false>(buf, tws);
+        store_two_real_forward<R, KK, BT>(buf, row0, L0, colmask, tmp_fwd);
+        acc.write(part + 3 * (int64_t)blockIdx.x);
+        return;
+    }
     const int row0 = blockIdx.x * B;
     for (int e = threadIdx.x; e < B * K; e += NT) {
         const int s = e / K, c = e - s * K, n0 = row0 + s;
@@ -469,33 +598,7 @@ __global__ void __launch_bounds__(NT) k_rows_primal(const cplx_t<R> *__restrict_
     }
     __syncthreads();
     C *out = run_fft<R, KT, BT, false>(buf, buf2, tws, B, pa.pl, tw);
-    PrimalSums<R> acc;
-    if constexpr (KT != 0) {
-        // the new xt stays in registers while the buffer is cleared
-        constexpr int LT = KT / 2, PER = BT * LT / NT;
-        static_assert(BT * LT % NT == 0, "pixels per thread");
-        R xtn[PER];
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int e = threadIdx.x + k * NT, s = e / LT, n1 = e % LT, n0 = row0 + s;
-            xtn[k] = R(0);
-            if (n0 < L0) {
-                const R g = s0[n0] * s1[n1] * out[s * K + ((n1 - LT / 2 + K) & (K - 1))].x;
-                xtn[k] = primal_pixel(P, (int64_t)n0 * LT + n1, g, acc);
-            }
-        }
-        __syncthreads();
-        // the new row in place, each thread also clearing the padding
-        // position K/2 away from its pixel's (the padding is [LT/2, K - LT/2))
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int e = threadIdx.x + k * NT, s = e / LT, n1 = e % LT, n0 = row0 + s;
-            const int pos = (n1 - LT / 2 + K) & (K - 1);
-            buf[s * K + pos] = C{n0 < L0 ? s0[n0] * s1[n1] * xtn[k] : R(0), R(0)};
-            buf[s * K + ((pos + LT) & (K - 1))] = C{0, 0};
-        }
-        __syncthreads();
-    } else {
+    {
         // the mixed-radix core leaves the result in one buffer: the forward
         // input is built in the other one
         C *fin = out == buf ? buf2 : buf;
@@ -542,7 +645,9 @@ template <typename R, int KT> struct RowPass {
         return KT ? pass_smem<R>(BT, KT) : (size_t)2 * nseq(c) * c->K1 * 2 * sizeof(R);
     }
     static PassArgs args(const ppd_ctx *c) { return PassArgs{c->plan1, nseq(c)}; }
-    static unsigned blocks(const ppd_ctx *c) { return (unsigned)((c->L0 + nseq(c) - 1) / nseq(c)); }
+    // rows per CTA: two per sequence in the power-of-two core
+    static int rows(const ppd_ctx *c) { return KT ? 2 * BT : nseq(c); }
+    static unsigned blocks(const ppd_ctx *c) { return (unsigned)((c->L0 + rows(c) - 1) / rows(c)); }
     static const cplx_t<R> *tw(const ppd_ctx *c) {
         return static_cast<const cplx_t<R> *>(KT ? c->twst1 : c->tw1);
     }

@@ -75,29 +75,22 @@ __global__ void k_cell_count(const int32_t *__restrict__ cell, const int32_t *__
 
 // ----------------------------------------------------------------- weights
 // FP32: per tap j a degree-KB_DEG polynomial in t = 2 frac - 1 (Chebyshev fit
-// of psi(frac + 3 - j) made on the host); coefficients poly[k*8 + j].
-__device__ __forceinline__ void kb_weights(float frac, float (&w)[KB_J], const float *poly, double, double) {
+// of psi(frac + 3 - j) made on the host); coefficients p[k*8 + j].  p is a
+// kernel argument, so with the loops unrolled every coefficient is a
+// constant-bank operand of its FMA: no load instruction.
+constexpr int KB_NC = (KB_DEG + 1) * KB_J;
+__device__ __forceinline__ void kb_weights(float frac, float (&w)[KB_J], const float (&p)[KB_NC], double, double) {
     const float t = fmaf(2.0f, frac, -1.0f);
-    const float4 *p4 = reinterpret_cast<const float4 *>(poly);   // 16-byte aligned rows of 8 taps
-    float4 lo = p4[2 * KB_DEG], hi = p4[2 * KB_DEG + 1];
-    w[0] = lo.x, w[1] = lo.y, w[2] = lo.z, w[3] = lo.w, w[4] = hi.x, w[5] = hi.y, w[6] = hi.z, w[7] = hi.w;
 #pragma unroll
-    for (int k = KB_DEG - 1; k >= 0; --k) {
-        lo = p4[2 * k];
-        hi = p4[2 * k + 1];
-        w[0] = fmaf(w[0], t, lo.x);
-        w[1] = fmaf(w[1], t, lo.y);
-        w[2] = fmaf(w[2], t, lo.z);
-        w[3] = fmaf(w[3], t, lo.w);
-        w[4] = fmaf(w[4], t, hi.x);
-        w[5] = fmaf(w[5], t, hi.y);
-        w[6] = fmaf(w[6], t, hi.z);
-        w[7] = fmaf(w[7], t, hi.w);
-    }
+    for (int j = 0; j < KB_J; ++j) w[j] = p[KB_DEG * KB_J + j];
+#pragma unroll
+    for (int k = KB_DEG - 1; k >= 0; --k)
+#pragma unroll
+        for (int j = 0; j < KB_J; ++j) w[j] = fmaf(w[j], t, p[k * KB_J + j]);
 }
 
 // FP64: the kernel itself, psi(d) = I0(beta sqrt(1 - (d/4)^2)) / I0(beta), d = frac + 3 - j.
-__device__ __forceinline__ void kb_weights(double frac, double (&w)[KB_J], const float *, double beta,
+__device__ __forceinline__ void kb_weights(double frac, double (&w)[KB_J], const float (&)[KB_NC], double beta,
                                            double inv_i0b) {
 #pragma unroll
     for (int j = 0; j < KB_J; ++j) {
@@ -116,7 +109,7 @@ template <typename R> struct VisArgs {
     // most DG_NT visibilities of one chunk, each with its partial slot
     const int32_t *u_start, *u_count, *u_chunk, *u_order;
     int K0, K1, ntile1;
-    const float *kbpoly;
+    float kbp[KB_NC];   // the FP32 weight polynomials (kb_weights)
     double beta, inv_i0b;
     const cplx_t<R> *y;
     cplx_t<R> *v, *z, *w, *p;
@@ -288,11 +281,9 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
     constexpr int TILE_BYTES = E * E * (int)sizeof(C);
     constexpr int TILE_STRIDE = (TILE_BYTES + 127) / 128 * 128;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *poly = reinterpret_cast<float *>(smem_raw + 2 * TILE_STRIDE);
     __shared__ uint64_t bar[2];
     __shared__ int ok_s;
 
-    for (int i = threadIdx.x; i < (KB_DEG + 1) * KB_J; i += DG_NT) poly[i] = A.kbpoly ? A.kbpoly[i] : 0.f;
     if (threadIdx.x == 0) {
         ok_s = 1;
         mbar_init(&bar[0], 1);
@@ -376,8 +367,8 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
             if (i + DG_NT < count) load_vis<R, MODE>(A, gi + DG_NT, nx);
             const int lb0 = (cur.rc.packed & 0xffff) - row0, lb1 = ((cur.rc.packed >> 16) & 0xffff) - col0;
             R w0[KB_J], w1[KB_J];
-            kb_weights(cur.rc.f0, w0, poly, A.beta, A.inv_i0b);
-            kb_weights(cur.rc.f1, w1, poly, A.beta, A.inv_i0b);
+            kb_weights(cur.rc.f0, w0, A.kbp, A.beta, A.inv_i0b);
+            kb_weights(cur.rc.f1, w1, A.kbp, A.beta, A.inv_i0b);
             C q{0, 0};
 #pragma unroll
             for (int a = 0; a < KB_J; ++a) {
@@ -525,11 +516,12 @@ __global__ void k_block_norms(const double *__restrict__ partials, const int32_t
 }
 
 // ----------------------------------------------------------------- gridding
-// Per CTA: phase 1 (thread per visibility) forms Theta v, the 8 products
-// w0[a] Theta v and the 8 weights w1[b] into a staging area; phase 2 (warp
-// per visibility) adds the 8 x 8 footprint w1[b] (w0[a] Theta v) into the
-// warp's private (T+8)^2 tile; phase 3 sums the private
-// tiles in warp order and writes the chunk's partial tile.  GR_DUAL fuses the
+// Per warp, in rounds of 32 visibilities of its slice of the chunk: phase 1
+// (lane per visibility) forms Theta v, the 8 products w0[a] Theta v and the 8
+// weights w1[b] into the warp's staging area; phase 2 (the warp per
+// visibility) adds the 8 x 8 footprint w1[b] (w0[a] Theta v) into the warp's
+// private (T+8)^2 tile.  Finally the CTA sums the private tiles in warp order
+// and writes the chunk's partial tile.  GR_DUAL fuses the
 // end of the data step: p = P_B(w) = y + c (w - y), v = U (z - p).
 // Lane l of the scattering warp owns footprint column l mod 8 of rows l/8
 // and l/8 + 4; with the private-tile pitch T + 8 = 8 mod 16 (in 8-byte
@@ -547,15 +539,14 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
     constexpr int E = T + HALO, P = E;   // P: pitch of the private tiles (8 mod 16 words)
     static_assert(P % 16 == 8, "private-tile pitch");
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    // staging, component-major with a pitch of NT + 1 so that the stores of
-    // consecutive threads and the reads of one visibility by a warp's lanes
-    // both hit distinct banks
-    constexpr int SP = NT + 1;
+    // per-warp staging of 32 visibilities, component-major with a pitch of
+    // 33 so that the stores of a warp's lanes and their reads of one
+    // visibility both hit distinct banks
+    constexpr int SP = 33, SW = 2 * 4 * SP;   // complex words per warp: 4 x SP pairs
     C *priv = reinterpret_cast<C *>(smem_raw);                          // NW * E * P
-    C *sa = priv + NW * E * P;                                          // 4 x SP pairs (w0[a] Theta v, w0[a+4] Theta v)
-    R *sb = reinterpret_cast<R *>(sa + 2 * 4 * SP);                     // 8 x SP: w1[b]
-    int *slb = reinterpret_cast<int *>(sb + KB_J * SP);                 // NT
-    float *poly = reinterpret_cast<float *>(slb + NT);                  // 64
+    C *sa_all = priv + NW * E * P;                                      // NW x 4 x SP pairs (w0[a] Theta v, w0[a+4] Theta v)
+    R *sb_all = reinterpret_cast<R *>(sa_all + NW * SW);                // NW x 8 x SP: w1[b]
+    int *slb_all = reinterpret_cast<int *>(sb_all + NW * KB_J * SP);    // NW x 32
 
     const int ch = blockIdx.x;
     const int start = A.ch_start[ch], count = A.ch_count[ch], tl = A.ch_tile[ch];
@@ -569,7 +560,6 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
     // warps that scatter: at least GRID_MINV visibilities each, so that a
     // small chunk clears and sums only as many private tiles as it fills
     const int nwu = min(NW, max(1, (count + GRID_MINV - 1) / GRID_MINV));
-    for (int i = threadIdx.x; i < (KB_DEG + 1) * KB_J; i += NT) poly[i] = A.kbpoly ? A.kbpoly[i] : 0.f;
     for (int e = threadIdx.x; e < nwu * E * P; e += NT) priv[e] = C{0, 0};
     R c = 0;
     // Algorithm 2 stopped early (stopping test): the prox output is the p
@@ -597,8 +587,8 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
 
     C *mine = priv + warp * E * P;
     const int bcol = lane & 7, a0 = lane >> 3;   // rows a0 and a0 + 4
-    // this thread's visibility of the current round, loaded one round ahead
-    // so that the loads of round r + 1 are in flight during the scatter of r
+    // a lane's visibility of the current round, loaded one round ahead so
+    // that the loads of round r + 1 are in flight during the scatter of r
     struct In {
         VisRec<R> rc;
         C a, b, z;   // GR_DUAL active: y, w, z (stopped early: p, -, z); inactive: v; operator modes: input
@@ -621,12 +611,26 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
         }
         o.th = A.theta_v ? A.theta_v[gi] : A.theta_s;
     };
+    // warp w owns a contiguous slice of the chunk (the sort order makes runs
+    // of visibilities share a first tap) and works through it in rounds of
+    // 32: each lane stages one visibility (dual update, Theta v, weights) in
+    // the warp's staging area, then the warp adds the 32 footprints one after
+    // the other, each lane accumulating its two cells in registers and
+    // writing the private tile only when the base cell changes.  Warps never
+    // wait for one another inside the loop.
+    C *sa = sa_all + warp * SW;
+    R *sb = sb_all + warp * KB_J * SP;
+    int *slb = slb_all + warp * 32;
+    const int seg = (count + nwu - 1) / nwu;
+    const int v0 = warp < nwu ? min(count, warp * seg) : count, v1 = min(count, v0 + seg);
     In cur;
-    if ((int)threadIdx.x < count) load_in(start + threadIdx.x, cur);
-    for (int base = 0; base < count; base += NT) {
-        const int n = min(NT, count - base);
-        if (threadIdx.x < n) {
-            const int gi = start + base + threadIdx.x;
+    if (v0 + lane < v1) load_in(start + v0 + lane, cur);
+    int run = -1;
+    C acc0{0, 0}, acc1{0, 0};
+    for (int base = v0; base < v1; base += 32) {
+        const int n = min(32, v1 - base);
+        if (lane < n) {
+            const int gi = start + base + lane;
             const VisRec<R> rc = cur.rc;
             C vv;
             if (MODE == GR_DUAL && act) {
@@ -650,11 +654,11 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
             const R th = cur.th;
             const C tv{th * vv.x, th * vv.y};
             R w0[KB_J], w1[KB_J];
-            kb_weights(rc.f0, w0, poly, A.beta, A.inv_i0b);
-            kb_weights(rc.f1, w1, poly, A.beta, A.inv_i0b);
+            kb_weights(rc.f0, w0, A.kbp, A.beta, A.inv_i0b);
+            kb_weights(rc.f1, w1, A.kbp, A.beta, A.inv_i0b);
 #pragma unroll
             for (int a = 0; a < KB_J / 2; ++a) {   // lane rows (a, a+4) read one pair
-                C *da = sa + 2 * (a * SP + threadIdx.x);
+                C *da = sa + 2 * (a * SP + lane);
                 if constexpr (sizeof(R) == 4) {
                     *reinterpret_cast<float4 *>(da) =
                         make_float4(w0[a] * tv.x, w0[a] * tv.y, w0[a + 4] * tv.x, w0[a + 4] * tv.y);
@@ -664,25 +668,13 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
                 }
             }
 #pragma unroll
-            for (int j = 0; j < KB_J; ++j) sb[j * SP + threadIdx.x] = w1[j];
+            for (int j = 0; j < KB_J; ++j) sb[j * SP + lane] = w1[j];
             const int lb0 = (rc.packed & 0xffff) - row0, lb1 = ((rc.packed >> 16) & 0xffff) - col0;
-            slb[threadIdx.x] = lb0 | (lb1 << 16);
+            slb[lane] = lb0 | (lb1 << 16);
         }
-        __syncthreads();
-        In nxt;
-        if (base + NT + (int)threadIdx.x < count) load_in(start + base + NT + threadIdx.x, nxt);
-        // warp w takes a contiguous segment of the staged visibilities; the
-        // sort order makes runs of visibilities share a first tap, so each
-        // lane accumulates its two footprint cells in registers and writes
-        // the warp's private tile only when the base cell changes.
-        const int seg = (n + nwu - 1) / nwu;
-        const int i0 = warp < nwu ? warp * seg : n, i1 = min(n, i0 + seg);
-        int run = -1;
-        C acc0{0, 0}, acc1{0, 0};
-        // the staged operands of visibility i + 1 are read while visibility i
-        // is accumulated (the staging is not written during the scatter)
-        auto fetch = [&](int i, int &lb, C &pa, C &pb, R &wb) {
-            lb = slb[i];
+        __syncwarp();
+        if (base + 32 + lane < v1) load_in(start + base + 32 + lane, cur);   // next round, in flight during the scatter
+        auto fetch = [&](int i, C &pa, C &pb, R &wb) {   // w0[a0] Theta v, w0[a0+4] Theta v, w1[bcol]
             if constexpr (sizeof(R) == 4) {
                 const float4 q = *reinterpret_cast<const float4 *>(sa + 2 * (a0 * SP + i));
                 pa = C{q.x, q.y};
@@ -693,15 +685,31 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
             }
             wb = sb[bcol * SP + i];
         };
-        int lbn = 0;
-        C pan{0, 0}, pbn{0, 0};   // w0[a0] Theta v, w0[a0+4] Theta v
-        R wbn = 0;
-        if (i0 < i1) fetch(i0, lbn, pan, pbn, wbn);
-        for (int i = i0; i < i1; ++i) {
-            const int lb = lbn;
-            const C pa = pan, pb = pbn;
-            const R wb = wbn;
-            if (i + 1 < i1) fetch(i + 1, lbn, pan, pbn, wbn);
+        auto accumulate = [&](const C &pa, const C &pb, R wb) {
+            acc0.x += wb * pa.x;
+            acc0.y += wb * pa.y;
+            acc1.x += wb * pb.x;
+            acc1.y += wb * pb.y;
+        };
+        int i = 0;
+        while (i < n) {
+            // four visibilities of the current run (the order is sorted by
+            // base cell, so equal ends mean four equal bases): no checks,
+            // all operand loads issued together
+            if (i + 4 <= n && slb[i] == run && slb[i + 3] == run) {
+                C pa[4], pb[4];
+                R wb[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) fetch(i + q, pa[q], pb[q], wb[q]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) accumulate(pa[q], pb[q], wb[q]);
+                i += 4;
+                continue;
+            }
+            const int lb = slb[i];
+            C pa, pb;
+            R wb;
+            fetch(i, pa, pb, wb);
             if (lb != run) {
                 if (run >= 0) {
                     C *cell = mine + ((run & 0xffff) + a0) * P + (run >> 16) + bcol;
@@ -713,20 +721,18 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
                 acc0 = C{0, 0};
                 acc1 = C{0, 0};
             }
-            acc0.x += wb * pa.x;
-            acc0.y += wb * pa.y;
-            acc1.x += wb * pb.x;
-            acc1.y += wb * pb.y;
+            accumulate(pa, pb, wb);
+            ++i;
         }
-        if (run >= 0) {
-            C *cell = mine + ((run & 0xffff) + a0) * P + (run >> 16) + bcol;
-            C g0 = cell[0], g1 = cell[4 * P];
-            cell[0] = cadd(g0, acc0);
-            cell[4 * P] = cadd(g1, acc1);
-        }
-        __syncthreads();
-        cur = nxt;
+        __syncwarp();   // the staging is rewritten by the next round
     }
+    if (run >= 0) {
+        C *cell = mine + ((run & 0xffff) + a0) * P + (run >> 16) + bcol;
+        C g0 = cell[0], g1 = cell[4 * P];
+        cell[0] = cadd(g0, acc0);
+        cell[4 * P] = cadd(g1, acc1);
+    }
+    __syncthreads();
     C *out = gpart + (int64_t)ch * E * E;
     for (int e = threadIdx.x; e < E * E; e += NT) {
         const int r = e / E, cc = e % E;
@@ -793,7 +799,7 @@ template <typename R> VisArgs<R> make_args(ppd_ctx *c) {
     A.K0 = c->K0;
     A.K1 = c->K1;
     A.ntile1 = c->K1 / c->T;
-    A.kbpoly = static_cast<const float *>(c->kbpoly);
+    for (int i = 0; i < KB_NC; ++i) A.kbp[i] = c->kbpoly_h.empty() ? 0.f : c->kbpoly_h[i];
     A.beta = c->beta;
     A.inv_i0b = 1.0 / std::cyl_bessel_i(0.0, c->beta);
     A.y = static_cast<const cplx_t<R> *>(c->y);
@@ -826,9 +832,9 @@ template <typename R> VisArgs<R> make_args(ppd_ctx *c) {
 }
 
 template <typename R, int T> size_t grid_smem() {
-    constexpr int NW = GridCfg<R>::NWARP, NT = NW * 32, E = T + HALO, P = E, SP = NT + 1;
-    return (size_t)NW * E * P * sizeof(cplx_t<R>) + 8 * SP * sizeof(cplx_t<R>) + KB_J * SP * sizeof(R) +
-           NT * sizeof(int) + (KB_DEG + 1) * KB_J * sizeof(float);
+    constexpr int NW = GridCfg<R>::NWARP, E = T + HALO, P = E, SP = 33;
+    return (size_t)NW * E * P * sizeof(cplx_t<R>) + (size_t)NW * 8 * SP * sizeof(cplx_t<R>) +
+           (size_t)NW * KB_J * SP * sizeof(R) + NW * 32 * sizeof(int);
 }
 
 template <typename R, int T>
@@ -838,7 +844,7 @@ int degrid_t(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const 
     A.perm = perm;
     constexpr int E = T + HALO;
     const size_t tile_stride = ((size_t)E * E * sizeof(cplx_t<R>) + 127) / 128 * 128;
-    const size_t sh = 2 * tile_stride + (KB_DEG + 1) * KB_J * sizeof(float);
+    const size_t sh = 2 * tile_stride;
     PPD_CHECK(smem_attr((const void *)k_degrid<R, T, DG_OP>, (int)sh));
     PPD_CHECK(smem_attr((const void *)k_degrid<R, T, DG_DUAL>, (int)sh));
     PPD_CHECK(smem_attr((const void *)k_degrid<R, T, DG_FIRST>, (int)sh));
@@ -945,6 +951,7 @@ int make_kb_poly(ppd_ctx *c) {
         for (int k = 0; k < n; ++k) out[(size_t)k * KB_J + j] = (float)mono[k];
     }
     PPD_CUDA(cudaMemcpy(c->kbpoly, out.data(), out.size() * sizeof(float), cudaMemcpyHostToDevice));
+    c->kbpoly_h = out;
     return PPD_OK;
 }
 
