@@ -531,6 +531,8 @@ def main():
     ap.add_argument("--isnr", type=float, default=30.0, help="input SNR (dB) of the study problems")
     ap.add_argument("--autotune", action="store_true", help="batch workloads: autotune each problem's gridding")
     ap.add_argument("--no-autotune", action="store_true", help="main bench: keep the library's default gridding")
+    ap.add_argument("--launch-overlap", action="store_true",
+                    help="kernels start while their predecessor drains (programmatic dependent launch)")
     ap.add_argument("--quick", action="store_true",
                     help="only the timed FP32 steps (for profiler launch lists); eta from 20 power steps")
     args = ap.parse_args()
@@ -592,7 +594,8 @@ def main():
     sp = stream.cuda_stream
 
     def make(prec, **kw):
-        s = ppd.Solver(p.L, p.n_blocks, precision=prec, stream=sp, tile=args.tile, chunk=args.chunk, **kw)
+        s = ppd.Solver(p.L, p.n_blocks, precision=prec, stream=sp, tile=args.tile, chunk=args.chunk,
+                       launch_overlap=int(args.launch_overlap), **kw)
         s.set_problem(p.omega, p.y, p.block, theta=p.theta, x_true=p.x_true)
         return s
 
@@ -760,6 +763,7 @@ def main():
         "config": {**workload_config(args.workload),
                    "l2": "flushed (256 MiB write) between timed steps", "graph": "one CUDA graph per iteration",
                    "replicas": world,
+                   "launches": "overlapped (programmatic dependent launch)" if args.launch_overlap else "serial",
                    "gridding": {"tile": prm32["tile"], "chunk": prm32["chunk"], "work_items": prm32["n_chunks"],
                                 "autotuned": not args.no_autotune and args.tile == 0 and args.chunk == 0}},
         "snr_iters": snr_iters,

@@ -84,7 +84,9 @@ typedef struct ppd_ctx ppd_ctx;
  * (Section 5.1: tau = 0.49, lambda = 1, kappa = 1e-4, n_itr = 1, no
  * randomisation; Section 5: oversampling 2 per axis, 8 x 8 Kaiser-Bessel). */
 typedef struct {
-    int32_t  n0, n1;            /* image rows / columns: powers of two, 16 <= n <= 4096 */
+    int32_t  n0, n1;            /* image rows / columns: multiples of 16 in [16, 4096] whose
+                                   doubles 2 n have no prime factor above 5 (powers of two
+                                   above 4096 in FP64) */
     int32_t  oversample;        /* grid K = oversample * n per axis; must be 2 */
     int32_t  kernel_width;      /* interpolation support J; must be 8 */
     double   kb_beta;           /* Kaiser-Bessel shape; 0 => 2.34 * J */
@@ -124,7 +126,10 @@ typedef struct {
                                    x_i = 0.5 + 2^-53 (s_i >> 11), s_i the SplitMix64 output
                                    for counter seed + (i + 1) * 0x9E3779B97F4A7C15 */
     int32_t  norm_method;       /* PPD_NORM_LANCZOS (default) or PPD_NORM_POWER */
-    int32_t  pad1;
+    int32_t  launch_overlap;    /* 1: a kernel of the iteration may start while the one before it
+                                   in its stream drains (programmatic dependent launch, compute
+                                   capability 9.0 and later); 0 (default): every kernel waits for
+                                   its predecessor to finish.  Results are the same either way. */
 } ppd_config;
 
 /* Per-call statistics (ppd_iterate).  All norms are computed in double. */

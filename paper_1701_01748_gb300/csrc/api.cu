@@ -119,7 +119,7 @@ void free_vis(ppd_ctx *c) {
     for (void *p : {c->rec, c->theta_v, c->y, c->v, c->z, c->w, c->p, c->y_raw, (void *)c->perm,
                     (void *)c->count_cell, (void *)c->ch.start, (void *)c->ch.count, (void *)c->ch.tile,
                     (void *)c->ch.block, (void *)c->ch.tile_first, (void *)c->ch.tile_n, (void *)c->ch.blk_ptr,
-                    (void *)c->ch.u_start, (void *)c->ch.u_count, (void *)c->ch.u_chunk, (void *)c->ch.u_pos, (void *)c->ch.u_order, (void *)c->ch.active, (void *)c->partials, (void *)c->scale, (void *)c->resid2,
+                    (void *)c->ch.u_start, (void *)c->ch.u_count, (void *)c->ch.u_chunk, (void *)c->ch.u_pos, (void *)c->ch.u_order, (void *)c->ch.order, (void *)c->ch.active, (void *)c->partials, (void *)c->scale, (void *)c->resid2,
                     (void *)c->eps_d, (void *)c->mu_d, c->gpart})
         dfree(p);
     c->rec = c->theta_v = c->y = c->v = c->z = c->w = c->p = c->y_raw = c->gpart = nullptr;
@@ -693,6 +693,8 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
         return fail(PPD_ERR_INVALID_ARG, "ppd_create: unknown norm_method");
     if (k.tile != 0 && k.tile != 16 && k.tile != 32) return fail(PPD_ERR_INVALID_ARG, "ppd_create: tile must be 16 or 32");
     if (k.chunk < 0) return fail(PPD_ERR_INVALID_ARG, "ppd_create: chunk must be >= 0");
+    if (k.launch_overlap != 0 && k.launch_overlap != 1)
+        return fail(PPD_ERR_INVALID_ARG, "ppd_create: launch_overlap must be 0 or 1");
     if (!(k.inner_tol >= 0) || !(k.stop_tol >= 0) || !(k.stop_eps_factor >= 0) || k.stop_every < 0 ||
         !std::isfinite(k.inner_tol) || !std::isfinite(k.stop_tol) || !std::isfinite(k.stop_eps_factor))
         return fail(PPD_ERR_INVALID_ARG, "ppd_create: invalid stopping-test parameter");
@@ -717,6 +719,11 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
     c->kappa = k.kappa;
     c->zeta = k.zeta > 0 ? k.zeta : 1.0;
     cudaGetDevice(&c->device);
+    {
+        int major = 0;
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, c->device);
+        c->overlap = k.launch_overlap == 1 && major >= 9;
+    }
     auto bail = [&](int st) {
         ppd_destroy(c);
         return st;
@@ -948,6 +955,10 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
     std::vector<int32_t> uord(nu);
     for (int64_t u = 0; u < nu; ++u) uord[u] = (int32_t)u;
     std::stable_sort(uord.begin(), uord.end(), [&](int32_t a, int32_t b) { return un[a] > un[b]; });
+    // the gridding's CTA order: chunks by decreasing size
+    std::vector<int32_t> cord(nch);
+    for (int64_t k = 0; k < nch; ++k) cord[k] = (int32_t)k;
+    std::stable_sort(cord.begin(), cord.end(), [&](int32_t a, int32_t b) { return cn[a] > cn[b]; });
     std::vector<int32_t> bptr(c->d + 1, 0), upos(nu);
     for (int64_t u = 0; u < nu; ++u) bptr[cbk[uc[u]] + 1]++;
     for (int j = 0; j < c->d; ++j) bptr[j + 1] += bptr[j];
@@ -964,7 +975,8 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
         (st = dalloc(&c->ch.block, nch)) || (st = dalloc(&c->ch.tile_first, ntiles)) ||
         (st = dalloc(&c->ch.tile_n, ntiles)) || (st = dalloc(&c->ch.blk_ptr, c->d + 1)) ||
         (st = dalloc(&c->ch.u_start, nu)) ||
-        (st = dalloc(&c->ch.u_count, nu)) || (st = dalloc(&c->ch.u_chunk, nu)) || (st = dalloc(&c->ch.u_pos, nu)) || (st = dalloc(&c->ch.u_order, nu)) || (st = dalloc(&c->ch.active, active.size())) ||
+        (st = dalloc(&c->ch.u_count, nu)) || (st = dalloc(&c->ch.u_chunk, nu)) || (st = dalloc(&c->ch.u_pos, nu)) || (st = dalloc(&c->ch.u_order, nu)) || (st = dalloc(&c->ch.order, nch)) ||
+        (st = dalloc(&c->ch.active, active.size())) ||
         (st = dalloc(&c->partials, 2 * NPART * (size_t)nu)) ||
         (st = dalloc(&c->scale, c->d)) || (st = dalloc(&c->resid2, c->d)) || (st = dalloc(&c->eps_d, c->d)) ||
         (st = dalloc(&c->mu_d, c->d)) || (st = dalloc_bytes(&c->gpart, (size_t)nch * E * E * cbsz)) ||
@@ -1003,6 +1015,7 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
         (e = cudaMemcpy(c->ch.u_chunk, uc.data(), nu * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->ch.u_pos, upos.data(), nu * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->ch.u_order, uord.data(), nu * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->ch.order, cord.data(), nch * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->ch.active, active.data(), active.size() * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->perm, c->perm_h.data(), M * 8, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->y_raw, yraw_sorted.data(), 2 * M * 8, cudaMemcpyHostToDevice))) {

@@ -20,6 +20,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/ppd.h"
@@ -55,6 +56,25 @@ constexpr int ERR_BOUNDS = 4;
 
 // bounded spin for mbarrier waits (iterations of try_wait)
 constexpr long long SPIN_LIMIT = 1ll << 21;
+
+// ---------------------------------------------------------------- overlapped launches
+// Programmatic dependent launch (PTX griddepcontrol, sm_90 and later).  A
+// kernel started by launch() below may be scheduled while the kernel before
+// it in the stream is still draining: its CTAs do their setup (shared
+// memory, static tables), then pdl_wait() returns once that kernel has
+// completed and its writes are visible.  Every CTA of such a kernel calls
+// pdl_wait() before it touches global data that another kernel writes or
+// reads, and before it exits, so a kernel's completion still implies the
+// completion of everything before it in the stream.  pdl_trigger(), issued
+// right after the wait, lets the next kernel's CTAs be scheduled; it takes
+// effect once every CTA has issued it or exited, so at most one kernel
+// waits ahead.  Both are no-ops in a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() {
+    pdl_wait();
+    pdl_trigger();
+}
 
 // ---------------------------------------------------------------- status
 struct Error {
@@ -125,6 +145,7 @@ struct Chunks {
     int64_t nu = 0;
     int32_t *u_start = nullptr, *u_count = nullptr, *u_chunk = nullptr, *u_pos = nullptr, *u_order = nullptr;
     int32_t *blk_ptr = nullptr;
+    int32_t *order = nullptr;    // chunks by decreasing size (the gridding's CTA order)
     int32_t *active = nullptr;   // tiles the combine pass writes (device)
     int64_t n_active = 0;
 };
@@ -235,6 +256,9 @@ struct ppd_ctx {
     // timing
     bool timing = false;
     bool capturing = false;
+    // kernels of a stream overlap the drain of their predecessor
+    // (programmatic dependent launch; off with per-kernel timing)
+    bool overlap = false;
     std::vector<ppd::TimingSite> sites_graph;   // fixed sites inside the captured graph
     std::vector<ppd::TimingSite> sites_eager;   // sites since last collect (eager launches)
     std::vector<cudaEvent_t> event_pool;
@@ -249,6 +273,27 @@ namespace ppd {
 // launch count and optional per-kernel events are recorded.
 int launch_begin(ppd_ctx *c, const char *name, cudaStream_t s, int *site);
 int launch_end(ppd_ctx *c, int site, cudaStream_t s);
+
+// Launches kernel k, which follows the pdl_wait() rule above, with
+// programmatic stream serialisation when the context allows it and `chain`
+// is set (the caller clears it after a cross-stream join, so that such a
+// kernel waits for all of its inputs in the ordinary way).  Errors are left
+// for launch_end to report.
+template <typename... P, typename... A>
+void launch(ppd_ctx *c, bool chain, void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+            A &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = (chain && c->overlap && !c->timing) ? 1 : 0;
+    (void)cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
 
 // ---------------------------------------------------------------- launchers
 // FFT (fft.cu)
@@ -346,17 +391,32 @@ template <typename R> struct PrimalSums {
     }
 };
 
+// The pixel's inputs of the primal step, loadable before g is known.
+template <typename R> struct PrimalIn {
+    R xo, xte, wd, un, ut, xtr;
+};
+template <typename R> __device__ __forceinline__ PrimalIn<R> primal_load(const PrimalArgs<R> &P, int64_t e) {
+    PrimalIn<R> in;
+    in.xo = P.x[e];
+    in.xte = P.xt[e];
+    in.wd = P.w0 ? P.w0[e] : R(1);
+    in.un = P.u0[e];
+    in.ut = P.ut[e];
+    in.xtr = P.xtrue ? P.xtrue[e] : R(0);
+    return in;
+}
+
 template <typename R>
-__device__ __forceinline__ R primal_pixel(const PrimalArgs<R> &P, int64_t e, R g, PrimalSums<R> &acc) {
+__device__ __forceinline__ R primal_pixel(const PrimalArgs<R> &P, int64_t e, R g, const PrimalIn<R> &in,
+                                          PrimalSums<R> &acc) {
     const R third = R(1.0 / 3.0);
-    const R xo = P.x[e], xte = P.xt[e];
-    const R wd = P.w0 ? P.w0[e] : R(1);
-    R un = P.u0[e];
+    const R xo = in.xo, xte = in.xte, wd = in.wd;
+    R un = in.un;
     if (!P.pmask || P.pmask[0]) {
         un = fmin(fmax(un + wd * (xte * third), -P.kappa), P.kappa);
         P.u0[e] = un;
     }
-    const R utot = (wd * un + P.ut[e]) * third;
+    const R utot = (wd * un + in.ut) * third;
     const R xb = fmax(R(0), xo - P.tau * (P.eta * g + P.zeta * utot));
     const R xtn = R(2) * xb - xo;
     P.xt[e] = xtn;
@@ -365,10 +425,14 @@ __device__ __forceinline__ R primal_pixel(const PrimalArgs<R> &P, int64_t e, R g
     PrimalSums<R>::kadd(acc.sd, acc.cd, dd * dd);
     PrimalSums<R>::kadd(acc.sx, acc.cx, xb * xb);
     if (P.xtrue) {
-        const R de = xb - P.xtrue[e];
+        const R de = xb - in.xtr;
         PrimalSums<R>::kadd(acc.se, acc.ce, de * de);
     }
     return xtn;
+}
+template <typename R>
+__device__ __forceinline__ R primal_pixel(const PrimalArgs<R> &P, int64_t e, R g, PrimalSums<R> &acc) {
+    return primal_pixel(P, e, g, primal_load(P, e), acc);
 }
 
 template <typename R> PrimalArgs<R> primal_args(ppd_ctx *c);

@@ -224,15 +224,17 @@ __device__ cplx_t<R> *fft_any(cplx_t<R> *a, cplx_t<R> *b, int nseq, const FftPla
 // ------------------------------------------------------------ pass geometry
 // rows per CTA in a row pass of the power-of-two core: enough butterflies for 256 threads
 template <typename R> __host__ __device__ constexpr int rows_per_cta(int K) { return 1024 / K > 0 ? 1024 / K : 1; }
-// columns per CTA in a column pass of the power-of-two core.  K <= 2048:
-// the strips are read from L2 (grid and row-pass output of these sizes stay
-// cached between the passes), so the fewest columns the 256-thread
-// butterfly split allows (1024 / K, at least 1) give the most CTAs for these
-// latency-bound passes.  Larger K: at least 32 contiguous bytes per grid row
-// (one DRAM sector: 4 float / 2 double columns), at most 128 KB of strip.
+// columns per CTA in a column pass of the power-of-two core.  K <= 1024:
+// the fewest columns the 256-thread butterfly split allows (1024 / K, at
+// least 1), the most CTAs for these latency-bound passes (measured: four
+// columns per CTA at K = 1024 made both column passes 40 % slower).  From
+// K = 2048 on, every row of a strip is at least one 32-byte sector (4 float /
+// 2 double columns; measured at K = 2048: forward pass 41 -> 31 us); beyond
+// that, 32 KB of strip, at most 128 KB.
 template <typename R> __host__ __device__ constexpr int cols_per_cta(int K) {
     constexpr int csz = 2 * (int)sizeof(R);
-    if (K <= 2048) return 1024 / K > 1 ? 1024 / K : 1;
+    if (K <= 1024) return 1024 / K > 1 ? 1024 / K : 1;
+    if (K == 2048) return 32 / csz;
     const int w32 = (32 * 1024) / (K * csz), wmin = 32 / csz;
     int w = w32 > wmin ? w32 : wmin;
     while (w > 1 && (long long)w * K * csz > 128 * 1024) w /= 2;
@@ -360,6 +362,7 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(const R *__restrict__ x, cplx_t
     C *buf = reinterpret_cast<C *>(smem_raw);
     C *buf2 = buf + B * K;
     const C *tws = KT ? stage_twiddles<R, BT, KT ? KT : 1>(buf, tw) : tw;
+    pdl_enter();   // the twiddles are static: staged while the previous kernel drains
     if constexpr (KT != 0) {   // two rows per sequence
         const int row0 = blockIdx.x * 2 * BT;
         for (int e = threadIdx.x; e < BT * KT; e += NT) {
@@ -404,6 +407,7 @@ __global__ void __launch_bounds__(NT) k_cols_fwd(const cplx_t<R> *__restrict__ t
     C *buf = reinterpret_cast<C *>(smem_raw);
     C *buf2 = buf + W * K;
     const C *tws = KT ? stage_twiddles<R, WT, KT ? KT : 1>(buf, tw) : tw;
+    pdl_enter();
     const int c0 = strips[blockIdx.x];
     // one pass over the padded strip: position p holds image row p + L0/2
     // (p < L0/2) or p - K + L0/2 (p >= K - L0/2), zero in between
@@ -433,6 +437,7 @@ __global__ void __launch_bounds__(NT) k_cols_inv(const cplx_t<R> *__restrict__ g
     C *buf = reinterpret_cast<C *>(smem_raw);
     C *buf2 = buf + W * K;
     const C *tws = KT ? stage_twiddles<R, WT, KT ? KT : 1>(buf, tw) : tw;
+    pdl_enter();
     const int c0 = strips[blockIdx.x];
     for (int e = threadIdx.x; e < W * K; e += NT) {
         const int r = e / W, s = e - r * W;   // r: stored (centred) row; natural frequency (r + K/2) mod K
@@ -466,6 +471,7 @@ __global__ void __launch_bounds__(NT) k_cols_inv_part(const cplx_t<R> *__restric
     C *buf = reinterpret_cast<C *>(smem_raw);
     C *buf2 = buf + W * K;
     const C *tws = KT ? stage_twiddles<R, WT, KT ? KT : 1>(buf, tw) : tw;
+    pdl_enter();
     const int c0 = strips[blockIdx.x];
     for (int e = threadIdx.x; e < W * K; e += NT) {
         const int r = e / W, s = e - r * W;   // r: stored (centred) row
@@ -511,6 +517,7 @@ __global__ void __launch_bounds__(NT) k_rows_inv(const cplx_t<R> *__restrict__ t
     C *buf = reinterpret_cast<C *>(smem_raw);
     C *buf2 = buf + B * K;
     const C *tws = KT ? stage_twiddles<R, BT, KT ? KT : 1>(buf, tw) : tw;
+    pdl_enter();
     if constexpr (KT != 0) {   // two rows per sequence
         const int row0 = blockIdx.x * 2 * BT;
         load_two_real_inverse<R, KT ? KT : 1, BT>(tmp, row0, L0, buf);
@@ -556,6 +563,7 @@ __global__ void __launch_bounds__(NT) k_rows_primal(const cplx_t<R> *__restrict_
     C *buf = reinterpret_cast<C *>(smem_raw);
     C *buf2 = buf + B * K;
     const C *tws = KT ? stage_twiddles<R, BT, KT ? KT : 1>(buf, tw) : tw;
+    pdl_enter();
     PrimalSums<R> acc;
     if constexpr (KT != 0) {
         // two rows per sequence (rows row0 + 2s and row0 + 2s + 1)
@@ -563,6 +571,19 @@ __global__ void __launch_bounds__(NT) k_rows_primal(const cplx_t<R> *__restrict_
         static_assert(BT * LT % NT == 0, "pixel pairs per thread");
         const int row0 = blockIdx.x * 2 * BT;
         load_two_real_inverse<R, KK, BT>(tmp_inv, row0, L0, buf);
+        // the primal step's pixel inputs, in flight during the inverse FFT
+        // (up to K = 1024; longer rows keep them for later: at K = 2048 the
+        // registers cost more than the overlap gains, 43 -> 49 us measured)
+        constexpr bool PRE = KK <= 1024;
+        PrimalIn<R> ina[PER], inb[PER];
+        if constexpr (PRE) {
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                const int e = threadIdx.x + k * NT, s = e / LT, n1 = e % LT, ra = row0 + 2 * s, rb = ra + 1;
+                if (ra < L0) ina[k] = primal_load(P, (int64_t)ra * LT + n1);
+                if (rb < L0) inb[k] = primal_load(P, (int64_t)rb * LT + n1);
+            }
+        }
         __syncthreads();
         fft_smem<R, KK, BT, false>(buf, tws);
         // the new xt of both rows stays in registers while the buffer is rewritten
@@ -572,8 +593,9 @@ __global__ void __launch_bounds__(NT) k_rows_primal(const cplx_t<R> *__restrict_
             const int e = threadIdx.x + k * NT, s = e / LT, n1 = e % LT, ra = row0 + 2 * s, rb = ra + 1;
             const C v = buf[s * KK + ((n1 - LT / 2 + KK) & (KK - 1))];
             xa[k] = xb[k] = R(0);
-            if (ra < L0) xa[k] = primal_pixel(P, (int64_t)ra * LT + n1, s0[ra] * s1[n1] * v.x, acc);
-            if (rb < L0) xb[k] = primal_pixel(P, (int64_t)rb * LT + n1, -s0[rb] * s1[n1] * v.y, acc);
+            const int64_t ea = (int64_t)ra * LT + n1, eb = (int64_t)rb * LT + n1;
+            if (ra < L0) xa[k] = primal_pixel(P, ea, s0[ra] * s1[n1] * v.x, PRE ? ina[k] : primal_load(P, ea), acc);
+            if (rb < L0) xb[k] = primal_pixel(P, eb, -s0[rb] * s1[n1] * v.y, PRE ? inb[k] : primal_load(P, eb), acc);
         }
         __syncthreads();
         // the new rows a + i b in place, each thread also clearing the padding
@@ -656,10 +678,10 @@ template <typename R, int KT> struct RowPass {
         PPD_CHECK(smem_attr((const void *)k_rows_fwd<R, KT>, sh));
         int site;
         PPD_CHECK(launch_begin(c, "fft_fwd_rows", s, &site));
-        k_rows_fwd<R, KT><<<blocks(c), NT, sh, s>>>(x, static_cast<cplx_t<R> *>(c->fft_tmp), tw(c),
-                                                   static_cast<const R *>(c->deap0),
-                                                   static_cast<const R *>(c->deap1), c->L0, c->L1, c->col_fwd,
-                                                   args(c));
+        // mostly the first kernel of its sequence: an ordinary launch
+        launch(c, false, k_rows_fwd<R, KT>, blocks(c), NT, sh, s, x, static_cast<cplx_t<R> *>(c->fft_tmp), tw(c),
+               static_cast<const R *>(c->deap0), static_cast<const R *>(c->deap1), c->L0, c->L1,
+               (const uint8_t *)c->col_fwd, args(c));
         return launch_end(c, site, s);
     }
     static int inv(ppd_ctx *c, R *img, cudaStream_t s) {
@@ -667,9 +689,9 @@ template <typename R, int KT> struct RowPass {
         PPD_CHECK(smem_attr((const void *)k_rows_inv<R, KT>, sh));
         int site;
         PPD_CHECK(launch_begin(c, "fft_inv_rows", s, &site));
-        k_rows_inv<R, KT><<<blocks(c), NT, sh, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp_inv), img, tw(c),
-                                                   static_cast<const R *>(c->deap0),
-                                                   static_cast<const R *>(c->deap1), c->L0, c->L1, args(c));
+        launch(c, true, k_rows_inv<R, KT>, blocks(c), NT, sh, s, static_cast<const cplx_t<R> *>(c->fft_tmp_inv),
+               img, tw(c), static_cast<const R *>(c->deap0), static_cast<const R *>(c->deap1), c->L0, c->L1,
+               args(c));
         return launch_end(c, site, s);
     }
     static int primal(ppd_ctx *c, cudaStream_t s) {
@@ -678,10 +700,11 @@ template <typename R, int KT> struct RowPass {
         int site;
         PPD_CHECK(launch_begin(c, "rows_primal", s, &site));
         const unsigned n = blocks(c);
-        k_rows_primal<R, KT><<<n, NT, sh, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp_inv),
-                                               static_cast<cplx_t<R> *>(c->fft_tmp), tw(c),
-                                               static_cast<const R *>(c->deap0), static_cast<const R *>(c->deap1),
-                                               c->col_fwd, primal_args<R>(c), c->prim_part, c->L0, c->L1, args(c));
+        // it follows the join of the two branches: an ordinary launch
+        launch(c, false, k_rows_primal<R, KT>, n, NT, sh, s, static_cast<const cplx_t<R> *>(c->fft_tmp_inv),
+               static_cast<cplx_t<R> *>(c->fft_tmp), tw(c), static_cast<const R *>(c->deap0),
+               static_cast<const R *>(c->deap1), (const uint8_t *)c->col_fwd, primal_args<R>(c), c->prim_part, c->L0,
+               c->L1, args(c));
         c->n_stat_parts = (int)n;
         return launch_end(c, site, s);
     }
@@ -703,8 +726,9 @@ template <typename R, int KT> struct ColPass {
         PPD_CHECK(smem_attr((const void *)k_cols_fwd<R, KT>, sh));
         int site;
         PPD_CHECK(launch_begin(c, "fft_fwd_cols", s, &site));
-        k_cols_fwd<R, KT><<<c->n_fwd_strips, NT, sh, s>>>(static_cast<const cplx_t<R> *>(c->fft_tmp), grid, tw(c),
-                                                         c->L0, c->K1, c->fwd_strips, c->row_fwd, args(c));
+        launch(c, true, k_cols_fwd<R, KT>, (unsigned)c->n_fwd_strips, NT, sh, s,
+               static_cast<const cplx_t<R> *>(c->fft_tmp), grid, tw(c), c->L0, c->K1,
+               (const int32_t *)c->fwd_strips, (const uint8_t *)c->row_fwd, args(c));
         return launch_end(c, site, s);
     }
     static int inv(ppd_ctx *c, const cplx_t<R> *grid, cudaStream_t s) {
@@ -713,8 +737,9 @@ template <typename R, int KT> struct ColPass {
         PPD_CHECK(smem_attr((const void *)k_cols_inv<R, KT>, sh));
         int site;
         PPD_CHECK(launch_begin(c, "fft_inv_cols", s, &site));
-        k_cols_inv<R, KT><<<c->n_inv_strips, NT, sh, s>>>(grid, static_cast<cplx_t<R> *>(c->fft_tmp_inv), tw(c),
-                                                         c->L0, c->K1, c->inv_strips, c->row_inv, args(c));
+        launch(c, true, k_cols_inv<R, KT>, (unsigned)c->n_inv_strips, NT, sh, s, grid,
+               static_cast<cplx_t<R> *>(c->fft_tmp_inv), tw(c), c->L0, c->K1, (const int32_t *)c->inv_strips,
+               (const uint8_t *)c->row_inv, args(c));
         return launch_end(c, site, s);
     }
     template <int T> static int inv_part_t(ppd_ctx *c, cudaStream_t s) {
@@ -722,9 +747,10 @@ template <typename R, int KT> struct ColPass {
         PPD_CHECK(smem_attr((const void *)k_cols_inv_part<R, KT, T>, sh));
         int site;
         PPD_CHECK(launch_begin(c, "fft_inv_cols", s, &site));
-        k_cols_inv_part<R, KT, T><<<c->n_inv_strips, NT, sh, s>>>(
-            static_cast<const cplx_t<R> *>(c->gpart), c->ch.tile_first, c->ch.tile_n,
-            static_cast<cplx_t<R> *>(c->fft_tmp_inv), tw(c), c->L0, c->K1, c->inv_strips, c->row_inv, args(c));
+        launch(c, true, k_cols_inv_part<R, KT, T>, (unsigned)c->n_inv_strips, NT, sh, s,
+               static_cast<const cplx_t<R> *>(c->gpart), (const int32_t *)c->ch.tile_first,
+               (const int32_t *)c->ch.tile_n, static_cast<cplx_t<R> *>(c->fft_tmp_inv), tw(c), c->L0, c->K1,
+               (const int32_t *)c->inv_strips, (const uint8_t *)c->row_inv, args(c));
         return launch_end(c, site, s);
     }
     static int inv_part(ppd_ctx *c, cudaStream_t s) {

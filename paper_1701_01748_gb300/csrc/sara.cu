@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(NT) k_sara_ana(const R *__restrict__ in, int i
     __shared__ R tin[AEXT * AEXT];
     __shared__ R rowf[AEXT * 2 * TSA];
     const int b = blockIdx.y;
+    pdl_enter();
     if (mode == 1 && pmask && !pmask[b + 1]) return;
     const int tpd1 = (n1 / 2 + TSA - 1) / TSA;
     const int R0 = (blockIdx.x / tpd1) * TSA, C0 = (blockIdx.x % tpd1) * TSA;
@@ -296,6 +297,7 @@ __global__ void __launch_bounds__(NT) k_sara_syn(const R *__restrict__ coef, con
     const int b = blockIdx.y;
     const int tpd1 = (n1 / 2 + TS - 1) / TS;
     const int R0 = (blockIdx.x / tpd1) * TS, C0 = (blockIdx.x % tpd1) * TS;
+    pdl_enter();
     SynVals<R> q;
     syn_load(q, coef + (int64_t)(b + 1) * N, wgt ? wgt + (int64_t)(b + 1) * N : nullptr,
              sll + (int64_t)b * sll_bstride, from_coef, L1, n0 >> 1, n1 >> 1, R0, C0, 2 * b + 2);
@@ -320,6 +322,7 @@ __global__ void __launch_bounds__(NT) k_sara_syn0(const R *__restrict__ coef, co
     const int tpd1 = (L1 / 2 + TS - 1) / TS;
     const int R0 = (blockIdx.x / tpd1) * TS, C0 = (blockIdx.x % tpd1) * TS;
     const int h0 = L0 >> 1, h1 = L1 >> 1;
+    pdl_enter();
     auto load = [&](SynVals<R> &q, int b) {
         syn_load(q, coef + (int64_t)(b + 1) * N, wgt ? wgt + (int64_t)(b + 1) * N : nullptr,
                  sll + (int64_t)b * sll_bstride, from_coef, L1, h0, h1, R0, C0, 2 * b + 2);
@@ -366,8 +369,9 @@ template <typename R> int analysis_all(ppd_ctx *c, const R *x, R *coef, int mode
         const int pitch = l == 0 ? L1 : n1;
         const int64_t bstride = l == 0 ? 0 : ll_stride;
         PPD_CHECK(launch_begin(c, "sara_analysis", s, &site));
-        k_sara_ana<R><<<dim3(tiles(n0 / 2, n1 / 2, TSA), N_WAVELETS), NT, 0, s>>>(
-            in, pitch, bstride, n0, n1, ll[l & 1], ll_stride, last, coef, wgt, L1, N, mode, alpha, pmask);
+        // level 0 starts its sequence (in the iteration: after the fork)
+        launch(c, l > 0, k_sara_ana<R>, dim3(tiles(n0 / 2, n1 / 2, TSA), N_WAVELETS), NT, 0, s, in, pitch, bstride,
+               n0, n1, ll[l & 1], ll_stride, (int)last, coef, wgt, L1, N, mode, alpha, pmask);
         PPD_CHECK(launch_end(c, site, s));
     }
     return PPD_OK;
@@ -387,8 +391,8 @@ int synthesis_levels(ppd_ctx *c, const R *coef, const R *wgt, const R **ll0, cud
         const int n0 = L0 >> l, n1 = L1 >> l;
         const bool coarsest = (l == c->levels - 1);
         PPD_CHECK(launch_begin(c, "sara_synthesis", s, &site));
-        k_sara_syn<R><<<dim3(tiles(n0 / 2, n1 / 2, TS), N_WAVELETS), NT, 0, s>>>(
-            coef, wgt, L1, N, coarsest ? coef : prev, coarsest ? 1 : 0, st, n0, n1, buf[k & 1], st);
+        launch(c, true, k_sara_syn<R>, dim3(tiles(n0 / 2, n1 / 2, TS), N_WAVELETS), NT, 0, s, coef, wgt, L1, N,
+               coarsest ? coef : prev, coarsest ? 1 : 0, st, n0, n1, buf[k & 1], st);
         PPD_CHECK(launch_end(c, site, s));
         prev = buf[k & 1];
     }
@@ -404,8 +408,8 @@ int synthesis_final(ppd_ctx *c, const R *coef, const R *wgt, const R *ll0, const
     const bool from_coef = ll0 == nullptr;   // levels == 1: LL' straight from the coefficients
     int site;
     PPD_CHECK(launch_begin(c, "sara_synthesis", s, &site));
-    k_sara_syn0<R><<<tiles(L0 / 2, L1 / 2, TS), NT, 0, s>>>(coef, wgt, L0, L1, c->N, from_coef ? coef : ll0,
-                                                           from_coef ? 1 : 0, st, dirac, scale, out);
+    launch(c, true, k_sara_syn0<R>, tiles(L0 / 2, L1 / 2, TS), NT, 0, s, coef, wgt, L0, L1, c->N,
+           from_coef ? coef : ll0, from_coef ? 1 : 0, st, dirac, scale, out);
     return launch_end(c, site, s);
 }
 

@@ -105,6 +105,7 @@ template <typename R> struct VisArgs {
     const R *theta_v;
     R theta_s;
     const int32_t *ch_start, *ch_count, *ch_tile, *ch_block;
+    const int32_t *ch_order;   // chunks by decreasing size: the gridding's CTA order
     // work units of the degridding and sub-iteration kernels: runs of at
     // most DG_NT visibilities of one chunk, each with its partial slot
     const int32_t *u_start, *u_count, *u_chunk, *u_order;
@@ -290,6 +291,7 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
         mbar_init(&bar[1], 1);
     }
     __syncthreads();
+    pdl_enter();   // the grid, v and p come from the kernels before
     auto origin = [&](int u, int &row0, int &col0) {
         const int tl = A.ch_tile[A.u_chunk[u]];
         row0 = (tl / A.ntile1) * T;
@@ -433,6 +435,7 @@ __global__ void __launch_bounds__(DG_NT) k_subiter(VisArgs<R> A, int only_first,
     using C = cplx_t<R>;
     const int u = blockIdx.x;   // one work unit (at most DG_NT visibilities)
     const int start = A.u_start[u], count = A.u_count[u], blk = A.ch_block[A.u_chunk[u]];
+    pdl_enter();
     const bool act = !A.bmask || A.bmask[blk];
     const bool first_blk = A.seen && !A.seen[blk];
     if (!act || (only_first && !first_blk)) {
@@ -546,21 +549,22 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
     C *priv = reinterpret_cast<C *>(smem_raw);                          // NW * E * P
     C *sa_all = priv + NW * E * P;                                      // NW x 4 x SP pairs (w0[a] Theta v, w0[a+4] Theta v)
     R *sb_all = reinterpret_cast<R *>(sa_all + NW * SW);                // NW x 8 x SP: w1[b]
-    int *slb_all = reinterpret_cast<int *>(sb_all + NW * KB_J * SP);    // NW x 32
 
-    const int ch = blockIdx.x;
+    // largest chunks first, so that the last wave holds the small ones
+    const int ch = A.ch_order[blockIdx.x];
     const int start = A.ch_start[ch], count = A.ch_count[ch], tl = A.ch_tile[ch];
     const int row0 = (tl / A.ntile1) * T, col0 = (tl % A.ntile1) * T;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // a block outside the active set D keeps v_j, so its chunks' partial
-    // tiles from the last gridding still hold G^dagger Theta^dagger v_j
     const int blk = A.ch_block[ch];
-    const bool act = MODE != GR_DUAL || !A.bmask || A.bmask[blk];
-    if (!act && !(A.regrid && *A.regrid)) return;
     // warps that scatter: at least GRID_MINV visibilities each, so that a
     // small chunk clears and sums only as many private tiles as it fills
     const int nwu = min(NW, max(1, (count + GRID_MINV - 1) / GRID_MINV));
     for (int e = threadIdx.x; e < nwu * E * P; e += NT) priv[e] = C{0, 0};
+    pdl_enter();
+    // a block outside the active set D keeps v_j, so its chunks' partial
+    // tiles from the last gridding still hold G^dagger Theta^dagger v_j
+    const bool act = MODE != GR_DUAL || !A.bmask || A.bmask[blk];
+    if (!act && !(A.regrid && *A.regrid)) return;
     R c = 0;
     // Algorithm 2 stopped early (stopping test): the prox output is the p
     // the stopping step kept, not P_B of the current w
@@ -620,15 +624,38 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
     // wait for one another inside the loop.
     C *sa = sa_all + warp * SW;
     R *sb = sb_all + warp * KB_J * SP;
-    int *slb = slb_all + warp * 32;
     const int seg = (count + nwu - 1) / nwu;
     const int v0 = warp < nwu ? min(count, warp * seg) : count, v1 = min(count, v0 + seg);
     In cur;
     if (v0 + lane < v1) load_in(start + v0 + lane, cur);
-    int run = -1;
+    int run = -1;   // base cell (packed local row | col << 16) of the run being accumulated
     C acc0{0, 0}, acc1{0, 0};
+    auto fetch = [&](int i, C &pa, C &pb, R &wb) {   // w0[a0] Theta v, w0[a0+4] Theta v, w1[bcol]
+        if constexpr (sizeof(R) == 4) {
+            const float4 q = *reinterpret_cast<const float4 *>(sa + 2 * (a0 * SP + i));
+            pa = C{q.x, q.y};
+            pb = C{q.z, q.w};
+        } else {
+            pa = sa[2 * (a0 * SP + i)];
+            pb = sa[2 * (a0 * SP + i) + 1];
+        }
+        wb = sb[bcol * SP + i];
+    };
+    auto accumulate = [&](const C &pa, const C &pb, R wb) {
+        acc0.x += wb * pa.x;
+        acc0.y += wb * pa.y;
+        acc1.x += wb * pb.x;
+        acc1.y += wb * pb.y;
+    };
+    auto flush = [&]() {   // add the run's two cells of this lane into the private tile
+        C *cell = mine + ((run & 0xffff) + a0) * P + (run >> 16) + bcol;
+        const C g0 = cell[0], g1 = cell[4 * P];
+        cell[0] = cadd(g0, acc0);
+        cell[4 * P] = cadd(g1, acc1);
+    };
     for (int base = v0; base < v1; base += 32) {
         const int n = min(32, v1 - base);
+        int mylb = -1;
         if (lane < n) {
             const int gi = start + base + lane;
             const VisRec<R> rc = cur.rc;
@@ -669,69 +696,46 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
             }
 #pragma unroll
             for (int j = 0; j < KB_J; ++j) sb[j * SP + lane] = w1[j];
-            const int lb0 = (rc.packed & 0xffff) - row0, lb1 = ((rc.packed >> 16) & 0xffff) - col0;
-            slb[lane] = lb0 | (lb1 << 16);
+            mylb = ((rc.packed & 0xffff) - row0) | ((((rc.packed >> 16) & 0xffff) - col0) << 16);
         }
+        // the visibilities of the round that start a new run (the order is
+        // sorted by base cell): lane 0 compares with the run carried over
+        const int prev = __shfl_up_sync(0xffffffffu, mylb, 1);
+        unsigned starts = __ballot_sync(0xffffffffu, lane < n && mylb != (lane == 0 ? run : prev));
         __syncwarp();
         if (base + 32 + lane < v1) load_in(start + base + 32 + lane, cur);   // next round, in flight during the scatter
-        auto fetch = [&](int i, C &pa, C &pb, R &wb) {   // w0[a0] Theta v, w0[a0+4] Theta v, w1[bcol]
-            if constexpr (sizeof(R) == 4) {
-                const float4 q = *reinterpret_cast<const float4 *>(sa + 2 * (a0 * SP + i));
-                pa = C{q.x, q.y};
-                pb = C{q.z, q.w};
-            } else {
-                pa = sa[2 * (a0 * SP + i)];
-                pb = sa[2 * (a0 * SP + i) + 1];
-            }
-            wb = sb[bcol * SP + i];
-        };
-        auto accumulate = [&](const C &pa, const C &pb, R wb) {
-            acc0.x += wb * pa.x;
-            acc0.y += wb * pa.y;
-            acc1.x += wb * pb.x;
-            acc1.y += wb * pb.y;
-        };
+        // the warp walks the round run by run (uniform control flow): at a
+        // run start the finished run is added to the tile, inside a run the
+        // footprints accumulate in registers, four at a time
         int i = 0;
         while (i < n) {
-            // four visibilities of the current run (the order is sorted by
-            // base cell, so equal ends mean four equal bases): no checks,
-            // all operand loads issued together
-            if (i + 4 <= n && slb[i] == run && slb[i + 3] == run) {
+            const int e = starts ? __ffs(starts) - 1 : n;
+            if (e == i) {
+                if (run >= 0) flush();
+                run = __shfl_sync(0xffffffffu, mylb, i);
+                acc0 = C{0, 0};
+                acc1 = C{0, 0};
+                starts &= starts - 1;
+                continue;
+            }
+            for (; i + 4 <= e; i += 4) {
                 C pa[4], pb[4];
                 R wb[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) fetch(i + q, pa[q], pb[q], wb[q]);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) accumulate(pa[q], pb[q], wb[q]);
-                i += 4;
-                continue;
             }
-            const int lb = slb[i];
-            C pa, pb;
-            R wb;
-            fetch(i, pa, pb, wb);
-            if (lb != run) {
-                if (run >= 0) {
-                    C *cell = mine + ((run & 0xffff) + a0) * P + (run >> 16) + bcol;
-                    C g0 = cell[0], g1 = cell[4 * P];
-                    cell[0] = cadd(g0, acc0);
-                    cell[4 * P] = cadd(g1, acc1);
-                }
-                run = lb;
-                acc0 = C{0, 0};
-                acc1 = C{0, 0};
+            for (; i < e; ++i) {
+                C pa, pb;
+                R wb;
+                fetch(i, pa, pb, wb);
+                accumulate(pa, pb, wb);
             }
-            accumulate(pa, pb, wb);
-            ++i;
         }
         __syncwarp();   // the staging is rewritten by the next round
     }
-    if (run >= 0) {
-        C *cell = mine + ((run & 0xffff) + a0) * P + (run >> 16) + bcol;
-        C g0 = cell[0], g1 = cell[4 * P];
-        cell[0] = cadd(g0, acc0);
-        cell[4 * P] = cadd(g1, acc1);
-    }
+    if (run >= 0) flush();
     __syncthreads();
     C *out = gpart + (int64_t)ch * E * E;
     for (int e = threadIdx.x; e < E * E; e += NT) {
@@ -769,6 +773,7 @@ __global__ void __launch_bounds__(256) k_combine(const cplx_t<R> *__restrict__ g
         n_s[threadIdx.x] = tile_n[tt];
     }
     __syncthreads();
+    pdl_enter();
     for (int e = part * (T * T / PARTS) + threadIdx.x; e < (part + 1) * (T * T / PARTS); e += 256) {
         const int lr = e / T, lc = e % T;
         C acc{0, 0};
@@ -796,6 +801,7 @@ template <typename R> VisArgs<R> make_args(ppd_ctx *c) {
     A.ch_count = c->ch.count;
     A.ch_tile = c->ch.tile;
     A.ch_block = c->ch.block;
+    A.ch_order = c->ch.order;
     A.K0 = c->K0;
     A.K1 = c->K1;
     A.ntile1 = c->K1 / c->T;
@@ -834,7 +840,7 @@ template <typename R> VisArgs<R> make_args(ppd_ctx *c) {
 template <typename R, int T> size_t grid_smem() {
     constexpr int NW = GridCfg<R>::NWARP, E = T + HALO, P = E, SP = 33;
     return (size_t)NW * E * P * sizeof(cplx_t<R>) + (size_t)NW * 8 * SP * sizeof(cplx_t<R>) +
-           (size_t)NW * KB_J * SP * sizeof(R) + NW * 32 * sizeof(int);
+           (size_t)NW * KB_J * SP * sizeof(R);
 }
 
 template <typename R, int T>
@@ -860,9 +866,8 @@ int degrid_t(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const 
     int site;
     PPD_CHECK(launch_begin(c, mode == DG_OP ? "degrid_op" : "degrid_dual", s, &site));
     const long long sf = c->wait_first;
-    if (mode == DG_OP) k_degrid<R, T, DG_OP><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A, nch, sf);
-    else if (mode == DG_DUAL) k_degrid<R, T, DG_DUAL><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A, nch, sf);
-    else k_degrid<R, T, DG_FIRST><<<nb, DG_NT, sh, s>>>(c->tmap_a, use_tma, grid, A, nch, sf);
+    auto k = mode == DG_OP ? k_degrid<R, T, DG_OP> : mode == DG_DUAL ? k_degrid<R, T, DG_DUAL> : k_degrid<R, T, DG_FIRST>;
+    launch(c, true, k, nb, DG_NT, sh, s, c->tmap_a, use_tma, grid, A, nch, sf);
     return launch_end(c, site, s);
 }
 
@@ -882,15 +887,15 @@ int grid_t(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_
     if (c->ch.n > 0) {
         PPD_CHECK(launch_begin(c, mode == GR_DUAL ? "grid_dual" : "grid_op", s, &site));
         const unsigned nb = (unsigned)c->ch.n;
-        if (mode == GR_OP) k_grid<R, T, GR_OP><<<nb, NT, sh, s>>>(A, gp);
-        else if (mode == GR_OP_U) k_grid<R, T, GR_OP_U><<<nb, NT, sh, s>>>(A, gp);
-        else k_grid<R, T, GR_DUAL><<<nb, NT, sh, s>>>(A, gp);
+        auto k = mode == GR_OP ? k_grid<R, T, GR_OP> : mode == GR_OP_U ? k_grid<R, T, GR_OP_U> : k_grid<R, T, GR_DUAL>;
+        launch(c, true, k, nb, NT, sh, s, A, gp);
         PPD_CHECK(launch_end(c, site, s));
     }
     if (c->ch.n_active == 0 || !combine) return PPD_OK;
     PPD_CHECK(launch_begin(c, "grid_combine", s, &site));
-    k_combine<R, T><<<(unsigned)c->ch.n_active * 4, 256, 0, s>>>(gp, c->ch.tile_first, c->ch.tile_n, c->ch.active,
-                                                            c->K1, c->K0 / T, c->K1 / T, grid);
+    launch(c, true, k_combine<R, T>, (unsigned)c->ch.n_active * 4, 256, 0, s, (const cplx_t<R> *)gp,
+           (const int32_t *)c->ch.tile_first, (const int32_t *)c->ch.tile_n, (const int32_t *)c->ch.active, c->K1,
+           c->K0 / T, c->K1 / T, grid);
     return launch_end(c, site, s);
 }
 
@@ -971,7 +976,7 @@ template <typename R> int subiter(ppd_ctx *c, cudaStream_t s, int only_first, do
     if (c->ch.nu == 0) return PPD_OK;
     int site;
     PPD_CHECK(launch_begin(c, "subiter", s, &site));
-    k_subiter<R><<<(unsigned)c->ch.nu, DG_NT, 0, s>>>(make_args<R>(c), only_first, (R)beta, write_p);
+    launch(c, true, k_subiter<R>, (unsigned)c->ch.nu, DG_NT, 0, s, make_args<R>(c), only_first, (R)beta, write_p);
     return launch_end(c, site, s);
 }
 
