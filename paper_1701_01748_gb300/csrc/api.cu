@@ -282,16 +282,10 @@ template <typename R> int iteration_body(ppd_ctx *c, cudaStream_t s, bool first)
     c->part_out = bank[0];
     c->next_step = c->cfg.n_itr;
     c->next_test_in = c->cfg.n_itr >= 2;
-    // small grids: the inverse column pass sums the partial tiles itself (no
-    // combined grid in memory); from K = 4096 on, a combine pass with one CTA
-    // group per tile reads them contiguously and the column pass reads the grid
-    if (c->K0 >= 4096) {
-        PPD_CHECK(grid_vis<R>(c, GR_DUAL, nullptr, nullptr, gv, s, /*combine=*/true));
-        PPD_CHECK(fft_inverse_cols<R>(c, gv, s));
-    } else {
-        PPD_CHECK(grid_vis<R>(c, GR_DUAL, nullptr, nullptr, gv, s, /*combine=*/false));
-        PPD_CHECK(fft_inverse_cols_partials<R>(c, s));
-    }
+    // the combine pass sums the partial tiles into the column-major grid,
+    // which the inverse column pass reads in whole columns
+    PPD_CHECK(grid_vis<R>(c, GR_DUAL, nullptr, nullptr, gv, s));
+    PPD_CHECK(fft_inverse_cols<R>(c, gv, s));
     if (fused_rows(c)) {
         if (fork) PPD_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
         // inverse row pass, primal step and the next iteration's forward row pass
@@ -693,6 +687,8 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
         return fail(PPD_ERR_INVALID_ARG, "ppd_create: unknown norm_method");
     if (k.tile != 0 && k.tile != 16 && k.tile != 32) return fail(PPD_ERR_INVALID_ARG, "ppd_create: tile must be 16 or 32");
     if (k.chunk < 0) return fail(PPD_ERR_INVALID_ARG, "ppd_create: chunk must be >= 0");
+    if (!(k.grid_warps == 0 || k.grid_warps == 4 || (k.grid_warps == 8 && k.precision == PPD_FP32_FP64NORMS)))
+        return fail(PPD_ERR_INVALID_ARG, "ppd_create: grid_warps must be 0, 4 or (FP32) 8");
     if (k.launch_overlap != 0 && k.launch_overlap != 1)
         return fail(PPD_ERR_INVALID_ARG, "ppd_create: launch_overlap must be 0 or 1");
     if (!(k.inner_tol >= 0) || !(k.stop_tol >= 0) || !(k.stop_eps_factor >= 0) || k.stop_every < 0 ||
@@ -714,6 +710,7 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
     c->T = k.tile ? k.tile : 16;
     if (c->K0 % c->T || c->K1 % c->T) c->T = 16;
     c->C = k.chunk ? k.chunk : 1024;
+    c->grid_nw = k.grid_warps ? k.grid_warps : (c->is_f32 ? 8 : 4);
     c->beta = k.kb_beta > 0 ? k.kb_beta : 2.34 * KB_J;
     c->tau = k.tau;
     c->kappa = k.kappa;
@@ -1270,6 +1267,7 @@ int ppd_get_params(ppd_ctx *c, ppd_params *o) {
     o->K1 = c->K1;
     o->tile = c->T;
     o->chunk = c->C;
+    o->grid_warps = c->grid_nw;
     o->n_chunks = c->ch.n;
     o->M = c->M;
     o->psiw_norm_sq = c->psiw2;
@@ -1443,9 +1441,10 @@ int ppd_autotune(ppd_ctx *c, int32_t iters, int32_t *tile_out, int32_t *chunk_ou
     const bool hth = c->has_theta, hU = c->has_U, hep = c->has_eps;
     const bool timing = c->timing;
     c->timing = false;
-    auto rebuild = [&](int T, int C) {
+    auto rebuild = [&](int T, int C, int NW) {
         c->T = T;
         c->C = C;
+        c->grid_nw = NW;
         int st = ppd_set_visibilities(c, c->M, uv.data(), y.data(), blk.data());
         if (st == PPD_OK) st = ppd_set_weights(c, hth ? th.data() : nullptr, hU ? U.data() : nullptr,
                                                hep ? ep.data() : nullptr);
@@ -1455,29 +1454,34 @@ int ppd_autotune(ppd_ctx *c, int32_t iters, int32_t *tile_out, int32_t *chunk_ou
     PPD_CUDA(cudaEventCreate(&e0));
     PPD_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    int bt = c->T, bc = c->C, st = PPD_OK;
+    int bt = c->T, bc = c->C, bw = c->grid_nw, st = PPD_OK;
+    const std::vector<int> warps = c->is_f32 ? std::vector<int>{8, 4} : std::vector<int>{4};
     for (int T : {16, 32}) {
         if (c->K0 % T || c->K1 % T || c->K0 < 2 * T || c->K1 < 2 * T) continue;
         for (int C : {512, 1024, 2048}) {
-            if ((st = rebuild(T, C))) break;
-            if ((st = ppd_iterate(c, 3, nullptr))) break;
-            cudaEventRecord(e0, c->stream);
-            if ((st = ppd_iterate(c, iters, nullptr))) break;
-            cudaEventRecord(e1, c->stream);
-            cudaEventSynchronize(e1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) {
-                best = ms;
-                bt = T;
-                bc = C;
+            for (int NW : warps) {
+                if ((st = rebuild(T, C, NW))) break;
+                if ((st = ppd_iterate(c, 3, nullptr))) break;
+                cudaEventRecord(e0, c->stream);
+                if ((st = ppd_iterate(c, iters, nullptr))) break;
+                cudaEventRecord(e1, c->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) {
+                    best = ms;
+                    bt = T;
+                    bc = C;
+                    bw = NW;
+                }
             }
+            if (st) break;
         }
         if (st) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (st == PPD_OK) st = rebuild(bt, bc);
+    if (st == PPD_OK) st = rebuild(bt, bc, bw);
     c->cfg.eta = eta_cfg;
     c->timing = timing;
     if (st) return st;

@@ -3,9 +3,13 @@
 // Layout of the solver state in HBM (one context, one GPU):
 //   image side   x, xt, g (= Phi^dagger v), ut (= Psi u): n0*n1 reals each
 //                u: the 9 SARA dual images, basis-major, 9*n0*n1 reals
-//                grid_a (forward FFT output) and grid_v (gridding output):
-//                K0*K1 complex each, row-major, zero frequency at the centre
-//                (plain grid index k stored at (k + K/2) mod K)
+//                grid_a (forward FFT output, row-major: the degridding reads
+//                its rows by TMA) and grid_v (gridding output, column-major:
+//                the inverse column pass reads whole columns): K0*K1 complex
+//                each, zero frequency at the centre (plain grid index k
+//                stored at (k + K/2) mod K); the FFT temporaries: the forward
+//                row pass output column-major (L0 per column), the inverse
+//                column pass output row-major (K1 per row)
 //   visibility   sorted by (tile, block, centred base row, centred base col,
 //   side         caller index); per visibility a 16 B (float) / 32 B (double)
 //                record {packed centred base cell, frac0, frac1, U} and the
@@ -157,6 +161,7 @@ struct ppd_ctx {
     int is_f32 = 1;
     size_t rsz = 4;            // sizeof(real)
     int L0 = 0, L1 = 0, K0 = 0, K1 = 0, T = 32, C = 1024, levels = 4, d = 1;
+    int grid_nw = 8;           // warps per gridding CTA (FP32: 4 or 8; FP64: 4)
     int64_t N = 0;
     double beta = 0;
     cudaStream_t stream = nullptr;
@@ -446,7 +451,6 @@ inline bool fused_rows(const ppd_ctx *c) { return c->K1 <= 2048; }
 template <typename R> int rows_primal(ppd_ctx *c, cudaStream_t s);
 template <typename R> int fft_forward_rows(ppd_ctx *c, const R *x, cudaStream_t s);
 template <typename R> int fft_forward_cols(ppd_ctx *c, cplx_t<R> *grid, cudaStream_t s);
-template <typename R> int fft_inverse_cols_partials(ppd_ctx *c, cudaStream_t s);
 template <typename R> int fft_inverse_cols(ppd_ctx *c, const cplx_t<R> *grid, cudaStream_t s);
 int reduce_primal_stats(ppd_ctx *c, cudaStream_t s);
 // stop_flag = (sqrt(stat_out[0] / stat_out[1]) < tol && every sqrt(resid2_j) <= fac eps_j)

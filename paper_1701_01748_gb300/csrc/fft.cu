@@ -332,7 +332,8 @@ __device__ __forceinline__ void load_two_real_inverse(const cplx_t<R> *__restric
 }
 
 // Writes the spectra of rows (row0 + 2s, row0 + 2s + 1) from the FFT of
-// a + i b in buf (natural order) to tmp (stored centred, marked columns).
+// a + i b in buf (natural order) to the column-major tmp (column c at
+// c L0, stored centred, marked columns): the two rows are adjacent there.
 template <typename R, int K, int NSEQ>
 __device__ __forceinline__ void store_two_real_forward(const cplx_t<R> *out, int row0, int L0,
                                                        const uint8_t *__restrict__ colmask,
@@ -340,16 +341,22 @@ __device__ __forceinline__ void store_two_real_forward(const cplx_t<R> *out, int
     using C = cplx_t<R>;
     for (int e = threadIdx.x; e < NSEQ * K; e += NT) {
         const int s = e / K, c = e % K, ra = row0 + 2 * s, rb = ra + 1;
-        if (!colmask[c]) continue;
+        if (!colmask[c] || ra >= L0) continue;
         const int kk = (c + K / 2) & (K - 1), kr = (K - kk) & (K - 1);
         C A, B;
         split_two_real(out[s * K + kk], out[s * K + kr], A, B);
-        if (ra < L0) tmp[(int64_t)ra * K + c] = A;
-        if (rb < L0) tmp[(int64_t)rb * K + c] = B;
+        C *dst = tmp + (int64_t)c * L0 + ra;   // ra and L0 even: rb < L0, 16-byte aligned pair
+        if constexpr (sizeof(R) == 4) {
+            *reinterpret_cast<float4 *>(dst) = make_float4(A.x, A.y, B.x, B.y);
+        } else {
+            dst[0] = A;
+            dst[1] = B;
+        }
     }
 }
 
-// forward row pass: tmp[n0][c] = FFT_axis1(Z x)[n0][(c + K1/2) mod K1]
+// forward row pass: tmp[n0][c] = FFT_axis1(Z x)[n0][(c + K1/2) mod K1],
+// tmp column-major (element (n0, c) at c L0 + n0) for the column pass
 template <typename R, int KT>
 __global__ void __launch_bounds__(NT) k_rows_fwd(const R *__restrict__ x, cplx_t<R> *__restrict__ tmp,
                                                  const cplx_t<R> *__restrict__ tw, const R *__restrict__ s0,
@@ -390,7 +397,7 @@ __global__ void __launch_bounds__(NT) k_rows_fwd(const R *__restrict__ x, cplx_t
     const C *out = run_fft<R, KT, BT, false>(buf, buf2, tws, B, pa.pl, tw);
     for (int e = threadIdx.x; e < B * K; e += NT) {
         const int s = e / K, c = e - s * K, n0 = row0 + s;
-        if (n0 < L0 && colmask[c]) tmp[(int64_t)n0 * K + c] = out[s * K + wrapK(c + K / 2, K)];
+        if (n0 < L0 && colmask[c]) tmp[(int64_t)c * L0 + n0] = out[s * K + wrapK(c + K / 2, K)];
     }
 }
 
@@ -410,11 +417,13 @@ __global__ void __launch_bounds__(NT) k_cols_fwd(const cplx_t<R> *__restrict__ t
     pdl_enter();
     const int c0 = strips[blockIdx.x];
     // one pass over the padded strip: position p holds image row p + L0/2
-    // (p < L0/2) or p - K + L0/2 (p >= K - L0/2), zero in between
+    // (p < L0/2) or p - K + L0/2 (p >= K - L0/2), zero in between; the
+    // column-major tmp makes consecutive threads read consecutive rows
+    (void)K1;
     for (int e = threadIdx.x; e < W * K; e += NT) {
-        const int p = e / W, s = e - p * W;
+        const int s = e / K, p = e - s * K;
         const int n0 = p < L0 / 2 ? p + L0 / 2 : (p >= K - L0 / 2 ? p - K + L0 / 2 : -1);
-        buf[e] = n0 >= 0 ? tmp[(int64_t)n0 * K1 + c0 + s] : C{0, 0};
+        buf[p * W + s] = n0 >= 0 ? tmp[(int64_t)(c0 + s) * L0 + n0] : C{0, 0};
     }
     __syncthreads();
     const C *out = run_fft<R, KT, WT, true>(buf, buf2, tws, W, pa.pl, tw);
@@ -424,7 +433,9 @@ __global__ void __launch_bounds__(NT) k_cols_fwd(const cplx_t<R> *__restrict__ t
     }
 }
 
-// inverse column pass: tmp[n0][c] = (F^H along axis 0 of grid)[(n0 - L0/2) mod K0][c]
+// inverse column pass: tmp[n0][c] = (F^H along axis 0 of grid)[(n0 - L0/2) mod K0][c],
+// the grid column-major (element (r, c) at c K0 + r, written by the combine
+// pass), so that consecutive threads read consecutive rows
 template <typename R, int KT>
 __global__ void __launch_bounds__(NT) k_cols_inv(const cplx_t<R> *__restrict__ grid, cplx_t<R> *__restrict__ tmp,
                                                  const cplx_t<R> *__restrict__ tw, int L0, int K1,
@@ -440,62 +451,8 @@ __global__ void __launch_bounds__(NT) k_cols_inv(const cplx_t<R> *__restrict__ g
     pdl_enter();
     const int c0 = strips[blockIdx.x];
     for (int e = threadIdx.x; e < W * K; e += NT) {
-        const int r = e / W, s = e - r * W;   // r: stored (centred) row; natural frequency (r + K/2) mod K
-        buf[wrapK(r + K / 2, K) * W + s] = rowmask[r] ? cconj(grid[(int64_t)r * K1 + c0 + s]) : C{0, 0};
-    }
-    __syncthreads();
-    const C *out = run_fft<R, KT, WT, true>(buf, buf2, tws, W, pa.pl, tw);
-    for (int e = threadIdx.x; e < W * L0; e += NT) {
-        const int n0 = e / W, s = e - n0 * W;
-        tmp[(int64_t)n0 * K1 + c0 + s] = cconj(out[wrapK(n0 - L0 / 2 + K, K) * W + s]);
-    }
-}
-
-// inverse column pass reading the gridding's per-chunk partial tiles
-// directly: each cell of the strip is the fixed-order sum that the combine
-// pass would write (its tile's chunks, then the halo rows/columns of the
-// tiles above, left and above-left), so the combined grid never goes to HBM.
-template <typename R, int KT, int T>
-__global__ void __launch_bounds__(NT) k_cols_inv_part(const cplx_t<R> *__restrict__ gpart,
-                                                      const int32_t *__restrict__ tile_first,
-                                                      const int32_t *__restrict__ tile_n, cplx_t<R> *__restrict__ tmp,
-                                                      const cplx_t<R> *__restrict__ tw, int L0, int K1,
-                                                      const int32_t *__restrict__ strips,
-                                                      const uint8_t *__restrict__ rowmask, PassArgs pa) {
-    using C = cplx_t<R>;
-    constexpr int WT = cols_ct<R, KT>();
-    constexpr int E = T + 8;
-    const int K = KT ? KT : pa.pl.K, W = KT ? WT : pa.nseq;
-    const int nt0 = K / T, nt1 = K1 / T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *buf = reinterpret_cast<C *>(smem_raw);
-    C *buf2 = buf + W * K;
-    const C *tws = KT ? stage_twiddles<R, WT, KT ? KT : 1>(buf, tw) : tw;
-    pdl_enter();
-    const int c0 = strips[blockIdx.x];
-    for (int e = threadIdx.x; e < W * K; e += NT) {
-        const int r = e / W, s = e - r * W;   // r: stored (centred) row
-        C acc{0, 0};
-        if (rowmask[r]) {
-            const int t0 = r / T, up = t0 == 0 ? nt0 - 1 : t0 - 1;
-            const int t1 = (c0 + s) / T, left = t1 == 0 ? nt1 - 1 : t1 - 1;
-            const int lr = r - t0 * T, lc = c0 + s - t1 * T;
-            auto add = [&](int tt0, int tt1, int rr, int cc) {
-                const int t = tt0 * nt1 + tt1;
-                const int f = tile_first[t], n = tile_n[t];
-#pragma unroll 4
-                for (int k = 0; k < n; ++k) {
-                    const C g = gpart[(int64_t)(f + k) * E * E + rr * E + cc];
-                    acc.x += g.x;
-                    acc.y += g.y;
-                }
-            };
-            add(t0, t1, lr, lc);
-            if (lr < 8) add(up, t1, lr + T, lc);
-            if (lc < 8) add(t0, left, lr, lc + T);
-            if (lr < 8 && lc < 8) add(up, left, lr + T, lc + T);
-        }
-        buf[wrapK(r + K / 2, K) * W + s] = cconj(acc);
+        const int s = e / K, r = e - s * K;   // r: stored (centred) row; natural frequency (r + K/2) mod K
+        buf[wrapK(r + K / 2, K) * W + s] = rowmask[r] ? cconj(grid[(int64_t)(c0 + s) * K + r]) : C{0, 0};
     }
     __syncthreads();
     const C *out = run_fft<R, KT, WT, true>(buf, buf2, tws, W, pa.pl, tw);
@@ -642,7 +599,7 @@ __global__ void __launch_bounds__(NT) k_rows_primal(const cplx_t<R> *__restrict_
     const C *res = run_fft<R, KT, BT, false>(buf, buf2, tws, B, pa.pl, tw);
     for (int e = threadIdx.x; e < B * K; e += NT) {
         const int s = e / K, c = e - s * K, n0 = row0 + s;
-        if (n0 < L0 && colmask[c]) tmp_fwd[(int64_t)n0 * K + c] = res[s * K + wrapK(c + K / 2, K)];
+        if (n0 < L0 && colmask[c]) tmp_fwd[(int64_t)c * L0 + n0] = res[s * K + wrapK(c + K / 2, K)];
     }
     acc.write(part + 3 * (int64_t)blockIdx.x);
 }
@@ -742,21 +699,6 @@ template <typename R, int KT> struct ColPass {
                (const uint8_t *)c->row_inv, args(c));
         return launch_end(c, site, s);
     }
-    template <int T> static int inv_part_t(ppd_ctx *c, cudaStream_t s) {
-        const int sh = (int)smem(c);
-        PPD_CHECK(smem_attr((const void *)k_cols_inv_part<R, KT, T>, sh));
-        int site;
-        PPD_CHECK(launch_begin(c, "fft_inv_cols", s, &site));
-        launch(c, true, k_cols_inv_part<R, KT, T>, (unsigned)c->n_inv_strips, NT, sh, s,
-               static_cast<const cplx_t<R> *>(c->gpart), (const int32_t *)c->ch.tile_first,
-               (const int32_t *)c->ch.tile_n, static_cast<cplx_t<R> *>(c->fft_tmp_inv), tw(c), c->L0, c->K1,
-               (const int32_t *)c->inv_strips, (const uint8_t *)c->row_inv, args(c));
-        return launch_end(c, site, s);
-    }
-    static int inv_part(ppd_ctx *c, cudaStream_t s) {
-        if (c->n_inv_strips == 0) return PPD_OK;
-        return c->T == 16 ? inv_part_t<16>(c, s) : inv_part_t<32>(c, s);
-    }
 };
 
 }  // namespace
@@ -793,12 +735,6 @@ template <typename R> int fft_inverse_cols(ppd_ctx *c, const cplx_t<R> *grid, cu
     PPD_FFT_DISPATCH(c->K0, ColPass, inv(c, grid, s))
 }
 
-// inverse column pass summing the gridding's partial tiles while loading
-// (the combine pass fused in)
-template <typename R> int fft_inverse_cols_partials(ppd_ctx *c, cudaStream_t s) {
-    PPD_FFT_DISPATCH(c->K0, ColPass, inv_part(c, s))
-}
-
 // inverse row pass into an image (second half of Z^T F^H)
 template <typename R> int fft_inverse_rows(ppd_ctx *c, R *img, cudaStream_t s) {
     PPD_FFT_DISPATCH(c->K1, RowPass, inv(c, img, s))
@@ -827,7 +763,6 @@ template <typename R> int fft_inverse(ppd_ctx *c, const cplx_t<R> *grid, R *img,
     template int fft_forward_rows<R>(ppd_ctx *, const R *, cudaStream_t);                                       \
     template int fft_forward_cols<R>(ppd_ctx *, cplx_t<R> *, cudaStream_t);                                     \
     template int fft_inverse_cols<R>(ppd_ctx *, const cplx_t<R> *, cudaStream_t);                              \
-    template int fft_inverse_cols_partials<R>(ppd_ctx *, cudaStream_t);                                         \
     template int fft_inverse_rows<R>(ppd_ctx *, R *, cudaStream_t);                                             \
     template int rows_primal<R>(ppd_ctx *, cudaStream_t);
 PPD_FFT_INST(float)

@@ -6,10 +6,14 @@
 // re-weighted scheme (Algorithm 1; W = I unless set) and the clip level
 // alpha = kappa ||Psi W||_S^2.  D_b below is the orthonormal DWT of basis b.
 //
-// The eight wavelet bases run together (grid.z = basis); every pass maps one
-// thread to one output sample and reads its filter taps through the L1/L2.
-// Filters are derived on the host by minimum-phase spectral factorisation
-// (Daubechies 1988) with a Durand-Kerner root finder.
+// The eight wavelet bases run together (grid.y = basis); the filter taps
+// sit in registers, the level tiles in shared memory.  Each filter pass
+// reads an input window once for every output that uses it: the analysis
+// forms the low (h) and high (g) half of a position together, the synthesis
+// an even and an odd output sample together (they read the same inputs with
+// the even and the odd taps).  Filters are derived on the host by
+// minimum-phase spectral factorisation (Daubechies 1988) with a
+// Durand-Kerner root finder.
 #include <cmath>
 #include <algorithm>
 #include <complex>
@@ -39,7 +43,7 @@ constexpr int TS = 8;                         // synthesis: quadrant positions p
 constexpr int AEXT = 2 * TSA + MAX_TAPS - 2;  // analysis input tile side (46)
 constexpr int SEXT = TS + MAX_TAPS / 2 - 1;   // synthesis quadrant tile side (15)
 static_assert(NT == 4 * TS * TS, "one synthesis output per thread");
-static_assert(2 * TSA % (NT / 32) == 0, "analysis column rows per warp");
+static_assert(TSA % (NT / 32) == 0 && AEXT % 2 == 0, "analysis: row pairs per warp, even tile pitch");
 
 // periodic index i mod n (i may be negative); indices inside [0, n) are
 // the common case and skip the division
@@ -116,26 +120,30 @@ __device__ __forceinline__ void ana_tile(const R *__restrict__ src, int in_pitch
         }
     }
     __syncthreads();
-    {   // rows: lane = output column q (low half, then high half)
-        for (int i = warp; i < EXT; i += NT / 32) {
-            const R *row = tin + i * AEXT + 2 * cc;
-            R acc = 0;
+    {   // rows: thread (row i, position q) forms both halves, low (h) into
+        // column q and high (g) into column TSA + q, from one pass over its F
+        // inputs, read two at a time (even offsets: 8-byte / 16-byte aligned)
+        const int q = threadIdx.x & (TSA - 1);
+        for (int i = threadIdx.x / TSA; i < EXT; i += NT / TSA) {
+            const R *row = tin + i * AEXT + 2 * q;
+            R lo = 0, hi = 0;
 #pragma unroll
-            for (int k = 0; k < F; ++k) acc += (hi1 ? f.g[k] : f.h[k]) * row[k];
-            rowf[i * 2 * TSA + lane] = acc;
+            for (int k = 0; k < F; k += 2) {
+                const auto v = *reinterpret_cast<const typename Cplx<R>::T *>(row + k);
+                lo += f.h[k] * v.x;
+                hi += f.g[k] * v.x;
+                lo += f.h[k + 1] * v.y;
+                hi += f.g[k + 1] * v.y;
+            }
+            rowf[i * 2 * TSA + q] = lo;
+            rowf[i * 2 * TSA + TSA + q] = hi;
         }
     }
     __syncthreads();
-#pragma unroll
-    for (int kq = 0; kq < NQ; ++kq) {   // columns: warp = output row
-        const int rq = warp + kq * (NT / 32);
-        const int rr = rq & (TSA - 1);
-        const bool hi0 = rq >= TSA;
-        const R *col = rowf + 2 * rr * 2 * TSA + lane;
-        R acc = 0;
-#pragma unroll
-        for (int k = 0; k < F; ++k) acc += (hi0 ? f.g[k] : f.h[k]) * col[k * 2 * TSA];
-        if (R0 + rr >= h0 || C0 + cc >= h1) continue;   // outside the quadrant
+    // columns: warp = output row rr of both halves (low h: quadrant row rr,
+    // high g: row TSA + rr), lane = column of the row-filtered tile
+    auto emit = [&](int rr, bool hi0, R acc, R u0, R w0) {
+        if (R0 + rr >= h0 || C0 + cc >= h1) return;   // outside the quadrant
         if (!hi0 && !hi1 && !last) {
             ll[(R0 + rr) * h1 + C0 + cc] = acc;
         } else {
@@ -145,10 +153,24 @@ __device__ __forceinline__ void ana_tile(const R *__restrict__ src, int in_pitch
             if (mode == 0) {
                 *dst = cv;
             } else {
-                const R u = pu[kq] + (wb ? pw[kq] * cv : cv);
+                const R u = u0 + (wb ? w0 * cv : cv);
                 *dst = fmin(fmax(u, -kappa), kappa);
             }
         }
+    };
+#pragma unroll
+    for (int kq = 0; kq < NQ / 2; ++kq) {
+        const int rr = warp + kq * (NT / 32);
+        const R *col = rowf + 2 * rr * 2 * TSA + lane;
+        R lo = 0, hi = 0;
+#pragma unroll
+        for (int k = 0; k < F; ++k) {
+            const R v = col[k * 2 * TSA];
+            lo += f.h[k] * v;
+            hi += f.g[k] * v;
+        }
+        emit(rr, false, lo, pu[kq], pw[kq]);
+        emit(rr, true, hi, pu[kq + NQ / 2], pw[kq + NQ / 2]);
     }
 }
 
@@ -165,7 +187,7 @@ __global__ void __launch_bounds__(NT) k_sara_ana(const R *__restrict__ in, int i
                                                  int n1, R *__restrict__ ll, int64_t ll_bstride, int last,
                                                  R *__restrict__ coef, const R *__restrict__ wgt, int L1, int64_t N,
                                                  int mode, R kappa, const uint8_t *__restrict__ pmask) {
-    __shared__ R tin[AEXT * AEXT];
+    __shared__ __align__(16) R tin[AEXT * AEXT];
     __shared__ R rowf[AEXT * 2 * TSA];
     const int b = blockIdx.y;
     pdl_enter();
@@ -231,55 +253,74 @@ template <typename R> __device__ __forceinline__ void syn_store(const SynVals<R>
     for (int qd = 0; qd < 4; ++qd) qs[qd * SEXT * SEXT + i * SEXT + j] = o.v[qd] * o.w[qd];
 }
 
+// Output sample of this thread in the 2TS x 2TS tile: row mm, column nnl,
+// the column parity the same for a whole warp (odd warps: odd columns), so
+// that the axis-1 pass below takes its taps as compile-time operands.
+__device__ __forceinline__ void syn_pos(int &mm, int &nnl) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    mm = (w >> 1) * 4 + (l >> 3);
+    nnl = 2 * (l & 7) + (w & 1);
+}
+static_assert(NT == 256 && TS == 8, "syn_pos covers the 16 x 16 tile with 8 warps");
+
+// Row pitch of the axis-0 results: the 4 rows x 8 columns a warp reads in
+// the axis-1 pass fall in disjoint banks.
+constexpr int TP = 24;
+
 // The two filter passes over the stored quadrant tiles (barrier first);
-// returns this thread's output (mm = tid / 2TS, nn = tid % 2TS; NT == 4 TS^2)
-// and leaves the shared tiles free for reuse.
+// returns this thread's output (position syn_pos; NT == 4 TS^2) and leaves
+// the shared tiles free for reuse.  An output pair 2p, 2p + 1 reads the same
+// F/2 inputs (quadrant row p + F/2 - 1 - kk for tap pair kk): the even
+// sample takes the even taps, the odd one the odd taps.
 template <typename R, int F>
-__device__ __forceinline__ R syn_compute(int R0, int C0, int b, const R *qs, R *tl, R *th) {
+__device__ __forceinline__ R syn_compute(int b, const R *qs, R *tl, R *th) {
     constexpr int EXT = TS + F / 2 - 1;
     const Taps<R, F> f(b);
-    const int base_r = R0 - F / 2 + 1, base_c = C0 - F / 2 + 1;
     __syncthreads();
-    for (int e = threadIdx.x; e < 2 * TS * EXT; e += NT) {   // inverse along axis 0
-        const int mm = e / EXT, j = e % EXT;
-        const int m = 2 * R0 + mm, par = mm & 1;
-        R sl0 = 0, sh0 = 0;
+    if (threadIdx.x < TS * EXT) {   // inverse along axis 0: rows 2p and 2p + 1, column j
+        const int p = threadIdx.x / EXT, j = threadIdx.x % EXT;
+        R le = 0, he = 0, lo = 0, ho = 0;
 #pragma unroll
         for (int kk = 0; kk < F / 2; ++kk) {
-            const int k = 2 * kk + par;
-            const int il = ((m - k) >> 1) - base_r;
-            const R a = par ? f.h[2 * kk + 1] : f.h[2 * kk], c = par ? f.g[2 * kk + 1] : f.g[2 * kk];
-            sl0 += a * qs[0 * SEXT * SEXT + il * SEXT + j] + c * qs[2 * SEXT * SEXT + il * SEXT + j];
-            sh0 += a * qs[1 * SEXT * SEXT + il * SEXT + j] + c * qs[3 * SEXT * SEXT + il * SEXT + j];
+            const int il = p + F / 2 - 1 - kk;
+            const R q0 = qs[0 * SEXT * SEXT + il * SEXT + j], q1 = qs[1 * SEXT * SEXT + il * SEXT + j];
+            const R q2 = qs[2 * SEXT * SEXT + il * SEXT + j], q3 = qs[3 * SEXT * SEXT + il * SEXT + j];
+            le += f.h[2 * kk] * q0 + f.g[2 * kk] * q2;
+            he += f.h[2 * kk] * q1 + f.g[2 * kk] * q3;
+            lo += f.h[2 * kk + 1] * q0 + f.g[2 * kk + 1] * q2;
+            ho += f.h[2 * kk + 1] * q1 + f.g[2 * kk + 1] * q3;
         }
-        tl[mm * SEXT + j] = sl0;
-        th[mm * SEXT + j] = sh0;
+        tl[2 * p * TP + j] = le;
+        th[2 * p * TP + j] = he;
+        tl[(2 * p + 1) * TP + j] = lo;
+        th[(2 * p + 1) * TP + j] = ho;
     }
     __syncthreads();
-    const int mm = threadIdx.x / (2 * TS), nnl = threadIdx.x % (2 * TS);   // inverse along axis 1
-    const int nn = 2 * C0 + nnl, par = nnl & 1;
+    int mm, nnl;   // inverse along axis 1
+    syn_pos(mm, nnl);
+    const R *rl = tl + mm * TP + (nnl >> 1) + F / 2 - 1, *rh = th + mm * TP + (nnl >> 1) + F / 2 - 1;
     R out = 0;
+    if (nnl & 1) {
 #pragma unroll
-    for (int kk = 0; kk < F / 2; ++kk) {
-        const int j = 2 * kk + par;
-        const int jl = ((nn - j) >> 1) - base_c;
-        const R a = par ? f.h[2 * kk + 1] : f.h[2 * kk], c = par ? f.g[2 * kk + 1] : f.g[2 * kk];
-        out += a * tl[mm * SEXT + jl] + c * th[mm * SEXT + jl];
+        for (int kk = 0; kk < F / 2; ++kk) out += f.h[2 * kk + 1] * rl[-kk] + f.g[2 * kk + 1] * rh[-kk];
+    } else {
+#pragma unroll
+        for (int kk = 0; kk < F / 2; ++kk) out += f.h[2 * kk] * rl[-kk] + f.g[2 * kk] * rh[-kk];
     }
     __syncthreads();
     return out;
 }
 
-template <typename R> __device__ __forceinline__ R syn_compute_b(int b, int R0, int C0, const R *qs, R *tl, R *th) {
+template <typename R> __device__ __forceinline__ R syn_compute_b(int b, const R *qs, R *tl, R *th) {
     switch (b) {
-        case 0: return syn_compute<R, 2>(R0, C0, b, qs, tl, th);
-        case 1: return syn_compute<R, 4>(R0, C0, b, qs, tl, th);
-        case 2: return syn_compute<R, 6>(R0, C0, b, qs, tl, th);
-        case 3: return syn_compute<R, 8>(R0, C0, b, qs, tl, th);
-        case 4: return syn_compute<R, 10>(R0, C0, b, qs, tl, th);
-        case 5: return syn_compute<R, 12>(R0, C0, b, qs, tl, th);
-        case 6: return syn_compute<R, 14>(R0, C0, b, qs, tl, th);
-        default: return syn_compute<R, 16>(R0, C0, b, qs, tl, th);
+        case 0: return syn_compute<R, 2>(b, qs, tl, th);
+        case 1: return syn_compute<R, 4>(b, qs, tl, th);
+        case 2: return syn_compute<R, 6>(b, qs, tl, th);
+        case 3: return syn_compute<R, 8>(b, qs, tl, th);
+        case 4: return syn_compute<R, 10>(b, qs, tl, th);
+        case 5: return syn_compute<R, 12>(b, qs, tl, th);
+        case 6: return syn_compute<R, 14>(b, qs, tl, th);
+        default: return syn_compute<R, 16>(b, qs, tl, th);
     }
 }
 
@@ -293,7 +334,7 @@ __global__ void __launch_bounds__(NT) k_sara_syn(const R *__restrict__ coef, con
                                                  int64_t sll_bstride, int n0, int n1, R *__restrict__ out,
                                                  int64_t out_bstride) {
     __shared__ R qs[4 * SEXT * SEXT];
-    __shared__ R tl[2 * TS * SEXT], th[2 * TS * SEXT];
+    __shared__ R tl[2 * TS * TP], th[2 * TS * TP];
     const int b = blockIdx.y;
     const int tpd1 = (n1 / 2 + TS - 1) / TS;
     const int R0 = (blockIdx.x / tpd1) * TS, C0 = (blockIdx.x % tpd1) * TS;
@@ -302,8 +343,9 @@ __global__ void __launch_bounds__(NT) k_sara_syn(const R *__restrict__ coef, con
     syn_load(q, coef + (int64_t)(b + 1) * N, wgt ? wgt + (int64_t)(b + 1) * N : nullptr,
              sll + (int64_t)b * sll_bstride, from_coef, L1, n0 >> 1, n1 >> 1, R0, C0, 2 * b + 2);
     syn_store(q, qs, 2 * b + 2);
-    const R v = syn_compute_b<R>(b, R0, C0, qs, tl, th);
-    const int mm = threadIdx.x / (2 * TS), nnl = threadIdx.x % (2 * TS);
+    const R v = syn_compute_b<R>(b, qs, tl, th);
+    int mm, nnl;
+    syn_pos(mm, nnl);
     if (2 * R0 + mm < n0 && 2 * C0 + nnl < n1)
         out[(int64_t)b * out_bstride + (int64_t)(2 * R0 + mm) * n1 + 2 * C0 + nnl] = v;
 }
@@ -318,7 +360,7 @@ __global__ void __launch_bounds__(NT) k_sara_syn0(const R *__restrict__ coef, co
                                                   int64_t sll_bstride, const R *__restrict__ dirac, R scale,
                                                   R *__restrict__ out) {
     __shared__ R qs[4 * SEXT * SEXT];
-    __shared__ R tl[2 * TS * SEXT], th[2 * TS * SEXT];
+    __shared__ R tl[2 * TS * TP], th[2 * TS * TP];
     const int tpd1 = (L1 / 2 + TS - 1) / TS;
     const int R0 = (blockIdx.x / tpd1) * TS, C0 = (blockIdx.x % tpd1) * TS;
     const int h0 = L0 >> 1, h1 = L1 >> 1;
@@ -334,9 +376,10 @@ __global__ void __launch_bounds__(NT) k_sara_syn0(const R *__restrict__ coef, co
     for (int b = 0; b < N_WAVELETS; ++b) {
         syn_store(q, qs, 2 * b + 2);
         if (b + 1 < N_WAVELETS) load(q, b + 1);
-        acc += syn_compute_b<R>(b, R0, C0, qs, tl, th);
+        acc += syn_compute_b<R>(b, qs, tl, th);
     }
-    const int mm = threadIdx.x / (2 * TS), nnl = threadIdx.x % (2 * TS);
+    int mm, nnl;
+    syn_pos(mm, nnl);
     if ((2 * R0 + mm < L0) && (2 * C0 + nnl < L1)) {
         const int64_t idx = (int64_t)(2 * R0 + mm) * L1 + 2 * C0 + nnl;
         out[idx] = scale * ((dirac ? dirac[idx] : R(0)) + acc);

@@ -531,14 +531,12 @@ __global__ void k_block_norms(const double *__restrict__ partials, const int32_t
 // words) the two rows a half-warp touches fall in disjoint bank halves, so
 // the read-modify-write of the tile is free of bank conflicts.
 constexpr int GRID_MINV = 16;   // least visibilities per scattering warp
-template <typename R> struct GridCfg;
-template <> struct GridCfg<float> { static constexpr int NWARP = 8; };
-template <> struct GridCfg<double> { static constexpr int NWARP = 4; };
-
-template <typename R, int T, int MODE>
-__global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, cplx_t<R> *__restrict__ gpart) {
+// NW warps per CTA (4 or 8; FP64: 4): eight split a chunk finer, four
+// leave room for more CTAs per SM (the autotuner picks per problem).
+template <typename R, int T, int MODE, int NW>
+__global__ void __launch_bounds__(NW * 32) k_grid(VisArgs<R> A, cplx_t<R> *__restrict__ gpart) {
     using C = cplx_t<R>;
-    constexpr int NW = GridCfg<R>::NWARP, NT = NW * 32;
+    constexpr int NT = NW * 32;
     constexpr int E = T + HALO, P = E;   // P: pitch of the private tiles (8 mod 16 words)
     static_assert(P % 16 == 8, "private-tile pitch");
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -750,20 +748,22 @@ __global__ void __launch_bounds__(GridCfg<R>::NWARP * 32) k_grid(VisArgs<R> A, c
 // One CTA per active tile (a tile with chunks, or below/right of one):
 // grid[r][c] = sum of the partial tiles covering the cell, in a fixed order:
 // the cell's own tile's chunks, then the halo rows/columns of the tiles
-// above, left and above-left (periodic grid).  Tiles never touched by any
-// visibility stay zero from the initial clear.
+// above, left and above-left (periodic grid).  The grid is column-major
+// (element (r, c) at c K0 + r, the layout the inverse column pass reads):
+// the T x T sums, formed from row-major partial-tile reads, are transposed
+// in shared memory and written as whole column segments.  Tiles never
+// touched by any visibility stay zero from the initial clear.
 template <typename R, int T>
 __global__ void __launch_bounds__(256) k_combine(const cplx_t<R> *__restrict__ gpart,
                                                  const int32_t *__restrict__ tile_first,
                                                  const int32_t *__restrict__ tile_n,
-                                                 const int32_t *__restrict__ active, int K1, int nt0, int nt1,
+                                                 const int32_t *__restrict__ active, int K0, int nt0, int nt1,
                                                  cplx_t<R> *__restrict__ grid) {
     using C = cplx_t<R>;
     constexpr int E = T + HALO;
     __shared__ int f_s[4], n_s[4];
-    constexpr int PARTS = 4;                       // CTAs per tile, T/PARTS rows each
-    const int t = active[blockIdx.x / PARTS];
-    const int part = blockIdx.x % PARTS;
+    __shared__ C tr[T][T + 1];
+    const int t = active[blockIdx.x];
     const int t0 = t / nt1, t1 = t - t0 * nt1;
     if (threadIdx.x < 4) {
         const int up = (t0 + nt0 - 1) % nt0, left = (t1 + nt1 - 1) % nt1;
@@ -774,7 +774,7 @@ __global__ void __launch_bounds__(256) k_combine(const cplx_t<R> *__restrict__ g
     }
     __syncthreads();
     pdl_enter();
-    for (int e = part * (T * T / PARTS) + threadIdx.x; e < (part + 1) * (T * T / PARTS); e += 256) {
+    for (int e = threadIdx.x; e < T * T; e += 256) {
         const int lr = e / T, lc = e % T;
         C acc{0, 0};
 #pragma unroll 4
@@ -788,7 +788,12 @@ __global__ void __launch_bounds__(256) k_combine(const cplx_t<R> *__restrict__ g
         if (lr < HALO && lc < HALO)
             for (int k = 0; k < n_s[3]; ++k)
                 acc = cadd(acc, gpart[(int64_t)(f_s[3] + k) * E * E + (lr + T) * E + lc + T]);
-        grid[(int64_t)(t0 * T + lr) * K1 + t1 * T + lc] = acc;
+        tr[lc][lr] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < T * T; e += 256) {
+        const int lc = e / T, lr = e % T;
+        grid[(int64_t)(t1 * T + lc) * K0 + t0 * T + lr] = tr[lc][lr];
     }
 }
 
@@ -837,8 +842,8 @@ template <typename R> VisArgs<R> make_args(ppd_ctx *c) {
     return A;
 }
 
-template <typename R, int T> size_t grid_smem() {
-    constexpr int NW = GridCfg<R>::NWARP, E = T + HALO, P = E, SP = 33;
+template <typename R, int T, int NW> size_t grid_smem() {
+    constexpr int E = T + HALO, P = E, SP = 33;
     return (size_t)NW * E * P * sizeof(cplx_t<R>) + (size_t)NW * 8 * SP * sizeof(cplx_t<R>) +
            (size_t)NW * KB_J * SP * sizeof(R);
 }
@@ -871,30 +876,39 @@ int degrid_t(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const 
     return launch_end(c, site, s);
 }
 
+template <typename R, int T, int NW> int grid_launch(ppd_ctx *c, int mode, const VisArgs<R> &A, cudaStream_t s) {
+    const size_t sh = grid_smem<R, T, NW>();
+    PPD_CHECK(smem_attr((const void *)k_grid<R, T, GR_OP, NW>, (int)sh));
+    PPD_CHECK(smem_attr((const void *)k_grid<R, T, GR_OP_U, NW>, (int)sh));
+    PPD_CHECK(smem_attr((const void *)k_grid<R, T, GR_DUAL, NW>, (int)sh));
+    int site;
+    PPD_CHECK(launch_begin(c, mode == GR_DUAL ? "grid_dual" : "grid_op", s, &site));
+    auto k = mode == GR_OP     ? k_grid<R, T, GR_OP, NW>
+             : mode == GR_OP_U ? k_grid<R, T, GR_OP_U, NW>
+                               : k_grid<R, T, GR_DUAL, NW>;
+    launch(c, true, k, (unsigned)c->ch.n, NW * 32, sh, s, A, static_cast<cplx_t<R> *>(c->gpart));
+    return launch_end(c, site, s);
+}
+
 template <typename R, int T>
 int grid_t(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_t<R> *grid, cudaStream_t s,
            bool combine) {
     VisArgs<R> A = make_args<R>(c);
     A.op_in = in;
     A.perm = perm;
-    const size_t sh = grid_smem<R, T>();
-    PPD_CHECK(smem_attr((const void *)k_grid<R, T, GR_OP>, (int)sh));
-    PPD_CHECK(smem_attr((const void *)k_grid<R, T, GR_OP_U>, (int)sh));
-    PPD_CHECK(smem_attr((const void *)k_grid<R, T, GR_DUAL>, (int)sh));
-    constexpr int NT = GridCfg<R>::NWARP * 32;
     cplx_t<R> *gp = static_cast<cplx_t<R> *>(c->gpart);
     int site;
     if (c->ch.n > 0) {
-        PPD_CHECK(launch_begin(c, mode == GR_DUAL ? "grid_dual" : "grid_op", s, &site));
-        const unsigned nb = (unsigned)c->ch.n;
-        auto k = mode == GR_OP ? k_grid<R, T, GR_OP> : mode == GR_OP_U ? k_grid<R, T, GR_OP_U> : k_grid<R, T, GR_DUAL>;
-        launch(c, true, k, nb, NT, sh, s, A, gp);
-        PPD_CHECK(launch_end(c, site, s));
+        if constexpr (sizeof(R) == 4) {
+            PPD_CHECK((c->grid_nw == 4 ? grid_launch<R, T, 4>(c, mode, A, s) : grid_launch<R, T, 8>(c, mode, A, s)));
+        } else {
+            PPD_CHECK((grid_launch<R, T, 4>(c, mode, A, s)));
+        }
     }
     if (c->ch.n_active == 0 || !combine) return PPD_OK;
     PPD_CHECK(launch_begin(c, "grid_combine", s, &site));
-    launch(c, true, k_combine<R, T>, (unsigned)c->ch.n_active * 4, 256, 0, s, (const cplx_t<R> *)gp,
-           (const int32_t *)c->ch.tile_first, (const int32_t *)c->ch.tile_n, (const int32_t *)c->ch.active, c->K1,
+    launch(c, true, k_combine<R, T>, (unsigned)c->ch.n_active, 256, 0, s, (const cplx_t<R> *)gp,
+           (const int32_t *)c->ch.tile_first, (const int32_t *)c->ch.tile_n, (const int32_t *)c->ch.active, c->K0,
            c->K0 / T, c->K1 / T, grid);
     return launch_end(c, site, s);
 }

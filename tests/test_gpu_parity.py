@@ -367,7 +367,7 @@ def test_autotune_picks_a_candidate_and_keeps_parity():
     s.set_problem(p.omega, p.y, p.block, theta=p.theta, x_true=p.x_true)
     tile, chunk = ppd.ppd_autotune(s.ctx, 3)
     prm = s.params()
-    assert tile in (16, 32) and chunk in (512, 1024, 2048)
+    assert tile in (16, 32) and chunk in (512, 1024, 2048) and prm["grid_warps"] in (4, 8)
     assert prm["tile"] == tile and prm["chunk"] == chunk and abs(prm["eta"] - S.eta) <= 1e-12 * S.eta
     st = oppd.init_state(S)
     for _ in range(10):
@@ -377,6 +377,33 @@ def test_autotune_picks_a_candidate_and_keeps_parity():
     perm, _, _, _ = ppd.ppd_get_bins(s.ctx, p.M)
     assert np.array_equal(perm, nufft.visibility_order(p.omega, p.block, 2 * p.L, 2 * p.L, tile)[0])
     s.close()
+
+
+@pytest.mark.parametrize("warps", [4, 8])
+@pytest.mark.parametrize("tile", [16, 32])
+def test_gridding_warps_per_cta(warps, tile):
+    """Four or eight warps per gridding CTA (each warp a slice of the chunk):
+    the same operator and iterates as the oracle."""
+    p = problem("small", **SMALL)
+    S = oppd.make_setup(p.omega, p.y, p.theta, p.block, p.n_blocks, p.L, power_iters=400, x_true=p.x_true)
+    s = solver(p, F32, eta=S.eta, grid_warps=warps, tile=tile, chunk=512)
+    assert s.params()["grid_warps"] == warps
+    P = nufft.Plan(p.omega, p.L, theta=p.theta)
+    yv = np.random.default_rng(12).normal(size=p.M) + 1j * np.random.default_rng(13).normal(size=p.M)
+    assert rel(op_adjoint(s, yv, F32), nufft.phi_adjoint(yv, P)) <= TOL[F32]["op"]
+    st = oppd.init_state(S)
+    for _ in range(8):
+        oppd.iterate(st, S)
+    s.iterate(8)
+    assert rel(s.image(), st.x) <= TOL[F32]["img"]
+    s.close()
+
+
+def test_grid_warps_values_are_checked():
+    for prec, warps in ((F32, 6), (F64, 8), (F32, -4)):
+        with pytest.raises(ppd.PPDError) as e:
+            ppd.Solver(32, 1, precision=prec, grid_warps=warps)
+        assert e.value.status == ppd.PPD_ERR_INVALID_ARG
 
 
 # ----------------------------------------------------------------- batched group
