@@ -765,6 +765,7 @@ def main():
                    "replicas": world,
                    "launches": "overlapped (programmatic dependent launch)" if args.launch_overlap else "serial",
                    "gridding": {"tile": prm32["tile"], "chunk": prm32["chunk"], "work_items": prm32["n_chunks"],
+                                "grid_warps": prm32["grid_warps"], "degrid_threads": prm32["degrid_threads"],
                                 "autotuned": not args.no_autotune and args.tile == 0 and args.chunk == 0}},
         "snr_iters": snr_iters,
         "fp64_plain": {"iters_per_s": ips64, "snr_db_at_end": target, "seconds_all": wall64},

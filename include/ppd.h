@@ -121,8 +121,9 @@ typedef struct {
     double   stop_eps_factor;   /* 0 => 1.005 */
     int32_t  stop_every;        /* test the rule after every stop_every-th iteration of a
                                    ppd_iterate call (one host synchronisation each); 0 => 1 */
-    int32_t  grid_warps;        /* warps per gridding CTA: 4 or 8 in FP32 (4 only in FP64); 0 => 8
-                                   in FP32, 4 in FP64; ppd_autotune chooses it in FP32 */
+    int32_t  grid_warps;        /* warps per gridding CTA: 4 or 8 in FP32 (4 only in FP64); 0 =>
+                                   FP32: 8, or 4 when the gridding has more than 12 work items
+                                   per SM; FP64: 4; ppd_autotune chooses it in FP32 */
     uint64_t seed;              /* start vector of the norm estimate: 0 => all ones; otherwise
                                    x_i = 0.5 + 2^-53 (s_i >> 11), s_i the SplitMix64 output
                                    for counter seed + (i + 1) * 0x9E3779B97F4A7C15 */
@@ -131,6 +132,9 @@ typedef struct {
                                    in its stream drains (programmatic dependent launch, compute
                                    capability 9.0 and later); 0 (default): every kernel waits for
                                    its predecessor to finish.  Results are the same either way. */
+    int32_t  degrid_threads;    /* threads per degridding CTA: 128 or 256 in FP32 (256 only in
+                                   FP64); 0 => 256; ppd_autotune chooses it in FP32 */
+    int32_t  pad1;
 } ppd_config;
 
 /* Per-call statistics (ppd_iterate).  All norms are computed in double. */
@@ -163,7 +167,7 @@ typedef struct {
     double   psiw_norm_sq;      /* ||Psi W||_S^2 of the prior weights (1 when W = I) */
     double   alpha;             /* clip level of the prior step, kappa * ||Psi W||_S^2 */
     int32_t  grid_warps;        /* warps per gridding CTA */
-    int32_t  pad0;
+    int32_t  degrid_threads;    /* threads per degridding CTA */
 } ppd_params;
 
 /* Fill *cfg with the paper's defaults (n0 = n1 = 0 must still be set). */
@@ -238,13 +242,14 @@ PPD_API int ppd_get_params(ppd_ctx *ctx, ppd_params *out);
 PPD_API int ppd_get_bins(ppd_ctx *ctx, int64_t *perm, int32_t *base0, int32_t *base1, int32_t *count);
 
 /* Autotuner for the gridding work decomposition: for each tile side
- * T in {16, 32}, work-item size C in {512, 1024, 2048} (visibilities per
- * CTA) and, in FP32, gridding warps per CTA in {4, 8}, rebuilds the
- * visibility order from the inputs of the last ppd_set_visibilities /
- * ppd_set_weights calls, times `iters` PPD iterations with CUDA events and
- * keeps the fastest; eta is kept, the solver state is reset to zero.  The
- * chosen tile and work-item size are returned (either pointer may be NULL);
- * ppd_get_params reports all three.
+ * T in {16, 32} and work-item size C in {512, 1024, 2048} (visibilities per
+ * CTA) it rebuilds the visibility order from the inputs of the last
+ * ppd_set_visibilities / ppd_set_weights calls and, in FP32, tries gridding
+ * warps per CTA in {4, 8} and degridding threads per CTA in {128, 256}; it
+ * times `iters` PPD iterations of each candidate with CUDA events and keeps
+ * the fastest; eta is kept, the solver state is reset to zero.  The chosen
+ * tile and work-item size are returned (either pointer may be NULL);
+ * ppd_get_params reports all four.
  * Errors: NOT_READY, INVALID_ARG, OOM, CUDA. */
 PPD_API int ppd_autotune(ppd_ctx *ctx, int32_t iters, int32_t *tile_out, int32_t *chunk_out);
 

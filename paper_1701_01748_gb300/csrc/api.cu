@@ -689,6 +689,9 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
     if (k.chunk < 0) return fail(PPD_ERR_INVALID_ARG, "ppd_create: chunk must be >= 0");
     if (!(k.grid_warps == 0 || k.grid_warps == 4 || (k.grid_warps == 8 && k.precision == PPD_FP32_FP64NORMS)))
         return fail(PPD_ERR_INVALID_ARG, "ppd_create: grid_warps must be 0, 4 or (FP32) 8");
+    if (!(k.degrid_threads == 0 || k.degrid_threads == 256 ||
+          (k.degrid_threads == 128 && k.precision == PPD_FP32_FP64NORMS)))
+        return fail(PPD_ERR_INVALID_ARG, "ppd_create: degrid_threads must be 0, 256 or (FP32) 128");
     if (k.launch_overlap != 0 && k.launch_overlap != 1)
         return fail(PPD_ERR_INVALID_ARG, "ppd_create: launch_overlap must be 0 or 1");
     if (!(k.inner_tol >= 0) || !(k.stop_tol >= 0) || !(k.stop_eps_factor >= 0) || k.stop_every < 0 ||
@@ -711,6 +714,7 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
     if (c->K0 % c->T || c->K1 % c->T) c->T = 16;
     c->C = k.chunk ? k.chunk : 1024;
     c->grid_nw = k.grid_warps ? k.grid_warps : (c->is_f32 ? 8 : 4);
+    c->degrid_nt = k.degrid_threads ? k.degrid_threads : 256;
     c->beta = k.kb_beta > 0 ? k.kb_beta : 2.34 * KB_J;
     c->tau = k.tau;
     c->kappa = k.kappa;
@@ -965,6 +969,14 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
     }
     c->ch.n = nch;
     c->ch.nu = nu;
+    // default gridding CTA shape (unless configured or autotuned): eight
+    // warps while the chunks make few waves, four (more CTAs per SM) beyond
+    // twelve chunks per SM
+    if (c->cfg.grid_warps == 0 && !c->shape_tuned && c->is_f32) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        c->grid_nw = nch > 12LL * std::max(sms, 1) ? 4 : 8;
+    }
     c->ch.n_active = (int64_t)active.size();
     const size_t cbsz = 2 * c->rsz;
     const int E = c->T + HALO;
@@ -1268,6 +1280,7 @@ int ppd_get_params(ppd_ctx *c, ppd_params *o) {
     o->tile = c->T;
     o->chunk = c->C;
     o->grid_warps = c->grid_nw;
+    o->degrid_threads = c->degrid_nt;
     o->n_chunks = c->ch.n;
     o->M = c->M;
     o->psiw_norm_sq = c->psiw2;
@@ -1441,10 +1454,9 @@ int ppd_autotune(ppd_ctx *c, int32_t iters, int32_t *tile_out, int32_t *chunk_ou
     const bool hth = c->has_theta, hU = c->has_U, hep = c->has_eps;
     const bool timing = c->timing;
     c->timing = false;
-    auto rebuild = [&](int T, int C, int NW) {
+    auto rebuild = [&](int T, int C) {
         c->T = T;
         c->C = C;
-        c->grid_nw = NW;
         int st = ppd_set_visibilities(c, c->M, uv.data(), y.data(), blk.data());
         if (st == PPD_OK) st = ppd_set_weights(c, hth ? th.data() : nullptr, hU ? U.data() : nullptr,
                                                hep ? ep.data() : nullptr);
@@ -1454,26 +1466,35 @@ int ppd_autotune(ppd_ctx *c, int32_t iters, int32_t *tile_out, int32_t *chunk_ou
     PPD_CUDA(cudaEventCreate(&e0));
     PPD_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    int bt = c->T, bc = c->C, bw = c->grid_nw, st = PPD_OK;
+    int bt = c->T, bc = c->C, bw = c->grid_nw, bd = c->degrid_nt, st = PPD_OK;
     const std::vector<int> warps = c->is_f32 ? std::vector<int>{8, 4} : std::vector<int>{4};
+    const std::vector<int> dthreads = c->is_f32 ? std::vector<int>{256, 128} : std::vector<int>{256};
     for (int T : {16, 32}) {
         if (c->K0 % T || c->K1 % T || c->K0 < 2 * T || c->K1 < 2 * T) continue;
         for (int C : {512, 1024, 2048}) {
+            // the CTA shapes need no new visibility order, only a new graph
+            if ((st = rebuild(T, C))) break;
             for (int NW : warps) {
-                if ((st = rebuild(T, C, NW))) break;
-                if ((st = ppd_iterate(c, 3, nullptr))) break;
-                cudaEventRecord(e0, c->stream);
-                if ((st = ppd_iterate(c, iters, nullptr))) break;
-                cudaEventRecord(e1, c->stream);
-                cudaEventSynchronize(e1);
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) {
-                    best = ms;
-                    bt = T;
-                    bc = C;
-                    bw = NW;
+                for (int ND : dthreads) {
+                    c->grid_nw = NW;
+                    c->degrid_nt = ND;
+                    drop_graph(c);
+                    if ((st = ppd_iterate(c, 3, nullptr))) break;
+                    cudaEventRecord(e0, c->stream);
+                    if ((st = ppd_iterate(c, iters, nullptr))) break;
+                    cudaEventRecord(e1, c->stream);
+                    cudaEventSynchronize(e1);
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best) {
+                        best = ms;
+                        bt = T;
+                        bc = C;
+                        bw = NW;
+                        bd = ND;
+                    }
                 }
+                if (st) break;
             }
             if (st) break;
         }
@@ -1481,7 +1502,10 @@ int ppd_autotune(ppd_ctx *c, int32_t iters, int32_t *tile_out, int32_t *chunk_ou
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (st == PPD_OK) st = rebuild(bt, bc, bw);
+    c->grid_nw = bw;
+    c->degrid_nt = bd;
+    c->shape_tuned = true;
+    if (st == PPD_OK) st = rebuild(bt, bc);
     c->cfg.eta = eta_cfg;
     c->timing = timing;
     if (st) return st;

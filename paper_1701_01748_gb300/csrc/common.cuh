@@ -162,6 +162,8 @@ struct ppd_ctx {
     size_t rsz = 4;            // sizeof(real)
     int L0 = 0, L1 = 0, K0 = 0, K1 = 0, T = 32, C = 1024, levels = 4, d = 1;
     int grid_nw = 8;           // warps per gridding CTA (FP32: 4 or 8; FP64: 4)
+    int degrid_nt = 256;       // threads per degridding CTA (FP32: 128 or 256; FP64: 256)
+    bool shape_tuned = false;  // the autotuner fixed grid_nw and degrid_nt
     int64_t N = 0;
     double beta = 0;
     cudaStream_t stream = nullptr;

@@ -273,8 +273,10 @@ __device__ __forceinline__ void load_vis(const VisArgs<R> &A, int gi, VisIn<R> &
     }
 }
 
-template <typename R, int T, int MODE>
-__global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
+// NTD threads per CTA (256 or 128; FP64: 256): the autotuner picks per
+// problem, fewer threads giving more CTAs per SM and shorter barriers.
+template <typename R, int T, int MODE, int NTD>
+__global__ void __launch_bounds__(NTD, sizeof(R) == 4 ? 768 / NTD : 1)
     k_degrid(const __grid_constant__ CUtensorMap tmap, int use_tma, const cplx_t<R> *__restrict__ grid, VisArgs<R> A,
              int n_units, long long spin_first) {
     using C = cplx_t<R>;
@@ -342,7 +344,7 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
                 break;
             }
         } else {
-            for (int e = threadIdx.x; e < E * E; e += DG_NT) {
+            for (int e = threadIdx.x; e < E * E; e += NTD) {
                 const int r = e / E, cc = e % E;
                 tile[e] = grid[(int64_t)((row0 + r) % A.K0) * A.K1 + (col0 + cc) % A.K1];
             }
@@ -363,10 +365,10 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
         // prox output is kept in p, the previous point of the first test
         const bool keep_start = first_blk && A.inner_tol > 0;
         Acc<R> s_w, s_r;
-        for (int i = threadIdx.x; i < count; i += DG_NT) {
+        for (int i = threadIdx.x; i < count; i += NTD) {
             const int gi = start + i;
             VisIn<R> nx;   // the next visibility: of this unit, else the next unit's first
-            if (i + DG_NT < count) load_vis<R, MODE>(A, gi + DG_NT, nx);
+            if (i + NTD < count) load_vis<R, MODE>(A, gi + NTD, nx);
             const int lb0 = (cur.rc.packed & 0xffff) - row0, lb1 = ((cur.rc.packed >> 16) & 0xffff) - col0;
             R w0[KB_J], w1[KB_J];
             kb_weights(cur.rc.f0, w0, A.kbp, A.beta, A.inv_i0b);
@@ -408,12 +410,12 @@ __global__ void __launch_bounds__(DG_NT, sizeof(R) == 4 ? 3 : 1)
                 const R ex = phix.x - cur.y.x, ey = phix.y - cur.y.y;
                 s_r.add(ex * ex + ey * ey);
             }
-            if (i + DG_NT < count) cur = nx;
+            if (i + NTD < count) cur = nx;
         }
         // this thread's first visibility of the next unit (loaded during the
         // unit's reduction and barrier below)
         if (nxt < n_units && (int)threadIdx.x < A.u_count[nxt]) load_vis<R, MODE>(A, A.u_start[nxt] + threadIdx.x, cur);
-        if (MODE != DG_OP) cta_sum2<DG_NT>(s_w.get(), s_r.get(), A.partials + NPART * (int64_t)A.u_pos[u]);
+        if (MODE != DG_OP) cta_sum2<NTD>(s_w.get(), s_r.get(), A.partials + NPART * (int64_t)A.u_pos[u]);
         __syncthreads();   // the tile buffer is refilled two units later
     }
 }
@@ -848,7 +850,7 @@ template <typename R, int T, int NW> size_t grid_smem() {
            (size_t)NW * KB_J * SP * sizeof(R);
 }
 
-template <typename R, int T>
+template <typename R, int T, int NTD>
 int degrid_t(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const int64_t *perm, cudaStream_t s) {
     VisArgs<R> A = make_args<R>(c);
     A.op_out = out;
@@ -856,13 +858,13 @@ int degrid_t(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const 
     constexpr int E = T + HALO;
     const size_t tile_stride = ((size_t)E * E * sizeof(cplx_t<R>) + 127) / 128 * 128;
     const size_t sh = 2 * tile_stride;
-    PPD_CHECK(smem_attr((const void *)k_degrid<R, T, DG_OP>, (int)sh));
-    PPD_CHECK(smem_attr((const void *)k_degrid<R, T, DG_DUAL>, (int)sh));
-    PPD_CHECK(smem_attr((const void *)k_degrid<R, T, DG_FIRST>, (int)sh));
+    PPD_CHECK(smem_attr((const void *)k_degrid<R, T, DG_OP, NTD>, (int)sh));
+    PPD_CHECK(smem_attr((const void *)k_degrid<R, T, DG_DUAL, NTD>, (int)sh));
+    PPD_CHECK(smem_attr((const void *)k_degrid<R, T, DG_FIRST, NTD>, (int)sh));
     const int use_tma = (c->tma_ok && grid == c->grid_a) ? 1 : 0;
     if (c->ch.nu == 0) return PPD_OK;
     int per_sm = 0;
-    PPD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_degrid<R, T, DG_DUAL>, DG_NT, sh));
+    PPD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_degrid<R, T, DG_DUAL, NTD>, NTD, sh));
     if (per_sm < 1) per_sm = 1;
     int sms = 0;
     PPD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
@@ -871,8 +873,10 @@ int degrid_t(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const 
     int site;
     PPD_CHECK(launch_begin(c, mode == DG_OP ? "degrid_op" : "degrid_dual", s, &site));
     const long long sf = c->wait_first;
-    auto k = mode == DG_OP ? k_degrid<R, T, DG_OP> : mode == DG_DUAL ? k_degrid<R, T, DG_DUAL> : k_degrid<R, T, DG_FIRST>;
-    launch(c, true, k, nb, DG_NT, sh, s, c->tmap_a, use_tma, grid, A, nch, sf);
+    auto k = mode == DG_OP     ? k_degrid<R, T, DG_OP, NTD>
+             : mode == DG_DUAL ? k_degrid<R, T, DG_DUAL, NTD>
+                               : k_degrid<R, T, DG_FIRST, NTD>;
+    launch(c, true, k, nb, NTD, sh, s, c->tmap_a, use_tma, grid, A, nch, sf);
     return launch_end(c, site, s);
 }
 
@@ -976,7 +980,13 @@ int make_kb_poly(ppd_ctx *c) {
 
 template <typename R>
 int degrid(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const int64_t *perm, cudaStream_t s) {
-    return c->T == 16 ? degrid_t<R, 16>(c, mode, grid, out, perm, s) : degrid_t<R, 32>(c, mode, grid, out, perm, s);
+    if constexpr (sizeof(R) == 4) {
+        if (c->degrid_nt == 128)
+            return c->T == 16 ? degrid_t<R, 16, 128>(c, mode, grid, out, perm, s)
+                              : degrid_t<R, 32, 128>(c, mode, grid, out, perm, s);
+    }
+    return c->T == 16 ? degrid_t<R, 16, 256>(c, mode, grid, out, perm, s)
+                      : degrid_t<R, 32, 256>(c, mode, grid, out, perm, s);
 }
 
 template <typename R>

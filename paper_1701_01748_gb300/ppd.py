@@ -42,7 +42,8 @@ class ppd_config(ct.Structure):
                 ("chunk", ct.c_int32), ("power_iters", ct.c_int32), ("power_tol", ct.c_double),
                 ("stream", ct.c_void_p), ("inner_solver", ct.c_int32), ("inner_tol", ct.c_double),
                 ("stop_tol", ct.c_double), ("stop_eps_factor", ct.c_double), ("stop_every", ct.c_int32),
-                ("grid_warps", ct.c_int32), ("seed", ct.c_uint64), ("norm_method", ct.c_int32), ("launch_overlap", ct.c_int32)]
+                ("grid_warps", ct.c_int32), ("seed", ct.c_uint64), ("norm_method", ct.c_int32), ("launch_overlap", ct.c_int32),
+                ("degrid_threads", ct.c_int32), ("pad1", ct.c_int32)]
 
 
 class ppd_stats(ct.Structure):
@@ -59,7 +60,7 @@ class ppd_params(ct.Structure):
                 ("n_chunks", ct.c_int64),
                 ("M", ct.c_int64), ("convergence_lhs", ct.c_double),
                 ("psiw_norm_sq", ct.c_double), ("alpha", ct.c_double), ("grid_warps", ct.c_int32),
-                ("pad0", ct.c_int32)]
+                ("degrid_threads", ct.c_int32)]
 
 
 class PPDError(RuntimeError):

@@ -367,7 +367,8 @@ def test_autotune_picks_a_candidate_and_keeps_parity():
     s.set_problem(p.omega, p.y, p.block, theta=p.theta, x_true=p.x_true)
     tile, chunk = ppd.ppd_autotune(s.ctx, 3)
     prm = s.params()
-    assert tile in (16, 32) and chunk in (512, 1024, 2048) and prm["grid_warps"] in (4, 8)
+    assert tile in (16, 32) and chunk in (512, 1024, 2048)
+    assert prm["grid_warps"] in (4, 8) and prm["degrid_threads"] in (128, 256)
     assert prm["tile"] == tile and prm["chunk"] == chunk and abs(prm["eta"] - S.eta) <= 1e-12 * S.eta
     st = oppd.init_state(S)
     for _ in range(10):
@@ -379,16 +380,19 @@ def test_autotune_picks_a_candidate_and_keeps_parity():
     s.close()
 
 
-@pytest.mark.parametrize("warps", [4, 8])
+@pytest.mark.parametrize("warps,dthreads", [(4, 128), (8, 256), (4, 256), (8, 128)])
 @pytest.mark.parametrize("tile", [16, 32])
-def test_gridding_warps_per_cta(warps, tile):
-    """Four or eight warps per gridding CTA (each warp a slice of the chunk):
-    the same operator and iterates as the oracle."""
+def test_gridding_and_degridding_cta_shapes(warps, dthreads, tile):
+    """Four or eight warps per gridding CTA (each warp a slice of the chunk),
+    128 or 256 threads per degridding CTA: the same operators and iterates as
+    the oracle."""
     p = problem("small", **SMALL)
     S = oppd.make_setup(p.omega, p.y, p.theta, p.block, p.n_blocks, p.L, power_iters=400, x_true=p.x_true)
-    s = solver(p, F32, eta=S.eta, grid_warps=warps, tile=tile, chunk=512)
-    assert s.params()["grid_warps"] == warps
+    s = solver(p, F32, eta=S.eta, grid_warps=warps, degrid_threads=dthreads, tile=tile, chunk=512)
+    assert s.params()["grid_warps"] == warps and s.params()["degrid_threads"] == dthreads
     P = nufft.Plan(p.omega, p.L, theta=p.theta)
+    x = np.random.default_rng(11).random((p.L, p.L))
+    assert rel(op_forward(s, x, F32), nufft.phi(x, P)) <= TOL[F32]["op"]
     yv = np.random.default_rng(12).normal(size=p.M) + 1j * np.random.default_rng(13).normal(size=p.M)
     assert rel(op_adjoint(s, yv, F32), nufft.phi_adjoint(yv, P)) <= TOL[F32]["op"]
     st = oppd.init_state(S)
@@ -399,10 +403,11 @@ def test_gridding_warps_per_cta(warps, tile):
     s.close()
 
 
-def test_grid_warps_values_are_checked():
-    for prec, warps in ((F32, 6), (F64, 8), (F32, -4)):
+def test_cta_shape_values_are_checked():
+    for prec, kw in ((F32, dict(grid_warps=6)), (F64, dict(grid_warps=8)), (F32, dict(grid_warps=-4)),
+                     (F32, dict(degrid_threads=64)), (F64, dict(degrid_threads=128))):
         with pytest.raises(ppd.PPDError) as e:
-            ppd.Solver(32, 1, precision=prec, grid_warps=warps)
+            ppd.Solver(32, 1, precision=prec, **kw)
         assert e.value.status == ppd.PPD_ERR_INVALID_ARG
 
 
