@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <map>
 #include <mutex>
 #include <set>
 #include <string>
@@ -27,14 +28,18 @@ int fail(int code, const std::string &msg) {
 }
 
 int smem_attr(const void *fn, int bytes) {
+    // the attribute is one value per device and kernel: it only ever grows,
+    // so that contexts of different sizes sharing a kernel (the mixed-radix
+    // FFT passes) never lower the limit another context's launches rely on
     static std::mutex mu;
-    static std::set<std::tuple<int, const void *, int>> done;
+    static std::map<std::pair<int, const void *>, int> limit;
     int dev = 0;
     PPD_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lock(mu);
-    if (done.count(std::make_tuple(dev, fn, bytes))) return PPD_OK;
+    auto it = limit.find(std::make_pair(dev, fn));
+    if (it != limit.end() && it->second >= bytes) return PPD_OK;
     PPD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    done.insert(std::make_tuple(dev, fn, bytes));
+    limit[std::make_pair(dev, fn)] = bytes;
     return PPD_OK;
 }
 

@@ -109,8 +109,8 @@ struct DeviceGuard {
 };
 
 // Lets kernel `fn` launch with `bytes` of dynamic shared memory on the
-// current device (the attribute is per device: it is set once for every
-// device, kernel and size seen).
+// current device (the attribute is one value per device and kernel, raised
+// to the largest size any context has asked for).
 int smem_attr(const void *fn, int bytes);
 
 #define PPD_CHECK(call)                 \

@@ -131,3 +131,26 @@ def test_unsupported_sizes_are_refused():
         with pytest.raises(ppd.PPDError) as e:
             ppd.ppd_create(cfg)
         assert e.value.status == ppd.PPD_ERR_UNSUPPORTED
+
+
+def test_contexts_of_different_sizes_share_the_mixed_radix_kernels():
+    """Two contexts whose row passes take the mixed-radix kernels with more
+    than 48 KB of shared memory each (K1 = 3840, then 3200): the second
+    context's set-up must not lower the limit the first one's launches need
+    (the shared-memory attribute is one value per kernel)."""
+    big = problem(16, 1920, M=3000, n_blocks=2)
+    small = problem(16, 1600, M=3000, n_blocks=2)
+    a = solver(big, F32, eta=1.0)
+    b = solver(small, F32, eta=1.0)
+    for s, p in ((a, big), (b, small), (a, big)):
+        x = np.random.default_rng(6).random((p.L, p.L1))
+        xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+        yd = torch.empty((p.M, 2), dtype=torch.float32, device="cuda")
+        ppd.ppd_op_forward(s.ctx, xd.data_ptr(), yd.data_ptr(), stream())
+        torch.cuda.synchronize()
+        y = yd.cpu().double().numpy() @ np.array([1.0, 1j])
+        assert rel(y, nufft.phi(x, nufft.Plan(p.omega, p.L, p.L1, theta=p.theta))) <= TOL[F32]["op"]
+    a.iterate(3)
+    assert np.isfinite(a.image()).all()
+    a.close()
+    b.close()
