@@ -87,8 +87,8 @@ def algorithmic_bytes_per_step(L: int, M: int, levels: int = 4, rsz: int = 4, xt
     syn += 8 * rsz * (ll(0) + det(0)) + rsz * N
     return {
         "degrid_dual": (16 + 5 * c) * M + c * K2,     # record, v, y, p in; z, w out; grid once
-        "grid_dual": (16 + 5 * c) * M + c * K2,       # record, y, w, z in; v, p out; grid once
-        "grid_combine": c * K2,
+        "grid_dual": (16 + 5 * c) * M,                # record, y, w, z in; v, p out (per-chunk partial tiles: overhead)
+        "grid_combine": c * K2,                       # the combined grid written once (partial tiles in: overhead)
         "subiter": (16 + 4 * c) * M,
         "fft_fwd_rows": rsz * N + c * 2 * N,
         "fft_fwd_cols": c * 2 * N + c * K2,
@@ -531,6 +531,9 @@ def main():
     ap.add_argument("--isnr", type=float, default=30.0, help="input SNR (dB) of the study problems")
     ap.add_argument("--autotune", action="store_true", help="batch workloads: autotune each problem's gridding")
     ap.add_argument("--no-autotune", action="store_true", help="main bench: keep the library's default gridding")
+    ap.add_argument("--grid-warps", type=int, default=0, help="warps per gridding CTA (0: library default)")
+    ap.add_argument("--degrid-threads", type=int, default=0,
+                    help="threads per degridding CTA (0: library default)")
     ap.add_argument("--launch-overlap", action="store_true",
                     help="kernels start while their predecessor drains (programmatic dependent launch)")
     ap.add_argument("--quick", action="store_true",
@@ -594,8 +597,10 @@ def main():
     sp = stream.cuda_stream
 
     def make(prec, **kw):
+        shape = dict(grid_warps=args.grid_warps, degrid_threads=args.degrid_threads) \
+            if prec == ppd.PPD_FP32_FP64NORMS else {}
         s = ppd.Solver(p.L, p.n_blocks, precision=prec, stream=sp, tile=args.tile, chunk=args.chunk,
-                       launch_overlap=int(args.launch_overlap), **kw)
+                       launch_overlap=int(args.launch_overlap), **shape, **kw)
         s.set_problem(p.omega, p.y, p.block, theta=p.theta, x_true=p.x_true)
         return s
 
