@@ -612,7 +612,9 @@ def main():
         s32 = make(ppd.PPD_FP32_FP64NORMS)
         if not args.no_autotune and args.tile == 0 and args.chunk == 0:
             _log("autotuning the gridding work decomposition")
-            ppd.ppd_autotune(s32.ctx, 10)
+            # enough iterations per candidate that the timing is stable (a 512^2
+            # iteration is ~0.14 ms), fewer for the large workloads
+            ppd.ppd_autotune(s32.ctx, 50 if p.M < 10_000_000 else 10)
         _log("set-up FP64 (eta by power iteration)")
         s64 = make(ppd.PPD_FP64_PLAIN)
     # the zero state of each solver, restored before every measured run (the

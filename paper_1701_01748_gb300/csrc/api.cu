@@ -770,9 +770,11 @@ int ppd_create(ppd_ctx **out, const ppd_config *cfg) {
     if ((st = dalloc(&c->prim_part, 3 * (size_t)std::max(c->n_prim_blocks, c->L0)))) return bail(st);
     if ((st = dalloc(&c->mask_cur, (size_t)c->d + N_BASES)) || (st = dalloc(&c->blk_seen, (size_t)c->d)) ||
         (st = dalloc(&c->regrid_d, 1)) || (st = dalloc(&c->inner_state, (size_t)c->d)) ||
-        (st = dalloc(&c->inner_steps, (size_t)c->d)) || (st = dalloc(&c->stop_flag, 1)))
+        (st = dalloc(&c->inner_steps, (size_t)c->d)) || (st = dalloc(&c->stop_flag, 1)) ||
+        (st = dalloc(&c->dg_claim, 2)))
         return bail(st);
     if (cudaMemsetAsync(c->mask_cur, 1, (size_t)c->d + N_BASES, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->dg_claim, 0, 2 * sizeof(int), c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->blk_seen, 0, (size_t)c->d, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->regrid_d, 0, sizeof(int), c->stream) != cudaSuccess)
         return bail(fail(PPD_ERR_CUDA, "ppd_create: initialisation"));
@@ -802,7 +804,8 @@ void ppd_destroy(ppd_ctx *c) {
                     (void *)c->col_fwd, c->fft_tmp_inv})
         dfree(p);
     for (void *p : {c->wgt, c->wcoef, (void *)c->mask_all, (void *)c->mask_cur, (void *)c->blk_seen,
-                    (void *)c->regrid_d, (void *)c->inner_state, (void *)c->inner_steps, (void *)c->stop_flag})
+                    (void *)c->regrid_d, (void *)c->inner_state, (void *)c->inner_steps, (void *)c->stop_flag,
+                    (void *)c->dg_claim})
         dfree(p);
     for (void *p : {c->x, c->xt, c->g, c->ut, c->xtrue, c->u, c->wtmp, c->wtmp2, c->grid_a, c->grid_v, c->fft_tmp,
                     c->tw0, c->tw1, c->twst0, c->twst1, c->deap0, c->deap1, c->kbpoly, (void *)c->prim_part, (void *)c->stat_out,

@@ -219,6 +219,7 @@ struct ppd_ctx {
     int *inner_state = nullptr, *inner_steps = nullptr;
     int next_step = 0, next_test_in = 0;
     int *stop_flag = nullptr;                          // global stopping rule (device, 1 int)
+    int *dg_claim = nullptr;                           // degridding work counters (device, 2 ints, zero between launches)
     cudaStream_t stream2 = nullptr;                   // prior (SARA) branch of the iteration
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     void *gpart = nullptr;           // n_chunks x (T+HALO)^2 complex

@@ -109,6 +109,9 @@ template <typename R> struct VisArgs {
     // work units of the degridding and sub-iteration kernels: runs of at
     // most DG_NT visibilities of one chunk, each with its partial slot
     const int32_t *u_start, *u_count, *u_chunk, *u_order;
+    // the degridding's work counters: [0] next position in u_order to claim,
+    // [1] CTAs finished (both back to zero after every launch)
+    int *claim;
     int K0, K1, ntile1;
     float kbp[KB_NC];   // the FP32 weight polynomials (kb_weights)
     double beta, inv_i0b;
@@ -249,8 +252,11 @@ template <typename R> __device__ int inner_stopped(const VisArgs<R> &A, int blk)
 // partial slot of the unit = (||w - y||^2, ||Theta G a - y||^2)
 //
 // Persistent CTAs walk the work units (the chunks) in the order u_order
-// (largest first) with a fixed stride, so that every CTA gets one of the
-// heavy units of the dense centre of the coverage before the light ones.
+// (largest first): CTA b starts at position b, then every CTA claims its
+// next position from a counter when it starts a unit (so the light units
+// of the tail go to whichever CTAs finish first); the last CTA to finish
+// resets the counters for the next launch.  Which CTA computes a unit does
+// not change any result.
 // The (T+8)^2 grid tile of the next unit is fetched by TMA into the other of
 // two shared buffers while the current unit is computed (interior tiles;
 // tiles that wrap around the grid edge are loaded with plain loads when they
@@ -310,16 +316,25 @@ __global__ void __launch_bounds__(NTD, sizeof(R) == 4 ? 768 / NTD : 1)
     };
     uint32_t ph = 0u;   // bit b: parity of the next completion of bar[b]
     const int32_t *ord = A.u_order;
-    if (threadIdx.x == 0 && (int)blockIdx.x < n_units) issue(ord[blockIdx.x], 0);
+    __shared__ int claim_s;
+    auto claim = [&](int from) {   // thread 0: the next position after `from` (n_units: none)
+        claim_s = from < n_units ? (int)gridDim.x + atomicAdd(A.claim, 1) : n_units;
+    };
+    if (threadIdx.x == 0) {
+        if ((int)blockIdx.x < n_units) issue(ord[blockIdx.x], 0);
+        claim(blockIdx.x);
+    }
     VisIn<R> cur;
     if ((int)blockIdx.x < n_units && (int)threadIdx.x < A.u_count[ord[blockIdx.x]])
         load_vis<R, MODE>(A, A.u_start[ord[blockIdx.x]] + threadIdx.x, cur);
+    __syncthreads();
+    int nxt_pos = min(claim_s, n_units);
     int it = 0;
-    for (int iu = blockIdx.x; iu < n_units; iu += gridDim.x, ++it) {
+    for (int iu = blockIdx.x; iu < n_units; iu = nxt_pos, nxt_pos = min(claim_s, n_units), ++it) {
         const int buf = it & 1;
         C *tile = reinterpret_cast<C *>(smem_raw + buf * TILE_STRIDE);
         const int u = ord[iu];
-        const int nxt = iu + gridDim.x < n_units ? ord[iu + gridDim.x] : n_units;
+        const int nxt = nxt_pos < n_units ? ord[nxt_pos] : n_units;
         if (threadIdx.x == 0 && nxt < n_units) issue(nxt, buf ^ 1);
         const int start = A.u_start[u], count = A.u_count[u], ch = A.u_chunk[u];
         int row0, col0;
@@ -416,7 +431,18 @@ __global__ void __launch_bounds__(NTD, sizeof(R) == 4 ? 768 / NTD : 1)
         // unit's reduction and barrier below)
         if (nxt < n_units && (int)threadIdx.x < A.u_count[nxt]) load_vis<R, MODE>(A, A.u_start[nxt] + threadIdx.x, cur);
         if (MODE != DG_OP) cta_sum2<NTD>(s_w.get(), s_r.get(), A.partials + NPART * (int64_t)A.u_pos[u]);
+        // the position after the next unit (read after the barrier below;
+        // rewritten only after the next unit's first barrier)
+        if (threadIdx.x == 0) claim(nxt_pos);
         __syncthreads();   // the tile buffer is refilled two units later
+    }
+    // no claim follows this CTA's exit: the last CTA out resets the counters
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(A.claim + 1, 1) == (int)gridDim.x - 1) {
+            A.claim[0] = 0;
+            A.claim[1] = 0;
+        }
     }
 }
 
@@ -830,6 +856,7 @@ template <typename R> VisArgs<R> make_args(ppd_ctx *c) {
     A.u_count = c->ch.u_count;
     A.u_chunk = c->ch.u_chunk;
     A.u_order = c->ch.u_order;
+    A.claim = c->dg_claim;
     A.eps = c->eps_d;
     A.err = c->err;
     A.bmask = c->rand_on ? c->mask_cur : nullptr;
