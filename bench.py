@@ -87,8 +87,8 @@ def algorithmic_bytes_per_step(L: int, M: int, levels: int = 4, rsz: int = 4, xt
     syn += 8 * rsz * (ll(0) + det(0)) + rsz * N
     return {
         "degrid_dual": (16 + 5 * c) * M + c * K2,     # record, v, y, p in; z, w out; grid once
-        "grid_dual": (16 + 5 * c) * M + c * K2,       # record, y, w, z in; v, p out; the combined grid written once
-                                                      # (per-chunk partial tiles: overhead)
+        "grid_dual": (16 + 5 * c) * M,                # record, y, w, z in; v, p out (per-chunk partial tiles: overhead)
+        "grid_combine": c * K2,                       # the combined grid written once (partial tiles in: overhead)
         "subiter": (16 + 4 * c) * M,
         "fft_fwd_rows": rsz * N + c * 2 * N,
         "fft_fwd_cols": c * 2 * N + c * K2,

@@ -124,7 +124,7 @@ void free_vis(ppd_ctx *c) {
     for (void *p : {c->rec, c->theta_v, c->y, c->v, c->z, c->w, c->p, c->y_raw, (void *)c->perm,
                     (void *)c->count_cell, (void *)c->ch.start, (void *)c->ch.count, (void *)c->ch.tile,
                     (void *)c->ch.block, (void *)c->ch.tile_first, (void *)c->ch.tile_n, (void *)c->ch.blk_ptr,
-                    (void *)c->ch.u_start, (void *)c->ch.u_count, (void *)c->ch.u_chunk, (void *)c->ch.u_pos, (void *)c->ch.u_order, (void *)c->ch.order, (void *)c->ch.tile_need, (void *)c->ch.tile_cnt, (void *)c->partials, (void *)c->scale, (void *)c->resid2,
+                    (void *)c->ch.u_start, (void *)c->ch.u_count, (void *)c->ch.u_chunk, (void *)c->ch.u_pos, (void *)c->ch.u_order, (void *)c->ch.order, (void *)c->ch.active, (void *)c->partials, (void *)c->scale, (void *)c->resid2,
                     (void *)c->eps_d, (void *)c->mu_d, c->gpart})
         dfree(p);
     c->rec = c->theta_v = c->y = c->v = c->z = c->w = c->p = c->y_raw = c->gpart = nullptr;
@@ -929,16 +929,6 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
         for (int t = 0; t < ntiles; ++t)
             if (mark[t]) active.push_back(t);
     }
-    // partial tiles reaching each tile: its own chunks and those of the tiles
-    // above, left and above-left (their halos), periodic
-    std::vector<int32_t> tneed(ntiles, 0);
-    {
-        const int nt0 = c->K0 / c->T, nt1 = c->K1 / c->T;
-        for (int t = 0; t < ntiles; ++t) {
-            const int a0 = t / nt1, a1 = t % nt1, up = (a0 + nt0 - 1) % nt0, left = (a1 + nt1 - 1) % nt1;
-            tneed[t] = tn[t] + tn[up * nt1 + a1] + tn[a0 * nt1 + left] + tn[up * nt1 + left];
-        }
-    }
     // FFT pruning: rows/columns the degridding reads (tiles with chunks plus
     // their halo) and rows/columns the gridding can write (active tiles)
     std::vector<char> rf(c->K0, 0), cf(c->K1, 0), ri(c->K0, 0), ci(c->K1, 0);
@@ -995,6 +985,7 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
         c->grid_nw = nch > 12LL * std::max(sms, 1) ? 4 : 8;
     }
+    c->ch.n_active = (int64_t)active.size();
     const size_t cbsz = 2 * c->rsz;
     const int E = c->T + HALO;
     if ((st = dalloc(&c->ch.start, nch)) || (st = dalloc(&c->ch.count, nch)) || (st = dalloc(&c->ch.tile, nch)) ||
@@ -1002,7 +993,7 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
         (st = dalloc(&c->ch.tile_n, ntiles)) || (st = dalloc(&c->ch.blk_ptr, c->d + 1)) ||
         (st = dalloc(&c->ch.u_start, nu)) ||
         (st = dalloc(&c->ch.u_count, nu)) || (st = dalloc(&c->ch.u_chunk, nu)) || (st = dalloc(&c->ch.u_pos, nu)) || (st = dalloc(&c->ch.u_order, nu)) || (st = dalloc(&c->ch.order, nch)) ||
-        (st = dalloc(&c->ch.tile_need, ntiles)) || (st = dalloc(&c->ch.tile_cnt, ntiles)) ||
+        (st = dalloc(&c->ch.active, active.size())) ||
         (st = dalloc(&c->partials, 2 * NPART * (size_t)nu)) ||
         (st = dalloc(&c->scale, c->d)) || (st = dalloc(&c->resid2, c->d)) || (st = dalloc(&c->eps_d, c->d)) ||
         (st = dalloc(&c->mu_d, c->d)) || (st = dalloc_bytes(&c->gpart, (size_t)nch * E * E * cbsz)) ||
@@ -1042,8 +1033,7 @@ int ppd_set_visibilities(ppd_ctx *c, int64_t M, const double *uv, const double *
         (e = cudaMemcpy(c->ch.u_pos, upos.data(), nu * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->ch.u_order, uord.data(), nu * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->ch.order, cord.data(), nch * 4, cudaMemcpyHostToDevice)) ||
-        (e = cudaMemcpy(c->ch.tile_need, tneed.data(), ntiles * 4, cudaMemcpyHostToDevice)) ||
-        (e = cudaMemset(c->ch.tile_cnt, 0, ntiles * 4)) ||
+        (e = cudaMemcpy(c->ch.active, active.data(), active.size() * 4, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->perm, c->perm_h.data(), M * 8, cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(c->y_raw, yraw_sorted.data(), 2 * M * 8, cudaMemcpyHostToDevice))) {
         free_vis(c);

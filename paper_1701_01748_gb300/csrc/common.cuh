@@ -141,10 +141,6 @@ struct Chunks {
     int64_t n = 0;
     int32_t *start = nullptr, *count = nullptr, *tile = nullptr, *block = nullptr;   // device
     int32_t *tile_first = nullptr, *tile_n = nullptr;                                // device, n_tiles
-    // device, n_tiles: partial tiles reaching each tile (own chunks and the
-    // chunks of the tiles above, left, above-left) and the gridding's
-    // delivery counters (zero between launches)
-    int32_t *tile_need = nullptr, *tile_cnt = nullptr;
     // work units of the degridding and sub-iterations: runs of at most UNIT
     // visibilities of one chunk (device arrays of nu entries); unit u writes
     // its norm partials to slot u_pos[u], block b owns slots blk_ptr[b] ..
@@ -154,7 +150,8 @@ struct Chunks {
     int32_t *u_start = nullptr, *u_count = nullptr, *u_chunk = nullptr, *u_pos = nullptr, *u_order = nullptr;
     int32_t *blk_ptr = nullptr;
     int32_t *order = nullptr;    // chunks by decreasing size (the gridding's CTA order)
-
+    int32_t *active = nullptr;   // tiles the combine pass writes (device)
+    int64_t n_active = 0;
 };
 
 }  // namespace ppd
@@ -331,7 +328,7 @@ int subiter(ppd_ctx *c, cudaStream_t s, int only_first = 0, double beta = 0.0, i
 int block_norms(ppd_ctx *c, int which, cudaStream_t s);
 template <typename R>
 int grid_vis(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm_in, cplx_t<R> *grid,
-             cudaStream_t s);
+             cudaStream_t s, bool combine = true);
 
 template <typename R>
 int grid_vis_into(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_t<R> *grid, void *gpart,

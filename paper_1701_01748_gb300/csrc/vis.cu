@@ -112,13 +112,6 @@ template <typename R> struct VisArgs {
     // the degridding's work counters: [0] next position in u_order to claim,
     // [1] CTAs finished (both back to zero after every launch)
     int *claim;
-    // the gridding's combine: per tile its first chunk and chunk count, the
-    // partial tiles that reach it (its own chunks and the halos of the
-    // chunks of the tiles above, left and above-left), the count delivered
-    // so far in this launch (zero between launches), the column-major grid
-    const int32_t *tile_first, *tile_n, *tile_need;
-    int *tile_cnt;
-    cplx_t<R> *grid_out;
     int K0, K1, ntile1;
     float kbp[KB_NC];   // the FP32 weight polynomials (kb_weights)
     double beta, inv_i0b;
@@ -566,71 +559,6 @@ __global__ void k_block_norms(const double *__restrict__ partials, const int32_t
 // words) the two rows a half-warp touches fall in disjoint bank halves, so
 // the read-modify-write of the tile is free of bank conflicts.
 constexpr int GRID_MINV = 16;   // least visibilities per scattering warp
-// Sum of the partial tiles covering tile t, in a fixed order (the tile's own
-// chunks, then the halo rows / columns of the chunks of the tiles above, left
-// and above-left; periodic grid), transposed in shared memory (tr: T x (T+1))
-// and written to the column-major grid (element (r, c) at c K0 + r) as whole
-// column segments.  Every thread of the CTA takes part.  The partial tiles
-// are read past L1 (other CTAs wrote them during this launch).
-template <typename R, int T, int NT>
-__device__ void combine_tile(const VisArgs<R> &A, int t, const cplx_t<R> *gpart, cplx_t<R> *tr) {
-    using C = cplx_t<R>;
-    constexpr int E = T + HALO;
-    const int nt1 = A.ntile1, nt0 = A.K0 / T, t0 = t / nt1, t1 = t - t0 * nt1;
-    const int up = (t0 + nt0 - 1) % nt0, left = (t1 + nt1 - 1) % nt1;
-    const int f0 = A.tile_first[t], n0 = A.tile_n[t];
-    const int f1 = A.tile_first[up * nt1 + t1], n1 = A.tile_n[up * nt1 + t1];
-    const int f2 = A.tile_first[t0 * nt1 + left], n2 = A.tile_n[t0 * nt1 + left];
-    const int f3 = A.tile_first[up * nt1 + left], n3 = A.tile_n[up * nt1 + left];
-    for (int e = threadIdx.x; e < T * T; e += NT) {
-        const int lr = e / T, lc = e % T;
-        C acc{0, 0};
-        for (int k = 0; k < n0; ++k) acc = cadd(acc, __ldcg(gpart + (int64_t)(f0 + k) * E * E + lr * E + lc));
-        if (lr < HALO)
-            for (int k = 0; k < n1; ++k) acc = cadd(acc, __ldcg(gpart + (int64_t)(f1 + k) * E * E + (lr + T) * E + lc));
-        if (lc < HALO)
-            for (int k = 0; k < n2; ++k) acc = cadd(acc, __ldcg(gpart + (int64_t)(f2 + k) * E * E + lr * E + lc + T));
-        if (lr < HALO && lc < HALO)
-            for (int k = 0; k < n3; ++k)
-                acc = cadd(acc, __ldcg(gpart + (int64_t)(f3 + k) * E * E + (lr + T) * E + lc + T));
-        tr[lc * (T + 1) + lr] = acc;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < T * T; e += NT) {
-        const int lc = e / T, lr = e % T;
-        A.grid_out[(int64_t)(t1 * T + lc) * A.K0 + t0 * T + lr] = tr[lc * (T + 1) + lr];
-    }
-    __syncthreads();
-}
-
-// After a CTA's partial tile of a chunk of tile tl is in memory: counts it
-// for the four tiles it reaches (own, below, right, below-right) and
-// combines every tile for which it was the last partial tile to arrive
-// (then clears that tile's counter for the next launch).
-template <typename R, int T, int NT>
-__device__ void deliver(const VisArgs<R> &A, int tl, const cplx_t<R> *gpart, cplx_t<R> *tr) {
-    __shared__ int todo[4];
-    __syncthreads();   // this CTA's partial-tile writes are issued
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const int nt1 = A.ntile1, nt0 = A.K0 / T, t0 = tl / nt1, t1 = tl - t0 * nt1;
-        const int d0 = (t0 + 1) % nt0, r1 = (t1 + 1) % nt1;
-        auto arrive = [&](int t) { return atomicAdd(A.tile_cnt + t, 1) + 1 == A.tile_need[t] ? t : -1; };
-        todo[0] = arrive(tl);
-        todo[1] = arrive(d0 * nt1 + t1);
-        todo[2] = arrive(t0 * nt1 + r1);
-        todo[3] = arrive(d0 * nt1 + r1);
-        __threadfence();
-    }
-    __syncthreads();
-    for (int q = 0; q < 4; ++q) {
-        const int t = todo[q];
-        if (t < 0) continue;
-        combine_tile<R, T, NT>(A, t, gpart, tr);
-        if (threadIdx.x == 0) A.tile_cnt[t] = 0;
-    }
-}
-
 // NW warps per CTA (4 or 8; FP64: 4): eight split a chunk finer, four
 // leave room for more CTAs per SM (the autotuner picks per problem).
 template <typename R, int T, int MODE, int NW>
@@ -662,10 +590,7 @@ __global__ void __launch_bounds__(NW * 32) k_grid(VisArgs<R> A, cplx_t<R> *__res
     // a block outside the active set D keeps v_j, so its chunks' partial
     // tiles from the last gridding still hold G^dagger Theta^dagger v_j
     const bool act = MODE != GR_DUAL || !A.bmask || A.bmask[blk];
-    if (!act && !(A.regrid && *A.regrid)) {
-        deliver<R, T, NT>(A, tl, gpart, priv);
-        return;
-    }
+    if (!act && !(A.regrid && *A.regrid)) return;
     R c = 0;
     // Algorithm 2 stopped early (stopping test): the prox output is the p
     // the stopping step kept, not P_B of the current w
@@ -845,7 +770,59 @@ __global__ void __launch_bounds__(NW * 32) k_grid(VisArgs<R> A, cplx_t<R> *__res
         for (int k = 0; k < nwu; ++k) s = cadd(s, priv[k * E * P + r * P + cc]);
         out[e] = s;
     }
-    deliver<R, T, NT>(A, tl, gpart, priv);   // the private tiles are free now
+}
+
+// ----------------------------------------------------------------- combine
+// One CTA per active tile (a tile with chunks, or below/right of one):
+// grid[r][c] = sum of the partial tiles covering the cell, in a fixed order:
+// the cell's own tile's chunks, then the halo rows/columns of the tiles
+// above, left and above-left (periodic grid).  The grid is column-major
+// (element (r, c) at c K0 + r, the layout the inverse column pass reads):
+// the T x T sums, formed from row-major partial-tile reads, are transposed
+// in shared memory and written as whole column segments.  Tiles never
+// touched by any visibility stay zero from the initial clear.
+template <typename R, int T>
+__global__ void __launch_bounds__(256) k_combine(const cplx_t<R> *__restrict__ gpart,
+                                                 const int32_t *__restrict__ tile_first,
+                                                 const int32_t *__restrict__ tile_n,
+                                                 const int32_t *__restrict__ active, int K0, int nt0, int nt1,
+                                                 cplx_t<R> *__restrict__ grid) {
+    using C = cplx_t<R>;
+    constexpr int E = T + HALO;
+    __shared__ int f_s[4], n_s[4];
+    __shared__ C tr[T][T + 1];
+    const int t = active[blockIdx.x];
+    const int t0 = t / nt1, t1 = t - t0 * nt1;
+    if (threadIdx.x < 4) {
+        const int up = (t0 + nt0 - 1) % nt0, left = (t1 + nt1 - 1) % nt1;
+        const int tt = threadIdx.x == 0 ? t : threadIdx.x == 1 ? up * nt1 + t1
+                       : threadIdx.x == 2 ? t0 * nt1 + left : up * nt1 + left;
+        f_s[threadIdx.x] = tile_first[tt];
+        n_s[threadIdx.x] = tile_n[tt];
+    }
+    __syncthreads();
+    pdl_enter();
+    for (int e = threadIdx.x; e < T * T; e += 256) {
+        const int lr = e / T, lc = e % T;
+        C acc{0, 0};
+#pragma unroll 4
+        for (int k = 0; k < n_s[0]; ++k) acc = cadd(acc, gpart[(int64_t)(f_s[0] + k) * E * E + lr * E + lc]);
+        if (lr < HALO)
+            for (int k = 0; k < n_s[1]; ++k)
+                acc = cadd(acc, gpart[(int64_t)(f_s[1] + k) * E * E + (lr + T) * E + lc]);
+        if (lc < HALO)
+            for (int k = 0; k < n_s[2]; ++k)
+                acc = cadd(acc, gpart[(int64_t)(f_s[2] + k) * E * E + lr * E + lc + T]);
+        if (lr < HALO && lc < HALO)
+            for (int k = 0; k < n_s[3]; ++k)
+                acc = cadd(acc, gpart[(int64_t)(f_s[3] + k) * E * E + (lr + T) * E + lc + T]);
+        tr[lc][lr] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < T * T; e += 256) {
+        const int lc = e / T, lr = e % T;
+        grid[(int64_t)(t1 * T + lc) * K0 + t0 * T + lr] = tr[lc][lr];
+    }
 }
 
 template <typename R> VisArgs<R> make_args(ppd_ctx *c) {
@@ -880,10 +857,6 @@ template <typename R> VisArgs<R> make_args(ppd_ctx *c) {
     A.u_chunk = c->ch.u_chunk;
     A.u_order = c->ch.u_order;
     A.claim = c->dg_claim;
-    A.tile_first = c->ch.tile_first;
-    A.tile_n = c->ch.tile_n;
-    A.tile_need = c->ch.tile_need;
-    A.tile_cnt = c->ch.tile_cnt;
     A.eps = c->eps_d;
     A.err = c->err;
     A.bmask = c->rand_on ? c->mask_cur : nullptr;
@@ -949,11 +922,13 @@ template <typename R, int T, int NW> int grid_launch(ppd_ctx *c, int mode, const
 }
 
 template <typename R, int T>
-int grid_t(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_t<R> *grid, cudaStream_t s) {
+int grid_t(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_t<R> *grid, cudaStream_t s,
+           bool combine) {
     VisArgs<R> A = make_args<R>(c);
     A.op_in = in;
     A.perm = perm;
-    A.grid_out = grid;
+    cplx_t<R> *gp = static_cast<cplx_t<R> *>(c->gpart);
+    int site;
     if (c->ch.n > 0) {
         if constexpr (sizeof(R) == 4) {
             PPD_CHECK((c->grid_nw == 4 ? grid_launch<R, T, 4>(c, mode, A, s) : grid_launch<R, T, 8>(c, mode, A, s)));
@@ -961,7 +936,12 @@ int grid_t(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_
             PPD_CHECK((grid_launch<R, T, 4>(c, mode, A, s)));
         }
     }
-    return PPD_OK;
+    if (c->ch.n_active == 0 || !combine) return PPD_OK;
+    PPD_CHECK(launch_begin(c, "grid_combine", s, &site));
+    launch(c, true, k_combine<R, T>, (unsigned)c->ch.n_active, 256, 0, s, (const cplx_t<R> *)gp,
+           (const int32_t *)c->ch.tile_first, (const int32_t *)c->ch.tile_n, (const int32_t *)c->ch.active, c->K0,
+           c->K0 / T, c->K1 / T, grid);
+    return launch_end(c, site, s);
 }
 
 }  // namespace
@@ -1037,8 +1017,10 @@ int degrid(ppd_ctx *c, int mode, const cplx_t<R> *grid, cplx_t<R> *out, const in
 }
 
 template <typename R>
-int grid_vis(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_t<R> *grid, cudaStream_t s) {
-    return c->T == 16 ? grid_t<R, 16>(c, mode, in, perm, grid, s) : grid_t<R, 32>(c, mode, in, perm, grid, s);
+int grid_vis(ppd_ctx *c, int mode, const cplx_t<R> *in, const int64_t *perm, cplx_t<R> *grid, cudaStream_t s,
+             bool combine) {
+    return c->T == 16 ? grid_t<R, 16>(c, mode, in, perm, grid, s, combine)
+                      : grid_t<R, 32>(c, mode, in, perm, grid, s, combine);
 }
 
 template <typename R> int subiter(ppd_ctx *c, cudaStream_t s, int only_first, double beta, int write_p) {
@@ -1075,8 +1057,8 @@ template int grid_vis_into<double>(ppd_ctx *, int, const double2 *, const int64_
                                    cudaStream_t);
 template int degrid<float>(ppd_ctx *, int, const float2 *, float2 *, const int64_t *, cudaStream_t);
 template int degrid<double>(ppd_ctx *, int, const double2 *, double2 *, const int64_t *, cudaStream_t);
-template int grid_vis<float>(ppd_ctx *, int, const float2 *, const int64_t *, float2 *, cudaStream_t);
-template int grid_vis<double>(ppd_ctx *, int, const double2 *, const int64_t *, double2 *, cudaStream_t);
+template int grid_vis<float>(ppd_ctx *, int, const float2 *, const int64_t *, float2 *, cudaStream_t, bool);
+template int grid_vis<double>(ppd_ctx *, int, const double2 *, const int64_t *, double2 *, cudaStream_t, bool);
 template int subiter<float>(ppd_ctx *, cudaStream_t, int, double, int);
 template int subiter<double>(ppd_ctx *, cudaStream_t, int, double, int);
 
