@@ -96,9 +96,9 @@ def test_ppd_two_iterations_at_1024():
     s.close()
 
 
-def test_ppd_iterations_at_2048_with_the_combine_pass():
-    """From K = 4096 on the iteration sums the gridding's partial tiles in a
-    separate combine pass before the inverse column FFT: 2048^2 image, 200k
+def test_ppd_iterations_at_2048_with_the_separate_row_passes():
+    """From K = 4096 on the iteration runs the row passes and the primal step
+    as separate kernels (no fused row/primal kernel): 2048^2 image, 200k
     visibilities in 8 blocks, three iterations against the oracle."""
     p = synth.make_problem("c2048", L=2048, M=200_000, n_blocks=8, uv_sigma=0.1, seed=1710, compact=True)
     eta = 2.09e-7              # a fixed step for the parity check (1 / 4.78e6, 1000 power steps; the iterates
