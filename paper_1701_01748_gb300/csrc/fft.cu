@@ -227,18 +227,16 @@ template <typename R> __host__ __device__ constexpr int rows_per_cta(int K) { re
 // columns per CTA in a column pass of the power-of-two core.  K <= 1024:
 // the fewest columns the 256-thread butterfly split allows (1024 / K, at
 // least 1), the most CTAs for these latency-bound passes (measured: four
-// columns per CTA at K = 1024 made both column passes 40 % slower).  From
-// K = 2048 on, every row of a strip is at least one 32-byte sector (4 float /
-// 2 double columns; measured at K = 2048: forward pass 41 -> 31 us); beyond
-// that, 32 KB of strip, at most 128 KB.
+// columns per CTA at K = 1024 made both column passes 40 % slower).  At
+// K = 2048 every row of a strip is one 32-byte sector (4 float / 2 double
+// columns; measured: forward pass 41 -> 31 us).  Longer columns: one per
+// CTA (the column-major inputs make its reads contiguous; 64 KB of strip in
+// FP32 at K = 8192 leaves room for three CTAs per SM, where two columns took
+// 128 KB and one CTA: 7.27 -> 6.96 ms per 4096^2 iteration).
 template <typename R> __host__ __device__ constexpr int cols_per_cta(int K) {
     constexpr int csz = 2 * (int)sizeof(R);
     if (K <= 1024) return 1024 / K > 1 ? 1024 / K : 1;
-    if (K == 2048) return 32 / csz;
-    const int w32 = (32 * 1024) / (K * csz), wmin = 32 / csz;
-    int w = w32 > wmin ? w32 : wmin;
-    while (w > 1 && (long long)w * K * csz > 128 * 1024) w /= 2;
-    return w < K ? w : K;
+    return K == 2048 ? 32 / csz : 1;
 }
 // twiddles go to shared memory beside nseq sequences when a CTA then stays
 // within 100 KB (two or more CTAs per SM), else they are read through the
