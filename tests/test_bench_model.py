@@ -25,9 +25,33 @@ def test_byte_model_counts_each_array_once():
         q = N / 4 ** (lev + 1)
         ana += 8 * 4 * ((0 if lev == 0 else 4 * q) + 2 * 3 * q + (2 * q if lev == 3 else q))
     assert b["sara_analysis"] == pytest.approx(ana)
+    # gridding: record, y, w, z read; p, v written; its per-chunk partial tiles are
+    # overhead, and the combined grid is counted once, in the combine pass
+    assert b["grid_dual"] == 16 * M + 5 * 8 * M
+    assert b["grid_combine"] == 8 * K2
+    # the column passes: the L x K temporary and the K x K grid once each
+    assert b["fft_fwd_cols"] == b["fft_inv_cols"] == 8 * 2 * N + 8 * K2
     # FP64 doubles every term
     b64 = bench.algorithmic_bytes_per_step(L, M, rsz=8)
     assert b64["fft_fwd_cols"] == 2 * b["fft_fwd_cols"]
+
+
+def test_committed_dram_summaries_parse_and_name_their_sources():
+    """Every profiles/ncu_dram_<workload>.txt names the sources digest it was
+    captured on and holds one line per kernel timing name that the bench's
+    byte model knows, with positive bytes per launch."""
+    prof = os.path.join(bench.ROOT, "profiles")
+    names = set(bench.algorithmic_bytes_per_step(64, 1000))
+    files = [f for f in os.listdir(prof) if f.startswith("ncu_dram_") and f.endswith(".txt")]
+    assert {"ncu_dram_c2_512.txt", "ncu_dram_c3_1024.txt", "ncu_dram_c5_4096.txt"} <= set(files)
+    for f in files:
+        lines = [ln.strip() for ln in open(os.path.join(prof, f)) if ln.strip()]
+        digests = [ln for ln in lines if ln.startswith("sources sha256:")]
+        assert len(digests) == 1 and len(digests[0].split(":", 1)[1].strip()) == 64, f
+        rows = [ln.split() for ln in lines if not ln.startswith("#") and ":" not in ln]
+        assert rows, f
+        for k, v, n, t in rows:
+            assert k in names and float(v) > 0 and int(n) >= 1 and float(t) > 0, (f, k)
 
 
 def test_traffic_only_for_the_sources_it_was_captured_on(tmp_path, monkeypatch):
